@@ -1,0 +1,27 @@
+"""Plain FP64 CPU oracle of the FEAST interval eigensolver (arXiv 1605.08771).
+
+This package is test infrastructure: it is imported only by the tests, by the
+package smoke check and by the CPU-baseline leg of the benchmark.  The product
+path (the CUDA library and its Python binding) never imports or runs it, and
+the oracle shares no code with that path.
+
+Modules:
+  quadrature  Gauss-Legendre nodes, contour nodes/weights, scalar filter (Eqs. 2-3)
+  dense       LU with partial pivoting, triangular solves, Cholesky-QR, Gram
+              orthogonalisation, Jacobi eigensolver
+  feast       filter application, Rayleigh-Ritz, selection, FEAST / XFEAST /
+              RFEAST drivers (Appendix algorithms)
+
+Parity pins: every function is checked in tests/test_oracle_*.py against
+closed forms, brute force or independent library routines.  The XFEAST and
+RFEAST iterates (which pairs are selected at each round, the residual
+histories) have no independent pin beyond the end result on planted spectra:
+their parity is "parity unpinned" beyond that end result.
+"""
+from .quadrature import gauss_legendre, contour_nodes, rational_filter  # noqa: F401
+from .dense import (lu_factor, lu_solve, lu_solve_adjoint, lu_unpack,  # noqa: F401
+                    cholesky_upper, cholqr, cholqr2, jacobi_eigh, gram_eig_orth,
+                    round_robin_pairs, solve_right_upper, CholeskyBreakdown)
+from .feast import (factor_shifts, filter_apply, rayleigh_ritz, select_pairs,  # noqa: F401
+                    feast_solve, norm_estimate, orthonormalize, FeastResult,
+                    PLAIN, XFEAST, RFEAST)

@@ -1,0 +1,138 @@
+"""Pins of the oracle's filter, Rayleigh-Ritz, selection and the three FEAST
+drivers against planted spectra (closed form), brute-force dense eig and the
+paper's qualitative claims."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle.feast import inside, select_pairs
+from workloads import (make_problem, random_subspace, spectrum_config1, spectrum_paper,
+                       spectrum_uniform)
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_setups.json")
+
+
+def small_problem(n=80, m_in=8, cplx=False, seed=3, m0=12, n_c=8, bulk=10.0):
+    lam, a, b = spectrum_uniform(n, m_in, seed=seed, bulk=bulk)
+    return make_problem("small", lam, a, b, m0, n_c, seed=seed, complex_=cplx)
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+@pytest.mark.parametrize("n_c", [3, 8])
+def test_filter_equals_closed_form_on_planted(cplx, n_c):
+    # rho(A) X = Q diag(rho(lambda)) Q^H X for A = Q diag(lambda) Q^H (Eq. 3)
+    P = small_problem(n=60, m_in=6, cplx=cplx, n_c=n_c)
+    X = random_subspace(P.n, 5, seed=9, complex_=cplx)
+    F = O.factor_shifts(P.A, P.lmin, P.lmax, n_c)
+    got = O.filter_apply(F, X)
+    rho = O.rational_filter(P.lam, F.z, F.w)
+    ref = P.Q @ (rho[:, None] * (P.Q.conj().T @ X))
+    if not cplx:
+        ref = ref.real
+        assert not np.iscomplexobj(got)
+    assert np.abs(got - ref).max() < 1e-12 * np.abs(X).max()
+
+
+def test_rayleigh_ritz_recovers_planted_pairs():
+    P = small_problem(n=50, m_in=5)
+    ins = inside(P.lam, P.lmin, P.lmax)
+    rp = O.rayleigh_ritz(P.A, P.Q[:, ins], P.anorm)
+    np.testing.assert_allclose(rp.lam, P.inside, atol=1e-13 * P.anorm)
+    assert rp.res.max() < 1e-14
+
+
+def test_select_pairs_rules():
+    lam = np.array([-3.0, -0.5, 0.1, 0.7, 2.0, 5.0])
+    res = np.array([1e-9, 0.3, 1e-12, 1e-4, 1e-10, 1e-2])
+    # 3 inside; fill 2 from outside by ascending residual (-3.0 then 2.0)
+    sel = select_pairs(lam, res, -1.0, 1.0, 5)
+    assert list(sel) == [0, 1, 2, 3, 4]
+    # more inside than m0: keep the lowest residuals inside
+    sel = select_pairs(lam, res, -1.0, 1.0, 2)
+    assert list(sel) == [2, 3]
+    # ties in residual broken by ascending lambda
+    sel = select_pairs(np.array([-4.0, 4.0, 0.0]), np.array([1e-3, 1e-3, 0.5]), -1.0, 1.0, 2)
+    assert list(sel) == [0, 2]
+
+
+def test_norm_estimate_is_close_lower_bound():
+    P = small_problem(n=120, m_in=10, bulk=30.0)
+    est = O.norm_estimate(P.A)
+    assert 0.9 * P.anorm <= est <= P.anorm * (1 + 1e-12)
+
+
+def _check_result(r, P, tol=1e-10):
+    assert r.status == 0
+    assert r.lam.size == P.inside.size
+    np.testing.assert_allclose(r.lam, P.inside, rtol=1e-10, atol=1e-12 * P.anorm)
+    assert r.res.max() <= tol
+    # span of returned vectors equals the planted invariant subspace
+    Qi = P.inside_vectors
+    ang = np.linalg.norm(r.X - Qi @ (Qi.conj().T @ r.X), 2)
+    assert ang < 1e-8
+
+
+@pytest.mark.parametrize("variant", [O.PLAIN, O.XFEAST, O.RFEAST])
+@pytest.mark.parametrize("cplx", [False, True])
+def test_feast_variants_find_planted_pairs(variant, cplx):
+    P = small_problem(n=90, m_in=8, cplx=cplx, m0=12)
+    X0 = random_subspace(P.n, P.m0, seed=5, complex_=cplx)
+    r = O.feast_solve(P.A, P.lmin, P.lmax, P.m0, 8, 1e-10, X0, variant=variant,
+                      anorm=P.anorm, max_iter=60)
+    _check_result(r, P)
+
+
+def test_feast_matches_brute_force_eig():
+    P = small_problem(n=64, m_in=6, cplx=True, m0=9)
+    X0 = random_subspace(P.n, P.m0, seed=2, complex_=True)
+    r = O.feast_solve(P.A, P.lmin, P.lmax, P.m0, 8, 1e-11, X0, anorm=P.anorm)
+    ev = np.linalg.eigvalsh(P.A)
+    np.testing.assert_allclose(r.lam, ev[(ev > P.lmin) & (ev < P.lmax)], atol=1e-12 * P.anorm)
+
+
+def test_feast_empty_interval_returns_zero_pairs():
+    lam = np.concatenate([np.linspace(-10, -2, 30), np.linspace(2, 10, 30)])
+    P = make_problem("gap", lam, -1.0, 1.0, 8, 8, seed=4)
+    X0 = random_subspace(P.n, 8, seed=1)
+    r = O.feast_solve(P.A, -1.0, 1.0, 8, 8, 1e-10, X0, anorm=P.anorm)
+    assert r.status == 0 and r.lam.size == 0
+
+
+def test_feast_rate_law_config1():
+    # rate |rho(lambda_{m0+1})| / min_{in I} |rho| (Sect. I, with |rho| ranking)
+    # predicts the iterations of plain FEAST on the n = 500 workload
+    lam, a, b = spectrum_config1(0)
+    P = make_problem("c1", lam, a, b, 60, 8, seed=0)
+    z, w = O.contour_nodes(a, b, 8)
+    rho = np.abs(O.rational_filter(lam, z, w))
+    srt = np.sort(rho)[::-1]
+    rate = srt[60] / rho[inside(lam, a, b)].min()
+    predicted = np.log(1e-10) / np.log(rate)
+    X0 = random_subspace(P.n, 60, seed=1)
+    r = O.feast_solve(P.A, a, b, 60, 8, 1e-10, X0, anorm=P.anorm)
+    _check_result(r, P)
+    assert abs(r.iterations - predicted) <= 2.5
+
+
+@pytest.mark.slow
+def test_expanded_variants_beat_feast_on_dense_spectrum():
+    # Sect. III: on the "Dense" n = 545 matrix XFEAST and RFEAST (m0 = 51) need
+    # fewer linear right-hand sides than FEAST to reach the same residual.
+    g = json.load(open(GOLDEN))["fig1_fig2_matrices"]
+    lam, a, b = spectrum_paper("dense", seed=0, n=g["n"], m_in=g["inside"])
+    m0 = g["m0_expanded_variants"]
+    n_c = g["n_c_dense"]
+    P = make_problem("dense", lam, a, b, m0, n_c, seed=0)
+    F = O.factor_shifts(P.A, a, b, n_c)
+    X0 = random_subspace(P.n, m0, seed=1)
+    rhs = {}
+    for v in [O.PLAIN, O.XFEAST, O.RFEAST]:
+        r = O.feast_solve(P.A, a, b, m0, n_c, 1e-10, X0, variant=v, anorm=P.anorm,
+                          factors=F, max_iter=100)
+        _check_result(r, P)
+        rhs[v] = r.filters * n_c * m0
+    assert rhs[O.XFEAST] < rhs[O.PLAIN]
+    assert rhs[O.RFEAST] < rhs[O.PLAIN]

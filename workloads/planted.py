@@ -1,0 +1,179 @@
+"""Planted-spectrum test matrices and seeded starting subspaces.
+
+A planted problem is A = Q diag(lambda) Q^H with Q drawn from the QR
+factorisation of a seeded Gaussian matrix, so the eigenpairs inside the search
+interval (lambda_min, lambda_max) are known in closed form.  The spectra follow
+the workloads of the paper (Sect. III: n = 545, 50 eigenvalues in [-1, 1], the
+other 495 either spread over [1.01, 20.81] or packed in [1.01, 1.1]) and the
+larger edge-clustered workloads the eigensolver is benchmarked on.
+
+Everything here is input generation: no quadrature, no factorisation, no
+Rayleigh-Ritz.  All arrays are returned in column-major (Fortran) order, the
+layout the C interface expects.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# Planted eigenvalues keep at least this distance from an interval edge, so an
+# open interval test on them is never decided by rounding.
+EDGE_MARGIN = 1e-12
+
+
+@dataclass
+class Problem:
+    """One planted Hermitian (or real symmetric) eigenproblem."""
+
+    name: str
+    A: np.ndarray            # n x n, Fortran order, float64 or complex128
+    lam: np.ndarray          # all n planted eigenvalues, ascending
+    Q: np.ndarray | None     # n x n eigenvectors (columns match lam), or None
+    lmin: float
+    lmax: float
+    m0: int
+    n_c: int
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return self.A.shape[0]
+
+    @property
+    def is_complex(self) -> bool:
+        return np.iscomplexobj(self.A)
+
+    @property
+    def inside(self) -> np.ndarray:
+        """Planted eigenvalues strictly inside (lmin, lmax), ascending."""
+        return self.lam[(self.lam > self.lmin) & (self.lam < self.lmax)]
+
+    @property
+    def inside_vectors(self) -> np.ndarray:
+        mask = (self.lam > self.lmin) & (self.lam < self.lmax)
+        return self.Q[:, mask]
+
+    @property
+    def anorm(self) -> float:
+        """Exact spectral norm max |lambda| of the planted matrix."""
+        return float(np.max(np.abs(self.lam)))
+
+
+def _uniform_avoiding(rng, count, lo, hi, lmin, lmax, gap):
+    """`count` draws uniform on [lo, lmin - gap) U (lmax + gap, hi]."""
+    left = max(0.0, (lmin - gap) - lo)
+    right = max(0.0, hi - (lmax + gap))
+    total = left + right
+    u = rng.uniform(0.0, total, size=count)
+    out = np.where(u < left, lo + u, (lmax + gap) + (u - left))
+    return out
+
+
+def spectrum_edge_clusters(rng, n, m_in, lmin, lmax, bulk_lo, bulk_hi,
+                           n_edge_in=0, n_edge_out=0, width=0.0):
+    """Eigenvalues with clusters hugging both interval edges.
+
+    m_in eigenvalues lie strictly inside (lmin, lmax); n_edge_in of them per
+    edge sit within `width` inside that edge.  n_edge_out per edge sit within
+    `width` outside it.  The rest of the n eigenvalues are uniform on
+    [bulk_lo, bulk_hi] outside the interval (and outside the edge bands when
+    there are outside clusters).
+    """
+    assert 2 * n_edge_in <= m_in
+    n_out_bulk = n - m_in - 2 * n_edge_out
+    assert n_out_bulk >= 0
+    parts = []
+    if n_edge_in:
+        parts.append(lmin + rng.uniform(EDGE_MARGIN, width, n_edge_in))
+        parts.append(lmax - rng.uniform(EDGE_MARGIN, width, n_edge_in))
+    inner = m_in - 2 * n_edge_in
+    lo_in = lmin + (width if n_edge_in else EDGE_MARGIN)
+    hi_in = lmax - (width if n_edge_in else EDGE_MARGIN)
+    parts.append(rng.uniform(lo_in, hi_in, inner))
+    if n_edge_out:
+        parts.append(lmin - rng.uniform(EDGE_MARGIN, width, n_edge_out))
+        parts.append(lmax + rng.uniform(EDGE_MARGIN, width, n_edge_out))
+    gap = width if n_edge_out else EDGE_MARGIN
+    parts.append(_uniform_avoiding(rng, n_out_bulk, bulk_lo, bulk_hi, lmin, lmax, gap))
+    lam = np.sort(np.concatenate(parts))
+    assert lam.size == n
+    assert np.sum((lam > lmin) & (lam < lmax)) == m_in
+    return lam
+
+
+def spectrum_config1(seed=0):
+    """n = 500 real symmetric: 40 of 500 eigenvalues in I = [-1, 1], 5 of them
+    within 1e-3 of each edge; the other 460 uniform in [-10, 10] outside I."""
+    rng = np.random.default_rng(seed)
+    lam = spectrum_edge_clusters(rng, 500, 40, -1.0, 1.0, -10.0, 10.0,
+                                 n_edge_in=5, n_edge_out=0, width=1e-3)
+    return lam, -1.0, 1.0
+
+
+def spectrum_config2(seed=0, n=8192, m_in=200, edge_in=30, edge_out=60,
+                     width=1e-4, bulk=50.0):
+    """Complex Hermitian edge-clustered spectrum: m_in eigenvalues in [-1, 1]
+    with edge_in packed within `width` inside each edge, edge_out packed within
+    `width` outside each edge, the rest uniform in [-bulk, bulk] outside I.
+    Defaults are the n = 8192 single-large-problem workload."""
+    rng = np.random.default_rng(seed)
+    lam = spectrum_edge_clusters(rng, n, m_in, -1.0, 1.0, -bulk, bulk,
+                                 n_edge_in=edge_in, n_edge_out=edge_out, width=width)
+    return lam, -1.0, 1.0
+
+
+def spectrum_paper(kind, seed=0, n=545, m_in=50):
+    """The two n = 545 spectra of the paper's Sect. III experiments: 50
+    eigenvalues in I = [-1, 1]; the other 495 in [1.01, 20.81] ("Sparse") or
+    [1.01, 1.1] ("Dense").  The in-interval eigenvalues are drawn uniformly."""
+    rng = np.random.default_rng(seed)
+    hi = {"sparse": 20.81, "dense": 1.1}[kind]
+    inside = rng.uniform(-1.0 + EDGE_MARGIN, 1.0 - EDGE_MARGIN, m_in)
+    outside = rng.uniform(1.01, hi, n - m_in)
+    return np.sort(np.concatenate([inside, outside])), -1.0, 1.0
+
+
+def spectrum_uniform(n, m_in, seed=0, lmin=-1.0, lmax=1.0, bulk=10.0):
+    """Uniform spectrum with exactly m_in eigenvalues in (lmin, lmax)."""
+    rng = np.random.default_rng(seed)
+    lam = spectrum_edge_clusters(rng, n, m_in, lmin, lmax, lmin - bulk, lmax + bulk)
+    return lam, lmin, lmax
+
+
+def haar_unitary(n, seed, complex_=False):
+    """Q from the Householder QR of a seeded N(0,1) (or complex Gaussian)
+    matrix, with the phases of diag(R) absorbed so Q is Haar distributed."""
+    rng = np.random.default_rng(seed)
+    G = rng.standard_normal((n, n))
+    if complex_:
+        G = (G + 1j * rng.standard_normal((n, n))) / np.sqrt(2.0)
+    Qm, R = np.linalg.qr(G)
+    d = np.diag(R)
+    ph = d / np.abs(d)
+    return np.asfortranarray(Qm * ph[None, :])
+
+
+def planted_matrix(Q, lam):
+    """A = Q diag(lam) Q^H, made exactly Hermitian, Fortran order."""
+    A = (Q * lam[None, :]) @ Q.conj().T
+    A = 0.5 * (A + A.conj().T)
+    return np.asfortranarray(A)
+
+
+def random_subspace(n, m, seed, complex_=False):
+    """Seeded N(0,1) starting subspace X0 (n x m), Fortran order.  Complex
+    entries have independent N(0, 1/2) real and imaginary parts."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0x5EED]))
+    X = rng.standard_normal((n, m))
+    if complex_:
+        X = (X + 1j * rng.standard_normal((n, m))) / np.sqrt(2.0)
+    return np.asfortranarray(X)
+
+
+def make_problem(name, lam, lmin, lmax, m0, n_c, seed=0, complex_=False, keep_q=True):
+    Q = haar_unitary(lam.size, seed + 1000, complex_)
+    A = planted_matrix(Q, lam)
+    return Problem(name=name, A=A, lam=lam, Q=Q if keep_q else None,
+                   lmin=lmin, lmax=lmax, m0=m0, n_c=n_c,
+                   meta={"seed": seed, "complex": complex_})
