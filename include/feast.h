@@ -1,0 +1,179 @@
+/*
+ * FEAST interval eigensolver for dense Hermitian / real symmetric matrices on
+ * one NVIDIA GB300 (sm_103a).  C ABI: plain pointers and sizes only.
+ *
+ * Method (Gavin & Polizzi, "Enhancing the Performance and Robustness of the
+ * FEAST Eigensolver", arXiv 1605.08771):
+ *   - the spectral projector rho(A) = (1/2 pi i) \oint (zI - A)^{-1} dz
+ *     (Sect. I, Eq. 2) applied to a subspace X by Gauss quadrature,
+ *     rho(A) X ~ sum_j w_j (z_j I - A)^{-1} X (Eq. 3), one shifted LU and
+ *     multi-right-hand-side solve per node;
+ *   - subspace iteration with Rayleigh-Ritz (Appendix, FEAST Algorithm);
+ *   - the two robustness variants: XFEAST, expanding the subspace with the
+ *     previous filtered blocks (Sect. II-A, XFEAST Algorithm), and RFEAST,
+ *     expanding it with Ritz residual vectors (Sect. II-B, RFEAST Algorithm).
+ *
+ * Conventions shared by every entry point:
+ *   - matrices are column-major; complex data is interleaved (re, im) double
+ *     precision, layout-compatible with C99 `double complex`;
+ *   - pointers documented "device" must be device memory of the context's
+ *     GPU, owned by the caller; pointers documented "host" are host memory;
+ *   - every call is stream-ordered on the context's stream and returns only
+ *     after its results are complete (it synchronises that stream);
+ *   - return value: 0 success, > 0 warning, < 0 error (feast_strerror).
+ *     On error the output buffers hold unspecified values.
+ *   - the contour is the ellipse with centre (lmin+lmax)/2, horizontal
+ *     semi-axis r = (lmax-lmin)/2 and vertical semi-axis aspect*r; n_c Gauss-
+ *     Legendre nodes are placed on its upper half and the lower half is their
+ *     mirror image, so n_c is also the number of shifted factorisations.
+ */
+#ifndef FEAST_GB300_H
+#define FEAST_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct feast_ctx feast_ctx;
+
+/* element type of A, X and eigenvectors */
+enum { FEAST_R64 = 0, /* real symmetric, double */
+       FEAST_C128 = 1 /* complex Hermitian, interleaved double complex */ };
+
+/* iteration variant */
+enum { FEAST_PLAIN = 0,  /* FEAST Algorithm (Appendix) */
+       FEAST_XFEAST = 1, /* expanding subspace from previous filtered blocks (Sect. II-A) */
+       FEAST_RFEAST = 2  /* expanding subspace with Ritz residuals (Sect. II-B) */ };
+
+/* arithmetic of the shifted factorisations and solves */
+enum { FEAST_PREC_F64 = 0,  /* complex FP64 LU and solves */
+       FEAST_PREC_MIXED = 1 /* complex FP32 LU and solves, FP64 iterative refinement */ };
+
+/* status codes */
+#define FEAST_OK 0
+#define FEAST_WARN_MAXITER 1        /* max_iter reached: best-effort pairs returned */
+#define FEAST_ERR_ARG (-1)          /* invalid argument */
+#define FEAST_ERR_NONFINITE (-2)    /* NaN or Inf in A or X */
+#define FEAST_ERR_SINGULAR (-3)     /* exactly singular shifted matrix */
+#define FEAST_ERR_ORTH (-4)         /* subspace could not be orthonormalised */
+#define FEAST_ERR_M0 (-5)           /* every Ritz value inside I: m0 too small */
+#define FEAST_ERR_CUDA (-6)         /* CUDA runtime error */
+#define FEAST_ERR_NOMEM (-7)        /* device allocation failed */
+#define FEAST_ERR_TIMEOUT (-8)      /* a bounded device wait gave up */
+
+typedef struct {
+  int variant;          /* FEAST_PLAIN (default), FEAST_XFEAST, FEAST_RFEAST */
+  int s;                /* XFEAST window blocks / RFEAST Rayleigh-Ritz passes (default 3) */
+  int prec;             /* FEAST_PREC_F64 (default) or FEAST_PREC_MIXED */
+  int max_iter;         /* maximum outer iterations (default 100) */
+  int refine_max;       /* mixed: maximum refinement steps per filter (default 10) */
+  int reserved;
+  double aspect;        /* ellipse vertical / horizontal semi-axis (default 1: circle) */
+  double anorm;         /* ||A||_2 when > 0; otherwise 40 power iterations estimate it */
+  double refine_tol;    /* mixed: stop when ||R||_F <= refine_tol (||A|| + |z|) ||Y||_F;
+                           0 = 2 eps sqrt(n) */
+  unsigned long long seed; /* seed of the N(0,1) starting subspace when x0 == NULL */
+  const void* x0;       /* optional device n x m0 starting subspace (leading dim n, dtype) */
+} feast_opts;
+
+/* Per-call statistics of the last feast_interval_solve on a context. */
+typedef struct {
+  int iterations;       /* outer iterations (Rayleigh-Ritz / check rounds) */
+  int filters;          /* applications of rho(A): each solves n_c*m0 right-hand sides
+                           per half-contour */
+  int refine_steps;     /* mixed: total refinement steps */
+  int m_expected;       /* XFEAST/RFEAST: count used by the stopping test */
+  double factor_ms;     /* time of the shifted factorisations */
+  double filter_ms;     /* total time of the filter applications */
+  double total_ms;      /* whole solve */
+  double max_residual;  /* max relative residual of the returned pairs */
+  double history[128];  /* max residual per iteration (first 128) */
+} feast_stats;
+
+void feast_opts_default(feast_opts* opts);
+
+/* Create a context on CUDA device `device`; `stream` is a cudaStream_t (NULL
+ * = the legacy default stream).  The context owns its workspace (device
+ * memory that grows to the largest problem seen).  Returns FEAST_OK,
+ * FEAST_ERR_ARG or FEAST_ERR_CUDA. */
+int feast_init(feast_ctx** ctx, int device, void* stream);
+/* Release the context and its workspace. */
+int feast_finalize(feast_ctx* ctx);
+const char* feast_strerror(int code);
+
+/* Contour nodes z_j and weights w_j of the upper half-contour (Eq. 3 with the
+ * circle/ellipse reading above): z and w receive n_c complex values each
+ * (host, 2*n_c doubles, interleaved).  Node j uses the j-th Gauss-Legendre
+ * abscissa t_j in ascending order, theta_j = (pi/2)(1 - t_j),
+ * z_j = c + r cos(theta_j) + i aspect r sin(theta_j),
+ * w_j = (omega_j/4)(aspect r cos(theta_j) + i r sin(theta_j)). */
+int feast_contour_nodes(double lmin, double lmax, int n_c, double aspect, double* z, double* w);
+
+/* Eigenpairs of the Hermitian n x n matrix A (device, leading dim lda >= n,
+ * dtype FEAST_R64 or FEAST_C128, not modified) with eigenvalues in the open
+ * interval (lmin, lmax).  m0 is the subspace size (more than the expected
+ * count, at most n), n_c the number of upper-half quadrature nodes, tol the
+ * stopping tolerance on max_k ||A x_k - lambda_k x_k|| / ||A||_2 over the
+ * returned pairs (Appendix step 3).  Outputs: evals (host, >= m0 doubles,
+ * ascending), evecs (device, n x m0, leading dim n, dtype; unit 2-norm
+ * columns), res (host, >= m0 doubles, relative residuals), *m_found pairs,
+ * *iterations outer iterations.  Only the first *m_found values/columns are
+ * meaningful.  stats may be NULL.  Returns FEAST_OK, FEAST_WARN_MAXITER or an
+ * error. */
+int feast_interval_solve(feast_ctx* ctx, const void* A, int dtype, int64_t n, int64_t lda,
+                         double lmin, double lmax, int m0, int n_c, double tol,
+                         const feast_opts* opts, double* evals, void* evecs, double* res,
+                         int* m_found, int* iterations, feast_stats* stats);
+
+/* Y = rho(A) X by the quadrature of Eq. 3 over both half-contours: real A:
+ * sum_j 2 Re(w_j (z_j I - A)^{-1} X); complex Hermitian A:
+ * sum_j [w_j (z_j I - A)^{-1} + conj(w_j) (conj(z_j) I - A)^{-1}] X.
+ * X, Y: device n x m (leading dim n, dtype).  opts supplies prec, aspect,
+ * refine_max, refine_tol, anorm (NULL = defaults). */
+int feast_filter_apply(feast_ctx* ctx, const void* A, int dtype, int64_t n, int64_t lda,
+                       double lmin, double lmax, int n_c, const feast_opts* opts,
+                       const void* X, int64_t m, void* Y);
+
+/* LU with partial pivoting of M_e = z_e I - A for nz shifts z (host, 2*nz
+ * doubles).  LU: device nz * n * n complex elements (complex double for
+ * FEAST_PREC_F64, complex float for FEAST_PREC_MIXED), factor e at offset
+ * e*n*n, unit-lower L below the diagonal, U on and above it.  perm: device
+ * nz*n int32, perm[e*n + i] = row of M_e now at row i (P M_e = L U). */
+int feast_shifted_lu(feast_ctx* ctx, const void* A, int dtype, int64_t n, int64_t lda,
+                     const double* z, int nz, int prec, void* LU, int32_t* perm);
+
+/* Y_e = M_e^{-1} B (adjoint = 0) or M_e^{-H} B (adjoint = 1) from factors of
+ * feast_shifted_lu (same prec), without refinement.  B: device n x m complex
+ * double; Y: device nz * n * m complex double, solve e at offset e*n*m. */
+int feast_shifted_solve(feast_ctx* ctx, const void* LU, const int32_t* perm, int64_t n, int nz,
+                        int prec, int adjoint, const void* B, int64_t m, void* Y);
+
+/* Orthonormalise the columns of X (device n x k, dtype, in place).
+ * method 0: Cholesky-QR twice, Gram-eigendecomposition route on breakdown;
+ * method 1: Gram-eigendecomposition X^H X = V S^2 V^H, U = X V S^{-1} over
+ * the directions with s^2 >= 1e-12 s_1^2, then one Cholesky-QR pass
+ * (Sect. II-A).  *rank receives the number of orthonormal columns written to
+ * the front of X. */
+int feast_orthonormalize(feast_ctx* ctx, int dtype, int64_t n, int64_t k, void* X, int method,
+                         int* rank);
+
+/* Eigenvalues (host, ascending) and eigenvectors (device k x k, leading dim
+ * k) of the Hermitian k x k matrix H (device, leading dim k, not modified) by
+ * two-sided Jacobi with round-robin ordering; *sweeps may be NULL. */
+int feast_jacobi_eigh(feast_ctx* ctx, int dtype, int64_t k, const void* H, double* evals,
+                      void* V, int* sweeps);
+
+/* Rayleigh-Ritz on the orthonormal basis Q (device n x k): A' = Q^H A Q,
+ * A' V = V Lambda, X = Q V (device n x k), relative residuals
+ * ||A x_j - lambda_j x_j|| / anorm (host), Ritz values ascending (host). */
+int feast_rayleigh_ritz(feast_ctx* ctx, const void* A, int dtype, int64_t n, int64_t lda,
+                        const void* Q, int64_t k, double anorm, double* evals, void* X,
+                        double* res);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FEAST_GB300_H */

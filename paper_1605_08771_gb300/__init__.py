@@ -1,0 +1,314 @@
+"""FEAST interval eigensolver on one GB300: thin Python binding.
+
+Every function here marshals arguments to the C ABI of libfeast_gb300.so
+(declared in include/feast.h) and nothing else: all arithmetic runs in the
+library's CUDA kernels.  PyTorch supplies device memory and the stream.  If
+the shared library is missing or a tensor is not on a CUDA device, the calls
+raise; there is no CPU fallback.
+
+Layout: the library is column-major.  Input tensors of any layout are copied
+to column-major device memory; returned matrices are column-major views
+(shape (n, m), strides (1, n)).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB, build as build_library  # noqa: F401
+
+FEAST_R64, FEAST_C128 = 0, 1
+FEAST_PLAIN, FEAST_XFEAST, FEAST_RFEAST = 0, 1, 2
+FEAST_PREC_F64, FEAST_PREC_MIXED = 0, 1
+FEAST_OK, FEAST_WARN_MAXITER = 0, 1
+
+VARIANTS = {"feast": FEAST_PLAIN, "xfeast": FEAST_XFEAST, "rfeast": FEAST_RFEAST}
+PRECS = {"f64": FEAST_PREC_F64, "mixed": FEAST_PREC_MIXED}
+
+EXPORTS = [
+    "feast_opts_default", "feast_init", "feast_finalize", "feast_strerror",
+    "feast_contour_nodes", "feast_interval_solve", "feast_filter_apply",
+    "feast_shifted_lu", "feast_shifted_solve", "feast_orthonormalize",
+    "feast_jacobi_eigh", "feast_rayleigh_ritz",
+]
+
+
+class FeastOpts(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int), ("s", ctypes.c_int), ("prec", ctypes.c_int),
+                ("max_iter", ctypes.c_int), ("refine_max", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("aspect", ctypes.c_double), ("anorm", ctypes.c_double), ("refine_tol", ctypes.c_double),
+                ("seed", ctypes.c_ulonglong), ("x0", ctypes.c_void_p)]
+
+
+class FeastStats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("filters", ctypes.c_int), ("refine_steps", ctypes.c_int),
+                ("m_expected", ctypes.c_int), ("factor_ms", ctypes.c_double), ("filter_ms", ctypes.c_double),
+                ("total_ms", ctypes.c_double), ("max_residual", ctypes.c_double),
+                ("history", ctypes.c_double * 128)]
+
+
+class FeastError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {feast_strerror(code)} (status {code})")
+
+
+_LIB = None
+
+
+def lib():
+    """Load libfeast_gb300.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB):
+        raise RuntimeError(f"{LIB} is missing: build it with paper_1605_08771_gb300.build.build()")
+    L = ctypes.CDLL(LIB)
+    P, I, D, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+    DP, IP = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+    sig = {
+        "feast_opts_default": (None, [ctypes.POINTER(FeastOpts)]),
+        "feast_init": (I, [ctypes.POINTER(P), I, P]),
+        "feast_finalize": (I, [P]),
+        "feast_strerror": (ctypes.c_char_p, [I]),
+        "feast_contour_nodes": (I, [D, D, I, D, DP, DP]),
+        "feast_interval_solve": (I, [P, P, I, I64, I64, D, D, I, I, D, ctypes.POINTER(FeastOpts),
+                                     DP, P, DP, IP, IP, ctypes.POINTER(FeastStats)]),
+        "feast_filter_apply": (I, [P, P, I, I64, I64, D, D, I, ctypes.POINTER(FeastOpts), P, I64, P]),
+        "feast_shifted_lu": (I, [P, P, I, I64, I64, DP, I, I, P, P]),
+        "feast_shifted_solve": (I, [P, P, P, I64, I, I, I, P, I64, P]),
+        "feast_orthonormalize": (I, [P, I, I64, I64, P, I, IP]),
+        "feast_jacobi_eigh": (I, [P, I, I64, P, DP, P, IP]),
+        "feast_rayleigh_ritz": (I, [P, P, I, I64, I64, P, I64, D, DP, P, DP]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = L
+    return L
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+def _torch():
+    import torch
+    return torch
+
+
+def _dtype_code(t):
+    torch = _torch()
+    if t.dtype == torch.float64:
+        return FEAST_R64
+    if t.dtype == torch.complex128:
+        return FEAST_C128
+    raise TypeError(f"unsupported dtype {t.dtype}: use float64 or complex128")
+
+
+def colmajor(t):
+    """Column-major (Fortran-order) device copy of a 2-D tensor, as a view of
+    shape t.shape with strides (1, rows)."""
+    if not t.is_cuda:
+        raise ValueError("FEAST takes CUDA tensors (no CPU path)")
+    if t.dim() == 1:
+        t = t[:, None]
+    if t.stride(0) == 1 and t.stride(1) == t.shape[0]:
+        return t
+    return t.transpose(0, 1).contiguous().transpose(0, 1)
+
+
+def empty_colmajor(rows, cols, dtype, device):
+    torch = _torch()
+    return torch.empty((cols, rows), dtype=dtype, device=device).transpose(0, 1)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check(code, where):
+    if code < 0:
+        raise FeastError(code, where)
+    return code
+
+
+# ---------------------------------------------------------------------------
+# C-ABI mirror
+# ---------------------------------------------------------------------------
+def feast_strerror(code: int) -> str:
+    return lib().feast_strerror(int(code)).decode()
+
+
+def feast_opts_default(**kw) -> FeastOpts:
+    o = FeastOpts()
+    lib().feast_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "variant" and isinstance(v, str):
+            v = VARIANTS[v]
+        if k == "prec" and isinstance(v, str):
+            v = PRECS[v]
+        setattr(o, k, v)
+    return o
+
+
+def feast_init(device: int = 0, stream=None):
+    """Create a library context on `device`; `stream` is a torch.cuda.Stream
+    (default: the current stream)."""
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    h = ctypes.c_void_p()
+    _check(lib().feast_init(ctypes.byref(h), int(device), ctypes.c_void_p(stream.cuda_stream)), "feast_init")
+    return h
+
+
+def feast_finalize(ctx) -> None:
+    _check(lib().feast_finalize(ctx), "feast_finalize")
+
+
+def feast_contour_nodes(lmin, lmax, n_c, aspect=1.0):
+    z = np.zeros(2 * n_c)
+    w = np.zeros(2 * n_c)
+    _check(lib().feast_contour_nodes(lmin, lmax, n_c, aspect,
+                                     z.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                     w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "feast_contour_nodes")
+    return z[0::2] + 1j * z[1::2], w[0::2] + 1j * w[1::2]
+
+
+def feast_interval_solve(ctx, A, lmin, lmax, m0, n_c, tol, opts: FeastOpts | None = None, x0=None):
+    """Eigenpairs of the Hermitian CUDA tensor A with eigenvalues in
+    (lmin, lmax).  Returns a dict with status, evals (numpy), evecs (CUDA,
+    n x m), res (numpy), iterations, stats (FeastStats)."""
+    A = colmajor(A)
+    n = A.shape[0]
+    dt = _dtype_code(A)
+    opts = opts or feast_opts_default()
+    keep = None
+    if x0 is not None:
+        keep = colmajor(x0.to(A.dtype))
+        opts.x0 = keep.data_ptr()
+    evals = np.zeros(m0)
+    res = np.zeros(m0)
+    V = empty_colmajor(n, m0, A.dtype, A.device)
+    mf, it = ctypes.c_int(0), ctypes.c_int(0)
+    st = FeastStats()
+    code = lib().feast_interval_solve(ctx, _ptr(A), dt, n, n, float(lmin), float(lmax), int(m0), int(n_c),
+                                      float(tol), ctypes.byref(opts),
+                                      evals.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(V),
+                                      res.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                      ctypes.byref(mf), ctypes.byref(it), ctypes.byref(st))
+    _check(code, "feast_interval_solve")
+    m = mf.value
+    return {"status": code, "evals": evals[:m].copy(), "evecs": V[:, :m], "res": res[:m].copy(),
+            "iterations": it.value, "stats": st}
+
+
+def feast_filter_apply(ctx, A, lmin, lmax, n_c, X, opts: FeastOpts | None = None):
+    """rho(A) X (Eq. 3) for CUDA tensors A (n x n) and X (n x m)."""
+    A = colmajor(A)
+    X = colmajor(X.to(A.dtype))
+    n, m = X.shape
+    Y = empty_colmajor(n, m, A.dtype, A.device)
+    opts = opts or feast_opts_default()
+    _check(lib().feast_filter_apply(ctx, _ptr(A), _dtype_code(A), n, n, float(lmin), float(lmax), int(n_c),
+                                    ctypes.byref(opts), _ptr(X), m, _ptr(Y)), "feast_filter_apply")
+    return Y
+
+
+def feast_shifted_lu(ctx, A, z, prec=FEAST_PREC_F64):
+    """LU factors of z_e I - A for the complex shifts z.  Returns (LU, perm):
+    LU a CUDA tensor (nz, n, n) holding column-major factors (complex128, or
+    complex64 for the mixed precision), perm (nz, n) int32."""
+    torch = _torch()
+    A = colmajor(A)
+    n = A.shape[0]
+    z = np.asarray(z, dtype=np.complex128)
+    zz = np.ascontiguousarray(np.stack([z.real, z.imag], axis=1).ravel())
+    nz = z.size
+    cd = torch.complex128 if prec == FEAST_PREC_F64 else torch.complex64
+    LU = torch.empty((nz, n, n), dtype=cd, device=A.device)
+    perm = torch.empty((nz, n), dtype=torch.int32, device=A.device)
+    _check(lib().feast_shifted_lu(ctx, _ptr(A), _dtype_code(A), n, n,
+                                  zz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nz, int(prec),
+                                  _ptr(LU), _ptr(perm)), "feast_shifted_lu")
+    # LU[e] memory is column-major: expose as matrices
+    return LU.transpose(1, 2), perm
+
+
+def feast_shifted_solve(ctx, LU, perm, B, adjoint=False, prec=FEAST_PREC_F64):
+    """Y_e = (z_e I - A)^{-1} B (or the adjoint) for every factor; returns a
+    CUDA tensor (nz, n, m) of column-major solutions viewed as matrices."""
+    torch = _torch()
+    B = colmajor(B.to(torch.complex128))
+    n, m = B.shape
+    nz = perm.shape[0]
+    LUm = LU.transpose(1, 2).contiguous()  # back to the column-major factor memory
+    Y = torch.empty((nz, m, n), dtype=torch.complex128, device=B.device)
+    _check(lib().feast_shifted_solve(ctx, _ptr(LUm), _ptr(perm), n, nz, int(prec), int(bool(adjoint)),
+                                     _ptr(B), m, _ptr(Y)), "feast_shifted_solve")
+    return Y.transpose(1, 2)
+
+
+def feast_orthonormalize(ctx, X, method=0):
+    """Orthonormal basis of span(X) (CUDA, n x k); returns (Q, rank)."""
+    Xw = colmajor(X).transpose(0, 1).clone().transpose(0, 1)  # private column-major copy
+    n, k = Xw.shape
+    r = ctypes.c_int(0)
+    _check(lib().feast_orthonormalize(ctx, _dtype_code(Xw), n, k, _ptr(Xw), int(method), ctypes.byref(r)),
+           "feast_orthonormalize")
+    return Xw[:, :r.value], r.value
+
+
+def feast_jacobi_eigh(ctx, H):
+    """Eigenvalues (numpy, ascending), eigenvectors (CUDA, k x k) and sweep
+    count of the Hermitian CUDA matrix H by the library's Jacobi kernel."""
+    H = colmajor(H)
+    k = H.shape[0]
+    ev = np.zeros(k)
+    V = empty_colmajor(k, k, H.dtype, H.device)
+    sw = ctypes.c_int(0)
+    _check(lib().feast_jacobi_eigh(ctx, _dtype_code(H), k, _ptr(H),
+                                   ev.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(V), ctypes.byref(sw)),
+           "feast_jacobi_eigh")
+    return ev, V, sw.value
+
+
+def feast_rayleigh_ritz(ctx, A, Q, anorm):
+    """Rayleigh-Ritz of A on the orthonormal basis Q: (evals, X, res)."""
+    A = colmajor(A)
+    Q = colmajor(Q.to(A.dtype))
+    n, k = Q.shape
+    ev = np.zeros(k)
+    res = np.zeros(k)
+    X = empty_colmajor(n, k, A.dtype, A.device)
+    _check(lib().feast_rayleigh_ritz(ctx, _ptr(A), _dtype_code(A), n, n, _ptr(Q), k, float(anorm),
+                                     ev.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(X),
+                                     res.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "feast_rayleigh_ritz")
+    return ev, X, res
+
+
+class Feast:
+    """Context manager owning one library context."""
+
+    def __init__(self, device=0, stream=None):
+        self.ctx = feast_init(device, stream)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def close(self):
+        if self.ctx is not None:
+            feast_finalize(self.ctx)
+            self.ctx = None
+
+    def solve(self, A, lmin, lmax, m0, n_c=8, tol=1e-10, x0=None, **opts):
+        return feast_interval_solve(self.ctx, A, lmin, lmax, m0, n_c, tol, feast_opts_default(**opts), x0=x0)
+
+    def filter(self, A, lmin, lmax, n_c, X, **opts):
+        return feast_filter_apply(self.ctx, A, lmin, lmax, n_c, X, feast_opts_default(**opts))

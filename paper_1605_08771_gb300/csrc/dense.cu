@@ -1,0 +1,578 @@
+// Dense FP64 kernels of the Rayleigh-Ritz side (see dense.cuh).
+//
+// Cholesky and Jacobi are single cooperative launches whose CTAs meet at the
+// bounded group barrier of common.cuh; every value read after a barrier that
+// another CTA may have written goes through L2 (ld.global.cg).
+#include "dense.cuh"
+
+#include <algorithm>
+
+namespace feast {
+
+namespace {
+
+template <typename S> __device__ __forceinline__ S ldcg(const S* p);
+template <> __device__ __forceinline__ double ldcg<double>(const double* p) { return __ldcg(p); }
+template <> __device__ __forceinline__ c128 ldcg<c128>(const c128* p) {
+  double2 v = __ldcg((const double2*)p);
+  return c128{v.x, v.y};
+}
+template <typename S> __device__ __forceinline__ S one();
+template <> __device__ __forceinline__ double one<double>() { return 1.0; }
+template <> __device__ __forceinline__ c128 one<c128>() { return c128{1.0, 0.0}; }
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  return v;
+}
+__device__ double block_sum(double v) {
+  __shared__ double sh[32];
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sh[i];
+    sh[0] = r;
+  }
+  __syncthreads();
+  r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+inline unsigned grid1d(int64_t total, int threads = 256) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(total, threads), 16384));
+}
+
+// ---------------------------------------------------------------------------
+template <typename S>
+__global__ void hermitize_kernel(S* H, int64_t k, int64_t ld) {
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < k * k;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = idx % k, j = idx / k;
+    if (i > j) continue;
+    S a = H[i + j * ld], b = H[j + i * ld];
+    if (i == j) {
+      H[i + i * ld] = cvt<S>(real_part(a));
+    } else {
+      S m = (a + conj(b)) * 0.5;
+      H[i + j * ld] = m;
+      H[j + i * ld] = conj(m);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Right-looking Cholesky, one column per step, two group barriers per column.
+template <typename S>
+__global__ void __launch_bounds__(256) chol_kernel(S* G, int64_t k, int64_t ld, CoopWork w, int P) {
+  extern __shared__ unsigned char smem_raw[];
+  S* row = (S*)smem_raw;
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t NT = (int64_t)P * blockDim.x;
+  const int64_t gw = gt >> 5, nw = NT >> 5;
+  const int lane = threadIdx.x & 31;
+  unsigned nb = 0;
+  for (int64_t j = 0; j < k; ++j) {
+    const double gjj = real_part(ldcg(&G[j + j * ld]));
+    if (!(gjj > 0.0) || !isfinite(gjj)) {
+      if (gt == 0) atomicCAS(&w.info[0], 0, (int)j + 1);
+      return;  // every CTA reads the same value and leaves together
+    }
+    const double rjj = sqrt(gjj);
+    const double inv = 1.0 / rjj;
+    for (int64_t l = j + 1 + gt; l < k; l += NT) G[j + l * ld] = ldcg(&G[j + l * ld]) * inv;
+    if (gt == 0) G[j + j * ld] = cvt<S>(rjj);
+    if (!group_barrier(w.counter, (++nb) * (unsigned)P, w.status)) return;
+    for (int64_t l = j + 1 + threadIdx.x; l < k; l += blockDim.x) row[l] = ldcg(&G[j + l * ld]);
+    __syncthreads();
+    for (int64_t l2 = j + 1 + gw; l2 < k; l2 += nw) {
+      const S r2 = row[l2];
+      for (int64_t l1 = j + 1 + lane; l1 <= l2; l1 += 32) {
+        S* g = &G[l1 + l2 * ld];
+        *g = ldcg(g) - conj(row[l1]) * r2;
+      }
+    }
+    if (!group_barrier(w.counter, (++nb) * (unsigned)P, w.status)) return;
+  }
+}
+
+// ---------------------------------------------------------------------------
+template <typename S>
+__global__ void tri_inv_kernel(const S* R, int64_t k, int64_t ld, S* Ri, int64_t ldi) {
+  const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (c >= k) return;
+  S* x = Ri + c * ldi;
+  for (int64_t i = c + 1 + lane; i < k; i += 32) x[i] = num<S>::zero();
+  if (lane == 0) x[c] = recip(R[c + c * ld]);
+  __syncwarp();
+  for (int64_t i = c - 1; i >= 0; --i) {
+    S acc = num<S>::zero();
+    for (int64_t l = i + 1 + lane; l <= c; l += 32) acc = acc + R[i + l * ld] * x[l];
+    if constexpr (std::is_same<S, double>::value) {
+      acc = warp_sum(acc);
+    } else {
+      acc.re = warp_sum(acc.re);
+      acc.im = warp_sum(acc.im);
+    }
+    if (lane == 0) x[i] = -(acc * recip(R[i + i * ld]));
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Jacobi, round-robin (circle-method) ordering: in round r the k/2 disjoint
+// pairs are (r, kk-1) and (r+i, r-i) mod (kk-1), i = 1..kk/2-1, kk = k
+// rounded up to even (index k is a dummy when k is odd).
+template <typename S>
+__global__ void __launch_bounds__(256)
+jacobi_kernel(S* H, int64_t k, int64_t ld, S* V, int64_t ldv, double tol, CoopWork w, int P, int max_sweeps) {
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t NT = (int64_t)P * blockDim.x;
+  unsigned nb = 0;
+  const int64_t kk = k + (k & 1), np = kk / 2, m1 = kk - 1;
+  double* rc = (double*)w.rot;
+  double* rs = rc + np;
+  S* re = (S*)(rs + np);
+  int* ron = (int*)(re + np);
+  int* rpp = ron + np;
+  int* rqq = rpp + np;
+
+  double part = 0.0;
+  for (int64_t idx = gt; idx < k * k; idx += NT) {
+    const int64_t i = idx % k, j = idx / k;
+    V[i + j * ldv] = (i == j) ? one<S>() : num<S>::zero();
+    part += abs2(H[i + j * ld]);
+  }
+  part = block_sum(part);
+  if (threadIdx.x == 0) w.partial[blockIdx.x] = part;
+  if (!group_barrier(w.counter, (++nb) * (unsigned)P, w.status)) return;
+  double fro2 = 0.0;
+  for (int q = 0; q < P; ++q) fro2 += __ldcg(&w.partial[q]);
+  const double thr = tol * sqrt(fro2);
+
+  int sweeps = 0;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    for (int64_t r = 0; r < m1; ++r) {
+      for (int64_t i = gt; i < np; i += NT) {
+        int64_t a, b;
+        if (i == 0) { a = r % m1; b = m1; }
+        else { a = (r + i) % m1; b = ((r - i) % m1 + m1) % m1; }
+        const int64_t p = a < b ? a : b, q = a < b ? b : a;
+        double c = 1.0, s = 0.0;
+        S e = one<S>();
+        int on = 0;
+        if (q < k) {
+          const S apq = ldcg(&H[p + q * ld]);
+          const double g = sqrt(abs2(apq));
+          if (g > thr) {
+            const double app = real_part(ldcg(&H[p + p * ld]));
+            const double aqq = real_part(ldcg(&H[q + q * ld]));
+            e = conj(apq) * (1.0 / g);
+            const double tau = (aqq - app) / (2.0 * g);
+            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + hypot(1.0, tau));
+            c = 1.0 / hypot(1.0, t);
+            s = t * c;
+            on = 1;
+            atomicAdd(&w.rotcount[sweep], 1u);
+          }
+        }
+        rc[i] = c; rs[i] = s; re[i] = e; ron[i] = on; rpp[i] = (int)p; rqq[i] = (int)q;
+      }
+      if (!group_barrier(w.counter, (++nb) * (unsigned)P, w.status)) return;
+      const int64_t nblk = np * np;
+      for (int64_t task = gt; task < nblk + k * np; task += NT) {
+        if (task < nblk) {
+          const int64_t I = task % np, J = task / np;
+          const int onI = __ldcg(&ron[I]), onJ = __ldcg(&ron[J]);
+          if (!onI && !onJ) continue;
+          const int pI = __ldcg(&rpp[I]), qI = __ldcg(&rqq[I]);
+          const int pJ = __ldcg(&rpp[J]), qJ = __ldcg(&rqq[J]);
+          const bool vqI = qI < k, vqJ = qJ < k;
+          S b00 = ldcg(&H[pI + (int64_t)pJ * ld]);
+          S b01 = vqJ ? ldcg(&H[pI + (int64_t)qJ * ld]) : num<S>::zero();
+          S b10 = vqI ? ldcg(&H[qI + (int64_t)pJ * ld]) : num<S>::zero();
+          S b11 = (vqI && vqJ) ? ldcg(&H[qI + (int64_t)qJ * ld]) : num<S>::zero();
+          if (onJ) {
+            const double c = __ldcg(&rc[J]), s = __ldcg(&rs[J]);
+            const S e = ldcg(&re[J]);
+            const S se = e * s, ce = e * c;
+            S n00 = b00 * c - b01 * se, n01 = b00 * s + b01 * ce;
+            S n10 = b10 * c - b11 * se, n11 = b10 * s + b11 * ce;
+            b00 = n00; b01 = n01; b10 = n10; b11 = n11;
+          }
+          if (onI) {
+            const double c = __ldcg(&rc[I]), s = __ldcg(&rs[I]);
+            const S ec = conj(ldcg(&re[I]));
+            const S sec = ec * s, cec = ec * c;
+            S n00 = b00 * c - b10 * sec, n10 = b00 * s + b10 * cec;
+            S n01 = b01 * c - b11 * sec, n11 = b01 * s + b11 * cec;
+            b00 = n00; b01 = n01; b10 = n10; b11 = n11;
+          }
+          if (I == J && onI) {
+            b01 = num<S>::zero();
+            b10 = num<S>::zero();
+            b00 = cvt<S>(real_part(b00));
+            b11 = cvt<S>(real_part(b11));
+          }
+          H[pI + (int64_t)pJ * ld] = b00;
+          if (vqJ) H[pI + (int64_t)qJ * ld] = b01;
+          if (vqI) H[qI + (int64_t)pJ * ld] = b10;
+          if (vqI && vqJ) H[qI + (int64_t)qJ * ld] = b11;
+        } else {
+          const int64_t tv = task - nblk;
+          const int64_t row = tv % k, J = tv / k;
+          if (!__ldcg(&ron[J])) continue;
+          const int pJ = __ldcg(&rpp[J]), qJ = __ldcg(&rqq[J]);
+          const double c = __ldcg(&rc[J]), s = __ldcg(&rs[J]);
+          const S e = ldcg(&re[J]);
+          S* vp = &V[row + (int64_t)pJ * ldv];
+          S* vq = &V[row + (int64_t)qJ * ldv];
+          const S a = ldcg(vp), b = ldcg(vq);
+          *vp = a * c - b * (e * s);
+          *vq = a * s + b * (e * c);
+        }
+      }
+      if (!group_barrier(w.counter, (++nb) * (unsigned)P, w.status)) return;
+    }
+    sweeps = sweep + 1;
+    if (__ldcg(&w.rotcount[sweep]) == 0u) break;
+  }
+  if (gt == 0) w.info[1] = sweeps;
+}
+
+// ---------------------------------------------------------------------------
+template <typename S>
+__global__ void get_diag_kernel(const S* H, int64_t k, int64_t ld, double* d) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x)
+    d[i] = real_part(H[i + i * ld]);
+}
+
+template <typename S>
+__global__ void col_norms2_kernel(const S* X, int64_t n, int64_t ld, double* out) {
+  const int64_t j = blockIdx.x;
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += abs2(X[i + j * ld]);
+  s = block_sum(s);
+  if (threadIdx.x == 0) out[j] = s;
+}
+
+template <typename S>
+__global__ void resid_norms2_kernel(const S* AX, const S* X, int64_t n, int64_t ld, const double* lam, double* out) {
+  const int64_t j = blockIdx.x;
+  const double l = lam[j];
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += abs2(AX[i + j * ld] - X[i + j * ld] * l);
+  s = block_sum(s);
+  if (threadIdx.x == 0) out[j] = s;
+}
+
+template <typename S>
+__global__ void ritz_residual_kernel(S* R, const S* AX, const S* X, int64_t n, int64_t k, int64_t ld,
+                                     const double* lam) {
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n * k;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx % n, j = idx / n;
+    R[i + j * ld] = AX[i + j * ld] - X[i + j * ld] * lam[j];
+  }
+}
+
+template <typename S>
+__global__ void gather_cols_kernel(S* dst, int64_t lddst, const S* src, int64_t ldsrc, int64_t n, const int* idx,
+                                   int64_t k, const double* scale) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * k; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t % n, j = t / n;
+    S v = src[i + (int64_t)idx[j] * ldsrc];
+    if (scale) v = v * scale[j];
+    dst[i + j * lddst] = v;
+  }
+}
+
+template <typename S>
+__global__ void scale_cols_kernel(S* X, int64_t n, int64_t k, int64_t ld, const double* scale) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * k; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t % n, j = t / n;
+    X[i + j * ld] = X[i + j * ld] * scale[j];
+  }
+}
+
+template <typename S>
+__global__ void accumulate_kernel(S* Xf, int64_t ld, const c128* Y, int64_t n, int64_t m, int nodes,
+                                  const c128* w) {
+  const int64_t nm = n * m;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nm; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t % n, c = t / n;
+    if constexpr (std::is_same<S, double>::value) {
+      double acc = 0.0;
+      for (int j = 0; j < nodes; ++j) acc += 2.0 * (w[j] * Y[(int64_t)j * nm + t]).re;
+      Xf[i + c * ld] = acc;
+    } else {
+      c128 acc{0.0, 0.0};
+      for (int j = 0; j < nodes; ++j) {
+        acc = acc + w[j] * Y[(int64_t)j * nm + t];
+        acc = acc + conj(w[j]) * Y[(int64_t)(nodes + j) * nm + t];
+      }
+      Xf[i + c * ld] = acc;
+    }
+  }
+}
+
+template <typename S>
+__global__ void refine_residual_kernel(c128* R, const S* X, int64_t ldx, const c128* Y, const c128* AY, int64_t n,
+                                       int64_t m, const c128* z_e) {
+  const int e = blockIdx.y;
+  const int64_t nm = n * m;
+  const c128 z = z_e[e];
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nm; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t % n, c = t / n;
+    const int64_t o = (int64_t)e * nm + t;
+    R[o] = cvt<c128>(X[i + c * ldx]) - z * Y[o] + AY[o];
+  }
+}
+
+__global__ void entry_norms2_kernel(const c128* R, const c128* Y, int64_t nm, double* out) {
+  const int e = blockIdx.y;
+  double sr = 0.0, sy = 0.0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nm; t += (int64_t)gridDim.x * blockDim.x) {
+    sr += abs2(R[(int64_t)e * nm + t]);
+    sy += abs2(Y[(int64_t)e * nm + t]);
+  }
+  sr = block_sum(sr);
+  sy = block_sum(sy);
+  if (threadIdx.x == 0) {
+    atomicAdd(&out[2 * e], sr);
+    atomicAdd(&out[2 * e + 1], sy);
+  }
+}
+
+// splitmix64 (Steele, Lea & Flood 2014) as a counter-based generator
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+template <typename S>
+__global__ void random_normal_kernel(S* X, int64_t n, int64_t m, int64_t ld, unsigned long long seed) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * m; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t % n, c = t / n;
+    const unsigned long long h1 = splitmix64(seed ^ splitmix64(2ull * (unsigned long long)t));
+    const unsigned long long h2 = splitmix64(seed ^ splitmix64(2ull * (unsigned long long)t + 1ull));
+    const double u1 = ((double)(h1 >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    const double u2 = ((double)(h2 >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    const double rad = sqrt(-2.0 * log(u1));
+    double sn, cs;
+    sincospi(2.0 * u2, &sn, &cs);
+    if constexpr (std::is_same<S, double>::value) {
+      X[i + c * ld] = rad * cs;
+    } else {
+      X[i + c * ld] = c128{rad * cs * 0.7071067811865476, rad * sn * 0.7071067811865476};
+    }
+  }
+}
+
+template <typename S>
+__global__ void copy_matrix_kernel(S* dst, int64_t ldd, const S* src, int64_t lds, int64_t n, int64_t m) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * m; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t % n, c = t / n;
+    dst[i + c * ldd] = src[i + c * lds];
+  }
+}
+
+template <typename S>
+__global__ void set_identity_kernel(S* X, int64_t k, int64_t ld) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < k * k; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t % k, c = t / k;
+    X[i + c * ld] = (i == c) ? one<S>() : num<S>::zero();
+  }
+}
+
+template <typename S>
+__global__ void check_finite_kernel(const S* X, int64_t n, int64_t m, int64_t ld, int* flag) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * m; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t % n, c = t / n;
+    if (!isfinite(abs2(X[i + c * ld]))) { *flag = 1; return; }
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+size_t coop_work_bytes(int64_t kmax, int num_sms) {
+  const int64_t np = (kmax + 2) / 2;
+  return 256 * 4 + sizeof(double) * 2 * (size_t)std::max(num_sms, 1024) + 256 +
+         sizeof(unsigned) * kMaxSweeps + 256 + (size_t)np * (2 * sizeof(double) + sizeof(c128) + 3 * sizeof(int)) + 256;
+}
+
+CoopWork coop_work_carve(void* base, int64_t kmax, int num_sms) {
+  char* p = (char*)base;
+  CoopWork w{};
+  w.counter = (unsigned*)p; p += 256;
+  w.status = (int*)p; p += 256;
+  w.info = (int*)p; p += 256;
+  p += 256;
+  w.partial = (double*)p; p += ((sizeof(double) * 2 * (size_t)std::max(num_sms, 1024) + 255) & ~size_t(255));
+  w.rotcount = (unsigned*)p; p += ((sizeof(unsigned) * kMaxSweeps + 255) & ~size_t(255));
+  w.rot = p;
+  (void)kmax;
+  return w;
+}
+
+template <typename S> void hermitize(S* H, int64_t k, int64_t ld, cudaStream_t s) {
+  hermitize_kernel<S><<<grid1d(k * k), 256, 0, s>>>(H, k, ld);
+  FEAST_LAUNCH_CHECK();
+}
+
+template <typename S>
+void cholesky_upper(S* G, int64_t k, int64_t ld, const CoopWork& w, int num_sms, cudaStream_t s) {
+  FEAST_CUDA_TRY(cudaMemsetAsync(w.counter, 0, 256 * 3, s));
+  const size_t smem = sizeof(S) * (size_t)k;
+  if (smem > 48 * 1024)
+    FEAST_CUDA_TRY(cudaFuncSetAttribute(chol_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int occ = 0;
+  FEAST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, chol_kernel<S>, 256, smem));
+  int P = (int)std::min<int64_t>((int64_t)std::max(1, occ) * num_sms, cdiv(k * k / 2 + 1, 256 * 16));
+  P = std::max(1, std::min(P, num_sms));
+  CoopWork wl = w;
+  void* args[] = {&G, &k, &ld, &wl, &P};
+  FEAST_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)chol_kernel<S>, dim3(P), dim3(256), args, smem, s));
+}
+
+template <typename S>
+void tri_inverse_upper(const S* R, int64_t k, int64_t ld, S* Rinv, int64_t ldi, cudaStream_t s) {
+  tri_inv_kernel<S><<<(unsigned)cdiv(k * 32, 256), 256, 0, s>>>(R, k, ld, Rinv, ldi);
+  FEAST_LAUNCH_CHECK();
+}
+
+template <typename S>
+void jacobi_eigh(S* H, int64_t k, int64_t ld, S* V, int64_t ldv, double tol, const CoopWork& w, int num_sms,
+                 cudaStream_t s) {
+  FEAST_CUDA_TRY(cudaMemsetAsync(w.counter, 0, 256 * 3, s));
+  FEAST_CUDA_TRY(cudaMemsetAsync(w.rotcount, 0, sizeof(unsigned) * kMaxSweeps, s));
+  int occ = 0;
+  FEAST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, jacobi_kernel<S>, 256, 0));
+  const int64_t tasks = (k / 2 + 1) * (k / 2 + 1) + k * (k / 2 + 1);
+  int P = (int)std::min<int64_t>((int64_t)std::max(1, occ) * num_sms, cdiv(tasks, 256 * 8));
+  P = std::max(1, std::min(P, num_sms));
+  int maxs = kMaxSweeps;
+  CoopWork wl = w;
+  void* args[] = {&H, &k, &ld, &V, &ldv, &tol, &wl, &P, &maxs};
+  FEAST_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)jacobi_kernel<S>, dim3(P), dim3(256), args, 0, s));
+}
+
+template <typename S> void get_diag(const S* H, int64_t k, int64_t ld, double* d, cudaStream_t s) {
+  get_diag_kernel<S><<<grid1d(k), 256, 0, s>>>(H, k, ld, d);
+  FEAST_LAUNCH_CHECK();
+}
+
+template <typename S> void col_norms2(const S* X, int64_t n, int64_t k, int64_t ld, double* out, cudaStream_t s) {
+  if (k <= 0) return;
+  col_norms2_kernel<S><<<(unsigned)k, 256, 0, s>>>(X, n, ld, out);
+  FEAST_LAUNCH_CHECK();
+}
+
+template <typename S>
+void resid_norms2(const S* AX, const S* X, int64_t n, int64_t k, int64_t ld, const double* lam, double* out,
+                  cudaStream_t s) {
+  if (k <= 0) return;
+  resid_norms2_kernel<S><<<(unsigned)k, 256, 0, s>>>(AX, X, n, ld, lam, out);
+  FEAST_LAUNCH_CHECK();
+}
+
+template <typename S>
+void ritz_residual(S* R, const S* AX, const S* X, int64_t n, int64_t k, int64_t ld, const double* lam, cudaStream_t s) {
+  ritz_residual_kernel<S><<<grid1d(n * k), 256, 0, s>>>(R, AX, X, n, k, ld, lam);
+  FEAST_LAUNCH_CHECK();
+}
+
+template <typename S>
+void gather_cols(S* dst, int64_t lddst, const S* src, int64_t ldsrc, int64_t n, const int* idx, int64_t k,
+                 const double* scale, cudaStream_t s) {
+  if (k <= 0) return;
+  gather_cols_kernel<S><<<grid1d(n * k), 256, 0, s>>>(dst, lddst, src, ldsrc, n, idx, k, scale);
+  FEAST_LAUNCH_CHECK();
+}
+
+template <typename S> void scale_cols(S* X, int64_t n, int64_t k, int64_t ld, const double* scale, cudaStream_t s) {
+  if (k <= 0) return;
+  scale_cols_kernel<S><<<grid1d(n * k), 256, 0, s>>>(X, n, k, ld, scale);
+  FEAST_LAUNCH_CHECK();
+}
+
+template <typename S>
+void accumulate_filter(S* Xf, int64_t ld, const c128* Y, int64_t n, int64_t m, int nodes, const c128* w,
+                       cudaStream_t s) {
+  accumulate_kernel<S><<<grid1d(n * m), 256, 0, s>>>(Xf, ld, Y, n, m, nodes, w);
+  FEAST_LAUNCH_CHECK();
+}
+
+template <typename S>
+void refine_residual(c128* R, const S* X, int64_t ldx, const c128* Y, const c128* AY, int64_t n, int64_t m,
+                     int entries, const c128* z_e, cudaStream_t s) {
+  dim3 g(grid1d(n * m), entries);
+  refine_residual_kernel<S><<<g, 256, 0, s>>>(R, X, ldx, Y, AY, n, m, z_e);
+  FEAST_LAUNCH_CHECK();
+}
+
+void entry_norms2(const c128* R, const c128* Y, int64_t n, int64_t m, int entries, double* out, cudaStream_t s) {
+  FEAST_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(double) * 2 * entries, s));
+  dim3 g((unsigned)std::min<int64_t>(cdiv(n * m, 256), 512), entries);
+  entry_norms2_kernel<<<g, 256, 0, s>>>(R, Y, n * m, out);
+  FEAST_LAUNCH_CHECK();
+}
+
+template <typename S> void random_normal(S* X, int64_t n, int64_t m, int64_t ld, unsigned long long seed,
+                                         cudaStream_t s) {
+  random_normal_kernel<S><<<grid1d(n * m), 256, 0, s>>>(X, n, m, ld, seed);
+  FEAST_LAUNCH_CHECK();
+}
+
+template <typename S> void copy_matrix(S* dst, int64_t ldd, const S* src, int64_t lds, int64_t n, int64_t m,
+                                       cudaStream_t s) {
+  if (n <= 0 || m <= 0) return;
+  copy_matrix_kernel<S><<<grid1d(n * m), 256, 0, s>>>(dst, ldd, src, lds, n, m);
+  FEAST_LAUNCH_CHECK();
+}
+
+template <typename S> void set_identity(S* X, int64_t k, int64_t ld, cudaStream_t s) {
+  set_identity_kernel<S><<<grid1d(k * k), 256, 0, s>>>(X, k, ld);
+  FEAST_LAUNCH_CHECK();
+}
+
+template <typename S> void check_finite(const S* X, int64_t n, int64_t m, int64_t ld, int* flag, cudaStream_t s) {
+  check_finite_kernel<S><<<grid1d(n * m), 256, 0, s>>>(X, n, m, ld, flag);
+  FEAST_LAUNCH_CHECK();
+}
+
+#define INST_S(S)                                                                                          \
+  template void hermitize<S>(S*, int64_t, int64_t, cudaStream_t);                                          \
+  template void cholesky_upper<S>(S*, int64_t, int64_t, const CoopWork&, int, cudaStream_t);               \
+  template void tri_inverse_upper<S>(const S*, int64_t, int64_t, S*, int64_t, cudaStream_t);               \
+  template void jacobi_eigh<S>(S*, int64_t, int64_t, S*, int64_t, double, const CoopWork&, int, cudaStream_t); \
+  template void get_diag<S>(const S*, int64_t, int64_t, double*, cudaStream_t);                            \
+  template void col_norms2<S>(const S*, int64_t, int64_t, int64_t, double*, cudaStream_t);                 \
+  template void resid_norms2<S>(const S*, const S*, int64_t, int64_t, int64_t, const double*, double*,     \
+                                cudaStream_t);                                                            \
+  template void ritz_residual<S>(S*, const S*, const S*, int64_t, int64_t, int64_t, const double*,         \
+                                 cudaStream_t);                                                           \
+  template void gather_cols<S>(S*, int64_t, const S*, int64_t, int64_t, const int*, int64_t, const double*, \
+                               cudaStream_t);                                                             \
+  template void scale_cols<S>(S*, int64_t, int64_t, int64_t, const double*, cudaStream_t);                 \
+  template void accumulate_filter<S>(S*, int64_t, const c128*, int64_t, int64_t, int, const c128*,         \
+                                     cudaStream_t);                                                       \
+  template void refine_residual<S>(c128*, const S*, int64_t, const c128*, const c128*, int64_t, int64_t,   \
+                                   int, const c128*, cudaStream_t);                                       \
+  template void random_normal<S>(S*, int64_t, int64_t, int64_t, unsigned long long, cudaStream_t);         \
+  template void copy_matrix<S>(S*, int64_t, const S*, int64_t, int64_t, int64_t, cudaStream_t);            \
+  template void set_identity<S>(S*, int64_t, int64_t, cudaStream_t);                                       \
+  template void check_finite<S>(const S*, int64_t, int64_t, int64_t, int*, cudaStream_t);
+
+INST_S(double)
+INST_S(c128)
+
+}  // namespace feast

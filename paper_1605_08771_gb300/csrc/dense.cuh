@@ -1,0 +1,93 @@
+// Small dense FP64 kernels around the filter: orthonormalisation (Gram,
+// Cholesky, triangular inverse), the Jacobi reduced eigensolver, Ritz
+// residual norms, column gathers, the weighted filter accumulation and the
+// FP64 refinement residual.  S is the subspace scalar: double (real symmetric
+// A) or c128 (complex Hermitian A).
+#pragma once
+
+#include "common.cuh"
+
+namespace feast {
+
+struct CoopWork {
+  unsigned* counter;   // [1] monotone barrier counter
+  int* status;         // [1] fatal status (DeviceStatus)
+  int* info;           // [4] kernel-specific outputs (Cholesky column, sweeps, ...)
+  double* partial;     // [>= 2*num_sms] partial sums
+  unsigned* rotcount;  // [kMaxSweeps]
+  void* rot;           // rotation parameters, >= k/2+1 entries of (c, s, e)
+};
+constexpr int kMaxSweeps = 64;
+size_t coop_work_bytes(int64_t kmax, int num_sms);
+CoopWork coop_work_carve(void* base, int64_t kmax, int num_sms);
+
+// H <- (H + H^H)/2 (k x k, ld)
+template <typename S> void hermitize(S* H, int64_t k, int64_t ld, cudaStream_t s);
+
+// In-place Cholesky G = R^H R, R in the upper triangle.  Returns through
+// w.info[0] the first failing column + 1 (0 = success) after the stream syncs.
+template <typename S>
+void cholesky_upper(S* G, int64_t k, int64_t ld, const CoopWork& w, int num_sms, cudaStream_t s);
+
+// Rinv = R^{-1} for upper-triangular R (k x k); the strict lower part of Rinv is zeroed.
+template <typename S>
+void tri_inverse_upper(const S* R, int64_t k, int64_t ld, S* Rinv, int64_t ldi, cudaStream_t s);
+
+// Two-sided Jacobi with round-robin ordering on the Hermitian k x k matrix H
+// (overwritten by its near-diagonal form); V receives the eigenvectors
+// (unsorted).  Sweeps counted in w.info[1].
+template <typename S>
+void jacobi_eigh(S* H, int64_t k, int64_t ld, S* V, int64_t ldv, double tol, const CoopWork& w,
+                 int num_sms, cudaStream_t s);
+
+// diag[i] = Re H[i,i]
+template <typename S> void get_diag(const S* H, int64_t k, int64_t ld, double* diag, cudaStream_t s);
+
+// out[j] = || X[:, j] ||_2^2
+template <typename S> void col_norms2(const S* X, int64_t n, int64_t k, int64_t ld, double* out, cudaStream_t s);
+
+// out[j] = || AX[:, j] - lam[j] X[:, j] ||_2^2
+template <typename S>
+void resid_norms2(const S* AX, const S* X, int64_t n, int64_t k, int64_t ld, const double* lam, double* out,
+                  cudaStream_t s);
+
+// R[:, j] = AX[:, j] - lam[j] X[:, j]
+template <typename S>
+void ritz_residual(S* R, const S* AX, const S* X, int64_t n, int64_t k, int64_t ld, const double* lam, cudaStream_t s);
+
+// dst[:, j] = src[:, idx[j]] * (scale ? scale[j] : 1)
+template <typename S>
+void gather_cols(S* dst, int64_t lddst, const S* src, int64_t ldsrc, int64_t n, const int* idx, int64_t k,
+                 const double* scale, cudaStream_t s);
+
+// X[:, j] *= scale[j]
+template <typename S> void scale_cols(S* X, int64_t n, int64_t k, int64_t ld, const double* scale, cudaStream_t s);
+
+// Xf = sum_e Re/complex weights:  real A: Xf = sum_j 2 Re(w_j Y_j);
+// complex Hermitian: Xf = sum_j w_j Y_j + conj(w_j) Yadj_j.  Y holds the
+// normal entries then (complex case) the adjoint entries, each n x m.
+template <typename S>
+void accumulate_filter(S* Xf, int64_t ld, const c128* Y, int64_t n, int64_t m, int nodes, const c128* w,
+                       cudaStream_t s);
+
+// R_e = X - z_e Y_e + AY_e for every entry e (complex FP64).
+template <typename S>
+void refine_residual(c128* R, const S* X, int64_t ldx, const c128* Y, const c128* AY, int64_t n, int64_t m,
+                     int entries, const c128* z_e, cudaStream_t s);
+
+// ||R_e||_F^2 and ||Y_e||_F^2 per entry (out[2e], out[2e+1])
+void entry_norms2(const c128* R, const c128* Y, int64_t n, int64_t m, int entries, double* out, cudaStream_t s);
+
+// X0 = seeded N(0,1) (complex: independent N(0,1/2) parts), counter-based
+template <typename S> void random_normal(S* X, int64_t n, int64_t m, int64_t ld, unsigned long long seed,
+                                         cudaStream_t s);
+
+// y = A x (FP64, A real or complex Hermitian) for the power-iteration norm estimate
+template <typename S> void copy_matrix(S* dst, int64_t ldd, const S* src, int64_t lds, int64_t n, int64_t m,
+                                       cudaStream_t s);
+template <typename S> void set_identity(S* X, int64_t k, int64_t ld, cudaStream_t s);
+
+// any non-finite entry in the n x m matrix -> *flag = 1
+template <typename S> void check_finite(const S* X, int64_t n, int64_t m, int64_t ld, int* flag, cudaStream_t s);
+
+}  // namespace feast

@@ -1,0 +1,519 @@
+// Shifted LU with partial pivoting and the blocked triangular solves.
+//
+// Right-looking blocked LU (panel width kPanel), all quadrature nodes in the
+// same launches:
+//   1. panel_lu_kernel: a cooperative launch, `P` CTAs per node each owning a
+//      contiguous slice of the panel's rows.  Per column: every CTA publishes
+//      its local pivot candidate (value, row, and the full panel row), one
+//      bounded group barrier, then every CTA picks the same winner, swaps the
+//      pivot row with the diagonal row where it owns them, scales its part of
+//      the column and applies the rank-1 update to the rest of the panel,
+//      tracking the next column's local maximum on the way.
+//   2. laswp_trsm_kernel: the panel's row interchanges applied to every column
+//      outside the panel (as a gather of at most 2*kPanel touched rows), and
+//      U12 = L11^{-1} A12 by a warp-per-column forward substitution.
+//   3. A22 -= L21 U12 with the batched GEMM.
+// The pivot choice is the first row of largest |m_ik|^2, as in the oracle.
+#include "factor.cuh"
+
+#include <algorithm>
+#include <climits>
+
+namespace feast {
+
+namespace {
+
+constexpr int kPanelThreads = 256;
+
+template <typename F>
+__device__ __forceinline__ void argmax_merge(double& v, int& i, double v2, int i2) {
+  if (v2 > v || (v2 == v && i2 >= 0 && (i < 0 || i2 < i))) { v = v2; i = i2; }
+}
+
+template <typename F>
+__device__ void block_argmax(double& v, int& i) {
+  __shared__ double sv[kPanelThreads / 32];
+  __shared__ int si[kPanelThreads / 32];
+  for (int off = 16; off > 0; off >>= 1) {
+    double v2 = __shfl_down_sync(0xffffffffu, v, off);
+    int i2 = __shfl_down_sync(0xffffffffu, i, off);
+    argmax_merge<F>(v, i, v2, i2);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) { sv[w] = v; si[w] = i; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < kPanelThreads / 32; ++k) argmax_merge<F>(sv[0], si[0], sv[k], si[k]);
+  }
+  __syncthreads();
+  v = sv[0];
+  i = si[0];
+}
+
+template <typename F>
+__global__ void __launch_bounds__(kPanelThreads)
+panel_lu_kernel(F* M, int64_t n, int64_t ld, int64_t stride, int k0, int jb, int P, int64_t R,
+                int32_t* ipiv, PanelWork w, unsigned base) {
+  const int b = blockIdx.x / P;
+  const int c = blockIdx.x % P;
+  const int t = threadIdx.x;
+  F* Mb = M + (int64_t)b * stride;
+  const int64_t row_lo = k0 + (int64_t)c * R;
+  const int64_t row_hi = min(n, row_lo + R);
+  unsigned* ctr = w.counters + b;
+  F* cand_row = (F*)w.cand_row;
+  F* diag_row = (F*)w.diag_row;
+  __shared__ F s_u[kPanel];
+  __shared__ F s_d[kPanel];
+  __shared__ int s_p;
+  __shared__ int s_win;
+
+  // local maximum of column k0
+  double v = -1.0;
+  int vi = -1;
+  for (int64_t i = row_lo + t; i < row_hi; i += kPanelThreads) {
+    double a = (double)abs2(Mb[i + (int64_t)k0 * ld]);
+    argmax_merge<F>(v, vi, a, (int)i);
+  }
+  block_argmax<F>(v, vi);
+
+  for (int j = 0; j < jb; ++j) {
+    const int64_t d = k0 + j;
+    const int64_t col = k0 + j;
+    const int par = j & 1;
+    const int64_t slot = ((int64_t)b * 2 + par) * w.pmax + c;
+    if (t == 0) {
+      w.cand_val[slot] = v;
+      w.cand_idx[slot] = vi;
+    }
+    if (vi >= 0)
+      for (int cc = t; cc < jb; cc += kPanelThreads)
+        cand_row[slot * kPanel + cc] = Mb[vi + (int64_t)(k0 + cc) * ld];
+    if (d >= row_lo && d < row_hi)
+      for (int cc = t; cc < jb; cc += kPanelThreads)
+        diag_row[((int64_t)b * 2 + par) * kPanel + cc] = Mb[d + (int64_t)(k0 + cc) * ld];
+    if (!group_barrier(ctr, base + (unsigned)(j + 1) * (unsigned)P, w.status)) return;
+
+    if (t == 0) {
+      double bv = -1.0;
+      int bi = -1;
+      const int64_t s0 = ((int64_t)b * 2 + par) * w.pmax;
+      for (int q = 0; q < P; ++q) {
+        double cv = __ldcg(&w.cand_val[s0 + q]);
+        int ci = __ldcg(&w.cand_idx[s0 + q]);
+        if (ci >= 0 && (cv > bv || (cv == bv && (bi < 0 || ci < bi)))) {
+          bv = cv;
+          bi = ci;
+          s_win = q;
+        }
+      }
+      s_p = bi;
+    }
+    __syncthreads();
+    const int p = s_p;
+    const int win = s_win;
+    if (p < 0) return;  // cannot happen for jb <= rows; defensive
+    for (int cc = t; cc < jb; cc += kPanelThreads) {
+      const int64_t ws = ((int64_t)b * 2 + par) * w.pmax + win;
+      const F* src = cand_row + ws * kPanel + cc;
+      const F* dsrc = diag_row + ((int64_t)b * 2 + par) * kPanel + cc;
+      F u, dd;
+      if constexpr (sizeof(F) == 16) {
+        double2 x = __ldcg((const double2*)src);
+        double2 y = __ldcg((const double2*)dsrc);
+        u = F{x.x, x.y};
+        dd = F{y.x, y.y};
+      } else {
+        float2 x = __ldcg((const float2*)src);
+        float2 y = __ldcg((const float2*)dsrc);
+        u = F{x.x, x.y};
+        dd = F{y.x, y.y};
+      }
+      s_u[cc] = u;
+      s_d[cc] = dd;
+    }
+    __syncthreads();
+    const F piv = s_u[j];
+    F inv;
+    if (abs2(piv) == 0) {
+      inv = num<F>::zero();
+      if (c == 0 && t == 0) atomicCAS(&w.zero_pivot[b], 0, (int)col + 1);
+    } else {
+      inv = recip(piv);
+    }
+    if (d >= row_lo && d < row_hi)
+      for (int cc = t; cc < jb; cc += kPanelThreads) Mb[d + (int64_t)(k0 + cc) * ld] = s_u[cc];
+    if (p != d && p >= row_lo && p < row_hi)
+      for (int cc = t; cc < jb; cc += kPanelThreads) Mb[p + (int64_t)(k0 + cc) * ld] = s_d[cc];
+    if (c == 0 && t == 0) ipiv[(int64_t)b * n + d] = p;
+    __syncthreads();
+
+    v = -1.0;
+    vi = -1;
+    const int64_t lo = max(row_lo, d + 1);
+    for (int64_t i = lo + t; i < row_hi; i += kPanelThreads) {
+      F* ri = Mb + i;
+      F l = ri[col * ld] * inv;
+      ri[col * ld] = l;
+      for (int cc = j + 1; cc < jb; ++cc) {
+        F x = ri[(int64_t)(k0 + cc) * ld] - l * s_u[cc];
+        ri[(int64_t)(k0 + cc) * ld] = x;
+        if (cc == j + 1) argmax_merge<F>(v, vi, (double)abs2(x), (int)i);
+      }
+    }
+    if (j + 1 < jb) block_argmax<F>(v, vi);
+    else __syncthreads();
+  }
+
+  // net effect of the panel's interchanges on the rows it touched:
+  // after the swaps, row dst holds the former row src
+  if (c == 0 && t == 0) {
+    int rows[2 * kPanel], content[2 * kPanel];
+    int cnt = 0;
+    auto slot_of = [&](int r) {
+      for (int q = 0; q < cnt; ++q)
+        if (rows[q] == r) return q;
+      rows[cnt] = r;
+      content[cnt] = r;
+      return cnt++;
+    };
+    for (int j = 0; j < jb; ++j) {
+      int a = slot_of(k0 + j);
+      int bb = slot_of(ipiv[(int64_t)b * n + k0 + j]);
+      int tmp = content[a];
+      content[a] = content[bb];
+      content[bb] = tmp;
+    }
+    int out = 0;
+    for (int q = 0; q < cnt; ++q)
+      if (content[q] != rows[q]) {
+        w.swap_dst[b * 2 * kPanel + out] = rows[q];
+        w.swap_src[b * 2 * kPanel + out] = content[q];
+        ++out;
+      }
+    w.swap_cnt[b] = out;
+  }
+}
+
+constexpr int kSwapWarps = 8;
+
+template <typename F>
+__global__ void __launch_bounds__(kSwapWarps * 32)
+laswp_trsm_kernel(F* M, int64_t n, int64_t ld, int64_t stride, int k0, int jb,
+                  const int* swap_src, const int* swap_dst, const int* swap_cnt) {
+  const int b = blockIdx.y;
+  F* Mb = M + (int64_t)b * stride;
+  __shared__ F L11[kPanel][kPanel + 1];
+  for (int l = threadIdx.x; l < jb * jb; l += blockDim.x) {
+    int i = l % jb, j = l / jb;
+    L11[i][j] = Mb[(k0 + i) + (int64_t)(k0 + j) * ld];
+  }
+  __syncthreads();
+  const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t idx = (int64_t)blockIdx.x * kSwapWarps + wp;
+  if (idx >= n - jb) return;
+  const int64_t c = idx < k0 ? idx : idx + jb;
+  F* colp = Mb + c * ld;
+  const int cnt = swap_cnt[b];
+  const int* src = swap_src + b * 2 * kPanel;
+  const int* dst = swap_dst + b * 2 * kPanel;
+  F v0 = num<F>::zero(), v1 = num<F>::zero();
+  if (lane < cnt) v0 = colp[src[lane]];
+  if (lane + 32 < cnt) v1 = colp[src[lane + 32]];
+  __syncwarp();
+  if (lane < cnt) colp[dst[lane]] = v0;
+  if (lane + 32 < cnt) colp[dst[lane + 32]] = v1;
+  __syncwarp();
+  if (c >= k0 + jb) {
+    F x = lane < jb ? colp[k0 + lane] : num<F>::zero();
+    for (int j = 0; j < jb - 1; ++j) {
+      F xj = shfl(x, j);
+      if (lane > j && lane < jb) x = x - L11[lane][j] * xj;
+    }
+    if (lane < jb) colp[k0 + lane] = x;
+  }
+}
+
+__global__ void build_perm_kernel(const int32_t* ipiv, int32_t* perm, int64_t n) {
+  extern __shared__ int32_t sp[];
+  const int b = blockIdx.x;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) sp[i] = (int32_t)i;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int32_t* ip = ipiv + (int64_t)b * n;
+    for (int64_t k = 0; k < n; ++k) {
+      int32_t p = ip[k];
+      if (p != k) {
+        int32_t tmp = sp[k];
+        sp[k] = sp[p];
+        sp[p] = tmp;
+      }
+    }
+  }
+  __syncthreads();
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) perm[(int64_t)b * n + i] = sp[i];
+}
+
+template <typename F, typename TA>
+__global__ void form_shifted_kernel(F* M, int64_t n, int64_t ld, int64_t stride,
+                                    const TA* A, int64_t lda, const c128* z) {
+  const int b = blockIdx.y;
+  const c128 zb = z[b];
+  F* Mb = M + (int64_t)b * stride;
+  const int64_t total = n * n;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx % n, j = idx / n;
+    c128 v = -cvt<c128>(A[i + j * lda]);
+    if (i == j) v = v + zb;
+    Mb[i + j * ld] = cvt<F>(v);
+  }
+}
+
+// Triangular block solve on a kPanel x kPanel diagonal block, warp per RHS
+// column.  mode 0: L (unit lower, stored), 1: U^H (lower, from the stored U),
+// 2: U (upper, stored), 3: L^H (unit upper, from the stored L).
+template <typename F>
+__global__ void __launch_bounds__(256)
+trsm_diag_kernel(const F* M, int64_t ld, int64_t stride, F* Y, int64_t n, int64_t m,
+                 int64_t ystride, int64_t r0, int bs, int mode) {
+  const int b = blockIdx.y;
+  const F* Mb = M + (int64_t)b * stride;
+  __shared__ F T[kPanel][kPanel + 1];
+  for (int l = threadIdx.x; l < bs * bs; l += blockDim.x) {
+    if (mode == 0 || mode == 2) {
+      int i = l % bs, j = l / bs;
+      T[i][j] = Mb[(r0 + i) + (r0 + j) * ld];
+    } else {
+      int j = l % bs, i = l / bs;
+      T[i][j] = conj(Mb[(r0 + j) + (r0 + i) * ld]);
+    }
+  }
+  __syncthreads();
+  const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t cidx = (int64_t)blockIdx.x * 8 + wp;
+  if (cidx >= m) return;
+  F* y = Y + (int64_t)b * ystride + cidx * n + r0;
+  F x = lane < bs ? y[lane] : num<F>::zero();
+  if (mode <= 1) {
+    for (int j = 0; j < bs; ++j) {
+      if (mode == 1 && lane == j) x = x * recip(T[j][j]);
+      F xj = shfl(x, j);
+      if (lane > j && lane < bs) x = x - T[lane][j] * xj;
+    }
+  } else {
+    for (int j = bs - 1; j >= 0; --j) {
+      if (mode == 2 && lane == j) x = x * recip(T[j][j]);
+      F xj = shfl(x, j);
+      if (lane < j) x = x - T[lane][j] * xj;
+    }
+  }
+  if (lane < bs) y[lane] = x;
+}
+
+template <typename F, typename TB>
+__global__ void permute_in_kernel(F* Y, int64_t ystride, const TB* B, int64_t ldb, int64_t bstride, int64_t n, int64_t m,
+                                  const int32_t* perm, bool adjoint) {
+  const int b = blockIdx.y;
+  const int64_t total = n * m;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx % n, c = idx / n;
+    const int64_t src = adjoint ? i : perm[(int64_t)b * n + i];
+    Y[(int64_t)b * ystride + idx] = cvt<F>(B[(int64_t)b * bstride + src + c * ldb]);
+  }
+}
+
+template <typename F, typename TO>
+__global__ void permute_out_kernel(TO* Out, int64_t ostride, const F* Y, int64_t ystride, int64_t n,
+                                   int64_t m, const int32_t* perm, bool adjoint, bool accumulate) {
+  const int b = blockIdx.y;
+  const int64_t total = n * m;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx % n, c = idx / n;
+    const int64_t dst = adjoint ? perm[(int64_t)b * n + i] : i;
+    TO* o = Out + (int64_t)b * ostride + dst + c * n;
+    TO v = cvt<TO>(Y[(int64_t)b * ystride + idx]);
+    *o = accumulate ? (*o + v) : v;
+  }
+}
+
+inline unsigned grid1d(int64_t total, int threads = 256) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(total, threads), 8192));
+}
+
+}  // namespace
+
+size_t panel_work_bytes(int nodes, int pmax, size_t eb) {
+  size_t s = 0;
+  auto add = [&](size_t bytes) { s += (bytes + 255) & ~size_t(255); };
+  add(sizeof(unsigned) * nodes);
+  add(sizeof(int));
+  add(sizeof(int) * nodes);
+  add(sizeof(double) * nodes * 2 * pmax);
+  add(sizeof(int) * nodes * 2 * pmax);
+  add(eb * nodes * 2 * pmax * kPanel);
+  add(eb * nodes * 2 * kPanel);
+  add(sizeof(int) * nodes * 2 * kPanel);
+  add(sizeof(int) * nodes * 2 * kPanel);
+  add(sizeof(int) * nodes);
+  return s;
+}
+
+PanelWork panel_work_carve(void* base, int nodes, int pmax, size_t eb) {
+  char* p = (char*)base;
+  auto take = [&](size_t bytes) { char* r = p; p += (bytes + 255) & ~size_t(255); return (void*)r; };
+  PanelWork w{};
+  w.counters = (unsigned*)take(sizeof(unsigned) * nodes);
+  w.status = (int*)take(sizeof(int));
+  w.zero_pivot = (int*)take(sizeof(int) * nodes);
+  w.cand_val = (double*)take(sizeof(double) * nodes * 2 * pmax);
+  w.cand_idx = (int*)take(sizeof(int) * nodes * 2 * pmax);
+  w.cand_row = take(eb * nodes * 2 * pmax * kPanel);
+  w.diag_row = take(eb * nodes * 2 * kPanel);
+  w.swap_src = (int*)take(sizeof(int) * nodes * 2 * kPanel);
+  w.swap_dst = (int*)take(sizeof(int) * nodes * 2 * kPanel);
+  w.swap_cnt = (int*)take(sizeof(int) * nodes);
+  w.pmax = pmax;
+  return w;
+}
+
+template <typename F, typename TA>
+void form_shifted(F* M, int64_t n, int64_t ld, int64_t stride, int nodes,
+                  const TA* A, int64_t lda, const c128* z, cudaStream_t s) {
+  dim3 grid(grid1d(n * n), nodes);
+  form_shifted_kernel<F, TA><<<grid, 256, 0, s>>>(M, n, ld, stride, A, lda, z);
+  FEAST_LAUNCH_CHECK();
+}
+
+template <typename F>
+void lu_factor_batched(F* M, int64_t n, int64_t ld, int64_t stride, int nodes,
+                       int32_t* ipiv, int32_t* perm, const PanelWork& w,
+                       int num_sms, cudaStream_t s) {
+  FEAST_CUDA_TRY(cudaMemsetAsync(w.counters, 0, sizeof(unsigned) * nodes, s));
+  FEAST_CUDA_TRY(cudaMemsetAsync(w.status, 0, sizeof(int), s));
+  FEAST_CUDA_TRY(cudaMemsetAsync(w.zero_pivot, 0, sizeof(int) * nodes, s));
+  int occ = 0;
+  FEAST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, panel_lu_kernel<F>, kPanelThreads, 0));
+  const int max_coop = std::max(1, occ) * num_sms;
+  unsigned base = 0;
+  for (int64_t k0 = 0; k0 < n; k0 += kPanel) {
+    const int jb = (int)std::min<int64_t>(kPanel, n - k0);
+    const int64_t H = n - k0;
+    int P = (int)std::min<int64_t>(cdiv(H, 64), std::max(1, max_coop / nodes));
+    P = std::max(1, std::min(P, w.pmax));
+    const int64_t R = cdiv(H, P);
+    P = (int)cdiv(H, R);  // no empty CTAs
+    int k0i = (int)k0;
+    PanelWork wl = w;
+    void* args[] = {&M, &n, &ld, &stride, &k0i, (void*)&jb, &P, (void*)&R, &ipiv, &wl, &base};
+    FEAST_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)panel_lu_kernel<F>, dim3(nodes * P),
+                                               dim3(kPanelThreads), args, 0, s));
+    base += (unsigned)jb * (unsigned)P;
+    if (n - jb > 0) {
+      dim3 g2((unsigned)cdiv(n - jb, kSwapWarps), nodes);
+      laswp_trsm_kernel<F><<<g2, kSwapWarps * 32, 0, s>>>(M, n, ld, stride, k0i, jb, w.swap_src, w.swap_dst,
+                                                           w.swap_cnt);
+      FEAST_LAUNCH_CHECK();
+    }
+    const int64_t r1 = k0 + jb;
+    if (r1 < n) {
+      GemmArgs g{};
+      g.M = n - r1; g.N = n - r1; g.K = jb;
+      g.A = M + r1 + k0 * ld; g.lda = ld; g.strideA = stride; g.opA = OP_N;
+      g.B = M + k0 + r1 * ld; g.ldb = ld; g.strideB = stride; g.opB = OP_N;
+      g.C = M + r1 + r1 * ld; g.ldc = ld; g.strideC = stride;
+      g.alpha = C1(-1.0); g.beta = C1(1.0); g.batch = nodes; g.ksplit = 1;
+      gemm<F, F, F>(g, s);
+    }
+  }
+  const size_t smem = sizeof(int32_t) * (size_t)n;
+  if (smem > 48 * 1024)
+    FEAST_CUDA_TRY(cudaFuncSetAttribute(build_perm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  build_perm_kernel<<<nodes, 256, smem, s>>>(ipiv, perm, n);
+  FEAST_LAUNCH_CHECK();
+}
+
+template <typename F>
+void lu_solve_batched(const F* M, int64_t n, int64_t ld, int64_t stride, int nodes,
+                      F* Y, int64_t m, int64_t ystride, bool adjoint, cudaStream_t s) {
+  if (m <= 0) return;
+  const int64_t nblk = cdiv(n, kPanel);
+  dim3 gd((unsigned)cdiv(m, 8), nodes);
+  // forward substitution with L (normal) or U^H (adjoint)
+  for (int64_t bi = 0; bi < nblk; ++bi) {
+    const int64_t r0 = bi * kPanel;
+    const int bs = (int)std::min<int64_t>(kPanel, n - r0);
+    const int64_t r1 = r0 + bs;
+    trsm_diag_kernel<F><<<gd, 256, 0, s>>>(M, ld, stride, Y, n, m, ystride, r0, bs, adjoint ? 1 : 0);
+    FEAST_LAUNCH_CHECK();
+    if (r1 < n) {
+      GemmArgs g{};
+      g.M = n - r1; g.N = m; g.K = bs;
+      if (!adjoint) { g.A = M + r1 + r0 * ld; g.opA = OP_N; }
+      else { g.A = M + r0 + r1 * ld; g.opA = OP_C; }
+      g.lda = ld; g.strideA = stride;
+      g.B = Y + r0; g.ldb = n; g.strideB = ystride; g.opB = OP_N;
+      g.C = Y + r1; g.ldc = n; g.strideC = ystride;
+      g.alpha = C1(-1.0); g.beta = C1(1.0); g.batch = nodes; g.ksplit = 1;
+      gemm<F, F, F>(g, s);
+    }
+  }
+  // back substitution with U (normal) or L^H (adjoint)
+  for (int64_t bi = nblk - 1; bi >= 0; --bi) {
+    const int64_t r0 = bi * kPanel;
+    const int bs = (int)std::min<int64_t>(kPanel, n - r0);
+    trsm_diag_kernel<F><<<gd, 256, 0, s>>>(M, ld, stride, Y, n, m, ystride, r0, bs, adjoint ? 3 : 2);
+    FEAST_LAUNCH_CHECK();
+    if (r0 > 0) {
+      GemmArgs g{};
+      g.M = r0; g.N = m; g.K = bs;
+      if (!adjoint) { g.A = M + r0 * ld; g.opA = OP_N; }
+      else { g.A = M + r0; g.opA = OP_C; }
+      g.lda = ld; g.strideA = stride;
+      g.B = Y + r0; g.ldb = n; g.strideB = ystride; g.opB = OP_N;
+      g.C = Y; g.ldc = n; g.strideC = ystride;
+      g.alpha = C1(-1.0); g.beta = C1(1.0); g.batch = nodes; g.ksplit = 1;
+      gemm<F, F, F>(g, s);
+    }
+  }
+}
+
+template <typename F, typename TB>
+void permute_in(F* Y, int64_t ystride, const TB* B, int64_t ldb, int64_t bstride, int64_t n, int64_t m,
+                const int32_t* perm, int nodes, bool adjoint, cudaStream_t s) {
+  dim3 grid(grid1d(n * m), nodes);
+  permute_in_kernel<F, TB><<<grid, 256, 0, s>>>(Y, ystride, B, ldb, bstride, n, m, perm, adjoint);
+  FEAST_LAUNCH_CHECK();
+}
+
+template <typename F, typename TO>
+void permute_out(TO* Out, int64_t ostride, const F* Y, int64_t ystride, int64_t n, int64_t m,
+                 const int32_t* perm, int nodes, bool adjoint, bool accumulate, cudaStream_t s) {
+  dim3 grid(grid1d(n * m), nodes);
+  permute_out_kernel<F, TO><<<grid, 256, 0, s>>>(Out, ostride, Y, ystride, n, m, perm, adjoint, accumulate);
+  FEAST_LAUNCH_CHECK();
+}
+
+#define INST_F(F)                                                                                    \
+  template void lu_factor_batched<F>(F*, int64_t, int64_t, int64_t, int, int32_t*, int32_t*,        \
+                                     const PanelWork&, int, cudaStream_t);                          \
+  template void lu_solve_batched<F>(const F*, int64_t, int64_t, int64_t, int, F*, int64_t, int64_t, \
+                                    bool, cudaStream_t);                                             \
+  template void form_shifted<F, double>(F*, int64_t, int64_t, int64_t, int, const double*, int64_t, \
+                                        const c128*, cudaStream_t);                                  \
+  template void form_shifted<F, c128>(F*, int64_t, int64_t, int64_t, int, const c128*, int64_t,     \
+                                      const c128*, cudaStream_t);                                    \
+  template void permute_in<F, double>(F*, int64_t, const double*, int64_t, int64_t, int64_t, int64_t,        \
+                                      const int32_t*, int, bool, cudaStream_t);                      \
+  template void permute_in<F, c128>(F*, int64_t, const c128*, int64_t, int64_t, int64_t, int64_t,            \
+                                    const int32_t*, int, bool, cudaStream_t);                        \
+  template void permute_out<F, c128>(c128*, int64_t, const F*, int64_t, int64_t, int64_t,           \
+                                     const int32_t*, int, bool, bool, cudaStream_t);
+
+INST_F(c128)
+INST_F(c64)
+
+}  // namespace feast

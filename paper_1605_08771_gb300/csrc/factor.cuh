@@ -1,0 +1,65 @@
+// Shifted complex LU with partial pivoting, batched over the quadrature nodes,
+// and the multi-right-hand-side triangular solves that apply (z_j I - A)^{-1}
+// and its adjoint.  F is the factor precision: c128 (FP64 path) or c64 (the
+// low-precision factor of the mixed path).
+#pragma once
+
+#include "common.cuh"
+#include "gemm.cuh"
+
+namespace feast {
+
+constexpr int kPanel = 32;        // panel width = triangular-solve block size
+
+// Scratch the cooperative panel kernel needs (device pointers, sized by
+// panel_work_bytes()).
+struct PanelWork {
+  unsigned* counters;   // [nodes] monotone barrier counters
+  int* status;          // [1] fatal device status (DeviceStatus)
+  int* zero_pivot;      // [nodes] first zero-pivot column + 1, or 0
+  double* cand_val;     // [nodes][2][pmax]
+  int* cand_idx;        // [nodes][2][pmax]
+  void* cand_row;       // [nodes][2][pmax][kPanel] of F
+  void* diag_row;       // [nodes][2][kPanel] of F
+  int* swap_src;        // [nodes][2*kPanel]
+  int* swap_dst;        // [nodes][2*kPanel]
+  int* swap_cnt;        // [nodes]
+  int pmax;
+};
+
+size_t panel_work_bytes(int nodes, int pmax, size_t elem_bytes);
+PanelWork panel_work_carve(void* base, int nodes, int pmax, size_t elem_bytes);
+
+// M_j = z_j I - A for the `nodes` shifts z (device array of c128), A real
+// (double) or complex (c128), column-major with leading dimension lda.
+template <typename F, typename TA>
+void form_shifted(F* M, int64_t n, int64_t ld, int64_t stride, int nodes,
+                  const TA* A, int64_t lda, const c128* z, cudaStream_t s);
+
+// In-place P_j M_j = L_j U_j for every node.  ipiv[j*n + k] is the row swapped
+// with row k at step k; perm[j*n + i] the original row now at row i.
+template <typename F>
+void lu_factor_batched(F* M, int64_t n, int64_t ld, int64_t stride, int nodes,
+                       int32_t* ipiv, int32_t* perm, const PanelWork& w,
+                       int num_sms, cudaStream_t s);
+
+// Y_e <- (P^T L U)^{-1} Y_e  (adjoint = false) or (P^T L U)^{-H} Y_e
+// (adjoint = true) for e = 0..nodes-1, Y_e = Y + e*ystride (n x m, ld n).
+// The row permutation is applied by permute_in / permute_out.
+template <typename F>
+void lu_solve_batched(const F* M, int64_t n, int64_t ld, int64_t stride, int nodes,
+                      F* Y, int64_t m, int64_t ystride, bool adjoint, cudaStream_t s);
+
+// Y_e = P B_e (normal) or B_e (adjoint) converted to F;  B_e = B + e*bstride is
+// n x m with ld ldb (bstride = 0: one right-hand side block for every node).
+template <typename F, typename TB>
+void permute_in(F* Y, int64_t ystride, const TB* B, int64_t ldb, int64_t bstride, int64_t n, int64_t m,
+                const int32_t* perm, int nodes, bool adjoint, cudaStream_t s);
+
+// Out_e = Y_e (normal) or P^T Y_e (adjoint), converted to TO, optionally
+// accumulated (Out_e += ...).
+template <typename F, typename TO>
+void permute_out(TO* Out, int64_t ostride, const F* Y, int64_t ystride, int64_t n, int64_t m,
+                 const int32_t* perm, int nodes, bool adjoint, bool accumulate, cudaStream_t s);
+
+}  // namespace feast

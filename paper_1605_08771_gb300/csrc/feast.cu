@@ -1,0 +1,1124 @@
+// Host driver of the FEAST interval eigensolver and the C ABI (include/feast.h).
+//
+// The driver follows the paper's Appendix: FEAST (filter, Rayleigh-Ritz,
+// check), XFEAST (window of s filtered blocks, Sect. II-A) and RFEAST (s
+// Rayleigh-Ritz passes expanding with Ritz residuals, Sect. II-B).  All
+// arithmetic runs in the CUDA kernels of factor.cu, gemm.cu and dense.cu; the
+// host only sequences launches, reads back the k Ritz values and residuals
+// it needs for the selection and stopping decisions, and sorts them.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "../../include/feast.h"
+#include "dense.cuh"
+#include "factor.cuh"
+#include "gemm.cuh"
+
+using namespace feast;
+
+// ---------------------------------------------------------------------------
+// context and workspace
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Arena {
+  struct Block { char* p; size_t cap, off; };
+  std::vector<Block> blocks;
+  void* alloc(size_t bytes) {
+    bytes = (bytes + 255) & ~size_t(255);
+    if (bytes == 0) bytes = 256;
+    for (auto& b : blocks)
+      if (b.cap - b.off >= bytes) {
+        void* r = b.p + b.off;
+        b.off += bytes;
+        return r;
+      }
+    size_t cap = std::max(bytes, size_t(64) << 20);
+    char* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, cap);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      throw std::bad_alloc();
+    }
+    blocks.push_back({p, cap, bytes});
+    return p;
+  }
+  void reset() {
+    for (auto& b : blocks) b.off = 0;
+  }
+  void release() {
+    for (auto& b : blocks) cudaFree(b.p);
+    blocks.clear();
+  }
+};
+
+}  // namespace
+
+struct feast_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  Arena arena;
+  feast_stats last{};
+};
+
+namespace {
+
+struct FeastError {
+  int code;
+};
+
+template <typename T> T* dalloc(feast_ctx* c, int64_t count) { return (T*)c->arena.alloc(sizeof(T) * (size_t)std::max<int64_t>(count, 1)); }
+
+void sync(feast_ctx* c) { FEAST_CUDA_TRY(cudaStreamSynchronize(c->stream)); }
+
+template <typename T> void to_host(feast_ctx* c, T* h, const T* d, int64_t count) {
+  if (count <= 0) return;
+  FEAST_CUDA_TRY(cudaMemcpyAsync(h, d, sizeof(T) * count, cudaMemcpyDeviceToHost, c->stream));
+  sync(c);
+}
+template <typename T> void to_dev(feast_ctx* c, T* d, const T* h, int64_t count) {
+  if (count <= 0) return;
+  FEAST_CUDA_TRY(cudaMemcpyAsync(d, h, sizeof(T) * count, cudaMemcpyHostToDevice, c->stream));
+  sync(c);  // the host vector may be reused right after
+}
+
+double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// ---------------------------------------------------------------------------
+// quadrature (Eq. 3 with the ellipse / Gauss-Legendre reading)
+// ---------------------------------------------------------------------------
+// Gauss-Legendre abscissae (ascending) and weights by Newton's method on
+// P_n with the three-term recurrence, started from cos(pi (j - 1/4)/(n + 1/2)).
+void gauss_legendre(int n, std::vector<double>& t, std::vector<double>& wt) {
+  t.assign(n, 0.0);
+  wt.assign(n, 0.0);
+  for (int j = 1; j <= n; ++j) {
+    double x = std::cos(M_PI * (j - 0.25) / (n + 0.5));
+    double p = 0, dp = 0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = x;
+      for (int k = 1; k < n; ++k) {
+        double p2 = ((2.0 * k + 1.0) * x * p1 - k * p0) / (k + 1.0);
+        p0 = p1;
+        p1 = p2;
+      }
+      p = p1;
+      dp = n * (x * p1 - p0) / (x * x - 1.0);
+      double dx = p / dp;
+      x -= dx;
+      if (std::fabs(dx) < 1e-16) break;
+    }
+    {
+      double p0 = 1.0, p1 = x;
+      for (int k = 1; k < n; ++k) {
+        double p2 = ((2.0 * k + 1.0) * x * p1 - k * p0) / (k + 1.0);
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (x * p1 - p0) / (x * x - 1.0);
+    }
+    t[n - j] = x;  // cos estimate descends with j: store ascending
+    wt[n - j] = 2.0 / ((1.0 - x * x) * dp * dp);
+  }
+}
+
+void contour(double lmin, double lmax, int nc, double aspect, std::vector<c128>& z, std::vector<c128>& w) {
+  std::vector<double> t, om;
+  gauss_legendre(nc, t, om);
+  const double c = 0.5 * (lmin + lmax), r = 0.5 * (lmax - lmin);
+  z.resize(nc);
+  w.resize(nc);
+  for (int j = 0; j < nc; ++j) {
+    const double th = 0.5 * M_PI * (1.0 - t[j]);
+    z[j] = c128{c + r * std::cos(th), aspect * r * std::sin(th)};
+    w[j] = c128{0.25 * om[j] * aspect * r * std::cos(th), 0.25 * om[j] * r * std::sin(th)};
+  }
+}
+
+// ---------------------------------------------------------------------------
+// selection rules (Sect. II-A end; Sect. II-B)
+// ---------------------------------------------------------------------------
+bool in_interval(double l, double a, double b) { return l > a && l < b; }
+
+std::vector<int> select_pairs(const std::vector<double>& lam, const std::vector<double>& res, double a, double b,
+                              int m0) {
+  const int k = (int)lam.size();
+  std::vector<int> ins, outs;
+  for (int i = 0; i < k; ++i) (in_interval(lam[i], a, b) ? ins : outs).push_back(i);
+  auto by_res = [&](int x, int y) { return res[x] < res[y] || (res[x] == res[y] && (lam[x] < lam[y] || (lam[x] == lam[y] && x < y))); };
+  std::stable_sort(ins.begin(), ins.end(), by_res);
+  std::stable_sort(outs.begin(), outs.end(), by_res);
+  std::vector<int> sel(ins.begin(), ins.begin() + std::min<int>((int)ins.size(), m0));
+  for (size_t i = 0; (int)sel.size() < m0 && i < outs.size(); ++i) sel.push_back(outs[i]);
+  std::sort(sel.begin(), sel.end(), [&](int x, int y) { return lam[x] < lam[y] || (lam[x] == lam[y] && x < y); });
+  return sel;
+}
+
+// ---------------------------------------------------------------------------
+// solver
+// ---------------------------------------------------------------------------
+template <typename S>
+struct Solver {
+  static constexpr bool kCplx = is_cx<S>::value;
+  feast_ctx* ctx;
+  cudaStream_t st;
+  const S* A;
+  int64_t n, lda;
+  double lmin, lmax;
+  int nc;
+  feast_opts o;
+  double anorm = 0.0;
+  int E = 0;  // solve entries per filter: nc (real) or 2 nc (complex)
+
+  std::vector<c128> z, w;
+  c128* d_w = nullptr;
+  c128* d_ze = nullptr;
+  void* M = nullptr;
+  int32_t* ipiv = nullptr;
+  int32_t* perm = nullptr;
+  PanelWork pw{};
+  CoopWork cw{};
+  int64_t kmax = 0, mmax = 0;
+
+  // filter scratch
+  c128* Y = nullptr;
+  c128* Yw = nullptr;   // F64: adjoint work; mixed: residual R
+  c128* AY = nullptr;
+  c64* Yc = nullptr;
+  double* d_en = nullptr;
+  int refine_steps = 0;
+  // Rayleigh-Ritz scratch
+  S *Qb = nullptr, *Wb = nullptr, *Xr = nullptr, *AXr = nullptr, *T1 = nullptr, *T2 = nullptr;
+  S *Ar0 = nullptr, *Ar = nullptr, *Vk = nullptr, *Gs = nullptr, *Ri = nullptr, *Cs = nullptr, *Cs2 = nullptr;
+  S* part = nullptr;
+  int64_t part_elems = 0;
+  double *d_lam = nullptr, *d_nrm = nullptr, *d_scale = nullptr;
+  int* d_idx = nullptr;
+  int* d_flag = nullptr;
+
+  std::vector<double> lam, res;  // last Rayleigh-Ritz
+  int last_sweeps = 0;
+
+  Solver(feast_ctx* c, const S* A_, int64_t n_, int64_t lda_, double a, double b, int nc_, const feast_opts& o_)
+      : ctx(c), st(c->stream), A(A_), n(n_), lda(lda_), lmin(a), lmax(b), nc(nc_), o(o_) {
+    E = kCplx ? 2 * nc : nc;
+  }
+
+  // ---- allocation ----
+  void alloc_common(int64_t kmax_, int64_t mmax_) {
+    kmax = std::max<int64_t>(kmax_, 1);
+    mmax = std::max<int64_t>(mmax_, 1);
+    contour(lmin, lmax, nc, o.aspect, z, w);
+    d_w = dalloc<c128>(ctx, nc);
+    d_ze = dalloc<c128>(ctx, E);
+    std::vector<c128> ze(E);
+    for (int j = 0; j < nc; ++j) {
+      ze[j] = z[j];
+      if (kCplx) ze[nc + j] = conj(z[j]);
+    }
+    to_dev(ctx, d_w, w.data(), nc);
+    to_dev(ctx, d_ze, ze.data(), E);
+    cw = coop_work_carve(ctx->arena.alloc(coop_work_bytes(kmax, ctx->num_sms)), kmax, ctx->num_sms);
+    d_flag = dalloc<int>(ctx, 4);
+    d_en = dalloc<double>(ctx, 2 * E);
+  }
+  void alloc_factors() {
+    const size_t eb = o.prec == FEAST_PREC_F64 ? sizeof(c128) : sizeof(c64);
+    M = ctx->arena.alloc(eb * (size_t)nc * n * n);
+    ipiv = dalloc<int32_t>(ctx, (int64_t)nc * n);
+    perm = dalloc<int32_t>(ctx, (int64_t)nc * n);
+    const int pmax = std::max(1, ctx->num_sms * 8);
+    pw = panel_work_carve(ctx->arena.alloc(panel_work_bytes(nc, pmax, eb)), nc, pmax, eb);
+  }
+  void alloc_filter(int64_t m) {
+    const int64_t nm = n * m;
+    Y = dalloc<c128>(ctx, E * nm);
+    if (o.prec == FEAST_PREC_F64) {
+      if (kCplx) Yw = dalloc<c128>(ctx, nc * nm);
+    } else {
+      Yw = dalloc<c128>(ctx, E * nm);
+      AY = dalloc<c128>(ctx, E * nm);
+      Yc = dalloc<c64>(ctx, E * nm);
+    }
+  }
+  void alloc_rr() {
+    Qb = dalloc<S>(ctx, n * kmax);
+    Wb = dalloc<S>(ctx, n * kmax);
+    Xr = dalloc<S>(ctx, n * kmax);
+    AXr = dalloc<S>(ctx, n * kmax);
+    T1 = dalloc<S>(ctx, n * kmax);
+    T2 = dalloc<S>(ctx, n * kmax);
+    const int64_t kk = kmax * kmax;
+    Ar0 = dalloc<S>(ctx, kk); Ar = dalloc<S>(ctx, kk); Vk = dalloc<S>(ctx, kk); Gs = dalloc<S>(ctx, kk);
+    Ri = dalloc<S>(ctx, kk); Cs = dalloc<S>(ctx, kk); Cs2 = dalloc<S>(ctx, kk);
+    part_elems = 32 * kk;
+    part = dalloc<S>(ctx, part_elems);
+    d_lam = dalloc<double>(ctx, kmax);
+    d_nrm = dalloc<double>(ctx, kmax);
+    d_scale = dalloc<double>(ctx, kmax);
+    d_idx = dalloc<int>(ctx, kmax);
+  }
+
+  // ---- small GEMM helpers ----
+  void mm(int64_t Mr, int64_t Nc, int64_t K, c128 alpha, const S* Am, int64_t la, int opA, const S* Bm, int64_t lb,
+          int opB, c128 beta, S* Cm, int64_t lc) {
+    gemm_simple<S, S, S>(Mr, Nc, K, alpha, Am, la, opA, Bm, lb, opB, beta, Cm, lc, st);
+  }
+  // C (Mr x Nc) = op(A) op(B) with a long reduction K: split-K
+  void mm_reduce(int64_t Mr, int64_t Nc, int64_t K, const S* Am, int64_t la, int opA, const S* Bm, int64_t lb,
+                 int opB, S* Cm, int64_t lc) {
+    int ks = (int)std::max<int64_t>(1, std::min<int64_t>(32, K / 256));
+    while (ks > 1 && (int64_t)ks * lc * Nc > part_elems) --ks;
+    gemm_simple<S, S, S>(Mr, Nc, K, C1(1.0), Am, la, opA, Bm, lb, opB, C1(0.0), Cm, lc, st, ks,
+                         ks > 1 ? (void*)part : nullptr);
+  }
+  // A times a block (FP64)
+  void apply_A(const S* Xm, int64_t k, S* Out) { mm(n, k, n, C1(1.0), A, lda, OP_N, Xm, n, OP_N, C1(0.0), Out, n); }
+
+  // ---- norm estimate: power iteration from ones/sqrt(n) ----
+  double estimate_norm() {
+    S* v = T1;
+    S* wv = T2;
+    std::vector<S> ones(n, cvt<S>(1.0 / std::sqrt((double)n)));
+    to_dev(ctx, v, ones.data(), n);
+    double est = 0.0, nr2 = 0.0;
+    for (int it = 0; it < 40; ++it) {
+      apply_A(v, 1, wv);
+      col_norms2<S>(wv, n, 1, n, d_nrm, st);
+      to_host(ctx, &nr2, d_nrm, 1);
+      est = std::sqrt(nr2);
+      if (est == 0.0) return 0.0;
+      double sc = 1.0 / est;
+      to_dev(ctx, d_scale, &sc, 1);
+      int zero = 0;
+      to_dev(ctx, d_idx, &zero, 1);
+      gather_cols<S>(v, n, wv, n, n, d_idx, 1, d_scale, st);
+    }
+    return est;
+  }
+
+  // ---- factorisation of all shifts ----
+  template <typename F>
+  void factor_t() {
+    F* Mf = (F*)M;
+    std::vector<c128> zf(z.begin(), z.end());
+    c128* d_zf = dalloc<c128>(ctx, nc);
+    to_dev(ctx, d_zf, zf.data(), nc);
+    form_shifted<F, S>(Mf, n, n, n * n, nc, A, lda, d_zf, st);
+    lu_factor_batched<F>(Mf, n, n, n * n, nc, ipiv, perm, pw, ctx->num_sms, st);
+    int status = 0;
+    std::vector<int> zp(nc);
+    to_host(ctx, &status, pw.status, 1);
+    to_host(ctx, zp.data(), pw.zero_pivot, nc);
+    if (status == DEV_BARRIER_TIMEOUT) throw FeastError{FEAST_ERR_TIMEOUT};
+    for (int j = 0; j < nc; ++j)
+      if (zp[j]) throw FeastError{FEAST_ERR_SINGULAR};
+  }
+  void factor() {
+    if (o.prec == FEAST_PREC_F64) factor_t<c128>();
+    else factor_t<c64>();
+  }
+
+  // ---- filter: Xf = rho(A) X (Eq. 3) ----
+  template <typename TB>
+  void solve_lowp(const TB* B, int64_t ldb, int64_t bstride, int64_t m, bool accumulate) {
+    const int64_t nm = n * m;
+    const c64* Mf = (const c64*)M;
+    permute_in<c64, TB>(Yc, nm, B, ldb, bstride, n, m, perm, nc, false, st);
+    lu_solve_batched<c64>(Mf, n, n, n * n, nc, Yc, m, nm, false, st);
+    permute_out<c64, c128>(Y, nm, Yc, nm, n, m, perm, nc, false, accumulate, st);
+    if (kCplx) {
+      permute_in<c64, TB>(Yc + nc * nm, nm, B + nc * bstride, ldb, bstride, n, m, perm, nc, true, st);
+      lu_solve_batched<c64>(Mf, n, n, n * n, nc, Yc + nc * nm, m, nm, true, st);
+      permute_out<c64, c128>(Y + nc * nm, nm, Yc + nc * nm, nm, n, m, perm, nc, true, accumulate, st);
+    }
+  }
+
+  void filter(const S* X, int64_t m, S* Xf) {
+    const int64_t nm = n * m;
+    if (o.prec == FEAST_PREC_F64) {
+      const c128* Mf = (const c128*)M;
+      permute_in<c128, S>(Y, nm, X, n, 0, n, m, perm, nc, false, st);
+      lu_solve_batched<c128>(Mf, n, n, n * n, nc, Y, m, nm, false, st);
+      if (kCplx) {
+        permute_in<c128, S>(Yw, nm, X, n, 0, n, m, perm, nc, true, st);
+        lu_solve_batched<c128>(Mf, n, n, n * n, nc, Yw, m, nm, true, st);
+        permute_out<c128, c128>(Y + nc * nm, nm, Yw, nm, n, m, perm, nc, true, false, st);
+      }
+    } else {
+      solve_lowp<S>(X, n, 0, m, false);
+      const double rtol = o.refine_tol > 0 ? o.refine_tol : 2.0 * 2.220446049250313e-16 * std::sqrt((double)n);
+      std::vector<double> en(2 * E), prev(E, -1.0);
+      for (int step = 0; step < o.refine_max; ++step) {
+        // R_e = X - (z_e I - A) Y_e in FP64
+        gemm_simple<S, c128, c128>(n, E * m, n, C1(1.0), A, lda, OP_N, Y, n, OP_N, C1(0.0), AY, n, st);
+        refine_residual<S>(Yw, X, n, Y, AY, n, m, E, d_ze, st);
+        entry_norms2(Yw, Y, n, m, E, d_en, st);
+        to_host(ctx, en.data(), d_en, 2 * E);
+        bool conv = true, stagnant = step > 0;
+        for (int e = 0; e < E; ++e) {
+          const c128 ze = e < nc ? z[e] : conj(z[e - nc]);
+          const double rn = std::sqrt(en[2 * e]), yn = std::sqrt(en[2 * e + 1]);
+          const bool ok = rn <= rtol * (anorm + std::sqrt(abs2(ze))) * yn;
+          if (!ok) {
+            conv = false;
+            if (prev[e] < 0 || rn < 0.5 * prev[e]) stagnant = false;
+          }
+          prev[e] = rn;
+        }
+        if (conv || stagnant) break;
+        solve_lowp<c128>(Yw, n, nm, m, true);
+        ++refine_steps;
+      }
+    }
+    accumulate_filter<S>(Xf, n, Y, n, m, nc, d_w, st);
+  }
+
+  // ---- orthonormalisation ----
+  // Qout = X R^{-1} with X^H X = R^H R.  X, Qout: nr x k (ld nr).  false on breakdown.
+  bool cholqr_once(const S* X, int64_t nr, int64_t k, S* Qout) {
+    mm_reduce(k, k, nr, X, nr, OP_C, X, nr, OP_N, Gs, k);
+    hermitize<S>(Gs, k, k, st);
+    cholesky_upper<S>(Gs, k, k, cw, ctx->num_sms, st);
+    int info[2] = {0, 0};
+    to_host(ctx, info, cw.info, 1);
+    int status = 0;
+    to_host(ctx, &status, cw.status, 1);
+    if (status == DEV_BARRIER_TIMEOUT) throw FeastError{FEAST_ERR_TIMEOUT};
+    if (info[0] != 0) return false;
+    tri_inverse_upper<S>(Gs, k, k, Ri, k, st);
+    mm(nr, k, k, C1(1.0), X, nr, OP_N, Ri, k, OP_N, C1(0.0), Qout, nr);
+    return true;
+  }
+  // Hermitian eigendecomposition of the k x k matrix H (ld k, overwritten);
+  // eigenvalues unsorted in `ev`, vectors in Vk (ld k)
+  void eig(S* H, int64_t k, std::vector<double>& ev) {
+    jacobi_eigh<S>(H, k, k, Vk, k, 1e-15, cw, ctx->num_sms, st);
+    get_diag<S>(H, k, k, d_lam, st);
+    ev.resize(k);
+    to_host(ctx, ev.data(), d_lam, k);
+    int status = 0;
+    to_host(ctx, &status, cw.status, 1);
+    to_host(ctx, &last_sweeps, cw.info + 1, 1);
+    if (status == DEV_BARRIER_TIMEOUT) throw FeastError{FEAST_ERR_TIMEOUT};
+  }
+  // Gram-eigendecomposition route (Sect. II-A): X^H X = V S^2 V^H, keep
+  // s^2 >= trunc s_1^2, U = X V S^{-1}, then one Cholesky-QR pass.
+  int64_t gram_eig_orth(const S* X, int64_t nr, int64_t k, S* Qout, S* tmp, double trunc) {
+    mm_reduce(k, k, nr, X, nr, OP_C, X, nr, OP_N, Gs, k);
+    hermitize<S>(Gs, k, k, st);
+    std::vector<double> s2;
+    eig(Gs, k, s2);
+    std::vector<int> ord(k);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return s2[a] > s2[b]; });
+    if (!(s2[ord[0]] > 0.0)) return 0;
+    std::vector<int> keep;
+    std::vector<double> sc;
+    for (int i : ord)
+      if (s2[i] >= trunc * s2[ord[0]]) {
+        keep.push_back(i);
+        sc.push_back(1.0 / std::sqrt(s2[i]));
+      }
+    const int64_t r = (int64_t)keep.size();
+    to_dev(ctx, d_idx, keep.data(), r);
+    to_dev(ctx, d_scale, sc.data(), r);
+    gather_cols<S>(Cs, k, Vk, k, k, d_idx, r, d_scale, st);
+    mm(nr, r, k, C1(1.0), X, nr, OP_N, Cs, k, OP_N, C1(0.0), tmp, nr);
+    if (!cholqr_once(tmp, nr, r, Qout)) return 0;
+    return r;
+  }
+  // Cholesky-QR twice; Gram route on breakdown.  Returns the rank (0 = failure).
+  int64_t orthonormalize(const S* X, int64_t nr, int64_t k, S* Qout, S* tmp) {
+    if (cholqr_once(X, nr, k, tmp) && cholqr_once(tmp, nr, k, Qout)) return k;
+    return gram_eig_orth(X, nr, k, Qout, tmp, 1e-12);
+  }
+
+  // ---- Rayleigh-Ritz ----
+  // W = A Q, A' = Q^H W (ld kmax) for the first k columns of Qb
+  void rr_project(int64_t k) {
+    apply_A(Qb, k, Wb);
+    mm_reduce(k, k, n, Qb, n, OP_C, Wb, n, OP_N, Ar0, kmax);
+    hermitize<S>(Ar0, k, kmax, st);
+  }
+  // diagonalise A'[0:k, 0:k]: lam (ascending), Xr = Q V, AXr = W V, res
+  void rr_solve(int64_t k) {
+    copy_matrix<S>(Ar, k, Ar0, kmax, k, k, st);
+    std::vector<double> ev;
+    eig(Ar, k, ev);
+    std::vector<int> ord(k);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return ev[a] < ev[b]; });
+    lam.resize(k);
+    for (int64_t i = 0; i < k; ++i) lam[i] = ev[ord[i]];
+    to_dev(ctx, d_idx, ord.data(), k);
+    gather_cols<S>(Cs, k, Vk, k, k, d_idx, k, nullptr, st);
+    mm(n, k, k, C1(1.0), Qb, n, OP_N, Cs, k, OP_N, C1(0.0), Xr, n);
+    mm(n, k, k, C1(1.0), Wb, n, OP_N, Cs, k, OP_N, C1(0.0), AXr, n);
+    to_dev(ctx, d_lam, lam.data(), k);
+    resid_norms2<S>(AXr, Xr, n, k, n, d_lam, d_nrm, st);
+    res.resize(k);
+    to_host(ctx, res.data(), d_nrm, k);
+    for (auto& r : res) r = std::sqrt(r) / anorm;
+  }
+
+  // ---- drivers ----
+  struct Out {
+    int status = 0;
+    std::vector<int> idx;  // returned pairs (indices into lam/res/Xr), ascending lambda
+    int iterations = 0, filters = 0, m_expected = -1;
+    std::vector<double> hist;
+  };
+
+  std::vector<int> in_sorted(const std::vector<int>& cand) {
+    std::vector<int> v;
+    for (int i : cand)
+      if (in_interval(lam[i], lmin, lmax)) v.push_back(i);
+    return v;
+  }
+  void finish(Out& out, std::vector<int> ins) {
+    std::sort(ins.begin(), ins.end(), [&](int a, int b) { return lam[a] < lam[b] || (lam[a] == lam[b] && a < b); });
+    out.idx = ins;
+  }
+  std::vector<int> lowest_residual(std::vector<int> v, int m) {
+    std::stable_sort(v.begin(), v.end(), [&](int a, int b) {
+      return res[a] < res[b] || (res[a] == res[b] && (lam[a] < lam[b] || (lam[a] == lam[b] && a < b)));
+    });
+    if ((int)v.size() > m) v.resize(std::max(m, 0));
+    return v;
+  }
+  double max_res(const std::vector<int>& v) {
+    double r = 0.0;
+    for (int i : v) r = std::max(r, res[i]);
+    return v.empty() ? INFINITY : r;
+  }
+
+  Out run_plain(S* X, int m0, double tol) {
+    Out out;
+    int64_t kx = m0;
+    S* Xf = T2;
+    for (int it = 1; it <= o.max_iter; ++it) {
+      filter(X, kx, Xf);
+      ++out.filters;
+      const int64_t k = orthonormalize(Xf, n, kx, Qb, T1);
+      if (k == 0) throw FeastError{FEAST_ERR_ORTH};
+      rr_project(k);
+      rr_solve(k);
+      std::vector<int> all(k);
+      std::iota(all.begin(), all.end(), 0);
+      std::vector<int> ins = in_sorted(all);
+      const double r = max_res(ins);
+      out.hist.push_back(r);
+      out.iterations = it;
+      if ((!ins.empty() && r <= tol) || (ins.empty() && it >= 2)) {
+        finish(out, ins);
+        return out;
+      }
+      copy_matrix<S>(X, n, Xr, n, n, k, st);
+      kx = k;
+    }
+    std::vector<int> all(lam.size());
+    std::iota(all.begin(), all.end(), 0);
+    finish(out, in_sorted(all));
+    out.status = FEAST_WARN_MAXITER;
+    return out;
+  }
+
+  // block QR of the window (see the XFEAST reading): returns k
+  int64_t block_qr(const std::vector<S*>& blocks, int64_t mb) {
+    int64_t kq = 0;
+    std::vector<double> nr2(mb);
+    for (S* B : blocks) {
+      col_norms2<S>(B, n, mb, n, d_nrm, st);
+      to_host(ctx, nr2.data(), d_nrm, mb);
+      double bn = 0.0;
+      for (double v : nr2) bn = std::max(bn, std::sqrt(v));
+      if (bn == 0.0) continue;
+      S* P = T1;
+      copy_matrix<S>(P, n, B, n, n, mb, st);
+      if (kq > 0)
+        for (int rep = 0; rep < 2; ++rep) {
+          mm_reduce(kq, mb, n, Qb, n, OP_C, P, n, OP_N, Cs2, kq);
+          mm(n, mb, kq, C1(-1.0), Qb, n, OP_N, Cs2, kq, OP_N, C1(1.0), P, n);
+        }
+      mm_reduce(mb, mb, n, P, n, OP_C, P, n, OP_N, Gs, mb);
+      hermitize<S>(Gs, mb, mb, st);
+      std::vector<double> s2;
+      eig(Gs, mb, s2);
+      std::vector<int> ord(mb);
+      std::iota(ord.begin(), ord.end(), 0);
+      std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return s2[a] < s2[b]; });
+      std::vector<int> keep;
+      std::vector<double> sc;
+      const double thr = (1e-13 * bn) * (1e-13 * bn);
+      for (int i : ord)
+        if (s2[i] >= thr) {
+          keep.push_back(i);
+          sc.push_back(1.0 / std::sqrt(s2[i]));
+        }
+      const int64_t r = (int64_t)keep.size();
+      if (r == 0) continue;
+      to_dev(ctx, d_idx, keep.data(), r);
+      to_dev(ctx, d_scale, sc.data(), r);
+      gather_cols<S>(Cs, mb, Vk, mb, mb, d_idx, r, d_scale, st);
+      S* U = T2;
+      mm(n, r, mb, C1(1.0), P, n, OP_N, Cs, mb, OP_N, C1(0.0), U, n);
+      if (kq > 0) {
+        mm_reduce(kq, r, n, Qb, n, OP_C, U, n, OP_N, Cs2, kq);
+        mm(n, r, kq, C1(-1.0), Qb, n, OP_N, Cs2, kq, OP_N, C1(1.0), U, n);
+      }
+      if (!cholqr_once(U, n, r, Qb + kq * n)) throw FeastError{FEAST_ERR_ORTH};
+      kq += r;
+    }
+    return kq;
+  }
+
+  // in-I count of Rayleigh-Ritz restricted to span(B) (the newest block)
+  int expected_count_newest(int64_t k, const S* B, int64_t mb) {
+    S* C = T1;  // k x mb (ld k), small
+    mm_reduce(k, mb, n, Qb, n, OP_C, B, n, OP_N, C, k);
+    S* Ct = T2;
+    const int64_t r = orthonormalize(C, k, mb, Ct, AXr /*scratch, k*mb fits*/);
+    if (r == 0) return 0;
+    // H = Ct^H A' Ct
+    mm(k, r, k, C1(1.0), Ar0, kmax, OP_N, Ct, k, OP_N, C1(0.0), Cs2, k);
+    mm(r, r, k, C1(1.0), Ct, k, OP_C, Cs2, k, OP_N, C1(0.0), Gs, r);
+    hermitize<S>(Gs, r, r, st);
+    std::vector<double> ev;
+    eig(Gs, r, ev);
+    int cnt = 0;
+    for (double v : ev) cnt += in_interval(v, lmin, lmax);
+    return cnt;
+  }
+
+  Out run_xfeast(S* X0, int m0, double tol, int s) {
+    Out out;
+    std::vector<S*> ring(s);
+    for (int i = 0; i < s; ++i) ring[i] = dalloc<S>(ctx, n * m0);
+    // step 0: X_0 with unit columns, then X_i = rho(A)^i X_0
+    col_norms2<S>(X0, n, m0, n, d_nrm, st);
+    std::vector<double> nr2(m0), sc(m0);
+    std::vector<int> iden(m0);
+    to_host(ctx, nr2.data(), d_nrm, m0);
+    for (int j = 0; j < m0; ++j) {
+      sc[j] = nr2[j] > 0 ? 1.0 / std::sqrt(nr2[j]) : 1.0;
+      iden[j] = j;
+    }
+    to_dev(ctx, d_scale, sc.data(), m0);
+    to_dev(ctx, d_idx, iden.data(), m0);
+    gather_cols<S>(ring[0], n, X0, n, n, d_idx, m0, d_scale, st);
+    for (int i = 1; i < s; ++i) {
+      filter(ring[i - 1], m0, ring[i]);
+      ++out.filters;
+    }
+    S* Xsel = dalloc<S>(ctx, n * m0);
+    std::vector<int> ins;
+    for (int it = 1; it <= o.max_iter; ++it) {
+      const int64_t k = block_qr(ring, m0);
+      if (k == 0) throw FeastError{FEAST_ERR_ORTH};
+      rr_project(k);
+      rr_solve(k);
+      std::vector<int> sel = select_pairs(lam, res, lmin, lmax, m0);
+      const int mexp = expected_count_newest(k, ring[s - 1], m0);
+      out.m_expected = mexp;
+      ins = lowest_residual(in_sorted(sel), mexp);
+      const double r = max_res(ins);
+      out.hist.push_back(r);
+      out.iterations = it;
+      if ((!ins.empty() && r <= tol) || (ins.empty() && it >= 2)) {
+        finish(out, ins);
+        return out;
+      }
+      if (it == o.max_iter) break;
+      to_dev(ctx, d_idx, sel.data(), (int64_t)sel.size());
+      gather_cols<S>(Xsel, n, Xr, n, n, d_idx, (int64_t)sel.size(), nullptr, st);
+      S* oldest = ring[0];
+      filter(Xsel, (int64_t)sel.size(), oldest);
+      ++out.filters;
+      std::rotate(ring.begin(), ring.begin() + 1, ring.end());
+    }
+    finish(out, ins);
+    out.status = FEAST_WARN_MAXITER;
+    return out;
+  }
+
+  Out run_rfeast(S* X, int m0, double tol, int s) {
+    Out out;
+    S* Xf = dalloc<S>(ctx, n * m0);
+    S* AXs = dalloc<S>(ctx, n * m0);
+    std::vector<int> ins;
+    int64_t kx = m0;
+    for (int it = 1; it <= o.max_iter; ++it) {
+      filter(X, kx, Xf);
+      ++out.filters;
+      int64_t k = orthonormalize(Xf, n, kx, Qb, T1);
+      if (k == 0) throw FeastError{FEAST_ERR_ORTH};
+      rr_project(k);
+      int mexp = 0;
+      std::vector<int> sel;
+      for (int j = 1; j <= s; ++j) {
+        rr_solve(k);
+        if (j == 1) {
+          mexp = 0;
+          for (double v : lam) mexp += in_interval(v, lmin, lmax);
+        }
+        sel = select_pairs(lam, res, lmin, lmax, m0);
+        const int64_t ms = (int64_t)sel.size();
+        to_dev(ctx, d_idx, sel.data(), ms);
+        gather_cols<S>(X, n, Xr, n, n, d_idx, ms, nullptr, st);
+        kx = ms;
+        if (j < s && k + ms <= kmax) {
+          gather_cols<S>(AXs, n, AXr, n, n, d_idx, ms, nullptr, st);
+          std::vector<double> ls(ms);
+          for (int64_t i = 0; i < ms; ++i) ls[i] = lam[sel[i]];
+          to_dev(ctx, d_lam, ls.data(), ms);
+          S* R = T1;
+          ritz_residual<S>(R, AXs, X, n, ms, n, d_lam, st);
+          col_norms2<S>(R, n, ms, n, d_nrm, st);
+          std::vector<double> nr2(ms), sc(ms);
+          std::vector<int> iden(ms);
+          to_host(ctx, nr2.data(), d_nrm, ms);
+          for (int64_t i = 0; i < ms; ++i) {
+            sc[i] = nr2[i] > 0 ? 1.0 / std::sqrt(nr2[i]) : 1.0;
+            iden[i] = (int)i;
+          }
+          to_dev(ctx, d_scale, sc.data(), ms);
+          to_dev(ctx, d_idx, iden.data(), ms);
+          scale_cols<S>(R, n, ms, n, d_scale, st);
+          for (int rep = 0; rep < 2; ++rep) {
+            mm_reduce(k, ms, n, Qb, n, OP_C, R, n, OP_N, Cs2, k);
+            mm(n, ms, k, C1(-1.0), Qb, n, OP_N, Cs2, k, OP_N, C1(1.0), R, n);
+          }
+          S* U = Qb + k * n;
+          const int64_t ku = orthonormalize(R, n, ms, U, T2);
+          if (ku == 0) break;  // nothing new to append
+          S* WU = Wb + k * n;
+          apply_A(U, ku, WU);
+          // A' blocks: [Q U]^H A [Q U] from the new columns only
+          mm_reduce(k, ku, n, Qb, n, OP_C, WU, n, OP_N, Ar0 + k * kmax, kmax);
+          mm_reduce(ku, k, n, U, n, OP_C, Wb, n, OP_N, Ar0 + k, kmax);
+          mm_reduce(ku, ku, n, U, n, OP_C, WU, n, OP_N, Ar0 + k + k * kmax, kmax);
+          hermitize<S>(Ar0, k + ku, kmax, st);
+          k += ku;
+        } else if (j < s) {
+          break;
+        }
+      }
+      out.m_expected = mexp;
+      ins = lowest_residual(in_sorted(sel), mexp);
+      const double r = max_res(ins);
+      out.hist.push_back(r);
+      out.iterations = it;
+      if ((!ins.empty() && r <= tol) || (ins.empty() && it >= 2)) {
+        finish(out, ins);
+        return out;
+      }
+    }
+    finish(out, ins);
+    out.status = FEAST_WARN_MAXITER;
+    return out;
+  }
+};
+
+int check_common(feast_ctx* ctx, const void* A, int dtype, int64_t n, int64_t lda, double lmin, double lmax,
+                 int n_c) {
+  if (!ctx || !A || n < 1 || lda < n || n_c < 1 || n_c > 256) return FEAST_ERR_ARG;
+  if (dtype != FEAST_R64 && dtype != FEAST_C128) return FEAST_ERR_ARG;
+  if (!std::isfinite(lmin) || !std::isfinite(lmax) || !(lmin < lmax)) return FEAST_ERR_ARG;
+  if (n > INT32_MAX / 2) return FEAST_ERR_ARG;
+  return FEAST_OK;
+}
+
+template <typename Fn>
+int guarded(feast_ctx* ctx, Fn&& fn) {
+  try {
+    int r = fn();
+    return r;
+  } catch (const FeastError& e) {
+    if (ctx) cudaStreamSynchronize(ctx->stream);
+    cudaGetLastError();
+    return e.code;
+  } catch (const CudaFailure& e) {
+    if (e.err == cudaErrorMemoryAllocation) { cudaGetLastError(); return FEAST_ERR_NOMEM; }
+    return FEAST_ERR_CUDA;
+  } catch (const std::bad_alloc&) {
+    cudaGetLastError();
+    return FEAST_ERR_NOMEM;
+  }
+}
+
+template <typename S>
+int check_finite_dev(feast_ctx* ctx, const S* X, int64_t n, int64_t m, int64_t ld) {
+  int* flag = dalloc<int>(ctx, 1);
+  FEAST_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
+  check_finite<S>(X, n, m, ld, flag, ctx->stream);
+  int h = 0;
+  to_host(ctx, &h, flag, 1);
+  return h ? FEAST_ERR_NONFINITE : FEAST_OK;
+}
+
+template <typename S>
+int solve_t(feast_ctx* ctx, const S* A, int64_t n, int64_t lda, double lmin, double lmax, int m0, int n_c,
+            double tol, const feast_opts& o, double* evals, S* evecs, double* resout, int* m_found, int* iters,
+            feast_stats* stats) {
+  const double t0 = now_ms();
+  ctx->arena.reset();
+  if (int r = check_finite_dev<S>(ctx, A, n, n, lda)) return r;
+  Solver<S> sv(ctx, A, n, lda, lmin, lmax, n_c, o);
+  const int s = std::max(1, o.s);
+  const int64_t kmax = (o.variant == FEAST_PLAIN) ? m0 : (int64_t)s * m0;
+  sv.alloc_common(kmax, m0);
+  sv.alloc_rr();
+  sv.alloc_filter(m0);
+  sv.alloc_factors();
+  sv.anorm = o.anorm > 0 ? o.anorm : sv.estimate_norm();
+  if (!(sv.anorm > 0)) sv.anorm = 1.0;
+  S* X = dalloc<S>(ctx, n * m0);
+  if (o.x0) {
+    copy_matrix<S>(X, n, (const S*)o.x0, n, n, m0, ctx->stream);
+    if (int r = check_finite_dev<S>(ctx, X, n, m0, n)) return r;
+  } else {
+    random_normal<S>(X, n, m0, n, o.seed, ctx->stream);
+  }
+  sync(ctx);
+  const double tf0 = now_ms();
+  sv.factor();
+  sync(ctx);
+  const double tf1 = now_ms();
+  typename Solver<S>::Out out;
+  if (o.variant == FEAST_XFEAST) out = sv.run_xfeast(X, m0, tol, s);
+  else if (o.variant == FEAST_RFEAST) out = sv.run_rfeast(X, m0, tol, s);
+  else out = sv.run_plain(X, m0, tol);
+  const int mf = (int)out.idx.size();
+  std::vector<double> ev(mf), rs(mf);
+  for (int i = 0; i < mf; ++i) {
+    ev[i] = sv.lam[out.idx[i]];
+    rs[i] = sv.res[out.idx[i]];
+  }
+  if (mf > 0) {
+    to_dev(ctx, sv.d_idx, out.idx.data(), mf);
+    gather_cols<S>(evecs, n, sv.Xr, n, n, sv.d_idx, mf, nullptr, ctx->stream);
+  }
+  sync(ctx);
+  for (int i = 0; i < mf; ++i) {
+    evals[i] = ev[i];
+    resout[i] = rs[i];
+  }
+  *m_found = mf;
+  *iters = out.iterations;
+  feast_stats st{};
+  st.iterations = out.iterations;
+  st.filters = out.filters;
+  st.refine_steps = sv.refine_steps;
+  st.m_expected = out.m_expected;
+  st.factor_ms = tf1 - tf0;
+  st.total_ms = now_ms() - t0;
+  st.max_residual = 0.0;
+  for (double r : rs) st.max_residual = std::max(st.max_residual, r);
+  for (size_t i = 0; i < out.hist.size() && i < 128; ++i) st.history[i] = out.hist[i];
+  ctx->last = st;
+  if (stats) *stats = st;
+  return out.status;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void feast_opts_default(feast_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->variant = FEAST_PLAIN;
+  o->s = 3;
+  o->prec = FEAST_PREC_F64;
+  o->max_iter = 100;
+  o->refine_max = 10;
+  o->aspect = 1.0;
+  o->anorm = 0.0;
+  o->refine_tol = 0.0;
+  o->seed = 0x1605087710ull;
+  o->x0 = nullptr;
+}
+
+int feast_init(feast_ctx** ctx, int device, void* stream) {
+  if (!ctx) return FEAST_ERR_ARG;
+  *ctx = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    cudaGetLastError();
+    return FEAST_ERR_CUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return FEAST_ERR_CUDA;
+  feast_ctx* c = new (std::nothrow) feast_ctx();
+  if (!c) return FEAST_ERR_NOMEM;
+  c->device = device;
+  c->stream = (cudaStream_t)stream;
+  if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    delete c;
+    return FEAST_ERR_CUDA;
+  }
+  *ctx = c;
+  return FEAST_OK;
+}
+
+int feast_finalize(feast_ctx* ctx) {
+  if (!ctx) return FEAST_ERR_ARG;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  ctx->arena.release();
+  delete ctx;
+  return FEAST_OK;
+}
+
+const char* feast_strerror(int code) {
+  switch (code) {
+    case FEAST_OK: return "success";
+    case FEAST_WARN_MAXITER: return "maximum number of iterations reached before convergence";
+    case FEAST_ERR_ARG: return "invalid argument";
+    case FEAST_ERR_NONFINITE: return "NaN or Inf in the input matrix or subspace";
+    case FEAST_ERR_SINGULAR: return "a shifted matrix z_j I - A is exactly singular";
+    case FEAST_ERR_ORTH: return "the subspace could not be orthonormalised";
+    case FEAST_ERR_M0: return "subspace size m0 too small for the interval";
+    case FEAST_ERR_CUDA: return "CUDA runtime error";
+    case FEAST_ERR_NOMEM: return "device memory allocation failed";
+    case FEAST_ERR_TIMEOUT: return "a bounded device-side wait timed out";
+    default: return "unknown status";
+  }
+}
+
+int feast_contour_nodes(double lmin, double lmax, int n_c, double aspect, double* z, double* w) {
+  if (!z || !w || n_c < 1 || n_c > 256 || !(lmin < lmax) || !(aspect > 0)) return FEAST_ERR_ARG;
+  std::vector<c128> zz, ww;
+  contour(lmin, lmax, n_c, aspect, zz, ww);
+  for (int j = 0; j < n_c; ++j) {
+    z[2 * j] = zz[j].re;
+    z[2 * j + 1] = zz[j].im;
+    w[2 * j] = ww[j].re;
+    w[2 * j + 1] = ww[j].im;
+  }
+  return FEAST_OK;
+}
+
+int feast_interval_solve(feast_ctx* ctx, const void* A, int dtype, int64_t n, int64_t lda, double lmin, double lmax,
+                         int m0, int n_c, double tol, const feast_opts* opts, double* evals, void* evecs,
+                         double* res, int* m_found, int* iterations, feast_stats* stats) {
+  if (int r = check_common(ctx, A, dtype, n, lda, lmin, lmax, n_c)) return r;
+  if (m0 < 1 || m0 > n || !(tol > 0) || !evals || !evecs || !res || !m_found || !iterations) return FEAST_ERR_ARG;
+  feast_opts o;
+  if (opts) o = *opts; else feast_opts_default(&o);
+  if (o.variant < 0 || o.variant > 2 || o.prec < 0 || o.prec > 1 || o.max_iter < 1 || !(o.aspect > 0)) return FEAST_ERR_ARG;
+  if (o.variant != FEAST_PLAIN && (o.s < 1 || (int64_t)o.s * m0 > 65536)) return FEAST_ERR_ARG;
+  if (o.refine_max < 0) return FEAST_ERR_ARG;
+  *m_found = 0;
+  *iterations = 0;
+  return guarded(ctx, [&]() {
+    FEAST_CUDA_TRY(cudaSetDevice(ctx->device));
+    if (dtype == FEAST_R64)
+      return solve_t<double>(ctx, (const double*)A, n, lda, lmin, lmax, m0, n_c, tol, o, evals, (double*)evecs, res,
+                             m_found, iterations, stats);
+    return solve_t<c128>(ctx, (const c128*)A, n, lda, lmin, lmax, m0, n_c, tol, o, evals, (c128*)evecs, res, m_found,
+                         iterations, stats);
+  });
+}
+
+int feast_filter_apply(feast_ctx* ctx, const void* A, int dtype, int64_t n, int64_t lda, double lmin, double lmax,
+                       int n_c, const feast_opts* opts, const void* X, int64_t m, void* Y) {
+  if (int r = check_common(ctx, A, dtype, n, lda, lmin, lmax, n_c)) return r;
+  if (!X || !Y || m < 1) return FEAST_ERR_ARG;
+  feast_opts o;
+  if (opts) o = *opts; else feast_opts_default(&o);
+  if (o.prec < 0 || o.prec > 1 || !(o.aspect > 0) || o.refine_max < 0) return FEAST_ERR_ARG;
+  return guarded(ctx, [&]() {
+    FEAST_CUDA_TRY(cudaSetDevice(ctx->device));
+    ctx->arena.reset();
+    auto run = [&](auto tag) {
+      using S = decltype(tag);
+      Solver<S> sv(ctx, (const S*)A, n, lda, lmin, lmax, n_c, o);
+      sv.alloc_common(1, m);
+      sv.alloc_filter(m);
+      sv.alloc_factors();
+      sv.kmax = 1;
+      sv.T1 = dalloc<S>(ctx, n);
+      sv.T2 = dalloc<S>(ctx, n);
+      sv.d_nrm = dalloc<double>(ctx, 1);
+      sv.d_scale = dalloc<double>(ctx, 1);
+      sv.d_idx = dalloc<int>(ctx, 1);
+      sv.anorm = o.anorm > 0 ? o.anorm : (o.prec == FEAST_PREC_MIXED ? sv.estimate_norm() : 1.0);
+      sv.factor();
+      sv.filter((const S*)X, m, (S*)Y);
+      sync(ctx);
+      ctx->last = feast_stats{};
+      ctx->last.refine_steps = sv.refine_steps;
+      return FEAST_OK;
+    };
+    if (dtype == FEAST_R64) return run(double{});
+    return run(c128{});
+  });
+}
+
+int feast_shifted_lu(feast_ctx* ctx, const void* A, int dtype, int64_t n, int64_t lda, const double* z, int nz,
+                     int prec, void* LU, int32_t* perm) {
+  if (int r = check_common(ctx, A, dtype, n, lda, -1.0, 1.0, nz)) return r;
+  if (!z || !LU || !perm || (prec != FEAST_PREC_F64 && prec != FEAST_PREC_MIXED)) return FEAST_ERR_ARG;
+  return guarded(ctx, [&]() {
+    FEAST_CUDA_TRY(cudaSetDevice(ctx->device));
+    ctx->arena.reset();
+    const size_t eb = prec == FEAST_PREC_F64 ? sizeof(c128) : sizeof(c64);
+    const int pmax = std::max(1, ctx->num_sms * 8);
+    PanelWork pw = panel_work_carve(ctx->arena.alloc(panel_work_bytes(nz, pmax, eb)), nz, pmax, eb);
+    c128* dz = dalloc<c128>(ctx, nz);
+    to_dev(ctx, dz, (const c128*)z, nz);
+    int32_t* ipiv = dalloc<int32_t>(ctx, (int64_t)nz * n);
+    auto go = [&](auto ftag) {
+      using F = decltype(ftag);
+      if (dtype == FEAST_R64) form_shifted<F, double>((F*)LU, n, n, n * n, nz, (const double*)A, lda, dz, ctx->stream);
+      else form_shifted<F, c128>((F*)LU, n, n, n * n, nz, (const c128*)A, lda, dz, ctx->stream);
+      lu_factor_batched<F>((F*)LU, n, n, n * n, nz, ipiv, perm, pw, ctx->num_sms, ctx->stream);
+    };
+    if (prec == FEAST_PREC_F64) go(c128{});
+    else go(c64{});
+    int status = 0;
+    std::vector<int> zp(nz);
+    to_host(ctx, &status, pw.status, 1);
+    to_host(ctx, zp.data(), pw.zero_pivot, nz);
+    if (status == DEV_BARRIER_TIMEOUT) return FEAST_ERR_TIMEOUT;
+    for (int v : zp)
+      if (v) return FEAST_ERR_SINGULAR;
+    return FEAST_OK;
+  });
+}
+
+int feast_shifted_solve(feast_ctx* ctx, const void* LU, const int32_t* perm, int64_t n, int nz, int prec, int adjoint,
+                        const void* B, int64_t m, void* Y) {
+  if (!ctx || !LU || !perm || !B || !Y || n < 1 || nz < 1 || m < 1) return FEAST_ERR_ARG;
+  if (prec != FEAST_PREC_F64 && prec != FEAST_PREC_MIXED) return FEAST_ERR_ARG;
+  return guarded(ctx, [&]() {
+    FEAST_CUDA_TRY(cudaSetDevice(ctx->device));
+    ctx->arena.reset();
+    const int64_t nm = n * m;
+    auto go = [&](auto ftag) {
+      using F = decltype(ftag);
+      F* W = dalloc<F>(ctx, nz * nm);
+      permute_in<F, c128>(W, nm, (const c128*)B, n, 0, n, m, perm, nz, adjoint != 0, ctx->stream);
+      lu_solve_batched<F>((const F*)LU, n, n, n * n, nz, W, m, nm, adjoint != 0, ctx->stream);
+      permute_out<F, c128>((c128*)Y, nm, W, nm, n, m, perm, nz, adjoint != 0, false, ctx->stream);
+    };
+    if (prec == FEAST_PREC_F64) go(c128{});
+    else go(c64{});
+    sync(ctx);
+    return FEAST_OK;
+  });
+}
+
+int feast_orthonormalize(feast_ctx* ctx, int dtype, int64_t n, int64_t k, void* X, int method, int* rank) {
+  if (!ctx || !X || !rank || n < 1 || k < 1 || k > n || (dtype != FEAST_R64 && dtype != FEAST_C128)) return FEAST_ERR_ARG;
+  if (method < 0 || method > 1) return FEAST_ERR_ARG;
+  return guarded(ctx, [&]() {
+    FEAST_CUDA_TRY(cudaSetDevice(ctx->device));
+    ctx->arena.reset();
+    auto run = [&](auto tag) {
+      using S = decltype(tag);
+      feast_opts o;
+      feast_opts_default(&o);
+      Solver<S> sv(ctx, nullptr, n, n, -1.0, 1.0, 1, o);
+      sv.kmax = k;
+      sv.cw = coop_work_carve(ctx->arena.alloc(coop_work_bytes(k, ctx->num_sms)), k, ctx->num_sms);
+      const int64_t kk = k * k;
+      sv.Gs = dalloc<S>(ctx, kk); sv.Ri = dalloc<S>(ctx, kk); sv.Vk = dalloc<S>(ctx, kk); sv.Cs = dalloc<S>(ctx, kk);
+      sv.part_elems = 32 * kk;
+      sv.part = dalloc<S>(ctx, sv.part_elems);
+      sv.d_lam = dalloc<double>(ctx, k); sv.d_scale = dalloc<double>(ctx, k); sv.d_idx = dalloc<int>(ctx, k);
+      S* Q = dalloc<S>(ctx, n * k);
+      S* T = dalloc<S>(ctx, n * k);
+      int64_t r = method == 0 ? sv.orthonormalize((S*)X, n, k, Q, T) : sv.gram_eig_orth((S*)X, n, k, Q, T, 1e-12);
+      if (r == 0) return FEAST_ERR_ORTH;
+      copy_matrix<S>((S*)X, n, Q, n, n, r, ctx->stream);
+      sync(ctx);
+      *rank = (int)r;
+      return FEAST_OK;
+    };
+    if (dtype == FEAST_R64) return run(double{});
+    return run(c128{});
+  });
+}
+
+int feast_jacobi_eigh(feast_ctx* ctx, int dtype, int64_t k, const void* H, double* evals, void* V, int* sweeps) {
+  if (!ctx || !H || !evals || !V || k < 1 || (dtype != FEAST_R64 && dtype != FEAST_C128)) return FEAST_ERR_ARG;
+  return guarded(ctx, [&]() {
+    FEAST_CUDA_TRY(cudaSetDevice(ctx->device));
+    ctx->arena.reset();
+    auto run = [&](auto tag) {
+      using S = decltype(tag);
+      feast_opts o;
+      feast_opts_default(&o);
+      Solver<S> sv(ctx, nullptr, 1, 1, -1.0, 1.0, 1, o);
+      sv.kmax = k;
+      sv.cw = coop_work_carve(ctx->arena.alloc(coop_work_bytes(k, ctx->num_sms)), k, ctx->num_sms);
+      sv.Vk = dalloc<S>(ctx, k * k);
+      sv.Cs = dalloc<S>(ctx, k * k);
+      sv.d_lam = dalloc<double>(ctx, k);
+      sv.d_idx = dalloc<int>(ctx, k);
+      S* Hw = dalloc<S>(ctx, k * k);
+      copy_matrix<S>(Hw, k, (const S*)H, k, k, k, ctx->stream);
+      std::vector<double> ev;
+      sv.eig(Hw, k, ev);
+      std::vector<int> ord(k);
+      std::iota(ord.begin(), ord.end(), 0);
+      std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return ev[a] < ev[b]; });
+      to_dev(ctx, sv.d_idx, ord.data(), k);
+      gather_cols<S>((S*)V, k, sv.Vk, k, k, sv.d_idx, k, nullptr, ctx->stream);
+      sync(ctx);
+      for (int64_t i = 0; i < k; ++i) evals[i] = ev[ord[i]];
+      if (sweeps) *sweeps = sv.last_sweeps;
+      return FEAST_OK;
+    };
+    if (dtype == FEAST_R64) return run(double{});
+    return run(c128{});
+  });
+}
+
+int feast_rayleigh_ritz(feast_ctx* ctx, const void* A, int dtype, int64_t n, int64_t lda, const void* Q, int64_t k,
+                        double anorm, double* evals, void* X, double* res) {
+  if (int r = check_common(ctx, A, dtype, n, lda, -1.0, 1.0, 1)) return r;
+  if (!Q || !evals || !X || !res || k < 1 || k > n || !(anorm > 0)) return FEAST_ERR_ARG;
+  return guarded(ctx, [&]() {
+    FEAST_CUDA_TRY(cudaSetDevice(ctx->device));
+    ctx->arena.reset();
+    auto run = [&](auto tag) {
+      using S = decltype(tag);
+      feast_opts o;
+      feast_opts_default(&o);
+      Solver<S> sv(ctx, (const S*)A, n, lda, -1.0, 1.0, 1, o);
+      sv.kmax = k;
+      sv.cw = coop_work_carve(ctx->arena.alloc(coop_work_bytes(k, ctx->num_sms)), k, ctx->num_sms);
+      sv.alloc_rr();
+      sv.anorm = anorm;
+      copy_matrix<S>(sv.Qb, n, (const S*)Q, n, n, k, ctx->stream);
+      sv.rr_project(k);
+      sv.rr_solve(k);
+      copy_matrix<S>((S*)X, n, sv.Xr, n, n, k, ctx->stream);
+      sync(ctx);
+      for (int64_t i = 0; i < k; ++i) {
+        evals[i] = sv.lam[i];
+        res[i] = sv.res[i];
+      }
+      return FEAST_OK;
+    };
+    if (dtype == FEAST_R64) return run(double{});
+    return run(c128{});
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,163 @@
+// Batched SIMT GEMM (see gemm.cuh).  Register-tiled: each CTA computes a
+// BM x BN tile of C, each thread TM x TN outputs strided by BM/TM rows and
+// BN/TN columns so that both the shared-memory reads and the column-major
+// epilogue stores of a warp are contiguous.
+#include "gemm.cuh"
+
+namespace feast {
+
+namespace {
+
+template <typename T> __device__ __forceinline__ T maybe_conj(T v, int op) { return op == OP_C ? conj(v) : v; }
+
+template <typename TC> __device__ __forceinline__ TC axpby(c128 alpha, TC acc, c128 beta, const TC* cptr, bool use_beta);
+template <> __device__ __forceinline__ double axpby<double>(c128 alpha, double acc, c128 beta, const double* c, bool ub) {
+  double r = alpha.re * acc;
+  if (ub) r = fma(beta.re, *c, r);
+  return r;
+}
+template <> __device__ __forceinline__ c128 axpby<c128>(c128 alpha, c128 acc, c128 beta, const c128* c, bool ub) {
+  c128 r = alpha * acc;
+  if (ub) r = r + beta * (*c);
+  return r;
+}
+template <> __device__ __forceinline__ c64 axpby<c64>(c128 alpha, c64 acc, c128 beta, const c64* c, bool ub) {
+  c64 a{(float)alpha.re, (float)alpha.im};
+  c64 r = a * acc;
+  if (ub) { c64 b{(float)beta.re, (float)beta.im}; r = r + b * (*c); }
+  return r;
+}
+
+template <typename TA, typename TB, typename TC, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+gemm_kernel(GemmArgs g) {
+  constexpr int NT = (BM / TM) * (BN / TN);
+  constexpr int SM = BM / TM, SN = BN / TN;
+  __shared__ TA As[BK][BM + 1];
+  __shared__ TB Bs[BK][BN + 1];
+
+  const int bz = blockIdx.z;
+  const int b = bz % g.batch;
+  const int kc = bz / g.batch;
+  const TA* A = (const TA*)g.A + (int64_t)b * g.strideA;
+  const TB* B = (const TB*)g.B + (int64_t)b * g.strideB;
+  const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+  const int64_t kper = cdiv(cdiv(g.K, BK), g.ksplit) * BK;
+  const int64_t kbeg = (int64_t)kc * kper;
+  const int64_t kend = min(g.K, kbeg + kper);
+
+  TC acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = num<TC>::zero();
+
+  const int t = threadIdx.x;
+  const int tm = t % SM, tn = t / SM;
+
+  for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
+    for (int l = t; l < BM * BK; l += NT) {
+      int mm, kk;
+      if (g.opA == OP_N) { mm = l % BM; kk = l / BM; } else { kk = l % BK; mm = l / BK; }
+      const int64_t gm = m0 + mm, gk = k0 + kk;
+      TA v = num<TA>::zero();
+      if (gm < g.M && gk < kend) v = maybe_conj(g.opA == OP_N ? A[gm + gk * g.lda] : A[gk + gm * g.lda], g.opA);
+      As[kk][mm] = v;
+    }
+    for (int l = t; l < BK * BN; l += NT) {
+      int kk, nn;
+      if (g.opB == OP_N) { kk = l % BK; nn = l / BK; } else { nn = l % BN; kk = l / BN; }
+      const int64_t gk = k0 + kk, gn = n0 + nn;
+      TB v = num<TB>::zero();
+      if (gn < g.N && gk < kend) v = maybe_conj(g.opB == OP_N ? B[gk + gn * g.ldb] : B[gn + gk * g.ldb], g.opB);
+      Bs[kk][nn] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      TA a[TM];
+      TB bb[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][tm + i * SM];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) bb[j] = Bs[kk][tn + j * SN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) mac(acc[i][j], a[i], bb[j]);
+    }
+    __syncthreads();
+  }
+
+  if (g.ksplit > 1) {
+    TC* P = (TC*)g.Cpart + ((int64_t)kc * g.batch + b) * g.ldc * g.N;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int64_t gn = n0 + tn + j * SN;
+#pragma unroll
+      for (int i = 0; i < TM; ++i) {
+        const int64_t gm = m0 + tm + i * SM;
+        if (gm < g.M && gn < g.N) P[gm + gn * g.ldc] = acc[i][j];
+      }
+    }
+    return;
+  }
+  TC* C = (TC*)g.C + (int64_t)b * g.strideC;
+  const bool ub = (g.beta.re != 0.0 || g.beta.im != 0.0);
+#pragma unroll
+  for (int j = 0; j < TN; ++j) {
+    const int64_t gn = n0 + tn + j * SN;
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+      const int64_t gm = m0 + tm + i * SM;
+      if (gm < g.M && gn < g.N) {
+        TC* c = C + gm + gn * g.ldc;
+        *c = axpby<TC>(g.alpha, acc[i][j], g.beta, c, ub);
+      }
+    }
+  }
+}
+
+template <typename TC>
+__global__ void gemm_reduce_splitk(GemmArgs g) {
+  const int64_t total = g.M * g.N;
+  const int b = blockIdx.y;
+  const bool ub = (g.beta.re != 0.0 || g.beta.im != 0.0);
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t m = idx % g.M, n = idx / g.M;
+    TC s = num<TC>::zero();
+    for (int kc = 0; kc < g.ksplit; ++kc) {
+      const TC* P = (const TC*)g.Cpart + ((int64_t)kc * g.batch + b) * g.ldc * g.N;
+      s = s + P[m + n * g.ldc];
+    }
+    TC* c = (TC*)g.C + (int64_t)b * g.strideC + m + n * g.ldc;
+    *c = axpby<TC>(g.alpha, s, g.beta, c, ub);
+  }
+}
+
+}  // namespace
+
+template <typename TA, typename TB, typename TC>
+void gemm(const GemmArgs& g0, cudaStream_t stream) {
+  if (g0.M <= 0 || g0.N <= 0 || g0.batch <= 0) return;
+  GemmArgs g = g0;
+  if (g.ksplit < 1) g.ksplit = 1;
+  constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4;
+  if (g.ksplit > 1 && g.Cpart == nullptr) g.ksplit = 1;
+  dim3 grid((unsigned)cdiv(g.M, BM), (unsigned)cdiv(g.N, BN), (unsigned)(g.batch * g.ksplit));
+  gemm_kernel<TA, TB, TC, BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, stream>>>(g);
+  FEAST_LAUNCH_CHECK();
+  if (g.ksplit > 1) {
+    int64_t total = g.M * g.N;
+    dim3 rg((unsigned)std::min<int64_t>(cdiv(total, 256), 4096), (unsigned)g.batch);
+    gemm_reduce_splitk<TC><<<rg, 256, 0, stream>>>(g);
+    FEAST_LAUNCH_CHECK();
+  }
+}
+
+template void gemm<c128, c128, c128>(const GemmArgs&, cudaStream_t);
+template void gemm<c64, c64, c64>(const GemmArgs&, cudaStream_t);
+template void gemm<double, double, double>(const GemmArgs&, cudaStream_t);
+template void gemm<double, c128, c128>(const GemmArgs&, cudaStream_t);
+
+}  // namespace feast

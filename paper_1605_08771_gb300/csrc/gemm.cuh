@@ -1,0 +1,51 @@
+// Batched dense GEMM on CUDA cores for the FP64 and complex-FP32 paths:
+//   C_b = alpha * op(A_b) * op(B_b) + beta * C_b,  op in {N, T, C (conjugate transpose)}
+// All matrices column-major.  Used for the LU trailing update, the blocked
+// triangular-solve updates, the FP64 refinement residual A*Y, and the
+// Rayleigh-Ritz / orthonormalisation products.
+#pragma once
+
+#include "common.cuh"
+
+namespace feast {
+
+enum Op : int { OP_N = 0, OP_T = 1, OP_C = 2 };
+
+struct GemmArgs {
+  int64_t M, N, K;
+  const void* A; int64_t lda, strideA; int opA;
+  const void* B; int64_t ldb, strideB; int opB;
+  void* C; int64_t ldc, strideC;
+  c128 alpha, beta;
+  int batch;
+  // split-K: when ksplit > 1, partial products go to Cpart (ksplit x batch
+  // column-major blocks of ldc x N) and gemm_reduce_splitk sums them.
+  int ksplit;
+  void* Cpart;
+};
+
+// Launch C = alpha op(A) op(B) + beta C on `stream`.  TA, TB are the stored
+// element types of A and B, TC the type of C (also the accumulation type).
+template <typename TA, typename TB, typename TC>
+void gemm(const GemmArgs& g, cudaStream_t stream);
+
+// Convenience wrapper for the common unbatched case.
+template <typename TA, typename TB, typename TC>
+inline void gemm_simple(int64_t M, int64_t N, int64_t K, c128 alpha,
+                        const TA* A, int64_t lda, int opA,
+                        const TB* B, int64_t ldb, int opB, c128 beta,
+                        TC* C, int64_t ldc, cudaStream_t stream,
+                        int ksplit = 1, void* Cpart = nullptr) {
+  GemmArgs g{};
+  g.M = M; g.N = N; g.K = K;
+  g.A = A; g.lda = lda; g.strideA = 0; g.opA = opA;
+  g.B = B; g.ldb = ldb; g.strideB = 0; g.opB = opB;
+  g.C = C; g.ldc = ldc; g.strideC = 0;
+  g.alpha = alpha; g.beta = beta; g.batch = 1;
+  g.ksplit = ksplit; g.Cpart = Cpart;
+  gemm<TA, TB, TC>(g, stream);
+}
+
+inline c128 C1(double re, double im = 0.0) { return c128{re, im}; }
+
+}  // namespace feast

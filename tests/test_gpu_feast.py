@@ -1,0 +1,118 @@
+"""End-to-end parity of feast_interval_solve (CUDA path, C ABI) with the FP64
+oracle and with the planted spectra: eigenvalue count exact, eigenvalues to
+1e-10 relative, residuals <= 1e-10 relative to ||A||_2, eigenvector spans;
+all three variants, both precisions; edge cases."""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1605_08771_gb300 as fg
+from gpu_common import cuda, ctx, host  # noqa: F401
+from workloads import (make_problem, random_subspace, spectrum_config1, spectrum_config2,
+                       spectrum_uniform)
+
+pytestmark = pytest.mark.gpu
+VARIANTS = [("feast", O.PLAIN), ("xfeast", O.XFEAST), ("rfeast", O.RFEAST)]
+
+
+def check_against_planted(out, P, tol=1e-10):
+    assert out["evals"].size == P.inside.size
+    np.testing.assert_allclose(out["evals"], P.inside, rtol=1e-10, atol=1e-12 * P.anorm)
+    assert np.max(out["res"]) <= tol
+    X = host(out["evecs"])
+    # recompute residuals independently in FP64 on the host
+    R = P.A @ X - X * out["evals"][None, :]
+    assert np.max(np.linalg.norm(R, axis=0)) / P.anorm <= 2 * tol
+    Qi = P.inside_vectors
+    assert np.linalg.norm(X - Qi @ (Qi.conj().T @ X), 2) <= 1e-8
+
+
+@pytest.mark.parametrize("vname,vor", VARIANTS)
+@pytest.mark.parametrize("cplx", [False, True])
+@pytest.mark.parametrize("prec", ["f64", "mixed"])
+def test_small_planted_vs_oracle(ctx, vname, vor, cplx, prec):
+    lam, a, b = spectrum_uniform(90, 8, seed=3, bulk=10.0)
+    P = make_problem("s", lam, a, b, 12, 8, seed=3, complex_=cplx)
+    X0 = random_subspace(P.n, P.m0, seed=5, complex_=cplx)
+    out = fg.feast_interval_solve(ctx, cuda(P.A), a, b, P.m0, 8, 1e-10,
+                                  fg.feast_opts_default(variant=vname, prec=prec, anorm=P.anorm),
+                                  x0=cuda(X0))
+    assert out["status"] == 0
+    check_against_planted(out, P)
+    ref = O.feast_solve(P.A, a, b, P.m0, 8, 1e-10, X0, variant=vor, anorm=P.anorm, max_iter=100)
+    assert ref.status == 0
+    np.testing.assert_allclose(out["evals"], ref.lam, atol=1e-12 * P.anorm)
+    assert abs(out["iterations"] - ref.iterations) <= 1
+
+
+@pytest.mark.parametrize("vname,vor", VARIANTS)
+def test_n500_workload_vs_oracle(ctx, vname, vor):
+    # n = 500 real symmetric, 40 eigenvalues in [-1, 1] (5 within 1e-3 of each
+    # edge), n_c = 8, m0 = 60, tol 1e-10, FP64
+    lam, a, b = spectrum_config1(0)
+    P = make_problem("c1", lam, a, b, 60, 8, seed=0)
+    X0 = random_subspace(P.n, 60, seed=1)
+    out = fg.feast_interval_solve(ctx, cuda(P.A), a, b, 60, 8, 1e-10,
+                                  fg.feast_opts_default(variant=vname, anorm=P.anorm), x0=cuda(X0))
+    assert out["status"] == 0
+    check_against_planted(out, P)
+    ref = O.feast_solve(P.A, a, b, 60, 8, 1e-10, X0, variant=vor, anorm=P.anorm)
+    np.testing.assert_allclose(out["evals"], ref.lam, atol=1e-12 * P.anorm)
+    assert abs(out["iterations"] - ref.iterations) <= 1
+
+
+@pytest.mark.parametrize("prec", ["f64", "mixed"])
+def test_edge_clustered_complex_rfeast(ctx, prec):
+    # scaled-down edge-cluster workload: clusters within 1e-4 inside and
+    # outside both edges, bulk in [-50, 50]; plain FEAST stalls here
+    lam, a, b = spectrum_config2(0, n=640, m_in=16, edge_in=3, edge_out=5, width=1e-4, bulk=50.0)
+    P = make_problem("c2s", lam, a, b, 24, 8, seed=0, complex_=True)
+    X0 = random_subspace(P.n, 24, seed=1, complex_=True)
+    out = fg.feast_interval_solve(ctx, cuda(P.A), a, b, 24, 8, 1e-10,
+                                  fg.feast_opts_default(variant="rfeast", prec=prec, anorm=P.anorm),
+                                  x0=cuda(X0))
+    assert out["status"] == 0
+    check_against_planted(out, P)
+
+
+def test_internal_random_start_and_norm_estimate(ctx):
+    lam, a, b = spectrum_uniform(200, 12, seed=8, bulk=15.0)
+    P = make_problem("r", lam, a, b, 18, 8, seed=8)
+    out = fg.feast_interval_solve(ctx, cuda(P.A), a, b, 18, 8, 1e-10, fg.feast_opts_default(seed=42))
+    assert out["status"] == 0
+    assert out["evals"].size == 12
+    np.testing.assert_allclose(out["evals"], P.inside, rtol=1e-10, atol=1e-12 * P.anorm)
+
+
+def test_empty_interval(ctx):
+    lam = np.concatenate([np.linspace(-10, -2, 30), np.linspace(2, 10, 30)])
+    P = make_problem("gap", lam, -1.0, 1.0, 8, 8, seed=4)
+    out = fg.feast_interval_solve(ctx, cuda(P.A), -1.0, 1.0, 8, 8, 1e-10, fg.feast_opts_default(anorm=10.0),
+                                  x0=cuda(random_subspace(60, 8, seed=1)))
+    assert out["status"] == 0 and out["evals"].size == 0
+
+
+def test_tiny_n(ctx):
+    A = np.asfortranarray(np.array([[0.25]]))
+    out = fg.feast_interval_solve(ctx, cuda(A), -1.0, 1.0, 1, 4, 1e-12, fg.feast_opts_default(anorm=0.25),
+                                  x0=cuda(np.ones((1, 1))))
+    assert out["evals"].size == 1 and abs(out["evals"][0] - 0.25) < 1e-15
+    A2 = np.asfortranarray(np.diag([0.5, 3.0]))
+    out = fg.feast_interval_solve(ctx, cuda(A2), -1.0, 1.0, 2, 8, 1e-12, fg.feast_opts_default(anorm=3.0),
+                                  x0=cuda(np.asfortranarray([[1.0, 0.3], [0.2, 1.0]])))
+    assert out["evals"].size == 1 and abs(out["evals"][0] - 0.5) < 1e-14
+
+
+def test_errors(ctx):
+    A = np.asfortranarray(np.eye(10))
+    with pytest.raises(fg.FeastError) as e:
+        fg.feast_interval_solve(ctx, cuda(A), -1.0, 1.0, 11, 8, 1e-10)   # m0 > n
+    assert e.value.code == -1
+    with pytest.raises(fg.FeastError) as e:
+        fg.feast_interval_solve(ctx, cuda(A), 1.0, -1.0, 4, 8, 1e-10)    # empty interval
+    assert e.value.code == -1
+    B = A.copy()
+    B[3, 4] = np.nan
+    with pytest.raises(fg.FeastError) as e:
+        fg.feast_interval_solve(ctx, cuda(B), -1.0, 1.0, 4, 8, 1e-10)
+    assert e.value.code == -2

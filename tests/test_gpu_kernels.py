@@ -1,0 +1,125 @@
+"""Kernel-level parity of the CUDA path with the FP64 oracle: shifted LU
+(pivots bit-exact in FP64), triangular solves and their adjoints, the filter
+of Eq. 3, Jacobi, orthonormalisation and Rayleigh-Ritz.  Sizes span several
+32-wide panels and a ragged tail."""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1605_08771_gb300 as fg
+from gpu_common import cuda, ctx, host, rand_hermitian, rand_mat  # noqa: F401
+from workloads import make_problem, random_subspace, spectrum_uniform
+
+pytestmark = pytest.mark.gpu
+ZS = np.array([0.3 + 0.5j, -0.7 + 0.2j, 1.1 + 0.05j])
+SIZES = [1, 2, 31, 32, 33, 65, 100, 257]
+
+
+@pytest.mark.parametrize("n", SIZES)
+@pytest.mark.parametrize("cplx", [False, True])
+@pytest.mark.parametrize("prec", [fg.FEAST_PREC_F64, fg.FEAST_PREC_MIXED])
+def test_shifted_lu_matches_oracle(ctx, n, cplx, prec):
+    A = rand_hermitian(n, cplx, seed=n)
+    LU, perm = fg.feast_shifted_lu(ctx, cuda(A), ZS, prec)
+    LU, perm = host(LU).astype(np.complex128), host(perm)
+    u = 1.2e-16 if prec == fg.FEAST_PREC_F64 else 6e-8
+    for e, z in enumerate(ZS):
+        M = z * np.eye(n) - A
+        L = np.tril(LU[e], -1) + np.eye(n)
+        U = np.triu(LU[e])
+        err = np.linalg.norm(M[perm[e], :] - L @ U) / np.linalg.norm(M)
+        assert err <= 8 * n * u, err
+        assert np.all(np.abs(np.tril(LU[e], -1)) <= 1 + 1e-6)
+        if prec == fg.FEAST_PREC_F64:
+            LUo, pivo = O.lu_factor(M)
+            permo = np.arange(n)
+            O.dense.apply_row_swaps(permo, pivo)
+            assert np.array_equal(perm[e], permo)          # pivots bit-exact
+            assert np.abs(LU[e] - LUo).max() <= 1e-12 * max(1.0, np.abs(LUo).max())
+
+
+@pytest.mark.parametrize("n", [1, 33, 100, 257])
+@pytest.mark.parametrize("cplx", [False, True])
+@pytest.mark.parametrize("adjoint", [False, True])
+@pytest.mark.parametrize("prec", [fg.FEAST_PREC_F64, fg.FEAST_PREC_MIXED])
+def test_shifted_solve_matches_oracle(ctx, n, cplx, adjoint, prec):
+    A = rand_hermitian(n, cplx, seed=7 * n + 1)
+    B = rand_mat(n, 5, True, seed=n)
+    LU, perm = fg.feast_shifted_lu(ctx, cuda(A), ZS, prec)
+    Y = host(fg.feast_shifted_solve(ctx, LU, perm, cuda(B), adjoint=adjoint, prec=prec))
+    tol = 1e-11 if prec == fg.FEAST_PREC_F64 else 2e-4
+    for e, z in enumerate(ZS):
+        LUo, pivo = O.lu_factor(z * np.eye(n) - A)
+        ref = (O.lu_solve_adjoint if adjoint else O.lu_solve)(LUo, pivo, B)
+        assert np.abs(Y[e] - ref).max() <= tol * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+@pytest.mark.parametrize("prec", [fg.FEAST_PREC_F64, fg.FEAST_PREC_MIXED])
+@pytest.mark.parametrize("n_c", [3, 8])
+def test_filter_matches_oracle_and_closed_form(ctx, cplx, prec, n_c):
+    lam, a, b = spectrum_uniform(150, 10, seed=11, bulk=20.0)
+    P = make_problem("f", lam, a, b, 12, n_c, seed=11, complex_=cplx)
+    X = random_subspace(P.n, 7, seed=2, complex_=cplx)
+    Y = host(fg.feast_filter_apply(ctx, cuda(P.A), a, b, n_c, cuda(X),
+                                   fg.feast_opts_default(prec=prec, anorm=P.anorm)))
+    F = O.factor_shifts(P.A, a, b, n_c)
+    ref = O.filter_apply(F, X)
+    rho = O.rational_filter(P.lam, F.z, F.w)
+    closed = P.Q @ (rho[:, None] * (P.Q.conj().T @ X))
+    assert np.abs(Y - ref).max() <= 1e-12 * np.abs(X).max()
+    assert np.abs(Y - (closed if cplx else closed.real)).max() <= 1e-12 * np.abs(X).max()
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 7, 33, 64, 130])
+@pytest.mark.parametrize("cplx", [False, True])
+def test_jacobi_matches_lapack(ctx, k, cplx):
+    H = rand_hermitian(k, cplx, seed=100 + k)
+    ev, V, sweeps = fg.feast_jacobi_eigh(ctx, cuda(H))
+    V = host(V)
+    scale = max(1.0, np.linalg.norm(H))
+    np.testing.assert_allclose(ev, np.linalg.eigvalsh(H), atol=1e-13 * scale)
+    evo, Vo, _ = O.jacobi_eigh(H)
+    np.testing.assert_allclose(ev, evo, atol=1e-13 * scale)
+    assert np.linalg.norm(V.conj().T @ V - np.eye(k)) <= 1e-13 * k
+    assert np.linalg.norm(H @ V - V * ev) <= 1e-13 * scale * k
+    assert sweeps < 30
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+@pytest.mark.parametrize("method", [0, 1])
+def test_orthonormalize(ctx, cplx, method):
+    n, k = 300, 40
+    X = rand_mat(n, k, cplx, seed=5) @ np.diag(np.logspace(0, -5, k))
+    Q, r = fg.feast_orthonormalize(ctx, cuda(X), method)
+    Q = host(Q)
+    assert r == k
+    assert np.linalg.norm(Q.conj().T @ Q - np.eye(k)) <= 1e-13
+    assert np.linalg.norm(Q @ (Q.conj().T @ X) - X) <= 1e-12 * np.linalg.norm(X)
+    Qo, _ = O.cholqr2(X) if method == 0 else (O.gram_eig_orth(X), None)
+    # same span
+    assert np.linalg.norm(Q @ (Q.conj().T @ Qo) - Qo) <= 1e-11
+
+
+def test_orthonormalize_rank_deficient_falls_back(ctx):
+    X = rand_mat(200, 10, True, seed=9)
+    Xd = np.asfortranarray(np.hstack([X, X[:, :4] * 2.0]))
+    Q, r = fg.feast_orthonormalize(ctx, cuda(Xd), 0)
+    assert r == 10
+    Q = host(Q)
+    assert np.linalg.norm(Q.conj().T @ Q - np.eye(10)) <= 1e-13
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_rayleigh_ritz_matches_oracle(ctx, cplx):
+    lam, a, b = spectrum_uniform(120, 9, seed=4, bulk=8.0)
+    P = make_problem("rr", lam, a, b, 12, 8, seed=4, complex_=cplx)
+    Q0, _ = np.linalg.qr(random_subspace(P.n, 14, seed=1, complex_=cplx))
+    Q0 = np.asfortranarray(Q0)
+    ev, X, res = fg.feast_rayleigh_ritz(ctx, cuda(P.A), cuda(Q0), P.anorm)
+    X = host(X)
+    rp = O.rayleigh_ritz(P.A, Q0, P.anorm)
+    np.testing.assert_allclose(ev, rp.lam, atol=1e-13 * P.anorm)
+    np.testing.assert_allclose(res, rp.res, atol=1e-13)
+    overlap = np.abs(np.sum(X.conj() * rp.X, axis=0))
+    np.testing.assert_allclose(overlap, 1.0, atol=1e-9)
