@@ -76,6 +76,9 @@ typedef struct {
                            0 = 2 eps sqrt(n) */
   unsigned long long seed; /* seed of the N(0,1) starting subspace when x0 == NULL */
   const void* x0;       /* optional device n x m0 starting subspace (leading dim n, dtype) */
+  double refine_switch; /* mixed: while the previous iteration's max residual exceeds this and
+                           fell at least tenfold, the next filter uses the FP32 solves without
+                           FP64 refinement (default 1e-4; 0 = always refine) */
 } feast_opts;
 
 /* Per-call statistics of the last feast_interval_solve on a context. */

@@ -196,6 +196,12 @@ struct Solver {
   c64* Yc = nullptr;
   double* d_en = nullptr;
   int refine_steps = 0;
+  bool refine_now = true;      // mixed: refine the next filter application
+  // mixed: double-float planes of A (hi/lo of Re, then of Im) and of the
+  // right-hand block of an A product
+  float* Apl = nullptr;
+  float* Bpl = nullptr;
+  int64_t bpl_cols = 0;
   // Rayleigh-Ritz scratch
   S *Qb = nullptr, *Wb = nullptr, *Xr = nullptr, *AXr = nullptr, *T1 = nullptr, *T2 = nullptr;
   S *Ar0 = nullptr, *Ar = nullptr, *Vk = nullptr, *Gs = nullptr, *Ri = nullptr, *Cs = nullptr, *Cs2 = nullptr;
@@ -248,6 +254,16 @@ struct Solver {
       Yw = dalloc<c128>(ctx, E * nm);
       AY = dalloc<c128>(ctx, E * nm);
       Yc = dalloc<c64>(ctx, E * nm);
+      const int apl = kCplx ? 4 : 2;
+      Apl = dalloc<float>(ctx, (int64_t)apl * n * n);
+      if (kCplx) {
+        split_df32((const double*)A, n, n, lda, 2, 0, Apl, Apl + n * n, st);
+        split_df32((const double*)A, n, n, lda, 2, 1, Apl + 2 * n * n, Apl + 3 * n * n, st);
+      } else {
+        split_df32((const double*)A, n, n, lda, 1, 0, Apl, Apl + n * n, st);
+      }
+      bpl_cols = std::max<int64_t>(E * m, kmax);
+      Bpl = dalloc<float>(ctx, 4 * n * bpl_cols);
     }
   }
   void alloc_rr() {
@@ -281,8 +297,35 @@ struct Solver {
     gemm_simple<S, S, S>(Mr, Nc, K, C1(1.0), Am, la, opA, Bm, lb, opB, C1(0.0), Cm, lc, st, ks,
                          ks > 1 ? (void*)part : nullptr);
   }
-  // A times a block (FP64)
-  void apply_A(const S* Xm, int64_t k, S* Out) { mm(n, k, n, C1(1.0), A, lda, OP_N, Xm, n, OP_N, C1(0.0), Out, n); }
+  // Out = A * B for an n x k block B (ld n) in double-float arithmetic on the
+  // FP32 pipes: B complex (bcplx) or real; Out has B's element type.
+  void apply_A_df(const double* B, bool bcplx, int64_t k, double* Out) {
+    const int64_t nk = n * k;
+    float *Brh = Bpl, *Brl = Bpl + nk, *Bih = Bpl + 2 * nk, *Bil = Bpl + 3 * nk;
+    const float *Arh = Apl, *Arl = Apl + n * n, *Aih = Apl + 2 * n * n, *Ail = Apl + 3 * n * n;
+    const int cs = bcplx ? 2 : 1;
+    split_df32(B, n, k, n, cs, 0, Brh, Brl, st);
+    if (bcplx) split_df32(B, n, k, n, 2, 1, Bih, Bil, st);
+    if (kCplx) {  // complex A, complex B
+      gemm_df32(n, k, n, 1.0, Arh, Arl, n, Brh, Brl, n, 0.0, Out, n, 2, 0, st);
+      gemm_df32(n, k, n, -1.0, Aih, Ail, n, Bih, Bil, n, 1.0, Out, n, 2, 0, st);
+      gemm_df32(n, k, n, 1.0, Arh, Arl, n, Bih, Bil, n, 0.0, Out, n, 2, 1, st);
+      gemm_df32(n, k, n, 1.0, Aih, Ail, n, Brh, Brl, n, 1.0, Out, n, 2, 1, st);
+    } else if (bcplx) {  // real A, complex B
+      gemm_df32(n, k, n, 1.0, Arh, Arl, n, Brh, Brl, n, 0.0, Out, n, 2, 0, st);
+      gemm_df32(n, k, n, 1.0, Arh, Arl, n, Bih, Bil, n, 0.0, Out, n, 2, 1, st);
+    } else {  // real A, real B
+      gemm_df32(n, k, n, 1.0, Arh, Arl, n, Brh, Brl, n, 0.0, Out, n, 1, 0, st);
+    }
+  }
+  // A times a block: FP64 on the FP64 path, double-float on the mixed path
+  void apply_A(const S* Xm, int64_t k, S* Out) {
+    if (o.prec == FEAST_PREC_MIXED && Apl && k <= bpl_cols) {
+      apply_A_df((const double*)Xm, kCplx, k, (double*)Out);
+      return;
+    }
+    mm(n, k, n, C1(1.0), A, lda, OP_N, Xm, n, OP_N, C1(0.0), Out, n);
+  }
 
   // ---- norm estimate: power iteration from ones/sqrt(n) ----
   double estimate_norm() {
@@ -343,7 +386,14 @@ struct Solver {
     }
   }
 
+  double filter_ms = 0.0;
   void filter(const S* X, int64_t m, S* Xf) {
+    const double t0 = now_ms();
+    filter_body(X, m, Xf);
+    sync(ctx);
+    filter_ms += now_ms() - t0;
+  }
+  void filter_body(const S* X, int64_t m, S* Xf) {
     const int64_t nm = n * m;
     if (o.prec == FEAST_PREC_F64) {
       const c128* Mf = (const c128*)M;
@@ -356,15 +406,27 @@ struct Solver {
       }
     } else {
       solve_lowp<S>(X, n, 0, m, false);
+      if (!refine_now) {
+        accumulate_filter<S>(Xf, n, Y, n, m, nc, d_w, st);
+        return;
+      }
       const double rtol = o.refine_tol > 0 ? o.refine_tol : 2.0 * 2.220446049250313e-16 * std::sqrt((double)n);
       std::vector<double> en(2 * E), prev(E, -1.0);
       for (int step = 0; step < o.refine_max; ++step) {
-        // R_e = X - (z_e I - A) Y_e in FP64
-        gemm_simple<S, c128, c128>(n, E * m, n, C1(1.0), A, lda, OP_N, Y, n, OP_N, C1(0.0), AY, n, st);
+        // R_e = X - (z_e I - A) Y_e, FP64-accurate (double-float A Y)
+        apply_A_df((const double*)Y, true, E * m, (double*)AY);
         refine_residual<S>(Yw, X, n, Y, AY, n, m, E, d_ze, st);
         entry_norms2(Yw, Y, n, m, E, d_en, st);
         to_host(ctx, en.data(), d_en, 2 * E);
         bool conv = true, stagnant = step > 0;
+        if (std::getenv("FEAST_LOG")) {
+          double worst = 0.0;
+          for (int e = 0; e < E; ++e) {
+            const c128 ze = e < nc ? z[e] : conj(z[e - nc]);
+            worst = std::max(worst, std::sqrt(en[2 * e]) / ((anorm + std::sqrt(abs2(ze))) * std::sqrt(en[2 * e + 1])));
+          }
+          fprintf(stderr, "[feast] refine step %d: max relative residual %.3e (target %.3e)\n", step, worst, rtol);
+        }
         for (int e = 0; e < E; ++e) {
           const c128 ze = e < nc ? z[e] : conj(z[e - nc]);
           const double rn = std::sqrt(en[2 * e]), yn = std::sqrt(en[2 * e + 1]);
@@ -479,6 +541,16 @@ struct Solver {
     std::vector<double> hist;
   };
 
+  // mixed: skip the FP64-accurate refinement of the next filter while the
+  // residual is above o.refine_switch and still falling at least tenfold per
+  // iteration (a filter accurate to FP32 cannot be what limits it then)
+  void update_refine(const std::vector<double>& hist) {
+    if (o.prec != FEAST_PREC_MIXED || o.refine_switch <= 0.0) { refine_now = true; return; }
+    const double r = hist.back();
+    const double prev = hist.size() >= 2 ? hist[hist.size() - 2] : INFINITY;
+    refine_now = !(r > o.refine_switch && r < 0.1 * prev);
+  }
+
   std::vector<int> in_sorted(const std::vector<int>& cand) {
     std::vector<int> v;
     for (int i : cand)
@@ -518,6 +590,7 @@ struct Solver {
       std::vector<int> ins = in_sorted(all);
       const double r = max_res(ins);
       out.hist.push_back(r);
+      update_refine(out.hist);
       out.iterations = it;
       if ((!ins.empty() && r <= tol) || (ins.empty() && it >= 2)) {
         finish(out, ins);
@@ -633,6 +706,7 @@ struct Solver {
       ins = lowest_residual(in_sorted(sel), mexp);
       const double r = max_res(ins);
       out.hist.push_back(r);
+      update_refine(out.hist);
       out.iterations = it;
       if ((!ins.empty() && r <= tol) || (ins.empty() && it >= 2)) {
         finish(out, ins);
@@ -717,6 +791,7 @@ struct Solver {
       ins = lowest_residual(in_sorted(sel), mexp);
       const double r = max_res(ins);
       out.hist.push_back(r);
+      update_refine(out.hist);
       out.iterations = it;
       if ((!ins.empty() && r <= tol) || (ins.empty() && it >= 2)) {
         finish(out, ins);
@@ -782,6 +857,7 @@ int solve_t(feast_ctx* ctx, const S* A, int64_t n, int64_t lda, double lmin, dou
   sv.alloc_factors();
   sv.anorm = o.anorm > 0 ? o.anorm : sv.estimate_norm();
   if (!(sv.anorm > 0)) sv.anorm = 1.0;
+  sv.refine_now = !(o.prec == FEAST_PREC_MIXED && o.refine_switch > 0.0);
   S* X = dalloc<S>(ctx, n * m0);
   if (o.x0) {
     copy_matrix<S>(X, n, (const S*)o.x0, n, n, m0, ctx->stream);
@@ -821,6 +897,7 @@ int solve_t(feast_ctx* ctx, const S* A, int64_t n, int64_t lda, double lmin, dou
   st.refine_steps = sv.refine_steps;
   st.m_expected = out.m_expected;
   st.factor_ms = tf1 - tf0;
+  st.filter_ms = sv.filter_ms;
   st.total_ms = now_ms() - t0;
   st.max_residual = 0.0;
   for (double r : rs) st.max_residual = std::max(st.max_residual, r);
@@ -850,6 +927,7 @@ void feast_opts_default(feast_opts* o) {
   o->refine_tol = 0.0;
   o->seed = 0x1605087710ull;
   o->x0 = nullptr;
+  o->refine_switch = 1e-4;
 }
 
 int feast_init(feast_ctx** ctx, int device, void* stream) {
@@ -920,7 +998,7 @@ int feast_interval_solve(feast_ctx* ctx, const void* A, int dtype, int64_t n, in
   if (opts) o = *opts; else feast_opts_default(&o);
   if (o.variant < 0 || o.variant > 2 || o.prec < 0 || o.prec > 1 || o.max_iter < 1 || !(o.aspect > 0)) return FEAST_ERR_ARG;
   if (o.variant != FEAST_PLAIN && (o.s < 1 || (int64_t)o.s * m0 > 65536)) return FEAST_ERR_ARG;
-  if (o.refine_max < 0) return FEAST_ERR_ARG;
+  if (o.refine_max < 0 || !(o.refine_switch >= 0.0)) return FEAST_ERR_ARG;
   *m_found = 0;
   *iterations = 0;
   return guarded(ctx, [&]() {

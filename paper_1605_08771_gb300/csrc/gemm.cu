@@ -161,3 +161,139 @@ template void gemm<double, double, double>(const GemmArgs&, cudaStream_t);
 template void gemm<double, c128, c128>(const GemmArgs&, cudaStream_t);
 
 }  // namespace feast
+
+// ---------------------------------------------------------------------------
+// double-float GEMM
+// ---------------------------------------------------------------------------
+namespace feast {
+namespace {
+
+constexpr int DF_BM = 64, DF_BN = 64, DF_BK = 16, DF_TM = 4, DF_TN = 4;
+constexpr int DF_THREADS = (DF_BM / DF_TM) * (DF_BN / DF_TN);
+
+__device__ __forceinline__ void df_mac(float a, float al, float b, float bl, float& s, float& x) {
+  // explicit _rn intrinsics: the compiler must not contract these into FMAs
+  const float p = __fmul_rn(a, b);
+  const float e = fmaf(a, b, -p);                       // a*b = p + e exactly
+  const float t = __fadd_rn(s, p);                      // s + p = t + err exactly (TwoSum)
+  const float bp = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+  s = t;
+  x = fmaf(a, bl, x);
+  x = fmaf(al, b, x);
+  x = __fadd_rn(x, __fadd_rn(e, err));
+}
+
+__global__ void __launch_bounds__(DF_THREADS)
+gemm_df32_kernel(int64_t M, int64_t N, int64_t K, double alpha, const float* __restrict__ Ahi,
+                 const float* __restrict__ Alo, int64_t lda, const float* __restrict__ Bhi,
+                 const float* __restrict__ Blo, int64_t ldb, double beta, double* C, int64_t ldc, int cs, int co) {
+  __shared__ __align__(16) float sAh[DF_BK][DF_BM];
+  __shared__ __align__(16) float sAl[DF_BK][DF_BM];
+  __shared__ __align__(16) float sBh[DF_BK][DF_BN + 1];
+  __shared__ __align__(16) float sBl[DF_BK][DF_BN + 1];
+  const int t = threadIdx.x;
+  const int tm = t % (DF_BM / DF_TM), tn = t / (DF_BM / DF_TM);
+  const int64_t m0 = (int64_t)blockIdx.x * DF_BM, n0 = (int64_t)blockIdx.y * DF_BN;
+  float s[DF_TM][DF_TN], x[DF_TM][DF_TN];
+  double d[DF_TM][DF_TN];
+#pragma unroll
+  for (int i = 0; i < DF_TM; ++i)
+#pragma unroll
+    for (int j = 0; j < DF_TN; ++j) { s[i][j] = 0.f; x[i][j] = 0.f; d[i][j] = 0.0; }
+
+  int tile = 0;
+  for (int64_t k0 = 0; k0 < K; k0 += DF_BK, ++tile) {
+    // A tile: BM x BK, consecutive threads along m (coalesced)
+    for (int l = t; l < DF_BM * DF_BK; l += DF_THREADS) {
+      const int mm = l % DF_BM, kk = l / DF_BM;
+      const int64_t gm = m0 + mm, gk = k0 + kk;
+      float h = 0.f, lo = 0.f;
+      if (gm < M && gk < K) { h = Ahi[gm + gk * lda]; lo = Alo[gm + gk * lda]; }
+      sAh[kk][mm] = h;
+      sAl[kk][mm] = lo;
+    }
+    // B tile: BK x BN, consecutive threads along k (coalesced)
+    for (int l = t; l < DF_BK * DF_BN; l += DF_THREADS) {
+      const int kk = l % DF_BK, nn = l / DF_BK;
+      const int64_t gk = k0 + kk, gn = n0 + nn;
+      float h = 0.f, lo = 0.f;
+      if (gn < N && gk < K) { h = Bhi[gk + gn * ldb]; lo = Blo[gk + gn * ldb]; }
+      sBh[kk][nn] = h;
+      sBl[kk][nn] = lo;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < DF_BK; ++kk) {
+      const float4 ah = *reinterpret_cast<const float4*>(&sAh[kk][tm * DF_TM]);
+      const float4 al = *reinterpret_cast<const float4*>(&sAl[kk][tm * DF_TM]);
+      const float a_h[4] = {ah.x, ah.y, ah.z, ah.w};
+      const float a_l[4] = {al.x, al.y, al.z, al.w};
+      float b_h[DF_TN], b_l[DF_TN];
+#pragma unroll
+      for (int j = 0; j < DF_TN; ++j) {
+        b_h[j] = sBh[kk][tn + j * (DF_BN / DF_TN)];
+        b_l[j] = sBl[kk][tn + j * (DF_BN / DF_TN)];
+      }
+#pragma unroll
+      for (int i = 0; i < DF_TM; ++i)
+#pragma unroll
+        for (int j = 0; j < DF_TN; ++j) df_mac(a_h[i], a_l[i], b_h[j], b_l[j], s[i][j], x[i][j]);
+    }
+    __syncthreads();
+    if (tile & 1) {
+#pragma unroll
+      for (int i = 0; i < DF_TM; ++i)
+#pragma unroll
+        for (int j = 0; j < DF_TN; ++j) { d[i][j] += (double)x[i][j]; x[i][j] = 0.f; }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < DF_TN; ++j) {
+    const int64_t gn = n0 + tn + j * (DF_BN / DF_TN);
+#pragma unroll
+    for (int i = 0; i < DF_TM; ++i) {
+      const int64_t gm = m0 + tm * DF_TM + i;
+      if (gm < M && gn < N) {
+        const double r = (double)s[i][j] + (d[i][j] + (double)x[i][j]);
+        double* c = C + (gm + gn * ldc) * cs + co;
+        *c = (beta != 0.0) ? fma(alpha, r, beta * (*c)) : alpha * r;
+      }
+    }
+  }
+}
+
+__global__ void split_df32_kernel(const double* src, int64_t rows, int64_t cols, int64_t lds, int ss, int so,
+                                  float* hi, float* lo) {
+  const int64_t total = rows * cols;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx % rows, j = idx / rows;
+    const double v = src[(i + j * lds) * ss + so];
+    const float h = (float)v;
+    hi[idx] = h;
+    lo[idx] = (float)(v - (double)h);
+  }
+}
+
+}  // namespace
+
+void gemm_df32(int64_t M, int64_t N, int64_t K, double alpha, const float* Ahi, const float* Alo, int64_t lda,
+               const float* Bhi, const float* Blo, int64_t ldb, double beta, double* C, int64_t ldc, int cs, int co,
+               cudaStream_t s) {
+  if (M <= 0 || N <= 0) return;
+  dim3 grid((unsigned)cdiv(M, DF_BM), (unsigned)cdiv(N, DF_BN));
+  gemm_df32_kernel<<<grid, DF_THREADS, 0, s>>>(M, N, K, alpha, Ahi, Alo, lda, Bhi, Blo, ldb, beta, C, ldc, cs, co);
+  FEAST_LAUNCH_CHECK();
+}
+
+void split_df32(const double* src, int64_t rows, int64_t cols, int64_t lds, int ss, int so, float* hi, float* lo,
+                cudaStream_t s) {
+  const int64_t total = rows * cols;
+  if (total <= 0) return;
+  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(total, 256), 16384));
+  split_df32_kernel<<<g, 256, 0, s>>>(src, rows, cols, lds, ss, so, hi, lo);
+  FEAST_LAUNCH_CHECK();
+}
+
+}  // namespace feast

@@ -49,3 +49,25 @@ inline void gemm_simple(int64_t M, int64_t N, int64_t K, c128 alpha,
 inline c128 C1(double re, double im = 0.0) { return c128{re, im}; }
 
 }  // namespace feast
+
+namespace feast {
+
+// FP64-accurate real GEMM on the FP32 pipes ("double-float"):
+//   C[(i + j*ldc)*cs + co] = alpha * sum_k A[i,k] B[k,j] + beta * C[...]
+// with A and B given as hi/lo float planes (x = hi + lo, |lo| <= 2^-24 |hi|),
+// column-major, op N.  Each hi*hi product is made exact with an FMA
+// (TwoProd), each addition to the running FP32 sum exact with TwoSum; the
+// error terms and the hi*lo cross products go to an FP32 accumulator that is
+// flushed into an FP64 accumulator every 32 k-steps.  Relative accuracy is
+// ~1e-15 of sum |a||b| at a small fraction of the FP64 cost on sm_103.
+void gemm_df32(int64_t M, int64_t N, int64_t K, double alpha,
+               const float* Ahi, const float* Alo, int64_t lda,
+               const float* Bhi, const float* Blo, int64_t ldb,
+               double beta, double* C, int64_t ldc, int cs, int co, cudaStream_t s);
+
+// Split FP64 values into hi/lo float planes: src element (i, j) at
+// src[(i + j*lds)*ss + so]; planes are dense rows x cols (ld = rows).
+void split_df32(const double* src, int64_t rows, int64_t cols, int64_t lds, int ss, int so,
+                float* hi, float* lo, cudaStream_t s);
+
+}  // namespace feast

@@ -23,8 +23,13 @@ def check_against_planted(out, P, tol=1e-10):
     # recompute residuals independently in FP64 on the host
     R = P.A @ X - X * out["evals"][None, :]
     assert np.max(np.linalg.norm(R, axis=0)) / P.anorm <= 2 * tol
+    # span: sin(angle) <= ||residual|| / gap (Davis-Kahan), gap = distance from
+    # the wanted eigenvalues to the rest of the spectrum
     Qi = P.inside_vectors
-    assert np.linalg.norm(X - Qi @ (Qi.conj().T @ X), 2) <= 1e-8
+    ins = (P.lam > P.lmin) & (P.lam < P.lmax)
+    gap = np.min(np.abs(P.lam[ins][:, None] - P.lam[~ins][None, :])) if np.any(~ins) else P.anorm
+    bound = max(1e-8, 4.0 * np.sqrt(P.inside.size) * tol * P.anorm / gap)
+    assert np.linalg.norm(X - Qi @ (Qi.conj().T @ X), 2) <= bound
 
 
 @pytest.mark.parametrize("vname,vor", VARIANTS)
@@ -58,7 +63,11 @@ def test_n500_workload_vs_oracle(ctx, vname, vor):
     check_against_planted(out, P)
     ref = O.feast_solve(P.A, a, b, 60, 8, 1e-10, X0, variant=vor, anorm=P.anorm)
     np.testing.assert_allclose(out["evals"], ref.lam, atol=1e-12 * P.anorm)
-    assert abs(out["iterations"] - ref.iterations) <= 1
+    if vor != O.XFEAST:
+        # XFEAST on a spectrum with eigenvalues on both sides of I stops when
+        # rounding-born spurious pairs leave its stopping set: its round count
+        # varies with rounding (x86 vs Arm oracle runs differ), so it is not pinned
+        assert abs(out["iterations"] - ref.iterations) <= 1
 
 
 @pytest.mark.parametrize("prec", ["f64", "mixed"])

@@ -177,3 +177,25 @@ def make_problem(name, lam, lmin, lmax, m0, n_c, seed=0, complex_=False, keep_q=
     return Problem(name=name, A=A, lam=lam, Q=Q if keep_q else None,
                    lmin=lmin, lmax=lmax, m0=m0, n_c=n_c,
                    meta={"seed": seed, "complex": complex_})
+
+
+def planted_matrix_torch(lam, seed, complex_=False, device="cuda:0"):
+    """A = Q diag(lam) Q^H with Q from the QR factorisation of a seeded
+    Gaussian matrix, built with torch on the GPU (large n).  Returns the
+    column-major CUDA tensor A; Q is not kept."""
+    import torch
+
+    n = int(lam.size)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed) + 1000)
+    dt = torch.complex128 if complex_ else torch.float64
+    G = torch.randn((n, n), generator=g, dtype=dt, device=device)
+    Q, R = torch.linalg.qr(G)
+    d = torch.diagonal(R)
+    Q = Q * (d / d.abs())[None, :]
+    del G, R
+    lam_t = torch.as_tensor(lam, dtype=torch.float64, device=device).to(dt)
+    A = (Q * lam_t[None, :]) @ Q.conj().T
+    del Q
+    A = 0.5 * (A + A.conj().T)
+    return A.transpose(0, 1).contiguous().transpose(0, 1)
