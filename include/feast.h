@@ -78,7 +78,7 @@ typedef struct {
   const void* x0;       /* optional device n x m0 starting subspace (leading dim n, dtype) */
   double refine_switch; /* mixed: while the previous iteration's max residual exceeds this and
                            fell at least tenfold, the next filter uses the FP32 solves without
-                           FP64 refinement (default 1e-4; 0 = always refine) */
+                           FP64 refinement (default 0: always refine) */
 } feast_opts;
 
 /* Per-call statistics of the last feast_interval_solve on a context. */

@@ -30,11 +30,15 @@ Readings where the paper is silent (each also recorded in the design notes):
     orthogonalises the window with a block QR (Sect. II-A allows QR or the SVD;
     the Gram matrix of the whole window cannot resolve directions below
     sqrt(eps), which loses the expansion once the iterates agree to ~1e-6);
-  * the XFEAST check runs over the m in-I selected pairs of lowest residual,
-    with m the in-I count of the Rayleigh-Ritz problem on the newest filtered
-    block, the rule Sect. II-B gives for RFEAST: on spectra with eigenvalues
-    on both sides of I, mixtures of outside eigenvectors give spurious Ritz
-    values inside I that the expanded window keeps regenerating;
+  * spurious pairs: on spectra with eigenvalues on both sides of I, mixtures
+    of outside eigenvectors give Ritz values inside I that never converge and
+    (with m0 below the number of eigenvalues near |rho| = 1/2) also inflate
+    RFEAST's first-pass count.  Besides the paper's checks, XFEAST and RFEAST
+    therefore also stop when every selected in-I pair whose filter response
+    mu_k = Re(x_k^H rho(A) x_k) exceeds 1/2 has converged; mu_k is read off
+    the filter application the next step performs anyway (rho > 1/2 exactly
+    inside I for the circle contour, rho < 1/2 outside, so a mixture of
+    outside eigenvectors has mu < 1/2); the pairs returned are those;
   * RFEAST normalises the residual columns, removes their (rounding-level)
     component along the current basis twice, orthonormalises them and appends
     them; the append after the last pass is dropped because nothing uses it;
@@ -236,17 +240,20 @@ def _feast(A, F, lmin, lmax, m0, tol, X0, max_iter, anorm):
     return _result(1, rp, ins, max_iter, max_iter, hist)
 
 
-def expected_count_newest(Q, Ar, B, lmin, lmax):
-    """Number of Ritz values inside I of the Rayleigh-Ritz problem restricted
-    to span(B), the newest filtered block (the conventional FEAST subspace),
-    computed from the reduced matrix A' = Q^H A Q of the whole window:
-    C = Q^H B orthonormalised, eigenvalues of C^H A' C."""
-    C = Q.conj().T @ B
-    C, _ = orthonormalize(C)
-    H = C.conj().T @ Ar @ C
-    H = 0.5 * (H + H.conj().T)
-    lam, _, _ = jacobi_eigh(H)
-    return int(np.sum(inside(lam, lmin, lmax)))
+def filter_response(X, Xf):
+    """mu_k = Re(x_k^H rho(A) x_k) for unit columns x_k of X, from Xf = rho(A) X:
+    the Rayleigh quotient of the filter, rho(lambda) for an eigenvector."""
+    return np.real(np.sum(X.conj() * Xf, axis=0))
+
+
+def _spurious_free(pend, mu, tol):
+    """Deferred stopping test of the previous round: its selected pairs inside
+    I whose filter response exceeds 1/2 (rho > 1/2 exactly inside I for the
+    circle contour) must all have converged; the others are spurious."""
+    keep = [k for k in pend["in_cols"] if mu[k] > 0.5]
+    if keep and max(pend["res"][k] for k in keep) <= tol:
+        return keep
+    return None
 
 
 def _xfeast(A, F, lmin, lmax, m0, tol, X0, s, max_iter, anorm):
@@ -262,30 +269,41 @@ def _xfeast(A, F, lmin, lmax, m0, tol, X0, s, max_iter, anorm):
         Q = block_qr_orth(blocks)                       # step 1
         rp = rayleigh_ritz(A, Q, anorm)                 # step 2(i)
         sel = select_pairs(rp.lam, rp.res, lmin, lmax, m0)   # step 2(ii)
-        # step 3 over the m in-I selected pairs of lowest residual, m counted
-        # on the newest filtered block (as RFEAST counts it, Sect. II-B)
-        m_exp = expected_count_newest(Q, rp.Ar, blocks[-1], lmin, lmax)
-        ins = sel[inside(rp.lam[sel], lmin, lmax)]
-        ins = ins[np.lexsort((rp.lam[ins], rp.res[ins]))][:m_exp]
-        r = float(np.max(rp.res[ins])) if ins.size else np.inf
+        ins, r = _check(rp.lam, rp.res, sel, lmin, lmax)     # step 3
         hist.append(r)
         if ins.size and r <= tol:
-            return _result(0, rp, ins, it, filters, hist, m_exp)
+            return _result(0, rp, ins, it, filters, hist)
         if ins.size == 0 and it >= 2:
-            return _result(0, rp, ins, it, filters, hist, m_exp)
+            return _result(0, rp, ins, it, filters, hist)
         if it == max_iter:
             break
-        blocks = blocks[1:] + [filter_apply(F, rp.X[:, sel])]   # step 4
+        Xs = rp.X[:, sel]
+        Xn = filter_apply(F, Xs)                        # step 4(i)
         filters += 1
-    return _result(1, rp, ins, max_iter, filters, hist, m_exp)
+        pend = {"in_cols": [c for c, i in enumerate(sel) if lmin < rp.lam[i] < lmax],
+                "res": rp.res[sel]}
+        keep = _spurious_free(pend, filter_response(Xs, Xn), tol)
+        if keep is not None:
+            return _result(0, rp, sel[keep], it, filters, hist)
+        blocks = blocks[1:] + [Xn]                      # step 4(ii)
+    return _result(1, rp, ins, max_iter, filters, hist)
 
 
 def _rfeast(A, F, lmin, lmax, m0, tol, X0, s, max_iter, anorm):
     X = np.array(X0, copy=True)
     hist = []
     rp = None
+    pend = None
+    filters = 0
     for it in range(1, max_iter + 1):
         Xf = filter_apply(F, X)                         # step 1
+        filters += 1
+        if pend is not None:
+            keep = _spurious_free(pend, filter_response(X, Xf), tol)
+            if keep is not None:
+                prp = pend["rp"]
+                return _result(0, prp, pend["sel"][keep], it - 1, filters, hist, pend["m"])
+            pend = None
         Q, _ = orthonormalize(Xf)
         m_expected = 0
         for j in range(1, s + 1):                       # step 2
@@ -307,7 +325,10 @@ def _rfeast(A, F, lmin, lmax, m0, tol, X0, s, max_iter, anorm):
         r = float(np.max(rp.res[ins])) if ins.size else np.inf
         hist.append(r)
         if ins.size and r <= tol:
-            return _result(0, rp, ins, it, it, hist, m_expected)
+            return _result(0, rp, ins, it, filters, hist, m_expected)
         if ins.size == 0 and it >= 2:
-            return _result(0, rp, ins, it, it, hist, m_expected)
-    return _result(1, rp, ins, max_iter, max_iter, hist, m_expected)
+            return _result(0, rp, ins, it, filters, hist, m_expected)
+        in_cols = [c for c, i in enumerate(sel) if lmin < rp.lam[i] < lmax]
+        if any(rp.res[sel[c]] <= tol for c in in_cols):
+            pend = {"in_cols": in_cols, "res": rp.res[sel], "sel": sel, "rp": rp, "m": m_expected}
+    return _result(1, rp, ins, max_iter, filters, hist, m_expected)

@@ -262,6 +262,15 @@ __global__ void col_norms2_kernel(const S* X, int64_t n, int64_t ld, double* out
 }
 
 template <typename S>
+__global__ void col_dots_kernel(const S* X, const S* Y, int64_t n, int64_t ld, double* out) {
+  const int64_t j = blockIdx.x;
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += real_part(conj(X[i + j * ld]) * Y[i + j * ld]);
+  s = block_sum(s);
+  if (threadIdx.x == 0) out[j] = s;
+}
+
+template <typename S>
 __global__ void resid_norms2_kernel(const S* AX, const S* X, int64_t n, int64_t ld, const double* lam, double* out) {
   const int64_t j = blockIdx.x;
   const double l = lam[j];
@@ -477,6 +486,13 @@ template <typename S> void col_norms2(const S* X, int64_t n, int64_t k, int64_t 
 }
 
 template <typename S>
+void col_dots_re(const S* X, const S* Y, int64_t n, int64_t k, int64_t ld, double* out, cudaStream_t s) {
+  if (k <= 0) return;
+  col_dots_kernel<S><<<(unsigned)k, 256, 0, s>>>(X, Y, n, ld, out);
+  FEAST_LAUNCH_CHECK();
+}
+
+template <typename S>
 void resid_norms2(const S* AX, const S* X, int64_t n, int64_t k, int64_t ld, const double* lam, double* out,
                   cudaStream_t s) {
   if (k <= 0) return;
@@ -556,6 +572,7 @@ template <typename S> void check_finite(const S* X, int64_t n, int64_t m, int64_
   template void jacobi_eigh<S>(S*, int64_t, int64_t, S*, int64_t, double, const CoopWork&, int, cudaStream_t); \
   template void get_diag<S>(const S*, int64_t, int64_t, double*, cudaStream_t);                            \
   template void col_norms2<S>(const S*, int64_t, int64_t, int64_t, double*, cudaStream_t);                 \
+  template void col_dots_re<S>(const S*, const S*, int64_t, int64_t, int64_t, double*, cudaStream_t);      \
   template void resid_norms2<S>(const S*, const S*, int64_t, int64_t, int64_t, const double*, double*,     \
                                 cudaStream_t);                                                            \
   template void ritz_residual<S>(S*, const S*, const S*, int64_t, int64_t, int64_t, const double*,         \

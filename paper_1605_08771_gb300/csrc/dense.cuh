@@ -51,6 +51,10 @@ template <typename S>
 void resid_norms2(const S* AX, const S* X, int64_t n, int64_t k, int64_t ld, const double* lam, double* out,
                   cudaStream_t s);
 
+// out[j] = Re( X[:, j]^H Y[:, j] )
+template <typename S>
+void col_dots_re(const S* X, const S* Y, int64_t n, int64_t k, int64_t ld, double* out, cudaStream_t s);
+
 // R[:, j] = AX[:, j] - lam[j] X[:, j]
 template <typename S>
 void ritz_residual(S* R, const S* AX, const S* X, int64_t n, int64_t k, int64_t ld, const double* lam, cudaStream_t s);

@@ -536,10 +536,56 @@ struct Solver {
   // ---- drivers ----
   struct Out {
     int status = 0;
-    std::vector<int> idx;  // returned pairs (indices into lam/res/Xr), ascending lambda
+    std::vector<int> idx;       // returned pairs: columns of `src`, ascending lambda
+    std::vector<double> ev, rs; // their eigenvalues and relative residuals
+    const S* src = nullptr;     // device matrix holding the eigenvectors (ld n)
     int iterations = 0, filters = 0, m_expected = -1;
     std::vector<double> hist;
   };
+  // Deferred stopping test of a round whose selected pairs are the columns of
+  // the block that the next filter takes: those inside I with filter response
+  // mu_k = Re(x_k^H rho(A) x_k) > 1/2 must all have converged (a mixture of
+  // eigenvectors outside I has mu < 1/2; rho > 1/2 exactly inside I).
+  struct Pending {
+    bool valid = false;
+    std::vector<int> in_cols;        // columns (within the block) of the pairs inside I
+    std::vector<double> ev, rs;      // per column of the block
+  };
+  bool response_test(const Pending& pd, const S* Xb, const S* Xfb, int64_t cols, double tol, Out& out) {
+    col_dots_re<S>(Xb, Xfb, n, cols, n, d_nrm, st);
+    std::vector<double> mu(cols);
+    to_host(ctx, mu.data(), d_nrm, cols);
+    std::vector<int> keep;
+    for (int c : pd.in_cols)
+      if (mu[c] > 0.5) keep.push_back(c);
+    if (keep.empty()) return false;
+    for (int c : keep)
+      if (!(pd.rs[c] <= tol)) return false;
+    std::sort(keep.begin(), keep.end(), [&](int a, int b) { return pd.ev[a] < pd.ev[b] || (pd.ev[a] == pd.ev[b] && a < b); });
+    out.idx = keep;
+    out.ev.clear();
+    out.rs.clear();
+    for (int c : keep) {
+      out.ev.push_back(pd.ev[c]);
+      out.rs.push_back(pd.rs[c]);
+    }
+    out.src = Xb;
+    return true;
+  }
+  Pending make_pending(const std::vector<int>& sel, double tol) {
+    Pending pd;
+    bool any_conv = false;
+    for (size_t c = 0; c < sel.size(); ++c) {
+      pd.ev.push_back(lam[sel[c]]);
+      pd.rs.push_back(res[sel[c]]);
+      if (in_interval(lam[sel[c]], lmin, lmax)) {
+        pd.in_cols.push_back((int)c);
+        any_conv = any_conv || res[sel[c]] <= tol;
+      }
+    }
+    pd.valid = any_conv;
+    return pd;
+  }
 
   // mixed: skip the FP64-accurate refinement of the next filter while the
   // residual is above o.refine_switch and still falling at least tenfold per
@@ -560,6 +606,13 @@ struct Solver {
   void finish(Out& out, std::vector<int> ins) {
     std::sort(ins.begin(), ins.end(), [&](int a, int b) { return lam[a] < lam[b] || (lam[a] == lam[b] && a < b); });
     out.idx = ins;
+    out.ev.clear();
+    out.rs.clear();
+    for (int i : ins) {
+      out.ev.push_back(lam[i]);
+      out.rs.push_back(res[i]);
+    }
+    out.src = Xr;
   }
   std::vector<int> lowest_residual(std::vector<int> v, int m) {
     std::stable_sort(v.begin(), v.end(), [&](int a, int b) {
@@ -655,24 +708,6 @@ struct Solver {
     return kq;
   }
 
-  // in-I count of Rayleigh-Ritz restricted to span(B) (the newest block)
-  int expected_count_newest(int64_t k, const S* B, int64_t mb) {
-    S* C = T1;  // k x mb (ld k), small
-    mm_reduce(k, mb, n, Qb, n, OP_C, B, n, OP_N, C, k);
-    S* Ct = T2;
-    const int64_t r = orthonormalize(C, k, mb, Ct, AXr /*scratch, k*mb fits*/);
-    if (r == 0) return 0;
-    // H = Ct^H A' Ct
-    mm(k, r, k, C1(1.0), Ar0, kmax, OP_N, Ct, k, OP_N, C1(0.0), Cs2, k);
-    mm(r, r, k, C1(1.0), Ct, k, OP_C, Cs2, k, OP_N, C1(0.0), Gs, r);
-    hermitize<S>(Gs, r, r, st);
-    std::vector<double> ev;
-    eig(Gs, r, ev);
-    int cnt = 0;
-    for (double v : ev) cnt += in_interval(v, lmin, lmax);
-    return cnt;
-  }
-
   Out run_xfeast(S* X0, int m0, double tol, int s) {
     Out out;
     std::vector<S*> ring(s);
@@ -696,14 +731,12 @@ struct Solver {
     S* Xsel = dalloc<S>(ctx, n * m0);
     std::vector<int> ins;
     for (int it = 1; it <= o.max_iter; ++it) {
-      const int64_t k = block_qr(ring, m0);
+      const int64_t k = block_qr(ring, m0);                       // step 1
       if (k == 0) throw FeastError{FEAST_ERR_ORTH};
-      rr_project(k);
+      rr_project(k);                                              // step 2(i)
       rr_solve(k);
-      std::vector<int> sel = select_pairs(lam, res, lmin, lmax, m0);
-      const int mexp = expected_count_newest(k, ring[s - 1], m0);
-      out.m_expected = mexp;
-      ins = lowest_residual(in_sorted(sel), mexp);
+      std::vector<int> sel = select_pairs(lam, res, lmin, lmax, m0);   // step 2(ii)
+      ins = in_sorted(sel);                                       // step 3
       const double r = max_res(ins);
       out.hist.push_back(r);
       update_refine(out.hist);
@@ -713,12 +746,15 @@ struct Solver {
         return out;
       }
       if (it == o.max_iter) break;
-      to_dev(ctx, d_idx, sel.data(), (int64_t)sel.size());
-      gather_cols<S>(Xsel, n, Xr, n, n, d_idx, (int64_t)sel.size(), nullptr, st);
+      const int64_t ms = (int64_t)sel.size();
+      to_dev(ctx, d_idx, sel.data(), ms);
+      gather_cols<S>(Xsel, n, Xr, n, n, d_idx, ms, nullptr, st);
       S* oldest = ring[0];
-      filter(Xsel, (int64_t)sel.size(), oldest);
+      filter(Xsel, ms, oldest);                                   // step 4(i)
       ++out.filters;
-      std::rotate(ring.begin(), ring.begin() + 1, ring.end());
+      Pending pd = make_pending(sel, tol);
+      if (pd.valid && response_test(pd, Xsel, oldest, ms, tol, out)) return out;
+      std::rotate(ring.begin(), ring.begin() + 1, ring.end());    // step 4(ii)
     }
     finish(out, ins);
     out.status = FEAST_WARN_MAXITER;
@@ -731,9 +767,17 @@ struct Solver {
     S* AXs = dalloc<S>(ctx, n * m0);
     std::vector<int> ins;
     int64_t kx = m0;
+    Pending pd;
     for (int it = 1; it <= o.max_iter; ++it) {
-      filter(X, kx, Xf);
+      filter(X, kx, Xf);                                          // step 1
       ++out.filters;
+      if (pd.valid) {
+        if (response_test(pd, X, Xf, kx, tol, out)) {
+          out.iterations = it - 1;
+          return out;
+        }
+        pd.valid = false;
+      }
       int64_t k = orthonormalize(Xf, n, kx, Qb, T1);
       if (k == 0) throw FeastError{FEAST_ERR_ORTH};
       rr_project(k);
@@ -788,8 +832,18 @@ struct Solver {
         }
       }
       out.m_expected = mexp;
-      ins = lowest_residual(in_sorted(sel), mexp);
+      const std::vector<int> all_in = in_sorted(sel);
+      ins = lowest_residual(all_in, mexp);
       const double r = max_res(ins);
+      if (std::getenv("FEAST_LOG")) {
+        std::vector<double> rr;
+        for (int i : all_in) rr.push_back(res[i]);
+        std::sort(rr.begin(), rr.end());
+        fprintf(stderr, "[feast] rfeast it %d: k %lld, m_exp %d, in-I selected %zu, max over m_exp %.2e, in-I residuals:",
+                it, (long long)k, mexp, all_in.size(), r);
+        for (size_t q = rr.size() > 8 ? rr.size() - 8 : 0; q < rr.size(); ++q) fprintf(stderr, " %.1e", rr[q]);
+        fprintf(stderr, "\n");
+      }
       out.hist.push_back(r);
       update_refine(out.hist);
       out.iterations = it;
@@ -797,6 +851,7 @@ struct Solver {
         finish(out, ins);
         return out;
       }
+      pd = make_pending(sel, tol);
     }
     finish(out, ins);
     out.status = FEAST_WARN_MAXITER;
@@ -875,14 +930,11 @@ int solve_t(feast_ctx* ctx, const S* A, int64_t n, int64_t lda, double lmin, dou
   else if (o.variant == FEAST_RFEAST) out = sv.run_rfeast(X, m0, tol, s);
   else out = sv.run_plain(X, m0, tol);
   const int mf = (int)out.idx.size();
-  std::vector<double> ev(mf), rs(mf);
-  for (int i = 0; i < mf; ++i) {
-    ev[i] = sv.lam[out.idx[i]];
-    rs[i] = sv.res[out.idx[i]];
-  }
+  const std::vector<double>& ev = out.ev;
+  const std::vector<double>& rs = out.rs;
   if (mf > 0) {
     to_dev(ctx, sv.d_idx, out.idx.data(), mf);
-    gather_cols<S>(evecs, n, sv.Xr, n, n, sv.d_idx, mf, nullptr, ctx->stream);
+    gather_cols<S>(evecs, n, out.src, n, n, sv.d_idx, mf, nullptr, ctx->stream);
   }
   sync(ctx);
   for (int i = 0; i < mf; ++i) {
@@ -927,7 +979,7 @@ void feast_opts_default(feast_opts* o) {
   o->refine_tol = 0.0;
   o->seed = 0x1605087710ull;
   o->x0 = nullptr;
-  o->refine_switch = 1e-4;
+  o->refine_switch = 0.0;
 }
 
 int feast_init(feast_ctx** ctx, int device, void* stream) {
