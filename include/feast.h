@@ -73,7 +73,7 @@ typedef struct {
   double aspect;        /* ellipse vertical / horizontal semi-axis (default 1: circle) */
   double anorm;         /* ||A||_2 when > 0; otherwise 40 power iterations estimate it */
   double refine_tol;    /* mixed: stop when ||R||_F <= refine_tol (||A|| + |z|) ||Y||_F;
-                           0 = 2 eps sqrt(n) */
+                           0 = 16 eps sqrt(n) */
   unsigned long long seed; /* seed of the N(0,1) starting subspace when x0 == NULL */
   const void* x0;       /* optional device n x m0 starting subspace (leading dim n, dtype) */
   double refine_switch; /* mixed: while the previous iteration's max residual exceeds this and
@@ -93,6 +93,11 @@ typedef struct {
   double total_ms;      /* whole solve */
   double max_residual;  /* max relative residual of the returned pairs */
   double history[128];  /* max residual per iteration (first 128) */
+  double gemm_df_ms;    /* mixed: summed device time (CUDA events) of the double-float
+                           GEMM launches, the dominant kernel of the mixed path */
+  double gemm_df_mac;   /* their real multiply-adds (M*N*K summed over launches) */
+  int gemm_df_launches; /* their number */
+  int reserved2;
 } feast_stats;
 
 void feast_opts_default(feast_opts* opts);
@@ -105,6 +110,10 @@ int feast_init(feast_ctx** ctx, int device, void* stream);
 /* Release the context and its workspace. */
 int feast_finalize(feast_ctx* ctx);
 const char* feast_strerror(int code);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (all contexts).  The difference across a call is its launch count. */
+uint64_t feast_kernel_launches(void);
 
 /* Contour nodes z_j and weights w_j of the upper half-contour (Eq. 3 with the
  * circle/ellipse reading above): z and w receive n_c complex values each

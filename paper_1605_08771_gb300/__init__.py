@@ -31,7 +31,7 @@ EXPORTS = [
     "feast_opts_default", "feast_init", "feast_finalize", "feast_strerror",
     "feast_contour_nodes", "feast_interval_solve", "feast_filter_apply",
     "feast_shifted_lu", "feast_shifted_solve", "feast_orthonormalize",
-    "feast_jacobi_eigh", "feast_rayleigh_ritz",
+    "feast_jacobi_eigh", "feast_rayleigh_ritz", "feast_kernel_launches",
 ]
 
 
@@ -46,7 +46,8 @@ class FeastStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("filters", ctypes.c_int), ("refine_steps", ctypes.c_int),
                 ("m_expected", ctypes.c_int), ("factor_ms", ctypes.c_double), ("filter_ms", ctypes.c_double),
                 ("total_ms", ctypes.c_double), ("max_residual", ctypes.c_double),
-                ("history", ctypes.c_double * 128)]
+                ("history", ctypes.c_double * 128), ("gemm_df_ms", ctypes.c_double),
+                ("gemm_df_mac", ctypes.c_double), ("gemm_df_launches", ctypes.c_int), ("reserved2", ctypes.c_int)]
 
 
 class FeastError(RuntimeError):
@@ -82,6 +83,7 @@ def lib():
         "feast_orthonormalize": (I, [P, I, I64, I64, P, I, IP]),
         "feast_jacobi_eigh": (I, [P, I, I64, P, DP, P, IP]),
         "feast_rayleigh_ritz": (I, [P, P, I, I64, I64, P, I64, D, DP, P, DP]),
+        "feast_kernel_launches": (ctypes.c_uint64, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -140,6 +142,10 @@ def _check(code, where):
 # ---------------------------------------------------------------------------
 def feast_strerror(code: int) -> str:
     return lib().feast_strerror(int(code)).decode()
+
+
+def feast_kernel_launches() -> int:
+    return int(lib().feast_kernel_launches())
 
 
 def feast_opts_default(**kw) -> FeastOpts:

@@ -122,7 +122,21 @@ enum DeviceStatus : int {
     }                                                                               \
   } while (0)
 
-#define FEAST_LAUNCH_CHECK() FEAST_CUDA_TRY(cudaGetLastError())
+// every kernel launch of the library passes through here (the count is
+// reported by feast_kernel_launches())
+void note_launch();
+unsigned long long launch_count();
+#define FEAST_LAUNCH_CHECK()                \
+  do {                                      \
+    ::feast::note_launch();                 \
+    FEAST_CUDA_TRY(cudaGetLastError());     \
+  } while (0)
+
+// CUDA-event timing of the double-float GEMM launches of one solve (the
+// dominant kernel of the mixed path): enable, then read the summed device
+// time, multiply-adds and launch count.
+void df_timer_begin();
+void df_timer_end(double* ms, double* macs, int* launches);
 
 struct CudaFailure {
   cudaError_t err;

@@ -450,6 +450,7 @@ void cholesky_upper(S* G, int64_t k, int64_t ld, const CoopWork& w, int num_sms,
   CoopWork wl = w;
   void* args[] = {&G, &k, &ld, &wl, &P};
   FEAST_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)chol_kernel<S>, dim3(P), dim3(256), args, smem, s));
+  note_launch();
 }
 
 template <typename S>
@@ -472,6 +473,7 @@ void jacobi_eigh(S* H, int64_t k, int64_t ld, S* V, int64_t ldv, double tol, con
   CoopWork wl = w;
   void* args[] = {&H, &k, &ld, &V, &ldv, &tol, &wl, &P, &maxs};
   FEAST_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)jacobi_kernel<S>, dim3(P), dim3(256), args, 0, s));
+  note_launch();
 }
 
 template <typename S> void get_diag(const S* H, int64_t k, int64_t ld, double* d, cudaStream_t s) {

@@ -411,6 +411,7 @@ void lu_factor_batched(F* M, int64_t n, int64_t ld, int64_t stride, int nodes,
     void* args[] = {&M, &n, &ld, &stride, &k0i, (void*)&jb, &P, (void*)&R, &ipiv, &wl, &base};
     FEAST_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)panel_lu_kernel<F>, dim3(nodes * P),
                                                dim3(kPanelThreads), args, 0, s));
+  note_launch();
     base += (unsigned)jb * (unsigned)P;
     if (n - jb > 0) {
       dim3 g2((unsigned)cdiv(n - jb, kSwapWarps), nodes);

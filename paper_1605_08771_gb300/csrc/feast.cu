@@ -410,8 +410,11 @@ struct Solver {
         accumulate_filter<S>(Xf, n, Y, n, m, nc, d_w, st);
         return;
       }
-      const double rtol = o.refine_tol > 0 ? o.refine_tol : 2.0 * 2.220446049250313e-16 * std::sqrt((double)n);
+      // default target 16 eps sqrt(n): just above the accuracy floor of the
+      // double-float residual (about 2^-48 relative per product)
+      const double rtol = o.refine_tol > 0 ? o.refine_tol : 16.0 * 2.220446049250313e-16 * std::sqrt((double)n);
       std::vector<double> en(2 * E), prev(E, -1.0);
+      double worst_prev = -1.0;
       for (int step = 0; step < o.refine_max; ++step) {
         // R_e = X - (z_e I - A) Y_e, FP64-accurate (double-float A Y)
         apply_A_df((const double*)Y, true, E * m, (double*)AY);
@@ -438,8 +441,18 @@ struct Solver {
           prev[e] = rn;
         }
         if (conv || stagnant) break;
+        // relative residual of the worst entry and its contraction per step
+        double worst = 0.0;
+        for (int e = 0; e < E; ++e) {
+          const c128 ze = e < nc ? z[e] : conj(z[e - nc]);
+          worst = std::max(worst, std::sqrt(en[2 * e]) / ((anorm + std::sqrt(abs2(ze))) * std::sqrt(en[2 * e + 1])));
+        }
         solve_lowp<c128>(Yw, n, nm, m, true);
         ++refine_steps;
+        // when the observed contraction already puts the next residual well
+        // below the target, the correction just applied finishes the refinement
+        if (worst_prev > 0.0 && worst * (worst / worst_prev) * 8.0 <= rtol) break;
+        worst_prev = worst;
       }
     }
     accumulate_filter<S>(Xf, n, Y, n, m, nc, d_w, st);
@@ -921,6 +934,7 @@ int solve_t(feast_ctx* ctx, const S* A, int64_t n, int64_t lda, double lmin, dou
     random_normal<S>(X, n, m0, n, o.seed, ctx->stream);
   }
   sync(ctx);
+  df_timer_begin();
   const double tf0 = now_ms();
   sv.factor();
   sync(ctx);
@@ -950,6 +964,7 @@ int solve_t(feast_ctx* ctx, const S* A, int64_t n, int64_t lda, double lmin, dou
   st.m_expected = out.m_expected;
   st.factor_ms = tf1 - tf0;
   st.filter_ms = sv.filter_ms;
+  df_timer_end(&st.gemm_df_ms, &st.gemm_df_mac, &st.gemm_df_launches);
   st.total_ms = now_ms() - t0;
   st.max_residual = 0.0;
   for (double r : rs) st.max_residual = std::max(st.max_residual, r);
@@ -1011,6 +1026,8 @@ int feast_finalize(feast_ctx* ctx) {
   delete ctx;
   return FEAST_OK;
 }
+
+uint64_t feast_kernel_launches(void) { return (uint64_t)feast::launch_count(); }
 
 const char* feast_strerror(int code) {
   switch (code) {

@@ -4,6 +4,9 @@
 // epilogue stores of a warp are contiguous.
 #include "gemm.cuh"
 
+#include <atomic>
+#include <vector>
+
 namespace feast {
 
 namespace {
@@ -278,13 +281,69 @@ __global__ void split_df32_kernel(const double* src, int64_t rows, int64_t cols,
 
 }  // namespace
 
+namespace {
+struct DfTimer {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  double macs = 0.0;
+  int launches = 0;
+};
+DfTimer& df_timer() {
+  static DfTimer t;
+  return t;
+}
+std::atomic<unsigned long long> g_launches{0};
+}  // namespace
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+unsigned long long launch_count() { return g_launches.load(); }
+
+void df_timer_begin() {
+  DfTimer& t = df_timer();
+  t.on = true;
+  t.used = 0;
+  t.macs = 0.0;
+  t.launches = 0;
+}
+void df_timer_end(double* ms, double* macs, int* launches) {
+  DfTimer& t = df_timer();
+  double tot = 0.0;
+  for (size_t i = 0; i + 1 < t.used; i += 2) {
+    float e = 0.f;
+    FEAST_CUDA_TRY(cudaEventSynchronize(t.pool[i + 1]));
+    FEAST_CUDA_TRY(cudaEventElapsedTime(&e, t.pool[i], t.pool[i + 1]));
+    tot += e;
+  }
+  if (ms) *ms = tot;
+  if (macs) *macs = t.macs;
+  if (launches) *launches = t.launches;
+  t.on = false;
+  t.used = 0;
+}
+
 void gemm_df32(int64_t M, int64_t N, int64_t K, double alpha, const float* Ahi, const float* Alo, int64_t lda,
                const float* Bhi, const float* Blo, int64_t ldb, double beta, double* C, int64_t ldc, int cs, int co,
                cudaStream_t s) {
   if (M <= 0 || N <= 0) return;
+  DfTimer& tm = df_timer();
+  if (tm.on) {
+    while (tm.pool.size() < tm.used + 2) {
+      cudaEvent_t e;
+      FEAST_CUDA_TRY(cudaEventCreate(&e));
+      tm.pool.push_back(e);
+    }
+    FEAST_CUDA_TRY(cudaEventRecord(tm.pool[tm.used], s));
+  }
   dim3 grid((unsigned)cdiv(M, DF_BM), (unsigned)cdiv(N, DF_BN));
   gemm_df32_kernel<<<grid, DF_THREADS, 0, s>>>(M, N, K, alpha, Ahi, Alo, lda, Bhi, Blo, ldb, beta, C, ldc, cs, co);
   FEAST_LAUNCH_CHECK();
+  if (tm.on) {
+    FEAST_CUDA_TRY(cudaEventRecord(tm.pool[tm.used + 1], s));
+    tm.used += 2;
+    tm.macs += (double)M * (double)N * (double)K;
+    tm.launches += 1;
+  }
 }
 
 void split_df32(const double* src, int64_t rows, int64_t cols, int64_t lds, int ss, int so, float* hi, float* lo,
