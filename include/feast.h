@@ -184,6 +184,24 @@ int feast_rayleigh_ritz(feast_ctx* ctx, const void* A, int dtype, int64_t n, int
                         const void* Q, int64_t k, double anorm, double* evals, void* X,
                         double* res);
 
+/* Allocation-free Jacobi eigensolver, for callers that cannot allocate device
+ * memory at call time: code running while a CUDA stream is captured, services
+ * that reserve their whole memory budget up front, frameworks whose caching
+ * allocator holds the free memory.  (The paper has no counterpart; this is a
+ * deployment variant of feast_jacobi_eigh.)  Same operation and outputs as
+ * feast_jacobi_eigh, without a context: device is the CUDA device, stream a
+ * cudaStream_t (NULL = legacy default stream), H device k x k (leading dim k,
+ * not modified), evals host (k doubles, ascending), V device k x k.
+ * All scratch lives in one static device array of 2.25 MiB inside the library
+ * (held by every GPU that loads the library until the process exits), so k is
+ * limited to 1 <= k <= 256; larger k returns FEAST_ERR_ARG.  No cudaMalloc,
+ * cudaFree or allocating library routine is called.  The first call on a
+ * device looks up the array's device address (once per device); make that
+ * first call before any stream capture.  Every call reuses the same array:
+ * calls that overlap on the GPU (other streams or host threads) race. */
+int feast_jacobi_eigh_noalloc(int device, void* stream, int dtype, int64_t k, const void* H,
+                              double* evals, void* V, int* sweeps);
+
 #ifdef __cplusplus
 }
 #endif

@@ -31,7 +31,7 @@ EXPORTS = [
     "feast_opts_default", "feast_init", "feast_finalize", "feast_strerror",
     "feast_contour_nodes", "feast_interval_solve", "feast_filter_apply",
     "feast_shifted_lu", "feast_shifted_solve", "feast_orthonormalize",
-    "feast_jacobi_eigh", "feast_rayleigh_ritz", "feast_kernel_launches",
+    "feast_jacobi_eigh", "feast_rayleigh_ritz", "feast_kernel_launches", "feast_jacobi_eigh_noalloc",
 ]
 
 
@@ -84,6 +84,7 @@ def lib():
         "feast_jacobi_eigh": (I, [P, I, I64, P, DP, P, IP]),
         "feast_rayleigh_ritz": (I, [P, P, I, I64, I64, P, I64, D, DP, P, DP]),
         "feast_kernel_launches": (ctypes.c_uint64, []),
+        "feast_jacobi_eigh_noalloc": (I, [I, P, I, I64, P, DP, P, IP]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
