@@ -332,16 +332,18 @@ __global__ void accumulate_kernel(S* Xf, int64_t ld, const c128* Y, int64_t n, i
 
 template <typename S>
 __global__ void refine_residual_kernel(c128* R, const S* X, int64_t ldx, const c128* Y, const c128* AY, int64_t n,
-                                       int64_t m, const c128* z_e) {
+                                       int64_t m, const c128* z_e, const int* active) {
   const int e = blockIdx.y;
   const int64_t nm = n * m;
   const c128 z = z_e[e];
+  const bool on = active[e] != 0;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nm; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = t % n, c = t / n;
     const int64_t o = (int64_t)e * nm + t;
-    R[o] = cvt<c128>(X[i + c * ldx]) - z * Y[o] + AY[o];
+    R[o] = on ? cvt<c128>(X[i + c * ldx]) - z * Y[o] + AY[o] : c128{0.0, 0.0};
   }
 }
+
 
 __global__ void entry_norms2_kernel(const c128* R, const c128* Y, int64_t nm, double* out) {
   const int e = blockIdx.y;
@@ -531,11 +533,12 @@ void accumulate_filter(S* Xf, int64_t ld, const c128* Y, int64_t n, int64_t m, i
 
 template <typename S>
 void refine_residual(c128* R, const S* X, int64_t ldx, const c128* Y, const c128* AY, int64_t n, int64_t m,
-                     int entries, const c128* z_e, cudaStream_t s) {
+                     int entries, const c128* z_e, const int* active, cudaStream_t s) {
   dim3 g(grid1d(n * m), entries);
-  refine_residual_kernel<S><<<g, 256, 0, s>>>(R, X, ldx, Y, AY, n, m, z_e);
+  refine_residual_kernel<S><<<g, 256, 0, s>>>(R, X, ldx, Y, AY, n, m, z_e, active);
   FEAST_LAUNCH_CHECK();
 }
+
 
 void entry_norms2(const c128* R, const c128* Y, int64_t n, int64_t m, int entries, double* out, cudaStream_t s) {
   FEAST_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(double) * 2 * entries, s));
@@ -585,7 +588,7 @@ template <typename S> void check_finite(const S* X, int64_t n, int64_t m, int64_
   template void accumulate_filter<S>(S*, int64_t, const c128*, int64_t, int64_t, int, const c128*,         \
                                      cudaStream_t);                                                       \
   template void refine_residual<S>(c128*, const S*, int64_t, const c128*, const c128*, int64_t, int64_t,   \
-                                   int, const c128*, cudaStream_t);                                       \
+                                   int, const c128*, const int*, cudaStream_t);                           \
   template void random_normal<S>(S*, int64_t, int64_t, int64_t, unsigned long long, cudaStream_t);         \
   template void copy_matrix<S>(S*, int64_t, const S*, int64_t, int64_t, int64_t, cudaStream_t);            \
   template void set_identity<S>(S*, int64_t, int64_t, cudaStream_t);                                       \

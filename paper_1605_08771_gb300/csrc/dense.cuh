@@ -74,10 +74,12 @@ template <typename S>
 void accumulate_filter(S* Xf, int64_t ld, const c128* Y, int64_t n, int64_t m, int nodes, const c128* w,
                        cudaStream_t s);
 
-// R_e = X - z_e Y_e + AY_e for every entry e (complex FP64).
+// R_e = X - z_e Y_e + AY_e for every entry e with active[e] != 0 (complex
+// FP64); R_e = 0 for the others.
 template <typename S>
 void refine_residual(c128* R, const S* X, int64_t ldx, const c128* Y, const c128* AY, int64_t n, int64_t m,
-                     int entries, const c128* z_e, cudaStream_t s);
+                     int entries, const c128* z_e, const int* active, cudaStream_t s);
+
 
 // ||R_e||_F^2 and ||Y_e||_F^2 per entry (out[2e], out[2e+1])
 void entry_norms2(const c128* R, const c128* Y, int64_t n, int64_t m, int entries, double* out, cudaStream_t s);

@@ -195,12 +195,14 @@ struct Solver {
   c128* AY = nullptr;
   c64* Yc = nullptr;
   double* d_en = nullptr;
+  int* d_act = nullptr;
   int refine_steps = 0;
   bool refine_now = true;      // mixed: refine the next filter application
   // mixed: double-float planes of A (hi/lo of Re, then of Im) and of the
   // right-hand block of an A product
   float* Apl = nullptr;
   float* Bpl = nullptr;
+  double* Tdf = nullptr;
   int64_t bpl_cols = 0;
   // Rayleigh-Ritz scratch
   S *Qb = nullptr, *Wb = nullptr, *Xr = nullptr, *AXr = nullptr, *T1 = nullptr, *T2 = nullptr;
@@ -213,6 +215,21 @@ struct Solver {
 
   std::vector<double> lam, res;  // last Rayleigh-Ritz
   int last_sweeps = 0;
+
+  // phase timing (FEAST_PROFILE set): synchronises around each phase
+  bool profile = std::getenv("FEAST_PROFILE") != nullptr;
+  std::vector<std::pair<const char*, double>> phases;
+  template <typename Fn> void phase(const char* name, Fn&& fn) {
+    if (!profile) { fn(); return; }
+    sync(ctx);
+    const double t0 = now_ms();
+    fn();
+    sync(ctx);
+    const double dt = now_ms() - t0;
+    for (auto& p : phases)
+      if (p.first == name) { p.second += dt; return; }
+    phases.push_back({name, dt});
+  }
 
   Solver(feast_ctx* c, const S* A_, int64_t n_, int64_t lda_, double a, double b, int nc_, const feast_opts& o_)
       : ctx(c), st(c->stream), A(A_), n(n_), lda(lda_), lmin(a), lmax(b), nc(nc_), o(o_) {
@@ -236,6 +253,7 @@ struct Solver {
     cw = coop_work_carve(ctx->arena.alloc(coop_work_bytes(kmax, ctx->num_sms)), kmax, ctx->num_sms);
     d_flag = dalloc<int>(ctx, 4);
     d_en = dalloc<double>(ctx, 2 * E);
+    d_act = dalloc<int>(ctx, E);
   }
   void alloc_factors() {
     const size_t eb = o.prec == FEAST_PREC_F64 ? sizeof(c128) : sizeof(c64);
@@ -254,16 +272,18 @@ struct Solver {
       Yw = dalloc<c128>(ctx, E * nm);
       AY = dalloc<c128>(ctx, E * nm);
       Yc = dalloc<c64>(ctx, E * nm);
-      const int apl = kCplx ? 4 : 2;
+      const int apl = kCplx ? 6 : 2;
       Apl = dalloc<float>(ctx, (int64_t)apl * n * n);
       if (kCplx) {
         split_df32((const double*)A, n, n, lda, 2, 0, Apl, Apl + n * n, st);
         split_df32((const double*)A, n, n, lda, 2, 1, Apl + 2 * n * n, Apl + 3 * n * n, st);
+        split_df32((const double*)A, n, n, lda, 2, 2, Apl + 4 * n * n, Apl + 5 * n * n, st);
       } else {
         split_df32((const double*)A, n, n, lda, 1, 0, Apl, Apl + n * n, st);
       }
       bpl_cols = std::max<int64_t>(E * m, kmax);
-      Bpl = dalloc<float>(ctx, 4 * n * bpl_cols);
+      Bpl = dalloc<float>(ctx, 6 * n * bpl_cols);
+      if (kCplx) Tdf = dalloc<double>(ctx, n * bpl_cols);
     }
   }
   void alloc_rr() {
@@ -298,19 +318,24 @@ struct Solver {
                          ks > 1 ? (void*)part : nullptr);
   }
   // Out = A * B for an n x k block B (ld n) in double-float arithmetic on the
-  // FP32 pipes: B complex (bcplx) or real; Out has B's element type.
+  // FP32 pipes: B complex (bcplx) or real; Out has B's element type.  Complex
+  // A times complex B takes three real products (3M): T1 = Ar Br, T2 = Ai Bi,
+  // T3 = (Ar + Ai)(Br + Bi), Re = T1 - T2, Im = T3 - T1 - T2.
   void apply_A_df(const double* B, bool bcplx, int64_t k, double* Out) {
-    const int64_t nk = n * k;
+    const int64_t nk = n * k, nn = n * n;
     float *Brh = Bpl, *Brl = Bpl + nk, *Bih = Bpl + 2 * nk, *Bil = Bpl + 3 * nk;
-    const float *Arh = Apl, *Arl = Apl + n * n, *Aih = Apl + 2 * n * n, *Ail = Apl + 3 * n * n;
+    float *Bsh = Bpl + 4 * nk, *Bsl = Bpl + 5 * nk;
+    const float *Arh = Apl, *Arl = Apl + nn, *Aih = Apl + 2 * nn, *Ail = Apl + 3 * nn;
+    const float *Ash = Apl + 4 * nn, *Asl = Apl + 5 * nn;
     const int cs = bcplx ? 2 : 1;
     split_df32(B, n, k, n, cs, 0, Brh, Brl, st);
     if (bcplx) split_df32(B, n, k, n, 2, 1, Bih, Bil, st);
-    if (kCplx) {  // complex A, complex B
+    if (kCplx) {  // complex A, complex B (3M)
+      split_df32(B, n, k, n, 2, 2, Bsh, Bsl, st);
       gemm_df32(n, k, n, 1.0, Arh, Arl, n, Brh, Brl, n, 0.0, Out, n, 2, 0, st);
-      gemm_df32(n, k, n, -1.0, Aih, Ail, n, Bih, Bil, n, 1.0, Out, n, 2, 0, st);
-      gemm_df32(n, k, n, 1.0, Arh, Arl, n, Bih, Bil, n, 0.0, Out, n, 2, 1, st);
-      gemm_df32(n, k, n, 1.0, Aih, Ail, n, Brh, Brl, n, 1.0, Out, n, 2, 1, st);
+      gemm_df32(n, k, n, 1.0, Aih, Ail, n, Bih, Bil, n, 0.0, Tdf, n, 1, 0, st);
+      gemm_df32(n, k, n, 1.0, Ash, Asl, n, Bsh, Bsl, n, 0.0, Out, n, 2, 1, st);
+      combine_3m(Out, Tdf, n, k, st);
     } else if (bcplx) {  // real A, complex B
       gemm_df32(n, k, n, 1.0, Arh, Arl, n, Brh, Brl, n, 0.0, Out, n, 2, 0, st);
       gemm_df32(n, k, n, 1.0, Arh, Arl, n, Bih, Bil, n, 0.0, Out, n, 2, 1, st);
@@ -405,7 +430,7 @@ struct Solver {
         permute_out<c128, c128>(Y + nc * nm, nm, Yw, nm, n, m, perm, nc, true, false, st);
       }
     } else {
-      solve_lowp<S>(X, n, 0, m, false);
+      phase("c64 solves", [&] { solve_lowp<S>(X, n, 0, m, false); });
       if (!refine_now) {
         accumulate_filter<S>(Xf, n, Y, n, m, nc, d_w, st);
         return;
@@ -415,39 +440,45 @@ struct Solver {
       const double rtol = o.refine_tol > 0 ? o.refine_tol : 16.0 * 2.220446049250313e-16 * std::sqrt((double)n);
       std::vector<double> en(2 * E), prev(E, -1.0);
       double worst_prev = -1.0;
+      // entries whose residual met the target drop out of later steps: their
+      // A*Y product is skipped and their residual set to zero
+      std::vector<int> active(E, 1);
       for (int step = 0; step < o.refine_max; ++step) {
         // R_e = X - (z_e I - A) Y_e, FP64-accurate (double-float A Y)
-        apply_A_df((const double*)Y, true, E * m, (double*)AY);
-        refine_residual<S>(Yw, X, n, Y, AY, n, m, E, d_ze, st);
+        for (int e0 = 0; e0 < E;) {
+          if (!active[e0]) { ++e0; continue; }
+          int e1 = e0;
+          while (e1 < E && active[e1]) ++e1;
+          phase("refine A*Y (df32)", [&] { apply_A_df((const double*)(Y + e0 * nm), true, (e1 - e0) * m, (double*)(AY + e0 * nm)); });
+          e0 = e1;
+        }
+        to_dev(ctx, d_act, active.data(), E);
+        refine_residual<S>(Yw, X, n, Y, AY, n, m, E, d_ze, d_act, st);
         entry_norms2(Yw, Y, n, m, E, d_en, st);
         to_host(ctx, en.data(), d_en, 2 * E);
         bool conv = true, stagnant = step > 0;
-        if (std::getenv("FEAST_LOG")) {
-          double worst = 0.0;
-          for (int e = 0; e < E; ++e) {
-            const c128 ze = e < nc ? z[e] : conj(z[e - nc]);
-            worst = std::max(worst, std::sqrt(en[2 * e]) / ((anorm + std::sqrt(abs2(ze))) * std::sqrt(en[2 * e + 1])));
-          }
-          fprintf(stderr, "[feast] refine step %d: max relative residual %.3e (target %.3e)\n", step, worst, rtol);
-        }
+        double worst = 0.0;
         for (int e = 0; e < E; ++e) {
+          if (!active[e]) continue;
           const c128 ze = e < nc ? z[e] : conj(z[e - nc]);
           const double rn = std::sqrt(en[2 * e]), yn = std::sqrt(en[2 * e + 1]);
-          const bool ok = rn <= rtol * (anorm + std::sqrt(abs2(ze))) * yn;
-          if (!ok) {
+          const double rel = rn / ((anorm + std::sqrt(abs2(ze))) * yn);
+          if (rel <= rtol) {
+            active[e] = 0;
+          } else {
             conv = false;
+            worst = std::max(worst, rel);
             if (prev[e] < 0 || rn < 0.5 * prev[e]) stagnant = false;
           }
           prev[e] = rn;
         }
+        if (std::getenv("FEAST_LOG"))
+          fprintf(stderr, "[feast] refine step %d: worst active relative residual %.3e (target %.3e), active %d/%d\n",
+                  step, worst, rtol, (int)std::count(active.begin(), active.end(), 1), E);
         if (conv || stagnant) break;
-        // relative residual of the worst entry and its contraction per step
-        double worst = 0.0;
-        for (int e = 0; e < E; ++e) {
-          const c128 ze = e < nc ? z[e] : conj(z[e - nc]);
-          worst = std::max(worst, std::sqrt(en[2 * e]) / ((anorm + std::sqrt(abs2(ze))) * std::sqrt(en[2 * e + 1])));
-        }
-        solve_lowp<c128>(Yw, n, nm, m, true);
+        // entries that met the target in this step still take this correction
+        // (their residual is fresh); earlier ones have R = 0
+        phase("c64 solves", [&] { solve_lowp<c128>(Yw, n, nm, m, true); });
         ++refine_steps;
         // when the observed contraction already puts the next residual well
         // below the target, the correction just applied finishes the refinement
@@ -514,14 +545,16 @@ struct Solver {
   }
   // Cholesky-QR twice; Gram route on breakdown.  Returns the rank (0 = failure).
   int64_t orthonormalize(const S* X, int64_t nr, int64_t k, S* Qout, S* tmp) {
-    if (cholqr_once(X, nr, k, tmp) && cholqr_once(tmp, nr, k, Qout)) return k;
+    bool ok = false;
+    phase("CholQR2", [&] { ok = cholqr_once(X, nr, k, tmp) && cholqr_once(tmp, nr, k, Qout); });
+    if (ok) return k;
     return gram_eig_orth(X, nr, k, Qout, tmp, 1e-12);
   }
 
   // ---- Rayleigh-Ritz ----
   // W = A Q, A' = Q^H W (ld kmax) for the first k columns of Qb
   void rr_project(int64_t k) {
-    apply_A(Qb, k, Wb);
+    phase("RR A*Q", [&] { apply_A(Qb, k, Wb); });
     mm_reduce(k, k, n, Qb, n, OP_C, Wb, n, OP_N, Ar0, kmax);
     hermitize<S>(Ar0, k, kmax, st);
   }
@@ -529,7 +562,7 @@ struct Solver {
   void rr_solve(int64_t k) {
     copy_matrix<S>(Ar, k, Ar0, kmax, k, k, st);
     std::vector<double> ev;
-    eig(Ar, k, ev);
+    phase("Jacobi (RR)", [&] { eig(Ar, k, ev); });
     std::vector<int> ord(k);
     std::iota(ord.begin(), ord.end(), 0);
     std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return ev[a] < ev[b]; });
@@ -971,6 +1004,11 @@ int solve_t(feast_ctx* ctx, const S* A, int64_t n, int64_t lda, double lmin, dou
   for (size_t i = 0; i < out.hist.size() && i < 128; ++i) st.history[i] = out.hist[i];
   ctx->last = st;
   if (stats) *stats = st;
+  if (sv.profile) {
+    fprintf(stderr, "[feast] phases (ms):");
+    for (auto& p : sv.phases) fprintf(stderr, " %s=%.1f", p.first, p.second);
+    fprintf(stderr, " factor=%.1f total=%.1f\n", st.factor_ms, st.total_ms);
+  }
   return out.status;
 }
 

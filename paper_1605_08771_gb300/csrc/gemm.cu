@@ -244,7 +244,7 @@ gemm_df32_kernel(int64_t M, int64_t N, int64_t K, double alpha, const float* __r
         for (int j = 0; j < DF_TN; ++j) df_mac(a_h[i], a_l[i], b_h[j], b_l[j], s[i][j], x[i][j]);
     }
     __syncthreads();
-    if (tile & 1) {
+    if ((tile & 3) == 3) {  // flush every 64 k-steps
 #pragma unroll
       for (int i = 0; i < DF_TM; ++i)
 #pragma unroll
@@ -266,13 +266,23 @@ gemm_df32_kernel(int64_t M, int64_t N, int64_t K, double alpha, const float* __r
   }
 }
 
+__global__ void combine_3m_kernel(double* C, const double* T2, int64_t total) {
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const double t1 = C[2 * idx], t3 = C[2 * idx + 1], t2 = T2[idx];
+    C[2 * idx] = t1 - t2;
+    C[2 * idx + 1] = (t3 - t1) - t2;
+  }
+}
+
 __global__ void split_df32_kernel(const double* src, int64_t rows, int64_t cols, int64_t lds, int ss, int so,
                                   float* hi, float* lo) {
   const int64_t total = rows * cols;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = idx % rows, j = idx / rows;
-    const double v = src[(i + j * lds) * ss + so];
+    const double* e = src + (i + j * lds) * ss;
+    const double v = (so == 2) ? e[0] + e[1] : e[so];
     const float h = (float)v;
     hi[idx] = h;
     lo[idx] = (float)(v - (double)h);
@@ -344,6 +354,14 @@ void gemm_df32(int64_t M, int64_t N, int64_t K, double alpha, const float* Ahi, 
     tm.macs += (double)M * (double)N * (double)K;
     tm.launches += 1;
   }
+}
+
+void combine_3m(double* C, const double* T2, int64_t n, int64_t k, cudaStream_t s) {
+  const int64_t total = n * k;
+  if (total <= 0) return;
+  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(total, 256), 16384));
+  combine_3m_kernel<<<g, 256, 0, s>>>(C, T2, total);
+  FEAST_LAUNCH_CHECK();
 }
 
 void split_df32(const double* src, int64_t rows, int64_t cols, int64_t lds, int ss, int so, float* hi, float* lo,

@@ -58,15 +58,20 @@ namespace feast {
 // column-major, op N.  Each hi*hi product is made exact with an FMA
 // (TwoProd), each addition to the running FP32 sum exact with TwoSum; the
 // error terms and the hi*lo cross products go to an FP32 accumulator that is
-// flushed into an FP64 accumulator every 32 k-steps.  Relative accuracy is
+// flushed into an FP64 accumulator every 64 k-steps.  Relative accuracy is
 // ~1e-15 of sum |a||b| at a small fraction of the FP64 cost on sm_103.
 void gemm_df32(int64_t M, int64_t N, int64_t K, double alpha,
                const float* Ahi, const float* Alo, int64_t lda,
                const float* Bhi, const float* Blo, int64_t ldb,
                double beta, double* C, int64_t ldc, int cs, int co, cudaStream_t s);
 
+// 3M complex combination: C_re = T1 - T2, C_im = T3 - T1 - T2 where T1 and T3
+// already sit in C (re, im) and T2 in a separate real array (n x k, ld n).
+void combine_3m(double* C, const double* T2, int64_t n, int64_t k, cudaStream_t s);
+
 // Split FP64 values into hi/lo float planes: src element (i, j) at
-// src[(i + j*lds)*ss + so]; planes are dense rows x cols (ld = rows).
+// src[(i + j*lds)*ss + so] (so = 2 with ss = 2: the sum Re + Im of a complex
+// element); planes are dense rows x cols (ld = rows).
 void split_df32(const double* src, int64_t rows, int64_t cols, int64_t lds, int ss, int so,
                 float* hi, float* lo, cudaStream_t s);
 
