@@ -16,6 +16,8 @@ struct CoopWork {
   double* partial;     // [>= 2*num_sms] partial sums
   unsigned* rotcount;  // [kMaxSweeps]
   void* rot;           // rotation parameters, >= k/2+1 entries of (c, s, e)
+  void* hbuf;          // optional k x k second buffer (ld k): when set, Jacobi runs
+                       // one grid barrier per round (double-buffered matrix)
 };
 constexpr int kMaxSweeps = 64;
 size_t coop_work_bytes(int64_t kmax, int num_sms);

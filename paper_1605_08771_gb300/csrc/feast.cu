@@ -251,6 +251,7 @@ struct Solver {
     to_dev(ctx, d_w, w.data(), nc);
     to_dev(ctx, d_ze, ze.data(), E);
     cw = coop_work_carve(ctx->arena.alloc(coop_work_bytes(kmax, ctx->num_sms)), kmax, ctx->num_sms);
+    cw.hbuf = dalloc<S>(ctx, kmax * kmax);
     d_flag = dalloc<int>(ctx, 4);
     d_en = dalloc<double>(ctx, 2 * E);
     d_act = dalloc<int>(ctx, E);
@@ -1251,6 +1252,7 @@ int feast_jacobi_eigh(feast_ctx* ctx, int dtype, int64_t k, const void* H, doubl
       Solver<S> sv(ctx, nullptr, 1, 1, -1.0, 1.0, 1, o);
       sv.kmax = k;
       sv.cw = coop_work_carve(ctx->arena.alloc(coop_work_bytes(k, ctx->num_sms)), k, ctx->num_sms);
+      sv.cw.hbuf = dalloc<S>(ctx, k * k);
       sv.Vk = dalloc<S>(ctx, k * k);
       sv.Cs = dalloc<S>(ctx, k * k);
       sv.d_lam = dalloc<double>(ctx, k);

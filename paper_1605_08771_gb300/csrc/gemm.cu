@@ -226,7 +226,8 @@ gemm_df32_kernel(int64_t M, int64_t N, int64_t K, double alpha, const float* __r
       sBl[kk][nn] = lo;
     }
     __syncthreads();
-#pragma unroll
+    // partial unroll keeps the loop body within the instruction cache
+#pragma unroll 4
     for (int kk = 0; kk < DF_BK; ++kk) {
       const float4 ah = *reinterpret_cast<const float4*>(&sAh[kk][tm * DF_TM]);
       const float4 al = *reinterpret_cast<const float4*>(&sAl[kk][tm * DF_TM]);
