@@ -271,16 +271,18 @@ __global__ void form_shifted_kernel(F* M, int64_t n, int64_t ld, int64_t stride,
   }
 }
 
-// Triangular block solve on a kPanel x kPanel diagonal block, warp per RHS
-// column.  mode 0: L (unit lower, stored), 1: U^H (lower, from the stored U),
-// 2: U (upper, stored), 3: L^H (unit upper, from the stored L).
-template <typename F>
+// Triangular solve on a TB x TB diagonal block, warp per right-hand-side
+// column, TB/32 rows per lane.  mode 0: L (unit lower, stored), 1: U^H
+// (lower, from the stored U), 2: U (upper, stored), 3: L^H (unit upper, from
+// the stored L).
+template <typename F, int TB>
 __global__ void __launch_bounds__(256)
 trsm_diag_kernel(const F* M, int64_t ld, int64_t stride, F* Y, int64_t n, int64_t m,
                  int64_t ystride, int64_t r0, int bs, int mode) {
+  constexpr int R = TB / 32;
   const int b = blockIdx.y;
   const F* Mb = M + (int64_t)b * stride;
-  __shared__ F T[kPanel][kPanel + 1];
+  __shared__ F T[TB][TB + 1];
   for (int l = threadIdx.x; l < bs * bs; l += blockDim.x) {
     if (mode == 0 || mode == 2) {
       int i = l % bs, j = l / bs;
@@ -295,22 +297,57 @@ trsm_diag_kernel(const F* M, int64_t ld, int64_t stride, F* Y, int64_t n, int64_
   const int64_t cidx = (int64_t)blockIdx.x * 8 + wp;
   if (cidx >= m) return;
   F* y = Y + (int64_t)b * ystride + cidx * n + r0;
-  F x = lane < bs ? y[lane] : num<F>::zero();
+  F x[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) x[r] = (lane + 32 * r < bs) ? y[lane + 32 * r] : num<F>::zero();
   if (mode <= 1) {
     for (int j = 0; j < bs; ++j) {
-      if (mode == 1 && lane == j) x = x * recip(T[j][j]);
-      F xj = shfl(x, j);
-      if (lane > j && lane < bs) x = x - T[lane][j] * xj;
+      const int jl = j & 31, jr = j >> 5;
+      if (mode == 1 && lane == jl) {
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+          if (r == jr) x[r] = x[r] * recip(T[j][j]);
+      }
+      F xs = num<F>::zero();
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (r == jr) xs = x[r];
+      const F xj = shfl(xs, jl);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int row = lane + 32 * r;
+        if (row > j && row < bs) x[r] = x[r] - T[row][j] * xj;
+      }
     }
   } else {
     for (int j = bs - 1; j >= 0; --j) {
-      if (mode == 2 && lane == j) x = x * recip(T[j][j]);
-      F xj = shfl(x, j);
-      if (lane < j) x = x - T[lane][j] * xj;
+      const int jl = j & 31, jr = j >> 5;
+      if (mode == 2 && lane == jl) {
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+          if (r == jr) x[r] = x[r] * recip(T[j][j]);
+      }
+      F xs = num<F>::zero();
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (r == jr) xs = x[r];
+      const F xj = shfl(xs, jl);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int row = lane + 32 * r;
+        if (row < j) x[r] = x[r] - T[row][j] * xj;
+      }
     }
   }
-  if (lane < bs) y[lane] = x;
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    if (lane + 32 * r < bs) y[lane + 32 * r] = x[r];
 }
+
+// solve block rows: 64 for complex-FP32 factors, 32 for complex-FP64 (whose
+// 64 x 64 shared tile would exceed the static shared-memory limit)
+template <typename F> struct SolveBlock { static constexpr int value = 64; };
+template <> struct SolveBlock<c128> { static constexpr int value = 32; };
 
 template <typename F, typename TB>
 __global__ void permute_in_kernel(F* Y, int64_t ystride, const TB* B, int64_t ldb, int64_t bstride, int64_t n, int64_t m,
@@ -441,14 +478,15 @@ template <typename F>
 void lu_solve_batched(const F* M, int64_t n, int64_t ld, int64_t stride, int nodes,
                       F* Y, int64_t m, int64_t ystride, bool adjoint, cudaStream_t s) {
   if (m <= 0) return;
-  const int64_t nblk = cdiv(n, kPanel);
+  constexpr int TBK = SolveBlock<F>::value;
+  const int64_t nblk = cdiv(n, TBK);
   dim3 gd((unsigned)cdiv(m, 8), nodes);
   // forward substitution with L (normal) or U^H (adjoint)
   for (int64_t bi = 0; bi < nblk; ++bi) {
-    const int64_t r0 = bi * kPanel;
-    const int bs = (int)std::min<int64_t>(kPanel, n - r0);
+    const int64_t r0 = bi * TBK;
+    const int bs = (int)std::min<int64_t>(TBK, n - r0);
     const int64_t r1 = r0 + bs;
-    trsm_diag_kernel<F><<<gd, 256, 0, s>>>(M, ld, stride, Y, n, m, ystride, r0, bs, adjoint ? 1 : 0);
+    trsm_diag_kernel<F, TBK><<<gd, 256, 0, s>>>(M, ld, stride, Y, n, m, ystride, r0, bs, adjoint ? 1 : 0);
     FEAST_LAUNCH_CHECK();
     if (r1 < n) {
       GemmArgs g{};
@@ -464,9 +502,9 @@ void lu_solve_batched(const F* M, int64_t n, int64_t ld, int64_t stride, int nod
   }
   // back substitution with U (normal) or L^H (adjoint)
   for (int64_t bi = nblk - 1; bi >= 0; --bi) {
-    const int64_t r0 = bi * kPanel;
-    const int bs = (int)std::min<int64_t>(kPanel, n - r0);
-    trsm_diag_kernel<F><<<gd, 256, 0, s>>>(M, ld, stride, Y, n, m, ystride, r0, bs, adjoint ? 3 : 2);
+    const int64_t r0 = bi * TBK;
+    const int bs = (int)std::min<int64_t>(TBK, n - r0);
+    trsm_diag_kernel<F, TBK><<<gd, 256, 0, s>>>(M, ld, stride, Y, n, m, ystride, r0, bs, adjoint ? 3 : 2);
     FEAST_LAUNCH_CHECK();
     if (r0 > 0) {
       GemmArgs g{};
