@@ -245,137 +245,6 @@ jacobi_kernel(S* H, int64_t k, int64_t ld, S* V, int64_t ldv, double tol, CoopWo
   if (gt == 0) w.info[1] = sweeps;
 }
 
-// Single-barrier variant: the matrix is double-buffered (read Hc, write Hn,
-// swap every round); every 2x2 block task recomputes the two rotations it
-// needs from Hc's diagonal blocks (bitwise the same values every task sees),
-// so the rotations need no separate phase.  Same rounds, thresholds and
-// rotation formulas as jacobi_kernel.
-template <typename S>
-__device__ __forceinline__ void jacobi_rot(const S* H, int64_t ld, int64_t k, int p, int q, double thr, double& c,
-                                           double& s, S& e, int& on) {
-  c = 1.0; s = 0.0; e = one<S>(); on = 0;
-  if (q >= k) return;
-  const S apq = ldcg(&H[p + (int64_t)q * ld]);
-  const double g = sqrt(abs2(apq));
-  if (!(g > thr)) return;
-  const double app = real_part(ldcg(&H[p + (int64_t)p * ld]));
-  const double aqq = real_part(ldcg(&H[q + (int64_t)q * ld]));
-  e = conj(apq) * (1.0 / g);
-  const double tau = (aqq - app) / (2.0 * g);
-  const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + hypot(1.0, tau));
-  c = 1.0 / hypot(1.0, t);
-  s = t * c;
-  on = 1;
-}
-
-__device__ __forceinline__ void rr_pair(int64_t r, int64_t i, int64_t m1, int& p, int& q) {
-  int64_t a, b;
-  if (i == 0) { a = r % m1; b = m1; }
-  else { a = (r + i) % m1; b = ((r - i) % m1 + m1) % m1; }
-  p = (int)(a < b ? a : b);
-  q = (int)(a < b ? b : a);
-}
-
-template <typename S>
-__global__ void __launch_bounds__(256)
-jacobi1_kernel(S* H, S* H2, int64_t k, int64_t ld, S* V, int64_t ldv, double tol, CoopWork w, int P, int max_sweeps) {
-  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t NT = (int64_t)P * blockDim.x;
-  unsigned nb = 0;
-  const int64_t kk = k + (k & 1), np = kk / 2, m1 = kk - 1;
-  // H2 is k x k with leading dimension k; H has leading dimension ld
-  double part = 0.0;
-  for (int64_t idx = gt; idx < k * k; idx += NT) {
-    const int64_t i = idx % k, j = idx / k;
-    V[i + j * ldv] = (i == j) ? one<S>() : num<S>::zero();
-    part += abs2(H[i + j * ld]);
-  }
-  part = block_sum(part);
-  if (threadIdx.x == 0) w.partial[blockIdx.x] = part;
-  if (!group_barrier(w.counter, (++nb) * (unsigned)P, w.status)) return;
-  double fro2 = 0.0;
-  for (int q = 0; q < P; ++q) fro2 += __ldcg(&w.partial[q]);
-  const double thr = tol * sqrt(fro2);
-
-  S* Hc = H;
-  S* Hn = H2;
-  int64_t ldc = ld, ldn = k;
-  int sweeps = 0;
-  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    for (int64_t r = 0; r < m1; ++r) {
-      const int64_t nblk = np * np;
-      for (int64_t task = gt; task < nblk + k * np; task += NT) {
-        if (task < nblk) {
-          const int64_t I = task % np, J = task / np;
-          int pI, qI, pJ, qJ, onI, onJ;
-          double cI, sI, cJ, sJ;
-          S eI, eJ;
-          rr_pair(r, I, m1, pI, qI);
-          rr_pair(r, J, m1, pJ, qJ);
-          jacobi_rot(Hc, ldc, k, pI, qI, thr, cI, sI, eI, onI);
-          if (J == I) { cJ = cI; sJ = sI; eJ = eI; onJ = onI; }
-          else jacobi_rot(Hc, ldc, k, pJ, qJ, thr, cJ, sJ, eJ, onJ);
-          if (I == J && onI) atomicAdd(&w.rotcount[sweep], 1u);
-          const bool vqI = qI < k, vqJ = qJ < k;
-          S b00 = ldcg(&Hc[pI + (int64_t)pJ * ldc]);
-          S b01 = vqJ ? ldcg(&Hc[pI + (int64_t)qJ * ldc]) : num<S>::zero();
-          S b10 = vqI ? ldcg(&Hc[qI + (int64_t)pJ * ldc]) : num<S>::zero();
-          S b11 = (vqI && vqJ) ? ldcg(&Hc[qI + (int64_t)qJ * ldc]) : num<S>::zero();
-          if (onJ) {
-            const S se = eJ * sJ, ce = eJ * cJ;
-            S n00 = b00 * cJ - b01 * se, n01 = b00 * sJ + b01 * ce;
-            S n10 = b10 * cJ - b11 * se, n11 = b10 * sJ + b11 * ce;
-            b00 = n00; b01 = n01; b10 = n10; b11 = n11;
-          }
-          if (onI) {
-            const S ec = conj(eI);
-            const S sec = ec * sI, cec = ec * cI;
-            S n00 = b00 * cI - b10 * sec, n10 = b00 * sI + b10 * cec;
-            S n01 = b01 * cI - b11 * sec, n11 = b01 * sI + b11 * cec;
-            b00 = n00; b01 = n01; b10 = n10; b11 = n11;
-          }
-          if (I == J && onI) {
-            b01 = num<S>::zero();
-            b10 = num<S>::zero();
-            b00 = cvt<S>(real_part(b00));
-            b11 = cvt<S>(real_part(b11));
-          }
-          Hn[pI + (int64_t)pJ * ldn] = b00;
-          if (vqJ) Hn[pI + (int64_t)qJ * ldn] = b01;
-          if (vqI) Hn[qI + (int64_t)pJ * ldn] = b10;
-          if (vqI && vqJ) Hn[qI + (int64_t)qJ * ldn] = b11;
-        } else {
-          const int64_t tv = task - nblk;
-          const int64_t row = tv % k, J = tv / k;
-          int pJ, qJ, onJ;
-          double cJ, sJ;
-          S eJ;
-          rr_pair(r, J, m1, pJ, qJ);
-          jacobi_rot(Hc, ldc, k, pJ, qJ, thr, cJ, sJ, eJ, onJ);
-          if (!onJ) continue;
-          S* vp = &V[row + (int64_t)pJ * ldv];
-          S* vq = &V[row + (int64_t)qJ * ldv];
-          const S a = ldcg(vp), b = ldcg(vq);  // written by other CTAs in earlier rounds
-          *vp = a * cJ - b * (eJ * sJ);
-          *vq = a * sJ + b * (eJ * cJ);
-        }
-      }
-      if (!group_barrier(w.counter, (++nb) * (unsigned)P, w.status)) return;
-      S* t = Hc; Hc = Hn; Hn = t;
-      const int64_t tl = ldc; ldc = ldn; ldn = tl;
-    }
-    sweeps = sweep + 1;
-    if (__ldcg(&w.rotcount[sweep]) == 0u) break;
-  }
-  if (Hc != H) {  // the last round wrote the second buffer: copy back
-    for (int64_t idx = gt; idx < k * k; idx += NT) {
-      const int64_t i = idx % k, j = idx / k;
-      H[i + j * ld] = ldcg(&Hc[i + j * ldc]);
-    }
-  }
-  if (gt == 0) w.info[1] = sweeps;
-}
-
 // ---------------------------------------------------------------------------
 template <typename S>
 __global__ void get_diag_kernel(const S* H, int64_t k, int64_t ld, double* d) {
@@ -527,6 +396,14 @@ __global__ void copy_matrix_kernel(S* dst, int64_t ldd, const S* src, int64_t ld
 }
 
 template <typename S>
+__global__ void set_diag_kernel(S* X, int64_t k, int64_t ld, const double* d) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < k * k; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t % k, c = t / k;
+    X[i + c * ld] = (i == c) ? cvt<S>(d[i]) : num<S>::zero();
+  }
+}
+
+template <typename S>
 __global__ void set_identity_kernel(S* X, int64_t k, int64_t ld) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < k * k; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = t % k, c = t / k;
@@ -561,7 +438,6 @@ CoopWork coop_work_carve(void* base, int64_t kmax, int num_sms) {
   w.partial = (double*)p; p += ((sizeof(double) * 2 * (size_t)std::max(num_sms, 1024) + 255) & ~size_t(255));
   w.rotcount = (unsigned*)p; p += ((sizeof(unsigned) * kMaxSweeps + 255) & ~size_t(255));
   w.rot = p;
-  w.hbuf = nullptr;
   (void)kmax;
   return w;
 }
@@ -605,13 +481,6 @@ void jacobi_eigh(S* H, int64_t k, int64_t ld, S* V, int64_t ldv, double tol, con
   P = std::max(1, std::min(P, num_sms));
   int maxs = kMaxSweeps;
   CoopWork wl = w;
-  if (w.hbuf) {
-    S* H2 = (S*)w.hbuf;
-    void* args[] = {&H, &H2, &k, &ld, &V, &ldv, &tol, &wl, &P, &maxs};
-    FEAST_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)jacobi1_kernel<S>, dim3(P), dim3(256), args, 0, s));
-    note_launch();
-    return;
-  }
   void* args[] = {&H, &k, &ld, &V, &ldv, &tol, &wl, &P, &maxs};
   FEAST_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)jacobi_kernel<S>, dim3(P), dim3(256), args, 0, s));
   note_launch();
@@ -699,6 +568,11 @@ template <typename S> void copy_matrix(S* dst, int64_t ldd, const S* src, int64_
   FEAST_LAUNCH_CHECK();
 }
 
+template <typename S> void set_diag(S* X, int64_t k, int64_t ld, const double* d, cudaStream_t s) {
+  set_diag_kernel<S><<<grid1d(k * k), 256, 0, s>>>(X, k, ld, d);
+  FEAST_LAUNCH_CHECK();
+}
+
 template <typename S> void set_identity(S* X, int64_t k, int64_t ld, cudaStream_t s) {
   set_identity_kernel<S><<<grid1d(k * k), 256, 0, s>>>(X, k, ld);
   FEAST_LAUNCH_CHECK();
@@ -731,6 +605,7 @@ template <typename S> void check_finite(const S* X, int64_t n, int64_t m, int64_
   template void random_normal<S>(S*, int64_t, int64_t, int64_t, unsigned long long, cudaStream_t);         \
   template void copy_matrix<S>(S*, int64_t, const S*, int64_t, int64_t, int64_t, cudaStream_t);            \
   template void set_identity<S>(S*, int64_t, int64_t, cudaStream_t);                                       \
+  template void set_diag<S>(S*, int64_t, int64_t, const double*, cudaStream_t);                            \
   template void check_finite<S>(const S*, int64_t, int64_t, int64_t, int*, cudaStream_t);
 
 INST_S(double)

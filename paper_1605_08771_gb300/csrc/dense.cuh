@@ -16,8 +16,6 @@ struct CoopWork {
   double* partial;     // [>= 2*num_sms] partial sums
   unsigned* rotcount;  // [kMaxSweeps]
   void* rot;           // rotation parameters, >= k/2+1 entries of (c, s, e)
-  void* hbuf;          // optional k x k second buffer (ld k): when set, Jacobi runs
-                       // one grid barrier per round (double-buffered matrix)
 };
 constexpr int kMaxSweeps = 64;
 size_t coop_work_bytes(int64_t kmax, int num_sms);
@@ -94,6 +92,8 @@ template <typename S> void random_normal(S* X, int64_t n, int64_t m, int64_t ld,
 template <typename S> void copy_matrix(S* dst, int64_t ldd, const S* src, int64_t lds, int64_t n, int64_t m,
                                        cudaStream_t s);
 template <typename S> void set_identity(S* X, int64_t k, int64_t ld, cudaStream_t s);
+// X = diag(d) (k x k)
+template <typename S> void set_diag(S* X, int64_t k, int64_t ld, const double* d, cudaStream_t s);
 
 // any non-finite entry in the n x m matrix -> *flag = 1
 template <typename S> void check_finite(const S* X, int64_t n, int64_t m, int64_t ld, int* flag, cudaStream_t s);

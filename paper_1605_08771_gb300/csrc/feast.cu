@@ -251,7 +251,6 @@ struct Solver {
     to_dev(ctx, d_w, w.data(), nc);
     to_dev(ctx, d_ze, ze.data(), E);
     cw = coop_work_carve(ctx->arena.alloc(coop_work_bytes(kmax, ctx->num_sms)), kmax, ctx->num_sms);
-    cw.hbuf = dalloc<S>(ctx, kmax * kmax);
     d_flag = dalloc<int>(ctx, 4);
     d_en = dalloc<double>(ctx, 2 * E);
     d_act = dalloc<int>(ctx, E);
@@ -859,6 +858,13 @@ struct Solver {
           to_dev(ctx, d_scale, sc.data(), ms);
           to_dev(ctx, d_idx, iden.data(), ms);
           scale_cols<S>(R, n, ms, n, d_scale, st);
+          // continue in the Ritz basis of this pass (same span): Q <- X, W <- A X,
+          // A' <- diag(lambda), so the next Jacobi starts from a matrix whose
+          // leading block is already diagonal
+          copy_matrix<S>(Qb, n, Xr, n, n, k, st);
+          copy_matrix<S>(Wb, n, AXr, n, n, k, st);
+          to_dev(ctx, d_lam, lam.data(), k);
+          set_diag<S>(Ar0, k, kmax, d_lam, st);
           for (int rep = 0; rep < 2; ++rep) {
             mm_reduce(k, ms, n, Qb, n, OP_C, R, n, OP_N, Cs2, k);
             mm(n, ms, k, C1(-1.0), Qb, n, OP_N, Cs2, k, OP_N, C1(1.0), R, n);
@@ -1252,7 +1258,6 @@ int feast_jacobi_eigh(feast_ctx* ctx, int dtype, int64_t k, const void* H, doubl
       Solver<S> sv(ctx, nullptr, 1, 1, -1.0, 1.0, 1, o);
       sv.kmax = k;
       sv.cw = coop_work_carve(ctx->arena.alloc(coop_work_bytes(k, ctx->num_sms)), k, ctx->num_sms);
-      sv.cw.hbuf = dalloc<S>(ctx, k * k);
       sv.Vk = dalloc<S>(ctx, k * k);
       sv.Cs = dalloc<S>(ctx, k * k);
       sv.d_lam = dalloc<double>(ctx, k);

@@ -245,7 +245,7 @@ gemm_df32_kernel(int64_t M, int64_t N, int64_t K, double alpha, const float* __r
         for (int j = 0; j < DF_TN; ++j) df_mac(a_h[i], a_l[i], b_h[j], b_l[j], s[i][j], x[i][j]);
     }
     __syncthreads();
-    if ((tile & 3) == 3) {  // flush every 64 k-steps
+    if (tile & 1) {  // flush every 32 k-steps
 #pragma unroll
       for (int i = 0; i < DF_TM; ++i)
 #pragma unroll

@@ -58,7 +58,7 @@ namespace feast {
 // column-major, op N.  Each hi*hi product is made exact with an FMA
 // (TwoProd), each addition to the running FP32 sum exact with TwoSum; the
 // error terms and the hi*lo cross products go to an FP32 accumulator that is
-// flushed into an FP64 accumulator every 64 k-steps.  Relative accuracy is
+// flushed into an FP64 accumulator every 32 k-steps.  Relative accuracy is
 // ~1e-15 of sum |a||b| at a small fraction of the FP64 cost on sm_103.
 void gemm_df32(int64_t M, int64_t N, int64_t K, double alpha,
                const float* Ahi, const float* Alo, int64_t lda,
