@@ -15,6 +15,7 @@
 //   3. A22 -= L21 U12 with the batched GEMM.
 // The pivot choice is the first row of largest |m_ik|^2, as in the oracle.
 #include "factor.cuh"
+#include "tc_update.cuh"
 
 #include <algorithm>
 #include <climits>
@@ -414,6 +415,7 @@ PanelWork panel_work_carve(void* base, int nodes, int pmax, size_t eb) {
   w.swap_dst = (int*)take(sizeof(int) * nodes * 2 * kPanel);
   w.swap_cnt = (int*)take(sizeof(int) * nodes);
   w.pmax = pmax;
+  w.tc_planes = nullptr;
   return w;
 }
 
@@ -458,6 +460,12 @@ void lu_factor_batched(F* M, int64_t n, int64_t ld, int64_t stride, int nodes,
     }
     const int64_t r1 = k0 + jb;
     if (r1 < n) {
+      if constexpr (std::is_same<F, c64>::value) {
+        if (w.tc_planes) {  // complex-FP32 factors: tcgen05 3xTF32 update
+          tc_trailing_update(M, n, ld, stride, nodes, k0, jb, w.tc_planes, w.status, s);
+          continue;
+        }
+      }
       GemmArgs g{};
       g.M = n - r1; g.N = n - r1; g.K = jb;
       g.A = M + r1 + k0 * ld; g.lda = ld; g.strideA = stride; g.opA = OP_N;

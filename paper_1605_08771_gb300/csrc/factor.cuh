@@ -25,6 +25,7 @@ struct PanelWork {
   int* swap_dst;        // [nodes][2*kPanel]
   int* swap_cnt;        // [nodes]
   int pmax;
+  void* tc_planes;      // complex-FP32 factors: scratch of the tensor-core trailing update
 };
 
 size_t panel_work_bytes(int nodes, int pmax, size_t elem_bytes);

@@ -19,6 +19,7 @@
 #include "dense.cuh"
 #include "factor.cuh"
 #include "gemm.cuh"
+#include "tc_update.cuh"
 
 using namespace feast;
 
@@ -262,6 +263,7 @@ struct Solver {
     perm = dalloc<int32_t>(ctx, (int64_t)nc * n);
     const int pmax = std::max(1, ctx->num_sms * 8);
     pw = panel_work_carve(ctx->arena.alloc(panel_work_bytes(nc, pmax, eb)), nc, pmax, eb);
+    if (o.prec == FEAST_PREC_MIXED) pw.tc_planes = ctx->arena.alloc(tc_update_planes_bytes(n, nc));
   }
   void alloc_filter(int64_t m) {
     const int64_t nm = n * m;
@@ -1171,6 +1173,7 @@ int feast_shifted_lu(feast_ctx* ctx, const void* A, int dtype, int64_t n, int64_
     const size_t eb = prec == FEAST_PREC_F64 ? sizeof(c128) : sizeof(c64);
     const int pmax = std::max(1, ctx->num_sms * 8);
     PanelWork pw = panel_work_carve(ctx->arena.alloc(panel_work_bytes(nz, pmax, eb)), nz, pmax, eb);
+    if (prec == FEAST_PREC_MIXED) pw.tc_planes = ctx->arena.alloc(tc_update_planes_bytes(n, nz));
     c128* dz = dalloc<c128>(ctx, nz);
     to_dev(ctx, dz, (const c128*)z, nz);
     int32_t* ipiv = dalloc<int32_t>(ctx, (int64_t)nz * n);

@@ -1,0 +1,357 @@
+// Tensor-core (tcgen05) trailing update of the complex-FP32 shifted LU:
+//     A22 -= L21 U12          for every quadrature node
+// on the 5th-generation tensor cores of sm_103a.
+//
+// Complex products become one real GEMM through the 2x2 real embedding with
+// interleaved rows: row 2i of the real left operand holds [Re L_i, -Im L_i],
+// row 2i+1 holds [Im L_i, Re L_i], and the right operand is [Re U; Im U], so
+// real row 2i of the product is Re(L U)_i and row 2i+1 is Im(L U)_i -- the
+// interleaved complex layout of A22 itself.  Each FP32 operand is split into
+// a TF32 head and a TF32 tail, hi = rna(a), lo = rna(a - hi), so that
+// |a - hi - lo| <= 2^-24 |a|; three TF32 products hi*hi + hi*lo + lo*hi
+// accumulate in FP32 in tensor memory (3xTF32, Ootomo & Yokota), which keeps
+// the factors FP32-accurate, so the FP64 refinement still contracts by the
+// same factor per step as with FP32 arithmetic.
+//
+// Kernel: one 128 x 128 output tile per CTA, four warps.  Thread 0 issues the
+// TMA loads of the 128B-swizzled K-major operand tiles, thread 32 issues the
+// tcgen05.mma instructions (M = 128, N = 128, K = 8) into a 128-column TMEM
+// accumulator, and all four warps read the accumulator back with tcgen05.ld
+// for the epilogue A22 -= D.  Every mbarrier wait is bounded by a wall-clock
+// limit; on expiry the kernel records the failure, lets the issued MMAs
+// complete, frees its TMEM and skips the stores.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "factor.cuh"
+#include "tc_update.cuh"
+
+namespace feast {
+
+namespace {
+
+constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 32;  // BK fp32 = 128 bytes = one swizzle row
+constexpr int TC_STAGES = 2;
+constexpr int TC_TILE_BYTES = TC_BM * TC_BK * 4;     // 16 KB per operand tile (BN == BM)
+constexpr int TC_STAGE_BYTES = 4 * TC_TILE_BYTES;    // A_hi, A_lo, B_hi, B_lo
+constexpr int TC_SMEM_BYTES = TC_STAGES * TC_STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int TC_TMEM_COLS = 128;
+constexpr unsigned long long kTcWaitNs = 2000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const unsigned long long t0 = globaltimer_ns();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (globaltimer_ns() - t0 > kTcWaitNs) return false;
+  }
+}
+
+// SWIZZLE_128B K-major shared-memory matrix descriptor (sm_100 family):
+// start address >> 4 in bits 0-13, leading offset (unused for swizzled
+// K-major) 1, stride offset 1024 B (one 8-row swizzle atom) >> 4 in bits
+// 32-45, descriptor version 1 in bits 46-47, layout SWIZZLE_128B (2) in 61-63.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor, kind::tf32: D = F32 (bits 4-5 = 1), A = B = TF32
+// (bits 7-9, 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 in 17-22,
+// M >> 4 in 24-28.
+constexpr uint32_t kIdescTf32 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
+                                ((uint32_t)(TC_BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t da, uint64_t db, uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+      :
+      : "r"(tmem), "l"(da), "l"(db), "r"(kIdescTf32), "r"(accum)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      :
+      : "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+__global__ void __launch_bounds__(128, 1)
+tc_update_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+                 const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, c64* M,
+                 int64_t ld, int64_t stride, int64_t r1, int64_t R, int64_t C, int rows_pad, int cols_pad,
+                 int ksteps, int* status) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = (uint64_t*)(smem + TC_STAGES * TC_STAGE_BYTES);  // full[2], empty[2], done
+  uint32_t* tmem_slot = (uint32_t*)(bars + 8);
+  __shared__ int s_fail;
+
+  const int node = blockIdx.z;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row0 = node * rows_pad + blockIdx.x * TC_BM;   // TMA row of the left operand
+  const int col0 = node * cols_pad + blockIdx.y * TC_BN;   // TMA row of the right operand
+  const uint32_t bar_full = smem_u32(&bars[0]), bar_empty = smem_u32(&bars[2]), bar_done = smem_u32(&bars[4]);
+
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    for (int s = 0; s < TC_STAGES; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_full + 8 * s));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_empty + 8 * s));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_done));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TC_TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (threadIdx.x == 0) {
+    // producer: TMA loads of the four operand tiles of each k-step
+    for (int ks = 0; ks < ksteps; ++ks) {
+      const int s = ks % TC_STAGES;
+      if (ks >= TC_STAGES && !mbar_wait(bar_empty + 8 * s, ((ks / TC_STAGES) - 1) & 1)) {
+        atomicExch(&s_fail, 1);
+        break;
+      }
+      uint8_t* st = smem + s * TC_STAGE_BYTES;
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_full + 8 * s),
+                   "r"(TC_STAGE_BYTES)
+                   : "memory");
+      const int x = ks * TC_BK;
+      tma_load_2d(smem_u32(st), &tmAh, x, row0, bar_full + 8 * s);
+      tma_load_2d(smem_u32(st + TC_TILE_BYTES), &tmAl, x, row0, bar_full + 8 * s);
+      tma_load_2d(smem_u32(st + 2 * TC_TILE_BYTES), &tmBh, x, col0, bar_full + 8 * s);
+      tma_load_2d(smem_u32(st + 3 * TC_TILE_BYTES), &tmBl, x, col0, bar_full + 8 * s);
+    }
+  } else if (threadIdx.x == 32) {
+    // MMA issuer: 4 k-steps of 8 per stage, 3 products each (3xTF32)
+    for (int ks = 0; ks < ksteps; ++ks) {
+      const int s = ks % TC_STAGES;
+      if (!mbar_wait(bar_full + 8 * s, (ks / TC_STAGES) & 1)) {
+        atomicExch(&s_fail, 1);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t base = smem_u32(smem + s * TC_STAGE_BYTES);
+#pragma unroll
+      for (int kk = 0; kk < TC_BK / 8; ++kk) {
+        const uint32_t off = kk * 32;  // 8 tf32 = 32 bytes along K inside the swizzle row
+        const uint64_t ah = sw128_desc(base + off), al = sw128_desc(base + TC_TILE_BYTES + off);
+        const uint64_t bh = sw128_desc(base + 2 * TC_TILE_BYTES + off), bl = sw128_desc(base + 3 * TC_TILE_BYTES + off);
+        mma_tf32(tmem, ah, bh, (ks > 0 || kk > 0) ? 1u : 0u);
+        mma_tf32(tmem, ah, bl, 1u);
+        mma_tf32(tmem, al, bh, 1u);
+      }
+      mma_commit(bar_empty + 8 * s);  // frees the stage when these MMAs are done
+    }
+    mma_commit(bar_done);  // completion of every MMA issued (also after a failure)
+  }
+  __syncwarp();
+
+  // epilogue: A22 -= D, read back from TMEM lane by lane (lane = real row)
+  const bool ok = mbar_wait(bar_done, 0);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (!ok) atomicExch(&s_fail, 1);
+  __syncthreads();
+  const bool fail = s_fail != 0;
+  const int64_t rr = (int64_t)blockIdx.x * TC_BM + warp * 32 + lane;  // real row within this node
+  const int64_t i = rr >> 1;
+  const int part = (int)(rr & 1);
+  float* Mb = (float*)(M + (int64_t)node * stride);
+#pragma unroll 1
+  for (int cc = 0; cc < TC_BN / 32; ++cc) {
+    uint32_t v[32];
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 32);
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    if (!fail && i < R) {
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        const int64_t j = (int64_t)blockIdx.y * TC_BN + cc * 32 + c;
+        if (j < C) {
+          float* p = Mb + 2 * ((r1 + i) + (r1 + j) * ld) + part;
+          *p = *p - __uint_as_float(v[c]);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
+  if (threadIdx.x == 0 && fail) atomicExch(status, DEV_BARRIER_TIMEOUT);
+}
+
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// Operand packing: left operand (rows_pad real rows x Kp) from L21 and right
+// operand (cols_pad rows x Kp) from U12, each as TF32 head/tail planes, K
+// contiguous.  A 32 x 32 complex tile is staged through shared memory so both
+// the reads of the column-major factor and the writes of the K-major planes
+// are coalesced.
+__global__ void tc_pack_kernel(const c64* M, int64_t ld, int64_t stride, int64_t k0, int jb, int64_t r1, int64_t R,
+                               int64_t C, int rows_pad, int cols_pad, int Kp, float* Ah, float* Al, float* Bh,
+                               float* Bl) {
+  __shared__ c64 tile[32][33];
+  const int node = blockIdx.z;
+  const c64* Mb = M + (int64_t)node * stride;
+  const bool left = blockIdx.y == 0;
+  const int64_t base = (int64_t)blockIdx.x * 32;  // complex rows (left) or columns (right)
+  const int64_t lim = left ? R : C;
+  if (base >= (left ? rows_pad / 2 : cols_pad)) return;
+  // load: tile[q][k] = L(base+q, k) (left) or U(k, base+q) (right)
+  for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
+    int q, k;
+    if (left) { q = t % 32; k = t / 32; } else { k = t % 32; q = t / 32; }
+    c64 v{0.f, 0.f};
+    if (base + q < lim && k < jb)
+      v = left ? Mb[(r1 + base + q) + (k0 + k) * ld] : Mb[(k0 + k) + (r1 + base + q) * ld];
+    tile[q][k] = v;
+  }
+  __syncthreads();
+  if (left) {
+    // 64 real rows x Kp
+    for (int t = threadIdx.x; t < 64 * Kp; t += blockDim.x) {
+      const int kk = t % Kp, rl = t / Kp;
+      const int q = rl >> 1, part = rl & 1;
+      float val = 0.f;
+      if (kk < 2 * jb) {
+        const c64 L = tile[q][kk % jb];
+        val = (kk < jb) ? (part ? L.im : L.re) : (part ? L.re : -L.im);
+      }
+      const float h = tf32_rna(val);
+      const int64_t o = ((int64_t)node * rows_pad + 2 * base + rl) * Kp + kk;
+      Ah[o] = h;
+      Al[o] = tf32_rna(val - h);
+    }
+  } else {
+    for (int t = threadIdx.x; t < 32 * Kp; t += blockDim.x) {
+      const int kk = t % Kp, q = t / Kp;
+      float val = 0.f;
+      if (kk < 2 * jb) {
+        const c64 U = tile[q][kk % jb];
+        val = (kk < jb) ? U.re : U.im;
+      }
+      const float h = tf32_rna(val);
+      const int64_t o = ((int64_t)node * cols_pad + base + q) * Kp + kk;
+      Bh[o] = h;
+      Bl[o] = tf32_rna(val - h);
+    }
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  });
+  return fn;
+}
+
+void make_map(CUtensorMap* map, float* base, int64_t rows, int Kp) {
+  auto fn = encode_fn();
+  if (!fn) throw CudaFailure(cudaErrorNotSupported);
+  cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)Kp * 4};
+  cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)TC_BM};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw CudaFailure(cudaErrorInvalidValue);
+}
+
+}  // namespace
+
+size_t tc_update_planes_bytes(int64_t n, int nodes) {
+  const int64_t rp = cdiv(2 * n, TC_BM) * TC_BM, cp = cdiv(n, TC_BN) * TC_BN;
+  const int64_t Kp = cdiv(2 * kPanel, TC_BK) * TC_BK;
+  return (size_t)4 * 2 * (size_t)nodes * (size_t)(rp + cp) * (size_t)Kp + 4096;
+}
+
+void tc_trailing_update(c64* M, int64_t n, int64_t ld, int64_t stride, int nodes, int64_t k0, int jb, void* planes,
+                        int* status, cudaStream_t s) {
+  const int64_t r1 = k0 + jb;
+  const int64_t R = n - r1, C = n - r1;
+  if (R <= 0) return;
+  const int rows_pad = (int)(cdiv(2 * R, TC_BM) * TC_BM);
+  const int cols_pad = (int)(cdiv(C, TC_BN) * TC_BN);
+  const int Kp = (int)(cdiv(2 * jb, TC_BK) * TC_BK);
+  float* Ah = (float*)planes;
+  float* Al = Ah + (int64_t)nodes * rows_pad * Kp;
+  float* Bh = Al + (int64_t)nodes * rows_pad * Kp;
+  float* Bl = Bh + (int64_t)nodes * cols_pad * Kp;
+  {
+    const int64_t blocks = std::max<int64_t>(rows_pad / 64, cols_pad / 32);
+    dim3 g((unsigned)blocks, 2, nodes);
+    tc_pack_kernel<<<g, 256, 0, s>>>(M, ld, stride, k0, jb, r1, R, C, rows_pad, cols_pad, Kp, Ah, Al, Bh, Bl);
+    FEAST_LAUNCH_CHECK();
+  }
+  CUtensorMap mAh, mAl, mBh, mBl;
+  make_map(&mAh, Ah, (int64_t)nodes * rows_pad, Kp);
+  make_map(&mAl, Al, (int64_t)nodes * rows_pad, Kp);
+  make_map(&mBh, Bh, (int64_t)nodes * cols_pad, Kp);
+  make_map(&mBl, Bl, (int64_t)nodes * cols_pad, Kp);
+  static bool attr = false;
+  if (!attr) {
+    FEAST_CUDA_TRY(cudaFuncSetAttribute(tc_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES));
+    attr = true;
+  }
+  dim3 grid((unsigned)(rows_pad / TC_BM), (unsigned)(cols_pad / TC_BN), (unsigned)nodes);
+  tc_update_kernel<<<grid, 128, TC_SMEM_BYTES, s>>>(mAh, mAl, mBh, mBl, M, ld, stride, r1, R, C, rows_pad, cols_pad,
+                                                    Kp / TC_BK, status);
+  FEAST_LAUNCH_CHECK();
+}
+
+}  // namespace feast
