@@ -438,41 +438,57 @@ void lu_factor_batched(F* M, int64_t n, int64_t ld, int64_t stride, int nodes,
   FEAST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, panel_lu_kernel<F>, kPanelThreads, 0));
   const int max_coop = std::max(1, occ) * num_sms;
   unsigned base = 0;
-  for (int64_t k0 = 0; k0 < n; k0 += kPanel) {
-    const int jb = (int)std::min<int64_t>(kPanel, n - k0);
-    const int64_t H = n - k0;
-    int P = (int)std::min<int64_t>(cdiv(H, 64), std::max(1, max_coop / nodes));
-    P = std::max(1, std::min(P, w.pmax));
-    const int64_t R = cdiv(H, P);
-    P = (int)cdiv(H, R);  // no empty CTAs
-    int k0i = (int)k0;
-    PanelWork wl = w;
-    void* args[] = {&M, &n, &ld, &stride, &k0i, (void*)&jb, &P, (void*)&R, &ipiv, &wl, &base};
-    FEAST_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)panel_lu_kernel<F>, dim3(nodes * P),
-                                               dim3(kPanelThreads), args, 0, s));
-  note_launch();
-    base += (unsigned)jb * (unsigned)P;
-    if (n - jb > 0) {
-      dim3 g2((unsigned)cdiv(n - jb, kSwapWarps), nodes);
-      laswp_trsm_kernel<F><<<g2, kSwapWarps * 32, 0, s>>>(M, n, ld, stride, k0i, jb, w.swap_src, w.swap_dst,
-                                                           w.swap_cnt);
-      FEAST_LAUNCH_CHECK();
-    }
-    const int64_t r1 = k0 + jb;
-    if (r1 < n) {
-      if constexpr (std::is_same<F, c64>::value) {
-        if (w.tc_planes) {  // complex-FP32 factors: tcgen05 3xTF32 update
-          tc_trailing_update(M, n, ld, stride, nodes, k0, jb, w.tc_planes, w.status, s);
-          continue;
-        }
+  // complex-FP32 factors with tensor-core scratch: two-level blocking, outer
+  // blocks of kTcBlock columns whose trailing update runs on the tensor cores,
+  // each factored by kPanel-wide panels with CUDA-core updates restricted to
+  // the block's columns and its row band; otherwise one level of kPanel.
+  bool tc = false;
+  if constexpr (std::is_same<F, c64>::value) tc = w.tc_planes != nullptr;
+  const int64_t NB = tc ? kTcBlock : kPanel;
+  for (int64_t k0 = 0; k0 < n; k0 += NB) {
+    const int64_t nbo = std::min<int64_t>(NB, n - k0);
+    const int64_t blk_end = k0 + nbo;
+    for (int64_t k1 = k0; k1 < blk_end; k1 += kPanel) {
+      const int jb = (int)std::min<int64_t>(kPanel, blk_end - k1);
+      const int64_t H = n - k1;
+      int P = (int)std::min<int64_t>(cdiv(H, 64), std::max(1, max_coop / nodes));
+      P = std::max(1, std::min(P, w.pmax));
+      const int64_t R = cdiv(H, P);
+      P = (int)cdiv(H, R);  // no empty CTAs
+      int k1i = (int)k1;
+      PanelWork wl = w;
+      void* args[] = {&M, &n, &ld, &stride, &k1i, (void*)&jb, &P, (void*)&R, &ipiv, &wl, &base};
+      FEAST_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)panel_lu_kernel<F>, dim3(nodes * P),
+                                                 dim3(kPanelThreads), args, 0, s));
+      note_launch();
+      base += (unsigned)jb * (unsigned)P;
+      if (n - jb > 0) {
+        dim3 g2((unsigned)cdiv(n - jb, kSwapWarps), nodes);
+        laswp_trsm_kernel<F><<<g2, kSwapWarps * 32, 0, s>>>(M, n, ld, stride, k1i, jb, w.swap_src, w.swap_dst,
+                                                             w.swap_cnt);
+        FEAST_LAUNCH_CHECK();
       }
-      GemmArgs g{};
-      g.M = n - r1; g.N = n - r1; g.K = jb;
-      g.A = M + r1 + k0 * ld; g.lda = ld; g.strideA = stride; g.opA = OP_N;
-      g.B = M + k0 + r1 * ld; g.ldb = ld; g.strideB = stride; g.opB = OP_N;
-      g.C = M + r1 + r1 * ld; g.ldc = ld; g.strideC = stride;
-      g.alpha = C1(-1.0); g.beta = C1(1.0); g.batch = nodes; g.ksplit = 1;
-      gemm<F, F, F>(g, s);
+      const int64_t r1 = k1 + jb;
+      auto update = [&](int64_t rows0, int64_t rows1, int64_t cols0, int64_t cols1) {
+        if (rows1 <= rows0 || cols1 <= cols0) return;
+        GemmArgs g{};
+        g.M = rows1 - rows0; g.N = cols1 - cols0; g.K = jb;
+        g.A = M + rows0 + k1 * ld; g.lda = ld; g.strideA = stride; g.opA = OP_N;
+        g.B = M + k1 + cols0 * ld; g.ldb = ld; g.strideB = stride; g.opB = OP_N;
+        g.C = M + rows0 + cols0 * ld; g.ldc = ld; g.strideC = stride;
+        g.alpha = C1(-1.0); g.beta = C1(1.0); g.batch = nodes; g.ksplit = 1;
+        gemm<F, F, F>(g, s);
+      };
+      if (!tc) {
+        update(r1, n, r1, n);                 // the whole trailing matrix
+      } else {
+        update(r1, n, r1, blk_end);           // the rest of the outer block
+        update(r1, blk_end, blk_end, n);      // the block's row band right of it
+      }
+    }
+    if constexpr (std::is_same<F, c64>::value) {
+      if (tc && blk_end < n)
+        tc_trailing_update(M, n, ld, stride, nodes, k0, (int)nbo, w.tc_planes, w.status, num_sms, s);
     }
   }
   const size_t smem = sizeof(int32_t) * (size_t)n;

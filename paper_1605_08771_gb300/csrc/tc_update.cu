@@ -107,18 +107,17 @@ __global__ void __launch_bounds__(128, 1)
 tc_update_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                  const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, c64* M,
                  int64_t ld, int64_t stride, int64_t r1, int64_t R, int64_t C, int rows_pad, int cols_pad,
-                 int ksteps, int* status) {
+                 int ksteps, int nodes, int* status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = (uint64_t*)(smem + TC_STAGES * TC_STAGE_BYTES);  // full[2], empty[2], done
   uint32_t* tmem_slot = (uint32_t*)(bars + 8);
   __shared__ int s_fail;
 
-  const int node = blockIdx.z;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row0 = node * rows_pad + blockIdx.x * TC_BM;   // TMA row of the left operand
-  const int col0 = node * cols_pad + blockIdx.y * TC_BN;   // TMA row of the right operand
   const uint32_t bar_full = smem_u32(&bars[0]), bar_empty = smem_u32(&bars[2]), bar_done = smem_u32(&bars[4]);
+  const int mtiles = rows_pad / TC_BM, ntiles = cols_pad / TC_BN;
+  const int64_t total = (int64_t)mtiles * ntiles * nodes;
 
   if (threadIdx.x == 0) {
     s_fail = 0;
@@ -139,88 +138,105 @@ tc_update_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
-  if (threadIdx.x == 0) {
-    // producer: TMA loads of the four operand tiles of each k-step
-    for (int ks = 0; ks < ksteps; ++ks) {
-      const int s = ks % TC_STAGES;
-      if (ks >= TC_STAGES && !mbar_wait(bar_empty + 8 * s, ((ks / TC_STAGES) - 1) & 1)) {
-        atomicExch(&s_fail, 1);
-        break;
+  // persistent loop over output tiles; k-steps are numbered globally (g) so
+  // the stage parities carry over from tile to tile
+  int it = 0;
+  for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x, ++it) {
+    const int node = (int)(tile / ((int64_t)mtiles * ntiles));
+    const int rem = (int)(tile % ((int64_t)mtiles * ntiles));
+    const int mt = rem % mtiles, nt = rem / mtiles;
+    const int row0 = node * rows_pad + mt * TC_BM;  // TMA row of the left operand
+    const int col0 = node * cols_pad + nt * TC_BN;  // TMA row of the right operand
+    const int gbase = it * ksteps;
+    if (threadIdx.x == 0 && !s_fail) {
+      // producer: TMA loads of the four operand tiles of each k-step
+      for (int ks = 0; ks < ksteps; ++ks) {
+        const int g = gbase + ks, s = g % TC_STAGES;
+        if (g >= TC_STAGES && !mbar_wait(bar_empty + 8 * s, ((g / TC_STAGES) - 1) & 1)) {
+          atomicExch(&s_fail, 1);
+          break;
+        }
+        uint8_t* st = smem + s * TC_STAGE_BYTES;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_full + 8 * s),
+                     "r"(TC_STAGE_BYTES)
+                     : "memory");
+        const int x = ks * TC_BK;
+        tma_load_2d(smem_u32(st), &tmAh, x, row0, bar_full + 8 * s);
+        tma_load_2d(smem_u32(st + TC_TILE_BYTES), &tmAl, x, row0, bar_full + 8 * s);
+        tma_load_2d(smem_u32(st + 2 * TC_TILE_BYTES), &tmBh, x, col0, bar_full + 8 * s);
+        tma_load_2d(smem_u32(st + 3 * TC_TILE_BYTES), &tmBl, x, col0, bar_full + 8 * s);
       }
-      uint8_t* st = smem + s * TC_STAGE_BYTES;
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_full + 8 * s),
-                   "r"(TC_STAGE_BYTES)
-                   : "memory");
-      const int x = ks * TC_BK;
-      tma_load_2d(smem_u32(st), &tmAh, x, row0, bar_full + 8 * s);
-      tma_load_2d(smem_u32(st + TC_TILE_BYTES), &tmAl, x, row0, bar_full + 8 * s);
-      tma_load_2d(smem_u32(st + 2 * TC_TILE_BYTES), &tmBh, x, col0, bar_full + 8 * s);
-      tma_load_2d(smem_u32(st + 3 * TC_TILE_BYTES), &tmBl, x, col0, bar_full + 8 * s);
-    }
-  } else if (threadIdx.x == 32) {
-    // MMA issuer: 4 k-steps of 8 per stage, 3 products each (3xTF32)
-    for (int ks = 0; ks < ksteps; ++ks) {
-      const int s = ks % TC_STAGES;
-      if (!mbar_wait(bar_full + 8 * s, (ks / TC_STAGES) & 1)) {
-        atomicExch(&s_fail, 1);
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t base = smem_u32(smem + s * TC_STAGE_BYTES);
+    } else if (threadIdx.x == 32) {
+      // MMA issuer: 4 k-steps of 8 per stage, 3 products each (3xTF32)
+      for (int ks = 0; ks < ksteps && !s_fail; ++ks) {
+        const int g = gbase + ks, s = g % TC_STAGES;
+        if (!mbar_wait(bar_full + 8 * s, (g / TC_STAGES) & 1)) {
+          atomicExch(&s_fail, 1);
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t base = smem_u32(smem + s * TC_STAGE_BYTES);
 #pragma unroll
-      for (int kk = 0; kk < TC_BK / 8; ++kk) {
-        const uint32_t off = kk * 32;  // 8 tf32 = 32 bytes along K inside the swizzle row
-        const uint64_t ah = sw128_desc(base + off), al = sw128_desc(base + TC_TILE_BYTES + off);
-        const uint64_t bh = sw128_desc(base + 2 * TC_TILE_BYTES + off), bl = sw128_desc(base + 3 * TC_TILE_BYTES + off);
-        mma_tf32(tmem, ah, bh, (ks > 0 || kk > 0) ? 1u : 0u);
-        mma_tf32(tmem, ah, bl, 1u);
-        mma_tf32(tmem, al, bh, 1u);
+        for (int kk = 0; kk < TC_BK / 8; ++kk) {
+          const uint32_t off = kk * 32;  // 8 tf32 = 32 bytes along K inside the swizzle row
+          const uint64_t ah = sw128_desc(base + off), al = sw128_desc(base + TC_TILE_BYTES + off);
+          const uint64_t bh = sw128_desc(base + 2 * TC_TILE_BYTES + off),
+                         bl = sw128_desc(base + 3 * TC_TILE_BYTES + off);
+          mma_tf32(tmem, ah, bh, (ks > 0 || kk > 0) ? 1u : 0u);
+          mma_tf32(tmem, ah, bl, 1u);
+          mma_tf32(tmem, al, bh, 1u);
+        }
+        mma_commit(bar_empty + 8 * s);  // frees the stage when these MMAs are done
       }
-      mma_commit(bar_empty + 8 * s);  // frees the stage when these MMAs are done
+      mma_commit(bar_done);  // completion of every MMA issued for this tile
     }
-    mma_commit(bar_done);  // completion of every MMA issued (also after a failure)
-  }
-  __syncwarp();
+    __syncwarp();
 
-  // epilogue: A22 -= D, read back from TMEM lane by lane (lane = real row)
-  const bool ok = mbar_wait(bar_done, 0);
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (!ok) atomicExch(&s_fail, 1);
-  __syncthreads();
-  const bool fail = s_fail != 0;
-  const int64_t rr = (int64_t)blockIdx.x * TC_BM + warp * 32 + lane;  // real row within this node
-  const int64_t i = rr >> 1;
-  const int part = (int)(rr & 1);
-  float* Mb = (float*)(M + (int64_t)node * stride);
+    // epilogue: A22 -= D, read back from TMEM lane by lane (lane = real row)
+    const bool ok = mbar_wait(bar_done, it & 1);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!ok) atomicExch(&s_fail, 1);
+    __syncthreads();
+    const bool fail = s_fail != 0;
+    const int64_t rr = (int64_t)mt * TC_BM + warp * 32 + lane;  // real row within this node
+    const int64_t i = rr >> 1;
+    const int part = (int)(rr & 1);
+    float* Mb = (float*)(M + (int64_t)node * stride);
 #pragma unroll 1
-  for (int cc = 0; cc < TC_BN / 32; ++cc) {
-    uint32_t v[32];
-    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 32);
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    if (!fail && i < R) {
+    for (int cc = 0; cc < TC_BN / 32; ++cc) {
+      uint32_t v[32];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 32);
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+          "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+            "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+            "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (!fail && i < R) {
 #pragma unroll
-      for (int c = 0; c < 32; ++c) {
-        const int64_t j = (int64_t)blockIdx.y * TC_BN + cc * 32 + c;
-        if (j < C) {
-          float* p = Mb + 2 * ((r1 + i) + (r1 + j) * ld) + part;
-          *p = *p - __uint_as_float(v[c]);
+        for (int c = 0; c < 32; ++c) {
+          const int64_t j = (int64_t)nt * TC_BN + cc * 32 + c;
+          if (j < C) {
+            float* p = Mb + 2 * ((r1 + i) + (r1 + j) * ld) + part;
+            *p = *p - __uint_as_float(v[c]);
+          }
         }
       }
     }
+    // the accumulator is read: the next tile's MMAs may overwrite it
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (fail) break;
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
-  if (threadIdx.x == 0 && fail) atomicExch(status, DEV_BARRIER_TIMEOUT);
+  if (threadIdx.x == 0 && s_fail) atomicExch(status, DEV_BARRIER_TIMEOUT);
 }
 
 __device__ __forceinline__ float tf32_rna(float x) {
@@ -231,10 +247,10 @@ __device__ __forceinline__ float tf32_rna(float x) {
 
 // Operand packing: left operand (rows_pad real rows x Kp) from L21 and right
 // operand (cols_pad rows x Kp) from U12, each as TF32 head/tail planes, K
-// contiguous.  A 32 x 32 complex tile is staged through shared memory so both
-// the reads of the column-major factor and the writes of the K-major planes
-// are coalesced.
-__global__ void tc_pack_kernel(const c64* M, int64_t ld, int64_t stride, int64_t k0, int jb, int64_t r1, int64_t R,
+// contiguous (Kp >= 2 kb).  32 x 32 complex tiles are staged through shared
+// memory so both the reads of the column-major factor and the writes of the
+// K-major planes are coalesced.
+__global__ void tc_pack_kernel(const c64* M, int64_t ld, int64_t stride, int64_t k0, int kb, int64_t r1, int64_t R,
                                int64_t C, int rows_pad, int cols_pad, int Kp, float* Ah, float* Al, float* Bh,
                                float* Bl) {
   __shared__ c64 tile[32][33];
@@ -244,43 +260,57 @@ __global__ void tc_pack_kernel(const c64* M, int64_t ld, int64_t stride, int64_t
   const int64_t base = (int64_t)blockIdx.x * 32;  // complex rows (left) or columns (right)
   const int64_t lim = left ? R : C;
   if (base >= (left ? rows_pad / 2 : cols_pad)) return;
-  // load: tile[q][k] = L(base+q, k) (left) or U(k, base+q) (right)
-  for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
-    int q, k;
-    if (left) { q = t % 32; k = t / 32; } else { k = t % 32; q = t / 32; }
-    c64 v{0.f, 0.f};
-    if (base + q < lim && k < jb)
-      v = left ? Mb[(r1 + base + q) + (k0 + k) * ld] : Mb[(k0 + k) + (r1 + base + q) * ld];
-    tile[q][k] = v;
-  }
-  __syncthreads();
-  if (left) {
-    // 64 real rows x Kp
-    for (int t = threadIdx.x; t < 64 * Kp; t += blockDim.x) {
-      const int kk = t % Kp, rl = t / Kp;
-      const int q = rl >> 1, part = rl & 1;
-      float val = 0.f;
-      if (kk < 2 * jb) {
-        const c64 L = tile[q][kk % jb];
-        val = (kk < jb) ? (part ? L.im : L.re) : (part ? L.re : -L.im);
-      }
-      const float h = tf32_rna(val);
-      const int64_t o = ((int64_t)node * rows_pad + 2 * base + rl) * Kp + kk;
-      Ah[o] = h;
-      Al[o] = tf32_rna(val - h);
+  for (int kc = 0; kc < Kp / 2; kc += 32) {       // k-chunks of the complex operand
+    __syncthreads();
+    for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
+      int q, k;
+      if (left) { q = t % 32; k = t / 32; } else { k = t % 32; q = t / 32; }
+      c64 v{0.f, 0.f};
+      if (base + q < lim && kc + k < kb)
+        v = left ? Mb[(r1 + base + q) + (k0 + kc + k) * ld] : Mb[(k0 + kc + k) + (r1 + base + q) * ld];
+      tile[q][k] = v;
     }
-  } else {
-    for (int t = threadIdx.x; t < 32 * Kp; t += blockDim.x) {
-      const int kk = t % Kp, q = t / Kp;
-      float val = 0.f;
-      if (kk < 2 * jb) {
-        const c64 U = tile[q][kk % jb];
-        val = (kk < jb) ? U.re : U.im;
+    __syncthreads();
+    if (left) {
+      // 64 real rows x (32 real-part columns + 32 imaginary-part columns)
+      for (int t = threadIdx.x; t < 64 * 64; t += blockDim.x) {
+        const int c = t % 64, rl = t / 64;
+        const int q = rl >> 1, part = rl & 1, k = c % 32;
+        const c64 L = tile[q][k];
+        float val;
+        int kk;
+        if (c < 32) { val = part ? L.im : L.re; kk = kc + k; }
+        else { val = part ? L.re : -L.im; kk = kb + kc + k; }
+        if (kc + k >= kb) continue;
+        const float h = tf32_rna(val);
+        const int64_t o = ((int64_t)node * rows_pad + 2 * base + rl) * Kp + kk;
+        Ah[o] = h;
+        Al[o] = tf32_rna(val - h);
       }
-      const float h = tf32_rna(val);
-      const int64_t o = ((int64_t)node * cols_pad + base + q) * Kp + kk;
-      Bh[o] = h;
-      Bl[o] = tf32_rna(val - h);
+    } else {
+      for (int t = threadIdx.x; t < 32 * 64; t += blockDim.x) {
+        const int c = t % 64, q = t / 64, k = c % 32;
+        if (kc + k >= kb) continue;
+        const c64 U = tile[q][k];
+        const float val = (c < 32) ? U.re : U.im;
+        const int kk = (c < 32) ? kc + k : kb + kc + k;
+        const float h = tf32_rna(val);
+        const int64_t o = ((int64_t)node * cols_pad + base + q) * Kp + kk;
+        Bh[o] = h;
+        Bl[o] = tf32_rna(val - h);
+      }
+    }
+  }
+  // zero the K padding [2 kb, Kp)
+  if (2 * kb < Kp) {
+    const int rowsb = left ? 64 : 32;
+    const int64_t rbase = left ? (int64_t)node * rows_pad + 2 * base : (int64_t)node * cols_pad + base;
+    float* H = left ? Ah : Bh;
+    float* Lo = left ? Al : Bl;
+    for (int t = threadIdx.x; t < rowsb * (Kp - 2 * kb); t += blockDim.x) {
+      const int kk = 2 * kb + t % (Kp - 2 * kb), rl = t / (Kp - 2 * kb);
+      H[(rbase + rl) * Kp + kk] = 0.f;
+      Lo[(rbase + rl) * Kp + kk] = 0.f;
     }
   }
 }
@@ -316,18 +346,18 @@ void make_map(CUtensorMap* map, float* base, int64_t rows, int Kp) {
 
 size_t tc_update_planes_bytes(int64_t n, int nodes) {
   const int64_t rp = cdiv(2 * n, TC_BM) * TC_BM, cp = cdiv(n, TC_BN) * TC_BN;
-  const int64_t Kp = cdiv(2 * kPanel, TC_BK) * TC_BK;
+  const int64_t Kp = cdiv(2 * kTcBlock, TC_BK) * TC_BK;
   return (size_t)4 * 2 * (size_t)nodes * (size_t)(rp + cp) * (size_t)Kp + 4096;
 }
 
-void tc_trailing_update(c64* M, int64_t n, int64_t ld, int64_t stride, int nodes, int64_t k0, int jb, void* planes,
-                        int* status, cudaStream_t s) {
-  const int64_t r1 = k0 + jb;
+void tc_trailing_update(c64* M, int64_t n, int64_t ld, int64_t stride, int nodes, int64_t k0, int kb, void* planes,
+                        int* status, int num_sms, cudaStream_t s) {
+  const int64_t r1 = k0 + kb;
   const int64_t R = n - r1, C = n - r1;
   if (R <= 0) return;
   const int rows_pad = (int)(cdiv(2 * R, TC_BM) * TC_BM);
   const int cols_pad = (int)(cdiv(C, TC_BN) * TC_BN);
-  const int Kp = (int)(cdiv(2 * jb, TC_BK) * TC_BK);
+  const int Kp = (int)(cdiv(2 * kb, TC_BK) * TC_BK);
   float* Ah = (float*)planes;
   float* Al = Ah + (int64_t)nodes * rows_pad * Kp;
   float* Bh = Al + (int64_t)nodes * rows_pad * Kp;
@@ -335,7 +365,7 @@ void tc_trailing_update(c64* M, int64_t n, int64_t ld, int64_t stride, int nodes
   {
     const int64_t blocks = std::max<int64_t>(rows_pad / 64, cols_pad / 32);
     dim3 g((unsigned)blocks, 2, nodes);
-    tc_pack_kernel<<<g, 256, 0, s>>>(M, ld, stride, k0, jb, r1, R, C, rows_pad, cols_pad, Kp, Ah, Al, Bh, Bl);
+    tc_pack_kernel<<<g, 256, 0, s>>>(M, ld, stride, k0, kb, r1, R, C, rows_pad, cols_pad, Kp, Ah, Al, Bh, Bl);
     FEAST_LAUNCH_CHECK();
   }
   CUtensorMap mAh, mAl, mBh, mBl;
@@ -348,9 +378,10 @@ void tc_trailing_update(c64* M, int64_t n, int64_t ld, int64_t stride, int nodes
     FEAST_CUDA_TRY(cudaFuncSetAttribute(tc_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES));
     attr = true;
   }
-  dim3 grid((unsigned)(rows_pad / TC_BM), (unsigned)(cols_pad / TC_BN), (unsigned)nodes);
+  const int64_t tiles = (int64_t)(rows_pad / TC_BM) * (cols_pad / TC_BN) * nodes;
+  const unsigned grid = (unsigned)std::min<int64_t>(tiles, num_sms);
   tc_update_kernel<<<grid, 128, TC_SMEM_BYTES, s>>>(mAh, mAl, mBh, mBl, M, ld, stride, r1, R, C, rows_pad, cols_pad,
-                                                    Kp / TC_BK, status);
+                                                    Kp / TC_BK, nodes, status);
   FEAST_LAUNCH_CHECK();
 }
 

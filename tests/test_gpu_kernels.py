@@ -15,10 +15,13 @@ ZS = np.array([0.3 + 0.5j, -0.7 + 0.2j, 1.1 + 0.05j])
 SIZES = [1, 2, 31, 32, 33, 65, 100, 257]
 
 
-@pytest.mark.parametrize("n", SIZES)
+@pytest.mark.parametrize("n", SIZES + [520])
 @pytest.mark.parametrize("cplx", [False, True])
 @pytest.mark.parametrize("prec", [fg.FEAST_PREC_F64, fg.FEAST_PREC_MIXED])
 def test_shifted_lu_matches_oracle(ctx, n, cplx, prec):
+    # the complex-FP32 factors run the two-level LU whose 128-column outer
+    # updates use the tensor cores: n = 257 and 520 span several outer blocks
+    # and a ragged tail
     A = rand_hermitian(n, cplx, seed=n)
     LU, perm = fg.feast_shifted_lu(ctx, cuda(A), ZS, prec)
     LU, perm = host(LU).astype(np.complex128), host(perm)
