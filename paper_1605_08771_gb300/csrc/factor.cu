@@ -236,6 +236,93 @@ laswp_trsm_kernel(F* M, int64_t n, int64_t ld, int64_t stride, int k0, int jb,
   }
 }
 
+// Net effect of the row interchanges ipiv[r0 .. r0+cnt) of every node on
+// the rows they touch (at most 2*cnt): after the swaps, row dst holds the
+// former row src.  One thread per node.
+__global__ void block_swap_summary_kernel(const int32_t* ipiv, int64_t n, int64_t r0, int cnt, int* src, int* dst,
+                                          int* cntp, int cap) {
+  const int b = blockIdx.x;
+  if (threadIdx.x != 0) return;
+  int* rows = dst + (int64_t)b * cap;     // scratch: touched rows
+  int* content = src + (int64_t)b * cap;  // scratch: original row now held
+  int c = 0;
+  auto slot_of = [&](int r) {
+    for (int q = 0; q < c; ++q)
+      if (rows[q] == r) return q;
+    rows[c] = r;
+    content[c] = r;
+    return c++;
+  };
+  for (int j = 0; j < cnt; ++j) {
+    const int a = slot_of((int)(r0 + j));
+    const int bb = slot_of(ipiv[(int64_t)b * n + r0 + j]);
+    const int t = content[a];
+    content[a] = content[bb];
+    content[bb] = t;
+  }
+  // compact to the moved rows only
+  int out = 0;
+  for (int q = 0; q < c; ++q)
+    if (content[q] != rows[q]) {
+      const int r = rows[q], sr = content[q];
+      rows[out] = r;
+      content[out] = sr;
+      ++out;
+    }
+  cntp[b] = out;
+}
+
+// Apply a per-node row permutation list (row dst <- former row src, at most
+// MAXS entries) to the columns [c0, c1) outside [s0, s1): warp per column.
+template <typename F, int MAXS>
+__global__ void __launch_bounds__(kSwapWarps * 32)
+row_gather_kernel(F* M, int64_t ld, int64_t stride, int64_t c0, int64_t c1, int64_t s0, int64_t s1,
+                  const int* src, const int* dst, const int* cntp, int cap) {
+  const int b = blockIdx.y;
+  const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t ncols = (c1 - c0) - (s1 - s0);
+  const int64_t idx = (int64_t)blockIdx.x * kSwapWarps + wp;
+  if (idx >= ncols) return;
+  const int64_t c = (c0 + idx < s0) ? c0 + idx : c0 + idx + (s1 - s0);
+  F* colp = M + (int64_t)b * stride + c * ld;
+  const int cnt = cntp[b];
+  const int* sr = src + (int64_t)b * cap;
+  const int* ds = dst + (int64_t)b * cap;
+  constexpr int PER = MAXS / 32;
+  F v[PER];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) v[q] = (lane + 32 * q < cnt) ? colp[sr[lane + 32 * q]] : num<F>::zero();
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < PER; ++q)
+    if (lane + 32 * q < cnt) colp[ds[lane + 32 * q]] = v[q];
+}
+
+// U <- L11^{-1} U on the rows [r0, r0 + jb) of the columns [c0, c1), L11 the
+// unit-lower diagonal block at (r0, r0): warp per column.
+template <typename F>
+__global__ void __launch_bounds__(kSwapWarps * 32)
+trsm_rows_kernel(F* M, int64_t ld, int64_t stride, int64_t r0, int jb, int64_t c0, int64_t c1) {
+  const int b = blockIdx.y;
+  F* Mb = M + (int64_t)b * stride;
+  __shared__ F L11[kPanel][kPanel + 1];
+  for (int l = threadIdx.x; l < jb * jb; l += blockDim.x) {
+    const int i = l % jb, j = l / jb;
+    L11[i][j] = Mb[(r0 + i) + (r0 + j) * ld];
+  }
+  __syncthreads();
+  const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t c = c0 + (int64_t)blockIdx.x * kSwapWarps + wp;
+  if (c >= c1) return;
+  F* colp = Mb + c * ld;
+  F x = lane < jb ? colp[r0 + lane] : num<F>::zero();
+  for (int j = 0; j < jb - 1; ++j) {
+    const F xj = shfl(x, j);
+    if (lane > j && lane < jb) x = x - L11[lane][j] * xj;
+  }
+  if (lane < jb) colp[r0 + lane] = x;
+}
+
 __global__ void build_perm_kernel(const int32_t* ipiv, int32_t* perm, int64_t n) {
   extern __shared__ int32_t sp[];
   const int b = blockIdx.x;
@@ -397,6 +484,9 @@ size_t panel_work_bytes(int nodes, int pmax, size_t eb) {
   add(sizeof(int) * nodes * 2 * kPanel);
   add(sizeof(int) * nodes * 2 * kPanel);
   add(sizeof(int) * nodes);
+  add(sizeof(int) * nodes * 2 * kTcBlock);
+  add(sizeof(int) * nodes * 2 * kTcBlock);
+  add(sizeof(int) * nodes);
   return s;
 }
 
@@ -414,6 +504,9 @@ PanelWork panel_work_carve(void* base, int nodes, int pmax, size_t eb) {
   w.swap_src = (int*)take(sizeof(int) * nodes * 2 * kPanel);
   w.swap_dst = (int*)take(sizeof(int) * nodes * 2 * kPanel);
   w.swap_cnt = (int*)take(sizeof(int) * nodes);
+  w.blk_src = (int*)take(sizeof(int) * nodes * 2 * kTcBlock);
+  w.blk_dst = (int*)take(sizeof(int) * nodes * 2 * kTcBlock);
+  w.blk_cnt = (int*)take(sizeof(int) * nodes);
   w.pmax = pmax;
   w.tc_planes = nullptr;
   return w;
@@ -445,49 +538,86 @@ void lu_factor_batched(F* M, int64_t n, int64_t ld, int64_t stride, int nodes,
   bool tc = false;
   if constexpr (std::is_same<F, c64>::value) tc = w.tc_planes != nullptr;
   const int64_t NB = tc ? kTcBlock : kPanel;
+  auto gemm_update = [&](int64_t rows0, int64_t rows1, int64_t cols0, int64_t cols1, int64_t kc, int kw) {
+    if (rows1 <= rows0 || cols1 <= cols0) return;
+    GemmArgs g{};
+    g.M = rows1 - rows0; g.N = cols1 - cols0; g.K = kw;
+    g.A = M + rows0 + kc * ld; g.lda = ld; g.strideA = stride; g.opA = OP_N;
+    g.B = M + kc + cols0 * ld; g.ldb = ld; g.strideB = stride; g.opB = OP_N;
+    g.C = M + rows0 + cols0 * ld; g.ldc = ld; g.strideC = stride;
+    g.alpha = C1(-1.0); g.beta = C1(1.0); g.batch = nodes; g.ksplit = 1;
+    gemm<F, F, F>(g, s);
+  };
+  auto panel = [&](int64_t k1, int jb) {
+    const int64_t H = n - k1;
+    int P = (int)std::min<int64_t>(cdiv(H, 64), std::max(1, max_coop / nodes));
+    P = std::max(1, std::min(P, w.pmax));
+    const int64_t R = cdiv(H, P);
+    P = (int)cdiv(H, R);  // no empty CTAs
+    int k1i = (int)k1;
+    PanelWork wl = w;
+    void* args[] = {&M, &n, &ld, &stride, &k1i, (void*)&jb, &P, (void*)&R, &ipiv, &wl, &base};
+    FEAST_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)panel_lu_kernel<F>, dim3(nodes * P),
+                                               dim3(kPanelThreads), args, 0, s));
+    note_launch();
+    base += (unsigned)jb * (unsigned)P;
+  };
   for (int64_t k0 = 0; k0 < n; k0 += NB) {
     const int64_t nbo = std::min<int64_t>(NB, n - k0);
     const int64_t blk_end = k0 + nbo;
-    for (int64_t k1 = k0; k1 < blk_end; k1 += kPanel) {
-      const int jb = (int)std::min<int64_t>(kPanel, blk_end - k1);
-      const int64_t H = n - k1;
-      int P = (int)std::min<int64_t>(cdiv(H, 64), std::max(1, max_coop / nodes));
-      P = std::max(1, std::min(P, w.pmax));
-      const int64_t R = cdiv(H, P);
-      P = (int)cdiv(H, R);  // no empty CTAs
-      int k1i = (int)k1;
-      PanelWork wl = w;
-      void* args[] = {&M, &n, &ld, &stride, &k1i, (void*)&jb, &P, (void*)&R, &ipiv, &wl, &base};
-      FEAST_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)panel_lu_kernel<F>, dim3(nodes * P),
-                                                 dim3(kPanelThreads), args, 0, s));
-      note_launch();
-      base += (unsigned)jb * (unsigned)P;
+    if (!tc) {
+      // one level: panel, interchanges + U12 for every other column, trailing update
+      const int jb = (int)nbo;
+      panel(k0, jb);
       if (n - jb > 0) {
         dim3 g2((unsigned)cdiv(n - jb, kSwapWarps), nodes);
-        laswp_trsm_kernel<F><<<g2, kSwapWarps * 32, 0, s>>>(M, n, ld, stride, k1i, jb, w.swap_src, w.swap_dst,
+        laswp_trsm_kernel<F><<<g2, kSwapWarps * 32, 0, s>>>(M, n, ld, stride, (int)k0, jb, w.swap_src, w.swap_dst,
                                                              w.swap_cnt);
         FEAST_LAUNCH_CHECK();
       }
-      const int64_t r1 = k1 + jb;
-      auto update = [&](int64_t rows0, int64_t rows1, int64_t cols0, int64_t cols1) {
-        if (rows1 <= rows0 || cols1 <= cols0) return;
-        GemmArgs g{};
-        g.M = rows1 - rows0; g.N = cols1 - cols0; g.K = jb;
-        g.A = M + rows0 + k1 * ld; g.lda = ld; g.strideA = stride; g.opA = OP_N;
-        g.B = M + k1 + cols0 * ld; g.ldb = ld; g.strideB = stride; g.opB = OP_N;
-        g.C = M + rows0 + cols0 * ld; g.ldc = ld; g.strideC = stride;
-        g.alpha = C1(-1.0); g.beta = C1(1.0); g.batch = nodes; g.ksplit = 1;
-        gemm<F, F, F>(g, s);
-      };
-      if (!tc) {
-        update(r1, n, r1, n);                 // the whole trailing matrix
-      } else {
-        update(r1, n, r1, blk_end);           // the rest of the outer block
-        update(r1, blk_end, blk_end, n);      // the block's row band right of it
-      }
+      gemm_update(blk_end, n, blk_end, n, k0, jb);
+      continue;
     }
-    if constexpr (std::is_same<F, c64>::value) {
-      if (tc && blk_end < n)
+    // two levels: factor the tall block [k0, n) x [k0, blk_end) panel by panel,
+    // interchanges and updates confined to the block's columns
+    for (int64_t k1 = k0; k1 < blk_end; k1 += kPanel) {
+      const int jb = (int)std::min<int64_t>(kPanel, blk_end - k1);
+      const int64_t r1 = k1 + jb;
+      panel(k1, jb);
+      if (nbo > jb) {
+        dim3 g2((unsigned)cdiv(nbo - jb, kSwapWarps), nodes);
+        row_gather_kernel<F, 2 * kPanel><<<g2, kSwapWarps * 32, 0, s>>>(M, ld, stride, k0, blk_end, k1, r1,
+                                                                         w.swap_src, w.swap_dst, w.swap_cnt,
+                                                                         2 * kPanel);
+        FEAST_LAUNCH_CHECK();
+      }
+      if (r1 < blk_end) {
+        dim3 g3((unsigned)cdiv(blk_end - r1, kSwapWarps), nodes);
+        trsm_rows_kernel<F><<<g3, kSwapWarps * 32, 0, s>>>(M, ld, stride, k1, jb, r1, blk_end);
+        FEAST_LAUNCH_CHECK();
+      }
+      gemm_update(r1, n, r1, blk_end, k1, jb);
+    }
+    // the block's interchanges on the columns left and right of it
+    block_swap_summary_kernel<<<nodes, 32, 0, s>>>(ipiv, n, k0, (int)nbo, w.blk_src, w.blk_dst, w.blk_cnt,
+                                                    2 * kTcBlock);
+    FEAST_LAUNCH_CHECK();
+    if (n - nbo > 0) {
+      dim3 g4((unsigned)cdiv(n - nbo, kSwapWarps), nodes);
+      row_gather_kernel<F, 2 * kTcBlock><<<g4, kSwapWarps * 32, 0, s>>>(M, ld, stride, 0, n, k0, blk_end, w.blk_src,
+                                                                         w.blk_dst, w.blk_cnt, 2 * kTcBlock);
+      FEAST_LAUNCH_CHECK();
+    }
+    if (blk_end < n) {
+      // U12 = L11^{-1} A12 for the block's row band, panel by panel
+      for (int64_t k1 = k0; k1 < blk_end; k1 += kPanel) {
+        const int jb = (int)std::min<int64_t>(kPanel, blk_end - k1);
+        dim3 g5((unsigned)cdiv(n - blk_end, kSwapWarps), nodes);
+        trsm_rows_kernel<F><<<g5, kSwapWarps * 32, 0, s>>>(M, ld, stride, k1, jb, blk_end, n);
+        FEAST_LAUNCH_CHECK();
+        gemm_update(k1 + jb, blk_end, blk_end, n, k1, jb);
+      }
+      if constexpr (std::is_same<F, c64>::value)
         tc_trailing_update(M, n, ld, stride, nodes, k0, (int)nbo, w.tc_planes, w.status, num_sms, s);
     }
   }

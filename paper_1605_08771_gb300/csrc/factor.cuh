@@ -6,6 +6,7 @@
 
 #include "common.cuh"
 #include "gemm.cuh"
+#include "tc_update.cuh"
 
 namespace feast {
 
@@ -24,6 +25,9 @@ struct PanelWork {
   int* swap_src;        // [nodes][2*kPanel]
   int* swap_dst;        // [nodes][2*kPanel]
   int* swap_cnt;        // [nodes]
+  int* blk_src;         // [nodes][2*kTcBlock] block interchange summary (two-level LU)
+  int* blk_dst;
+  int* blk_cnt;         // [nodes]
   int pmax;
   void* tc_planes;      // complex-FP32 factors: scratch of the tensor-core trailing update
 };
