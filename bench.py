@@ -301,7 +301,7 @@ def run_ours(args, rank, world, dev):
 
     line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 2), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "c64+df32" if w["prec"] == "mixed" else "c128",
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64+df32" if w["prec"] != "f64" else "c128",
             "data": "synthetic planted spectrum (seeded), no dataset",
             "config": {"workload": workload_name(w), "n": n, "m0": m0, "n_c": nc, "variant": w["variant"],
                        "s": w["s"], "prec": w["prec"], "tol": w["tol"],
@@ -319,7 +319,7 @@ def run_ours(args, rank, world, dev):
             "gpu_launches": int(launches), "clocks": clocks, "peak_source": peak_kind}
 
     # mixed vs FP64 on the same input (one untimed-by-steps solve, CUDA events)
-    if args.fp64 and w["prec"] == "mixed":
+    if args.fp64 and w["prec"] != "f64":
         o64 = fg.feast_opts_default(variant=w["variant"], s=w["s"], prec="f64", anorm=anorm, max_iter=30)
         barrier()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -408,7 +408,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=0, help="override n (scaled workload, for quick checks)")
-    ap.add_argument("--prec", default="mixed", choices=["mixed", "f64"])
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "mixed_tc", "f64"])
     ap.add_argument("--variant", default="rfeast", choices=["feast", "xfeast", "rfeast"])
     ap.add_argument("--no-fp64", dest="fp64", action="store_false")
     ap.add_argument("--no-cpu", dest="cpu", action="store_false")

@@ -48,8 +48,12 @@ enum { FEAST_PLAIN = 0,  /* FEAST Algorithm (Appendix) */
        FEAST_RFEAST = 2  /* expanding subspace with Ritz residuals (Sect. II-B) */ };
 
 /* arithmetic of the shifted factorisations and solves */
-enum { FEAST_PREC_F64 = 0,  /* complex FP64 LU and solves */
-       FEAST_PREC_MIXED = 1 /* complex FP32 LU and solves, FP64 iterative refinement */ };
+enum { FEAST_PREC_F64 = 0,      /* complex FP64 LU and solves */
+       FEAST_PREC_MIXED = 1,    /* complex FP32 LU and solves, FP64 iterative refinement */
+       FEAST_PREC_MIXED_TC = 2  /* as FEAST_PREC_MIXED, the LU's trailing updates on the
+                                   tensor cores (4xTF32 split products, FP32 accumulate):
+                                   slightly less accurate factors, so refinement may take
+                                   one more step */ };
 
 /* status codes */
 #define FEAST_OK 0
@@ -66,7 +70,7 @@ enum { FEAST_PREC_F64 = 0,  /* complex FP64 LU and solves */
 typedef struct {
   int variant;          /* FEAST_PLAIN (default), FEAST_XFEAST, FEAST_RFEAST */
   int s;                /* XFEAST window blocks / RFEAST Rayleigh-Ritz passes (default 3) */
-  int prec;             /* FEAST_PREC_F64 (default) or FEAST_PREC_MIXED */
+  int prec;             /* FEAST_PREC_F64 (default), FEAST_PREC_MIXED or FEAST_PREC_MIXED_TC */
   int max_iter;         /* maximum outer iterations (default 100) */
   int refine_max;       /* mixed: maximum refinement steps per filter (default 10) */
   int reserved;
@@ -150,7 +154,7 @@ int feast_filter_apply(feast_ctx* ctx, const void* A, int dtype, int64_t n, int6
 
 /* LU with partial pivoting of M_e = z_e I - A for nz shifts z (host, 2*nz
  * doubles).  LU: device nz * n * n complex elements (complex double for
- * FEAST_PREC_F64, complex float for FEAST_PREC_MIXED), factor e at offset
+ * FEAST_PREC_F64, complex float for the mixed precisions), factor e at offset
  * e*n*n, unit-lower L below the diagonal, U on and above it.  perm: device
  * nz*n int32, perm[e*n + i] = row of M_e now at row i (P M_e = L U). */
 int feast_shifted_lu(feast_ctx* ctx, const void* A, int dtype, int64_t n, int64_t lda,

@@ -21,11 +21,11 @@ from .build import LIB, build as build_library  # noqa: F401
 
 FEAST_R64, FEAST_C128 = 0, 1
 FEAST_PLAIN, FEAST_XFEAST, FEAST_RFEAST = 0, 1, 2
-FEAST_PREC_F64, FEAST_PREC_MIXED = 0, 1
+FEAST_PREC_F64, FEAST_PREC_MIXED, FEAST_PREC_MIXED_TC = 0, 1, 2
 FEAST_OK, FEAST_WARN_MAXITER = 0, 1
 
 VARIANTS = {"feast": FEAST_PLAIN, "xfeast": FEAST_XFEAST, "rfeast": FEAST_RFEAST}
-PRECS = {"f64": FEAST_PREC_F64, "mixed": FEAST_PREC_MIXED}
+PRECS = {"f64": FEAST_PREC_F64, "mixed": FEAST_PREC_MIXED, "mixed_tc": FEAST_PREC_MIXED_TC}
 
 EXPORTS = [
     "feast_opts_default", "feast_init", "feast_finalize", "feast_strerror",

@@ -263,7 +263,7 @@ struct Solver {
     perm = dalloc<int32_t>(ctx, (int64_t)nc * n);
     const int pmax = std::max(1, ctx->num_sms * 8);
     pw = panel_work_carve(ctx->arena.alloc(panel_work_bytes(nc, pmax, eb)), nc, pmax, eb);
-    if (o.prec == FEAST_PREC_MIXED) pw.tc_planes = ctx->arena.alloc(tc_update_planes_bytes(n, nc));
+    if (o.prec == FEAST_PREC_MIXED_TC) pw.tc_planes = ctx->arena.alloc(tc_update_planes_bytes(n, nc));
   }
   void alloc_filter(int64_t m) {
     const int64_t nm = n * m;
@@ -347,7 +347,7 @@ struct Solver {
   }
   // A times a block: FP64 on the FP64 path, double-float on the mixed path
   void apply_A(const S* Xm, int64_t k, S* Out) {
-    if (o.prec == FEAST_PREC_MIXED && Apl && k <= bpl_cols) {
+    if (o.prec != FEAST_PREC_F64 && Apl && k <= bpl_cols) {
       apply_A_df((const double*)Xm, kCplx, k, (double*)Out);
       return;
     }
@@ -640,7 +640,7 @@ struct Solver {
   // residual is above o.refine_switch and still falling at least tenfold per
   // iteration (a filter accurate to FP32 cannot be what limits it then)
   void update_refine(const std::vector<double>& hist) {
-    if (o.prec != FEAST_PREC_MIXED || o.refine_switch <= 0.0) { refine_now = true; return; }
+    if (o.prec == FEAST_PREC_F64 || o.refine_switch <= 0.0) { refine_now = true; return; }
     const double r = hist.back();
     const double prev = hist.size() >= 2 ? hist[hist.size() - 2] : INFINITY;
     refine_now = !(r > o.refine_switch && r < 0.1 * prev);
@@ -968,7 +968,7 @@ int solve_t(feast_ctx* ctx, const S* A, int64_t n, int64_t lda, double lmin, dou
   sv.alloc_factors();
   sv.anorm = o.anorm > 0 ? o.anorm : sv.estimate_norm();
   if (!(sv.anorm > 0)) sv.anorm = 1.0;
-  sv.refine_now = !(o.prec == FEAST_PREC_MIXED && o.refine_switch > 0.0);
+  sv.refine_now = !(o.prec != FEAST_PREC_F64 && o.refine_switch > 0.0);
   S* X = dalloc<S>(ctx, n * m0);
   if (o.x0) {
     copy_matrix<S>(X, n, (const S*)o.x0, n, n, m0, ctx->stream);
@@ -1113,7 +1113,7 @@ int feast_interval_solve(feast_ctx* ctx, const void* A, int dtype, int64_t n, in
   if (m0 < 1 || m0 > n || !(tol > 0) || !evals || !evecs || !res || !m_found || !iterations) return FEAST_ERR_ARG;
   feast_opts o;
   if (opts) o = *opts; else feast_opts_default(&o);
-  if (o.variant < 0 || o.variant > 2 || o.prec < 0 || o.prec > 1 || o.max_iter < 1 || !(o.aspect > 0)) return FEAST_ERR_ARG;
+  if (o.variant < 0 || o.variant > 2 || o.prec < 0 || o.prec > 2 || o.max_iter < 1 || !(o.aspect > 0)) return FEAST_ERR_ARG;
   if (o.variant != FEAST_PLAIN && (o.s < 1 || (int64_t)o.s * m0 > 65536)) return FEAST_ERR_ARG;
   if (o.refine_max < 0 || !(o.refine_switch >= 0.0)) return FEAST_ERR_ARG;
   *m_found = 0;
@@ -1134,7 +1134,7 @@ int feast_filter_apply(feast_ctx* ctx, const void* A, int dtype, int64_t n, int6
   if (!X || !Y || m < 1) return FEAST_ERR_ARG;
   feast_opts o;
   if (opts) o = *opts; else feast_opts_default(&o);
-  if (o.prec < 0 || o.prec > 1 || !(o.aspect > 0) || o.refine_max < 0) return FEAST_ERR_ARG;
+  if (o.prec < 0 || o.prec > 2 || !(o.aspect > 0) || o.refine_max < 0) return FEAST_ERR_ARG;
   return guarded(ctx, [&]() {
     FEAST_CUDA_TRY(cudaSetDevice(ctx->device));
     ctx->arena.reset();
@@ -1150,7 +1150,7 @@ int feast_filter_apply(feast_ctx* ctx, const void* A, int dtype, int64_t n, int6
       sv.d_nrm = dalloc<double>(ctx, 1);
       sv.d_scale = dalloc<double>(ctx, 1);
       sv.d_idx = dalloc<int>(ctx, 1);
-      sv.anorm = o.anorm > 0 ? o.anorm : (o.prec == FEAST_PREC_MIXED ? sv.estimate_norm() : 1.0);
+      sv.anorm = o.anorm > 0 ? o.anorm : (o.prec != FEAST_PREC_F64 ? sv.estimate_norm() : 1.0);
       sv.factor();
       sv.filter((const S*)X, m, (S*)Y);
       sync(ctx);
@@ -1166,14 +1166,14 @@ int feast_filter_apply(feast_ctx* ctx, const void* A, int dtype, int64_t n, int6
 int feast_shifted_lu(feast_ctx* ctx, const void* A, int dtype, int64_t n, int64_t lda, const double* z, int nz,
                      int prec, void* LU, int32_t* perm) {
   if (int r = check_common(ctx, A, dtype, n, lda, -1.0, 1.0, nz)) return r;
-  if (!z || !LU || !perm || (prec != FEAST_PREC_F64 && prec != FEAST_PREC_MIXED)) return FEAST_ERR_ARG;
+  if (!z || !LU || !perm || (prec < FEAST_PREC_F64 || prec > FEAST_PREC_MIXED_TC)) return FEAST_ERR_ARG;
   return guarded(ctx, [&]() {
     FEAST_CUDA_TRY(cudaSetDevice(ctx->device));
     ctx->arena.reset();
     const size_t eb = prec == FEAST_PREC_F64 ? sizeof(c128) : sizeof(c64);
     const int pmax = std::max(1, ctx->num_sms * 8);
     PanelWork pw = panel_work_carve(ctx->arena.alloc(panel_work_bytes(nz, pmax, eb)), nz, pmax, eb);
-    if (prec == FEAST_PREC_MIXED) pw.tc_planes = ctx->arena.alloc(tc_update_planes_bytes(n, nz));
+    if (prec == FEAST_PREC_MIXED_TC) pw.tc_planes = ctx->arena.alloc(tc_update_planes_bytes(n, nz));
     c128* dz = dalloc<c128>(ctx, nz);
     to_dev(ctx, dz, (const c128*)z, nz);
     int32_t* ipiv = dalloc<int32_t>(ctx, (int64_t)nz * n);
@@ -1199,7 +1199,7 @@ int feast_shifted_lu(feast_ctx* ctx, const void* A, int dtype, int64_t n, int64_
 int feast_shifted_solve(feast_ctx* ctx, const void* LU, const int32_t* perm, int64_t n, int nz, int prec, int adjoint,
                         const void* B, int64_t m, void* Y) {
   if (!ctx || !LU || !perm || !B || !Y || n < 1 || nz < 1 || m < 1) return FEAST_ERR_ARG;
-  if (prec != FEAST_PREC_F64 && prec != FEAST_PREC_MIXED) return FEAST_ERR_ARG;
+  if (prec < FEAST_PREC_F64 || prec > FEAST_PREC_MIXED_TC) return FEAST_ERR_ARG;
   return guarded(ctx, [&]() {
     FEAST_CUDA_TRY(cudaSetDevice(ctx->device));
     ctx->arena.reset();

@@ -7,13 +7,14 @@
 // row 2i+1 holds [Im L_i, Re L_i], and the right operand is [Re U; Im U], so
 // real row 2i of the product is Re(L U)_i and row 2i+1 is Im(L U)_i -- the
 // interleaved complex layout of A22 itself.  Each FP32 operand is split into
-// a TF32 head and a TF32 tail, hi = rna(a), lo = rna(a - hi), so that
-// |a - hi - lo| <= 2^-24 |a|; the four TF32 products hi*hi + hi*lo + lo*hi +
-// lo*lo accumulate in FP32 in tensor memory.  (Dropping lo*lo, as 3xTF32
-// does, leaves 2^-22 |a||b| per product; measured on the n = 8192 workload
-// that made the first refined residual 3.4x larger than with FP32 factors and
-// cost an extra refinement step.)  The factors are thereby as accurate as
-// FP32 ones, so the FP64 refinement contracts by the same factor per step.
+// three TF32 parts, hi = rna(a), mid = rna(a - hi), lo = rna(a - hi - mid);
+// the subtractions are exact and 3 x 11 significand bits cover FP32's 24, so
+// hi + mid + lo == a.  Six TF32 products -- hi*hi, hi*mid, mid*hi, hi*lo,
+// lo*hi, mid*mid -- accumulate in FP32 in tensor memory; the dropped ones are
+// below 2^-32 |a||b|.  (A two-part split, hi + rna(a - hi), keeps only about
+// 22 bits of each operand: measured on the n = 8192 workload its factors
+// made the first refined residual 3.5x larger than FP32 factors do, with or
+// without the lo*lo product, and cost an extra refinement step.)
 //
 // Kernel: one 128 x 128 output tile per CTA, four warps.  Thread 0 issues the
 // TMA loads of the 128B-swizzled K-major operand tiles, thread 32 issues the
@@ -22,13 +23,11 @@
 // for the epilogue A22 -= D.  Every mbarrier wait is bounded by a wall-clock
 // limit; on expiry the kernel records the failure, lets the issued MMAs
 // complete, frees its TMEM and skips the stores.
-#include <cuda.h>
-#include <cudaTypedefs.h>
-
 #include <mutex>
 
 #include "factor.cuh"
 #include "tc_update.cuh"
+#include "tcgen05.cuh"
 
 namespace feast {
 
@@ -37,45 +36,9 @@ namespace {
 constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 32;  // BK fp32 = 128 bytes = one swizzle row
 constexpr int TC_STAGES = 2;
 constexpr int TC_TILE_BYTES = TC_BM * TC_BK * 4;     // 16 KB per operand tile (BN == BM)
-constexpr int TC_STAGE_BYTES = 4 * TC_TILE_BYTES;    // A_hi, A_lo, B_hi, B_lo
+constexpr int TC_STAGE_BYTES = 6 * TC_TILE_BYTES;    // A hi/mid/lo, B hi/mid/lo
 constexpr int TC_SMEM_BYTES = TC_STAGES * TC_STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
 constexpr int TC_TMEM_COLS = 128;
-constexpr unsigned long long kTcWaitNs = 2000000000ull;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  const unsigned long long t0 = globaltimer_ns();
-  while (true) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if (globaltimer_ns() - t0 > kTcWaitNs) return false;
-  }
-}
-
-// SWIZZLE_128B K-major shared-memory matrix descriptor (sm_100 family):
-// start address >> 4 in bits 0-13, leading offset (unused for swizzled
-// K-major) 1, stride offset 1024 B (one 8-row swizzle atom) >> 4 in bits
-// 32-45, descriptor version 1 in bits 46-47, layout SWIZZLE_128B (2) in 61-63.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(1024 >> 4) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
-  return d;
-}
-
 // Instruction descriptor, kind::tf32: D = F32 (bits 4-5 = 1), A = B = TF32
 // (bits 7-9, 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 in 17-22,
 // M >> 4 in 24-28.
@@ -92,24 +55,10 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t da, uint64_t db
       : "memory");
 }
 
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-               : "memory");
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-      :
-      : "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
-      : "memory");
-}
-
 __global__ void __launch_bounds__(128, 1)
-tc_update_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
-                 const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, c64* M,
+tc_update_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, c64* M,
                  int64_t ld, int64_t stride, int64_t r1, int64_t R, int64_t C, int rows_pad, int cols_pad,
-                 int ksteps, int nodes, int* status) {
+                 int ksteps, int nodes, int a_part_rows, int b_part_rows, int* status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = (uint64_t*)(smem + TC_STAGES * TC_STAGE_BYTES);  // full[2], empty[2], done
@@ -151,7 +100,8 @@ tc_update_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant
     const int col0 = node * cols_pad + nt * TC_BN;  // TMA row of the right operand
     const int gbase = it * ksteps;
     if (threadIdx.x == 0 && !s_fail) {
-      // producer: TMA loads of the four operand tiles of each k-step
+      // producer: TMA loads of the six operand tiles of each k-step (the
+      // three parts of each operand are consecutive row blocks of one map)
       for (int ks = 0; ks < ksteps; ++ks) {
         const int g = gbase + ks, s = g % TC_STAGES;
         if (g >= TC_STAGES && !mbar_wait(bar_empty + 8 * s, ((g / TC_STAGES) - 1) & 1)) {
@@ -163,13 +113,15 @@ tc_update_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant
                      "r"(TC_STAGE_BYTES)
                      : "memory");
         const int x = ks * TC_BK;
-        tma_load_2d(smem_u32(st), &tmAh, x, row0, bar_full + 8 * s);
-        tma_load_2d(smem_u32(st + TC_TILE_BYTES), &tmAl, x, row0, bar_full + 8 * s);
-        tma_load_2d(smem_u32(st + 2 * TC_TILE_BYTES), &tmBh, x, col0, bar_full + 8 * s);
-        tma_load_2d(smem_u32(st + 3 * TC_TILE_BYTES), &tmBl, x, col0, bar_full + 8 * s);
+#pragma unroll
+        for (int part = 0; part < 3; ++part) {
+          tma_load_2d(smem_u32(st + part * TC_TILE_BYTES), &tmA, x, part * a_part_rows + row0, bar_full + 8 * s);
+          tma_load_2d(smem_u32(st + (3 + part) * TC_TILE_BYTES), &tmB, x, part * b_part_rows + col0,
+                      bar_full + 8 * s);
+        }
       }
     } else if (threadIdx.x == 32) {
-      // MMA issuer: 4 k-steps of 8 per stage, 4 products each (4xTF32)
+      // MMA issuer: 4 k-steps of 8 per stage, 6 split products each
       for (int ks = 0; ks < ksteps && !s_fail; ++ks) {
         const int g = gbase + ks, s = g % TC_STAGES;
         if (!mbar_wait(bar_full + 8 * s, (g / TC_STAGES) & 1)) {
@@ -181,13 +133,17 @@ tc_update_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant
 #pragma unroll
         for (int kk = 0; kk < TC_BK / 8; ++kk) {
           const uint32_t off = kk * 32;  // 8 tf32 = 32 bytes along K inside the swizzle row
-          const uint64_t ah = sw128_desc(base + off), al = sw128_desc(base + TC_TILE_BYTES + off);
-          const uint64_t bh = sw128_desc(base + 2 * TC_TILE_BYTES + off),
-                         bl = sw128_desc(base + 3 * TC_TILE_BYTES + off);
+          const uint64_t ah = sw128_desc(base + off), am = sw128_desc(base + TC_TILE_BYTES + off),
+                         al = sw128_desc(base + 2 * TC_TILE_BYTES + off);
+          const uint64_t bh = sw128_desc(base + 3 * TC_TILE_BYTES + off),
+                         bm = sw128_desc(base + 4 * TC_TILE_BYTES + off),
+                         bl = sw128_desc(base + 5 * TC_TILE_BYTES + off);
           mma_tf32(tmem, ah, bh, (ks > 0 || kk > 0) ? 1u : 0u);
+          mma_tf32(tmem, ah, bm, 1u);
+          mma_tf32(tmem, am, bh, 1u);
           mma_tf32(tmem, ah, bl, 1u);
           mma_tf32(tmem, al, bh, 1u);
-          mma_tf32(tmem, al, bl, 1u);
+          mma_tf32(tmem, am, bm, 1u);
         }
         mma_commit(bar_empty + 8 * s);  // frees the stage when these MMAs are done
       }
@@ -248,14 +204,22 @@ __device__ __forceinline__ float tf32_rna(float x) {
   return __uint_as_float(r);
 }
 
+// three-part TF32 split of an FP32 value: hi + mid + lo == x exactly
+__device__ __forceinline__ void tf32_split3(float x, float& h, float& m, float& l) {
+  h = tf32_rna(x);
+  const float r = x - h;  // exact
+  m = tf32_rna(r);
+  l = tf32_rna(r - m);    // r - m exact, and it has at most 11 significant bits
+}
+
 // Operand packing: left operand (rows_pad real rows x Kp) from L21 and right
-// operand (cols_pad rows x Kp) from U12, each as TF32 head/tail planes, K
-// contiguous (Kp >= 2 kb).  32 x 32 complex tiles are staged through shared
-// memory so both the reads of the column-major factor and the writes of the
-// K-major planes are coalesced.
+// operand (cols_pad rows x Kp) from U12, each as three TF32 planes (hi, mid,
+// lo; plane stride a_part / b_part floats), K contiguous (Kp >= 2 kb).
+// 32 x 32 complex tiles are staged through shared memory so both the reads of
+// the column-major factor and the writes of the K-major planes are coalesced.
 __global__ void tc_pack_kernel(const c64* M, int64_t ld, int64_t stride, int64_t k0, int kb, int64_t r1, int64_t R,
-                               int64_t C, int rows_pad, int cols_pad, int Kp, float* Ah, float* Al, float* Bh,
-                               float* Bl) {
+                               int64_t C, int rows_pad, int cols_pad, int Kp, float* A, int64_t a_part, float* B,
+                               int64_t b_part) {
   __shared__ c64 tile[32][33];
   const int node = blockIdx.z;
   const c64* Mb = M + (int64_t)node * stride;
@@ -285,10 +249,8 @@ __global__ void tc_pack_kernel(const c64* M, int64_t ld, int64_t stride, int64_t
         if (c < 32) { val = part ? L.im : L.re; kk = kc + k; }
         else { val = part ? L.re : -L.im; kk = kb + kc + k; }
         if (kc + k >= kb) continue;
-        const float h = tf32_rna(val);
         const int64_t o = ((int64_t)node * rows_pad + 2 * base + rl) * Kp + kk;
-        Ah[o] = h;
-        Al[o] = tf32_rna(val - h);
+        tf32_split3(val, A[o], A[a_part + o], A[2 * a_part + o]);
       }
     } else {
       for (int t = threadIdx.x; t < 32 * 64; t += blockDim.x) {
@@ -297,10 +259,8 @@ __global__ void tc_pack_kernel(const c64* M, int64_t ld, int64_t stride, int64_t
         const c64 U = tile[q][k];
         const float val = (c < 32) ? U.re : U.im;
         const int kk = (c < 32) ? kc + k : kb + kc + k;
-        const float h = tf32_rna(val);
         const int64_t o = ((int64_t)node * cols_pad + base + q) * Kp + kk;
-        Bh[o] = h;
-        Bl[o] = tf32_rna(val - h);
+        tf32_split3(val, B[o], B[b_part + o], B[2 * b_part + o]);
       }
     }
   }
@@ -308,32 +268,20 @@ __global__ void tc_pack_kernel(const c64* M, int64_t ld, int64_t stride, int64_t
   if (2 * kb < Kp) {
     const int rowsb = left ? 64 : 32;
     const int64_t rbase = left ? (int64_t)node * rows_pad + 2 * base : (int64_t)node * cols_pad + base;
-    float* H = left ? Ah : Bh;
-    float* Lo = left ? Al : Bl;
+    float* P = left ? A : B;
+    const int64_t ps = left ? a_part : b_part;
     for (int t = threadIdx.x; t < rowsb * (Kp - 2 * kb); t += blockDim.x) {
       const int kk = 2 * kb + t % (Kp - 2 * kb), rl = t / (Kp - 2 * kb);
-      H[(rbase + rl) * Kp + kk] = 0.f;
-      Lo[(rbase + rl) * Kp + kk] = 0.f;
+      const int64_t o = (rbase + rl) * Kp + kk;
+      P[o] = 0.f;
+      P[ps + o] = 0.f;
+      P[2 * ps + o] = 0.f;
     }
   }
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-  });
-  return fn;
-}
-
 void make_map(CUtensorMap* map, float* base, int64_t rows, int Kp) {
-  auto fn = encode_fn();
+  auto fn = tensor_map_encode_fn();
   if (!fn) throw CudaFailure(cudaErrorNotSupported);
   cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)Kp * 4};
@@ -347,10 +295,24 @@ void make_map(CUtensorMap* map, float* base, int64_t rows, int Kp) {
 
 }  // namespace
 
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  });
+  return fn;
+}
+
 size_t tc_update_planes_bytes(int64_t n, int nodes) {
   const int64_t rp = cdiv(2 * n, TC_BM) * TC_BM, cp = cdiv(n, TC_BN) * TC_BN;
   const int64_t Kp = cdiv(2 * kTcBlock, TC_BK) * TC_BK;
-  return (size_t)4 * 2 * (size_t)nodes * (size_t)(rp + cp) * (size_t)Kp + 4096;
+  return (size_t)4 * 3 * (size_t)nodes * (size_t)(rp + cp) * (size_t)Kp + 4096;
 }
 
 void tc_trailing_update(c64* M, int64_t n, int64_t ld, int64_t stride, int nodes, int64_t k0, int kb, void* planes,
@@ -361,21 +323,19 @@ void tc_trailing_update(c64* M, int64_t n, int64_t ld, int64_t stride, int nodes
   const int rows_pad = (int)(cdiv(2 * R, TC_BM) * TC_BM);
   const int cols_pad = (int)(cdiv(C, TC_BN) * TC_BN);
   const int Kp = (int)(cdiv(2 * kb, TC_BK) * TC_BK);
-  float* Ah = (float*)planes;
-  float* Al = Ah + (int64_t)nodes * rows_pad * Kp;
-  float* Bh = Al + (int64_t)nodes * rows_pad * Kp;
-  float* Bl = Bh + (int64_t)nodes * cols_pad * Kp;
+  const int64_t a_rows = (int64_t)nodes * rows_pad, b_rows = (int64_t)nodes * cols_pad;
+  float* A = (float*)planes;           // 3 planes of a_rows x Kp
+  float* B = A + 3 * a_rows * Kp;      // 3 planes of b_rows x Kp
   {
     const int64_t blocks = std::max<int64_t>(rows_pad / 64, cols_pad / 32);
     dim3 g((unsigned)blocks, 2, nodes);
-    tc_pack_kernel<<<g, 256, 0, s>>>(M, ld, stride, k0, kb, r1, R, C, rows_pad, cols_pad, Kp, Ah, Al, Bh, Bl);
+    tc_pack_kernel<<<g, 256, 0, s>>>(M, ld, stride, k0, kb, r1, R, C, rows_pad, cols_pad, Kp, A, a_rows * Kp, B,
+                                     b_rows * Kp);
     FEAST_LAUNCH_CHECK();
   }
-  CUtensorMap mAh, mAl, mBh, mBl;
-  make_map(&mAh, Ah, (int64_t)nodes * rows_pad, Kp);
-  make_map(&mAl, Al, (int64_t)nodes * rows_pad, Kp);
-  make_map(&mBh, Bh, (int64_t)nodes * cols_pad, Kp);
-  make_map(&mBl, Bl, (int64_t)nodes * cols_pad, Kp);
+  CUtensorMap mA, mB;
+  make_map(&mA, A, 3 * a_rows, Kp);
+  make_map(&mB, B, 3 * b_rows, Kp);
   static bool attr = false;
   if (!attr) {
     FEAST_CUDA_TRY(cudaFuncSetAttribute(tc_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES));
@@ -383,8 +343,8 @@ void tc_trailing_update(c64* M, int64_t n, int64_t ld, int64_t stride, int nodes
   }
   const int64_t tiles = (int64_t)(rows_pad / TC_BM) * (cols_pad / TC_BN) * nodes;
   const unsigned grid = (unsigned)std::min<int64_t>(tiles, num_sms);
-  tc_update_kernel<<<grid, 128, TC_SMEM_BYTES, s>>>(mAh, mAl, mBh, mBl, M, ld, stride, r1, R, C, rows_pad, cols_pad,
-                                                    Kp / TC_BK, nodes, status);
+  tc_update_kernel<<<grid, 128, TC_SMEM_BYTES, s>>>(mA, mB, M, ld, stride, r1, R, C, rows_pad, cols_pad, Kp / TC_BK,
+                                                    nodes, (int)a_rows, (int)b_rows, status);
   FEAST_LAUNCH_CHECK();
 }
 

@@ -1,4 +1,4 @@
-// Tensor-core (tcgen05, 4xTF32) trailing update of the complex-FP32 shifted LU.
+// Tensor-core (tcgen05, split-TF32) trailing update of the complex-FP32 shifted LU.
 #pragma once
 
 #include "common.cuh"
@@ -9,7 +9,7 @@ namespace feast {
 // cores (K = 2 * kTcBlock real).
 constexpr int kTcBlock = 128;
 
-// Scratch bytes of the TF32 head/tail operand planes for matrices of order
+// Scratch bytes of the three TF32 operand planes for matrices of order
 // up to n, `nodes` shifts and blocks of up to kTcBlock columns.
 size_t tc_update_planes_bytes(int64_t n, int nodes);
 

@@ -34,7 +34,7 @@ def check_against_planted(out, P, tol=1e-10):
 
 @pytest.mark.parametrize("vname,vor", VARIANTS)
 @pytest.mark.parametrize("cplx", [False, True])
-@pytest.mark.parametrize("prec", ["f64", "mixed"])
+@pytest.mark.parametrize("prec", ["f64", "mixed", "mixed_tc"])
 def test_small_planted_vs_oracle(ctx, vname, vor, cplx, prec):
     lam, a, b = spectrum_uniform(90, 8, seed=3, bulk=10.0)
     P = make_problem("s", lam, a, b, 12, 8, seed=3, complex_=cplx)

@@ -15,13 +15,16 @@ ZS = np.array([0.3 + 0.5j, -0.7 + 0.2j, 1.1 + 0.05j])
 SIZES = [1, 2, 31, 32, 33, 65, 100, 257]
 
 
+PRECS_ALL = [fg.FEAST_PREC_F64, fg.FEAST_PREC_MIXED, fg.FEAST_PREC_MIXED_TC]
+
+
 @pytest.mark.parametrize("n", SIZES + [520])
 @pytest.mark.parametrize("cplx", [False, True])
-@pytest.mark.parametrize("prec", [fg.FEAST_PREC_F64, fg.FEAST_PREC_MIXED])
+@pytest.mark.parametrize("prec", PRECS_ALL)
 def test_shifted_lu_matches_oracle(ctx, n, cplx, prec):
-    # the complex-FP32 factors run the two-level LU whose 128-column outer
-    # updates use the tensor cores: n = 257 and 520 span several outer blocks
-    # and a ragged tail
+    # FEAST_PREC_MIXED_TC runs the two-level LU whose 128-column outer updates
+    # use the tensor cores: n = 257 and 520 span several outer blocks and a
+    # ragged tail
     A = rand_hermitian(n, cplx, seed=n)
     LU, perm = fg.feast_shifted_lu(ctx, cuda(A), ZS, prec)
     LU, perm = host(LU).astype(np.complex128), host(perm)
@@ -44,7 +47,7 @@ def test_shifted_lu_matches_oracle(ctx, n, cplx, prec):
 @pytest.mark.parametrize("n", [1, 33, 100, 257])
 @pytest.mark.parametrize("cplx", [False, True])
 @pytest.mark.parametrize("adjoint", [False, True])
-@pytest.mark.parametrize("prec", [fg.FEAST_PREC_F64, fg.FEAST_PREC_MIXED])
+@pytest.mark.parametrize("prec", PRECS_ALL)
 def test_shifted_solve_matches_oracle(ctx, n, cplx, adjoint, prec):
     A = rand_hermitian(n, cplx, seed=7 * n + 1)
     B = rand_mat(n, 5, True, seed=n)
@@ -58,7 +61,7 @@ def test_shifted_solve_matches_oracle(ctx, n, cplx, adjoint, prec):
 
 
 @pytest.mark.parametrize("cplx", [False, True])
-@pytest.mark.parametrize("prec", [fg.FEAST_PREC_F64, fg.FEAST_PREC_MIXED])
+@pytest.mark.parametrize("prec", PRECS_ALL)
 @pytest.mark.parametrize("n_c", [3, 8])
 def test_filter_matches_oracle_and_closed_form(ctx, cplx, prec, n_c):
     lam, a, b = spectrum_uniform(150, 10, seed=11, bulk=20.0)
