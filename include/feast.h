@@ -73,7 +73,9 @@ typedef struct {
   int prec;             /* FEAST_PREC_F64 (default), FEAST_PREC_MIXED or FEAST_PREC_MIXED_TC */
   int max_iter;         /* maximum outer iterations (default 100) */
   int refine_max;       /* mixed: maximum refinement steps per filter (default 10) */
-  int reserved;
+  int refine_gemm;      /* mixed: the FP64-accurate products A Y of the refinement on the
+                           tensor cores (0, default: bf16 digit split, Ozaki scheme) or
+                           in double-float arithmetic on the FP32 pipes (1) */
   double aspect;        /* ellipse vertical / horizontal semi-axis (default 1: circle) */
   double anorm;         /* ||A||_2 when > 0; otherwise 40 power iterations estimate it */
   double refine_tol;    /* mixed: stop when ||R||_F <= refine_tol (||A|| + |z|) ||Y||_F;
@@ -97,10 +99,10 @@ typedef struct {
   double total_ms;      /* whole solve */
   double max_residual;  /* max relative residual of the returned pairs */
   double history[128];  /* max residual per iteration (first 128) */
-  double gemm_df_ms;    /* mixed: summed device time (CUDA events) of the double-float
-                           GEMM launches, the dominant kernel of the mixed path */
-  double gemm_df_mac;   /* their real multiply-adds (M*N*K summed over launches) */
-  int gemm_df_launches; /* their number */
+  double refine_gemm_ms;    /* mixed: summed device time (CUDA events) of the FP64-accurate
+                               refinement GEMM launches */
+  double refine_gemm_mac;   /* their real multiply-adds (M*N*K summed over launches) */
+  int refine_gemm_launches; /* their number */
   int reserved2;
 } feast_stats;
 
@@ -187,6 +189,22 @@ int feast_jacobi_eigh(feast_ctx* ctx, int dtype, int64_t k, const void* H, doubl
 int feast_rayleigh_ritz(feast_ctx* ctx, const void* A, int dtype, int64_t n, int64_t lda,
                         const void* Q, int64_t k, double anorm, double* evals, void* X,
                         double* res);
+
+/* C = A B for real FP64 matrices, column major on the device: A is M x K
+ * (leading dim lda >= M), B is K x N (ldb >= K), C is M x N (ldc >= M, not
+ * aliasing A or B).  This is the FP64-accurate product A Y that the mixed
+ * precision's iterative refinement needs for its residual R = X - (zI - A) Y
+ * (the refinement itself is not in the paper, which solves in full
+ * precision).  method 0: bf16 tensor cores with error-free digit splitting
+ * (Ozaki scheme: six 8-bit digits per element with a per-row / per-column
+ * exponent, 21 digit products accumulated exactly in 128-long K chunks),
+ * error about 2^-47 sum_k 2^(e_i + f_j) where 2^e_i > max_k |A_ik| and
+ * 2^f_j > max_k |B_kj|; method 1: double-float arithmetic on the FP32 pipes,
+ * error about 2^-44 sum_k |A_ik| |B_kj|.  Scratch comes from the context.
+ * Returns FEAST_ERR_ARG for M, N or K < 1, bad leading dimensions or method,
+ * FEAST_ERR_TIMEOUT when a bounded device wait gave up. */
+int feast_gemm_f64acc(feast_ctx* ctx, int method, int64_t M, int64_t N, int64_t K, const double* A, int64_t lda,
+                      const double* B, int64_t ldb, double* C, int64_t ldc);
 
 /* Allocation-free Jacobi eigensolver, for callers that cannot allocate device
  * memory at call time: code running while a CUDA stream is captured, services

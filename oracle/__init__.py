@@ -11,6 +11,8 @@ Modules:
               orthogonalisation, Jacobi eigensolver
   feast       filter application, Rayleigh-Ritz, selection, FEAST / XFEAST /
               RFEAST drivers (Appendix algorithms)
+  exact       correctly rounded FP64 dot products (TwoProduct + exact
+              summation): reference of the FP64-accurate refinement products
 
 Parity pins: every function is checked in tests/test_oracle_*.py against
 closed forms, brute force or independent library routines.  The XFEAST and
@@ -25,3 +27,4 @@ from .dense import (lu_factor, lu_solve, lu_solve_adjoint, lu_unpack,  # noqa: F
 from .feast import (factor_shifts, filter_apply, rayleigh_ritz, select_pairs,  # noqa: F401
                     feast_solve, norm_estimate, orthonormalize, FeastResult,
                     PLAIN, XFEAST, RFEAST)
+from .exact import two_prod, dot_exact, matmul_entries  # noqa: F401

@@ -32,12 +32,13 @@ EXPORTS = [
     "feast_contour_nodes", "feast_interval_solve", "feast_filter_apply",
     "feast_shifted_lu", "feast_shifted_solve", "feast_orthonormalize",
     "feast_jacobi_eigh", "feast_rayleigh_ritz", "feast_kernel_launches", "feast_jacobi_eigh_noalloc",
+    "feast_gemm_f64acc",
 ]
 
 
 class FeastOpts(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int), ("s", ctypes.c_int), ("prec", ctypes.c_int),
-                ("max_iter", ctypes.c_int), ("refine_max", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("max_iter", ctypes.c_int), ("refine_max", ctypes.c_int), ("refine_gemm", ctypes.c_int),
                 ("aspect", ctypes.c_double), ("anorm", ctypes.c_double), ("refine_tol", ctypes.c_double),
                 ("seed", ctypes.c_ulonglong), ("x0", ctypes.c_void_p), ("refine_switch", ctypes.c_double)]
 
@@ -46,8 +47,9 @@ class FeastStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("filters", ctypes.c_int), ("refine_steps", ctypes.c_int),
                 ("m_expected", ctypes.c_int), ("factor_ms", ctypes.c_double), ("filter_ms", ctypes.c_double),
                 ("total_ms", ctypes.c_double), ("max_residual", ctypes.c_double),
-                ("history", ctypes.c_double * 128), ("gemm_df_ms", ctypes.c_double),
-                ("gemm_df_mac", ctypes.c_double), ("gemm_df_launches", ctypes.c_int), ("reserved2", ctypes.c_int)]
+                ("history", ctypes.c_double * 128), ("refine_gemm_ms", ctypes.c_double),
+                ("refine_gemm_mac", ctypes.c_double), ("refine_gemm_launches", ctypes.c_int),
+                ("reserved2", ctypes.c_int)]
 
 
 class FeastError(RuntimeError):
@@ -85,6 +87,7 @@ def lib():
         "feast_rayleigh_ritz": (I, [P, P, I, I64, I64, P, I64, D, DP, P, DP]),
         "feast_kernel_launches": (ctypes.c_uint64, []),
         "feast_jacobi_eigh_noalloc": (I, [I, P, I, I64, P, DP, P, IP]),
+        "feast_gemm_f64acc": (I, [P, I, I64, I64, I64, P, I64, P, I64, P, I64]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -295,6 +298,22 @@ def feast_rayleigh_ritz(ctx, A, Q, anorm):
                                      ev.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(X),
                                      res.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "feast_rayleigh_ritz")
     return ev, X, res
+
+
+def feast_gemm_f64acc(ctx, A, B, method=0):
+    """C = A B for real float64 CUDA matrices, FP64-accurate: method 0 on the
+    bf16 tensor cores (digit splitting), 1 in double-float arithmetic."""
+    torch = _torch()
+    A = colmajor(A.to(torch.float64))
+    B = colmajor(B.to(torch.float64))
+    M, K = A.shape
+    K2, N = B.shape
+    if K2 != K:
+        raise ValueError("inner dimensions differ")
+    C = empty_colmajor(M, N, torch.float64, A.device)
+    _check(lib().feast_gemm_f64acc(ctx, int(method), M, N, K, _ptr(A), M, _ptr(B), K, _ptr(C), M),
+           "feast_gemm_f64acc")
+    return C
 
 
 class Feast:

@@ -132,11 +132,13 @@ unsigned long long launch_count();
     FEAST_CUDA_TRY(cudaGetLastError());     \
   } while (0)
 
-// CUDA-event timing of the double-float GEMM launches of one solve (the
-// dominant kernel of the mixed path): enable, then read the summed device
-// time, multiply-adds and launch count.
-void df_timer_begin();
-void df_timer_end(double* ms, double* macs, int* launches);
+// CUDA-event timing of the FP64-accurate GEMM launches of the mixed path's
+// refinement (its dominant kernel): enable for one solve, bracket each launch,
+// then read the summed device time, multiply-adds and launch count.
+void refine_timer_begin();
+void refine_timer_end(double* ms, double* macs, int* launches);
+void refine_timer_launch_begin(cudaStream_t s);
+void refine_timer_launch_end(cudaStream_t s, double macs);
 
 struct CudaFailure {
   cudaError_t err;

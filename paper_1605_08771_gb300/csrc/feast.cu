@@ -19,6 +19,7 @@
 #include "dense.cuh"
 #include "factor.cuh"
 #include "gemm.cuh"
+#include "oz_gemm.cuh"
 #include "tc_update.cuh"
 
 using namespace feast;
@@ -205,6 +206,11 @@ struct Solver {
   float* Bpl = nullptr;
   double* Tdf = nullptr;
   int64_t bpl_cols = 0;
+  // tensor-core refinement products: digit planes of A (Re, Im, Re + Im for
+  // complex A) and buffers for those of the right operand
+  bool use_oz = false;
+  OzOperand Aoz[3];
+  void* Boz[3] = {nullptr, nullptr, nullptr};
   // Rayleigh-Ritz scratch
   S *Qb = nullptr, *Wb = nullptr, *Xr = nullptr, *AXr = nullptr, *T1 = nullptr, *T2 = nullptr;
   S *Ar0 = nullptr, *Ar = nullptr, *Vk = nullptr, *Gs = nullptr, *Ri = nullptr, *Cs = nullptr, *Cs2 = nullptr;
@@ -252,7 +258,8 @@ struct Solver {
     to_dev(ctx, d_w, w.data(), nc);
     to_dev(ctx, d_ze, ze.data(), E);
     cw = coop_work_carve(ctx->arena.alloc(coop_work_bytes(kmax, ctx->num_sms)), kmax, ctx->num_sms);
-    d_flag = dalloc<int>(ctx, 4);
+    d_flag = dalloc<int>(ctx, 4);  // [0]: status word of the tensor-core refinement GEMM
+    FEAST_CUDA_TRY(cudaMemsetAsync(d_flag, 0, 4 * sizeof(int), st));
     d_en = dalloc<double>(ctx, 2 * E);
     d_act = dalloc<int>(ctx, E);
   }
@@ -274,17 +281,33 @@ struct Solver {
       Yw = dalloc<c128>(ctx, E * nm);
       AY = dalloc<c128>(ctx, E * nm);
       Yc = dalloc<c64>(ctx, E * nm);
-      const int apl = kCplx ? 6 : 2;
-      Apl = dalloc<float>(ctx, (int64_t)apl * n * n);
-      if (kCplx) {
-        split_df32((const double*)A, n, n, lda, 2, 0, Apl, Apl + n * n, st);
-        split_df32((const double*)A, n, n, lda, 2, 1, Apl + 2 * n * n, Apl + 3 * n * n, st);
-        split_df32((const double*)A, n, n, lda, 2, 2, Apl + 4 * n * n, Apl + 5 * n * n, st);
-      } else {
-        split_df32((const double*)A, n, n, lda, 1, 0, Apl, Apl + n * n, st);
-      }
       bpl_cols = std::max<int64_t>(E * m, kmax);
-      Bpl = dalloc<float>(ctx, 6 * n * bpl_cols);
+      use_oz = o.refine_gemm == 0;
+      if (use_oz) {
+        // rows of A are read through its Hermitian symmetry, A(i, k) =
+        // conj(A[k + i lda]), so every split reads contiguous columns
+        if (kCplx) {
+          for (int t = 0; t < 3; ++t) Aoz[t] = oz_operand(ctx->arena.alloc(oz_operand_bytes(n, n, true)), n, n, true);
+          oz_split((const double*)A, 2, 0, n, 1, lda, Aoz[0], st);  // Re A(i, k)
+          oz_split((const double*)A, 2, 3, n, 1, lda, Aoz[1], st);  // Im A(i, k)
+          oz_split((const double*)A, 2, 4, n, 1, lda, Aoz[2], st);  // Re + Im
+        } else {
+          Aoz[0] = oz_operand(ctx->arena.alloc(oz_operand_bytes(n, n, true)), n, n, true);
+          oz_split((const double*)A, 1, 0, n, 1, lda, Aoz[0], st);
+        }
+        for (int t = 0; t < (kCplx ? 3 : 2); ++t) Boz[t] = ctx->arena.alloc(oz_operand_bytes(bpl_cols, n, false));
+      } else {
+        const int apl = kCplx ? 6 : 2;
+        Apl = dalloc<float>(ctx, (int64_t)apl * n * n);
+        if (kCplx) {
+          split_df32((const double*)A, n, n, lda, 2, 0, Apl, Apl + n * n, st);
+          split_df32((const double*)A, n, n, lda, 2, 1, Apl + 2 * n * n, Apl + 3 * n * n, st);
+          split_df32((const double*)A, n, n, lda, 2, 2, Apl + 4 * n * n, Apl + 5 * n * n, st);
+        } else {
+          split_df32((const double*)A, n, n, lda, 1, 0, Apl, Apl + n * n, st);
+        }
+        Bpl = dalloc<float>(ctx, 6 * n * bpl_cols);
+      }
       if (kCplx) Tdf = dalloc<double>(ctx, n * bpl_cols);
     }
   }
@@ -345,10 +368,44 @@ struct Solver {
       gemm_df32(n, k, n, 1.0, Arh, Arl, n, Brh, Brl, n, 0.0, Out, n, 1, 0, st);
     }
   }
-  // A times a block: FP64 on the FP64 path, double-float on the mixed path
+  // Out = A * B on the tensor cores: each real product from digit planes
+  // (oz_gemm), complex A by the same three products (3M) as apply_A_df
+  void apply_A_oz(const double* B, bool bcplx, int64_t k, double* Out) {
+    OzOperand Bo[3];
+    const int nb = kCplx ? 3 : (bcplx ? 2 : 1);
+    for (int t = 0; t < nb; ++t) Bo[t] = oz_operand(Boz[t], k, n, false);
+    const int sms = ctx->num_sms;
+    oz_split(B, bcplx ? 2 : 1, 0, n, 1, n, Bo[0], st);
+    if (bcplx) oz_split(B, 2, 1, n, 1, n, Bo[1], st);
+    if (kCplx) {
+      oz_split(B, 2, 2, n, 1, n, Bo[2], st);
+      oz_gemm(n, k, Aoz[0], Bo[0], Out, n, 2, 0, d_flag, sms, st);
+      oz_gemm(n, k, Aoz[1], Bo[1], Tdf, n, 1, 0, d_flag, sms, st);
+      oz_gemm(n, k, Aoz[2], Bo[2], Out, n, 2, 1, d_flag, sms, st);
+      combine_3m(Out, Tdf, n, k, st);
+    } else if (bcplx) {
+      oz_gemm(n, k, Aoz[0], Bo[0], Out, n, 2, 0, d_flag, sms, st);
+      oz_gemm(n, k, Aoz[0], Bo[1], Out, n, 2, 1, d_flag, sms, st);
+    } else {
+      oz_gemm(n, k, Aoz[0], Bo[0], Out, n, 1, 0, d_flag, sms, st);
+    }
+  }
+  // FP64-accurate A times an n x k block on the mixed path
+  void apply_A_acc(const double* B, bool bcplx, int64_t k, double* Out) {
+    if (use_oz) apply_A_oz(B, bcplx, k, Out);
+    else apply_A_df(B, bcplx, k, Out);
+  }
+  // a timed-out wait inside the tensor-core GEMM
+  void check_oz_status() {
+    if (!use_oz) return;
+    int f = 0;
+    to_host(ctx, &f, d_flag, 1);
+    if (f == DEV_BARRIER_TIMEOUT) throw FeastError{FEAST_ERR_TIMEOUT};
+  }
+  // A times a block: FP64 on the FP64 path, FP64-accurate products on the mixed path
   void apply_A(const S* Xm, int64_t k, S* Out) {
-    if (o.prec != FEAST_PREC_F64 && Apl && k <= bpl_cols) {
-      apply_A_df((const double*)Xm, kCplx, k, (double*)Out);
+    if (o.prec != FEAST_PREC_F64 && (Apl || use_oz) && k <= bpl_cols) {
+      apply_A_acc((const double*)Xm, kCplx, k, (double*)Out);
       return;
     }
     mm(n, k, n, C1(1.0), A, lda, OP_N, Xm, n, OP_N, C1(0.0), Out, n);
@@ -418,6 +475,7 @@ struct Solver {
     const double t0 = now_ms();
     filter_body(X, m, Xf);
     sync(ctx);
+    check_oz_status();
     filter_ms += now_ms() - t0;
   }
   void filter_body(const S* X, int64_t m, S* Xf) {
@@ -451,7 +509,7 @@ struct Solver {
           if (!active[e0]) { ++e0; continue; }
           int e1 = e0;
           while (e1 < E && active[e1]) ++e1;
-          phase("refine A*Y (df32)", [&] { apply_A_df((const double*)(Y + e0 * nm), true, (e1 - e0) * m, (double*)(AY + e0 * nm)); });
+          phase("refine A*Y", [&] { apply_A_acc((const double*)(Y + e0 * nm), true, (e1 - e0) * m, (double*)(AY + e0 * nm)); });
           e0 = e1;
         }
         to_dev(ctx, d_act, active.data(), E);
@@ -977,7 +1035,7 @@ int solve_t(feast_ctx* ctx, const S* A, int64_t n, int64_t lda, double lmin, dou
     random_normal<S>(X, n, m0, n, o.seed, ctx->stream);
   }
   sync(ctx);
-  df_timer_begin();
+  refine_timer_begin();
   const double tf0 = now_ms();
   sv.factor();
   sync(ctx);
@@ -1007,7 +1065,8 @@ int solve_t(feast_ctx* ctx, const S* A, int64_t n, int64_t lda, double lmin, dou
   st.m_expected = out.m_expected;
   st.factor_ms = tf1 - tf0;
   st.filter_ms = sv.filter_ms;
-  df_timer_end(&st.gemm_df_ms, &st.gemm_df_mac, &st.gemm_df_launches);
+  refine_timer_end(&st.refine_gemm_ms, &st.refine_gemm_mac, &st.refine_gemm_launches);
+  sv.check_oz_status();
   st.total_ms = now_ms() - t0;
   st.max_residual = 0.0;
   for (double r : rs) st.max_residual = std::max(st.max_residual, r);
@@ -1037,6 +1096,7 @@ void feast_opts_default(feast_opts* o) {
   o->prec = FEAST_PREC_F64;
   o->max_iter = 100;
   o->refine_max = 10;
+  o->refine_gemm = 0;
   o->aspect = 1.0;
   o->anorm = 0.0;
   o->refine_tol = 0.0;
@@ -1115,7 +1175,7 @@ int feast_interval_solve(feast_ctx* ctx, const void* A, int dtype, int64_t n, in
   if (opts) o = *opts; else feast_opts_default(&o);
   if (o.variant < 0 || o.variant > 2 || o.prec < 0 || o.prec > 2 || o.max_iter < 1 || !(o.aspect > 0)) return FEAST_ERR_ARG;
   if (o.variant != FEAST_PLAIN && (o.s < 1 || (int64_t)o.s * m0 > 65536)) return FEAST_ERR_ARG;
-  if (o.refine_max < 0 || !(o.refine_switch >= 0.0)) return FEAST_ERR_ARG;
+  if (o.refine_max < 0 || !(o.refine_switch >= 0.0) || o.refine_gemm < 0 || o.refine_gemm > 1) return FEAST_ERR_ARG;
   *m_found = 0;
   *iterations = 0;
   return guarded(ctx, [&]() {
@@ -1134,7 +1194,8 @@ int feast_filter_apply(feast_ctx* ctx, const void* A, int dtype, int64_t n, int6
   if (!X || !Y || m < 1) return FEAST_ERR_ARG;
   feast_opts o;
   if (opts) o = *opts; else feast_opts_default(&o);
-  if (o.prec < 0 || o.prec > 2 || !(o.aspect > 0) || o.refine_max < 0) return FEAST_ERR_ARG;
+  if (o.prec < 0 || o.prec > 2 || !(o.aspect > 0) || o.refine_max < 0 || o.refine_gemm < 0 || o.refine_gemm > 1)
+    return FEAST_ERR_ARG;
   return guarded(ctx, [&]() {
     FEAST_CUDA_TRY(cudaSetDevice(ctx->device));
     ctx->arena.reset();
@@ -1314,6 +1375,38 @@ int feast_rayleigh_ritz(feast_ctx* ctx, const void* A, int dtype, int64_t n, int
     };
     if (dtype == FEAST_R64) return run(double{});
     return run(c128{});
+  });
+}
+
+int feast_gemm_f64acc(feast_ctx* ctx, int method, int64_t M, int64_t N, int64_t K, const double* A, int64_t lda,
+                      const double* B, int64_t ldb, double* C, int64_t ldc) {
+  if (!ctx || !A || !B || !C || M < 1 || N < 1 || K < 1 || lda < M || ldb < K || ldc < M) return FEAST_ERR_ARG;
+  if (method != 0 && method != 1) return FEAST_ERR_ARG;
+  if (M > INT32_MAX / kOzDigits || N > INT32_MAX / kOzDigits) return FEAST_ERR_ARG;
+  return guarded(ctx, [&]() {
+    FEAST_CUDA_TRY(cudaSetDevice(ctx->device));
+    ctx->arena.reset();
+    cudaStream_t st = ctx->stream;
+    if (method == 0) {
+      int* flag = dalloc<int>(ctx, 1);
+      FEAST_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), st));
+      const OzOperand Ao = oz_operand(ctx->arena.alloc(oz_operand_bytes(M, K, true)), M, K, true);
+      const OzOperand Bo = oz_operand(ctx->arena.alloc(oz_operand_bytes(N, K, false)), N, K, false);
+      oz_split(A, 1, 0, K, lda, 1, Ao, st);  // row i: A[i + k lda]
+      oz_split(B, 1, 0, K, 1, ldb, Bo, st);  // column j: B[k + j ldb]
+      oz_gemm(M, N, Ao, Bo, C, ldc, 1, 0, flag, ctx->num_sms, st);
+      int f = 0;
+      to_host(ctx, &f, flag, 1);
+      if (f == DEV_BARRIER_TIMEOUT) return FEAST_ERR_TIMEOUT;
+    } else {
+      float* Ap = dalloc<float>(ctx, 2 * M * K);
+      float* Bp = dalloc<float>(ctx, 2 * K * N);
+      split_df32(A, M, K, lda, 1, 0, Ap, Ap + M * K, st);
+      split_df32(B, K, N, ldb, 1, 0, Bp, Bp + K * N, st);
+      gemm_df32(M, N, K, 1.0, Ap, Ap + M * K, M, Bp, Bp + K * N, K, 0.0, C, ldc, 1, 0, st);
+      sync(ctx);
+    }
+    return FEAST_OK;
   });
 }
 

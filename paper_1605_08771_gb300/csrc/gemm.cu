@@ -293,15 +293,15 @@ __global__ void split_df32_kernel(const double* src, int64_t rows, int64_t cols,
 }  // namespace
 
 namespace {
-struct DfTimer {
+struct RefineTimer {
   bool on = false;
   std::vector<cudaEvent_t> pool;
   size_t used = 0;
   double macs = 0.0;
   int launches = 0;
 };
-DfTimer& df_timer() {
-  static DfTimer t;
+RefineTimer& refine_timer() {
+  static RefineTimer t;
   return t;
 }
 std::atomic<unsigned long long> g_launches{0};
@@ -310,15 +310,15 @@ std::atomic<unsigned long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 unsigned long long launch_count() { return g_launches.load(); }
 
-void df_timer_begin() {
-  DfTimer& t = df_timer();
+void refine_timer_begin() {
+  RefineTimer& t = refine_timer();
   t.on = true;
   t.used = 0;
   t.macs = 0.0;
   t.launches = 0;
 }
-void df_timer_end(double* ms, double* macs, int* launches) {
-  DfTimer& t = df_timer();
+void refine_timer_end(double* ms, double* macs, int* launches) {
+  RefineTimer& t = refine_timer();
   double tot = 0.0;
   for (size_t i = 0; i + 1 < t.used; i += 2) {
     float e = 0.f;
@@ -332,29 +332,34 @@ void df_timer_end(double* ms, double* macs, int* launches) {
   t.on = false;
   t.used = 0;
 }
+void refine_timer_launch_begin(cudaStream_t s) {
+  RefineTimer& t = refine_timer();
+  if (!t.on) return;
+  while (t.pool.size() < t.used + 2) {
+    cudaEvent_t e;
+    FEAST_CUDA_TRY(cudaEventCreate(&e));
+    t.pool.push_back(e);
+  }
+  FEAST_CUDA_TRY(cudaEventRecord(t.pool[t.used], s));
+}
+void refine_timer_launch_end(cudaStream_t s, double macs) {
+  RefineTimer& t = refine_timer();
+  if (!t.on) return;
+  FEAST_CUDA_TRY(cudaEventRecord(t.pool[t.used + 1], s));
+  t.used += 2;
+  t.macs += macs;
+  t.launches += 1;
+}
 
 void gemm_df32(int64_t M, int64_t N, int64_t K, double alpha, const float* Ahi, const float* Alo, int64_t lda,
                const float* Bhi, const float* Blo, int64_t ldb, double beta, double* C, int64_t ldc, int cs, int co,
                cudaStream_t s) {
   if (M <= 0 || N <= 0) return;
-  DfTimer& tm = df_timer();
-  if (tm.on) {
-    while (tm.pool.size() < tm.used + 2) {
-      cudaEvent_t e;
-      FEAST_CUDA_TRY(cudaEventCreate(&e));
-      tm.pool.push_back(e);
-    }
-    FEAST_CUDA_TRY(cudaEventRecord(tm.pool[tm.used], s));
-  }
+  refine_timer_launch_begin(s);
   dim3 grid((unsigned)cdiv(M, DF_BM), (unsigned)cdiv(N, DF_BN));
   gemm_df32_kernel<<<grid, DF_THREADS, 0, s>>>(M, N, K, alpha, Ahi, Alo, lda, Bhi, Blo, ldb, beta, C, ldc, cs, co);
   FEAST_LAUNCH_CHECK();
-  if (tm.on) {
-    FEAST_CUDA_TRY(cudaEventRecord(tm.pool[tm.used + 1], s));
-    tm.used += 2;
-    tm.macs += (double)M * (double)N * (double)K;
-    tm.launches += 1;
-  }
+  refine_timer_launch_end(s, (double)M * (double)N * (double)K);
 }
 
 void combine_3m(double* C, const double* T2, int64_t n, int64_t k, cudaStream_t s) {

@@ -1,0 +1,431 @@
+// FP64-accurate real GEMM on the bf16 tensor cores (sm_103a tcgen05) by
+// error-free digit splitting -- the Ozaki scheme (Ozaki, Ogita, Oishi & Rump,
+// Numer. Algorithms 59, 2012) with the chunked exact accumulation of its
+// low-precision tensor-core variants.
+//
+// Splitting.  Each row i of A (and each column j of B) gets an exponent e with
+// max |x| < 2^e and is written as x = 2^(e-8) sum_{p<6} d_p 2^(-8p), where the
+// integer digits come from r <- 256 r, d = rint(r), r <- r - d starting at
+// r = x 2^-e (all exact in FP64): |d_0| <= 256, |d_p| <= 128.  Plane p stores
+// d_p 2^(-8p), exact in bf16 (at most 8 significant bits).  Then
+//     (A B)_ij = 2^(eA_i + eB_j - 16) sum_{p,q} sum_k a_p(i,k) b_q(k,j),
+// and the 21 plane products with p + q <= 5 keep about 47 bits; the rest are
+// below 2^-48 relative to sum_k 2^(eA_i + eB_j).
+//
+// Exact accumulation.  The products of one level l = p + q are integers times
+// 2^(-8l) and over 128 consecutive k their sum stays below 2^24 times that
+// unit (|d_0 d_0| <= 2^16; a level l >= 1 term is at most 2^14 (l + 3)), so
+// an FP32 tensor-core accumulator holds it exactly.  Levels 0-3 therefore
+// accumulate in four TMEM accumulators over one 128-wide K chunk at a time;
+// after each chunk the epilogue warps read them and add them into a running
+// double-float (hi, lo) pair per output with TwoSum (Knuth), so no bit is lost.
+// Levels 4-5 are 2^-32 smaller: they share a fifth accumulator over the whole
+// K, whose FP32 rounding stays near 2^-50 of the result.
+//
+// Kernel: persistent, one 128 x 96 output tile at a time per CTA.  Warp 0
+// issues the TMA loads (K-major, 64B swizzle, 32 k of all 12 digit planes per
+// stage, two stages); one thread of warp 1 issues tcgen05.mma kind::f16
+// (M = 128, N = 96, K = 16); warps 2-9 drain the accumulators (lane = output
+// row, each warp half of the columns).  The MMAs into the shared level-4/5
+// accumulator come first in each stage, so the tensor cores keep working
+// while the previous chunk is drained.  Every wait is bounded; on expiry the
+// kernel records the failure, lets the issued MMAs and loads complete, frees
+// its TMEM and skips the stores.
+#include <mutex>
+
+#include "oz_gemm.cuh"
+#include "tcgen05.cuh"
+
+namespace feast {
+
+namespace {
+
+constexpr int OZ_D = kOzDigits;
+constexpr int OZ_BM = kOzTileM, OZ_BN = kOzTileN, OZ_BK = kOzTileK;  // BK bf16 = 64 bytes = one swizzle row
+constexpr int OZ_CHUNK = 4;                                           // stages per exact chunk (128 k)
+constexpr int OZ_STAGES = 2;
+constexpr int OZ_A_TILE = OZ_BM * OZ_BK * 2;  // 8 KB
+constexpr int OZ_B_TILE = OZ_BN * OZ_BK * 2;  // 6 KB
+constexpr int OZ_STAGE_BYTES = OZ_D * (OZ_A_TILE + OZ_B_TILE);
+constexpr int OZ_LO_BYTES = OZ_BM * OZ_BN * 4;  // low halves of the running double-float sums
+constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE_BYTES + OZ_LO_BYTES + 1024 + 256;
+constexpr int OZ_EXACT = 4;                   // levels drained per chunk
+constexpr int OZ_MERGED_COL = OZ_EXACT * OZ_BN;
+constexpr int OZ_TMEM_COLS = 512;
+constexpr int OZ_EPI_WARPS = 8;
+constexpr int OZ_THREADS = 32 * (2 + OZ_EPI_WARPS);
+constexpr int OZ_COLS_PER_WARP = OZ_BN / 2;   // 48
+constexpr int OZ_GROUP_M = 8;                 // tile raster: groups of 8 row tiles
+
+static_assert(OZ_MERGED_COL + OZ_BN <= OZ_TMEM_COLS, "TMEM columns");
+static_assert(OZ_SMEM <= 227 * 1024, "shared memory");
+static_assert(OZ_COLS_PER_WARP % 16 == 0, "column groups of 16");
+
+// kind::f16 instruction descriptor: D = F32 (bits 4-5 = 1), A = B = BF16
+// (bits 7-9, 10-12 = 1), both K-major, N >> 3 in 17-22, M >> 4 in 24-28.
+constexpr uint32_t kIdescBf16 =
+    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) | ((uint32_t)(OZ_BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+      :
+      : "r"(tmem), "l"(da), "l"(db), "r"(kIdescBf16), "r"(accum)
+      : "memory");
+}
+
+// TwoSum (Knuth): s + e == a + b exactly; explicit _rn keeps the compiler
+// from reassociating or contracting
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+}
+
+// x 2^k: one exact multiplication when 2^k is a normal double
+__device__ __forceinline__ double pow2_scale(double x, int k) {
+  if (k >= -1022 && k <= 1023) return x * __longlong_as_double((long long)(k + 1023) << 52);
+  return ldexp(x, k);
+}
+
+__device__ __forceinline__ void tile_coords(int t, int mtiles, int ntiles, int& mt, int& nt) {
+  const int per = OZ_GROUP_M * ntiles;
+  const int first = (t / per) * OZ_GROUP_M;
+  const int gm = min(mtiles - first, OZ_GROUP_M);
+  const int r = t % per;
+  mt = first + r % gm;
+  nt = r / gm;
+}
+
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
+               int Mpad, int Npad, int kstages, const int* __restrict__ eA, const int* __restrict__ eB, double* C,
+               int64_t ldc, int cs, int co, int* status) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  float* lo_sm = (float*)(smem + OZ_STAGES * OZ_STAGE_BYTES);        // [column][row]
+  uint64_t* bars = (uint64_t*)(smem + OZ_STAGES * OZ_STAGE_BYTES + OZ_LO_BYTES);  // full[2] empty[2] chunk drained final
+  uint32_t* tmem_slot = (uint32_t*)(bars + 8);
+  __shared__ int s_fail;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t bar_full = smem_u32(&bars[0]), bar_empty = smem_u32(&bars[2]);
+  const uint32_t bar_chunk = smem_u32(&bars[4]), bar_drained = smem_u32(&bars[5]), bar_final = smem_u32(&bars[6]);
+  const int mtiles = Mpad / OZ_BM, ntiles = Npad / OZ_BN;
+  const int tiles = mtiles * ntiles;
+  const int nchunks = (kstages + OZ_CHUNK - 1) / OZ_CHUNK;
+
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    for (int s = 0; s < OZ_STAGES; ++s) {
+      mbar_init(bar_full + 8 * s, 1);
+      mbar_init(bar_empty + 8 * s, 1);
+    }
+    mbar_init(bar_chunk, 1);
+    mbar_init(bar_drained, OZ_EPI_WARPS);
+    mbar_init(bar_final, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(OZ_TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  volatile int* fail = &s_fail;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- producer: the 12 digit-plane tiles of every stage ----
+      int g = 0;
+      for (int tile = blockIdx.x; tile < tiles && !*fail; tile += gridDim.x) {
+        int mt, nt;
+        tile_coords(tile, mtiles, ntiles, mt, nt);
+        for (int ks = 0; ks < kstages; ++ks, ++g) {
+          const int st = g % OZ_STAGES;
+          if (g >= OZ_STAGES && !mbar_wait(bar_empty + 8 * st, ((g / OZ_STAGES) - 1) & 1)) {
+            atomicExch(&s_fail, 1);
+            break;
+          }
+          if (*fail) break;
+          const uint32_t base = smem_u32(smem + st * OZ_STAGE_BYTES);
+          mbar_expect_tx(bar_full + 8 * st, OZ_STAGE_BYTES);
+          const int x = ks * OZ_BK;
+#pragma unroll
+          for (int p = 0; p < OZ_D; ++p)
+            tma_load_2d(base + p * OZ_A_TILE, &tmA, x, p * Mpad + mt * OZ_BM, bar_full + 8 * st);
+#pragma unroll
+          for (int q = 0; q < OZ_D; ++q)
+            tma_load_2d(base + OZ_D * OZ_A_TILE + q * OZ_B_TILE, &tmB, x, q * Npad + nt * OZ_BN, bar_full + 8 * st);
+        }
+      }
+      // loads still in flight land before the CTA leaves
+      for (int h = g - OZ_STAGES; h < g; ++h)
+        if (h >= 0) mbar_wait(bar_full + 8 * (h % OZ_STAGES), (h / OZ_STAGES) & 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer ----
+      int g = 0, q = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+        for (int c = 0; c < nchunks && ok; ++c, ++q) {
+          const int s0 = c * OZ_CHUNK, s1 = min(kstages, s0 + OZ_CHUNK);
+          for (int ks = s0; ks < s1; ++ks, ++g) {
+            const int st = g % OZ_STAGES;
+            if (*fail || !mbar_wait(bar_full + 8 * st, (g / OZ_STAGES) & 1)) { ok = false; break; }
+            tc_fence_after();
+            const bool tile_first = ks == 0, chunk_first = ks == s0;
+            // the previous tile's accumulators, the shared one included, must be read first
+            if (tile_first && q > 0) {
+              if (!mbar_wait(bar_drained, (q - 1) & 1)) { ok = false; break; }
+              tc_fence_after();
+            }
+            const uint32_t abase = smem_u32(smem + st * OZ_STAGE_BYTES);
+            const uint32_t bbase = abase + OZ_D * OZ_A_TILE;
+            // levels 4 and 5 into the shared accumulator
+            bool first = tile_first;
+#pragma unroll
+            for (int kk = 0; kk < OZ_BK / 16; ++kk) {
+#pragma unroll
+              for (int p = 0; p < OZ_D; ++p) {
+#pragma unroll
+                for (int qq = 0; qq < OZ_D; ++qq) {
+                  if (p + qq < OZ_EXACT || p + qq > OZ_D - 1) continue;
+                  mma_bf16(tmem + OZ_MERGED_COL, sw64_desc(abase + p * OZ_A_TILE + kk * 32),
+                           sw64_desc(bbase + qq * OZ_B_TILE + kk * 32), first ? 0u : 1u);
+                  first = false;
+                }
+              }
+            }
+            // levels 0-3 restart at each chunk: wait for the previous chunk's drain
+            if (chunk_first && !tile_first && q > 0) {
+              if (!mbar_wait(bar_drained, (q - 1) & 1)) { ok = false; break; }
+              tc_fence_after();
+            }
+#pragma unroll
+            for (int kk = 0; kk < OZ_BK / 16; ++kk) {
+#pragma unroll
+              for (int l = 0; l < OZ_EXACT; ++l) {
+#pragma unroll
+                for (int p = 0; p <= l; ++p) {
+                  const bool restart = chunk_first && kk == 0 && p == 0;
+                  mma_bf16(tmem + l * OZ_BN, sw64_desc(abase + p * OZ_A_TILE + kk * 32),
+                           sw64_desc(bbase + (l - p) * OZ_B_TILE + kk * 32), restart ? 0u : 1u);
+                }
+              }
+            }
+            mma_commit(bar_empty + 8 * st);  // frees the stage once these MMAs are done
+          }
+          if (ok) mma_commit(bar_chunk);     // the chunk's sums are complete in TMEM
+        }
+      }
+      if (!ok) atomicExch(&s_fail, 1);
+      // every issued MMA completes before TMEM is released
+      mma_commit(bar_final);
+      mbar_wait(bar_final, 0);
+    }
+  } else {
+    // ---- epilogue: drain the exact levels after every chunk ----
+    const int quad = warp & 3;                 // TMEM lanes this warp may access
+    const int half = (warp - 2) >> 2;          // column half
+    const int row = quad * 32 + lane;          // output row within the tile
+    const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * OZ_COLS_PER_WARP);
+    int q = 0;
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+      int mt, nt;
+      tile_coords(tile, mtiles, ntiles, mt, nt);
+      // running sum of output (row, column j) = H[j] + Lo[j]; the high parts
+      // live in registers, the low parts in shared memory (one word per thread
+      // and column, consecutive rows adjacent)
+      float H[OZ_COLS_PER_WARP];
+      float* Lo = lo_sm + (size_t)half * OZ_COLS_PER_WARP * OZ_BM + row;
+#pragma unroll
+      for (int j = 0; j < OZ_COLS_PER_WARP; ++j) { H[j] = 0.f; Lo[j * OZ_BM] = 0.f; }
+      bool ok = true;
+      for (int c = 0; c < nchunks; ++c, ++q) {
+        if (*fail || !mbar_wait(bar_chunk, q & 1)) { ok = false; break; }
+        tc_fence_after();
+#pragma unroll
+        for (int gcol = 0; gcol < OZ_COLS_PER_WARP / 16; ++gcol) {
+          uint32_t va[16], vb[16];
+          const uint32_t ta = tbase + gcol * 16;
+          tmem_ld16(ta, va);
+          tmem_ld16(ta + OZ_BN, vb);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            float& h = H[gcol * 16 + j];
+            float e0, e1;
+            two_sum(h, __uint_as_float(va[j]), h, e0);
+            two_sum(h, __uint_as_float(vb[j]), h, e1);
+            float& lo = Lo[(gcol * 16 + j) * OZ_BM];
+            lo = __fadd_rn(lo, __fadd_rn(e0, e1));
+          }
+          tmem_ld16(ta + 2 * OZ_BN, va);
+          tmem_ld16(ta + 3 * OZ_BN, vb);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            float& h = H[gcol * 16 + j];
+            float e2;
+            two_sum(h, __uint_as_float(va[j]), h, e2);
+            float& lo = Lo[(gcol * 16 + j) * OZ_BM];
+            lo = __fadd_rn(lo, __fadd_rn(e2, __uint_as_float(vb[j])));
+          }
+        }
+        if (c == nchunks - 1) {
+#pragma unroll
+          for (int gcol = 0; gcol < OZ_COLS_PER_WARP / 16; ++gcol) {
+            uint32_t v[16];
+            tmem_ld16(tbase + OZ_MERGED_COL + gcol * 16, v);
+            tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              float& lo = Lo[(gcol * 16 + j) * OZ_BM];
+              lo = __fadd_rn(lo, __uint_as_float(v[j]));
+            }
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar_drained);
+      }
+      if (!ok) {
+        atomicExch(&s_fail, 1);
+        break;
+      }
+      const int i = mt * OZ_BM + row;
+      if (i < M) {
+        const int ei = eA[i] - 16;
+#pragma unroll
+        for (int j = 0; j < OZ_COLS_PER_WARP; ++j) {
+          const int col = nt * OZ_BN + half * OZ_COLS_PER_WARP + j;
+          if (col < N)
+            C[((int64_t)i + (int64_t)col * ldc) * cs + co] = pow2_scale((double)H[j] + (double)Lo[j * OZ_BM], ei + eB[col]);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_TMEM_COLS));
+  if (threadIdx.x == 0 && s_fail) atomicExch(status, DEV_BARRIER_TIMEOUT);
+}
+
+// One CTA per vector: exponent from the vector's max |x|, then the six digits
+// of every element.  Padded vectors and the K padding are zero.
+__global__ void oz_split_kernel(const double* __restrict__ src, int ss, int mode, int64_t K, int64_t se, int64_t sv,
+                                int64_t nvec, int64_t vpad, int64_t kpad, uint16_t* __restrict__ planes,
+                                int* __restrict__ exps) {
+  const int64_t v = blockIdx.x;
+  const int64_t plane = vpad * kpad;
+  uint16_t* out = planes + v * kpad;
+  if (v >= nvec) {
+    for (int64_t k = threadIdx.x; k < kpad; k += blockDim.x)
+      for (int p = 0; p < OZ_D; ++p) out[p * plane + k] = 0;
+    if (threadIdx.x == 0) exps[v] = 0;
+    return;
+  }
+  auto value = [&](int64_t k) -> double {
+    const double* e = src + (k * se + v * sv) * ss;
+    switch (mode) {
+      case 1: return e[1];
+      case 2: return e[0] + e[1];
+      case 3: return -e[1];
+      case 4: return e[0] - e[1];
+      default: return e[0];
+    }
+  };
+  double amax = 0.0;
+  for (int64_t k = threadIdx.x; k < K; k += blockDim.x) amax = fmax(amax, fabs(value(k)));
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = amax;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) red[0] = m;
+  }
+  __syncthreads();
+  int e = 0;
+  if (red[0] > 0.0) frexp(red[0], &e);  // max |x| < 2^e
+  if (threadIdx.x == 0) exps[v] = e;
+  for (int64_t k = threadIdx.x; k < kpad; k += blockDim.x) {
+    double r = k < K ? ldexp(value(k), -e) : 0.0;
+#pragma unroll
+    for (int p = 0; p < OZ_D; ++p) {
+      r *= 256.0;
+      const double d = rint(r);
+      r -= d;
+      // d 2^(-8p) has at most 8 significant bits: its bf16 pattern is the
+      // upper half of the FP32 pattern
+      out[p * plane + k] = (uint16_t)(__float_as_uint((float)ldexp(d, -8 * p)) >> 16);
+    }
+  }
+}
+
+void make_map_bf16(CUtensorMap* map, const uint16_t* base, int64_t rows, int64_t kpad, int box_rows) {
+  auto fn = tensor_map_encode_fn();
+  if (!fn) throw CudaFailure(cudaErrorNotSupported);
+  cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)kpad * 2};
+  cuuint32_t box[2] = {(cuuint32_t)OZ_BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)base, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw CudaFailure(cudaErrorInvalidValue);
+}
+
+}  // namespace
+
+OzOperand oz_operand(void* buf, int64_t nvec, int64_t K, bool left) {
+  OzOperand op;
+  op.nvec = nvec;
+  op.vpad = oz_vpad(nvec, left);
+  op.K = K;
+  op.kpad = oz_kpad(K);
+  op.planes = (uint16_t*)buf;
+  op.exps = (int*)((char*)buf + (size_t)OZ_D * op.vpad * op.kpad * 2);
+  return op;
+}
+
+void oz_split(const double* src, int ss, int mode, int64_t K, int64_t se, int64_t sv, const OzOperand& op,
+              cudaStream_t s) {
+  if (op.vpad <= 0) return;
+  oz_split_kernel<<<(unsigned)op.vpad, 256, 0, s>>>(src, ss, mode, K, se, sv, op.nvec, op.vpad, op.kpad, op.planes,
+                                                     op.exps);
+  FEAST_LAUNCH_CHECK();
+}
+
+void oz_gemm(int64_t M, int64_t N, const OzOperand& A, const OzOperand& B, double* C, int64_t ldc, int cs, int co,
+             int* status, int num_sms, cudaStream_t s) {
+  if (M <= 0 || N <= 0) return;
+  if (A.K != B.K || A.kpad != B.kpad || A.vpad % OZ_BM || B.vpad % OZ_BN || A.kpad % OZ_BK || M > A.nvec || N > B.nvec)
+    throw CudaFailure(cudaErrorInvalidValue);
+  CUtensorMap mA, mB;
+  make_map_bf16(&mA, A.planes, (int64_t)OZ_D * A.vpad, A.kpad, OZ_BM);
+  make_map_bf16(&mB, B.planes, (int64_t)OZ_D * B.vpad, B.kpad, OZ_BN);
+  static std::once_flag attr;
+  cudaError_t aerr = cudaSuccess;
+  std::call_once(attr, [&] {
+    aerr = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
+  });
+  FEAST_CUDA_TRY(aerr);
+  const int64_t tiles = (A.vpad / OZ_BM) * (B.vpad / OZ_BN);
+  const unsigned grid = (unsigned)std::min<int64_t>(tiles, num_sms);
+  refine_timer_launch_begin(s);
+  oz_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM, s>>>(mA, mB, (int)M, (int)N, (int)A.vpad, (int)B.vpad,
+                                                   (int)(A.kpad / OZ_BK), A.exps, B.exps, C, ldc, cs, co, status);
+  FEAST_LAUNCH_CHECK();
+  refine_timer_launch_end(s, (double)M * (double)N * (double)A.K);
+}
+
+}  // namespace feast

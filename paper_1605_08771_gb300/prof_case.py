@@ -26,6 +26,7 @@ def main():
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--m", type=int, default=0)
     ap.add_argument("--prec", default="mixed")
+    ap.add_argument("--refine-gemm", type=int, default=0, help="0 tensor cores (digit split), 1 double-float")
     args = ap.parse_args()
     import torch
 
@@ -46,9 +47,10 @@ def main():
             g = torch.Generator(device="cuda:0")
             g.manual_seed(3)
             X = torch.randn((n, m), generator=g, dtype=torch.complex128, device="cuda:0")
-            f.filter(A, a, b, 8, X, prec=args.prec, anorm=anorm)
+            f.filter(A, a, b, 8, X, prec=args.prec, anorm=anorm, refine_gemm=args.refine_gemm)
         else:
-            out = f.solve(A, a, b, m, 8, 1e-10, variant="rfeast", prec=args.prec, anorm=anorm)
+            out = f.solve(A, a, b, m, 8, 1e-10, variant="rfeast", prec=args.prec, anorm=anorm,
+                          refine_gemm=args.refine_gemm)
             print("status", out["status"], "pairs", out["evals"].size, "iterations", out["iterations"])
     torch.cuda.synchronize()
 
