@@ -569,6 +569,12 @@ struct Solver {
   // Hermitian eigendecomposition of the k x k matrix H (ld k, overwritten);
   // eigenvalues unsorted in `ev`, vectors in Vk (ld k)
   void eig(S* H, int64_t k, std::vector<double>& ev) {
+    const bool log = std::getenv("FEAST_LOG") != nullptr;
+    double t0 = 0.0;
+    if (log) {
+      sync(ctx);
+      t0 = now_ms();
+    }
     jacobi_eigh<S>(H, k, k, Vk, k, 1e-15, cw, ctx->num_sms, st);
     get_diag<S>(H, k, k, d_lam, st);
     ev.resize(k);
@@ -577,6 +583,7 @@ struct Solver {
     to_host(ctx, &status, cw.status, 1);
     to_host(ctx, &last_sweeps, cw.info + 1, 1);
     if (status == DEV_BARRIER_TIMEOUT) throw FeastError{FEAST_ERR_TIMEOUT};
+    if (log) fprintf(stderr, "[feast] jacobi k=%lld sweeps=%d %.1f ms\n", (long long)k, last_sweeps, now_ms() - t0);
   }
   // Gram-eigendecomposition route (Sect. II-A): X^H X = V S^2 V^H, keep
   // s^2 >= trunc s_1^2, U = X V S^{-1}, then one Cholesky-QR pass.
