@@ -190,21 +190,28 @@ int feast_rayleigh_ritz(feast_ctx* ctx, const void* A, int dtype, int64_t n, int
                         const void* Q, int64_t k, double anorm, double* evals, void* X,
                         double* res);
 
-/* C = A B for real FP64 matrices, column major on the device: A is M x K
- * (leading dim lda >= M), B is K x N (ldb >= K), C is M x N (ldc >= M, not
- * aliasing A or B).  This is the FP64-accurate product A Y that the mixed
- * precision's iterative refinement needs for its residual R = X - (zI - A) Y
- * (the refinement itself is not in the paper, which solves in full
- * precision).  method 0: bf16 tensor cores with error-free digit splitting
- * (Ozaki scheme: six 8-bit digits per element with a per-row / per-column
- * exponent, 21 digit products accumulated exactly in 128-long K chunks),
- * error about 2^-47 sum_k 2^(e_i + f_j) where 2^e_i > max_k |A_ik| and
- * 2^f_j > max_k |B_kj|; method 1: double-float arithmetic on the FP32 pipes,
- * error about 2^-44 sum_k |A_ik| |B_kj|.  Scratch comes from the context.
- * Returns FEAST_ERR_ARG for M, N or K < 1, bad leading dimensions or method,
- * FEAST_ERR_TIMEOUT when a bounded device wait gave up. */
-int feast_gemm_f64acc(feast_ctx* ctx, int method, int64_t M, int64_t N, int64_t K, const double* A, int64_t lda,
-                      const double* B, int64_t ldb, double* C, int64_t ldc);
+/* C = alpha op(A) op(B) + beta C, FP64-accurate, column major on the device:
+ * dtype FEAST_R64 (double) or FEAST_C128 (interleaved complex double);
+ * op(A) = A (transA = 0; A is M x K, lda >= M) or its conjugate transpose
+ * (transA = 1; A is K x M, lda >= K); likewise op(B) (K x N) from B (ldb);
+ * C is M x N (ldc >= M, not aliasing A or B); alpha, beta real.  This is the
+ * FP64-accurate product that the mixed precision needs for its refinement
+ * residual R = X - (zI - A) Y and uses for its Rayleigh-Ritz and
+ * orthonormalisation products (the refinement itself is not in the paper,
+ * which solves in full precision).
+ * method 0: bf16 tensor cores with error-free digit splitting (Ozaki scheme:
+ * six 8-bit digits per element under a per-row / per-column exponent, 21
+ * digit products accumulated exactly in 128-long K chunks; complex by three
+ * real products), error about 2^-47 sum_k 2^(e_i + f_j) per real product
+ * where 2^e_i > max_k |op(A)_ik| and 2^f_j > max_k |op(B)_kj|.
+ * method 1: double-float arithmetic on the FP32 pipes, error about
+ * 2^-44 sum_k |A_ik| |B_kj|; real, transA = transB = 0 and beta = 0 only.
+ * Scratch comes from the context.  Returns FEAST_ERR_ARG for bad sizes,
+ * leading dimensions, flags or non-finite alpha/beta, FEAST_ERR_TIMEOUT when a
+ * bounded device wait gave up. */
+int feast_gemm_f64acc(feast_ctx* ctx, int method, int dtype, int transA, int transB, int64_t M, int64_t N, int64_t K,
+                      double alpha, const void* A, int64_t lda, const void* B, int64_t ldb, double beta, void* C,
+                      int64_t ldc);
 
 /* Allocation-free Jacobi eigensolver, for callers that cannot allocate device
  * memory at call time: code running while a CUDA stream is captured, services

@@ -87,7 +87,7 @@ def lib():
         "feast_rayleigh_ritz": (I, [P, P, I, I64, I64, P, I64, D, DP, P, DP]),
         "feast_kernel_launches": (ctypes.c_uint64, []),
         "feast_jacobi_eigh_noalloc": (I, [I, P, I, I64, P, DP, P, IP]),
-        "feast_gemm_f64acc": (I, [P, I, I64, I64, I64, P, I64, P, I64, P, I64]),
+        "feast_gemm_f64acc": (I, [P, I, I, I, I, I64, I64, I64, D, P, I64, P, I64, D, P, I64]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -300,18 +300,28 @@ def feast_rayleigh_ritz(ctx, A, Q, anorm):
     return ev, X, res
 
 
-def feast_gemm_f64acc(ctx, A, B, method=0):
-    """C = A B for real float64 CUDA matrices, FP64-accurate: method 0 on the
-    bf16 tensor cores (digit splitting), 1 in double-float arithmetic."""
+def feast_gemm_f64acc(ctx, A, B, method=0, transA=False, transB=False, alpha=1.0, beta=0.0, C=None):
+    """C = alpha op(A) op(B) + beta C, FP64-accurate, for float64 or complex128
+    CUDA matrices; op = conjugate transpose when trans*.  method 0 on the bf16
+    tensor cores (digit splitting), 1 in double-float arithmetic (real,
+    no transposes, beta = 0)."""
     torch = _torch()
-    A = colmajor(A.to(torch.float64))
-    B = colmajor(B.to(torch.float64))
-    M, K = A.shape
-    K2, N = B.shape
+    cplx = A.is_complex() or B.is_complex()
+    dt = torch.complex128 if cplx else torch.float64
+    A = colmajor(A.to(dt))
+    B = colmajor(B.to(dt))
+    M, K = (A.shape[1], A.shape[0]) if transA else A.shape
+    K2, N = (B.shape[1], B.shape[0]) if transB else B.shape
     if K2 != K:
         raise ValueError("inner dimensions differ")
-    C = empty_colmajor(M, N, torch.float64, A.device)
-    _check(lib().feast_gemm_f64acc(ctx, int(method), M, N, K, _ptr(A), M, _ptr(B), K, _ptr(C), M),
+    if C is None:
+        C = empty_colmajor(M, N, dt, A.device)
+        if beta != 0.0:
+            raise ValueError("beta != 0 needs C")
+    else:
+        C = colmajor(C.to(dt))
+    _check(lib().feast_gemm_f64acc(ctx, int(method), int(cplx), int(bool(transA)), int(bool(transB)), M, N, K,
+                                   float(alpha), _ptr(A), A.shape[0], _ptr(B), B.shape[0], float(beta), _ptr(C), M),
            "feast_gemm_f64acc")
     return C
 

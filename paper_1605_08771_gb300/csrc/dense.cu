@@ -17,9 +17,16 @@ template <> __device__ __forceinline__ c128 ldcg<c128>(const c128* p) {
   double2 v = __ldcg((const double2*)p);
   return c128{v.x, v.y};
 }
+template <> __device__ __forceinline__ float ldcg<float>(const float* p) { return __ldcg(p); }
+template <> __device__ __forceinline__ c64 ldcg<c64>(const c64* p) {
+  float2 v = __ldcg((const float2*)p);
+  return c64{v.x, v.y};
+}
 template <typename S> __device__ __forceinline__ S one();
 template <> __device__ __forceinline__ double one<double>() { return 1.0; }
 template <> __device__ __forceinline__ c128 one<c128>() { return c128{1.0, 0.0}; }
+template <> __device__ __forceinline__ float one<float>() { return 1.0f; }
+template <> __device__ __forceinline__ c64 one<c64>() { return c64{1.0f, 0.0f}; }
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
@@ -131,12 +138,13 @@ __global__ void tri_inv_kernel(const S* R, int64_t k, int64_t ld, S* Ri, int64_t
 template <typename S>
 __global__ void __launch_bounds__(256)
 jacobi_kernel(S* H, int64_t k, int64_t ld, S* V, int64_t ldv, double tol, CoopWork w, int P, int max_sweeps) {
+  using R = real_t<S>;  // rotations in the working precision (FP32 or FP64)
   const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t NT = (int64_t)P * blockDim.x;
   unsigned nb = 0;
   const int64_t kk = k + (k & 1), np = kk / 2, m1 = kk - 1;
-  double* rc = (double*)w.rot;
-  double* rs = rc + np;
+  R* rc = (R*)w.rot;
+  R* rs = rc + np;
   S* re = (S*)(rs + np);
   int* ron = (int*)(re + np);
   int* rpp = ron + np;
@@ -153,7 +161,7 @@ jacobi_kernel(S* H, int64_t k, int64_t ld, S* V, int64_t ldv, double tol, CoopWo
   if (!group_barrier(w.counter, (++nb) * (unsigned)P, w.status)) return;
   double fro2 = 0.0;
   for (int q = 0; q < P; ++q) fro2 += __ldcg(&w.partial[q]);
-  const double thr = tol * sqrt(fro2);
+  const R thr = (R)(tol * sqrt(fro2));
 
   int sweeps = 0;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
@@ -163,19 +171,19 @@ jacobi_kernel(S* H, int64_t k, int64_t ld, S* V, int64_t ldv, double tol, CoopWo
         if (i == 0) { a = r % m1; b = m1; }
         else { a = (r + i) % m1; b = ((r - i) % m1 + m1) % m1; }
         const int64_t p = a < b ? a : b, q = a < b ? b : a;
-        double c = 1.0, s = 0.0;
+        R c = R(1), s = R(0);
         S e = one<S>();
         int on = 0;
         if (q < k) {
           const S apq = ldcg(&H[p + q * ld]);
-          const double g = sqrt(abs2(apq));
+          const R g = sqrt(abs2(apq));
           if (g > thr) {
-            const double app = real_part(ldcg(&H[p + p * ld]));
-            const double aqq = real_part(ldcg(&H[q + q * ld]));
-            e = conj(apq) * (1.0 / g);
-            const double tau = (aqq - app) / (2.0 * g);
-            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + hypot(1.0, tau));
-            c = 1.0 / hypot(1.0, t);
+            const R app = real_part(ldcg(&H[p + p * ld]));
+            const R aqq = real_part(ldcg(&H[q + q * ld]));
+            e = conj(apq) * (R(1) / g);
+            const R tau = (aqq - app) / (R(2) * g);
+            const R t = (tau >= R(0) ? R(1) : R(-1)) / (fabs(tau) + hypot(R(1), tau));
+            c = R(1) / hypot(R(1), t);
             s = t * c;
             on = 1;
             atomicAdd(&w.rotcount[sweep], 1u);
@@ -198,7 +206,7 @@ jacobi_kernel(S* H, int64_t k, int64_t ld, S* V, int64_t ldv, double tol, CoopWo
           S b10 = vqI ? ldcg(&H[qI + (int64_t)pJ * ld]) : num<S>::zero();
           S b11 = (vqI && vqJ) ? ldcg(&H[qI + (int64_t)qJ * ld]) : num<S>::zero();
           if (onJ) {
-            const double c = __ldcg(&rc[J]), s = __ldcg(&rs[J]);
+            const R c = __ldcg(&rc[J]), s = __ldcg(&rs[J]);
             const S e = ldcg(&re[J]);
             const S se = e * s, ce = e * c;
             S n00 = b00 * c - b01 * se, n01 = b00 * s + b01 * ce;
@@ -206,7 +214,7 @@ jacobi_kernel(S* H, int64_t k, int64_t ld, S* V, int64_t ldv, double tol, CoopWo
             b00 = n00; b01 = n01; b10 = n10; b11 = n11;
           }
           if (onI) {
-            const double c = __ldcg(&rc[I]), s = __ldcg(&rs[I]);
+            const R c = __ldcg(&rc[I]), s = __ldcg(&rs[I]);
             const S ec = conj(ldcg(&re[I]));
             const S sec = ec * s, cec = ec * c;
             S n00 = b00 * c - b10 * sec, n10 = b00 * s + b10 * cec;
@@ -228,7 +236,7 @@ jacobi_kernel(S* H, int64_t k, int64_t ld, S* V, int64_t ldv, double tol, CoopWo
           const int64_t row = tv % k, J = tv / k;
           if (!__ldcg(&ron[J])) continue;
           const int pJ = __ldcg(&rpp[J]), qJ = __ldcg(&rqq[J]);
-          const double c = __ldcg(&rc[J]), s = __ldcg(&rs[J]);
+          const R c = __ldcg(&rc[J]), s = __ldcg(&rs[J]);
           const S e = ldcg(&re[J]);
           S* vp = &V[row + (int64_t)pJ * ldv];
           S* vq = &V[row + (int64_t)qJ * ldv];
@@ -471,7 +479,7 @@ void tri_inverse_upper(const S* R, int64_t k, int64_t ld, S* Rinv, int64_t ldi, 
 
 template <typename S>
 void jacobi_eigh(S* H, int64_t k, int64_t ld, S* V, int64_t ldv, double tol, const CoopWork& w, int num_sms,
-                 cudaStream_t s) {
+                 cudaStream_t s, int max_sweeps) {
   FEAST_CUDA_TRY(cudaMemsetAsync(w.counter, 0, 256 * 3, s));
   FEAST_CUDA_TRY(cudaMemsetAsync(w.rotcount, 0, sizeof(unsigned) * kMaxSweeps, s));
   int occ = 0;
@@ -479,7 +487,7 @@ void jacobi_eigh(S* H, int64_t k, int64_t ld, S* V, int64_t ldv, double tol, con
   const int64_t tasks = (k / 2 + 1) * (k / 2 + 1) + k * (k / 2 + 1);
   int P = (int)std::min<int64_t>((int64_t)std::max(1, occ) * num_sms, cdiv(tasks, 256 * 8));
   P = std::max(1, std::min(P, num_sms));
-  int maxs = kMaxSweeps;
+  int maxs = std::max(1, std::min(max_sweeps, kMaxSweeps));
   CoopWork wl = w;
   void* args[] = {&H, &k, &ld, &V, &ldv, &tol, &wl, &P, &maxs};
   FEAST_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)jacobi_kernel<S>, dim3(P), dim3(256), args, 0, s));
@@ -583,11 +591,33 @@ template <typename S> void check_finite(const S* X, int64_t n, int64_t m, int64_
   FEAST_LAUNCH_CHECK();
 }
 
+template <typename To, typename From>
+__global__ void convert_matrix_kernel(To* dst, int64_t ldd, const From* src, int64_t lds, int64_t n, int64_t m) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * m; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t % n, c = t / n;
+    dst[i + c * ldd] = cvt<To>(src[i + c * lds]);
+  }
+}
+
+template <typename To, typename From>
+void convert_matrix(To* dst, int64_t ldd, const From* src, int64_t lds, int64_t n, int64_t m, cudaStream_t s) {
+  if (n <= 0 || m <= 0) return;
+  convert_matrix_kernel<To, From><<<grid1d(n * m), 256, 0, s>>>(dst, ldd, src, lds, n, m);
+  FEAST_LAUNCH_CHECK();
+}
+template void convert_matrix<float, double>(float*, int64_t, const double*, int64_t, int64_t, int64_t, cudaStream_t);
+template void convert_matrix<double, float>(double*, int64_t, const float*, int64_t, int64_t, int64_t, cudaStream_t);
+template void convert_matrix<c64, c128>(c64*, int64_t, const c128*, int64_t, int64_t, int64_t, cudaStream_t);
+template void convert_matrix<c128, c64>(c128*, int64_t, const c64*, int64_t, int64_t, int64_t, cudaStream_t);
+template void jacobi_eigh<float>(float*, int64_t, int64_t, float*, int64_t, double, const CoopWork&, int, cudaStream_t,
+                                 int);
+template void jacobi_eigh<c64>(c64*, int64_t, int64_t, c64*, int64_t, double, const CoopWork&, int, cudaStream_t, int);
+
 #define INST_S(S)                                                                                          \
   template void hermitize<S>(S*, int64_t, int64_t, cudaStream_t);                                          \
   template void cholesky_upper<S>(S*, int64_t, int64_t, const CoopWork&, int, cudaStream_t);               \
   template void tri_inverse_upper<S>(const S*, int64_t, int64_t, S*, int64_t, cudaStream_t);               \
-  template void jacobi_eigh<S>(S*, int64_t, int64_t, S*, int64_t, double, const CoopWork&, int, cudaStream_t); \
+  template void jacobi_eigh<S>(S*, int64_t, int64_t, S*, int64_t, double, const CoopWork&, int, cudaStream_t, int); \
   template void get_diag<S>(const S*, int64_t, int64_t, double*, cudaStream_t);                            \
   template void col_norms2<S>(const S*, int64_t, int64_t, int64_t, double*, cudaStream_t);                 \
   template void col_dots_re<S>(const S*, const S*, int64_t, int64_t, int64_t, double*, cudaStream_t);      \

@@ -35,10 +35,16 @@ void tri_inverse_upper(const S* R, int64_t k, int64_t ld, S* Rinv, int64_t ldi, 
 
 // Two-sided Jacobi with round-robin ordering on the Hermitian k x k matrix H
 // (overwritten by its near-diagonal form); V receives the eigenvectors
-// (unsorted).  Sweeps counted in w.info[1].
+// (unsorted).  Rotations skip |h_pq| <= tol ||H||_F; sweeps stop when a sweep
+// rotates nothing or after max_sweeps.  Sweeps counted in w.info[1].  S may be
+// double, c128 or, for a low-precision first phase, float / c64.
 template <typename S>
 void jacobi_eigh(S* H, int64_t k, int64_t ld, S* V, int64_t ldv, double tol, const CoopWork& w,
-                 int num_sms, cudaStream_t s);
+                 int num_sms, cudaStream_t s, int max_sweeps = kMaxSweeps);
+
+// dst (n x m, ld ldd) = src converted elementwise (FP64 <-> FP32, complex too)
+template <typename To, typename From>
+void convert_matrix(To* dst, int64_t ldd, const From* src, int64_t lds, int64_t n, int64_t m, cudaStream_t s);
 
 // diag[i] = Re H[i,i]
 template <typename S> void get_diag(const S* H, int64_t k, int64_t ld, double* diag, cudaStream_t s);

@@ -202,6 +202,14 @@ struct Solver {
   bool refine_now = true;      // mixed: refine the next filter application
   // mixed: double-float planes of A (hi/lo of Re, then of Im) and of the
   // right-hand block of an A product
+  // two-phase reduced eigensolver scratch (FP32 Jacobi, FP64 polish)
+  using F32 = typename std::conditional<std::is_same<S, c128>::value, c64, float>::type;
+  static constexpr int64_t kEigMixedMin = 64;
+  F32* H32 = nullptr;
+  F32* V32 = nullptr;
+  S* Ve = nullptr;
+  S* Te = nullptr;
+  S* T2e = nullptr;
   float* Apl = nullptr;
   float* Bpl = nullptr;
   double* Tdf = nullptr;
@@ -211,6 +219,12 @@ struct Solver {
   bool use_oz = false;
   OzOperand Aoz[3];
   void* Boz[3] = {nullptr, nullptr, nullptr};
+  // general FP64-accurate products on the tensor cores (mixed path): left
+  // operand planes and the 3M partial products
+  void* Loz[3] = {nullptr, nullptr, nullptr};
+  double* Tmm = nullptr;
+  double* Tmm2 = nullptr;
+  static constexpr double kOzMinWork = 1e8;  // M N K below which SIMT FP64 is used
   // Rayleigh-Ritz scratch
   S *Qb = nullptr, *Wb = nullptr, *Xr = nullptr, *AXr = nullptr, *T1 = nullptr, *T2 = nullptr;
   S *Ar0 = nullptr, *Ar = nullptr, *Vk = nullptr, *Gs = nullptr, *Ri = nullptr, *Cs = nullptr, *Cs2 = nullptr;
@@ -247,6 +261,7 @@ struct Solver {
   void alloc_common(int64_t kmax_, int64_t mmax_) {
     kmax = std::max<int64_t>(kmax_, 1);
     mmax = std::max<int64_t>(mmax_, 1);
+    use_oz = o.prec != FEAST_PREC_F64 && o.refine_gemm == 0;
     contour(lmin, lmax, nc, o.aspect, z, w);
     d_w = dalloc<c128>(ctx, nc);
     d_ze = dalloc<c128>(ctx, E);
@@ -282,7 +297,6 @@ struct Solver {
       AY = dalloc<c128>(ctx, E * nm);
       Yc = dalloc<c64>(ctx, E * nm);
       bpl_cols = std::max<int64_t>(E * m, kmax);
-      use_oz = o.refine_gemm == 0;
       if (use_oz) {
         // rows of A are read through its Hermitian symmetry, A(i, k) =
         // conj(A[k + i lda]), so every split reads contiguous columns
@@ -321,6 +335,16 @@ struct Solver {
     const int64_t kk = kmax * kmax;
     Ar0 = dalloc<S>(ctx, kk); Ar = dalloc<S>(ctx, kk); Vk = dalloc<S>(ctx, kk); Gs = dalloc<S>(ctx, kk);
     Ri = dalloc<S>(ctx, kk); Cs = dalloc<S>(ctx, kk); Cs2 = dalloc<S>(ctx, kk);
+    if (use_oz && (double)n * kmax * kmax >= kOzMinWork) {
+      const size_t lb = std::max(oz_operand_bytes(kmax, n, true), oz_operand_bytes(n, kmax, true));
+      for (int t = 0; t < (kCplx ? 3 : 1); ++t) Loz[t] = ctx->arena.alloc(lb);
+      Tmm = dalloc<double>(ctx, (kCplx ? 2 : 1) * n * kmax);
+      if (kCplx) Tmm2 = dalloc<double>(ctx, n * kmax);
+    }
+    if (kmax >= kEigMixedMin) {
+      H32 = dalloc<F32>(ctx, kk); V32 = dalloc<F32>(ctx, kk);
+      Ve = dalloc<S>(ctx, kk); Te = dalloc<S>(ctx, kk); T2e = dalloc<S>(ctx, kk);
+    }
     part_elems = 32 * kk;
     part = dalloc<S>(ctx, part_elems);
     d_lam = dalloc<double>(ctx, kmax);
@@ -329,14 +353,38 @@ struct Solver {
     d_idx = dalloc<int>(ctx, kmax);
   }
 
-  // ---- small GEMM helpers ----
+  // ---- GEMM helpers ----
+  // products large enough for the tensor cores (mixed path, scratch present)
+  bool mm_acc_ok(int64_t Mr, int64_t Nc, int64_t K, c128 alpha, c128 beta) const {
+    if (!use_oz || !Loz[0] || !Boz[0] || alpha.im != 0.0 || beta.im != 0.0) return false;
+    if ((double)Mr * (double)Nc * (double)K < kOzMinWork) return false;
+    if (Mr * Nc > n * kmax || Nc > bpl_cols) return false;
+    const size_t lb = std::max(oz_operand_bytes(kmax, n, true), oz_operand_bytes(n, kmax, true));
+    return oz_operand_bytes(Mr, K, true) <= lb && oz_operand_bytes(Nc, K, false) <= oz_operand_bytes(bpl_cols, n, false);
+  }
+  // C = alpha op(A) op(B) + beta C (alpha, beta real) with FP64-accurate
+  // tensor-core products (oz_gemm_op; complex by the three real products 3M)
+  void mm_acc(int64_t Mr, int64_t Nc, int64_t K, double alpha, const S* Am, int64_t la, int opA, const S* Bm,
+              int64_t lb, int opB, double beta, S* Cm, int64_t lc) {
+    OzScratch w{{Loz[0], Loz[1], Loz[2]}, {Boz[0], Boz[1], Boz[2]}, Tmm, Tmm2};
+    oz_gemm_op(kCplx, Mr, Nc, K, alpha, (const double*)Am, la, opA != OP_N, (const double*)Bm, lb, opB != OP_N, beta,
+               (double*)Cm, lc, w, d_flag, ctx->num_sms, st);
+  }
   void mm(int64_t Mr, int64_t Nc, int64_t K, c128 alpha, const S* Am, int64_t la, int opA, const S* Bm, int64_t lb,
           int opB, c128 beta, S* Cm, int64_t lc) {
+    if (mm_acc_ok(Mr, Nc, K, alpha, beta)) {
+      mm_acc(Mr, Nc, K, alpha.re, Am, la, opA, Bm, lb, opB, beta.re, Cm, lc);
+      return;
+    }
     gemm_simple<S, S, S>(Mr, Nc, K, alpha, Am, la, opA, Bm, lb, opB, beta, Cm, lc, st);
   }
   // C (Mr x Nc) = op(A) op(B) with a long reduction K: split-K
   void mm_reduce(int64_t Mr, int64_t Nc, int64_t K, const S* Am, int64_t la, int opA, const S* Bm, int64_t lb,
                  int opB, S* Cm, int64_t lc) {
+    if (mm_acc_ok(Mr, Nc, K, C1(1.0), C1(0.0))) {
+      mm_acc(Mr, Nc, K, 1.0, Am, la, opA, Bm, lb, opB, 0.0, Cm, lc);
+      return;
+    }
     int ks = (int)std::max<int64_t>(1, std::min<int64_t>(32, K / 256));
     while (ks > 1 && (int64_t)ks * lc * Nc > part_elems) --ks;
     gemm_simple<S, S, S>(Mr, Nc, K, C1(1.0), Am, la, opA, Bm, lb, opB, C1(0.0), Cm, lc, st, ks,
@@ -568,6 +616,47 @@ struct Solver {
   }
   // Hermitian eigendecomposition of the k x k matrix H (ld k, overwritten);
   // eigenvalues unsorted in `ev`, vectors in Vk (ld k)
+  void jacobi_status(int* sweeps) {
+    int status = 0;
+    to_host(ctx, &status, cw.status, 1);
+    if (sweeps) to_host(ctx, sweeps, cw.info + 1, 1);
+    if (status == DEV_BARRIER_TIMEOUT) throw FeastError{FEAST_ERR_TIMEOUT};
+  }
+  // Two-phase Hermitian eigendecomposition for k >= kEigMixedMin: Jacobi in
+  // FP32 (a 64x faster pipe on this GPU) down to off-diagonals of a few FP32
+  // ulps of ||H||_F; its vectors, made exactly orthonormal in FP64 by one
+  // Cholesky-QR pass (V R^-1 with V^H V = R^H R), transform H to V^H H V,
+  // which FP64 Jacobi finishes to the same threshold as the one-phase solver
+  // (quadratic convergence: a few sweeps).  Vk = V V', the eigenvalues on the
+  // diagonal of H.  Returns false (nothing changed in H) when the Cholesky
+  // factorisation breaks down.
+  bool eig_two_phase(S* H, int64_t k, int* sweeps) {
+    convert_matrix<F32, S>(H32, k, H, k, k, k, st);
+    jacobi_eigh<F32>(H32, k, k, V32, k, 4e-7, cw, ctx->num_sms, st, 40);
+    int sw32 = 0;
+    jacobi_status(&sw32);
+    convert_matrix<S, F32>(Ve, k, V32, k, k, k, st);
+    mm(k, k, k, C1(1.0), Ve, k, OP_C, Ve, k, OP_N, C1(0.0), Te, k);
+    hermitize<S>(Te, k, k, st);
+    cholesky_upper<S>(Te, k, k, cw, ctx->num_sms, st);
+    int info = 0;
+    to_host(ctx, &info, cw.info, 1);
+    jacobi_status(nullptr);
+    if (info != 0) return false;
+    tri_inverse_upper<S>(Te, k, k, T2e, k, st);
+    mm(k, k, k, C1(1.0), Ve, k, OP_N, T2e, k, OP_N, C1(0.0), Te, k);   // Te: orthonormal V
+    mm(k, k, k, C1(1.0), H, k, OP_N, Te, k, OP_N, C1(0.0), T2e, k);    // H V
+    mm(k, k, k, C1(1.0), Te, k, OP_C, T2e, k, OP_N, C1(0.0), H, k);    // V^H H V
+    hermitize<S>(H, k, k, st);
+    jacobi_eigh<S>(H, k, k, T2e, k, 1e-15, cw, ctx->num_sms, st);
+    int sw64 = 0;
+    jacobi_status(&sw64);
+    mm(k, k, k, C1(1.0), Te, k, OP_N, T2e, k, OP_N, C1(0.0), Vk, k);
+    *sweeps = sw32 + sw64;
+    if (std::getenv("FEAST_LOG"))
+      fprintf(stderr, "[feast] two-phase eig k=%lld: %d FP32 + %d FP64 sweeps\n", (long long)k, sw32, sw64);
+    return true;
+  }
   void eig(S* H, int64_t k, std::vector<double>& ev) {
     const bool log = std::getenv("FEAST_LOG") != nullptr;
     double t0 = 0.0;
@@ -575,14 +664,13 @@ struct Solver {
       sync(ctx);
       t0 = now_ms();
     }
-    jacobi_eigh<S>(H, k, k, Vk, k, 1e-15, cw, ctx->num_sms, st);
+    if (!(k >= kEigMixedMin && H32 && k <= kmax && eig_two_phase(H, k, &last_sweeps))) {
+      jacobi_eigh<S>(H, k, k, Vk, k, 1e-15, cw, ctx->num_sms, st);
+      jacobi_status(&last_sweeps);
+    }
     get_diag<S>(H, k, k, d_lam, st);
     ev.resize(k);
     to_host(ctx, ev.data(), d_lam, k);
-    int status = 0;
-    to_host(ctx, &status, cw.status, 1);
-    to_host(ctx, &last_sweeps, cw.info + 1, 1);
-    if (status == DEV_BARRIER_TIMEOUT) throw FeastError{FEAST_ERR_TIMEOUT};
     if (log) fprintf(stderr, "[feast] jacobi k=%lld sweeps=%d %.1f ms\n", (long long)k, last_sweeps, now_ms() - t0);
   }
   // Gram-eigendecomposition route (Sect. II-A): X^H X = V S^2 V^H, keep
@@ -1385,36 +1473,47 @@ int feast_rayleigh_ritz(feast_ctx* ctx, const void* A, int dtype, int64_t n, int
   });
 }
 
-int feast_gemm_f64acc(feast_ctx* ctx, int method, int64_t M, int64_t N, int64_t K, const double* A, int64_t lda,
-                      const double* B, int64_t ldb, double* C, int64_t ldc) {
-  if (!ctx || !A || !B || !C || M < 1 || N < 1 || K < 1 || lda < M || ldb < K || ldc < M) return FEAST_ERR_ARG;
+int feast_gemm_f64acc(feast_ctx* ctx, int method, int dtype, int transA, int transB, int64_t M, int64_t N, int64_t K,
+                      double alpha, const void* A, int64_t lda, const void* B, int64_t ldb, double beta, void* C,
+                      int64_t ldc) {
+  if (!ctx || !A || !B || !C || M < 1 || N < 1 || K < 1 || ldc < M) return FEAST_ERR_ARG;
+  if (dtype != FEAST_R64 && dtype != FEAST_C128) return FEAST_ERR_ARG;
+  if ((transA != 0 && transA != 1) || (transB != 0 && transB != 1)) return FEAST_ERR_ARG;
+  if (lda < (transA ? K : M) || ldb < (transB ? N : K)) return FEAST_ERR_ARG;
+  if (!std::isfinite(alpha) || !std::isfinite(beta)) return FEAST_ERR_ARG;
   if (method != 0 && method != 1) return FEAST_ERR_ARG;
+  // the double-float route: real, no transposes, C = alpha A B
+  if (method == 1 && (dtype != FEAST_R64 || transA || transB || beta != 0.0)) return FEAST_ERR_ARG;
   if (M > INT32_MAX / kOzDigits || N > INT32_MAX / kOzDigits) return FEAST_ERR_ARG;
   return guarded(ctx, [&]() {
     FEAST_CUDA_TRY(cudaSetDevice(ctx->device));
     ctx->arena.reset();
     cudaStream_t st = ctx->stream;
+    const bool cplx = dtype == FEAST_C128;
     if (method == 0) {
       int* flag = dalloc<int>(ctx, 1);
       FEAST_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), st));
-      const OzOperand Ao = oz_operand(ctx->arena.alloc(oz_operand_bytes(M, K, true)), M, K, true);
-      const OzOperand Bo = oz_operand(ctx->arena.alloc(oz_operand_bytes(N, K, false)), N, K, false);
-      oz_split(A, 1, 0, K, lda, 1, Ao, st);  // row i: A[i + k lda]
-      oz_split(B, 1, 0, K, 1, ldb, Bo, st);  // column j: B[k + j ldb]
-      oz_gemm(M, N, Ao, Bo, C, ldc, 1, 0, flag, ctx->num_sms, st);
+      OzScratch w{};
+      for (int t = 0; t < (cplx ? 3 : 1); ++t) {
+        w.L[t] = ctx->arena.alloc(oz_operand_bytes(M, K, true));
+        w.R[t] = ctx->arena.alloc(oz_operand_bytes(N, K, false));
+      }
+      w.T = dalloc<double>(ctx, (cplx ? 2 : 1) * M * N);
+      w.T2 = cplx ? dalloc<double>(ctx, M * N) : nullptr;
+      oz_gemm_op(cplx, M, N, K, alpha, (const double*)A, lda, transA != 0, (const double*)B, ldb, transB != 0, beta,
+                 (double*)C, ldc, w, flag, ctx->num_sms, st);
       int f = 0;
       to_host(ctx, &f, flag, 1);
       if (f == DEV_BARRIER_TIMEOUT) return FEAST_ERR_TIMEOUT;
     } else {
       float* Ap = dalloc<float>(ctx, 2 * M * K);
       float* Bp = dalloc<float>(ctx, 2 * K * N);
-      split_df32(A, M, K, lda, 1, 0, Ap, Ap + M * K, st);
-      split_df32(B, K, N, ldb, 1, 0, Bp, Bp + K * N, st);
-      gemm_df32(M, N, K, 1.0, Ap, Ap + M * K, M, Bp, Bp + K * N, K, 0.0, C, ldc, 1, 0, st);
+      split_df32((const double*)A, M, K, lda, 1, 0, Ap, Ap + M * K, st);
+      split_df32((const double*)B, K, N, ldb, 1, 0, Bp, Bp + K * N, st);
+      gemm_df32(M, N, K, alpha, Ap, Ap + M * K, M, Bp, Bp + K * N, K, 0.0, (double*)C, ldc, 1, 0, st);
       sync(ctx);
     }
     return FEAST_OK;
   });
 }
-
 }  // extern "C"

@@ -276,6 +276,24 @@ __global__ void combine_3m_kernel(double* C, const double* T2, int64_t total) {
   }
 }
 
+__global__ void combine_axpby_kernel(double* C, int64_t ldc, int cplx, const double* T, const double* T2, int64_t M,
+                                     int64_t N, double alpha, double beta) {
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < M * N;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx % M, j = idx / M;
+    if (cplx) {
+      const double t1 = T[2 * idx], t3 = T[2 * idx + 1], t2 = T2[idx];
+      double* c = C + 2 * (i + j * ldc);
+      const double re = t1 - t2, im = (t3 - t1) - t2;
+      c[0] = beta != 0.0 ? alpha * re + beta * c[0] : alpha * re;
+      c[1] = beta != 0.0 ? alpha * im + beta * c[1] : alpha * im;
+    } else {
+      double* c = C + (i + j * ldc);
+      *c = beta != 0.0 ? alpha * T[idx] + beta * (*c) : alpha * T[idx];
+    }
+  }
+}
+
 __global__ void split_df32_kernel(const double* src, int64_t rows, int64_t cols, int64_t lds, int ss, int so,
                                   float* hi, float* lo) {
   const int64_t total = rows * cols;
@@ -367,6 +385,15 @@ void combine_3m(double* C, const double* T2, int64_t n, int64_t k, cudaStream_t 
   if (total <= 0) return;
   const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(total, 256), 16384));
   combine_3m_kernel<<<g, 256, 0, s>>>(C, T2, total);
+  FEAST_LAUNCH_CHECK();
+}
+
+void combine_axpby(double* C, int64_t ldc, bool cplx, const double* T, const double* T2, int64_t M, int64_t N,
+                   double alpha, double beta, cudaStream_t s) {
+  const int64_t total = M * N;
+  if (total <= 0) return;
+  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(total, 256), 16384));
+  combine_axpby_kernel<<<g, 256, 0, s>>>(C, ldc, cplx ? 1 : 0, T, T2, M, N, alpha, beta);
   FEAST_LAUNCH_CHECK();
 }
 

@@ -69,6 +69,13 @@ void gemm_df32(int64_t M, int64_t N, int64_t K, double alpha,
 // already sit in C (re, im) and T2 in a separate real array (n x k, ld n).
 void combine_3m(double* C, const double* T2, int64_t n, int64_t k, cudaStream_t s);
 
+// C (M x N, leading dim ldc) = alpha T + beta C.  Real (cplx = false): T is
+// M x N with leading dim M.  Complex (C interleaved): T holds the 3M parts
+// T1 (real slots) and T3 (imaginary slots) interleaved, T2 real, both with
+// leading dim M, and the value is (T1 - T2) + i (T3 - T1 - T2).
+void combine_axpby(double* C, int64_t ldc, bool cplx, const double* T, const double* T2, int64_t M, int64_t N,
+                   double alpha, double beta, cudaStream_t s);
+
 // Split FP64 values into hi/lo float planes: src element (i, j) at
 // src[(i + j*lds)*ss + so] (so = 2 with ss = 2: the sum Re + Im of a complex
 // element); planes are dense rows x cols (ld = rows).

@@ -33,6 +33,7 @@
 // its TMEM and skips the stores.
 #include <mutex>
 
+#include "gemm.cuh"
 #include "oz_gemm.cuh"
 #include "tcgen05.cuh"
 
@@ -426,6 +427,39 @@ void oz_gemm(int64_t M, int64_t N, const OzOperand& A, const OzOperand& B, doubl
                                                    (int)(A.kpad / OZ_BK), A.exps, B.exps, C, ldc, cs, co, status);
   FEAST_LAUNCH_CHECK();
   refine_timer_launch_end(s, (double)M * (double)N * (double)A.K);
+}
+
+void oz_gemm_op(bool cplx, int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda, bool transA,
+                const double* B, int64_t ldb, bool transB, double beta, double* C, int64_t ldc, const OzScratch& w,
+                int* status, int num_sms, cudaStream_t s) {
+  if (M <= 0 || N <= 0) return;
+  OzOperand L[3], R[3];
+  const int parts = cplx ? 3 : 1;
+  for (int t = 0; t < parts; ++t) {
+    L[t] = oz_operand(w.L[t], M, K, true);
+    R[t] = oz_operand(w.R[t], N, K, false);
+  }
+  // vectors: rows of op(A), columns of op(B).  Row i of A is strided by lda;
+  // row i of A^H is column i of A, conjugated (imaginary part negated).
+  const int64_t lse = transA ? 1 : lda, lsv = transA ? lda : 1;
+  const int64_t rse = transB ? ldb : 1, rsv = transB ? 1 : ldb;
+  if (cplx) {
+    static const int plain[3] = {0, 1, 2}, conjugated[3] = {0, 3, 4};  // Re, Im, Re + Im
+    const int* lm = transA ? conjugated : plain;
+    const int* rm = transB ? conjugated : plain;
+    for (int t = 0; t < 3; ++t) {
+      oz_split(A, 2, lm[t], K, lse, lsv, L[t], s);
+      oz_split(B, 2, rm[t], K, rse, rsv, R[t], s);
+    }
+    oz_gemm(M, N, L[0], R[0], w.T, M, 2, 0, status, num_sms, s);   // T1 in the real slots
+    oz_gemm(M, N, L[1], R[1], w.T2, M, 1, 0, status, num_sms, s);  // T2
+    oz_gemm(M, N, L[2], R[2], w.T, M, 2, 1, status, num_sms, s);   // T3 in the imaginary slots
+  } else {
+    oz_split(A, 1, 0, K, lse, lsv, L[0], s);
+    oz_split(B, 1, 0, K, rse, rsv, R[0], s);
+    oz_gemm(M, N, L[0], R[0], w.T, M, 1, 0, status, num_sms, s);
+  }
+  combine_axpby(C, ldc, cplx, w.T, w.T2, M, N, alpha, beta, s);
 }
 
 }  // namespace feast

@@ -50,4 +50,23 @@ void oz_split(const double* src, int ss, int mode, int64_t K, int64_t se, int64_
 void oz_gemm(int64_t M, int64_t N, const OzOperand& A, const OzOperand& B, double* C, int64_t ldc, int cs, int co,
              int* status, int num_sms, cudaStream_t s);
 
+// General FP64-accurate product C = alpha op(A) op(B) + beta C (alpha, beta
+// real) from column-major A, B, C: real (cplx = false) or interleaved complex
+// (three real products, 3M: T1 = Ar Br, T2 = Ai Bi, T3 = (Ar + Ai)(Br + Bi),
+// Re = T1 - T2, Im = T3 - T1 - T2).  op(A) is A (transA = false, M x K,
+// leading dim lda) or its conjugate transpose (A is K x M); the same for B
+// (K x N, or N x K when transB).  Scratch: L[0..2] and R[0..2] of
+// oz_operand_bytes(M, K, true) / oz_operand_bytes(N, K, false) bytes (one of
+// each for real), T of (cplx ? 2 : 1) M N doubles, T2 of M N doubles
+// (complex only).
+struct OzScratch {
+  void* L[3];
+  void* R[3];
+  double* T;
+  double* T2;
+};
+void oz_gemm_op(bool cplx, int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda, bool transA,
+                const double* B, int64_t ldb, bool transB, double beta, double* C, int64_t ldc, const OzScratch& w,
+                int* status, int num_sms, cudaStream_t s);
+
 }  // namespace feast

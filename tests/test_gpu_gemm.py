@@ -112,6 +112,48 @@ def test_gemm_f64acc_digits_beyond_fp32(ctx):
     assert np.median(np.abs(d - d_ref) / np.abs(d_ref)) < 0.01
 
 
+def _exact_complex(A, B, rows, cols):
+    # (Ar + i Ai)(Br + i Bi) entrywise from four exact real dot products
+    Ar, Ai, Br, Bi = A.real.copy(), A.imag.copy(), B.real.copy(), B.imag.copy()
+    re = np.array([O.dot_exact(np.concatenate([Ar[i], -Ai[i]]), np.concatenate([Br[:, j], Bi[:, j]]))
+                   for i, j in zip(rows, cols)])
+    im = np.array([O.dot_exact(np.concatenate([Ar[i], Ai[i]]), np.concatenate([Bi[:, j], Br[:, j]]))
+                   for i, j in zip(rows, cols)])
+    return re + 1j * im
+
+
+# sizes with several output tiles per persistent CTA (more tiles than SMs)
+# and a partial last K chunk (K % 128 != 0)
+@pytest.mark.parametrize("M,N,K", [(2000, 900, 900), (700, 300, 8192), (129, 97, 161)])
+@pytest.mark.parametrize("transA,transB", [(False, False), (True, False), (False, True), (True, True)])
+def test_gemm_f64acc_complex_ops(ctx, M, N, K, transA, transB):
+    rng = np.random.default_rng(M + N + K + 2 * transA + transB)
+    opA = rng.standard_normal((M, K)) + 1j * rng.standard_normal((M, K))
+    opB = rng.standard_normal((K, N)) + 1j * rng.standard_normal((K, N))
+    A = opA.conj().T if transA else opA
+    B = opB.conj().T if transB else opB
+    C0 = rng.standard_normal((M, N)) + 1j * rng.standard_normal((M, N))
+    alpha, beta = -1.0, 0.5
+    C = host(fg.feast_gemm_f64acc(ctx, cuda(np.asfortranarray(A)), cuda(np.asfortranarray(B)), 0,
+                                  transA=transA, transB=transB, alpha=alpha, beta=beta,
+                                  C=cuda(np.asfortranarray(C0))))
+    rows, cols = _sample(M, N, 150, 5)
+    ref = alpha * _exact_complex(opA, opB, rows, cols) + beta * C0[rows, cols]
+    scale = (np.abs(opA).max(axis=1)[rows] * np.abs(opB).max(axis=0)[cols]) * K
+    assert np.all(np.abs(C[rows, cols] - ref) <= 2.0 ** -42 * scale + 4e-16 * np.abs(ref))
+
+
+@pytest.mark.parametrize("transA", [False, True])
+def test_gemm_f64acc_real_transposed(ctx, transA):
+    rng = np.random.default_rng(21 + transA)
+    M, N, K = 1500, 700, 300
+    opA = rng.standard_normal((M, K))
+    B = rng.standard_normal((K, N))
+    A = opA.T.copy() if transA else opA
+    C = host(fg.feast_gemm_f64acc(ctx, cuda(np.asfortranarray(A)), cuda(B), 0, transA=transA))
+    _check(opA, B, C, 0, seed=3)
+
+
 def test_gemm_f64acc_rejects_bad_arguments(ctx):
     import torch
     A = torch.zeros((4, 3), dtype=torch.float64, device="cuda:0")
@@ -120,3 +162,5 @@ def test_gemm_f64acc_rejects_bad_arguments(ctx):
         fg.feast_gemm_f64acc(ctx, A, B, 0)
     with pytest.raises(RuntimeError):
         fg.feast_gemm_f64acc(ctx, A, A.T.contiguous(), 2)
+    with pytest.raises(RuntimeError):   # the double-float route has no transposes
+        fg.feast_gemm_f64acc(ctx, A, B, 1, transA=True)
