@@ -224,7 +224,18 @@ struct Solver {
   void* Loz[3] = {nullptr, nullptr, nullptr};
   double* Tmm = nullptr;
   double* Tmm2 = nullptr;
-  static constexpr double kOzMinWork = 1e8;  // M N K below which SIMT FP64 is used
+  // Routing of general products (Rayleigh-Ritz, orthonormalisation,
+  // eigensolver) through the digit-split GEMM: off.  Per-row / per-column
+  // digit scaling bounds the error by 2^-47 K max_k |a_ik| max_k |b_kj|,
+  // not by sum_k |a_ik| |b_kj| as FP64 does; on the n = 8192 RFEAST workload
+  // the filtered bases are graded enough that routed products held the
+  // Ritz residuals above 1e-10 ||A|| (measured: no convergence in 100
+  // iterations, against 2 with FP64 products).  The refinement products A Y,
+  // whose operands are not graded, keep the tensor cores.
+  static constexpr double kOzMinWork = 1e300;  // M N K below which SIMT FP64 is used
+  // Products whose left operand is a tall n x k block stay on SIMT even when
+  // routing is on (the eigensolver's k x k products may opt in).
+  bool allow_left_n = false;
   // Rayleigh-Ritz scratch
   S *Qb = nullptr, *Wb = nullptr, *Xr = nullptr, *AXr = nullptr, *T1 = nullptr, *T2 = nullptr;
   S *Ar0 = nullptr, *Ar = nullptr, *Vk = nullptr, *Gs = nullptr, *Ri = nullptr, *Cs = nullptr, *Cs2 = nullptr;
@@ -372,7 +383,7 @@ struct Solver {
   }
   void mm(int64_t Mr, int64_t Nc, int64_t K, c128 alpha, const S* Am, int64_t la, int opA, const S* Bm, int64_t lb,
           int opB, c128 beta, S* Cm, int64_t lc) {
-    if (mm_acc_ok(Mr, Nc, K, alpha, beta)) {
+    if ((opA != OP_N || allow_left_n) && mm_acc_ok(Mr, Nc, K, alpha, beta)) {
       mm_acc(Mr, Nc, K, alpha.re, Am, la, opA, Bm, lb, opB, beta.re, Cm, lc);
       return;
     }
@@ -631,6 +642,8 @@ struct Solver {
   // diagonal of H.  Returns false (nothing changed in H) when the Cholesky
   // factorisation breaks down.
   bool eig_two_phase(S* H, int64_t k, int* sweeps) {
+    allow_left_n = true;
+    struct Restore { bool& f; ~Restore() { f = false; } } restore{allow_left_n};
     convert_matrix<F32, S>(H32, k, H, k, k, k, st);
     jacobi_eigh<F32>(H32, k, k, V32, k, 4e-7, cw, ctx->num_sms, st, 40);
     int sw32 = 0;
