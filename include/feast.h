@@ -85,6 +85,11 @@ typedef struct {
   double refine_switch; /* mixed: while the previous iteration's max residual exceeds this and
                            fell at least tenfold, the next filter uses the FP32 solves without
                            FP64 refinement (default 0: always refine) */
+  int tc_solve;         /* mixed, n > 128: block updates of the complex-FP32 triangular solves
+                           on the FP32 SIMT pipes (0, default) or on the tensor cores (1: exact
+                           three-part TF32 split, FP32 accumulate; bound by the operand planes'
+                           L2 traffic, slower at m0 = 300) */
+  int reserved;
 } feast_opts;
 
 /* Per-call statistics of the last feast_interval_solve on a context. */
@@ -163,7 +168,9 @@ int feast_shifted_lu(feast_ctx* ctx, const void* A, int dtype, int64_t n, int64_
                      const double* z, int nz, int prec, void* LU, int32_t* perm);
 
 /* Y_e = M_e^{-1} B (adjoint = 0) or M_e^{-H} B (adjoint = 1) from factors of
- * feast_shifted_lu (same prec), without refinement.  B: device n x m complex
+ * feast_shifted_lu (same prec), without refinement.  FEAST_PREC_MIXED_TC
+ * also runs the block updates of the triangular solves on the tensor cores
+ * (the route opts.tc_solve = 1 selects in the solver).  B: device n x m complex
  * double; Y: device nz * n * m complex double, solve e at offset e*n*m. */
 int feast_shifted_solve(feast_ctx* ctx, const void* LU, const int32_t* perm, int64_t n, int nz,
                         int prec, int adjoint, const void* B, int64_t m, void* Y);

@@ -672,46 +672,77 @@ void lu_factor_batched(F* M, int64_t n, int64_t ld, int64_t stride, int nodes,
 
 template <typename F>
 void lu_solve_batched(const F* M, int64_t n, int64_t ld, int64_t stride, int nodes,
-                      F* Y, int64_t m, int64_t ystride, bool adjoint, cudaStream_t s) {
+                      F* Y, int64_t m, int64_t ystride, bool adjoint, cudaStream_t s, void* tc_planes, int* status,
+                      int num_sms) {
   if (m <= 0) return;
   constexpr int TBK = SolveBlock<F>::value;
-  const int64_t nblk = cdiv(n, TBK);
   dim3 gd((unsigned)cdiv(m, 8), nodes);
-  // forward substitution with L (normal) or U^H (adjoint)
-  for (int64_t bi = 0; bi < nblk; ++bi) {
-    const int64_t r0 = bi * TBK;
-    const int bs = (int)std::min<int64_t>(TBK, n - r0);
-    const int64_t r1 = r0 + bs;
-    trsm_diag_kernel<F, TBK><<<gd, 256, 0, s>>>(M, ld, stride, Y, n, m, ystride, r0, bs, adjoint ? 1 : 0);
-    FEAST_LAUNCH_CHECK();
-    if (r1 < n) {
-      GemmArgs g{};
-      g.M = n - r1; g.N = m; g.K = bs;
-      if (!adjoint) { g.A = M + r1 + r0 * ld; g.opA = OP_N; }
-      else { g.A = M + r0 + r1 * ld; g.opA = OP_C; }
-      g.lda = ld; g.strideA = stride;
-      g.B = Y + r0; g.ldb = n; g.strideB = ystride; g.opB = OP_N;
-      g.C = Y + r1; g.ldc = n; g.strideC = ystride;
-      g.alpha = C1(-1.0); g.beta = C1(1.0); g.batch = nodes; g.ksplit = 1;
-      gemm<F, F, F>(g, s);
+  // SIMT block update Y[c0 + i] -= op(block of the factor at a) Y[k0 + j]
+  auto simt_update = [&](int64_t rows, int64_t k, const F* a, int opA, int64_t c_off, int64_t k_off) {
+    GemmArgs g{};
+    g.M = rows; g.N = m; g.K = k;
+    g.A = a; g.opA = opA; g.lda = ld; g.strideA = stride;
+    g.B = Y + k_off; g.ldb = n; g.strideB = ystride; g.opB = OP_N;
+    g.C = Y + c_off; g.ldc = n; g.strideC = ystride;
+    g.alpha = C1(-1.0); g.beta = C1(1.0); g.batch = nodes; g.ksplit = 1;
+    gemm<F, F, F>(g, s);
+  };
+  // rows [b0, b1) solved by TBK-row diagonal blocks (forward: top down)
+  auto forward_rows = [&](int64_t b0, int64_t b1, int64_t upd_end) {
+    for (int64_t r0 = b0; r0 < b1; r0 += TBK) {
+      const int bs = (int)std::min<int64_t>(TBK, b1 - r0);
+      const int64_t r1 = r0 + bs;
+      trsm_diag_kernel<F, TBK><<<gd, 256, 0, s>>>(M, ld, stride, Y, n, m, ystride, r0, bs, adjoint ? 1 : 0);
+      FEAST_LAUNCH_CHECK();
+      if (r1 < upd_end) {
+        if (!adjoint) simt_update(upd_end - r1, bs, M + r1 + r0 * ld, OP_N, r1, r0);
+        else simt_update(upd_end - r1, bs, M + r0 + r1 * ld, OP_C, r1, r0);
+      }
     }
+  };
+  // rows [b0, b1) solved bottom up; updates reach rows [upd_begin, r0)
+  auto backward_rows = [&](int64_t b0, int64_t b1, int64_t upd_begin) {
+    for (int64_t r0 = b0 + ((b1 - b0 - 1) / TBK) * TBK; r0 >= b0; r0 -= TBK) {
+      const int bs = (int)std::min<int64_t>(TBK, b1 - r0);
+      trsm_diag_kernel<F, TBK><<<gd, 256, 0, s>>>(M, ld, stride, Y, n, m, ystride, r0, bs, adjoint ? 3 : 2);
+      FEAST_LAUNCH_CHECK();
+      if (r0 > upd_begin) {
+        if (!adjoint) simt_update(r0 - upd_begin, bs, M + upd_begin + r0 * ld, OP_N, upd_begin, r0);
+        else simt_update(r0 - upd_begin, bs, M + r0 + upd_begin * ld, OP_C, upd_begin, r0);
+      }
+    }
+  };
+  bool tc = false;
+  if constexpr (std::is_same<F, c64>::value) tc = tc_planes != nullptr && n > kTcBlock;
+  if (!tc) {
+    forward_rows(0, n, n);
+    backward_rows(0, n, 0);
+    return;
   }
-  // back substitution with U (normal) or L^H (adjoint)
-  for (int64_t bi = nblk - 1; bi >= 0; --bi) {
-    const int64_t r0 = bi * TBK;
-    const int bs = (int)std::min<int64_t>(TBK, n - r0);
-    trsm_diag_kernel<F, TBK><<<gd, 256, 0, s>>>(M, ld, stride, Y, n, m, ystride, r0, bs, adjoint ? 3 : 2);
-    FEAST_LAUNCH_CHECK();
-    if (r0 > 0) {
-      GemmArgs g{};
-      g.M = r0; g.N = m; g.K = bs;
-      if (!adjoint) { g.A = M + r0 * ld; g.opA = OP_N; }
-      else { g.A = M + r0; g.opA = OP_C; }
-      g.lda = ld; g.strideA = stride;
-      g.B = Y + r0; g.ldb = n; g.strideB = ystride; g.opB = OP_N;
-      g.C = Y; g.ldc = n; g.strideC = ystride;
-      g.alpha = C1(-1.0); g.beta = C1(1.0); g.batch = nodes; g.ksplit = 1;
-      gemm<F, F, F>(g, s);
+  if constexpr (std::is_same<F, c64>::value) {
+    // 128-row blocks: the diagonal block by the SIMT path above, the update
+    // of the remaining rows on the tensor cores
+    const int64_t TB2 = kTcBlock;
+    for (int64_t r0 = 0; r0 < n; r0 += TB2) {
+      const int bs = (int)std::min<int64_t>(TB2, n - r0);
+      const int64_t r1 = r0 + bs;
+      forward_rows(r0, r1, r1);
+      if (r1 < n) {
+        // forward: Y[r1:] -= L[r1:, r0:r1] Y[r0:r1]; adjoint: U[r0:r1, r1:]^H
+        const TcSrc a = adjoint ? TcSrc{M, stride, ld, r0, r1, false, true} : TcSrc{M, stride, ld, r1, r0, true, false};
+        const TcSrc b{Y, ystride, n, r0, 0, false, false};
+        tc_block_update(a, b, bs, n - r1, m, Y, n, ystride, r1, 0, nodes, tc_planes, status, num_sms, s);
+      }
+    }
+    for (int64_t r0 = ((n - 1) / TB2) * TB2; r0 >= 0; r0 -= TB2) {
+      const int bs = (int)std::min<int64_t>(TB2, n - r0);
+      backward_rows(r0, r0 + bs, r0);
+      if (r0 > 0) {
+        // backward: Y[:r0] -= U[:r0, r0:r1] Y[r0:r1]; adjoint: L[r0:r1, :r0]^H
+        const TcSrc a = adjoint ? TcSrc{M, stride, ld, r0, 0, false, true} : TcSrc{M, stride, ld, 0, r0, true, false};
+        const TcSrc b{Y, ystride, n, r0, 0, false, false};
+        tc_block_update(a, b, bs, r0, m, Y, n, ystride, 0, 0, nodes, tc_planes, status, num_sms, s);
+      }
     }
   }
 }
@@ -736,7 +767,7 @@ void permute_out(TO* Out, int64_t ostride, const F* Y, int64_t ystride, int64_t 
   template void lu_factor_batched<F>(F*, int64_t, int64_t, int64_t, int, int32_t*, int32_t*,        \
                                      const PanelWork&, int, cudaStream_t);                          \
   template void lu_solve_batched<F>(const F*, int64_t, int64_t, int64_t, int, F*, int64_t, int64_t, \
-                                    bool, cudaStream_t);                                             \
+                                    bool, cudaStream_t, void*, int*, int);                           \
   template void form_shifted<F, double>(F*, int64_t, int64_t, int64_t, int, const double*, int64_t, \
                                         const c128*, cudaStream_t);                                  \
   template void form_shifted<F, c128>(F*, int64_t, int64_t, int64_t, int, const c128*, int64_t,     \

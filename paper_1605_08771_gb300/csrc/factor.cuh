@@ -50,10 +50,14 @@ void lu_factor_batched(F* M, int64_t n, int64_t ld, int64_t stride, int nodes,
 
 // Y_e <- (P^T L U)^{-1} Y_e  (adjoint = false) or (P^T L U)^{-H} Y_e
 // (adjoint = true) for e = 0..nodes-1, Y_e = Y + e*ystride (n x m, ld n).
-// The row permutation is applied by permute_in / permute_out.
+// The row permutation is applied by permute_in / permute_out.  Complex-FP32
+// factors with tc_planes (scratch of tc_update_planes_bytes(n, m, nodes)
+// bytes) take the block updates of the triangular solves on the tensor
+// cores (128-row blocks); otherwise SIMT (64-row blocks).
 template <typename F>
 void lu_solve_batched(const F* M, int64_t n, int64_t ld, int64_t stride, int nodes,
-                      F* Y, int64_t m, int64_t ystride, bool adjoint, cudaStream_t s);
+                      F* Y, int64_t m, int64_t ystride, bool adjoint, cudaStream_t s,
+                      void* tc_planes = nullptr, int* status = nullptr, int num_sms = 0);
 
 // Y_e = P B_e (normal) or B_e (adjoint) converted to F;  B_e = B + e*bstride is
 // n x m with ld ldb (bstride = 0: one right-hand side block for every node).

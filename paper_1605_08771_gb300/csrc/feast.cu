@@ -216,6 +216,8 @@ struct Solver {
   int64_t bpl_cols = 0;
   // tensor-core refinement products: digit planes of A (Re, Im, Re + Im for
   // complex A) and buffers for those of the right operand
+  // tensor-core block updates of the complex-FP32 triangular solves
+  void* solve_planes = nullptr;
   bool use_oz = false;
   OzOperand Aoz[3];
   void* Boz[3] = {nullptr, nullptr, nullptr};
@@ -296,7 +298,7 @@ struct Solver {
     perm = dalloc<int32_t>(ctx, (int64_t)nc * n);
     const int pmax = std::max(1, ctx->num_sms * 8);
     pw = panel_work_carve(ctx->arena.alloc(panel_work_bytes(nc, pmax, eb)), nc, pmax, eb);
-    if (o.prec == FEAST_PREC_MIXED_TC) pw.tc_planes = ctx->arena.alloc(tc_update_planes_bytes(n, nc));
+    if (o.prec == FEAST_PREC_MIXED_TC) pw.tc_planes = ctx->arena.alloc(tc_update_planes_bytes(n, n, nc));
   }
   void alloc_filter(int64_t m) {
     const int64_t nm = n * m;
@@ -307,6 +309,8 @@ struct Solver {
       Yw = dalloc<c128>(ctx, E * nm);
       AY = dalloc<c128>(ctx, E * nm);
       Yc = dalloc<c64>(ctx, E * nm);
+      if (o.tc_solve == 1 && n > kTcBlock)
+        solve_planes = ctx->arena.alloc(tc_update_planes_bytes(n, m, nc));
       bpl_cols = std::max<int64_t>(E * m, kmax);
       if (use_oz) {
         // rows of A are read through its Hermitian symmetry, A(i, k) =
@@ -456,7 +460,6 @@ struct Solver {
   }
   // a timed-out wait inside the tensor-core GEMM
   void check_oz_status() {
-    if (!use_oz) return;
     int f = 0;
     to_host(ctx, &f, d_flag, 1);
     if (f == DEV_BARRIER_TIMEOUT) throw FeastError{FEAST_ERR_TIMEOUT};
@@ -520,11 +523,11 @@ struct Solver {
     const int64_t nm = n * m;
     const c64* Mf = (const c64*)M;
     permute_in<c64, TB>(Yc, nm, B, ldb, bstride, n, m, perm, nc, false, st);
-    lu_solve_batched<c64>(Mf, n, n, n * n, nc, Yc, m, nm, false, st);
+    lu_solve_batched<c64>(Mf, n, n, n * n, nc, Yc, m, nm, false, st, solve_planes, d_flag, ctx->num_sms);
     permute_out<c64, c128>(Y, nm, Yc, nm, n, m, perm, nc, false, accumulate, st);
     if (kCplx) {
       permute_in<c64, TB>(Yc + nc * nm, nm, B + nc * bstride, ldb, bstride, n, m, perm, nc, true, st);
-      lu_solve_batched<c64>(Mf, n, n, n * n, nc, Yc + nc * nm, m, nm, true, st);
+      lu_solve_batched<c64>(Mf, n, n, n * n, nc, Yc + nc * nm, m, nm, true, st, solve_planes, d_flag, ctx->num_sms);
       permute_out<c64, c128>(Y + nc * nm, nm, Yc + nc * nm, nm, n, m, perm, nc, true, accumulate, st);
     }
   }
@@ -1284,6 +1287,7 @@ int feast_interval_solve(feast_ctx* ctx, const void* A, int dtype, int64_t n, in
   if (o.variant < 0 || o.variant > 2 || o.prec < 0 || o.prec > 2 || o.max_iter < 1 || !(o.aspect > 0)) return FEAST_ERR_ARG;
   if (o.variant != FEAST_PLAIN && (o.s < 1 || (int64_t)o.s * m0 > 65536)) return FEAST_ERR_ARG;
   if (o.refine_max < 0 || !(o.refine_switch >= 0.0) || o.refine_gemm < 0 || o.refine_gemm > 1) return FEAST_ERR_ARG;
+  if (o.tc_solve < 0 || o.tc_solve > 1) return FEAST_ERR_ARG;
   *m_found = 0;
   *iterations = 0;
   return guarded(ctx, [&]() {
@@ -1302,7 +1306,8 @@ int feast_filter_apply(feast_ctx* ctx, const void* A, int dtype, int64_t n, int6
   if (!X || !Y || m < 1) return FEAST_ERR_ARG;
   feast_opts o;
   if (opts) o = *opts; else feast_opts_default(&o);
-  if (o.prec < 0 || o.prec > 2 || !(o.aspect > 0) || o.refine_max < 0 || o.refine_gemm < 0 || o.refine_gemm > 1)
+  if (o.prec < 0 || o.prec > 2 || !(o.aspect > 0) || o.refine_max < 0 || o.refine_gemm < 0 || o.refine_gemm > 1 ||
+      o.tc_solve < 0 || o.tc_solve > 1)
     return FEAST_ERR_ARG;
   return guarded(ctx, [&]() {
     FEAST_CUDA_TRY(cudaSetDevice(ctx->device));
@@ -1342,7 +1347,7 @@ int feast_shifted_lu(feast_ctx* ctx, const void* A, int dtype, int64_t n, int64_
     const size_t eb = prec == FEAST_PREC_F64 ? sizeof(c128) : sizeof(c64);
     const int pmax = std::max(1, ctx->num_sms * 8);
     PanelWork pw = panel_work_carve(ctx->arena.alloc(panel_work_bytes(nz, pmax, eb)), nz, pmax, eb);
-    if (prec == FEAST_PREC_MIXED_TC) pw.tc_planes = ctx->arena.alloc(tc_update_planes_bytes(n, nz));
+    if (prec == FEAST_PREC_MIXED_TC) pw.tc_planes = ctx->arena.alloc(tc_update_planes_bytes(n, n, nz));
     c128* dz = dalloc<c128>(ctx, nz);
     to_dev(ctx, dz, (const c128*)z, nz);
     int32_t* ipiv = dalloc<int32_t>(ctx, (int64_t)nz * n);
@@ -1376,14 +1381,22 @@ int feast_shifted_solve(feast_ctx* ctx, const void* LU, const int32_t* perm, int
     auto go = [&](auto ftag) {
       using F = decltype(ftag);
       F* W = dalloc<F>(ctx, nz * nm);
+      // FEAST_PREC_MIXED_TC: block updates on the tensor cores (n > 128)
+      void* planes = nullptr;
+      int* flag = dalloc<int>(ctx, 1);
+      FEAST_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
+      if (prec == FEAST_PREC_MIXED_TC && n > kTcBlock) planes = ctx->arena.alloc(tc_update_planes_bytes(n, m, nz));
       permute_in<F, c128>(W, nm, (const c128*)B, n, 0, n, m, perm, nz, adjoint != 0, ctx->stream);
-      lu_solve_batched<F>((const F*)LU, n, n, n * n, nz, W, m, nm, adjoint != 0, ctx->stream);
+      lu_solve_batched<F>((const F*)LU, n, n, n * n, nz, W, m, nm, adjoint != 0, ctx->stream, planes, flag,
+                          ctx->num_sms);
       permute_out<F, c128>((c128*)Y, nm, W, nm, n, m, perm, nz, adjoint != 0, false, ctx->stream);
+      int f = 0;
+      to_host(ctx, &f, flag, 1);
+      return f == DEV_BARRIER_TIMEOUT ? FEAST_ERR_TIMEOUT : FEAST_OK;
     };
-    if (prec == FEAST_PREC_F64) go(c128{});
-    else go(c64{});
+    const int r = prec == FEAST_PREC_F64 ? go(c128{}) : go(c64{});
     sync(ctx);
-    return FEAST_OK;
+    return r;
   });
 }
 

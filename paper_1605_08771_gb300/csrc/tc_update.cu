@@ -1,6 +1,8 @@
-// Tensor-core (tcgen05) trailing update of the complex-FP32 shifted LU:
-//     A22 -= L21 U12          for every quadrature node
-// on the 5th-generation tensor cores of sm_103a.
+// Tensor-core (tcgen05) complex-FP32 rank-kb update C -= A B for every
+// quadrature node, on the 5th-generation tensor cores of sm_103a.  It serves
+// the trailing update of the shifted LU (A22 -= L21 U12) and the block
+// updates of the triangular solves (Y2 -= L21 Y1, Y1 -= U12 Y2, and the same
+// with conjugate-transposed factor blocks for the adjoint solves).
 //
 // Complex products become one real GEMM through the 2x2 real embedding with
 // interleaved rows: row 2i of the real left operand holds [Re L_i, -Im L_i],
@@ -16,11 +18,11 @@
 // made the first refined residual 3.5x larger than FP32 factors do, with or
 // without the lo*lo product, and cost an extra refinement step.)
 //
-// Kernel: one 128 x 128 output tile per CTA, four warps.  Thread 0 issues the
+// Kernel: 128 x 128 output tiles, persistent CTAs of four warps.  Thread 0 issues the
 // TMA loads of the 128B-swizzled K-major operand tiles, thread 32 issues the
 // tcgen05.mma instructions (M = 128, N = 128, K = 8) into a 128-column TMEM
 // accumulator, and all four warps read the accumulator back with tcgen05.ld
-// for the epilogue A22 -= D.  Every mbarrier wait is bounded by a wall-clock
+// for the epilogue C -= D.  Every mbarrier wait is bounded by a wall-clock
 // limit; on expiry the kernel records the failure, lets the issued MMAs
 // complete, frees its TMEM and skips the stores.
 #include <mutex>
@@ -56,8 +58,9 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t da, uint64_t db
 }
 
 __global__ void __launch_bounds__(128, 1)
-tc_update_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, c64* M,
-                 int64_t ld, int64_t stride, int64_t r1, int64_t R, int64_t C, int rows_pad, int cols_pad,
+tc_update_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, c64* Cm,
+                 int64_t ldc, int64_t cstride, int64_t c_r0, int64_t c_c0, int64_t R, int64_t C, int rows_pad,
+                 int cols_pad,
                  int ksteps, int nodes, int a_part_rows, int b_part_rows, int* status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -160,7 +163,7 @@ tc_update_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
     const int64_t rr = (int64_t)mt * TC_BM + warp * 32 + lane;  // real row within this node
     const int64_t i = rr >> 1;
     const int part = (int)(rr & 1);
-    float* Mb = (float*)(M + (int64_t)node * stride);
+    float* Cb = (float*)(Cm + (int64_t)node * cstride);
 #pragma unroll 1
     for (int cc = 0; cc < TC_BN / 32; ++cc) {
       uint32_t v[32];
@@ -180,7 +183,7 @@ tc_update_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
         for (int c = 0; c < 32; ++c) {
           const int64_t j = (int64_t)nt * TC_BN + cc * 32 + c;
           if (j < C) {
-            float* p = Mb + 2 * ((r1 + i) + (r1 + j) * ld) + part;
+            float* p = Cb + 2 * ((c_r0 + i) + (c_c0 + j) * ldc) + part;
             *p = *p - __uint_as_float(v[c]);
           }
         }
@@ -212,29 +215,36 @@ __device__ __forceinline__ void tf32_split3(float x, float& h, float& m, float& 
   l = tf32_rna(r - m);    // r - m exact, and it has at most 11 significant bits
 }
 
-// Operand packing: left operand (rows_pad real rows x Kp) from L21 and right
-// operand (cols_pad rows x Kp) from U12, each as three TF32 planes (hi, mid,
-// lo; plane stride a_part / b_part floats), K contiguous (Kp >= 2 kb).
-// 32 x 32 complex tiles are staged through shared memory so both the reads of
-// the column-major factor and the writes of the K-major planes are coalesced.
-__global__ void tc_pack_kernel(const c64* M, int64_t ld, int64_t stride, int64_t k0, int kb, int64_t r1, int64_t R,
-                               int64_t C, int rows_pad, int cols_pad, int Kp, float* A, int64_t a_part, float* B,
-                               int64_t b_part) {
+// Operand packing into three TF32 planes (hi, mid, lo; plane stride a_part /
+// b_part floats), K contiguous (Kp >= 2 kb).  Left operand: rows_pad real
+// rows, row 2i = [Re A_i, -Im A_i], row 2i+1 = [Im A_i, Re A_i]; right
+// operand: cols_pad rows, row j = [Re B_:j ; Im B_:j].  Each source block is
+// read through TcSrc (conjugate transposes included); 32 x 32 complex tiles
+// are staged through shared memory, the global reads running along the
+// source's leading dimension.
+__device__ __forceinline__ c64 tc_src_load(const TcSrc& src, int node, int64_t v, int64_t k) {
+  const c64* b = src.base + (int64_t)node * src.node_stride;
+  if (!src.conj_t) return b[(src.r0 + (src.vec_rows ? v : k)) + (src.c0 + (src.vec_rows ? k : v)) * src.ld];
+  const c64 x = b[(src.r0 + (src.vec_rows ? v : k)) + (src.c0 + (src.vec_rows ? k : v)) * src.ld];
+  return c64{x.re, -x.im};
+}
+
+__global__ void tc_pack_kernel(TcSrc sa, TcSrc sb, int kb, int64_t R, int64_t C, int rows_pad, int cols_pad, int Kp,
+                               float* A, int64_t a_part, float* B, int64_t b_part) {
   __shared__ c64 tile[32][33];
   const int node = blockIdx.z;
-  const c64* Mb = M + (int64_t)node * stride;
   const bool left = blockIdx.y == 0;
+  const TcSrc& src = left ? sa : sb;
   const int64_t base = (int64_t)blockIdx.x * 32;  // complex rows (left) or columns (right)
   const int64_t lim = left ? R : C;
   if (base >= (left ? rows_pad / 2 : cols_pad)) return;
   for (int kc = 0; kc < Kp / 2; kc += 32) {       // k-chunks of the complex operand
     __syncthreads();
     for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
-      int q, k;
-      if (left) { q = t % 32; k = t / 32; } else { k = t % 32; q = t / 32; }
+      int q, k;  // consecutive threads along the source's leading dimension
+      if (src.vec_rows) { q = t % 32; k = t / 32; } else { k = t % 32; q = t / 32; }
       c64 v{0.f, 0.f};
-      if (base + q < lim && kc + k < kb)
-        v = left ? Mb[(r1 + base + q) + (k0 + kc + k) * ld] : Mb[(k0 + kc + k) + (r1 + base + q) * ld];
+      if (base + q < lim && kc + k < kb) v = tc_src_load(src, node, base + q, kc + k);
       tile[q][k] = v;
     }
     __syncthreads();
@@ -309,17 +319,17 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encode_fn() {
   return fn;
 }
 
-size_t tc_update_planes_bytes(int64_t n, int nodes) {
-  const int64_t rp = cdiv(2 * n, TC_BM) * TC_BM, cp = cdiv(n, TC_BN) * TC_BN;
+size_t tc_update_planes_bytes(int64_t rows, int64_t cols, int nodes) {
+  const int64_t rp = cdiv(2 * rows, TC_BM) * TC_BM, cp = cdiv(cols, TC_BN) * TC_BN;
   const int64_t Kp = cdiv(2 * kTcBlock, TC_BK) * TC_BK;
   return (size_t)4 * 3 * (size_t)nodes * (size_t)(rp + cp) * (size_t)Kp + 4096;
 }
 
-void tc_trailing_update(c64* M, int64_t n, int64_t ld, int64_t stride, int nodes, int64_t k0, int kb, void* planes,
-                        int* status, int num_sms, cudaStream_t s) {
-  const int64_t r1 = k0 + kb;
-  const int64_t R = n - r1, C = n - r1;
-  if (R <= 0) return;
+void tc_block_update(const TcSrc& a, const TcSrc& b, int kb, int64_t R, int64_t C, c64* Cm, int64_t ldc,
+                     int64_t cstride, int64_t c_r0, int64_t c_c0, int nodes, void* planes, int* status, int num_sms,
+                     cudaStream_t s) {
+  if (R <= 0 || C <= 0 || kb <= 0) return;
+  if (kb > kTcBlock) throw CudaFailure(cudaErrorInvalidValue);
   const int rows_pad = (int)(cdiv(2 * R, TC_BM) * TC_BM);
   const int cols_pad = (int)(cdiv(C, TC_BN) * TC_BN);
   const int Kp = (int)(cdiv(2 * kb, TC_BK) * TC_BK);
@@ -329,23 +339,32 @@ void tc_trailing_update(c64* M, int64_t n, int64_t ld, int64_t stride, int nodes
   {
     const int64_t blocks = std::max<int64_t>(rows_pad / 64, cols_pad / 32);
     dim3 g((unsigned)blocks, 2, nodes);
-    tc_pack_kernel<<<g, 256, 0, s>>>(M, ld, stride, k0, kb, r1, R, C, rows_pad, cols_pad, Kp, A, a_rows * Kp, B,
-                                     b_rows * Kp);
+    tc_pack_kernel<<<g, 256, 0, s>>>(a, b, kb, R, C, rows_pad, cols_pad, Kp, A, a_rows * Kp, B, b_rows * Kp);
     FEAST_LAUNCH_CHECK();
   }
   CUtensorMap mA, mB;
   make_map(&mA, A, 3 * a_rows, Kp);
   make_map(&mB, B, 3 * b_rows, Kp);
-  static bool attr = false;
-  if (!attr) {
-    FEAST_CUDA_TRY(cudaFuncSetAttribute(tc_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES));
-    attr = true;
-  }
+  static std::once_flag attr;
+  cudaError_t aerr = cudaSuccess;
+  std::call_once(attr, [&] {
+    aerr = cudaFuncSetAttribute(tc_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES);
+  });
+  FEAST_CUDA_TRY(aerr);
   const int64_t tiles = (int64_t)(rows_pad / TC_BM) * (cols_pad / TC_BN) * nodes;
   const unsigned grid = (unsigned)std::min<int64_t>(tiles, num_sms);
-  tc_update_kernel<<<grid, 128, TC_SMEM_BYTES, s>>>(mA, mB, M, ld, stride, r1, R, C, rows_pad, cols_pad, Kp / TC_BK,
-                                                    nodes, (int)a_rows, (int)b_rows, status);
+  tc_update_kernel<<<grid, 128, TC_SMEM_BYTES, s>>>(mA, mB, Cm, ldc, cstride, c_r0, c_c0, R, C, rows_pad, cols_pad,
+                                                    Kp / TC_BK, nodes, (int)a_rows, (int)b_rows, status);
   FEAST_LAUNCH_CHECK();
+}
+
+void tc_trailing_update(c64* M, int64_t n, int64_t ld, int64_t stride, int nodes, int64_t k0, int kb, void* planes,
+                        int* status, int num_sms, cudaStream_t s) {
+  const int64_t r1 = k0 + kb;
+  // A22 -= L21 U12: L21 = M[r1:, k0:r1] (vectors along rows), U12 = M[k0:r1, r1:]
+  const TcSrc a{M, stride, ld, r1, k0, true, false};
+  const TcSrc b{M, stride, ld, k0, r1, false, false};
+  tc_block_update(a, b, kb, n - r1, n - r1, M, ld, stride, r1, r1, nodes, planes, status, num_sms, s);
 }
 
 }  // namespace feast

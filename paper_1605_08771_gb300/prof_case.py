@@ -27,6 +27,7 @@ def main():
     ap.add_argument("--m", type=int, default=0)
     ap.add_argument("--prec", default="mixed")
     ap.add_argument("--refine-gemm", type=int, default=0, help="0 tensor cores (digit split), 1 double-float")
+    ap.add_argument("--tc-solve", type=int, default=0, help="0 SIMT block updates of the solves, 1 tensor cores")
     args = ap.parse_args()
     import torch
 
@@ -47,10 +48,11 @@ def main():
             g = torch.Generator(device="cuda:0")
             g.manual_seed(3)
             X = torch.randn((n, m), generator=g, dtype=torch.complex128, device="cuda:0")
-            f.filter(A, a, b, 8, X, prec=args.prec, anorm=anorm, refine_gemm=args.refine_gemm)
+            f.filter(A, a, b, 8, X, prec=args.prec, anorm=anorm, refine_gemm=args.refine_gemm,
+                     tc_solve=args.tc_solve)
         else:
             out = f.solve(A, a, b, m, 8, 1e-10, variant="rfeast", prec=args.prec, anorm=anorm,
-                          refine_gemm=args.refine_gemm)
+                          refine_gemm=args.refine_gemm, tc_solve=args.tc_solve)
             print("status", out["status"], "pairs", out["evals"].size, "iterations", out["iterations"])
     torch.cuda.synchronize()
 
