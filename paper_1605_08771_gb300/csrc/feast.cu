@@ -200,8 +200,6 @@ struct Solver {
   int* d_act = nullptr;
   int refine_steps = 0;
   bool refine_now = true;      // mixed: refine the next filter application
-  // mixed: double-float planes of A (hi/lo of Re, then of Im) and of the
-  // right-hand block of an A product
   // two-phase reduced eigensolver scratch (FP32 Jacobi, FP64 polish)
   using F32 = typename std::conditional<std::is_same<S, c128>::value, c64, float>::type;
   static constexpr int64_t kEigMixedMin = 64;
@@ -210,34 +208,26 @@ struct Solver {
   S* Ve = nullptr;
   S* Te = nullptr;
   S* T2e = nullptr;
+  // mixed, opts.refine_gemm = 1: double-float planes of A (hi/lo of Re, Im,
+  // Re + Im) and of the right-hand block of an A product
   float* Apl = nullptr;
   float* Bpl = nullptr;
   double* Tdf = nullptr;
   int64_t bpl_cols = 0;
-  // tensor-core refinement products: digit planes of A (Re, Im, Re + Im for
+  // mixed, opts.refine_gemm = 0: digit planes of A (Re, Im, Re + Im for
   // complex A) and buffers for those of the right operand
-  // tensor-core block updates of the complex-FP32 triangular solves
-  void* solve_planes = nullptr;
   bool use_oz = false;
   OzOperand Aoz[3];
   void* Boz[3] = {nullptr, nullptr, nullptr};
-  // general FP64-accurate products on the tensor cores (mixed path): left
-  // operand planes and the 3M partial products
-  void* Loz[3] = {nullptr, nullptr, nullptr};
-  double* Tmm = nullptr;
-  double* Tmm2 = nullptr;
-  // Routing of general products (Rayleigh-Ritz, orthonormalisation,
-  // eigensolver) through the digit-split GEMM: off.  Per-row / per-column
-  // digit scaling bounds the error by 2^-47 K max_k |a_ik| max_k |b_kj|,
-  // not by sum_k |a_ik| |b_kj| as FP64 does; on the n = 8192 RFEAST workload
-  // the filtered bases are graded enough that routed products held the
-  // Ritz residuals above 1e-10 ||A|| (measured: no convergence in 100
-  // iterations, against 2 with FP64 products).  The refinement products A Y,
-  // whose operands are not graded, keep the tensor cores.
-  static constexpr double kOzMinWork = 1e300;  // M N K below which SIMT FP64 is used
-  // Products whose left operand is a tall n x k block stay on SIMT even when
-  // routing is on (the eigensolver's k x k products may opt in).
-  bool allow_left_n = false;
+  // mixed, opts.tc_solve = 1: operand planes of the tensor-core block
+  // updates of the complex-FP32 triangular solves
+  void* solve_planes = nullptr;
+  // The Rayleigh-Ritz, orthonormalisation and eigensolver products stay FP64
+  // on this path.  Routed through the digit-split GEMM (error bounded by
+  // max-based norms) the graded filtered bases held the n = 8192 RFEAST
+  // residuals above 1e-10 ||A||; through the double-float GEMM (termwise
+  // 2^-44) the edge-cluster pairs, whose filter response is within rounding
+  // of 1/2, took 4 iterations instead of 2.
   // Rayleigh-Ritz scratch
   S *Qb = nullptr, *Wb = nullptr, *Xr = nullptr, *AXr = nullptr, *T1 = nullptr, *T2 = nullptr;
   S *Ar0 = nullptr, *Ar = nullptr, *Vk = nullptr, *Gs = nullptr, *Ri = nullptr, *Cs = nullptr, *Cs2 = nullptr;
@@ -350,12 +340,6 @@ struct Solver {
     const int64_t kk = kmax * kmax;
     Ar0 = dalloc<S>(ctx, kk); Ar = dalloc<S>(ctx, kk); Vk = dalloc<S>(ctx, kk); Gs = dalloc<S>(ctx, kk);
     Ri = dalloc<S>(ctx, kk); Cs = dalloc<S>(ctx, kk); Cs2 = dalloc<S>(ctx, kk);
-    if (use_oz && (double)n * kmax * kmax >= kOzMinWork) {
-      const size_t lb = std::max(oz_operand_bytes(kmax, n, true), oz_operand_bytes(n, kmax, true));
-      for (int t = 0; t < (kCplx ? 3 : 1); ++t) Loz[t] = ctx->arena.alloc(lb);
-      Tmm = dalloc<double>(ctx, (kCplx ? 2 : 1) * n * kmax);
-      if (kCplx) Tmm2 = dalloc<double>(ctx, n * kmax);
-    }
     if (kmax >= kEigMixedMin) {
       H32 = dalloc<F32>(ctx, kk); V32 = dalloc<F32>(ctx, kk);
       Ve = dalloc<S>(ctx, kk); Te = dalloc<S>(ctx, kk); T2e = dalloc<S>(ctx, kk);
@@ -368,38 +352,14 @@ struct Solver {
     d_idx = dalloc<int>(ctx, kmax);
   }
 
-  // ---- GEMM helpers ----
-  // products large enough for the tensor cores (mixed path, scratch present)
-  bool mm_acc_ok(int64_t Mr, int64_t Nc, int64_t K, c128 alpha, c128 beta) const {
-    if (!use_oz || !Loz[0] || !Boz[0] || alpha.im != 0.0 || beta.im != 0.0) return false;
-    if ((double)Mr * (double)Nc * (double)K < kOzMinWork) return false;
-    if (Mr * Nc > n * kmax || Nc > bpl_cols) return false;
-    const size_t lb = std::max(oz_operand_bytes(kmax, n, true), oz_operand_bytes(n, kmax, true));
-    return oz_operand_bytes(Mr, K, true) <= lb && oz_operand_bytes(Nc, K, false) <= oz_operand_bytes(bpl_cols, n, false);
-  }
-  // C = alpha op(A) op(B) + beta C (alpha, beta real) with FP64-accurate
-  // tensor-core products (oz_gemm_op; complex by the three real products 3M)
-  void mm_acc(int64_t Mr, int64_t Nc, int64_t K, double alpha, const S* Am, int64_t la, int opA, const S* Bm,
-              int64_t lb, int opB, double beta, S* Cm, int64_t lc) {
-    OzScratch w{{Loz[0], Loz[1], Loz[2]}, {Boz[0], Boz[1], Boz[2]}, Tmm, Tmm2};
-    oz_gemm_op(kCplx, Mr, Nc, K, alpha, (const double*)Am, la, opA != OP_N, (const double*)Bm, lb, opB != OP_N, beta,
-               (double*)Cm, lc, w, d_flag, ctx->num_sms, st);
-  }
+  // ---- small GEMM helpers ----
   void mm(int64_t Mr, int64_t Nc, int64_t K, c128 alpha, const S* Am, int64_t la, int opA, const S* Bm, int64_t lb,
           int opB, c128 beta, S* Cm, int64_t lc) {
-    if ((opA != OP_N || allow_left_n) && mm_acc_ok(Mr, Nc, K, alpha, beta)) {
-      mm_acc(Mr, Nc, K, alpha.re, Am, la, opA, Bm, lb, opB, beta.re, Cm, lc);
-      return;
-    }
     gemm_simple<S, S, S>(Mr, Nc, K, alpha, Am, la, opA, Bm, lb, opB, beta, Cm, lc, st);
   }
   // C (Mr x Nc) = op(A) op(B) with a long reduction K: split-K
   void mm_reduce(int64_t Mr, int64_t Nc, int64_t K, const S* Am, int64_t la, int opA, const S* Bm, int64_t lb,
                  int opB, S* Cm, int64_t lc) {
-    if (mm_acc_ok(Mr, Nc, K, C1(1.0), C1(0.0))) {
-      mm_acc(Mr, Nc, K, 1.0, Am, la, opA, Bm, lb, opB, 0.0, Cm, lc);
-      return;
-    }
     int ks = (int)std::max<int64_t>(1, std::min<int64_t>(32, K / 256));
     while (ks > 1 && (int64_t)ks * lc * Nc > part_elems) --ks;
     gemm_simple<S, S, S>(Mr, Nc, K, C1(1.0), Am, la, opA, Bm, lb, opB, C1(0.0), Cm, lc, st, ks,
@@ -645,8 +605,6 @@ struct Solver {
   // diagonal of H.  Returns false (nothing changed in H) when the Cholesky
   // factorisation breaks down.
   bool eig_two_phase(S* H, int64_t k, int* sweeps) {
-    allow_left_n = true;
-    struct Restore { bool& f; ~Restore() { f = false; } } restore{allow_left_n};
     convert_matrix<F32, S>(H32, k, H, k, k, k, st);
     jacobi_eigh<F32>(H32, k, k, V32, k, 4e-7, cw, ctx->num_sms, st, 40);
     int sw32 = 0;
