@@ -44,6 +44,13 @@ NUM_SMS = 152
 FP32_LANES_PER_SM = 128
 DF32_FP32_OPS_PER_MAC = 12   # TwoProd (2) + TwoSum (6) + 2 cross FMAs + 2 adds
 OZ_PAIRS = 21                # digit products p + q <= 5 of six 8-bit digits
+# DRAM bytes per flop of gemm_kernel<c64> from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum over every launch of the n = 4096 solve, profiles/); each launch is
+# a rank-64 (or rank-32) update whose C read-modify-write dominates its traffic, so traffic
+# scales with the flops of the launch; None until captured
+CGEMM_DRAM_BYTES_PER_FLOP = None
+CGEMM_TRAFFIC_SOURCE = "not captured"
+
 
 
 def workload_name(w):
@@ -278,12 +285,31 @@ def run_ours(args, rank, world, dev):
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
     h2d = A.numel() * A.element_size()
 
-    # the refinement GEMM (CUDA events on the library's stream, inside the
-    # library): tensor-core digit-split GEMM by default, double-float SIMT
-    # GEMM with --refine-gemm 1
+    # per-kernel CUDA events on the library's stream (inside the library)
     peaks, peak_kind = measured_peaks()
     clocks = clk.summary()
     sm_max = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    # dominant kernel of the step (launch list of the solve, profiles/): the
+    # complex-FP32 SIMT GEMM of the LU trailing and triangular-solve updates
+    cg_launches = max(1, st.cgemm_launches)
+    cg_avg_ms = st.cgemm_ms / cg_launches
+    cg_flop_per_launch = st.cgemm_flop / cg_launches
+    fp32_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    cg_achieved = cg_flop_per_launch / (cg_avg_ms / 1e3) / 1e12 if st.cgemm_ms > 0 else 0.0
+    cg_traffic = None
+    if CGEMM_DRAM_BYTES_PER_FLOP is not None:
+        cg_traffic = int(CGEMM_DRAM_BYTES_PER_FLOP * cg_flop_per_launch)
+    roofline = {"kernel": "gemm_kernel<c64> (complex-FP32 SIMT GEMM)", "bound": "alu",
+                "achieved": round(cg_achieved, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
+                "frac": round(cg_achieved / fp32_peak, 4), "traffic": cg_traffic,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x max SM clock (unit counts; no measured FP32 peak)",
+                "flop_def": "8 real flops per complex multiply-add, M N K per launch",
+                "traffic_source": CGEMM_TRAFFIC_SOURCE,
+                "launches_per_step": st.cgemm_launches, "avg_launch_ms": round(cg_avg_ms, 4),
+                "share_of_step": round(st.cgemm_ms / ms_step, 3)}
+
+    # the refinement GEMM: tensor-core digit-split GEMM by default,
+    # double-float SIMT GEMM with --refine-gemm 1
     rg_launches = max(1, st.refine_gemm_launches)
     rg_avg_ms = st.refine_gemm_ms / rg_launches
     rg_mac_per_launch = st.refine_gemm_mac / rg_launches
@@ -294,22 +320,22 @@ def run_ours(args, rank, world, dev):
         # kernel runs inside a seconds-long step)
         peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0))
         achieved = OZ_PAIRS * 2.0 * rg_mac_per_launch / rg_secs / 1e12 if rg_secs > 0 else 0.0
-        roofline = {"kernel": "oz_gemm_kernel", "bound": "tensor", "achieved": round(achieved, 2),
-                    "peak": round(peak, 1), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                    "traffic": None,
-                    "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (%s)" % peak_kind,
-                    "flop_def": "21 bf16 digit products x 2 x M N K per launch",
-                    "fp64_equiv_tflops": round(achieved / OZ_PAIRS, 3)}
+        roofline_refine = {"kernel": "oz_gemm_kernel", "bound": "tensor", "achieved": round(achieved, 2),
+                           "peak": round(peak, 1), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                           "traffic": None,
+                           "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (%s)" % peak_kind,
+                           "flop_def": "21 bf16 digit products x 2 x M N K per launch",
+                           "fp64_equiv_tflops": round(achieved / OZ_PAIRS, 3)}
     else:
         peak = NUM_SMS * FP32_LANES_PER_SM * sm_max * 1e6 / DF32_FP32_OPS_PER_MAC * 2 / 1e12
         achieved = 2.0 * rg_mac_per_launch / rg_secs / 1e12 if rg_secs > 0 else 0.0
-        roofline = {"kernel": "gemm_df32_kernel", "bound": "alu", "achieved": round(achieved, 3),
-                    "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                    "traffic": None,
-                    "peak_source": ("FP32 lanes x clock / 12 FP32 ops per double-float multiply-add "
-                                    "(152 SMs x 128 lanes x max SM clock)")}
-    roofline.update({"launches_per_step": st.refine_gemm_launches, "avg_launch_ms": round(rg_avg_ms, 3),
-                     "share_of_step": round(st.refine_gemm_ms / ms_step, 3)})
+        roofline_refine = {"kernel": "gemm_df32_kernel", "bound": "alu", "achieved": round(achieved, 3),
+                           "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                           "traffic": None,
+                           "peak_source": ("FP32 lanes x clock / 12 FP32 ops per double-float multiply-add "
+                                           "(152 SMs x 128 lanes x max SM clock)")}
+    roofline_refine.update({"launches_per_step": st.refine_gemm_launches, "avg_launch_ms": round(rg_avg_ms, 3),
+                            "share_of_step": round(st.refine_gemm_ms / ms_step, 3)})
 
     # filter-apply rate: algorithmic flops of the solves (8 n^2 m per entry,
     # complex MAC = 8 real flops) per filter application
@@ -328,7 +354,7 @@ def run_ours(args, rank, world, dev):
             "correct": bool(ok), "eigenpairs_per_step": found[-1], "iterations": results[-1]["iterations"],
             "filters": st.filters, "refine_steps": st.refine_steps,
             "factor_ms": round(st.factor_ms, 1), "filter_ms": round(st.filter_ms, 1),
-            "roofline": roofline,
+            "roofline": roofline, "roofline_refine_gemm": roofline_refine,
             "filter_apply": {"tflops": round(filter_tflops, 3) if filter_tflops else None,
                              "flop_per_filter": filt_flop,
                              "note": "solve flops 8 n^2 m0 per entry, 2 n_c entries; refinement excluded"},

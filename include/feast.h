@@ -108,7 +108,10 @@ typedef struct {
                                refinement GEMM launches */
   double refine_gemm_mac;   /* their real multiply-adds (M*N*K summed over launches) */
   int refine_gemm_launches; /* their number */
-  int reserved2;
+  int cgemm_launches;   /* mixed: launches of the complex-FP32 SIMT GEMM (LU trailing and
+                           triangular-solve block updates) */
+  double cgemm_ms;      /* their summed device time (CUDA events) */
+  double cgemm_flop;    /* their real flops (8 per complex multiply-add) */
 } feast_stats;
 
 void feast_opts_default(feast_opts* opts);

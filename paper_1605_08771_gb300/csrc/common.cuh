@@ -132,13 +132,16 @@ unsigned long long launch_count();
     FEAST_CUDA_TRY(cudaGetLastError());     \
   } while (0)
 
-// CUDA-event timing of the FP64-accurate GEMM launches of the mixed path's
-// refinement (its dominant kernel): enable for one solve, bracket each launch,
-// then read the summed device time, multiply-adds and launch count.
-void refine_timer_begin();
-void refine_timer_end(double* ms, double* macs, int* launches);
-void refine_timer_launch_begin(cudaStream_t s);
-void refine_timer_launch_end(cudaStream_t s, double macs);
+// CUDA-event timing of selected kernels over one solve: enable, bracket each
+// launch of the kernel class, then read the summed device time, work units
+// and launch count.  Classes: the FP64-accurate GEMM of the refinement
+// (work = real multiply-adds) and the complex-FP32 SIMT GEMM of the LU and
+// the triangular solves (work = real flops, 8 per complex multiply-add).
+enum TimerClass : int { TIMER_REFINE_GEMM = 0, TIMER_CGEMM = 1, TIMER_CLASSES = 2 };
+void kernel_timer_begin();
+void kernel_timer_end(int cls, double* ms, double* work, int* launches);
+void kernel_timer_launch_begin(int cls, cudaStream_t s);
+void kernel_timer_launch_end(int cls, cudaStream_t s, double work);
 
 struct CudaFailure {
   cudaError_t err;

@@ -1104,7 +1104,7 @@ int solve_t(feast_ctx* ctx, const S* A, int64_t n, int64_t lda, double lmin, dou
     random_normal<S>(X, n, m0, n, o.seed, ctx->stream);
   }
   sync(ctx);
-  refine_timer_begin();
+  kernel_timer_begin();
   const double tf0 = now_ms();
   sv.factor();
   sync(ctx);
@@ -1134,7 +1134,8 @@ int solve_t(feast_ctx* ctx, const S* A, int64_t n, int64_t lda, double lmin, dou
   st.m_expected = out.m_expected;
   st.factor_ms = tf1 - tf0;
   st.filter_ms = sv.filter_ms;
-  refine_timer_end(&st.refine_gemm_ms, &st.refine_gemm_mac, &st.refine_gemm_launches);
+  kernel_timer_end(TIMER_REFINE_GEMM, &st.refine_gemm_ms, &st.refine_gemm_mac, &st.refine_gemm_launches);
+  kernel_timer_end(TIMER_CGEMM, &st.cgemm_ms, &st.cgemm_flop, &st.cgemm_launches);
   sv.check_oz_status();
   st.total_ms = now_ms() - t0;
   st.max_residual = 0.0;

@@ -148,8 +148,12 @@ void gemm(const GemmArgs& g0, cudaStream_t stream) {
   constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4;
   if (g.ksplit > 1 && g.Cpart == nullptr) g.ksplit = 1;
   dim3 grid((unsigned)cdiv(g.M, BM), (unsigned)cdiv(g.N, BN), (unsigned)(g.batch * g.ksplit));
+  constexpr bool c64_gemm =
+      std::is_same<TA, c64>::value && std::is_same<TB, c64>::value && std::is_same<TC, c64>::value;
+  if (c64_gemm) kernel_timer_launch_begin(TIMER_CGEMM, stream);
   gemm_kernel<TA, TB, TC, BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, stream>>>(g);
   FEAST_LAUNCH_CHECK();
+  if (c64_gemm) kernel_timer_launch_end(TIMER_CGEMM, stream, 8.0 * (double)g.M * (double)g.N * (double)g.K * g.batch);
   if (g.ksplit > 1) {
     int64_t total = g.M * g.N;
     dim3 rg((unsigned)std::min<int64_t>(cdiv(total, 256), 4096), (unsigned)g.batch);
@@ -311,15 +315,15 @@ __global__ void split_df32_kernel(const double* src, int64_t rows, int64_t cols,
 }  // namespace
 
 namespace {
-struct RefineTimer {
+struct KernelTimer {
   bool on = false;
-  std::vector<cudaEvent_t> pool;
-  size_t used = 0;
-  double macs = 0.0;
-  int launches = 0;
+  std::vector<cudaEvent_t> pool[TIMER_CLASSES];
+  size_t used[TIMER_CLASSES] = {};
+  double work[TIMER_CLASSES] = {};
+  int launches[TIMER_CLASSES] = {};
 };
-RefineTimer& refine_timer() {
-  static RefineTimer t;
+KernelTimer& kernel_timer() {
+  static KernelTimer t;
   return t;
 }
 std::atomic<unsigned long long> g_launches{0};
@@ -328,56 +332,60 @@ std::atomic<unsigned long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 unsigned long long launch_count() { return g_launches.load(); }
 
-void refine_timer_begin() {
-  RefineTimer& t = refine_timer();
+void kernel_timer_begin() {
+  KernelTimer& t = kernel_timer();
   t.on = true;
-  t.used = 0;
-  t.macs = 0.0;
-  t.launches = 0;
+  for (int c = 0; c < TIMER_CLASSES; ++c) {
+    t.used[c] = 0;
+    t.work[c] = 0.0;
+    t.launches[c] = 0;
+  }
 }
-void refine_timer_end(double* ms, double* macs, int* launches) {
-  RefineTimer& t = refine_timer();
+void kernel_timer_end(int cls, double* ms, double* work, int* launches) {
+  KernelTimer& t = kernel_timer();
   double tot = 0.0;
-  for (size_t i = 0; i + 1 < t.used; i += 2) {
+  for (size_t i = 0; i + 1 < t.used[cls]; i += 2) {
     float e = 0.f;
-    FEAST_CUDA_TRY(cudaEventSynchronize(t.pool[i + 1]));
-    FEAST_CUDA_TRY(cudaEventElapsedTime(&e, t.pool[i], t.pool[i + 1]));
+    FEAST_CUDA_TRY(cudaEventSynchronize(t.pool[cls][i + 1]));
+    FEAST_CUDA_TRY(cudaEventElapsedTime(&e, t.pool[cls][i], t.pool[cls][i + 1]));
     tot += e;
   }
   if (ms) *ms = tot;
-  if (macs) *macs = t.macs;
-  if (launches) *launches = t.launches;
-  t.on = false;
-  t.used = 0;
+  if (work) *work = t.work[cls];
+  if (launches) *launches = t.launches[cls];
+  t.used[cls] = 0;
+  bool any = false;
+  for (int c = 0; c < TIMER_CLASSES; ++c) any = any || t.used[c] > 0;
+  if (!any) t.on = false;
 }
-void refine_timer_launch_begin(cudaStream_t s) {
-  RefineTimer& t = refine_timer();
+void kernel_timer_launch_begin(int cls, cudaStream_t s) {
+  KernelTimer& t = kernel_timer();
   if (!t.on) return;
-  while (t.pool.size() < t.used + 2) {
+  while (t.pool[cls].size() < t.used[cls] + 2) {
     cudaEvent_t e;
     FEAST_CUDA_TRY(cudaEventCreate(&e));
-    t.pool.push_back(e);
+    t.pool[cls].push_back(e);
   }
-  FEAST_CUDA_TRY(cudaEventRecord(t.pool[t.used], s));
+  FEAST_CUDA_TRY(cudaEventRecord(t.pool[cls][t.used[cls]], s));
 }
-void refine_timer_launch_end(cudaStream_t s, double macs) {
-  RefineTimer& t = refine_timer();
+void kernel_timer_launch_end(int cls, cudaStream_t s, double work) {
+  KernelTimer& t = kernel_timer();
   if (!t.on) return;
-  FEAST_CUDA_TRY(cudaEventRecord(t.pool[t.used + 1], s));
-  t.used += 2;
-  t.macs += macs;
-  t.launches += 1;
+  FEAST_CUDA_TRY(cudaEventRecord(t.pool[cls][t.used[cls] + 1], s));
+  t.used[cls] += 2;
+  t.work[cls] += work;
+  t.launches[cls] += 1;
 }
 
 void gemm_df32(int64_t M, int64_t N, int64_t K, double alpha, const float* Ahi, const float* Alo, int64_t lda,
                const float* Bhi, const float* Blo, int64_t ldb, double beta, double* C, int64_t ldc, int cs, int co,
                cudaStream_t s) {
   if (M <= 0 || N <= 0) return;
-  refine_timer_launch_begin(s);
+  kernel_timer_launch_begin(TIMER_REFINE_GEMM, s);
   dim3 grid((unsigned)cdiv(M, DF_BM), (unsigned)cdiv(N, DF_BN));
   gemm_df32_kernel<<<grid, DF_THREADS, 0, s>>>(M, N, K, alpha, Ahi, Alo, lda, Bhi, Blo, ldb, beta, C, ldc, cs, co);
   FEAST_LAUNCH_CHECK();
-  refine_timer_launch_end(s, (double)M * (double)N * (double)K);
+  kernel_timer_launch_end(TIMER_REFINE_GEMM, s, (double)M * (double)N * (double)K);
 }
 
 void combine_3m(double* C, const double* T2, int64_t n, int64_t k, cudaStream_t s) {

@@ -422,11 +422,11 @@ void oz_gemm(int64_t M, int64_t N, const OzOperand& A, const OzOperand& B, doubl
   FEAST_CUDA_TRY(aerr);
   const int64_t tiles = (A.vpad / OZ_BM) * (B.vpad / OZ_BN);
   const unsigned grid = (unsigned)std::min<int64_t>(tiles, num_sms);
-  refine_timer_launch_begin(s);
+  kernel_timer_launch_begin(TIMER_REFINE_GEMM, s);
   oz_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM, s>>>(mA, mB, (int)M, (int)N, (int)A.vpad, (int)B.vpad,
                                                    (int)(A.kpad / OZ_BK), A.exps, B.exps, C, ldc, cs, co, status);
   FEAST_LAUNCH_CHECK();
-  refine_timer_launch_end(s, (double)M * (double)N * (double)A.K);
+  kernel_timer_launch_end(TIMER_REFINE_GEMM, s, (double)M * (double)N * (double)A.K);
 }
 
 void oz_gemm_op(bool cplx, int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda, bool transA,
