@@ -166,6 +166,7 @@ jacobi_kernel(S* H, int64_t k, int64_t ld, S* V, int64_t ldv, double tol, CoopWo
   int sweeps = 0;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     for (int64_t r = 0; r < m1; ++r) {
+      int any_on = 0;
       for (int64_t i = gt; i < np; i += NT) {
         int64_t a, b;
         if (i == 0) { a = r % m1; b = m1; }
@@ -186,12 +187,20 @@ jacobi_kernel(S* H, int64_t k, int64_t ld, S* V, int64_t ldv, double tol, CoopWo
             c = R(1) / hypot(R(1), t);
             s = t * c;
             on = 1;
-            atomicAdd(&w.rotcount[sweep], 1u);
           }
         }
+        any_on |= on;
         rc[i] = c; rs[i] = s; re[i] = e; ron[i] = on; rpp[i] = (int)p; rqq[i] = (int)q;
       }
+      // a round that rotates no pair skips its update phase and second barrier
+      // (late sweeps rotate few pairs): one count per round, read after the barrier
+      const int64_t gr = (int64_t)sweep * m1 + r;
+      if (__syncthreads_or(any_on) && threadIdx.x == 0) {
+        atomicAdd(&w.roundcount[gr], 1u);
+        atomicAdd(&w.rotcount[sweep], 1u);
+      }
       if (!group_barrier(w.counter, (++nb) * (unsigned)P, w.status)) return;
+      if (__ldcg(&w.roundcount[gr]) == 0u) continue;
       const int64_t nblk = np * np;
       for (int64_t task = gt; task < nblk + k * np; task += NT) {
         if (task < nblk) {
@@ -433,7 +442,8 @@ __global__ void check_finite_kernel(const S* X, int64_t n, int64_t m, int64_t ld
 size_t coop_work_bytes(int64_t kmax, int num_sms) {
   const int64_t np = (kmax + 2) / 2;
   return 256 * 4 + sizeof(double) * 2 * (size_t)std::max(num_sms, 1024) + 256 +
-         sizeof(unsigned) * kMaxSweeps + 256 + (size_t)np * (2 * sizeof(double) + sizeof(c128) + 3 * sizeof(int)) + 256;
+         sizeof(unsigned) * kMaxSweeps + 256 + sizeof(unsigned) * kMaxSweeps * (size_t)(kmax + 2) + 256 +
+         (size_t)np * (2 * sizeof(double) + sizeof(c128) + 3 * sizeof(int)) + 256;
 }
 
 CoopWork coop_work_carve(void* base, int64_t kmax, int num_sms) {
@@ -445,8 +455,8 @@ CoopWork coop_work_carve(void* base, int64_t kmax, int num_sms) {
   p += 256;
   w.partial = (double*)p; p += ((sizeof(double) * 2 * (size_t)std::max(num_sms, 1024) + 255) & ~size_t(255));
   w.rotcount = (unsigned*)p; p += ((sizeof(unsigned) * kMaxSweeps + 255) & ~size_t(255));
+  w.roundcount = (unsigned*)p; p += ((sizeof(unsigned) * kMaxSweeps * (size_t)(kmax + 2) + 255) & ~size_t(255));
   w.rot = p;
-  (void)kmax;
   return w;
 }
 
@@ -482,6 +492,7 @@ void jacobi_eigh(S* H, int64_t k, int64_t ld, S* V, int64_t ldv, double tol, con
                  cudaStream_t s, int max_sweeps) {
   FEAST_CUDA_TRY(cudaMemsetAsync(w.counter, 0, 256 * 3, s));
   FEAST_CUDA_TRY(cudaMemsetAsync(w.rotcount, 0, sizeof(unsigned) * kMaxSweeps, s));
+  FEAST_CUDA_TRY(cudaMemsetAsync(w.roundcount, 0, sizeof(unsigned) * kMaxSweeps * (size_t)(k + 2), s));
   int occ = 0;
   FEAST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, jacobi_kernel<S>, 256, 0));
   const int64_t tasks = (k / 2 + 1) * (k / 2 + 1) + k * (k / 2 + 1);

@@ -14,7 +14,8 @@ struct CoopWork {
   int* status;         // [1] fatal status (DeviceStatus)
   int* info;           // [4] kernel-specific outputs (Cholesky column, sweeps, ...)
   double* partial;     // [>= 2*num_sms] partial sums
-  unsigned* rotcount;  // [kMaxSweeps]
+  unsigned* rotcount;  // [kMaxSweeps] CTAs that rotated in each sweep
+  unsigned* roundcount;  // [kMaxSweeps * (kmax + 2)] CTAs that rotated in each round
   void* rot;           // rotation parameters, >= k/2+1 entries of (c, s, e)
 };
 constexpr int kMaxSweeps = 64;
