@@ -54,6 +54,10 @@ def main():
             out = f.solve(A, a, b, m, 8, 1e-10, variant="rfeast", prec=args.prec, anorm=anorm,
                           refine_gemm=args.refine_gemm, tc_solve=args.tc_solve)
             print("status", out["status"], "pairs", out["evals"].size, "iterations", out["iterations"])
+            st = out["stats"]
+            print("cgemm launches %d flop %.6e ms %.3f; refine gemm launches %d mac %.6e ms %.3f"
+                  % (st.cgemm_launches, st.cgemm_flop, st.cgemm_ms, st.refine_gemm_launches,
+                     st.refine_gemm_mac, st.refine_gemm_ms))
     torch.cuda.synchronize()
 
 
