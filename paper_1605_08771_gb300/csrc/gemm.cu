@@ -261,12 +261,6 @@ void gemm(const GemmArgs& g0, cudaStream_t stream) {
       else if (g.opA == OP_N) cgemm_prefetch_kernel<OP_N, OP_C, 3><<<grid, CP_NT, 0, stream>>>(g);
       else cgemm_prefetch_kernel<OP_C, OP_C, 3><<<grid, CP_NT, 0, stream>>>(g);
     } else {
-        if (g.opA == OP_N && g.opB == OP_N) cgemm_prefetch_kernel<OP_N, OP_N, 2><<<grid, CP_NT, 0, stream>>>(g);
-        else if (g.opB == OP_N) cgemm_prefetch_kernel<OP_C, OP_N, 2><<<grid, CP_NT, 0, stream>>>(g);
-        else if (g.opA == OP_N) cgemm_prefetch_kernel<OP_N, OP_C, 2><<<grid, CP_NT, 0, stream>>>(g);
-        else cgemm_prefetch_kernel<OP_C, OP_C, 2><<<grid, CP_NT, 0, stream>>>(g);
-      }
-    } else {
       gemm_kernel<TA, TB, TC, BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, stream>>>(g);
     }
   } else {
