@@ -44,13 +44,13 @@ NUM_SMS = 152
 FP32_LANES_PER_SM = 128
 DF32_FP32_OPS_PER_MAC = 12   # TwoProd (2) + TwoSum (6) + 2 cross FMAs + 2 adds
 OZ_PAIRS = 21                # digit products p + q <= 5 of six 8-bit digits
-# DRAM bytes per flop of gemm_kernel<c64> from one ncu capture (dram__bytes_read.sum +
+# DRAM bytes per flop of cgemm_prefetch_kernel from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum over every launch of the n = 4096 solve, profiles/); each launch is
 # a rank-64 (or rank-32) update whose C read-modify-write dominates its traffic, so traffic
 # scales with the flops of the launch; None until captured
 CGEMM_DRAM_BYTES_PER_FLOP = 171.68e9 / 5.2540e12
-CGEMM_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum over the 3151 gemm_kernel<c64> launches "
-                        "of the n = 4096 solve (171.68 GB, cold-cache replay) / their 5.254e12 flops, "
+CGEMM_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum over the 3151 cgemm_prefetch_kernel "
+                        "launches of the n = 4096 solve (171.68 GB, cold-cache replay) / their 5.254e12 flops, "
                         "x flops per launch")
 
 
@@ -301,7 +301,7 @@ def run_ours(args, rank, world, dev):
     cg_traffic = None
     if CGEMM_DRAM_BYTES_PER_FLOP is not None:
         cg_traffic = int(CGEMM_DRAM_BYTES_PER_FLOP * cg_flop_per_launch)
-    roofline = {"kernel": "gemm_kernel<c64> (complex-FP32 SIMT GEMM)", "bound": "alu",
+    roofline = {"kernel": "cgemm_prefetch_kernel (complex-FP32 SIMT GEMM)", "bound": "alu",
                 "achieved": round(cg_achieved, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
                 "frac": round(cg_achieved / fp32_peak, 4), "traffic": cg_traffic,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x max SM clock (unit counts; no measured FP32 peak)",
