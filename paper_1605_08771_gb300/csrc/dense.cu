@@ -602,6 +602,215 @@ template <typename S> void check_finite(const S* X, int64_t n, int64_t m, int64_
   FEAST_LAUNCH_CHECK();
 }
 
+// ---------------------------------------------------------------------------
+// Block Jacobi (low-precision first phase of the two-phase eigensolver).
+// Rows are grouped in blocks of BJ_B; in round r the blocks are paired by the
+// same round-robin schedule as the scalar kernel.  One CTA per pair
+// diagonalises its (2 BJ_B)-square subproblem in shared memory with one
+// cyclic Jacobi sweep and writes the accumulated unitary U; a second launch
+// forms U_P^H H[P, Q] U_Q for every pair of pairs and V[:, P] U_P.  Each
+// output tile reads only its own input tile, so the rounds need no grid-wide
+// barrier; a sweep is nb - 1 rounds instead of k - 1.
+constexpr int BJ_B = 16, BJ_P = 2 * BJ_B;
+
+__device__ __forceinline__ void bj_pair(int ip, int r, int nbe, int& I, int& J) {
+  const int m1 = nbe - 1;
+  int a, b;
+  if (ip == 0) { a = r % m1; b = m1; }
+  else { a = (r + ip) % m1; b = ((r - ip) % m1 + m1) % m1; }
+  I = a < b ? a : b;
+  J = a < b ? b : a;
+}
+// global row of subproblem index t of pair (I, J), or -1 (dummy block)
+__device__ __forceinline__ int bj_row(int t, int I, int J, int nb) {
+  const int blk = t < BJ_B ? I : J;
+  return blk < nb ? blk * BJ_B + (t % BJ_B) : -1;
+}
+
+template <typename S>
+__global__ void __launch_bounds__(256) bj_solve_kernel(const S* __restrict__ HP, int64_t ld, int nb, int nbe, int r,
+                                                       float thr, S* __restrict__ U, int* rotated) {
+  using R = real_t<S>;
+  __shared__ S A[BJ_P][BJ_P + 1];
+  __shared__ S Us[BJ_P][BJ_P + 1];
+  __shared__ R pc[BJ_B], ps[BJ_B];
+  __shared__ S pe[BJ_B];
+  __shared__ int pon[BJ_B], pp[BJ_B], pq[BJ_B];
+  __shared__ int any;
+  const int ip = blockIdx.x, t = threadIdx.x;
+  int I, J;
+  bj_pair(ip, r, nbe, I, J);
+  for (int l = t; l < BJ_P * BJ_P; l += blockDim.x) {
+    const int i = l % BJ_P, j = l / BJ_P;
+    const int gi = bj_row(i, I, J, nb), gj = bj_row(j, I, J, nb);
+    A[i][j] = (gi >= 0 && gj >= 0) ? HP[gi + (int64_t)gj * ld] : num<S>::zero();
+    Us[i][j] = i == j ? one<S>() : num<S>::zero();
+  }
+  if (t == 0) any = 0;
+  __syncthreads();
+  constexpr int m1 = BJ_P - 1;
+  for (int rr = 0; rr < m1; ++rr) {
+    if (t < BJ_B) {
+      int a, b;
+      if (t == 0) { a = rr % m1; b = m1; }
+      else { a = (rr + t) % m1; b = ((rr - t) % m1 + m1) % m1; }
+      const int p = a < b ? a : b, q = a < b ? b : a;
+      R c = R(1), sn = R(0);
+      S e = one<S>();
+      int on = 0;
+      const S apq = A[p][q];
+      const R g = sqrt(abs2(apq));
+      if (g > thr) {
+        const R app = real_part(A[p][p]), aqq = real_part(A[q][q]);
+        e = conj(apq) * (R(1) / g);
+        const R tau = (aqq - app) / (R(2) * g);
+        const R tt = (tau >= R(0) ? R(1) : R(-1)) / (fabs(tau) + hypot(R(1), tau));
+        c = R(1) / hypot(R(1), tt);
+        sn = tt * c;
+        on = 1;
+        any = 1;
+      }
+      pc[t] = c; ps[t] = sn; pe[t] = e; pon[t] = on; pp[t] = p; pq[t] = q;
+    }
+    __syncthreads();
+    {
+      // 2 x 2 block (I', J') of the rows of pair I' and the columns of pair J'
+      const int bI = t % BJ_B, bJ = t / BJ_B;
+      const int onI = pon[bI], onJ = pon[bJ];
+      if (onI || onJ) {
+        const int pI = pp[bI], qI = pq[bI], pJ = pp[bJ], qJ = pq[bJ];
+        S b00 = A[pI][pJ], b01 = A[pI][qJ], b10 = A[qI][pJ], b11 = A[qI][qJ];
+        if (onJ) {
+          const R c = pc[bJ], sn = ps[bJ];
+          const S se = pe[bJ] * sn, ce = pe[bJ] * c;
+          S n00 = b00 * c - b01 * se, n01 = b00 * sn + b01 * ce;
+          S n10 = b10 * c - b11 * se, n11 = b10 * sn + b11 * ce;
+          b00 = n00; b01 = n01; b10 = n10; b11 = n11;
+        }
+        if (onI) {
+          const R c = pc[bI], sn = ps[bI];
+          const S ec = conj(pe[bI]);
+          const S sec = ec * sn, cec = ec * c;
+          S n00 = b00 * c - b10 * sec, n10 = b00 * sn + b10 * cec;
+          S n01 = b01 * c - b11 * sec, n11 = b01 * sn + b11 * cec;
+          b00 = n00; b01 = n01; b10 = n10; b11 = n11;
+        }
+        if (bI == bJ && onI) {
+          b01 = num<S>::zero();
+          b10 = num<S>::zero();
+          b00 = cvt<S>(real_part(b00));
+          b11 = cvt<S>(real_part(b11));
+        }
+        A[pI][pJ] = b00; A[pI][qJ] = b01; A[qI][pJ] = b10; A[qI][qJ] = b11;
+      }
+      // U <- U G_J' for the columns of each rotated pair
+      for (int l = t; l < BJ_P * BJ_B; l += blockDim.x) {
+        const int row = l % BJ_P, j = l / BJ_P;
+        if (!pon[j]) continue;
+        const int p = pp[j], q = pq[j];
+        const R c = pc[j], sn = ps[j];
+        const S e = pe[j];
+        const S a = Us[row][p], b = Us[row][q];
+        Us[row][p] = a * c - b * (e * sn);
+        Us[row][q] = a * sn + b * (e * c);
+      }
+    }
+    __syncthreads();
+  }
+  for (int l = t; l < BJ_P * BJ_P; l += blockDim.x) {
+    const int i = l % BJ_P, j = l / BJ_P;
+    U[(int64_t)ip * BJ_P * BJ_P + i + j * BJ_P] = Us[i][j];
+  }
+  if (t == 0 && any) atomicOr(rotated, 1);
+}
+
+// H[P, Q] <- U_P^H H[P, Q] U_Q for pair tiles (P, Q) (grid npairs x npairs)
+template <typename S>
+__global__ void __launch_bounds__(256) bj_apply_h_kernel(S* HP, int64_t ld, int nb, int nbe, int r,
+                                                         const S* __restrict__ U) {
+  __shared__ S T[BJ_P][BJ_P + 1];
+  __shared__ S X[BJ_P][BJ_P + 1];
+  __shared__ S UPs[BJ_P][BJ_P + 1];
+  __shared__ S UQs[BJ_P][BJ_P + 1];
+  const int P = blockIdx.x, Q = blockIdx.y, t = threadIdx.x;
+  int IP, JP, IQ, JQ;
+  bj_pair(P, r, nbe, IP, JP);
+  bj_pair(Q, r, nbe, IQ, JQ);
+  for (int l = t; l < BJ_P * BJ_P; l += blockDim.x) {
+    const int i = l % BJ_P, j = l / BJ_P;
+    const int gi = bj_row(i, IP, JP, nb), gj = bj_row(j, IQ, JQ, nb);
+    T[i][j] = (gi >= 0 && gj >= 0) ? HP[gi + (int64_t)gj * ld] : num<S>::zero();
+    UPs[i][j] = U[(int64_t)P * BJ_P * BJ_P + l];
+    UQs[i][j] = U[(int64_t)Q * BJ_P * BJ_P + l];
+  }
+  __syncthreads();
+  for (int l = t; l < BJ_P * BJ_P; l += blockDim.x) {
+    const int i = l % BJ_P, j = l / BJ_P;
+    S acc = num<S>::zero();
+#pragma unroll 8
+    for (int m = 0; m < BJ_P; ++m) acc = acc + T[i][m] * UQs[m][j];
+    X[i][j] = acc;
+  }
+  __syncthreads();
+  for (int l = t; l < BJ_P * BJ_P; l += blockDim.x) {
+    const int i = l % BJ_P, j = l / BJ_P;
+    const int gi = bj_row(i, IP, JP, nb), gj = bj_row(j, IQ, JQ, nb);
+    if (gi < 0 || gj < 0) continue;
+    S acc = num<S>::zero();
+#pragma unroll 8
+    for (int m = 0; m < BJ_P; ++m) acc = acc + conj(UPs[m][i]) * X[m][j];
+    HP[gi + (int64_t)gj * ld] = acc;
+  }
+}
+
+// V[rows, P] <- V[rows, P] U_P for 32-row chunks (grid npairs x kp / 32)
+template <typename S>
+__global__ void __launch_bounds__(256) bj_apply_v_kernel(S* VP, int64_t ld, int kp, int nb, int nbe, int r,
+                                                         const S* __restrict__ U) {
+  __shared__ S W[BJ_P][BJ_P + 1];
+  __shared__ S UPs[BJ_P][BJ_P + 1];
+  const int P = blockIdx.x, t = threadIdx.x;
+  const int64_t r0 = (int64_t)blockIdx.y * BJ_P;
+  int IP, JP;
+  bj_pair(P, r, nbe, IP, JP);
+  for (int l = t; l < BJ_P * BJ_P; l += blockDim.x) {
+    const int i = l % BJ_P, j = l / BJ_P;
+    const int gj = bj_row(j, IP, JP, nb);
+    W[i][j] = (gj >= 0 && r0 + i < kp) ? VP[(r0 + i) + (int64_t)gj * ld] : num<S>::zero();
+    UPs[i][j] = U[(int64_t)P * BJ_P * BJ_P + l];
+  }
+  __syncthreads();
+  for (int l = t; l < BJ_P * BJ_P; l += blockDim.x) {
+    const int i = l % BJ_P, j = l / BJ_P;
+    const int gj = bj_row(j, IP, JP, nb);
+    if (gj < 0 || r0 + i >= kp) continue;
+    S acc = num<S>::zero();
+#pragma unroll 8
+    for (int m = 0; m < BJ_P; ++m) acc = acc + W[i][m] * UPs[m][j];
+    VP[(r0 + i) + (int64_t)gj * ld] = acc;
+  }
+}
+
+// HP (kp x kp) <- H (k x k, ld k) converted and zero-padded; VP <- I
+template <typename F, typename S>
+__global__ void bj_load_kernel(F* HP, F* VP, int64_t kp, const S* H, int64_t k) {
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < kp * kp;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx % kp, j = idx / kp;
+    HP[idx] = (i < k && j < k) ? cvt<F>(H[i + j * k]) : num<F>::zero();
+    VP[idx] = i == j ? one<F>() : num<F>::zero();
+  }
+}
+
+template <typename F>
+__global__ void bj_store_kernel(F* V, int64_t k, const F* VP, int64_t kp) {
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < k * k;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx % k, j = idx / k;
+    V[idx] = VP[i + j * kp];
+  }
+}
+
 template <typename To, typename From>
 __global__ void convert_matrix_kernel(To* dst, int64_t ldd, const From* src, int64_t lds, int64_t n, int64_t m) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * m; t += (int64_t)gridDim.x * blockDim.x) {
@@ -623,6 +832,45 @@ template void convert_matrix<c128, c64>(c128*, int64_t, const c64*, int64_t, int
 template void jacobi_eigh<float>(float*, int64_t, int64_t, float*, int64_t, double, const CoopWork&, int, cudaStream_t,
                                  int);
 template void jacobi_eigh<c64>(c64*, int64_t, int64_t, c64*, int64_t, double, const CoopWork&, int, cudaStream_t, int);
+
+int64_t block_jacobi_pad(int64_t k) { return cdiv(k, BJ_B) * BJ_B; }
+size_t block_jacobi_u_bytes(int64_t kmax) {
+  const int64_t nb = cdiv(kmax, BJ_B), nbe = nb + (nb & 1);
+  return (size_t)(nbe / 2) * BJ_P * BJ_P * sizeof(c128);
+}
+
+template <typename F, typename S>
+int block_jacobi(const S* H, int64_t k, F* V, double thr, F* HP, F* VP, F* Ubuf, int* d_rot, int max_sweeps,
+                 cudaStream_t s) {
+  const int64_t kp = block_jacobi_pad(k);
+  const int nb = (int)(kp / BJ_B), nbe = nb + (nb & 1), npairs = nbe / 2, rounds = nbe - 1;
+  bj_load_kernel<F, S><<<grid1d(kp * kp), 256, 0, s>>>(HP, VP, kp, H, k);
+  FEAST_LAUNCH_CHECK();
+  int sweeps = 0;
+  for (int sw = 0; sw < max_sweeps; ++sw) {
+    FEAST_CUDA_TRY(cudaMemsetAsync(d_rot, 0, sizeof(int), s));
+    for (int r = 0; r < rounds; ++r) {
+      bj_solve_kernel<F><<<npairs, 256, 0, s>>>(HP, kp, nb, nbe, r, (float)thr, Ubuf, d_rot);
+      FEAST_LAUNCH_CHECK();
+      bj_apply_h_kernel<F><<<dim3(npairs, npairs), 256, 0, s>>>(HP, kp, nb, nbe, r, Ubuf);
+      FEAST_LAUNCH_CHECK();
+      bj_apply_v_kernel<F><<<dim3(npairs, (unsigned)(kp / BJ_P + (kp % BJ_P != 0))), 256, 0, s>>>(VP, kp, (int)kp, nb,
+                                                                                                 nbe, r, Ubuf);
+      FEAST_LAUNCH_CHECK();
+    }
+    ++sweeps;
+    int rot = 0;
+    FEAST_CUDA_TRY(cudaMemcpyAsync(&rot, d_rot, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FEAST_CUDA_TRY(cudaStreamSynchronize(s));
+    if (!rot) break;
+  }
+  bj_store_kernel<F><<<grid1d(k * k), 256, 0, s>>>(V, k, VP, kp);
+  FEAST_LAUNCH_CHECK();
+  return sweeps;
+}
+template int block_jacobi<float, double>(const double*, int64_t, float*, double, float*, float*, float*, int*, int,
+                                         cudaStream_t);
+template int block_jacobi<c64, c128>(const c128*, int64_t, c64*, double, c64*, c64*, c64*, int*, int, cudaStream_t);
 
 #define INST_S(S)                                                                                          \
   template void hermitize<S>(S*, int64_t, int64_t, cudaStream_t);                                          \

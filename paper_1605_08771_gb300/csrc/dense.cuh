@@ -43,6 +43,21 @@ template <typename S>
 void jacobi_eigh(S* H, int64_t k, int64_t ld, S* V, int64_t ldv, double tol, const CoopWork& w,
                  int num_sms, cudaStream_t s, int max_sweeps = kMaxSweeps);
 
+// Low-precision block Jacobi (F = float / c64) on the Hermitian k x k matrix
+// H (FP64, ld k, not modified): block-pair rounds, each pair's 32 x 32
+// subproblem diagonalised in shared memory, the unitaries applied to the whole
+// working copy.  Rotations skip |h_pq| <= thr (absolute).  V (k x k, ld k)
+// receives the accumulated eigenvectors; returns the sweeps taken (at most
+// max_sweeps; the last one rotated nothing unless the limit was reached).
+// Scratch: HP, VP of block_jacobi_pad(k)^2 elements, Ubuf of
+// block_jacobi_u_bytes(k) bytes, d_rot one int.  Synchronises the stream once
+// per sweep.
+int64_t block_jacobi_pad(int64_t k);
+size_t block_jacobi_u_bytes(int64_t kmax);
+template <typename F, typename S>
+int block_jacobi(const S* H, int64_t k, F* V, double thr, F* HP, F* VP, F* Ubuf, int* d_rot, int max_sweeps,
+                 cudaStream_t s);
+
 // dst (n x m, ld ldd) = src converted elementwise (FP64 <-> FP32, complex too)
 template <typename To, typename From>
 void convert_matrix(To* dst, int64_t ldd, const From* src, int64_t lds, int64_t n, int64_t m, cudaStream_t s);

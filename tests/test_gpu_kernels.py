@@ -116,6 +116,32 @@ def test_orthonormalize_rank_deficient_falls_back(ctx):
     assert np.linalg.norm(Q.conj().T @ Q - np.eye(10)) <= 1e-13
 
 
+@pytest.mark.parametrize("k", [64, 130, 257])
+@pytest.mark.parametrize("cplx", [False, True])
+def test_rayleigh_ritz_two_phase_eigensolver(ctx, k, cplx):
+    # k >= 64 takes the two-phase reduced eigensolver (FP32 block Jacobi,
+    # FP64 orthonormalisation and Jacobi polish); the spectrum has exact
+    # triples and pairs 1e-9 apart, so the FP32 phase cannot separate them
+    n = 320
+    rng = np.random.default_rng(k + 7 * cplx)
+    lam = np.sort(rng.uniform(-5.0, 5.0, n))
+    lam[10:13] = lam[10]
+    lam[40:42] = lam[40] + np.array([0.0, 1e-9])
+    lam = np.sort(lam)
+    P = make_problem("rr2", lam, -1.0, 1.0, 12, 8, seed=k, complex_=cplx)
+    Q0, _ = np.linalg.qr(random_subspace(P.n, k, seed=3, complex_=cplx))
+    Q0 = np.asfortranarray(Q0)
+    ev, X, res = fg.feast_rayleigh_ritz(ctx, cuda(P.A), cuda(Q0), P.anorm)
+    X = host(X)
+    rp = O.rayleigh_ritz(P.A, Q0, P.anorm)
+    np.testing.assert_allclose(ev, rp.lam, atol=1e-13 * P.anorm)
+    np.testing.assert_allclose(res, rp.res, atol=1e-12)
+    # Ritz vectors: orthonormal, and each one's residual as small as the oracle's
+    np.testing.assert_allclose(X.conj().T @ X, np.eye(k), atol=1e-12)
+    R = P.A @ X - X * ev[None, :]
+    assert np.linalg.norm(R, axis=0).max() <= np.linalg.norm(P.A @ rp.X - rp.X * rp.lam[None, :], axis=0).max() + 1e-11 * P.anorm
+
+
 @pytest.mark.parametrize("cplx", [False, True])
 def test_rayleigh_ritz_matches_oracle(ctx, cplx):
     lam, a, b = spectrum_uniform(120, 9, seed=4, bulk=8.0)
