@@ -365,6 +365,16 @@ struct Solver {
           int opB, c128 beta, S* Cm, int64_t lc) {
     gemm_simple<S, S, S>(Mr, Nc, K, alpha, Am, la, opA, Bm, lb, opB, beta, Cm, lc, st);
   }
+  // C = op(A) op(B) for a k x k x k product of the eigensolver: split-K so
+  // that the FP64 work spreads over every SM (k = 900 gives only 15 x 15
+  // output tiles)
+  void mm_square(int64_t k, const S* Am, int opA, const S* Bm, S* Cm) {
+    const int64_t tiles = cdiv(k, 64) * cdiv(k, 64);
+    int ks = (int)std::min<int64_t>({32, std::max<int64_t>(1, k / 64), cdiv(4 * ctx->num_sms, tiles)});
+    while (ks > 1 && (int64_t)ks * k * k > part_elems) --ks;
+    gemm_simple<S, S, S>(k, k, k, C1(1.0), Am, k, opA, Bm, k, OP_N, C1(0.0), Cm, k, st, ks,
+                         ks > 1 ? (void*)part : nullptr);
+  }
   // C (Mr x Nc) = op(A) op(B) with a long reduction K: split-K
   void mm_reduce(int64_t Mr, int64_t Nc, int64_t K, const S* Am, int64_t la, int opA, const S* Bm, int64_t lb,
                  int opB, S* Cm, int64_t lc) {
@@ -621,7 +631,7 @@ struct Solver {
     for (double v : cn) fro2 += v;
     const int sw32 = block_jacobi<F32, S>(H, k, V32, 4e-7 * std::sqrt(fro2), HPb, VPb, Ubj, d_bjrot, 40, st);
     convert_matrix<S, F32>(Ve, k, V32, k, k, k, st);
-    mm(k, k, k, C1(1.0), Ve, k, OP_C, Ve, k, OP_N, C1(0.0), Te, k);
+    mm_square(k, Ve, OP_C, Ve, Te);
     hermitize<S>(Te, k, k, st);
     cholesky_upper<S>(Te, k, k, cw, ctx->num_sms, st);
     int info = 0;
@@ -629,14 +639,14 @@ struct Solver {
     jacobi_status(nullptr);
     if (info != 0) return false;
     tri_inverse_upper<S>(Te, k, k, T2e, k, st);
-    mm(k, k, k, C1(1.0), Ve, k, OP_N, T2e, k, OP_N, C1(0.0), Te, k);   // Te: orthonormal V
-    mm(k, k, k, C1(1.0), H, k, OP_N, Te, k, OP_N, C1(0.0), T2e, k);    // H V
-    mm(k, k, k, C1(1.0), Te, k, OP_C, T2e, k, OP_N, C1(0.0), H, k);    // V^H H V
+    mm_square(k, Ve, OP_N, T2e, Te);   // Te: orthonormal V
+    mm_square(k, H, OP_N, Te, T2e);    // H V
+    mm_square(k, Te, OP_C, T2e, H);    // V^H H V
     hermitize<S>(H, k, k, st);
     jacobi_eigh<S>(H, k, k, T2e, k, 1e-15, cw, ctx->num_sms, st);
     int sw64 = 0;
     jacobi_status(&sw64);
-    mm(k, k, k, C1(1.0), Te, k, OP_N, T2e, k, OP_N, C1(0.0), Vk, k);
+    mm_square(k, Te, OP_N, T2e, Vk);
     *sweeps = sw32 + sw64;
     if (std::getenv("FEAST_LOG"))
       fprintf(stderr, "[feast] two-phase eig k=%lld: %d FP32 + %d FP64 sweeps\n", (long long)k, sw32, sw64);
