@@ -199,6 +199,21 @@ def build_problem(w, device):
     return A_store, lam
 
 
+def aggregate_ranks(ms_total, pairs, world, device="cpu"):
+    """Whole-job figures over the ranks of one node: the pairs all ranks
+    found, over the slowest rank's time (each rank runs its own replica of
+    the problem; no data-path collective).  Returns (t_max_ms, pairs_sum)."""
+    if world <= 1:
+        return float(ms_total), float(pairs)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms_total)], dtype=torch.float64, device=device)
+    p = torch.tensor([float(pairs)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(p.item())
+
+
 def run_ours(args, rank, world, dev):
     import torch
     import paper_1605_08771_gb300 as fg
@@ -253,18 +268,8 @@ def run_ours(args, rank, world, dev):
     found = [r["evals"].size for r in results]
     ok = all(r["status"] == 0 and r["evals"].size == inside.size and np.max(r["res"]) <= w["tol"]
              and np.max(np.abs(r["evals"] - inside)) <= 1e-10 * anorm for r in results)
-    value_rank = sum(found) / (ms_total / 1e3)
-    t_max = ms_total
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([ms_total, float(sum(found))], dtype=torch.float64, device=f"cuda:{dev}")
-        tmax = tt.clone()
-        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt[1:], op=dist.ReduceOp.SUM)
-        t_max = float(tmax[0])
-        value = float(tt[1]) / (t_max / 1e3)
-    else:
-        value = value_rank
+    t_max, pairs_all = aggregate_ranks(ms_total, sum(found), world, device=f"cuda:{dev}")
+    value = pairs_all / (t_max / 1e3)
     st = results[-1]["stats"]
 
     # e2e: A in pinned host memory, copied in; results copied out; all timed
