@@ -126,16 +126,29 @@ gemm_kernel(GemmArgs g) {
 // global memory into registers while the current slice is multiplied from
 // shared memory: the plain kernel stalls on those loads (long-scoreboard
 // stalls dominate its profile).  op(A), op(B) in {N, C}; no split-K.
-// Measured on the n = 8192 solve: 1.27 s against 1.58 s for the plain
-// kernel; bounded at 2 CTAs per SM (more registers, no spills) it took 1.46 s.
+// The C tile read by the epilogue is copied to shared memory with cp.async
+// at the start.  Measured on the n = 8192 solve: 1.15 s of complex GEMM
+// (1.27 s without the C copy, 1.58 s for the plain kernel; bounded at 2 CTAs
+// per SM, with more registers and no spills, 1.46 s).
 constexpr int CP_BM = 64, CP_BN = 64, CP_BK = 16, CP_T = 4;
 constexpr int CP_SM = CP_BM / CP_T, CP_SN = CP_BN / CP_T, CP_NT = CP_SM * CP_SN;
 constexpr int CP_AL = CP_BM * CP_BK / CP_NT, CP_BL = CP_BN * CP_BK / CP_NT;  // 4 and 4
+
+// C tile of the epilogue (beta != 0): copied to shared memory with cp.async
+// at the start, so its global-memory latency overlaps the multiplication
+constexpr int CP_DSMEM = CP_BM * CP_BN * (int)sizeof(c64);
+
+__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(sdst)),
+               "l"(gsrc)
+               : "memory");
+}
 
 template <int OPA, int OPB, int MINB>
 __global__ void __launch_bounds__(CP_NT, MINB) cgemm_prefetch_kernel(GemmArgs g) {
   __shared__ c64 As[CP_BK][CP_BM + 1];
   __shared__ c64 Bs[CP_BK][CP_BN + 1];
+  extern __shared__ c64 Cs[];  // CP_BM x CP_BN, each thread's own outputs
   constexpr bool an = OPA == OP_N, bn = OPB == OP_N;
   const int b = blockIdx.z;
   const c64* A = (const c64*)g.A + (int64_t)b * g.strideA;
@@ -144,6 +157,20 @@ __global__ void __launch_bounds__(CP_NT, MINB) cgemm_prefetch_kernel(GemmArgs g)
   const int t = threadIdx.x;
   const int tm = t % CP_SM, tn = t / CP_SM;
   c64 ra[CP_AL], rb[CP_BL];
+  c64* C = (c64*)g.C + (int64_t)b * g.strideC;
+  const bool ub = (g.beta.re != 0.0 || g.beta.im != 0.0);
+  if (ub) {
+#pragma unroll
+    for (int j = 0; j < CP_T; ++j) {
+      const int64_t gn = n0 + tn + j * CP_SN;
+#pragma unroll
+      for (int i = 0; i < CP_T; ++i) {
+        const int64_t gm = m0 + tm + i * CP_SM;
+        if (gm < g.M && gn < g.N) cp_async8(&Cs[(tm + i * CP_SM) + (tn + j * CP_SN) * CP_BM], C + gm + gn * g.ldc);
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
   auto load = [&](int64_t k0) {
 #pragma unroll
     for (int r = 0; r < CP_AL; ++r) {
@@ -208,8 +235,8 @@ __global__ void __launch_bounds__(CP_NT, MINB) cgemm_prefetch_kernel(GemmArgs g)
         }
     }
   }
-  c64* C = (c64*)g.C + (int64_t)b * g.strideC;
-  const bool ub = (g.beta.re != 0.0 || g.beta.im != 0.0);
+  if (ub) asm volatile("cp.async.wait_all;" ::: "memory");
+  const c64 al{(float)g.alpha.re, (float)g.alpha.im}, be{(float)g.beta.re, (float)g.beta.im};
 #pragma unroll
   for (int j = 0; j < CP_T; ++j) {
     const int64_t gn = n0 + tn + j * CP_SN;
@@ -217,8 +244,9 @@ __global__ void __launch_bounds__(CP_NT, MINB) cgemm_prefetch_kernel(GemmArgs g)
     for (int i = 0; i < CP_T; ++i) {
       const int64_t gm = m0 + tm + i * CP_SM;
       if (gm < g.M && gn < g.N) {
-        c64* c = C + gm + gn * g.ldc;
-        *c = axpby<c64>(g.alpha, c64{cr[i][j], ci[i][j]}, g.beta, c, ub);
+        c64 r = al * c64{cr[i][j], ci[i][j]};
+        if (ub) r = r + be * Cs[(tm + i * CP_SM) + (tn + j * CP_SN) * CP_BM];
+        C[gm + gn * g.ldc] = r;
       }
     }
   }
@@ -256,10 +284,18 @@ void gemm(const GemmArgs& g0, cudaStream_t stream) {
   if (c64_gemm) kernel_timer_launch_begin(TIMER_CGEMM, stream);
   if constexpr (c64_gemm) {
     if (g.ksplit == 1 && g.opA != OP_T && g.opB != OP_T) {
-      if (g.opA == OP_N && g.opB == OP_N) cgemm_prefetch_kernel<OP_N, OP_N, 3><<<grid, CP_NT, 0, stream>>>(g);
-      else if (g.opB == OP_N) cgemm_prefetch_kernel<OP_C, OP_N, 3><<<grid, CP_NT, 0, stream>>>(g);
-      else if (g.opA == OP_N) cgemm_prefetch_kernel<OP_N, OP_C, 3><<<grid, CP_NT, 0, stream>>>(g);
-      else cgemm_prefetch_kernel<OP_C, OP_C, 3><<<grid, CP_NT, 0, stream>>>(g);
+      static bool attr = [] {
+        cudaFuncSetAttribute(cgemm_prefetch_kernel<OP_N, OP_N, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, CP_DSMEM);
+        cudaFuncSetAttribute(cgemm_prefetch_kernel<OP_C, OP_N, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, CP_DSMEM);
+        cudaFuncSetAttribute(cgemm_prefetch_kernel<OP_N, OP_C, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, CP_DSMEM);
+        cudaFuncSetAttribute(cgemm_prefetch_kernel<OP_C, OP_C, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, CP_DSMEM);
+        return true;
+      }();
+      (void)attr;
+      if (g.opA == OP_N && g.opB == OP_N) cgemm_prefetch_kernel<OP_N, OP_N, 3><<<grid, CP_NT, CP_DSMEM, stream>>>(g);
+      else if (g.opB == OP_N) cgemm_prefetch_kernel<OP_C, OP_N, 3><<<grid, CP_NT, CP_DSMEM, stream>>>(g);
+      else if (g.opA == OP_N) cgemm_prefetch_kernel<OP_N, OP_C, 3><<<grid, CP_NT, CP_DSMEM, stream>>>(g);
+      else cgemm_prefetch_kernel<OP_C, OP_C, 3><<<grid, CP_NT, CP_DSMEM, stream>>>(g);
     } else {
       gemm_kernel<TA, TB, TC, BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, stream>>>(g);
     }
