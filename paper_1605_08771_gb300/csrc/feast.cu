@@ -226,12 +226,12 @@ struct Solver {
   // mixed, opts.tc_solve = 1: operand planes of the tensor-core block
   // updates of the complex-FP32 triangular solves
   void* solve_planes = nullptr;
-  // The Rayleigh-Ritz, orthonormalisation and eigensolver products stay FP64
-  // on this path.  Routed through the digit-split GEMM (error bounded by
-  // max-based norms) the graded filtered bases held the n = 8192 RFEAST
-  // residuals above 1e-10 ||A||; through the double-float GEMM (termwise
-  // 2^-44) the edge-cluster pairs, whose filter response is within rounding
-  // of 1/2, took 4 iterations instead of 2.
+  // The Rayleigh-Ritz, orthonormalisation and eigensolver products are not
+  // routed through the digit-split GEMM: its error is bounded by row/column
+  // maxima, and on the graded filtered bases it held the n = 8192 RFEAST
+  // residuals above 1e-10 ||A||.  Their op-N products take the double-float
+  // GEMM (mm_df below); the Hermitian reductions over n (Gram matrices,
+  // Q^H W) stay FP64.
   // Rayleigh-Ritz scratch
   S *Qb = nullptr, *Wb = nullptr, *Xr = nullptr, *AXr = nullptr, *T1 = nullptr, *T2 = nullptr;
   S *Ar0 = nullptr, *Ar = nullptr, *Vk = nullptr, *Gs = nullptr, *Ri = nullptr, *Cs = nullptr, *Cs2 = nullptr;
@@ -344,6 +344,10 @@ struct Solver {
     const int64_t kk = kmax * kmax;
     Ar0 = dalloc<S>(ctx, kk); Ar = dalloc<S>(ctx, kk); Vk = dalloc<S>(ctx, kk); Gs = dalloc<S>(ctx, kk);
     Ri = dalloc<S>(ctx, kk); Cs = dalloc<S>(ctx, kk); Cs2 = dalloc<S>(ctx, kk);
+    if (o.prec != FEAST_PREC_F64 && (double)n * kmax * kmax >= kDfMinWork) {
+      Ldf = dalloc<float>(ctx, 4 * n * kmax);
+      Rdf = dalloc<float>(ctx, 4 * kk);
+    }
     if (kmax >= kEigMixedMin) {
       H32 = dalloc<F32>(ctx, kk); V32 = dalloc<F32>(ctx, kk);
       const int64_t kp = block_jacobi_pad(kmax);
@@ -361,8 +365,48 @@ struct Solver {
   }
 
   // ---- small GEMM helpers ----
+  // Mixed path: products C = alpha A B + beta C with op N on both sides (the
+  // tall n x k products Q V, W V, X R^-1, Q C and the eigensolver's k x k
+  // products) in double-float arithmetic on the FP32 pipes, error ~2^-44
+  // termwise, several times the FP64 rate of this GPU.  Complex products take
+  // the four real products (4M): the three-product form (3M) forms Im as
+  // T3 - T1 - T2, whose cancellation made the n = 8192 RFEAST solve take 4
+  // iterations instead of 2; 4M keeps 2.
+  float* Ldf = nullptr;  // 4 planes (Re hi/lo, Im hi/lo) of n x kmax
+  float* Rdf = nullptr;  // 4 planes of kmax x kmax
+  static constexpr double kDfMinWork = 1e6;
+  bool mm_df_ok(int64_t Mr, int64_t Nc, int64_t K, c128 alpha, c128 beta, int opA, int opB) const {
+    if (!Ldf || opA != OP_N || opB != OP_N || alpha.im != 0.0 || beta.im != 0.0) return false;
+    if ((double)Mr * (double)Nc * (double)K < kDfMinWork) return false;
+    return Mr * K <= n * kmax && K * Nc <= kmax * kmax;
+  }
+  // complex C = alpha A B + beta C by four real double-float products (4M)
+  void mm_df(int64_t Mr, int64_t Nc, int64_t K, double alpha, const S* Am, int64_t la, const S* Bm, int64_t lb,
+             double beta, S* Cm, int64_t lc) {
+    const int64_t ak = Mr * K, bk = K * Nc;
+    double* C = (double*)Cm;
+    if constexpr (std::is_same<S, c128>::value) {
+      split_df32((const double*)Am, Mr, K, la, 2, 0, Ldf, Ldf + ak, st);
+      split_df32((const double*)Am, Mr, K, la, 2, 1, Ldf + 2 * ak, Ldf + 3 * ak, st);
+      split_df32((const double*)Bm, K, Nc, lb, 2, 0, Rdf, Rdf + bk, st);
+      split_df32((const double*)Bm, K, Nc, lb, 2, 1, Rdf + 2 * bk, Rdf + 3 * bk, st);
+      // Re C = alpha (Ar Br - Ai Bi) + beta Re C ; Im C = alpha (Ar Bi + Ai Br) + beta Im C
+      gemm_df32(Mr, Nc, K, alpha, Ldf, Ldf + ak, Mr, Rdf, Rdf + bk, K, beta, C, lc, 2, 0, st, -1);
+      gemm_df32(Mr, Nc, K, -alpha, Ldf + 2 * ak, Ldf + 3 * ak, Mr, Rdf + 2 * bk, Rdf + 3 * bk, K, 1.0, C, lc, 2, 0, st, -1);
+      gemm_df32(Mr, Nc, K, alpha, Ldf, Ldf + ak, Mr, Rdf + 2 * bk, Rdf + 3 * bk, K, beta, C, lc, 2, 1, st, -1);
+      gemm_df32(Mr, Nc, K, alpha, Ldf + 2 * ak, Ldf + 3 * ak, Mr, Rdf, Rdf + bk, K, 1.0, C, lc, 2, 1, st, -1);
+    } else {
+      split_df32((const double*)Am, Mr, K, la, 1, 0, Ldf, Ldf + ak, st);
+      split_df32((const double*)Bm, K, Nc, lb, 1, 0, Rdf, Rdf + bk, st);
+      gemm_df32(Mr, Nc, K, alpha, Ldf, Ldf + ak, Mr, Rdf, Rdf + bk, K, beta, C, lc, 1, 0, st, -1);
+    }
+  }
   void mm(int64_t Mr, int64_t Nc, int64_t K, c128 alpha, const S* Am, int64_t la, int opA, const S* Bm, int64_t lb,
           int opB, c128 beta, S* Cm, int64_t lc) {
+    if (mm_df_ok(Mr, Nc, K, alpha, beta, opA, opB) && (Cm != Am && Cm != Bm)) {
+      mm_df(Mr, Nc, K, alpha.re, Am, la, Bm, lb, beta.re, Cm, lc);
+      return;
+    }
     gemm_simple<S, S, S>(Mr, Nc, K, alpha, Am, la, opA, Bm, lb, opB, beta, Cm, lc, st);
   }
   // C = op(A) op(B) for a k x k x k product of the eigensolver: split-K so

@@ -529,13 +529,13 @@ void kernel_timer_launch_end(int cls, cudaStream_t s, double work) {
 
 void gemm_df32(int64_t M, int64_t N, int64_t K, double alpha, const float* Ahi, const float* Alo, int64_t lda,
                const float* Bhi, const float* Blo, int64_t ldb, double beta, double* C, int64_t ldc, int cs, int co,
-               cudaStream_t s) {
+               cudaStream_t s, int timer_class) {
   if (M <= 0 || N <= 0) return;
-  kernel_timer_launch_begin(TIMER_REFINE_GEMM, s);
+  if (timer_class >= 0) kernel_timer_launch_begin(timer_class, s);
   dim3 grid((unsigned)cdiv(M, DF_BM), (unsigned)cdiv(N, DF_BN));
   gemm_df32_kernel<<<grid, DF_THREADS, 0, s>>>(M, N, K, alpha, Ahi, Alo, lda, Bhi, Blo, ldb, beta, C, ldc, cs, co);
   FEAST_LAUNCH_CHECK();
-  kernel_timer_launch_end(TIMER_REFINE_GEMM, s, (double)M * (double)N * (double)K);
+  if (timer_class >= 0) kernel_timer_launch_end(timer_class, s, (double)M * (double)N * (double)K);
 }
 
 void combine_3m(double* C, const double* T2, int64_t n, int64_t k, cudaStream_t s) {

@@ -60,10 +60,12 @@ namespace feast {
 // error terms and the hi*lo cross products go to an FP32 accumulator that is
 // flushed into an FP64 accumulator every 32 k-steps.  Relative accuracy is
 // ~1e-15 of sum |a||b| at a small fraction of the FP64 cost on sm_103.
+// timer_class: the kernel-timer class the launch is recorded under (-1: none).
 void gemm_df32(int64_t M, int64_t N, int64_t K, double alpha,
                const float* Ahi, const float* Alo, int64_t lda,
                const float* Bhi, const float* Blo, int64_t ldb,
-               double beta, double* C, int64_t ldc, int cs, int co, cudaStream_t s);
+               double beta, double* C, int64_t ldc, int cs, int co, cudaStream_t s,
+               int timer_class = TIMER_REFINE_GEMM);
 
 // 3M complex combination: C_re = T1 - T2, C_im = T3 - T1 - T2 where T1 and T3
 // already sit in C (re, im) and T2 in a separate real array (n x k, ld n).
