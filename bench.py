@@ -48,9 +48,9 @@ OZ_PAIRS = 21                # digit products p + q <= 5 of six 8-bit digits
 # dram__bytes_write.sum over every launch of the n = 4096 solve, profiles/); each launch is
 # a rank-64 (or rank-32) update whose C read-modify-write dominates its traffic, so traffic
 # scales with the flops of the launch; None until captured
-CGEMM_DRAM_BYTES_PER_FLOP = 171.68e9 / 5.2540e12
+CGEMM_DRAM_BYTES_PER_FLOP = 171.81e9 / 5.2540e12
 CGEMM_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum over the 3151 cgemm_prefetch_kernel "
-                        "launches of the n = 4096 solve (171.68 GB, cold-cache replay) / their 5.254e12 flops, "
+                        "launches of the n = 4096 solve (171.81 GB, cold-cache replay) / their 5.254e12 flops, "
                         "x flops per launch")
 
 

@@ -313,7 +313,13 @@ def _rfeast(A, F, lmin, lmax, m0, tol, X0, s, max_iter, anorm):
             sel = select_pairs(rp.lam, rp.res, lmin, lmax, m0)   # (ii)
             X = rp.X[:, sel]
             if j < s:                                   # (iii)
-                R = rp.AX[:, sel] - X * rp.lam[sel][None, :]
+                # residuals of the pairs not yet converged only: a converged
+                # pair's residual is rounding noise, whose normalised
+                # direction adds spurious Ritz pairs (Sect. II-B)
+                act = sel[rp.res[sel] > tol]
+                if act.size == 0:
+                    break
+                R = rp.AX[:, act] - rp.X[:, act] * rp.lam[act][None, :]
                 Rn = normalize_columns(R)
                 for _ in range(2):
                     Rn = Rn - Q @ (Q.conj().T @ Rn)

@@ -637,17 +637,23 @@ struct Solver {
   // ---- orthonormalisation ----
   // Qout = X R^{-1} with X^H X = R^H R.  X, Qout: nr x k (ld nr).  false on breakdown.
   bool cholqr_once(const S* X, int64_t nr, int64_t k, S* Qout) {
-    mm_reduce(k, k, nr, X, nr, OP_C, X, nr, OP_N, Gs, k);
-    hermitize<S>(Gs, k, k, st);
-    cholesky_upper<S>(Gs, k, k, cw, ctx->num_sms, st);
+    phase("CholQR: Gram", [&] {
+      mm_reduce(k, k, nr, X, nr, OP_C, X, nr, OP_N, Gs, k);
+      hermitize<S>(Gs, k, k, st);
+    });
     int info[2] = {0, 0};
-    to_host(ctx, info, cw.info, 1);
     int status = 0;
-    to_host(ctx, &status, cw.status, 1);
+    phase("CholQR: Cholesky", [&] {
+      cholesky_upper<S>(Gs, k, k, cw, ctx->num_sms, st);
+      to_host(ctx, info, cw.info, 1);
+      to_host(ctx, &status, cw.status, 1);
+    });
     if (status == DEV_BARRIER_TIMEOUT) throw FeastError{FEAST_ERR_TIMEOUT};
     if (info[0] != 0) return false;
-    tri_inverse_upper<S>(Gs, k, k, Ri, k, st);
-    mm(nr, k, k, C1(1.0), X, nr, OP_N, Ri, k, OP_N, C1(0.0), Qout, nr);
+    phase("CholQR: X R^-1", [&] {
+      tri_inverse_upper<S>(Gs, k, k, Ri, k, st);
+      mm(nr, k, k, C1(1.0), X, nr, OP_N, Ri, k, OP_N, C1(0.0), Qout, nr);
+    });
     return true;
   }
   // Hermitian eigendecomposition of the k x k matrix H (ld k, overwritten);
@@ -673,24 +679,33 @@ struct Solver {
     to_host(ctx, cn.data(), d_nrm, k);
     double fro2 = 0.0;
     for (double v : cn) fro2 += v;
-    const int sw32 = block_jacobi<F32, S>(H, k, V32, 4e-7 * std::sqrt(fro2), HPb, VPb, Ubj, d_bjrot, 40, st);
-    convert_matrix<S, F32>(Ve, k, V32, k, k, k, st);
-    mm_square(k, Ve, OP_C, Ve, Te);
-    hermitize<S>(Te, k, k, st);
-    cholesky_upper<S>(Te, k, k, cw, ctx->num_sms, st);
+    int sw32 = 0;
+    phase("eig: FP32 block Jacobi", [&] {
+      sw32 = block_jacobi<F32, S>(H, k, V32, 4e-7 * std::sqrt(fro2), HPb, VPb, Ubj, d_bjrot, 40, st);
+    });
     int info = 0;
-    to_host(ctx, &info, cw.info, 1);
-    jacobi_status(nullptr);
+    phase("eig: Cholesky-QR of V", [&] {
+      convert_matrix<S, F32>(Ve, k, V32, k, k, k, st);
+      mm_square(k, Ve, OP_C, Ve, Te);
+      hermitize<S>(Te, k, k, st);
+      cholesky_upper<S>(Te, k, k, cw, ctx->num_sms, st);
+      to_host(ctx, &info, cw.info, 1);
+      jacobi_status(nullptr);
+    });
     if (info != 0) return false;
-    tri_inverse_upper<S>(Te, k, k, T2e, k, st);
-    mm_square(k, Ve, OP_N, T2e, Te);   // Te: orthonormal V
-    mm_square(k, H, OP_N, Te, T2e);    // H V
-    mm_square(k, Te, OP_C, T2e, H);    // V^H H V
-    hermitize<S>(H, k, k, st);
-    jacobi_eigh<S>(H, k, k, T2e, k, 1e-15, cw, ctx->num_sms, st);
+    phase("eig: V^H H V", [&] {
+      tri_inverse_upper<S>(Te, k, k, T2e, k, st);
+      mm_square(k, Ve, OP_N, T2e, Te);   // Te: orthonormal V
+      mm_square(k, H, OP_N, Te, T2e);    // H V
+      mm_square(k, Te, OP_C, T2e, H);    // V^H H V
+      hermitize<S>(H, k, k, st);
+    });
     int sw64 = 0;
-    jacobi_status(&sw64);
-    mm_square(k, Te, OP_N, T2e, Vk);
+    phase("eig: FP64 Jacobi", [&] {
+      jacobi_eigh<S>(H, k, k, T2e, k, 1e-15, cw, ctx->num_sms, st);
+      jacobi_status(&sw64);
+    });
+    phase("eig: V V'", [&] { mm_square(k, Te, OP_N, T2e, Vk); });
     *sweeps = sw32 + sw64;
     if (std::getenv("FEAST_LOG"))
       fprintf(stderr, "[feast] two-phase eig k=%lld: %d FP32 + %d FP64 sweeps\n", (long long)k, sw32, sw64);
@@ -750,8 +765,10 @@ struct Solver {
   // W = A Q, A' = Q^H W (ld kmax) for the first k columns of Qb
   void rr_project(int64_t k) {
     phase("RR A*Q", [&] { apply_A(Qb, k, Wb); });
-    mm_reduce(k, k, n, Qb, n, OP_C, Wb, n, OP_N, Ar0, kmax);
-    hermitize<S>(Ar0, k, kmax, st);
+    phase("RR Q^H W", [&] {
+      mm_reduce(k, k, n, Qb, n, OP_C, Wb, n, OP_N, Ar0, kmax);
+      hermitize<S>(Ar0, k, kmax, st);
+    });
   }
   // diagonalise A'[0:k, 0:k]: lam (ascending), Xr = Q V, AXr = W V, res
   void rr_solve(int64_t k) {
@@ -764,11 +781,13 @@ struct Solver {
     lam.resize(k);
     for (int64_t i = 0; i < k; ++i) lam[i] = ev[ord[i]];
     to_dev(ctx, d_idx, ord.data(), k);
-    gather_cols<S>(Cs, k, Vk, k, k, d_idx, k, nullptr, st);
-    mm(n, k, k, C1(1.0), Qb, n, OP_N, Cs, k, OP_N, C1(0.0), Xr, n);
-    mm(n, k, k, C1(1.0), Wb, n, OP_N, Cs, k, OP_N, C1(0.0), AXr, n);
-    to_dev(ctx, d_lam, lam.data(), k);
-    resid_norms2<S>(AXr, Xr, n, k, n, d_lam, d_nrm, st);
+    phase("RR X = QV, AX = WV", [&] {
+      gather_cols<S>(Cs, k, Vk, k, k, d_idx, k, nullptr, st);
+      mm(n, k, k, C1(1.0), Qb, n, OP_N, Cs, k, OP_N, C1(0.0), Xr, n);
+      mm(n, k, k, C1(1.0), Wb, n, OP_N, Cs, k, OP_N, C1(0.0), AXr, n);
+      to_dev(ctx, d_lam, lam.data(), k);
+      resid_norms2<S>(AXr, Xr, n, k, n, d_lam, d_nrm, st);
+    });
     res.resize(k);
     to_host(ctx, res.data(), d_nrm, k);
     for (auto& r : res) r = std::sqrt(r) / anorm;
@@ -1044,15 +1063,23 @@ struct Solver {
           ritz_residual<S>(R, AXs, X, n, ms, n, d_lam, st);
           col_norms2<S>(R, n, ms, n, d_nrm, st);
           std::vector<double> nr2(ms), sc(ms);
-          std::vector<int> iden(ms);
           to_host(ctx, nr2.data(), d_nrm, ms);
-          for (int64_t i = 0; i < ms; ++i) {
-            sc[i] = nr2[i] > 0 ? 1.0 / std::sqrt(nr2[i]) : 1.0;
-            iden[i] = (int)i;
-          }
-          to_dev(ctx, d_scale, sc.data(), ms);
-          to_dev(ctx, d_idx, iden.data(), ms);
-          scale_cols<S>(R, n, ms, n, d_scale, st);
+          // only the pairs that have not converged expand the subspace: a
+          // converged pair's residual is at the rounding level of A X, and its
+          // normalised direction would add spurious Ritz pairs, not information
+          std::vector<int> act;
+          for (int64_t i = 0; i < ms; ++i)
+            if (res[sel[i]] > tol && nr2[i] > 0) act.push_back((int)i);
+          const int64_t ma = (int64_t)act.size();
+          if (std::getenv("FEAST_LOG"))
+            fprintf(stderr, "[feast] rfeast it %d j %d: %lld of %lld residuals appended\n", it, j, (long long)ma,
+                    (long long)ms);
+          if (ma == 0) break;  // every selected pair has converged
+          for (int64_t c = 0; c < ma; ++c) sc[c] = 1.0 / std::sqrt(nr2[act[c]]);
+          to_dev(ctx, d_scale, sc.data(), ma);
+          to_dev(ctx, d_idx, act.data(), ma);
+          gather_cols<S>(AXs, n, T1, n, n, d_idx, ma, d_scale, st);
+          R = AXs;
           // continue in the Ritz basis of this pass (same span): Q <- X, W <- A X,
           // A' <- diag(lambda), so the next Jacobi starts from a matrix whose
           // leading block is already diagonal
@@ -1060,20 +1087,24 @@ struct Solver {
           copy_matrix<S>(Wb, n, AXr, n, n, k, st);
           to_dev(ctx, d_lam, lam.data(), k);
           set_diag<S>(Ar0, k, kmax, d_lam, st);
-          for (int rep = 0; rep < 2; ++rep) {
-            mm_reduce(k, ms, n, Qb, n, OP_C, R, n, OP_N, Cs2, k);
-            mm(n, ms, k, C1(-1.0), Qb, n, OP_N, Cs2, k, OP_N, C1(1.0), R, n);
-          }
+          phase("RFEAST R - Q Q^H R", [&] {
+            for (int rep = 0; rep < 2; ++rep) {
+              mm_reduce(k, ma, n, Qb, n, OP_C, R, n, OP_N, Cs2, k);
+              mm(n, ma, k, C1(-1.0), Qb, n, OP_N, Cs2, k, OP_N, C1(1.0), R, n);
+            }
+          });
           S* U = Qb + k * n;
-          const int64_t ku = orthonormalize(R, n, ms, U, T2);
+          const int64_t ku = orthonormalize(R, n, ma, U, T2);
           if (ku == 0) break;  // nothing new to append
           S* WU = Wb + k * n;
-          apply_A(U, ku, WU);
+          phase("RR A*Q", [&] { apply_A(U, ku, WU); });
           // A' blocks: [Q U]^H A [Q U] from the new columns only
-          mm_reduce(k, ku, n, Qb, n, OP_C, WU, n, OP_N, Ar0 + k * kmax, kmax);
-          mm_reduce(ku, k, n, U, n, OP_C, Wb, n, OP_N, Ar0 + k, kmax);
-          mm_reduce(ku, ku, n, U, n, OP_C, WU, n, OP_N, Ar0 + k + k * kmax, kmax);
-          hermitize<S>(Ar0, k + ku, kmax, st);
+          phase("RFEAST A' blocks", [&] {
+            mm_reduce(k, ku, n, Qb, n, OP_C, WU, n, OP_N, Ar0 + k * kmax, kmax);
+            mm_reduce(ku, k, n, U, n, OP_C, Wb, n, OP_N, Ar0 + k, kmax);
+            mm_reduce(ku, ku, n, U, n, OP_C, WU, n, OP_N, Ar0 + k + k * kmax, kmax);
+            hermitize<S>(Ar0, k + ku, kmax, st);
+          });
           k += ku;
         } else if (j < s) {
           break;
