@@ -9,7 +9,7 @@ import pytest
 
 import oracle as O
 from oracle.feast import inside, select_pairs
-from workloads import (make_problem, random_subspace, spectrum_config1, spectrum_paper,
+from workloads import (make_problem, random_subspace, spectrum_config1, spectrum_config2, spectrum_paper,
                        spectrum_uniform)
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_setups.json")
@@ -136,3 +136,46 @@ def test_expanded_variants_beat_feast_on_dense_spectrum():
         rhs[v] = r.filters * n_c * m0
     assert rhs[O.XFEAST] < rhs[O.PLAIN]
     assert rhs[O.RFEAST] < rhs[O.PLAIN]
+
+
+def test_rfeast_expansion_is_robust_to_rounding_noise():
+    # RFEAST appends only the residuals of selected pairs that have not yet
+    # converged (reading of Sect. II-B): a converged pair's residual is at the
+    # rounding level of A X, and its normalised direction only adds spurious
+    # in-I Ritz pairs.  With noise of 1e-11 ||A|| in every A Q product the
+    # edge-cluster solve must still converge in the noiseless number of rounds
+    # (appending every residual, it did not converge in 20).
+    import oracle.feast as OF
+
+    lam, a, b = spectrum_config2(0, n=768, m_in=18, edge_in=2, edge_out=5)
+    P = make_problem("c2", lam, a, b, 28, 8, seed=0, complex_=True)
+    X0 = random_subspace(P.n, P.m0, seed=1, complex_=True)
+    F = O.factor_shifts(P.A, a, b, 8)
+    clean = O.feast_solve(P.A, a, b, P.m0, 8, 1e-10, X0, variant=O.RFEAST, anorm=P.anorm, factors=F,
+                          max_iter=20)
+    # (eigenvectors inside the 1e-4 edge clusters are not individually
+    # determined to 1e-8, so spans are not compared here)
+    assert clean.status == 0 and clean.lam.size == P.inside.size
+
+    rng = np.random.default_rng(5)
+    rr = OF.rayleigh_ritz
+
+    class NoisyA:
+        def __init__(self, A):
+            self.A = A
+
+        def __matmul__(self, X):
+            W = self.A @ X
+            e = rng.standard_normal(W.shape) + 1j * rng.standard_normal(W.shape)
+            return W + 1e-11 * P.anorm * e / np.sqrt(2 * W.shape[0])
+
+    try:
+        OF.rayleigh_ritz = lambda A, Q, anorm: rr(NoisyA(A), Q, anorm)
+        noisy = O.feast_solve(P.A, a, b, P.m0, 8, 1e-10, X0, variant=O.RFEAST, anorm=P.anorm, factors=F,
+                              max_iter=20)
+    finally:
+        OF.rayleigh_ritz = rr
+    assert noisy.status == 0
+    assert noisy.iterations <= clean.iterations
+    np.testing.assert_allclose(noisy.lam, P.inside, rtol=1e-9, atol=1e-11 * P.anorm)
+    assert noisy.res.max() <= 1e-10
