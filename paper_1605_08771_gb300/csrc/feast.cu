@@ -346,7 +346,8 @@ struct Solver {
     Ri = dalloc<S>(ctx, kk); Cs = dalloc<S>(ctx, kk); Cs2 = dalloc<S>(ctx, kk);
     if (o.prec != FEAST_PREC_F64 && (double)n * kmax * kmax >= kDfMinWork) {
       Ldf = dalloc<float>(ctx, 4 * n * kmax);
-      Rdf = dalloc<float>(ctx, 4 * kk);
+      Rdf = dalloc<float>(ctx, 4 * n * kmax);
+      Pdf = dalloc<double>(ctx, (int64_t)kDfMaxSplit * 2 * kk);
     }
     if (kmax >= kEigMixedMin) {
       H32 = dalloc<F32>(ctx, kk); V32 = dalloc<F32>(ctx, kk);
@@ -366,19 +367,62 @@ struct Solver {
 
   // ---- small GEMM helpers ----
   // Mixed path: products C = alpha A B + beta C with op N on both sides (the
-  // tall n x k products Q V, W V, X R^-1, Q C and the eigensolver's k x k
-  // products) in double-float arithmetic on the FP32 pipes, error ~2^-44
-  // termwise, several times the FP64 rate of this GPU.  Complex products take
-  // the four real products (4M): the three-product form (3M) forms Im as
-  // T3 - T1 - T2, whose cancellation made the n = 8192 RFEAST solve take 4
-  // iterations instead of 2; 4M keeps 2.
+  // tall n x k products Q V, W V, X R^-1, Q C) and the reductions over n
+  // below in double-float arithmetic on the FP32 pipes, several times the
+  // FP64 rate of this GPU.  The low word of each product sum is accumulated in
+  // FP32 and flushed to FP64 every 32 terms; the error stays within 2^-44 of
+  // sum |a||b| (the parity tests' bound), against ~1e-16 sqrt(K) in FP64.  The
+  // eigensolver's k x k products and the Gram matrices stay FP64.  Complex
+  // products take the four real products (4M): the three-product form (3M)
+  // forms Im as T3 - T1 - T2, whose cancellation made the n = 8192 RFEAST solve
+  // take 4 iterations instead of 2; 4M keeps 2.
   float* Ldf = nullptr;  // 4 planes (Re hi/lo, Im hi/lo) of n x kmax
-  float* Rdf = nullptr;  // 4 planes of kmax x kmax
+  float* Rdf = nullptr;  // 4 planes of n x kmax
+  double* Pdf = nullptr; // split-K partial products of the reductions over n
   static constexpr double kDfMinWork = 1e6;
+  static constexpr int kDfMaxSplit = 16;
   bool mm_df_ok(int64_t Mr, int64_t Nc, int64_t K, c128 alpha, c128 beta, int opA, int opB) const {
     if (!Ldf || opA != OP_N || opB != OP_N || alpha.im != 0.0 || beta.im != 0.0) return false;
     if ((double)Mr * (double)Nc * (double)K < kDfMinWork) return false;
-    return Mr * K <= n * kmax && K * Nc <= kmax * kmax;
+    return Mr * K <= n * kmax && K * Nc <= n * kmax;
+  }
+  // Reductions over n, C = A^H B (C: Mr x Nc with Mr, Nc <= kmax, K = n:
+  // Q^H W, Q^H R and the RFEAST blocks of A'), other than Gram matrices
+  // (A == B, which Cholesky-QR needs in FP64): double-float 4M, the reduction
+  // split into slices over all SMs.  At n = 8192 they keep the RFEAST solve at
+  // 2 rounds once only unconverged pairs expand the subspace (appending every
+  // residual, the noise they add stopped it from converging).
+  bool mm_df_reduce_ok(int64_t Mr, int64_t Nc, int64_t K, const S* Am, int opA, const S* Bm, int opB) const {
+    if (!Ldf || !Pdf || opA != OP_C || opB != OP_N || Am == Bm) return false;
+    if ((double)Mr * (double)Nc * (double)K < kDfMinWork) return false;
+    return Mr <= kmax && Nc <= kmax && Mr * K <= n * kmax && K * Nc <= n * kmax;
+  }
+  void mm_df_reduce(int64_t Mr, int64_t Nc, int64_t K, const S* Am, int64_t la, const S* Bm, int64_t lb, S* Cm,
+                    int64_t lc) {
+    const int64_t ak = Mr * K, bk = K * Nc;
+    const int64_t tiles = cdiv(Mr, 64) * cdiv(Nc, 64);
+    int ks = (int)std::min<int64_t>({(int64_t)kDfMaxSplit, std::max<int64_t>(1, K / 256),
+                                     std::max<int64_t>(1, cdiv(3 * ctx->num_sms, tiles))});
+    const int w = kCplx ? 2 : 1;
+    const int64_t czs = (int64_t)w * Mr * Nc;
+    if constexpr (std::is_same<S, c128>::value) {
+      // planes of A^H: Re, then -Im (conjugate); of B: Re, Im
+      split_df32_t((const double*)Am, Mr, K, la, 2, 0, false, Ldf, Ldf + ak, st);
+      split_df32_t((const double*)Am, Mr, K, la, 2, 1, true, Ldf + 2 * ak, Ldf + 3 * ak, st);
+      split_df32((const double*)Bm, K, Nc, lb, 2, 0, Rdf, Rdf + bk, st);
+      split_df32((const double*)Bm, K, Nc, lb, 2, 1, Rdf + 2 * bk, Rdf + 3 * bk, st);
+      double* P = Pdf;
+      gemm_df32(Mr, Nc, K, 1.0, Ldf, Ldf + ak, Mr, Rdf, Rdf + bk, K, 0.0, P, Mr, 2, 0, st, -1, ks, czs);
+      gemm_df32(Mr, Nc, K, -1.0, Ldf + 2 * ak, Ldf + 3 * ak, Mr, Rdf + 2 * bk, Rdf + 3 * bk, K, 1.0, P, Mr, 2, 0, st,
+                -1, ks, czs);
+      gemm_df32(Mr, Nc, K, 1.0, Ldf, Ldf + ak, Mr, Rdf + 2 * bk, Rdf + 3 * bk, K, 0.0, P, Mr, 2, 1, st, -1, ks, czs);
+      gemm_df32(Mr, Nc, K, 1.0, Ldf + 2 * ak, Ldf + 3 * ak, Mr, Rdf, Rdf + bk, K, 1.0, P, Mr, 2, 1, st, -1, ks, czs);
+    } else {
+      split_df32_t((const double*)Am, Mr, K, la, 1, 0, false, Ldf, Ldf + ak, st);
+      split_df32((const double*)Bm, K, Nc, lb, 1, 0, Rdf, Rdf + bk, st);
+      gemm_df32(Mr, Nc, K, 1.0, Ldf, Ldf + ak, Mr, Rdf, Rdf + bk, K, 0.0, Pdf, Mr, 1, 0, st, -1, ks, czs);
+    }
+    sum_partials((double*)Cm, lc, Pdf, Mr, Nc, ks, kCplx, st);
   }
   // complex C = alpha A B + beta C by four real double-float products (4M)
   void mm_df(int64_t Mr, int64_t Nc, int64_t K, double alpha, const S* Am, int64_t la, const S* Bm, int64_t lb,
@@ -422,6 +466,10 @@ struct Solver {
   // C (Mr x Nc) = op(A) op(B) with a long reduction K: split-K
   void mm_reduce(int64_t Mr, int64_t Nc, int64_t K, const S* Am, int64_t la, int opA, const S* Bm, int64_t lb,
                  int opB, S* Cm, int64_t lc) {
+    if (mm_df_reduce_ok(Mr, Nc, K, Am, opA, Bm, opB)) {
+      mm_df_reduce(Mr, Nc, K, Am, la, Bm, lb, Cm, lc);
+      return;
+    }
     int ks = (int)std::max<int64_t>(1, std::min<int64_t>(32, K / 256));
     while (ks > 1 && (int64_t)ks * lc * Nc > part_elems) --ks;
     gemm_simple<S, S, S>(Mr, Nc, K, C1(1.0), Am, la, opA, Bm, lb, opB, C1(0.0), Cm, lc, st, ks,
@@ -704,6 +752,13 @@ struct Solver {
     phase("eig: FP64 Jacobi", [&] {
       jacobi_eigh<S>(H, k, k, T2e, k, 1e-15, cw, ctx->num_sms, st);
       jacobi_status(&sw64);
+      if (std::getenv("FEAST_LOG")) {
+        std::vector<unsigned> rc(sw64 > 0 ? sw64 : 1);
+        to_host(ctx, rc.data(), cw.rotcount, rc.size());
+        fprintf(stderr, "[feast] FP64 Jacobi k=%lld rotations per sweep:", (long long)k);
+        for (unsigned v : rc) fprintf(stderr, " %u", v);
+        fprintf(stderr, "\n");
+      }
     });
     phase("eig: V V'", [&] { mm_square(k, Te, OP_N, T2e, Vk); });
     *sweeps = sw32 + sw64;

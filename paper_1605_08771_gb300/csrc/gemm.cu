@@ -344,7 +344,8 @@ __device__ __forceinline__ void df_mac(float a, float al, float b, float bl, flo
 __global__ void __launch_bounds__(DF_THREADS)
 gemm_df32_kernel(int64_t M, int64_t N, int64_t K, double alpha, const float* __restrict__ Ahi,
                  const float* __restrict__ Alo, int64_t lda, const float* __restrict__ Bhi,
-                 const float* __restrict__ Blo, int64_t ldb, double beta, double* C, int64_t ldc, int cs, int co) {
+                 const float* __restrict__ Blo, int64_t ldb, double beta, double* C, int64_t ldc, int cs, int co,
+                 int64_t kper, int64_t czs) {
   __shared__ __align__(16) float sAh[DF_BK][DF_BM];
   __shared__ __align__(16) float sAl[DF_BK][DF_BM];
   __shared__ __align__(16) float sBh[DF_BK][DF_BN + 1];
@@ -360,13 +361,16 @@ gemm_df32_kernel(int64_t M, int64_t N, int64_t K, double alpha, const float* __r
     for (int j = 0; j < DF_TN; ++j) { s[i][j] = 0.f; x[i][j] = 0.f; d[i][j] = 0.0; }
 
   int tile = 0;
-  for (int64_t k0 = 0; k0 < K; k0 += DF_BK, ++tile) {
+  // split-K: slice z of the reduction writes its own output block
+  const int64_t kbeg = (int64_t)blockIdx.z * kper, kend = min(K, kbeg + kper);
+  C += (int64_t)blockIdx.z * czs;
+  for (int64_t k0 = kbeg; k0 < kend; k0 += DF_BK, ++tile) {
     // A tile: BM x BK, consecutive threads along m (coalesced)
     for (int l = t; l < DF_BM * DF_BK; l += DF_THREADS) {
       const int mm = l % DF_BM, kk = l / DF_BM;
       const int64_t gm = m0 + mm, gk = k0 + kk;
       float h = 0.f, lo = 0.f;
-      if (gm < M && gk < K) { h = Ahi[gm + gk * lda]; lo = Alo[gm + gk * lda]; }
+      if (gm < M && gk < kend) { h = Ahi[gm + gk * lda]; lo = Alo[gm + gk * lda]; }
       sAh[kk][mm] = h;
       sAl[kk][mm] = lo;
     }
@@ -375,7 +379,7 @@ gemm_df32_kernel(int64_t M, int64_t N, int64_t K, double alpha, const float* __r
       const int kk = l % DF_BK, nn = l / DF_BK;
       const int64_t gk = k0 + kk, gn = n0 + nn;
       float h = 0.f, lo = 0.f;
-      if (gn < N && gk < K) { h = Bhi[gk + gn * ldb]; lo = Blo[gk + gn * ldb]; }
+      if (gn < N && gk < kend) { h = Bhi[gk + gn * ldb]; lo = Blo[gk + gn * ldb]; }
       sBh[kk][nn] = h;
       sBl[kk][nn] = lo;
     }
@@ -445,6 +449,46 @@ __global__ void combine_axpby_kernel(double* C, int64_t ldc, int cplx, const dou
       double* c = C + (i + j * ldc);
       *c = beta != 0.0 ? alpha * T[idx] + beta * (*c) : alpha * T[idx];
     }
+  }
+}
+
+// hi/lo planes (rows x cols, ld rows) of a transposed source: element (i, j)
+// is src[(j + i*lds)*ss + so], negated when neg; staged through shared memory
+// so both sides are coalesced
+__global__ void split_df32_t_kernel(const double* src, int64_t rows, int64_t cols, int64_t lds, int ss, int so, int neg,
+                                    float* hi, float* lo) {
+  __shared__ double tile[32][33];
+  const int64_t i0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int64_t i = i0 + r, j = j0 + threadIdx.x;
+    double v = 0.0;
+    if (i < rows && j < cols) v = src[(j + i * lds) * ss + so];
+    tile[r][threadIdx.x] = neg ? -v : v;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int64_t j = j0 + r, i = i0 + threadIdx.x;
+    if (i < rows && j < cols) {
+      const double v = tile[threadIdx.x][r];
+      const float h = (float)v;
+      hi[i + j * rows] = h;
+      lo[i + j * rows] = (float)(v - (double)h);
+    }
+  }
+}
+
+// C (M x N, ld ldc, interleaved complex when cplx) = sum over ks partial
+// blocks P (each M x N with leading dim M, same element layout)
+__global__ void sum_partials_kernel(double* C, int64_t ldc, const double* P, int64_t M, int64_t N, int ks, int cplx) {
+  const int w = cplx ? 2 : 1;
+  const int64_t blk = M * N * w;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < M * N * w;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = idx / w, part = idx % w;
+    const int64_t i = e % M, j = e / M;
+    double acc = 0.0;
+    for (int z = 0; z < ks; ++z) acc += P[z * blk + idx];
+    C[(i + j * ldc) * w + part] = acc;
   }
 }
 
@@ -529,11 +573,14 @@ void kernel_timer_launch_end(int cls, cudaStream_t s, double work) {
 
 void gemm_df32(int64_t M, int64_t N, int64_t K, double alpha, const float* Ahi, const float* Alo, int64_t lda,
                const float* Bhi, const float* Blo, int64_t ldb, double beta, double* C, int64_t ldc, int cs, int co,
-               cudaStream_t s, int timer_class) {
+               cudaStream_t s, int timer_class, int ksplit, int64_t czs) {
   if (M <= 0 || N <= 0) return;
   if (timer_class >= 0) kernel_timer_launch_begin(timer_class, s);
-  dim3 grid((unsigned)cdiv(M, DF_BM), (unsigned)cdiv(N, DF_BN));
-  gemm_df32_kernel<<<grid, DF_THREADS, 0, s>>>(M, N, K, alpha, Ahi, Alo, lda, Bhi, Blo, ldb, beta, C, ldc, cs, co);
+  ksplit = std::max(1, ksplit);
+  const int64_t kper = cdiv(cdiv(K, ksplit), 2 * DF_BK) * (2 * DF_BK);
+  dim3 grid((unsigned)cdiv(M, DF_BM), (unsigned)cdiv(N, DF_BN), (unsigned)ksplit);
+  gemm_df32_kernel<<<grid, DF_THREADS, 0, s>>>(M, N, K, alpha, Ahi, Alo, lda, Bhi, Blo, ldb, beta, C, ldc, cs, co, kper,
+                                               czs);
   FEAST_LAUNCH_CHECK();
   if (timer_class >= 0) kernel_timer_launch_end(timer_class, s, (double)M * (double)N * (double)K);
 }
@@ -552,6 +599,22 @@ void combine_axpby(double* C, int64_t ldc, bool cplx, const double* T, const dou
   if (total <= 0) return;
   const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(total, 256), 16384));
   combine_axpby_kernel<<<g, 256, 0, s>>>(C, ldc, cplx ? 1 : 0, T, T2, M, N, alpha, beta);
+  FEAST_LAUNCH_CHECK();
+}
+
+void split_df32_t(const double* src, int64_t rows, int64_t cols, int64_t lds, int ss, int so, bool neg, float* hi,
+                  float* lo, cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return;
+  dim3 g((unsigned)cdiv(rows, 32), (unsigned)cdiv(cols, 32));
+  split_df32_t_kernel<<<g, dim3(32, 8), 0, s>>>(src, rows, cols, lds, ss, so, neg ? 1 : 0, hi, lo);
+  FEAST_LAUNCH_CHECK();
+}
+
+void sum_partials(double* C, int64_t ldc, const double* P, int64_t M, int64_t N, int ks, bool cplx, cudaStream_t s) {
+  const int64_t total = M * N * (cplx ? 2 : 1);
+  if (total <= 0) return;
+  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(total, 256), 16384));
+  sum_partials_kernel<<<g, 256, 0, s>>>(C, ldc, P, M, N, ks, cplx ? 1 : 0);
   FEAST_LAUNCH_CHECK();
 }
 

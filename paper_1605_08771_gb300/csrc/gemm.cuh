@@ -58,14 +58,17 @@ namespace feast {
 // column-major, op N.  Each hi*hi product is made exact with an FMA
 // (TwoProd), each addition to the running FP32 sum exact with TwoSum; the
 // error terms and the hi*lo cross products go to an FP32 accumulator that is
-// flushed into an FP64 accumulator every 32 k-steps.  Relative accuracy is
-// ~1e-15 of sum |a||b| at a small fraction of the FP64 cost on sm_103.
+// flushed into an FP64 accumulator every 32 k-steps.  The error stays within
+// 2^-44 of sum |a||b| (the parity tests' bound, K up to 4099), at a small
+// fraction of the FP64 cost on sm_103.
 // timer_class: the kernel-timer class the launch is recorded under (-1: none).
+// ksplit > 1: the reduction is cut into ksplit slices, slice z writing its own
+// output block at C + z * czs (to be summed by sum_partials).
 void gemm_df32(int64_t M, int64_t N, int64_t K, double alpha,
                const float* Ahi, const float* Alo, int64_t lda,
                const float* Bhi, const float* Blo, int64_t ldb,
                double beta, double* C, int64_t ldc, int cs, int co, cudaStream_t s,
-               int timer_class = TIMER_REFINE_GEMM);
+               int timer_class = TIMER_REFINE_GEMM, int ksplit = 1, int64_t czs = 0);
 
 // 3M complex combination: C_re = T1 - T2, C_im = T3 - T1 - T2 where T1 and T3
 // already sit in C (re, im) and T2 in a separate real array (n x k, ld n).
@@ -77,6 +80,16 @@ void combine_3m(double* C, const double* T2, int64_t n, int64_t k, cudaStream_t 
 // leading dim M, and the value is (T1 - T2) + i (T3 - T1 - T2).
 void combine_axpby(double* C, int64_t ldc, bool cplx, const double* T, const double* T2, int64_t M, int64_t N,
                    double alpha, double beta, cudaStream_t s);
+
+// hi/lo planes (rows x cols, ld rows) of the transpose of a column-major
+// source: plane element (i, j) = src[(j + i*lds)*ss + so] (negated when neg,
+// e.g. the imaginary part of a conjugate transpose).
+void split_df32_t(const double* src, int64_t rows, int64_t cols, int64_t lds, int ss, int so, bool neg, float* hi,
+                  float* lo, cudaStream_t s);
+
+// C (M x N, leading dim ldc; interleaved complex when cplx) = sum of ks
+// partial blocks P + z * M * N * (cplx ? 2 : 1), each with leading dim M.
+void sum_partials(double* C, int64_t ldc, const double* P, int64_t M, int64_t N, int ks, bool cplx, cudaStream_t s);
 
 // Split FP64 values into hi/lo float planes: src element (i, j) at
 // src[(i + j*lds)*ss + so] (so = 2 with ss = 2: the sum Re + Im of a complex
