@@ -137,7 +137,8 @@ __global__ void tri_inv_kernel(const S* R, int64_t k, int64_t ld, S* Ri, int64_t
 // rounded up to even (index k is a dummy when k is odd).
 template <typename S>
 __global__ void __launch_bounds__(256)
-jacobi_kernel(S* H, int64_t k, int64_t ld, S* V, int64_t ldv, double tol, CoopWork w, int P, int max_sweeps) {
+jacobi_kernel(S* H, int64_t k, int64_t ld, S* V, int64_t ldv, double tol, CoopWork w, int P, int max_sweeps,
+              int init_v) {
   using R = real_t<S>;  // rotations in the working precision (FP32 or FP64)
   const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t NT = (int64_t)P * blockDim.x;
@@ -145,15 +146,16 @@ jacobi_kernel(S* H, int64_t k, int64_t ld, S* V, int64_t ldv, double tol, CoopWo
   const int64_t kk = k + (k & 1), np = kk / 2, m1 = kk - 1;
   R* rc = (R*)w.rot;
   R* rs = rc + np;
-  S* re = (S*)(rs + np);
-  int* ron = (int*)(re + np);
+  S* rse = (S*)(rs + np);  // e s and e c of each pair's rotation
+  S* rce = rse + np;
+  int* ron = (int*)(rce + np);
   int* rpp = ron + np;
   int* rqq = rpp + np;
 
   double part = 0.0;
   for (int64_t idx = gt; idx < k * k; idx += NT) {
     const int64_t i = idx % k, j = idx / k;
-    V[i + j * ldv] = (i == j) ? one<S>() : num<S>::zero();
+    if (init_v) V[i + j * ldv] = (i == j) ? one<S>() : num<S>::zero();
     part += abs2(H[i + j * ld]);
   }
   part = block_sum(part);
@@ -173,7 +175,7 @@ jacobi_kernel(S* H, int64_t k, int64_t ld, S* V, int64_t ldv, double tol, CoopWo
         else { a = (r + i) % m1; b = ((r - i) % m1 + m1) % m1; }
         const int64_t p = a < b ? a : b, q = a < b ? b : a;
         R c = R(1), s = R(0);
-        S e = one<S>();
+        S se = num<S>::zero(), ce = one<S>();
         int on = 0;
         if (q < k) {
           const S apq = ldcg(&H[p + q * ld]);
@@ -181,16 +183,18 @@ jacobi_kernel(S* H, int64_t k, int64_t ld, S* V, int64_t ldv, double tol, CoopWo
           if (g > thr) {
             const R app = real_part(ldcg(&H[p + p * ld]));
             const R aqq = real_part(ldcg(&H[q + q * ld]));
-            e = conj(apq) * (R(1) / g);
+            const S e = conj(apq) * (R(1) / g);
             const R tau = (aqq - app) / (R(2) * g);
             const R t = (tau >= R(0) ? R(1) : R(-1)) / (fabs(tau) + hypot(R(1), tau));
             c = R(1) / hypot(R(1), t);
             s = t * c;
+            se = e * s;
+            ce = e * c;
             on = 1;
           }
         }
         any_on |= on;
-        rc[i] = c; rs[i] = s; re[i] = e; ron[i] = on; rpp[i] = (int)p; rqq[i] = (int)q;
+        rc[i] = c; rs[i] = s; rse[i] = se; rce[i] = ce; ron[i] = on; rpp[i] = (int)p; rqq[i] = (int)q;
       }
       // a round that rotates no pair skips its update phase and second barrier
       // (late sweeps rotate few pairs): one count per round, read after the barrier
@@ -204,7 +208,10 @@ jacobi_kernel(S* H, int64_t k, int64_t ld, S* V, int64_t ldv, double tol, CoopWo
       const int64_t nblk = np * np;
       for (int64_t task = gt; task < nblk + k * np; task += NT) {
         if (task < nblk) {
+          // H stays exactly Hermitian: block (I, J) with I <= J is rotated and
+          // written with its mirror (J, I)
           const int64_t I = task % np, J = task / np;
+          if (I > J) continue;
           const int onI = __ldcg(&ron[I]), onJ = __ldcg(&ron[J]);
           if (!onI && !onJ) continue;
           const int pI = __ldcg(&rpp[I]), qI = __ldcg(&rqq[I]);
@@ -216,16 +223,14 @@ jacobi_kernel(S* H, int64_t k, int64_t ld, S* V, int64_t ldv, double tol, CoopWo
           S b11 = (vqI && vqJ) ? ldcg(&H[qI + (int64_t)qJ * ld]) : num<S>::zero();
           if (onJ) {
             const R c = __ldcg(&rc[J]), s = __ldcg(&rs[J]);
-            const S e = ldcg(&re[J]);
-            const S se = e * s, ce = e * c;
+            const S se = ldcg(&rse[J]), ce = ldcg(&rce[J]);
             S n00 = b00 * c - b01 * se, n01 = b00 * s + b01 * ce;
             S n10 = b10 * c - b11 * se, n11 = b10 * s + b11 * ce;
             b00 = n00; b01 = n01; b10 = n10; b11 = n11;
           }
           if (onI) {
             const R c = __ldcg(&rc[I]), s = __ldcg(&rs[I]);
-            const S ec = conj(ldcg(&re[I]));
-            const S sec = ec * s, cec = ec * c;
+            const S sec = conj(ldcg(&rse[I])), cec = conj(ldcg(&rce[I]));
             S n00 = b00 * c - b10 * sec, n10 = b00 * s + b10 * cec;
             S n01 = b01 * c - b11 * sec, n11 = b01 * s + b11 * cec;
             b00 = n00; b01 = n01; b10 = n10; b11 = n11;
@@ -240,18 +245,24 @@ jacobi_kernel(S* H, int64_t k, int64_t ld, S* V, int64_t ldv, double tol, CoopWo
           if (vqJ) H[pI + (int64_t)qJ * ld] = b01;
           if (vqI) H[qI + (int64_t)pJ * ld] = b10;
           if (vqI && vqJ) H[qI + (int64_t)qJ * ld] = b11;
+          if (I != J) {
+            H[pJ + (int64_t)pI * ld] = conj(b00);
+            if (vqJ) H[qJ + (int64_t)pI * ld] = conj(b01);
+            if (vqI) H[pJ + (int64_t)qI * ld] = conj(b10);
+            if (vqI && vqJ) H[qJ + (int64_t)qI * ld] = conj(b11);
+          }
         } else {
           const int64_t tv = task - nblk;
           const int64_t row = tv % k, J = tv / k;
           if (!__ldcg(&ron[J])) continue;
           const int pJ = __ldcg(&rpp[J]), qJ = __ldcg(&rqq[J]);
           const R c = __ldcg(&rc[J]), s = __ldcg(&rs[J]);
-          const S e = ldcg(&re[J]);
+          const S se = ldcg(&rse[J]), ce = ldcg(&rce[J]);
           S* vp = &V[row + (int64_t)pJ * ldv];
           S* vq = &V[row + (int64_t)qJ * ldv];
           const S a = ldcg(vp), b = ldcg(vq);
-          *vp = a * c - b * (e * s);
-          *vq = a * s + b * (e * c);
+          *vp = a * c - b * se;
+          *vq = a * s + b * ce;
         }
       }
       if (!group_barrier(w.counter, (++nb) * (unsigned)P, w.status)) return;
@@ -443,7 +454,7 @@ size_t coop_work_bytes(int64_t kmax, int num_sms) {
   const int64_t np = (kmax + 2) / 2;
   return 256 * 4 + sizeof(double) * 2 * (size_t)std::max(num_sms, 1024) + 256 +
          sizeof(unsigned) * kMaxSweeps + 256 + sizeof(unsigned) * kMaxSweeps * (size_t)(kmax + 2) + 256 +
-         (size_t)np * (2 * sizeof(double) + sizeof(c128) + 3 * sizeof(int)) + 256;
+         (size_t)np * (2 * sizeof(double) + 2 * sizeof(c128) + 3 * sizeof(int)) + 256;
 }
 
 CoopWork coop_work_carve(void* base, int64_t kmax, int num_sms) {
@@ -489,7 +500,7 @@ void tri_inverse_upper(const S* R, int64_t k, int64_t ld, S* Rinv, int64_t ldi, 
 
 template <typename S>
 void jacobi_eigh(S* H, int64_t k, int64_t ld, S* V, int64_t ldv, double tol, const CoopWork& w, int num_sms,
-                 cudaStream_t s, int max_sweeps) {
+                 cudaStream_t s, int max_sweeps, bool init_v) {
   FEAST_CUDA_TRY(cudaMemsetAsync(w.counter, 0, 256 * 3, s));
   FEAST_CUDA_TRY(cudaMemsetAsync(w.rotcount, 0, sizeof(unsigned) * kMaxSweeps, s));
   FEAST_CUDA_TRY(cudaMemsetAsync(w.roundcount, 0, sizeof(unsigned) * kMaxSweeps * (size_t)(k + 2), s));
@@ -499,8 +510,9 @@ void jacobi_eigh(S* H, int64_t k, int64_t ld, S* V, int64_t ldv, double tol, con
   int P = (int)std::min<int64_t>((int64_t)std::max(1, occ) * num_sms, cdiv(tasks, 256 * 8));
   P = std::max(1, std::min(P, num_sms));
   int maxs = std::max(1, std::min(max_sweeps, kMaxSweeps));
+  int iv = init_v ? 1 : 0;
   CoopWork wl = w;
-  void* args[] = {&H, &k, &ld, &V, &ldv, &tol, &wl, &P, &maxs};
+  void* args[] = {&H, &k, &ld, &V, &ldv, &tol, &wl, &P, &maxs, &iv};
   FEAST_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)jacobi_kernel<S>, dim3(P), dim3(256), args, 0, s));
   note_launch();
 }
@@ -830,8 +842,9 @@ template void convert_matrix<double, float>(double*, int64_t, const float*, int6
 template void convert_matrix<c64, c128>(c64*, int64_t, const c128*, int64_t, int64_t, int64_t, cudaStream_t);
 template void convert_matrix<c128, c64>(c128*, int64_t, const c64*, int64_t, int64_t, int64_t, cudaStream_t);
 template void jacobi_eigh<float>(float*, int64_t, int64_t, float*, int64_t, double, const CoopWork&, int, cudaStream_t,
-                                 int);
-template void jacobi_eigh<c64>(c64*, int64_t, int64_t, c64*, int64_t, double, const CoopWork&, int, cudaStream_t, int);
+                                 int, bool);
+template void jacobi_eigh<c64>(c64*, int64_t, int64_t, c64*, int64_t, double, const CoopWork&, int, cudaStream_t, int,
+                               bool);
 
 int64_t block_jacobi_pad(int64_t k) { return cdiv(k, BJ_B) * BJ_B; }
 size_t block_jacobi_u_bytes(int64_t kmax) {
@@ -872,11 +885,210 @@ template int block_jacobi<float, double>(const double*, int64_t, float*, double,
                                          cudaStream_t);
 template int block_jacobi<c64, c128>(const c128*, int64_t, c64*, double, c64*, c64*, c64*, int*, int, cudaStream_t);
 
+// ---------------------------------------------------------------------------
+// Cluster finish of the FP64 Jacobi.  Once only pairs inside groups of nearly
+// equal diagonal entries still exceed the threshold, a full sweep walks every
+// round (with a grid barrier each) to rotate a few pairs.  Instead, the
+// above-threshold pairs are listed, grouped into connected index sets on the
+// host, and each set's submatrix is diagonalised by cyclic Jacobi in one CTA's
+// shared memory; its unitary then updates the set's columns of V.
+
+// pairs (i < j) with |h_ij| > thr: count in *cnt, the first cap in list
+template <typename S>
+__global__ void offdiag_scan_kernel(const S* H, int64_t k, int64_t ld, double thr2, int* cnt, int* list, int cap) {
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < k * k;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx % k, j = idx / k;
+    if (i < j && abs2(H[i + j * ld]) > thr2) {
+      const int pos = atomicAdd(cnt, 1);
+      if (pos < cap) {
+        list[2 * pos] = (int)i;
+        list[2 * pos + 1] = (int)j;
+      }
+    }
+  }
+}
+
+constexpr int CJ_LD = kClusterMax + 1;
+
+// one CTA per index set c = idx[off[c] .. off[c+1]) (ascending, size <= kClusterMax)
+template <typename S>
+__global__ void __launch_bounds__(256) cluster_jacobi_kernel(S* H, int64_t ld, const int* __restrict__ idx,
+                                                             const int* __restrict__ off, double thr, int max_sweeps,
+                                                             S* __restrict__ Ubuf, int* sweeps_out) {
+  using R = real_t<S>;
+  extern __shared__ unsigned char cj_smem[];
+  S* A = reinterpret_cast<S*>(cj_smem);                 // m x m, row stride CJ_LD
+  S* U = A + kClusterMax * CJ_LD;
+  __shared__ R pc[kClusterMax / 2], ps[kClusterMax / 2];
+  __shared__ S pe[kClusterMax / 2];
+  __shared__ int pon[kClusterMax / 2], pp[kClusterMax / 2], pq[kClusterMax / 2];
+  __shared__ int any;
+  const int c = blockIdx.x, t = threadIdx.x;
+  const int* ix = idx + off[c];
+  const int m = off[c + 1] - off[c];
+  const int mm = m + (m & 1), np = mm / 2, m1 = mm - 1;
+  for (int l = t; l < m * m; l += blockDim.x) {
+    const int i = l % m, j = l / m;
+    A[i * CJ_LD + j] = H[ix[i] + (int64_t)ix[j] * ld];
+    U[i * CJ_LD + j] = i == j ? one<S>() : num<S>::zero();
+  }
+  __syncthreads();
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (t == 0) any = 0;
+    __syncthreads();
+    for (int r = 0; r < m1; ++r) {
+      if (t < np) {
+        int a, b;
+        if (t == 0) { a = r % m1; b = m1; }
+        else { a = (r + t) % m1; b = ((r - t) % m1 + m1) % m1; }
+        const int p = a < b ? a : b, q = a < b ? b : a;
+        R cs = R(1), sn = R(0);
+        S e = one<S>();
+        int on = 0;
+        if (q < m) {
+          const S apq = A[p * CJ_LD + q];
+          const R g = sqrt(abs2(apq));
+          if (g > thr) {
+            const R app = real_part(A[p * CJ_LD + p]), aqq = real_part(A[q * CJ_LD + q]);
+            e = conj(apq) * (R(1) / g);
+            const R tau = (aqq - app) / (R(2) * g);
+            const R tt = (tau >= R(0) ? R(1) : R(-1)) / (fabs(tau) + hypot(R(1), tau));
+            cs = R(1) / hypot(R(1), tt);
+            sn = tt * cs;
+            on = 1;
+            any = 1;
+          }
+        }
+        pc[t] = cs; ps[t] = sn; pe[t] = e; pon[t] = on; pp[t] = p; pq[t] = q;
+      }
+      __syncthreads();
+      // 2 x 2 blocks (rows of pair I, columns of pair J), as in jacobi_kernel
+      for (int task = t; task < np * np; task += blockDim.x) {
+        const int I = task % np, J = task / np;
+        const int onI = pon[I], onJ = pon[J];
+        if (!onI && !onJ) continue;
+        const int pI = pp[I], qI = pq[I], pJ = pp[J], qJ = pq[J];
+        const bool vqI = qI < m, vqJ = qJ < m;
+        S b00 = A[pI * CJ_LD + pJ];
+        S b01 = vqJ ? A[pI * CJ_LD + qJ] : num<S>::zero();
+        S b10 = vqI ? A[qI * CJ_LD + pJ] : num<S>::zero();
+        S b11 = (vqI && vqJ) ? A[qI * CJ_LD + qJ] : num<S>::zero();
+        if (onJ) {
+          const R cs = pc[J], sn = ps[J];
+          const S se = pe[J] * sn, ce = pe[J] * cs;
+          S n00 = b00 * cs - b01 * se, n01 = b00 * sn + b01 * ce;
+          S n10 = b10 * cs - b11 * se, n11 = b10 * sn + b11 * ce;
+          b00 = n00; b01 = n01; b10 = n10; b11 = n11;
+        }
+        if (onI) {
+          const R cs = pc[I], sn = ps[I];
+          const S ec = conj(pe[I]);
+          const S sec = ec * sn, cec = ec * cs;
+          S n00 = b00 * cs - b10 * sec, n10 = b00 * sn + b10 * cec;
+          S n01 = b01 * cs - b11 * sec, n11 = b01 * sn + b11 * cec;
+          b00 = n00; b01 = n01; b10 = n10; b11 = n11;
+        }
+        if (I == J && onI) {
+          b01 = num<S>::zero();
+          b10 = num<S>::zero();
+          b00 = cvt<S>(real_part(b00));
+          b11 = cvt<S>(real_part(b11));
+        }
+        A[pI * CJ_LD + pJ] = b00;
+        if (vqJ) A[pI * CJ_LD + qJ] = b01;
+        if (vqI) A[qI * CJ_LD + pJ] = b10;
+        if (vqI && vqJ) A[qI * CJ_LD + qJ] = b11;
+      }
+      // U <- U G_J for the columns of each rotated pair
+      for (int task = t; task < m * np; task += blockDim.x) {
+        const int row = task % m, J = task / m;
+        if (!pon[J]) continue;
+        const int p = pp[J], q = pq[J];
+        const R cs = pc[J], sn = ps[J];
+        const S e = pe[J];
+        const S a = U[row * CJ_LD + p], b = U[row * CJ_LD + q];
+        U[row * CJ_LD + p] = a * cs - b * (e * sn);
+        U[row * CJ_LD + q] = a * sn + b * (e * cs);
+      }
+      __syncthreads();
+    }
+    const int rotated = any;
+    __syncthreads();
+    if (!rotated) break;
+  }
+  for (int l = t; l < m * m; l += blockDim.x) {
+    const int i = l % m, j = l / m;
+    H[ix[i] + (int64_t)ix[j] * ld] = A[i * CJ_LD + j];
+    Ubuf[(int64_t)c * kClusterMax * kClusterMax + i + (int64_t)j * kClusterMax] = U[i * CJ_LD + j];
+  }
+  if (t == 0) sweeps_out[c] = sweep + (sweep < max_sweeps ? 1 : 0);
+}
+
+// V[rows, set c] <- V[rows, set c] U_c for 64-row chunks (grid nsets x ceil(k / 64))
+template <typename S>
+__global__ void __launch_bounds__(256) cluster_apply_v_kernel(S* V, int64_t k, int64_t ldv, const int* __restrict__ idx,
+                                                              const int* __restrict__ off, const S* __restrict__ Ubuf) {
+  extern __shared__ unsigned char cj_smem[];
+  S* W = reinterpret_cast<S*>(cj_smem);                 // 64 rows x m, row stride CJ_LD
+  S* U = W + 64 * CJ_LD;                                // m x m, row stride CJ_LD
+  const int c = blockIdx.x, t = threadIdx.x;
+  const int* ix = idx + off[c];
+  const int m = off[c + 1] - off[c];
+  const int64_t r0 = (int64_t)blockIdx.y * 64;
+  for (int l = t; l < m * m; l += blockDim.x) {
+    const int i = l % m, j = l / m;
+    U[i * CJ_LD + j] = Ubuf[(int64_t)c * kClusterMax * kClusterMax + i + (int64_t)j * kClusterMax];
+  }
+  for (int l = t; l < 64 * m; l += blockDim.x) {
+    const int rr = l % 64, j = l / 64;
+    W[rr * CJ_LD + j] = (r0 + rr < k) ? V[(r0 + rr) + (int64_t)ix[j] * ldv] : num<S>::zero();
+  }
+  __syncthreads();
+  for (int l = t; l < 64 * m; l += blockDim.x) {
+    const int rr = l % 64, j = l / 64;
+    if (r0 + rr >= k) continue;
+    S acc = num<S>::zero();
+    for (int q = 0; q < m; ++q) acc = acc + W[rr * CJ_LD + q] * U[q * CJ_LD + j];
+    V[(r0 + rr) + (int64_t)ix[j] * ldv] = acc;
+  }
+}
+
+template <typename S>
+void offdiag_scan(const S* H, int64_t k, int64_t ld, double thr, int* cnt, int* list, int cap, cudaStream_t s) {
+  FEAST_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int), s));
+  if (k < 2) return;
+  offdiag_scan_kernel<S><<<grid1d(k * k), 256, 0, s>>>(H, k, ld, thr * thr, cnt, list, cap);
+  FEAST_LAUNCH_CHECK();
+}
+
+template <typename S>
+void cluster_jacobi(S* H, int64_t k, int64_t ld, S* V, int64_t ldv, const int* idx, const int* off, int nsets,
+                    double thr, S* Ubuf, int* sweeps_out, cudaStream_t s) {
+  if (nsets <= 0) return;
+  const int smem = 2 * kClusterMax * CJ_LD * (int)sizeof(S);
+  static bool attr = [] {
+    cudaFuncSetAttribute(cluster_jacobi_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         2 * kClusterMax * CJ_LD * (int)sizeof(S));
+    cudaFuncSetAttribute(cluster_apply_v_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (64 + kClusterMax) * CJ_LD * (int)sizeof(S));
+    return true;
+  }();
+  (void)attr;
+  cluster_jacobi_kernel<S><<<nsets, 256, smem, s>>>(H, ld, idx, off, thr, kMaxSweeps, Ubuf, sweeps_out);
+  FEAST_LAUNCH_CHECK();
+  cluster_apply_v_kernel<S><<<dim3((unsigned)nsets, (unsigned)cdiv(k, 64)), 256,
+                              (64 + kClusterMax) * CJ_LD * (int)sizeof(S), s>>>(V, k, ldv, idx, off, Ubuf);
+  FEAST_LAUNCH_CHECK();
+}
+
 #define INST_S(S)                                                                                          \
   template void hermitize<S>(S*, int64_t, int64_t, cudaStream_t);                                          \
   template void cholesky_upper<S>(S*, int64_t, int64_t, const CoopWork&, int, cudaStream_t);               \
   template void tri_inverse_upper<S>(const S*, int64_t, int64_t, S*, int64_t, cudaStream_t);               \
-  template void jacobi_eigh<S>(S*, int64_t, int64_t, S*, int64_t, double, const CoopWork&, int, cudaStream_t, int); \
+  template void jacobi_eigh<S>(S*, int64_t, int64_t, S*, int64_t, double, const CoopWork&, int, cudaStream_t, int,  \
+                               bool);                                                                     \
   template void get_diag<S>(const S*, int64_t, int64_t, double*, cudaStream_t);                            \
   template void col_norms2<S>(const S*, int64_t, int64_t, int64_t, double*, cudaStream_t);                 \
   template void col_dots_re<S>(const S*, const S*, int64_t, int64_t, int64_t, double*, cudaStream_t);      \
@@ -895,7 +1107,10 @@ template int block_jacobi<c64, c128>(const c128*, int64_t, c64*, double, c64*, c
   template void copy_matrix<S>(S*, int64_t, const S*, int64_t, int64_t, int64_t, cudaStream_t);            \
   template void set_identity<S>(S*, int64_t, int64_t, cudaStream_t);                                       \
   template void set_diag<S>(S*, int64_t, int64_t, const double*, cudaStream_t);                            \
-  template void check_finite<S>(const S*, int64_t, int64_t, int64_t, int*, cudaStream_t);
+  template void check_finite<S>(const S*, int64_t, int64_t, int64_t, int*, cudaStream_t);                  \
+  template void offdiag_scan<S>(const S*, int64_t, int64_t, double, int*, int*, int, cudaStream_t);        \
+  template void cluster_jacobi<S>(S*, int64_t, int64_t, S*, int64_t, const int*, const int*, int, double,  \
+                                  S*, int*, cudaStream_t);
 
 INST_S(double)
 INST_S(c128)

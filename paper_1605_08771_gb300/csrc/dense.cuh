@@ -16,7 +16,7 @@ struct CoopWork {
   double* partial;     // [>= 2*num_sms] partial sums
   unsigned* rotcount;  // [kMaxSweeps] CTAs that rotated in each sweep
   unsigned* roundcount;  // [kMaxSweeps * (kmax + 2)] CTAs that rotated in each round
-  void* rot;           // rotation parameters, >= k/2+1 entries of (c, s, e)
+  void* rot;           // rotation parameters, >= k/2+1 entries of (c, s, e s, e c)
 };
 constexpr int kMaxSweeps = 64;
 size_t coop_work_bytes(int64_t kmax, int num_sms);
@@ -38,10 +38,27 @@ void tri_inverse_upper(const S* R, int64_t k, int64_t ld, S* Rinv, int64_t ldi, 
 // (overwritten by its near-diagonal form); V receives the eigenvectors
 // (unsorted).  Rotations skip |h_pq| <= tol ||H||_F; sweeps stop when a sweep
 // rotates nothing or after max_sweeps.  Sweeps counted in w.info[1].  S may be
-// double, c128 or, for a low-precision first phase, float / c64.
+// double, c128 or, for a low-precision first phase, float / c64.  init_v =
+// false continues from the current H and V (V not reset to the identity).
 template <typename S>
 void jacobi_eigh(S* H, int64_t k, int64_t ld, S* V, int64_t ldv, double tol, const CoopWork& w,
-                 int num_sms, cudaStream_t s, int max_sweeps = kMaxSweeps);
+                 int num_sms, cudaStream_t s, int max_sweeps = kMaxSweeps, bool init_v = true);
+
+// Cluster finish of the FP64 Jacobi.  offdiag_scan lists the pairs i < j with
+// |h_ij| > thr (absolute): *cnt (device) receives their number, list the
+// first cap of them as (i, j).  cluster_jacobi diagonalises, for each of the
+// nsets index sets idx[off[c] .. off[c+1]) (ascending, 2 .. kClusterMax
+// entries, disjoint), the submatrix H[set, set] in place by cyclic Jacobi to
+// the same threshold, and applies its unitary to V[:, set] (V: k x k, ld
+// ldv).  Entries of H between a set and the rest are not updated: the caller
+// ensures they are below thr.  Scratch Ubuf: nsets kClusterMax^2 elements;
+// sweeps_out: nsets ints.
+constexpr int kClusterMax = 64;
+template <typename S>
+void offdiag_scan(const S* H, int64_t k, int64_t ld, double thr, int* cnt, int* list, int cap, cudaStream_t s);
+template <typename S>
+void cluster_jacobi(S* H, int64_t k, int64_t ld, S* V, int64_t ldv, const int* idx, const int* off, int nsets,
+                    double thr, S* Ubuf, int* sweeps_out, cudaStream_t s);
 
 // Low-precision block Jacobi (F = float / c64) on the Hermitian k x k matrix
 // H (FP64, ld k, not modified): block-pair rounds, each pair's 32 x 32

@@ -212,6 +212,15 @@ struct Solver {
   S* Ve = nullptr;
   S* Te = nullptr;
   S* T2e = nullptr;
+  // cluster finish of the FP64 polish: pair list, index sets, their unitaries
+  int* d_ccnt = nullptr;
+  int* d_clist = nullptr;
+  int* d_cidx = nullptr;
+  int* d_coff = nullptr;
+  int* d_csw = nullptr;
+  S* Ucl = nullptr;
+  int64_t ccap = 0;
+  static constexpr int kPolishSweeps = 2;  // full FP64 sweeps before the cluster finish
   // mixed, opts.refine_gemm = 1: double-float planes of A (hi/lo of Re, Im,
   // Re + Im) and of the right-hand block of an A product
   float* Apl = nullptr;
@@ -356,6 +365,13 @@ struct Solver {
       Ubj = (F32*)ctx->arena.alloc(block_jacobi_u_bytes(kmax));
       d_bjrot = dalloc<int>(ctx, 1);
       Ve = dalloc<S>(ctx, kk); Te = dalloc<S>(ctx, kk); T2e = dalloc<S>(ctx, kk);
+      ccap = 32 * kmax;
+      d_ccnt = dalloc<int>(ctx, 1);
+      d_clist = dalloc<int>(ctx, 2 * ccap);
+      d_cidx = dalloc<int>(ctx, kmax);
+      d_coff = dalloc<int>(ctx, kmax / 2 + 2);
+      d_csw = dalloc<int>(ctx, kmax / 2 + 1);
+      Ucl = dalloc<S>(ctx, (kmax / 2 + 1) * kClusterMax * kClusterMax);
     }
     part_elems = 32 * kk;
     part = dalloc<S>(ctx, part_elems);
@@ -749,22 +765,113 @@ struct Solver {
       hermitize<S>(H, k, k, st);
     });
     int sw64 = 0;
-    phase("eig: FP64 Jacobi", [&] {
-      jacobi_eigh<S>(H, k, k, T2e, k, 1e-15, cw, ctx->num_sms, st);
-      jacobi_status(&sw64);
-      if (std::getenv("FEAST_LOG")) {
-        std::vector<unsigned> rc(sw64 > 0 ? sw64 : 1);
-        to_host(ctx, rc.data(), cw.rotcount, rc.size());
-        fprintf(stderr, "[feast] FP64 Jacobi k=%lld rotations per sweep:", (long long)k);
-        for (unsigned v : rc) fprintf(stderr, " %u", v);
-        fprintf(stderr, "\n");
-      }
-    });
+    phase("eig: FP64 Jacobi", [&] { sw64 = polish(H, k); });
     phase("eig: V V'", [&] { mm_square(k, Te, OP_N, T2e, Vk); });
     *sweeps = sw32 + sw64;
     if (std::getenv("FEAST_LOG"))
       fprintf(stderr, "[feast] two-phase eig k=%lld: %d FP32 + %d FP64 sweeps\n", (long long)k, sw32, sw64);
     return true;
+  }
+  // FP64 Jacobi polish of the nearly diagonal k x k matrix H (ld k), vectors
+  // into T2e: kPolishSweeps full sweeps, then while some off-diagonal entry
+  // exceeds the threshold (1e-15 ||H||_F) and the entries that do link only
+  // small index sets (at most kClusterMax, the groups of nearly equal diagonal
+  // entries), each set is finished in shared memory (cluster_jacobi) instead
+  // of by further sweeps, which would walk all k - 1 rounds to rotate a few
+  // pairs.  Otherwise one more full sweep.  Returns the full sweeps taken.
+  int polish(S* H, int64_t k) {
+    const bool log = std::getenv("FEAST_LOG") != nullptr;
+    int sweeps = 0, s1 = 0;
+    jacobi_eigh<S>(H, k, k, T2e, k, 1e-15, cw, ctx->num_sms, st, kPolishSweeps, true);
+    jacobi_status(&s1);
+    sweeps += s1;
+    if (!d_ccnt) {
+      if (s1 >= kPolishSweeps) {
+        jacobi_eigh<S>(H, k, k, T2e, k, 1e-15, cw, ctx->num_sms, st, kMaxSweeps, false);
+        jacobi_status(&s1);
+        sweeps += s1;
+      }
+      return sweeps;
+    }
+    std::vector<double> cn(k);
+    col_norms2<S>(H, k, k, k, d_nrm, st);
+    to_host(ctx, cn.data(), d_nrm, k);
+    double fro2 = 0.0;
+    for (double v : cn) fro2 += v;
+    const double thr = 1e-15 * std::sqrt(fro2);
+    std::vector<int> parent(k), list, setidx, setoff, swc;
+    for (int pass = 0; pass < 16; ++pass) {
+      // a hair above the kernels' threshold, so that a pair the scan reports
+      // is one the Jacobi kernels rotate
+      offdiag_scan<S>(H, k, k, thr * (1.0 + 1e-6), d_ccnt, d_clist, (int)ccap, st);
+      int cnt = 0;
+      to_host(ctx, &cnt, d_ccnt, 1);
+      if (cnt == 0) return sweeps;
+      bool sets_ok = cnt <= ccap;
+      int nsets = 0, maxset = 0;
+      if (sets_ok) {
+        list.resize(2 * (size_t)cnt);
+        to_host(ctx, list.data(), d_clist, 2 * (int64_t)cnt);
+        std::iota(parent.begin(), parent.end(), 0);
+        auto find = [&](int x) {
+          while (parent[x] != x) x = parent[x] = parent[parent[x]];
+          return x;
+        };
+        for (int e = 0; e < cnt; ++e) {
+          const int a = find(list[2 * e]), b = find(list[2 * e + 1]);
+          if (a != b) parent[std::max(a, b)] = std::min(a, b);
+        }
+        // members of each set in ascending index order
+        std::vector<int> root_of(k, -1), count;
+        std::vector<char> used(k, 0);
+        for (int e = 0; e < 2 * cnt; ++e) used[list[e]] = 1;
+        std::vector<int> setid(k, -1);
+        for (int64_t i = 0; i < k; ++i)
+          if (used[i]) {
+            const int r = find((int)i);
+            if (root_of[r] < 0) {
+              root_of[r] = nsets++;
+              count.push_back(0);
+            }
+            setid[i] = root_of[r];
+            ++count[setid[i]];
+          }
+        setoff.assign(nsets + 1, 0);
+        for (int c = 0; c < nsets; ++c) {
+          setoff[c + 1] = setoff[c] + count[c];
+          maxset = std::max(maxset, count[c]);
+        }
+        sets_ok = maxset <= kClusterMax;
+        if (sets_ok) {
+          setidx.assign(setoff[nsets], 0);
+          std::vector<int> fill(setoff.begin(), setoff.end() - 1);
+          for (int64_t i = 0; i < k; ++i)
+            if (setid[i] >= 0) setidx[fill[setid[i]]++] = (int)i;
+        }
+      }
+      if (log)
+        fprintf(stderr, "[feast] FP64 polish k=%lld pass %d: %d pairs above threshold, %d sets, largest %d%s\n",
+                (long long)k, pass, cnt, nsets, maxset, sets_ok ? "" : " -> full sweep");
+      if (sets_ok) {
+        to_dev(ctx, d_cidx, setidx.data(), (int64_t)setidx.size());
+        to_dev(ctx, d_coff, setoff.data(), (int64_t)nsets + 1);
+        cluster_jacobi<S>(H, k, k, T2e, k, d_cidx, d_coff, nsets, thr, Ucl, d_csw, st);
+        if (log) {
+          swc.resize(nsets);
+          to_host(ctx, swc.data(), d_csw, nsets);
+          fprintf(stderr, "[feast] FP64 polish k=%lld: set sweeps max %d\n", (long long)k,
+                  *std::max_element(swc.begin(), swc.end()));
+        }
+      } else {
+        jacobi_eigh<S>(H, k, k, T2e, k, 1e-15, cw, ctx->num_sms, st, 1, false);
+        jacobi_status(&s1);
+        sweeps += s1;
+      }
+    }
+    // still not below the threshold: finish with full sweeps
+    jacobi_eigh<S>(H, k, k, T2e, k, 1e-15, cw, ctx->num_sms, st, kMaxSweeps, false);
+    jacobi_status(&s1);
+    return sweeps + s1;
   }
   void eig(S* H, int64_t k, std::vector<double>& ev) {
     const bool log = std::getenv("FEAST_LOG") != nullptr;

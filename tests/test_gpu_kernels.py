@@ -92,6 +92,41 @@ def test_jacobi_matches_lapack(ctx, k, cplx):
     assert sweeps < 30
 
 
+@pytest.mark.parametrize("big_group", [False, True])
+@pytest.mark.parametrize("cplx", [False, True])
+def test_two_phase_eigensolver_cluster_finish(ctx, cplx, big_group, capfd, monkeypatch):
+    # Rayleigh-Ritz on an invariant subspace whose eigenvalues come in groups
+    # 1e-9 apart: after the first full FP64 sweeps of the two-phase reduced
+    # eigensolver only pairs inside the groups exceed the threshold, and each
+    # group is finished in shared memory; a group larger than the set limit
+    # (64) falls back to full sweeps
+    monkeypatch.setenv("FEAST_LOG", "1")
+    n, k = 320, 200
+    rng = np.random.default_rng(41 + 2 * cplx + big_group)
+    lam = rng.uniform(-10.0, 10.0, n)
+    start = 0
+    for size in [2, 3, 5, 8, 13, 21, 40] + ([70] if big_group else []):
+        lam[start:start + size] = lam[start] + 1e-9 * rng.standard_normal(size)
+        start += size
+    Qp, _ = np.linalg.qr(rand_mat(n, n, cplx, seed=77 + big_group))
+    A = (Qp * lam[None, :]) @ Qp.conj().T
+    A = np.asfortranarray(0.5 * (A + A.conj().T))
+    Rk, _ = np.linalg.qr(rand_mat(k, k, cplx, seed=78 + big_group))
+    Q0 = np.asfortranarray(Qp[:, :k] @ Rk)
+    anorm = np.abs(lam).max()
+    ev, X, res = fg.feast_rayleigh_ritz(ctx, cuda(A), cuda(Q0), anorm)
+    X = host(X)
+    np.testing.assert_allclose(ev, np.sort(lam[:k]), atol=1e-13 * anorm)
+    np.testing.assert_allclose(X.conj().T @ X, np.eye(k), atol=1e-12)
+    assert res.max() <= 1e-12
+    log = capfd.readouterr().err
+    passes = [l for l in log.splitlines() if "FP64 polish" in l and "pass" in l]
+    if big_group:
+        assert any("full sweep" in l for l in passes), log[-3000:]
+    else:
+        assert any("full sweep" not in l for l in passes), log[-3000:]
+
+
 @pytest.mark.parametrize("cplx", [False, True])
 @pytest.mark.parametrize("method", [0, 1])
 def test_orthonormalize(ctx, cplx, method):
