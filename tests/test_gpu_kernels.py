@@ -60,6 +60,23 @@ def test_shifted_solve_matches_oracle(ctx, n, cplx, adjoint, prec):
         assert np.abs(Y[e] - ref).max() <= tol * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_shifted_solve_complex_fp32_large_n(ctx, adjoint):
+    # n = 1100: 17 full 64-row diagonal blocks and a ragged one, each followed
+    # by a block update of every remaining row; the reference is LAPACK's
+    # FP64 solve of each shifted system
+    n = 1100
+    A = np.asfortranarray(0.1 * rand_hermitian(n, True, seed=5))  # spectrum within about +-5
+    B = rand_mat(n, 7, True, seed=6)
+    prec = fg.FEAST_PREC_MIXED
+    LU, perm = fg.feast_shifted_lu(ctx, cuda(A), ZS, prec)
+    Y = host(fg.feast_shifted_solve(ctx, LU, perm, cuda(B), adjoint=adjoint, prec=prec))
+    for e, z in enumerate(ZS):
+        Mz = z * np.eye(n) - A
+        ref = np.linalg.solve(Mz.conj().T if adjoint else Mz, B)
+        assert np.abs(Y[e] - ref).max() <= 2e-4 * np.abs(ref).max()
+
+
 @pytest.mark.parametrize("cplx", [False, True])
 @pytest.mark.parametrize("prec", PRECS_ALL)
 @pytest.mark.parametrize("n_c", [3, 8])
