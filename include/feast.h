@@ -112,6 +112,9 @@ typedef struct {
                            triangular-solve block updates) */
   double cgemm_ms;      /* their summed device time (CUDA events) */
   double cgemm_flop;    /* their real flops (8 per complex multiply-add) */
+  int rr_passes;        /* Rayleigh-Ritz passes (reduced eigenproblems solved) */
+  double rr_k_sum;      /* sum of their dimensions k */
+  double rr_k3_sum;     /* sum of k^3 */
 } feast_stats;
 
 void feast_opts_default(feast_opts* opts);

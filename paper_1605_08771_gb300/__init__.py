@@ -50,7 +50,8 @@ class FeastStats(ctypes.Structure):
                 ("total_ms", ctypes.c_double), ("max_residual", ctypes.c_double),
                 ("history", ctypes.c_double * 128), ("refine_gemm_ms", ctypes.c_double),
                 ("refine_gemm_mac", ctypes.c_double), ("refine_gemm_launches", ctypes.c_int),
-                ("cgemm_launches", ctypes.c_int), ("cgemm_ms", ctypes.c_double), ("cgemm_flop", ctypes.c_double)]
+                ("cgemm_launches", ctypes.c_int), ("cgemm_ms", ctypes.c_double), ("cgemm_flop", ctypes.c_double),
+                ("rr_passes", ctypes.c_int), ("rr_k_sum", ctypes.c_double), ("rr_k3_sum", ctypes.c_double)]
 
 
 class FeastError(RuntimeError):

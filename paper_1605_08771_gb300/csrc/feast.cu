@@ -199,6 +199,8 @@ struct Solver {
   double* d_en = nullptr;
   int* d_act = nullptr;
   int refine_steps = 0;
+  int rr_passes = 0;  // Rayleigh-Ritz passes and the sums of their k and k^3
+  double rr_k_sum = 0.0, rr_k3_sum = 0.0;
   bool refine_now = true;      // mixed: refine the next filter application
   // two-phase reduced eigensolver scratch (FP32 Jacobi, FP64 polish)
   using F32 = typename std::conditional<std::is_same<S, c128>::value, c64, float>::type;
@@ -934,6 +936,9 @@ struct Solver {
   }
   // diagonalise A'[0:k, 0:k]: lam (ascending), Xr = Q V, AXr = W V, res
   void rr_solve(int64_t k) {
+    ++rr_passes;
+    rr_k_sum += (double)k;
+    rr_k3_sum += (double)k * (double)k * (double)k;
     copy_matrix<S>(Ar, k, Ar0, kmax, k, k, st);
     std::vector<double> ev;
     phase("Jacobi (RR)", [&] { eig(Ar, k, ev); });
@@ -1390,6 +1395,9 @@ int solve_t(feast_ctx* ctx, const S* A, int64_t n, int64_t lda, double lmin, dou
   st.filters = out.filters;
   st.refine_steps = sv.refine_steps;
   st.m_expected = out.m_expected;
+  st.rr_passes = sv.rr_passes;
+  st.rr_k_sum = sv.rr_k_sum;
+  st.rr_k3_sum = sv.rr_k3_sum;
   st.factor_ms = tf1 - tf0;
   st.filter_ms = sv.filter_ms;
   kernel_timer_end(TIMER_REFINE_GEMM, &st.refine_gemm_ms, &st.refine_gemm_mac, &st.refine_gemm_launches);
