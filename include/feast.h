@@ -45,7 +45,9 @@ enum { FEAST_R64 = 0, /* real symmetric, double */
 /* iteration variant */
 enum { FEAST_PLAIN = 0,  /* FEAST Algorithm (Appendix) */
        FEAST_XFEAST = 1, /* expanding subspace from previous filtered blocks (Sect. II-A) */
-       FEAST_RFEAST = 2  /* expanding subspace with Ritz residuals (Sect. II-B) */ };
+       FEAST_RFEAST = 2  /* expanding subspace with Ritz residuals (Sect. II-B); only the
+                            selected pairs whose relative residual is still above tol expand
+                            it (a converged pair's residual is rounding noise) */ };
 
 /* arithmetic of the shifted factorisations and solves */
 enum { FEAST_PREC_F64 = 0,      /* complex FP64 LU and solves */
