@@ -82,6 +82,13 @@ def test_edge_clustered_complex_rfeast(ctx, prec):
                                   x0=cuda(X0))
     assert out["status"] == 0
     check_against_planted(out, P)
+    # the Rayleigh-Ritz passes: at least one and at most s = 3 per round,
+    # none larger than s m0 = 72
+    st = out["stats"]
+    assert out["iterations"] <= st.rr_passes <= 3 * out["iterations"]
+    assert st.rr_passes <= st.rr_k_sum <= 72 * st.rr_passes
+    assert st.rr_k_sum ** 3 / st.rr_passes ** 2 <= st.rr_k3_sum * (1 + 1e-12)
+    assert st.rr_k3_sum <= st.rr_passes * 72.0 ** 3
 
 
 def test_internal_random_start_and_norm_estimate(ctx):
