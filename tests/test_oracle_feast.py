@@ -179,3 +179,19 @@ def test_rfeast_expansion_is_robust_to_rounding_noise():
     assert noisy.iterations <= clean.iterations
     np.testing.assert_allclose(noisy.lam, P.inside, rtol=1e-9, atol=1e-11 * P.anorm)
     assert noisy.res.max() <= 1e-10
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_ritz_residuals_orthogonal_to_ritz_vectors(cplx):
+    # Sect. II-B: for Rayleigh-Ritz on an orthonormal basis, x_j^H r_k = 0 for
+    # all Ritz vectors x_j and residuals r_k = A x_k - lambda_k x_k, which is
+    # why RFEAST can append R without orthogonalising it against X in exact
+    # arithmetic; here the basis is a random (not invariant) subspace
+    P = small_problem(n=120, m_in=10, cplx=cplx, m0=16)
+    Q, _ = np.linalg.qr(random_subspace(P.n, 16, seed=4, complex_=cplx))
+    rp = O.rayleigh_ritz(P.A, Q, P.anorm)
+    R = rp.AX - rp.X * rp.lam[None, :]
+    assert np.linalg.norm(R) > 1e-3 * P.anorm          # not an invariant subspace
+    assert np.abs(rp.X.conj().T @ R).max() <= 1e-12 * P.anorm
+    # and the residual norms the oracle reports are those of R
+    np.testing.assert_allclose(rp.res, np.linalg.norm(R, axis=0) / P.anorm, rtol=1e-12)
