@@ -50,9 +50,10 @@ void jacobi_eigh(S* H, int64_t k, int64_t ld, S* V, int64_t ldv, double tol, con
 // nsets index sets idx[off[c] .. off[c+1]) (ascending, 2 .. kClusterMax
 // entries, disjoint), the submatrix H[set, set] in place by cyclic Jacobi to
 // the same threshold, and applies its unitary to V[:, set] (V: k x k, ld
-// ldv).  Entries of H between a set and the rest are not updated: the caller
-// ensures they are below thr.  Scratch Ubuf: nsets kClusterMax^2 elements;
-// sweeps_out: nsets ints.
+// ldv).  Entries of H between a set and the rest are left as they are: they
+// were at most thr when the sets were formed, and the set's rotation could
+// make the true ones (not stored) up to sqrt(set size) times larger.  Scratch
+// Ubuf: nsets kClusterMax^2 elements; sweeps_out: nsets ints (sweeps taken).
 constexpr int kClusterMax = 64;
 template <typename S>
 void offdiag_scan(const S* H, int64_t k, int64_t ld, double thr, int* cnt, int* list, int cap, cudaStream_t s);
