@@ -3,9 +3,11 @@
 // The driver follows the paper's Appendix: FEAST (filter, Rayleigh-Ritz,
 // check), XFEAST (window of s filtered blocks, Sect. II-A) and RFEAST (s
 // Rayleigh-Ritz passes expanding with Ritz residuals, Sect. II-B).  All
-// arithmetic runs in the CUDA kernels of factor.cu, gemm.cu and dense.cu; the
-// host only sequences launches, reads back the k Ritz values and residuals
-// it needs for the selection and stopping decisions, and sorts them.
+// arithmetic runs in the CUDA kernels of factor.cu, gemm.cu, oz_gemm.cu,
+// tc_update.cu and dense.cu; the host only sequences launches, reads back the
+// k Ritz values and residuals it needs for the selection and stopping
+// decisions and sorts them, and groups the FP64 polish's remaining
+// above-threshold pairs into index sets.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
