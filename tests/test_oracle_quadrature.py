@@ -87,3 +87,24 @@ def test_planted_mistake_in_weights_is_caught(monkeypatch):
     monkeypatch.setattr(quad, "contour_nodes", wrong)
     z, w = quad.contour_nodes(-1.0, 1.0, 8)
     assert abs(rational_filter(0.0, z, w) - 1.0) > 0.5
+
+
+@pytest.mark.parametrize("n_c", [2, 4, 8, 16])
+def test_filter_above_half_exactly_inside_the_circle(n_c):
+    # the XFEAST/RFEAST filter-response test keeps a pair inside I only if
+    # mu = x^H rho(A) x exceeds 1/2; that separates I from its complement
+    # because, for the circle, rho(lambda) > 1/2 strictly inside I and < 1/2
+    # outside (with rho = 1/2 at the edges): checked on a dense grid, up to
+    # 1e-6 of the half-width from each edge
+    lmin, lmax = -1.0, 1.0
+    z, w = contour_nodes(lmin, lmax, n_c)
+    inside = np.linspace(lmin + 1e-6, lmax - 1e-6, 20001)
+    outside = np.concatenate([np.linspace(lmax + 1e-6, 60.0, 20001), np.linspace(-60.0, lmin - 1e-6, 20001)])
+    assert np.all(rational_filter(inside, z, w) > 0.5)
+    assert np.all(rational_filter(outside, z, w) < 0.5)
+    # and a mixture of eigenvectors from outside I responds below 1/2
+    rng = np.random.default_rng(n_c)
+    c = rng.standard_normal(40) + 1j * rng.standard_normal(40)
+    c /= np.linalg.norm(c)
+    lam_out = rng.choice(outside, 40)
+    assert np.sum(np.abs(c) ** 2 * rational_filter(lam_out, z, w)) < 0.5
