@@ -195,3 +195,24 @@ def test_ritz_residuals_orthogonal_to_ritz_vectors(cplx):
     assert np.abs(rp.X.conj().T @ R).max() <= 1e-12 * P.anorm
     # and the residual norms the oracle reports are those of R
     np.testing.assert_allclose(rp.res, np.linalg.norm(R, axis=0) / P.anorm, rtol=1e-12)
+
+
+@pytest.mark.parametrize("variant", [O.PLAIN, O.XFEAST, O.RFEAST])
+def test_invariant_start_converges_in_one_round(variant):
+    # X0 spanning an invariant subspace that holds every eigenvector with
+    # lambda in I: the filter keeps the span, the first Rayleigh-Ritz pass
+    # returns the planted eigenvalues exactly, so every variant stops after
+    # one round with all m pairs (RFEAST's expected count m is exact too)
+    P = small_problem(n=100, m_in=8, cplx=True, m0=12)
+    ins = np.where(inside(P.lam, P.lmin, P.lmax))[0]
+    outs = np.argsort(np.abs(P.lam - 0.5 * (P.lmin + P.lmax)))
+    outs = [i for i in outs if i not in set(ins)][:P.m0 - ins.size]
+    B = P.Q[:, np.concatenate([ins, outs])]
+    R, _ = np.linalg.qr(random_subspace(P.m0, P.m0, seed=3, complex_=True))
+    X0 = np.asfortranarray(B @ R)
+    r = O.feast_solve(P.A, P.lmin, P.lmax, P.m0, 8, 1e-10, X0, variant=variant, anorm=P.anorm)
+    assert r.status == 0 and r.iterations == 1
+    np.testing.assert_allclose(r.lam, P.inside, atol=1e-13 * P.anorm)
+    assert r.res.max() < 1e-13
+    if variant == O.RFEAST:
+        assert r.m_expected == ins.size
