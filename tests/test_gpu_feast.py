@@ -132,3 +132,24 @@ def test_errors(ctx):
     with pytest.raises(fg.FeastError) as e:
         fg.feast_interval_solve(ctx, cuda(B), -1.0, 1.0, 4, 8, 1e-10)
     assert e.value.code == -2
+
+
+@pytest.mark.parametrize("vname,vor", VARIANTS)
+@pytest.mark.parametrize("prec", ["f64", "mixed"])
+def test_invariant_start_converges_in_one_round(ctx, vname, vor, prec):
+    # X0 spanning an invariant subspace that holds every eigenvector inside I:
+    # one round for every variant, as in the oracle, with RFEAST's expected
+    # count exact
+    lam, a, b = spectrum_uniform(100, 8, seed=3, bulk=10.0)
+    P = make_problem("inv", lam, a, b, 12, 8, seed=3, complex_=True)
+    ins = np.where((P.lam > a) & (P.lam < b))[0]
+    outs = [i for i in np.argsort(np.abs(P.lam - 0.5 * (a + b))) if i not in set(ins)][:P.m0 - ins.size]
+    R, _ = np.linalg.qr(random_subspace(P.m0, P.m0, seed=3, complex_=True))
+    X0 = np.asfortranarray(P.Q[:, np.concatenate([ins, outs])] @ R)
+    out = fg.feast_interval_solve(ctx, cuda(P.A), a, b, P.m0, 8, 1e-10,
+                                  fg.feast_opts_default(variant=vname, prec=prec, anorm=P.anorm), x0=cuda(X0))
+    ref = O.feast_solve(P.A, a, b, P.m0, 8, 1e-10, X0, variant=vor, anorm=P.anorm)
+    assert out["status"] == 0 and out["iterations"] == 1 == ref.iterations
+    check_against_planted(out, P)
+    if vname == "rfeast":
+        assert out["stats"].m_expected == ins.size == ref.m_expected
