@@ -12,6 +12,7 @@ from .planted import (  # noqa: F401
     random_subspace,
     spectrum_config1,
     spectrum_config2,
+    spectrum_config3,
     spectrum_paper,
     spectrum_uniform,
     make_problem,

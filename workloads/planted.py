@@ -123,6 +123,30 @@ def spectrum_config2(seed=0, n=8192, m_in=200, edge_in=30, edge_out=60,
     return lam, -1.0, 1.0
 
 
+def spectrum_config3(seed):
+    """One problem of the batched workload (64 independent real symmetric
+    problems, seeds 0..63): n uniform in 512..4096, m uniform in 10..170
+    eigenvalues inside the problem's own interval, an edge cluster of 2..20
+    eigenvalues per edge within 1e-3 of it, half of each cluster inside and half
+    outside (the reading of the unspecified cluster side), the rest uniform
+    over an outer range 10x the interval's half-width; m0 = ceil(1.5 m),
+    n_c = 8 or 16.  Returns (lam, lmin, lmax, m0, n_c)."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 3]))
+    n = int(rng.integers(512, 4097))
+    m = int(rng.integers(10, 171))
+    cl = int(rng.integers(2, 21))
+    c_in = min(cl // 2, m // 2)
+    c_out = cl - cl // 2
+    c = float(rng.uniform(-5.0, 5.0))
+    r = float(rng.uniform(0.5, 2.0))
+    lmin, lmax = c - r, c + r
+    lam = spectrum_edge_clusters(rng, n, m, lmin, lmax, c - 10.0 * r, c + 10.0 * r,
+                                 n_edge_in=c_in, n_edge_out=c_out, width=1e-3 * r)
+    m0 = int(np.ceil(1.5 * m))
+    n_c = int(rng.choice([8, 16]))
+    return lam, lmin, lmax, m0, n_c
+
+
 def spectrum_paper(kind, seed=0, n=545, m_in=50):
     """The two n = 545 spectra of the paper's Sect. III experiments: 50
     eigenvalues in I = [-1, 1]; the other 495 in [1.01, 20.81] ("Sparse") or
