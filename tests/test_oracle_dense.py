@@ -142,3 +142,21 @@ def test_block_qr_orth_keeps_small_but_resolved_directions():
         assert np.linalg.norm(Q @ (Q.conj().T @ B) - B) < 1e-12 * np.linalg.norm(B)
     # the Gram route of the whole window cannot see those directions
     assert gram_eig_orth(np.hstack(blocks)).shape[1] == 10
+
+
+def test_lu_pivot_ties_take_the_first_row():
+    # reading R11: the pivot is the first row of largest |m_ik|^2; here every
+    # candidate of column 0 ties in magnitude (with different phases), so the
+    # first step keeps row 0; a real 2 x 2 tie does the same
+    M = np.array([[1.0, 2.0, 0.5],
+                  [1j, 3.0, 1.0],
+                  [-1.0, 1.0, 2.0]], dtype=complex)
+    LU, piv = lu_factor(M)
+    assert int(piv[0]) == 0
+    # after step 1 the column-1 entries of rows 1 and 2 are 3 - 2j and 3: |3 - 2j| > 3
+    assert int(piv[1]) == 1
+    T = np.array([[2.0, 0.0], [2.0, 1.0]], dtype=complex)   # exact tie in column 0
+    LU2, piv2 = lu_factor(T)
+    assert int(piv2[0]) == 0
+    P, L, U = lu_unpack(LU2, piv2)
+    np.testing.assert_allclose(P @ T, L @ U, atol=1e-15)
