@@ -16,9 +16,12 @@ Modules:
 
 Parity pins: every function is checked in tests/test_oracle_*.py against
 closed forms, brute force or independent library routines.  The XFEAST and
-RFEAST iterates (which pairs are selected at each round, the residual
-histories) have no independent pin beyond the end result on planted spectra:
-their parity is "parity unpinned" beyond that end result.
+RFEAST drivers are pinned by the end result on planted spectra, by one-round
+convergence where the mathematics fixes it (an invariant start; an expanded
+subspace that spans the whole space, s m0 = n), and by the Rayleigh-Ritz
+dimensions the literal RFEAST expansion must produce.  Their iterates beyond
+that (which pairs are selected at each round of a multi-round solve, the
+residual histories) have no independent pin: "parity unpinned" there.
 """
 from .quadrature import gauss_legendre, contour_nodes, rational_filter  # noqa: F401
 from .dense import (lu_factor, lu_solve, lu_solve_adjoint, lu_unpack,  # noqa: F401
@@ -26,5 +29,5 @@ from .dense import (lu_factor, lu_solve, lu_solve_adjoint, lu_unpack,  # noqa: F
                     round_robin_pairs, solve_right_upper, CholeskyBreakdown)
 from .feast import (factor_shifts, filter_apply, rayleigh_ritz, select_pairs,  # noqa: F401
                     feast_solve, norm_estimate, orthonormalize, FeastResult,
-                    PLAIN, XFEAST, RFEAST)
+                    PLAIN, XFEAST, RFEAST, EXPAND_ALL, EXPAND_UNCONVERGED)
 from .exact import two_prod, dot_exact, matmul_entries  # noqa: F401

@@ -30,18 +30,27 @@ Readings where the paper is silent (each also recorded in the design notes):
     orthogonalises the window with a block QR (Sect. II-A allows QR or the SVD;
     the Gram matrix of the whole window cannot resolve directions below
     sqrt(eps), which loses the expansion once the iterates agree to ~1e-6);
-  * spurious pairs: on spectra with eigenvalues on both sides of I, mixtures
-    of outside eigenvectors give Ritz values inside I that never converge and
-    (with m0 below the number of eigenvalues near |rho| = 1/2) also inflate
-    RFEAST's first-pass count.  Besides the paper's checks, XFEAST and RFEAST
-    therefore also stop when every selected in-I pair whose filter response
-    mu_k = Re(x_k^H rho(A) x_k) exceeds 1/2 has converged; mu_k is read off
-    the filter application the next step performs anyway (rho > 1/2 exactly
-    inside I for the circle contour, rho < 1/2 outside, so a mixture of
-    outside eigenvectors has mu < 1/2); the pairs returned are those;
-  * RFEAST normalises the residual columns, removes their (rounding-level)
-    component along the current basis twice, orthonormalises them and appends
-    them; the append after the last pass is dropped because nothing uses it;
+  * the RFEAST expansion appends R = A X - X Lambda for every selected pair,
+    as step 2(iii) of the RFEAST Algorithm says (expand="all", the default);
+    the columns of R are normalised, their (rounding-level) component along
+    the current basis is removed twice, and they are orthonormalised before
+    the append (same span as [X' R]); the append after the last pass is
+    dropped because nothing uses it;
+  * option expand="unconverged" (a reading, not the paper's text): only the
+    selected pairs whose relative residual is still above tol expand the
+    subspace, and the passes end once every selected pair has converged; a
+    converged pair's residual is rounding noise, whose normalised direction
+    adds spurious Ritz pairs (Sect. II-B reports them) but no information;
+  * option response_stop=True (a reading, not the paper's text): on spectra
+    with eigenvalues on both sides of I, mixtures of outside eigenvectors give
+    Ritz values inside I that never converge and (with m0 below the number
+    of eigenvalues near |rho| = 1/2) also inflate RFEAST's first-pass count.
+    XFEAST and RFEAST then also stop when every selected in-I pair whose
+    filter response mu_k = Re(x_k^H rho(A) x_k) exceeds 1/2 has converged;
+    mu_k is read off the filter application the next step performs anyway
+    (rho > 1/2 exactly inside I for the circle contour, rho < 1/2 outside, so
+    a mixture of outside eigenvectors has mu < 1/2); the pairs returned are
+    those.  Off by default: the paper's checks (step 3) alone decide;
   * selection ties are broken by ascending eigenvalue; with more than m0 pairs
     inside I the m0 of lowest residual are kept;
   * ||A||_2 is the caller's value when given, else 40 power iterations from the
@@ -60,6 +69,7 @@ from .dense import (CholeskyBreakdown, block_qr_orth, cholqr2, gram_eig_orth, ja
 from .quadrature import contour_nodes
 
 PLAIN, XFEAST, RFEAST = "feast", "xfeast", "rfeast"
+EXPAND_ALL, EXPAND_UNCONVERGED = "all", "unconverged"
 
 
 # --------------------------------------------------------------------------
@@ -187,6 +197,7 @@ class FeastResult:
     filters: int                # applications of rho(A) (n_c * m0 solves each)
     history: list = field(default_factory=list)   # max residual per round
     m_expected: int | None = None
+    rr_dims: list = field(default_factory=list)   # dimension of every Rayleigh-Ritz pass
 
 
 def _check(lam, res, sel, lmin, lmax):
@@ -196,9 +207,17 @@ def _check(lam, res, sel, lmin, lmax):
 
 
 def feast_solve(A, lmin, lmax, m0, n_c, tol, X0, variant=PLAIN, s=3,
-                max_iter=100, aspect=1.0, anorm=None, factors=None):
+                max_iter=100, aspect=1.0, anorm=None, factors=None,
+                expand=EXPAND_ALL, response_stop=False):
     """Eigenpairs of Hermitian A with eigenvalues in the open interval
-    (lmin, lmax), by FEAST / XFEAST / RFEAST (Appendix)."""
+    (lmin, lmax), by FEAST / XFEAST / RFEAST (Appendix).
+
+    expand: RFEAST residual columns appended at step 2(iii): "all" selected
+    pairs (the paper) or only the "unconverged" ones (a reading).
+    response_stop: XFEAST/RFEAST also stop on converged non-spurious pairs
+    by filter response (a reading; off = the paper's checks only)."""
+    if expand not in (EXPAND_ALL, EXPAND_UNCONVERGED):
+        raise ValueError(expand)
     A = np.asarray(A)
     if anorm is None or anorm <= 0:
         anorm = norm_estimate(A)
@@ -206,38 +225,39 @@ def feast_solve(A, lmin, lmax, m0, n_c, tol, X0, variant=PLAIN, s=3,
     if variant == PLAIN:
         return _feast(A, F, lmin, lmax, m0, tol, X0, max_iter, anorm)
     if variant == XFEAST:
-        return _xfeast(A, F, lmin, lmax, m0, tol, X0, s, max_iter, anorm)
+        return _xfeast(A, F, lmin, lmax, m0, tol, X0, s, max_iter, anorm, response_stop)
     if variant == RFEAST:
-        return _rfeast(A, F, lmin, lmax, m0, tol, X0, s, max_iter, anorm)
+        return _rfeast(A, F, lmin, lmax, m0, tol, X0, s, max_iter, anorm, expand, response_stop)
     raise ValueError(variant)
 
 
-def _result(status, rp, idx, it, filters, hist, m_expected=None):
+def _result(status, rp, idx, it, filters, hist, m_expected=None, dims=None):
     order = np.argsort(rp.lam[idx], kind="stable")
     idx = idx[order]
     return FeastResult(status=status, lam=rp.lam[idx].copy(), X=rp.X[:, idx].copy(),
                        res=rp.res[idx].copy(), iterations=it, filters=filters,
-                       history=hist, m_expected=m_expected)
+                       history=hist, m_expected=m_expected, rr_dims=list(dims or []))
 
 
 def _feast(A, F, lmin, lmax, m0, tol, X0, max_iter, anorm):
     X = np.array(X0, copy=True)
-    hist = []
+    hist, dims = [], []
     rp = None
     for it in range(1, max_iter + 1):
         Xf = filter_apply(F, X)                         # step 1
         Q, _ = orthonormalize(Xf)                       # B' = I
+        dims.append(Q.shape[1])
         rp = rayleigh_ritz(A, Q, anorm)                 # step 2(i)
         X = rp.X                                        # step 2(ii)
         sel = np.arange(rp.lam.size)
         ins, r = _check(rp.lam, rp.res, sel, lmin, lmax)   # step 3
         hist.append(r)
         if ins.size and r <= tol:
-            return _result(0, rp, ins, it, it, hist)
+            return _result(0, rp, ins, it, it, hist, dims=dims)
         if ins.size == 0 and it >= 2:
-            return _result(0, rp, ins, it, it, hist)
+            return _result(0, rp, ins, it, it, hist, dims=dims)
     ins, _ = _check(rp.lam, rp.res, np.arange(rp.lam.size), lmin, lmax)
-    return _result(1, rp, ins, max_iter, max_iter, hist)
+    return _result(1, rp, ins, max_iter, max_iter, hist, dims=dims)
 
 
 def filter_response(X, Xf):
@@ -256,42 +276,44 @@ def _spurious_free(pend, mu, tol):
     return None
 
 
-def _xfeast(A, F, lmin, lmax, m0, tol, X0, s, max_iter, anorm):
+def _xfeast(A, F, lmin, lmax, m0, tol, X0, s, max_iter, anorm, response_stop):
     # step 0: X' = [X_0, X_1, ..., X_{s-1}] with X_i = rho(A)^i X_0
     blocks = [normalize_columns(np.array(X0, copy=True))]
     filters = 0
     for _ in range(1, s):
         blocks.append(filter_apply(F, blocks[-1]))
         filters += 1
-    hist = []
+    hist, dims = [], []
     rp = None
     for it in range(1, max_iter + 1):
         Q = block_qr_orth(blocks)                       # step 1
+        dims.append(Q.shape[1])
         rp = rayleigh_ritz(A, Q, anorm)                 # step 2(i)
         sel = select_pairs(rp.lam, rp.res, lmin, lmax, m0)   # step 2(ii)
         ins, r = _check(rp.lam, rp.res, sel, lmin, lmax)     # step 3
         hist.append(r)
         if ins.size and r <= tol:
-            return _result(0, rp, ins, it, filters, hist)
+            return _result(0, rp, ins, it, filters, hist, dims=dims)
         if ins.size == 0 and it >= 2:
-            return _result(0, rp, ins, it, filters, hist)
+            return _result(0, rp, ins, it, filters, hist, dims=dims)
         if it == max_iter:
             break
         Xs = rp.X[:, sel]
         Xn = filter_apply(F, Xs)                        # step 4(i)
         filters += 1
-        pend = {"in_cols": [c for c, i in enumerate(sel) if lmin < rp.lam[i] < lmax],
-                "res": rp.res[sel]}
-        keep = _spurious_free(pend, filter_response(Xs, Xn), tol)
-        if keep is not None:
-            return _result(0, rp, sel[keep], it, filters, hist)
+        if response_stop:
+            pend = {"in_cols": [c for c, i in enumerate(sel) if lmin < rp.lam[i] < lmax],
+                    "res": rp.res[sel]}
+            keep = _spurious_free(pend, filter_response(Xs, Xn), tol)
+            if keep is not None:
+                return _result(0, rp, sel[keep], it, filters, hist, dims=dims)
         blocks = blocks[1:] + [Xn]                      # step 4(ii)
-    return _result(1, rp, ins, max_iter, filters, hist)
+    return _result(1, rp, ins, max_iter, filters, hist, dims=dims)
 
 
-def _rfeast(A, F, lmin, lmax, m0, tol, X0, s, max_iter, anorm):
+def _rfeast(A, F, lmin, lmax, m0, tol, X0, s, max_iter, anorm, expand, response_stop):
     X = np.array(X0, copy=True)
-    hist = []
+    hist, dims = [], []
     rp = None
     pend = None
     filters = 0
@@ -302,23 +324,25 @@ def _rfeast(A, F, lmin, lmax, m0, tol, X0, s, max_iter, anorm):
             keep = _spurious_free(pend, filter_response(X, Xf), tol)
             if keep is not None:
                 prp = pend["rp"]
-                return _result(0, prp, pend["sel"][keep], it - 1, filters, hist, pend["m"])
+                return _result(0, prp, pend["sel"][keep], it - 1, filters, hist, pend["m"], dims=dims)
             pend = None
         Q, _ = orthonormalize(Xf)
         m_expected = 0
         for j in range(1, s + 1):                       # step 2
+            dims.append(Q.shape[1])
             rp = rayleigh_ritz(A, Q, anorm)             # (i)
             if j == 1:
                 m_expected = int(np.sum(inside(rp.lam, lmin, lmax)))
             sel = select_pairs(rp.lam, rp.res, lmin, lmax, m0)   # (ii)
             X = rp.X[:, sel]
             if j < s:                                   # (iii)
-                # residuals of the pairs not yet converged only: a converged
-                # pair's residual is rounding noise, whose normalised
-                # direction adds spurious Ritz pairs (Sect. II-B)
-                act = sel[rp.res[sel] > tol]
-                if act.size == 0:
-                    break
+                if expand == EXPAND_ALL:
+                    act = sel                           # R = A X_{i+1} - X_{i+1} Lambda
+                else:
+                    # the pairs not yet converged only (a reading)
+                    act = sel[rp.res[sel] > tol]
+                    if act.size == 0:
+                        break
                 R = rp.AX[:, act] - rp.X[:, act] * rp.lam[act][None, :]
                 Rn = normalize_columns(R)
                 for _ in range(2):
@@ -331,10 +355,10 @@ def _rfeast(A, F, lmin, lmax, m0, tol, X0, s, max_iter, anorm):
         r = float(np.max(rp.res[ins])) if ins.size else np.inf
         hist.append(r)
         if ins.size and r <= tol:
-            return _result(0, rp, ins, it, filters, hist, m_expected)
+            return _result(0, rp, ins, it, filters, hist, m_expected, dims=dims)
         if ins.size == 0 and it >= 2:
-            return _result(0, rp, ins, it, filters, hist, m_expected)
+            return _result(0, rp, ins, it, filters, hist, m_expected, dims=dims)
         in_cols = [c for c, i in enumerate(sel) if lmin < rp.lam[i] < lmax]
-        if any(rp.res[sel[c]] <= tol for c in in_cols):
+        if response_stop and any(rp.res[sel[c]] <= tol for c in in_cols):
             pend = {"in_cols": in_cols, "res": rp.res[sel], "sel": sel, "rp": rp, "m": m_expected}
-    return _result(1, rp, ins, max_iter, filters, hist, m_expected)
+    return _result(1, rp, ins, max_iter, filters, hist, m_expected, dims=dims)

@@ -138,21 +138,23 @@ def test_expanded_variants_beat_feast_on_dense_spectrum():
     assert rhs[O.RFEAST] < rhs[O.PLAIN]
 
 
-def test_rfeast_expansion_is_robust_to_rounding_noise():
-    # RFEAST appends only the residuals of selected pairs that have not yet
-    # converged (reading of Sect. II-B): a converged pair's residual is at the
-    # rounding level of A X, and its normalised direction only adds spurious
-    # in-I Ritz pairs.  With noise of 1e-11 ||A|| in every A Q product the
-    # edge-cluster solve must still converge in the noiseless number of rounds
-    # (appending every residual, it did not converge in 20).
+def test_rfeast_unconverged_option_is_robust_to_rounding_noise():
+    # Option expand="unconverged" (a reading of Sect. II-B, not the paper's
+    # step 2(iii)): only the residuals of selected pairs that have not yet
+    # converged are appended.  A converged pair's residual is at the rounding
+    # level of A X, and its normalised direction only adds spurious in-I Ritz
+    # pairs.  With noise of 1e-11 ||A|| in every A Q product the edge-cluster
+    # solve must still converge in the noiseless number of rounds with the
+    # option, while the paper's literal expansion (every selected residual)
+    # does not converge within 20 rounds: the measured reason for the option.
     import oracle.feast as OF
 
     lam, a, b = spectrum_config2(0, n=768, m_in=18, edge_in=2, edge_out=5)
     P = make_problem("c2", lam, a, b, 28, 8, seed=0, complex_=True)
     X0 = random_subspace(P.n, P.m0, seed=1, complex_=True)
     F = O.factor_shifts(P.A, a, b, 8)
-    clean = O.feast_solve(P.A, a, b, P.m0, 8, 1e-10, X0, variant=O.RFEAST, anorm=P.anorm, factors=F,
-                          max_iter=20)
+    kw = dict(variant=O.RFEAST, anorm=P.anorm, factors=F, max_iter=20)
+    clean = O.feast_solve(P.A, a, b, P.m0, 8, 1e-10, X0, expand=O.EXPAND_UNCONVERGED, **kw)
     # (eigenvectors inside the 1e-4 edge clusters are not individually
     # determined to 1e-8, so spans are not compared here)
     assert clean.status == 0 and clean.lam.size == P.inside.size
@@ -171,14 +173,65 @@ def test_rfeast_expansion_is_robust_to_rounding_noise():
 
     try:
         OF.rayleigh_ritz = lambda A, Q, anorm: rr(NoisyA(A), Q, anorm)
-        noisy = O.feast_solve(P.A, a, b, P.m0, 8, 1e-10, X0, variant=O.RFEAST, anorm=P.anorm, factors=F,
-                              max_iter=20)
+        noisy = O.feast_solve(P.A, a, b, P.m0, 8, 1e-10, X0, expand=O.EXPAND_UNCONVERGED, **kw)
+        literal = O.feast_solve(P.A, a, b, P.m0, 8, 1e-10, X0, expand=O.EXPAND_ALL, **kw)
     finally:
         OF.rayleigh_ritz = rr
     assert noisy.status == 0
     assert noisy.iterations <= clean.iterations
     np.testing.assert_allclose(noisy.lam, P.inside, rtol=1e-9, atol=1e-11 * P.anorm)
     assert noisy.res.max() <= 1e-10
+    assert literal.status == 1
+
+
+FULL_SPAN_CASES = [(v, s, kw) for v in (O.XFEAST, O.RFEAST) for s in (2, 3)
+                   for kw in ([{}, {"response_stop": True}] if v == O.XFEAST else
+                              [{}, {"expand": O.EXPAND_UNCONVERGED, "response_stop": True}])]
+
+
+@pytest.mark.parametrize("variant,s,kw", FULL_SPAN_CASES)
+@pytest.mark.parametrize("cplx", [False, True])
+@pytest.mark.parametrize("n,seed", [(48, 0), (60, 1), (72, 2)])
+def test_full_span_expansion_converges_in_one_round(variant, s, kw, cplx, n, seed):
+    # With s m0 = n the expanded subspace of the first round is the whole
+    # space for a generic X0: the XFEAST warm-up window [X0, rho X0, ...,
+    # rho^{s-1} X0] is a block Krylov space of rho(A) (Sect. II-A), and the
+    # RFEAST space [X', R_1, ..., R_{s-1}] one of A (each R = A X - X Lambda
+    # adds A times the selected Ritz vectors, Sect. II-B).  Rayleigh-Ritz on
+    # the whole space is exact, so round 1 must return exactly the planted
+    # eigenpairs in I with the exact count, under every reading.  (Outside
+    # eigenvalues within 2 ||I|| keep the Krylov bases numerically full.)
+    lam, a, b = spectrum_uniform(n, n // 8, seed=seed, bulk=2.0)
+    m0 = n // s
+    P = make_problem("full", lam, a, b, m0, 8, seed=seed, complex_=cplx)
+    X0 = random_subspace(n, m0, seed=seed + 11, complex_=cplx)
+    r = O.feast_solve(P.A, a, b, m0, 8, 1e-10, X0, variant=variant, s=s, anorm=P.anorm, max_iter=3, **kw)
+    assert r.status == 0 and r.iterations == 1
+    assert r.lam.size == P.inside.size
+    np.testing.assert_allclose(r.lam, P.inside, atol=1e-12 * P.anorm)
+    assert r.res.max() <= 1e-10
+    assert r.rr_dims[-1] == n
+    if variant == O.RFEAST:
+        assert r.m_expected <= m0
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_rfeast_literal_expansion_appends_every_selected_residual(cplx):
+    # RFEAST step 2(iii): R = A X_{i+1} - X_{i+1} Lambda over all m0 selected
+    # pairs, so the Rayleigh-Ritz passes of a round have dimensions m0, 2 m0,
+    # ..., s m0 (while the space is smaller than n); with the "unconverged"
+    # reading a pass appends only the residuals above tol, so fewer
+    P = small_problem(n=150, m_in=8, cplx=cplx, m0=12)
+    X0 = random_subspace(P.n, P.m0, seed=5, complex_=cplx)
+    lit = O.feast_solve(P.A, P.lmin, P.lmax, P.m0, 8, 1e-10, X0, variant=O.RFEAST, s=3, anorm=P.anorm)
+    _check_result(lit, P)
+    assert lit.rr_dims[:3] == [12, 24, 36]
+    assert len(lit.rr_dims) == 3 * lit.iterations
+    assert all(d % 12 == 0 for d in lit.rr_dims)
+    opt = O.feast_solve(P.A, P.lmin, P.lmax, P.m0, 8, 1e-10, X0, variant=O.RFEAST, s=3, anorm=P.anorm,
+                        expand=O.EXPAND_UNCONVERGED)
+    _check_result(opt, P)
+    assert sum(opt.rr_dims) <= sum(lit.rr_dims)
 
 
 @pytest.mark.parametrize("cplx", [False, True])
