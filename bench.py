@@ -8,15 +8,22 @@ inside each edge, 60 lie within 1e-4 outside each edge, the rest uniform in
 [-50, 50]; n_c = 8 Gauss nodes, m0 = 300, tol 1e-10.  Plain FEAST stalls on it
 (more than m0 eigenvalues have |rho| near 1/2), so it runs RFEAST (s = 3), the
 paper's residual-expansion variant, in the mixed precision (complex FP32
-factorisations and solves, FP64-accurate refinement and Rayleigh-Ritz).
+factorisations and solves, FP64-accurate refinement and Rayleigh-Ritz), with
+two readings of the paper switched on: only unconverged pairs expand the
+subspace (rfeast_expand = 1) and the filter-response stop (response_stop = 1);
+with the paper's literal checks alone, spurious in-I Ritz pairs of this
+two-sided spectrum keep the step-3 check from passing.
 
 A step is one complete feast_interval_solve (factorisations, filters,
 Rayleigh-Ritz, checks) with A resident in HBM.  value = eigenpairs found inside
 I (all at residual <= 1e-10) / seconds, summed over ranks.  Also reported:
 e2e (same call with A in pinned host memory and the results copied back inside
-the timed region), the roofline of the dominant kernel (the double-float GEMM),
-the filter-apply rate, the FP64 path on the same input (mixed vs FP64), the CPU
-oracle on a bounded sample, clocks and the number of kernel launches.
+the timed region), the roofline of the dominant kernel of the factorisations and solves, the
+filter-apply rate, per-pair errors against the planted spectrum and the FP64
+path, the FP64 path on the same input (mixed vs FP64), the n = 500 plain FP64
+FEAST workload, the CPU oracle (timed in full on the n = 500 workload and on
+this workload scaled to n = 2048, and extrapolated to n = 8192 from a sample
+of the same matrix), clocks and the number of kernel launches.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -39,7 +46,13 @@ if ROOT not in sys.path:
 METRIC = "converged eigenpairs/sec at residual 1e-10; filter-apply TFLOP/s vs peak; mixed vs FP64"
 UNIT = "eigenpairs/s"
 WORKLOAD = dict(n=8192, m_in=200, edge_in=30, edge_out=60, width=1e-4, bulk=50.0,
-                lmin=-1.0, lmax=1.0, m0=300, n_c=8, tol=1e-10, variant="rfeast", s=3, seed=0)
+                lmin=-1.0, lmax=1.0, m0=300, n_c=8, tol=1e-10, variant="rfeast", s=3, seed=0,
+                rfeast_expand=1, response_stop=1)
+# the n = 500 plain FP64 FEAST workload (real symmetric, 40 of 500 eigenvalues in
+# [-1, 1], 5 within 1e-3 of each edge; n_c = 8, m0 = 60)
+CONFIG1 = dict(n=500, m0=60, n_c=8, tol=1e-10, lmin=-1.0, lmax=1.0, seed=0)
+# eigenvalue gate: |lambda - lambda_planted| <= 1e-10 |lambda| + 1e-12 ||A||
+EIG_RTOL, EIG_ATOL_ANORM = 1e-10, 1e-12
 NUM_SMS = 152
 FP32_LANES_PER_SM = 128
 DF32_FP32_OPS_PER_MAC = 12   # TwoProd (2) + TwoSum (6) + 2 cross FMAs + 2 adds
@@ -56,10 +69,38 @@ CGEMM_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum over t
 
 
 def workload_name(w):
+    rd = ""
+    if w["variant"] == "rfeast" and (w.get("rfeast_expand") or w.get("response_stop")):
+        rd = " (readings: unconverged-only expansion, filter-response stop)"
     return (f"complex Hermitian planted n={w['n']}, {w['m_in']} eigenvalues in [-1,1] with "
             f"{w['edge_in']}+{w['edge_in']} within {w['width']:g} inside and {w['edge_out']}+{w['edge_out']} "
             f"within {w['width']:g} outside the edges, bulk in [-{w['bulk']:g},{w['bulk']:g}]; "
-            f"n_c={w['n_c']}, m0={w['m0']}, {w['variant'].upper()} s={w['s']}")
+            f"n_c={w['n_c']}, m0={w['m0']}, {w['variant'].upper()} s={w['s']}{rd}")
+
+
+def scaled_workload(n):
+    """The benchmark workload scaled to n (counts and m0 in proportion)."""
+    w = dict(WORKLOAD)
+    scale = n / w["n"]
+    w.update(n=n, m_in=max(4, int(w["m_in"] * scale)), edge_in=max(1, int(w["edge_in"] * scale)),
+             edge_out=max(1, int(w["edge_out"] * scale)), m0=max(8, int(w["m0"] * scale)))
+    return w
+
+
+def pair_errors(evals, res, planted, anorm):
+    """Per-pair pointwise relative eigenvalue errors and relative residuals
+    against the planted eigenvalues (None when the counts differ)."""
+    if evals.size != planted.size:
+        return None
+    err = np.abs(evals - planted)
+    rel = err / np.maximum(np.abs(planted), 1e-300)
+    gate = bool(np.all(err <= EIG_RTOL * np.abs(planted) + EIG_ATOL_ANORM * anorm))
+    return {"count": int(evals.size), "gate": gate,
+            "eig_rel_err_max": float(rel.max()) if rel.size else 0.0,
+            "eig_abs_err_max_rel_anorm": float(err.max() / anorm) if err.size else 0.0,
+            "residual_max": float(np.max(res)) if res.size else 0.0,
+            "eig_rel_err": [float("%.3g" % v) for v in rel],
+            "residual": [float("%.3g" % v) for v in res]}
 
 
 # ---------------------------------------------------------------------------
@@ -137,7 +178,7 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle on a bounded sample
 # ---------------------------------------------------------------------------
-def oracle_sample(A_host, w, filters, rr_k_sum, rr_k3_sum, budget_s=30.0):
+def oracle_sample(A_host, w, filters, rr_k_sum, rr_k3_sum, budget_s=30.0, ns_max=2048):
     """Time the FP64 CPU oracle on bounded pieces of the same solve and
     extrapolate to the full solve by operation counts.
 
@@ -159,7 +200,7 @@ def oracle_sample(A_host, w, filters, rr_k_sum, rr_k3_sum, budget_s=30.0):
         t0 = time.time()
         LU, piv = oracle.lu_factor(M)
         t_lu = time.time() - t0
-        if t_lu > 1.5 or ns >= 2048 or time.time() - t_start > budget_s / 3:
+        if t_lu > 1.5 or ns >= min(ns_max, A_host.shape[0]) or time.time() - t_start > budget_s / 3:
             break
         ns *= 2
     ms = max(8, int(round(m0 * ns / n)))
@@ -214,15 +255,119 @@ def aggregate_ranks(ms_total, pairs, world, device="cpu"):
     return float(t.item()), float(p.item())
 
 
+def tc_peak(peaks):
+    """Tensor-core roof of the complex-FP32 factorisation and solve GEMMs:
+    TF32 dense = the measured sustained bf16 rate x the nominal TF32:bf16
+    ratio 1:2 (the kernels run inside a seconds-long step)."""
+    bf16 = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0))
+    return bf16 / 2.0, bf16
+
+
+def factor_solve_roofline(st, ms_step, peaks, peak_kind, sm_max):
+    """Roofline of the dominant kernel of the shifted factorisations and
+    solves (the complex-FP32 GEMM updates): achieved = its algorithmic flops
+    (8 per complex multiply-add, M N K per launch) / its CUDA-event time per
+    launch, against the tensor-core roof of the step's factorisation GEMMs."""
+    tf32, bf16 = tc_peak(peaks)
+    cg_launches = max(1, st.cgemm_launches)
+    cg_avg_ms = st.cgemm_ms / cg_launches
+    cg_flop_per_launch = st.cgemm_flop / cg_launches
+    achieved = cg_flop_per_launch / (cg_avg_ms / 1e3) / 1e12 if st.cgemm_ms > 0 else 0.0
+    fp32_simt = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    traffic = int(CGEMM_DRAM_BYTES_PER_FLOP * cg_flop_per_launch) if CGEMM_DRAM_BYTES_PER_FLOP else None
+    return {"kernel": "cgemm_prefetch_kernel (complex-FP32 GEMM updates of the LU and solves, SIMT)",
+            "bound": "tensor", "achieved": round(achieved, 3), "peak": round(tf32, 1), "unit": "TFLOP/s",
+            "frac": round(achieved / tf32, 4), "traffic": traffic,
+            "peak_source": ("dense TF32 tensor roof = MEASURED_PEAKS.json bf16_tflops_sustained (%s, %.1f) x "
+                            "nominal TF32:bf16 ratio 1/2" % (peak_kind, bf16)),
+            "flop_def": "8 real flops per complex multiply-add, M N K per launch",
+            "frac_of_fp32_simt_lanes": round(achieved / fp32_simt, 4),
+            "traffic_source": CGEMM_TRAFFIC_SOURCE,
+            "launches_per_step": st.cgemm_launches, "avg_launch_ms": round(cg_avg_ms, 4),
+            "share_of_step": round(st.cgemm_ms / ms_step, 3)}
+
+
+def host_residuals(A, V, evals, anorm):
+    """||A x - lambda x|| / ||A|| of the returned pairs, recomputed in FP64 by
+    torch (a check outside the library)."""
+    import torch
+    if evals.size == 0:
+        return np.zeros(0)
+    lam = torch.as_tensor(evals, dtype=torch.float64, device=V.device).to(V.dtype)
+    R = A @ V - V * lam[None, :]
+    return (torch.linalg.vector_norm(R, dim=0) / anorm).cpu().numpy()
+
+
+def run_config1(fg, ctx, stream, dev, cpu):
+    """The n = 500 plain FP64 FEAST workload: time-to-solution on the GPU
+    (median of 5 after one warm-up) and, with cpu, the oracle timed in full on
+    the same matrix and starting subspace."""
+    import torch
+    from workloads import make_problem, random_subspace, spectrum_config1
+    c = CONFIG1
+    lam, a, b = spectrum_config1(c["seed"])
+    P = make_problem("c1", lam, a, b, c["m0"], c["n_c"], seed=c["seed"])
+    X0 = random_subspace(P.n, c["m0"], seed=1)
+    A = torch.from_numpy(P.A).to(f"cuda:{dev}")
+    x0 = torch.from_numpy(X0).to(f"cuda:{dev}")
+    opts = fg.feast_opts_default(variant="feast", prec="f64", anorm=P.anorm)
+    times, out = [], None
+    for i in range(6):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fg.feast_interval_solve(ctx, A, a, b, c["m0"], c["n_c"], c["tol"], opts, x0=x0)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i > 0:
+            times.append(e0.elapsed_time(e1))
+    ms = float(np.median(times))
+    pe = pair_errors(out["evals"], out["res"], P.inside, P.anorm)
+    line = {"workload": "real symmetric planted n=500, 40 eigenvalues in [-1,1] (5 within 1e-3 of each edge), "
+                        "460 uniform in [-10,10] outside; n_c=8, m0=60, plain FEAST, FP64",
+            "ms_per_solve": round(ms, 2), "value": round(out["evals"].size / (ms / 1e3), 2), "unit": UNIT,
+            "iterations": out["iterations"], "correct": bool(out["status"] == 0 and pe is not None and pe["gate"]
+                                                             and pe["residual_max"] <= c["tol"]),
+            "eig_rel_err_max": pe["eig_rel_err_max"] if pe else None,
+            "residual_max": pe["residual_max"] if pe else None}
+    if cpu:
+        import oracle
+        t0 = time.time()
+        r = oracle.feast_solve(P.A, a, b, c["m0"], c["n_c"], c["tol"], X0, anorm=P.anorm)
+        t = time.time() - t0
+        line["oracle"] = {"seconds": round(t, 2), "value": round(r.lam.size / t, 3), "iterations": r.iterations,
+                          "timed": "in full (same matrix and X0)"}
+        line["speedup_vs_oracle"] = round(t * 1e3 / ms, 1)
+    return line
+
+
+def oracle_full_scaled(n):
+    """The oracle timed in full on the benchmark workload scaled to n (same
+    generator and readings), with its own iteration and filter counts."""
+    import oracle
+    from workloads import make_problem, random_subspace, spectrum_config2
+    w = scaled_workload(n)
+    lam, a, b = spectrum_config2(w["seed"], n=w["n"], m_in=w["m_in"], edge_in=w["edge_in"],
+                                 edge_out=w["edge_out"], width=w["width"], bulk=w["bulk"])
+    P = make_problem("c2", lam, a, b, w["m0"], w["n_c"], seed=w["seed"], complex_=True)
+    X0 = random_subspace(n, w["m0"], seed=1, complex_=True)
+    t0 = time.time()
+    r = oracle.feast_solve(P.A, a, b, w["m0"], w["n_c"], w["tol"], X0, variant=oracle.RFEAST, s=w["s"],
+                           anorm=P.anorm, max_iter=30,
+                           expand=oracle.EXPAND_UNCONVERGED if w["rfeast_expand"] else oracle.EXPAND_ALL,
+                           response_stop=bool(w["response_stop"]))
+    t = time.time() - t0
+    pe = pair_errors(r.lam, r.res, P.inside, P.anorm)
+    return {"n": n, "m0": w["m0"], "seconds": round(t, 1), "value": round(r.lam.size / t, 4), "unit": UNIT,
+            "iterations": r.iterations, "filters": r.filters, "rr_dims": r.rr_dims, "status": r.status,
+            "correct": bool(pe is not None and pe["gate"]), "timed": "in full"}
+
+
 def run_ours(args, rank, world, dev):
     import torch
     import paper_1605_08771_gb300 as fg
 
-    w = dict(WORKLOAD)
-    if args.n:
-        scale = args.n / w["n"]
-        w.update(n=args.n, m_in=max(4, int(w["m_in"] * scale)), edge_in=max(1, int(w["edge_in"] * scale)),
-                 edge_out=max(1, int(w["edge_out"] * scale)), m0=max(8, int(w["m0"] * scale)))
+    w = scaled_workload(args.n) if args.n else dict(WORKLOAD)
     w["prec"] = args.prec
     w["variant"] = args.variant
     fg.build_library()
@@ -233,8 +378,11 @@ def run_ours(args, rank, world, dev):
     inside = lam[(lam > w["lmin"]) & (lam < w["lmax"])]
     anorm = float(np.max(np.abs(lam)))
     ctx = fg.feast_init(dev, stream)
+    rd = dict(rfeast_expand=w["rfeast_expand"], response_stop=w["response_stop"]) if w["variant"] != "feast" else {}
+    if w["variant"] == "xfeast":
+        rd.pop("rfeast_expand")
     opts = fg.feast_opts_default(variant=w["variant"], s=w["s"], prec=w["prec"], anorm=anorm, max_iter=30,
-                                 refine_gemm=args.refine_gemm)
+                                 refine_gemm=args.refine_gemm, **rd)
 
     def solve(Adev):
         return fg.feast_interval_solve(ctx, Adev, w["lmin"], w["lmax"], w["m0"], w["n_c"], w["tol"], opts)
@@ -266,11 +414,15 @@ def run_ours(args, rank, world, dev):
     launches = fg.feast_kernel_launches() - launches0
     ms_step = ms_total / args.steps
     found = [r["evals"].size for r in results]
-    ok = all(r["status"] == 0 and r["evals"].size == inside.size and np.max(r["res"]) <= w["tol"]
-             and np.max(np.abs(r["evals"] - inside)) <= 1e-10 * anorm for r in results)
+    errs = [pair_errors(r["evals"], r["res"], inside, anorm) for r in results]
+    ok = all(r["status"] == 0 and e is not None and e["gate"] and e["residual_max"] <= w["tol"]
+             for r, e in zip(results, errs))
     t_max, pairs_all = aggregate_ranks(ms_total, sum(found), world, device=f"cuda:{dev}")
     value = pairs_all / (t_max / 1e3)
     st = results[-1]["stats"]
+    last = results[-1]
+    hres = host_residuals(A, last["evecs"], last["evals"], anorm)
+    ok = ok and bool(hres.size == 0 or hres.max() <= 2 * w["tol"])
 
     # e2e: A in pinned host memory, copied in; results copied out; all timed
     Ah = A_store.cpu().pin_memory()
@@ -296,24 +448,8 @@ def run_ours(args, rank, world, dev):
     peaks, peak_kind = measured_peaks()
     clocks = clk.summary()
     sm_max = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    # dominant kernel of the step (launch list of the solve, profiles/): the
-    # complex-FP32 SIMT GEMM of the LU trailing and triangular-solve updates
-    cg_launches = max(1, st.cgemm_launches)
-    cg_avg_ms = st.cgemm_ms / cg_launches
-    cg_flop_per_launch = st.cgemm_flop / cg_launches
-    fp32_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    cg_achieved = cg_flop_per_launch / (cg_avg_ms / 1e3) / 1e12 if st.cgemm_ms > 0 else 0.0
-    cg_traffic = None
-    if CGEMM_DRAM_BYTES_PER_FLOP is not None:
-        cg_traffic = int(CGEMM_DRAM_BYTES_PER_FLOP * cg_flop_per_launch)
-    roofline = {"kernel": "cgemm_prefetch_kernel (complex-FP32 SIMT GEMM)", "bound": "alu",
-                "achieved": round(cg_achieved, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
-                "frac": round(cg_achieved / fp32_peak, 4), "traffic": cg_traffic,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x max SM clock (unit counts; no measured FP32 peak)",
-                "flop_def": "8 real flops per complex multiply-add, M N K per launch",
-                "traffic_source": CGEMM_TRAFFIC_SOURCE,
-                "launches_per_step": st.cgemm_launches, "avg_launch_ms": round(cg_avg_ms, 4),
-                "share_of_step": round(st.cgemm_ms / ms_step, 3)}
+    roofline = factor_solve_roofline(st, ms_step, peaks, peak_kind, sm_max)
+    tf32_peak, _ = tc_peak(peaks)
 
     # the refinement GEMM: tensor-core digit-split GEMM by default,
     # double-float SIMT GEMM with --refine-gemm 1
@@ -345,33 +481,43 @@ def run_ours(args, rank, world, dev):
                             "share_of_step": round(st.refine_gemm_ms / ms_step, 3)})
 
     # filter-apply rate: algorithmic flops of the solves (8 n^2 m per entry,
-    # complex MAC = 8 real flops) per filter application
+    # complex MAC = 8 real flops) per filter application, refinement excluded
     n, m0, nc = w["n"], w["m0"], w["n_c"]
     filt_flop = 2 * nc * 8.0 * n * n * m0
     filter_tflops = filt_flop * st.filters / (st.filter_ms / 1e3) / 1e12 if st.filter_ms > 0 else None
 
+    pe = errs[-1] or {}
     line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 2), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": ("c64+bf16x21" if args.refine_gemm == 0 else "c64+df32") if w["prec"] != "f64" else "c128",
             "data": "synthetic planted spectrum (seeded), no dataset",
             "config": {"workload": workload_name(w), "n": n, "m0": m0, "n_c": nc, "variant": w["variant"],
                        "s": w["s"], "prec": w["prec"], "tol": w["tol"],
+                       "rfeast_expand": w["rfeast_expand"], "response_stop": w["response_stop"],
                        "l2": "inputs larger than L2 (A is %.2f GB, L2 129 MB)" % (h2d / 1e9),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "correct": bool(ok), "eigenpairs_per_step": found[-1], "iterations": results[-1]["iterations"],
+            "correct": bool(ok),
+            "gate": "every step: count exact, |dl| <= 1e-10 |l| + 1e-12 ||A|| per pair, residual <= tol, "
+                    "host-recomputed residual <= 2 tol",
+            "eigenpairs_per_step": found[-1], "iterations": last["iterations"],
             "filters": st.filters, "refine_steps": st.refine_steps,
             "factor_ms": round(st.factor_ms, 1), "filter_ms": round(st.filter_ms, 1),
+            "pairs_vs_planted": pe,
+            "host_residual_max": float(hres.max()) if hres.size else None,
             "roofline": roofline, "roofline_refine_gemm": roofline_refine,
             "filter_apply": {"tflops": round(filter_tflops, 3) if filter_tflops else None,
+                             "peak": round(tf32_peak, 1),
+                             "frac": round(filter_tflops / tf32_peak, 4) if filter_tflops else None,
                              "flop_per_filter": filt_flop,
-                             "note": "solve flops 8 n^2 m0 per entry, 2 n_c entries; refinement excluded"},
+                             "note": ("solve flops 8 n^2 m0 per entry, 2 n_c entries, refinement excluded, over "
+                                      "the whole filter time (solves, refinement, accumulation); peak as roofline")},
             "e2e": {"value": round(e2e_found / e2e_steps / (e2e_ms / 1e3), 4), "unit": UNIT,
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_ms, 1)},
             "gpu_launches": int(launches), "clocks": clocks, "peak_source": peak_kind}
 
-    # mixed vs FP64 on the same input (one untimed-by-steps solve, CUDA events)
+    # mixed vs FP64 on the same input (one solve, CUDA events), per-pair errors
     if args.fp64 and w["prec"] != "f64":
-        o64 = fg.feast_opts_default(variant=w["variant"], s=w["s"], prec="f64", anorm=anorm, max_iter=30)
+        o64 = fg.feast_opts_default(variant=w["variant"], s=w["s"], prec="f64", anorm=anorm, max_iter=30, **rd)
         barrier()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)
@@ -379,63 +525,78 @@ def run_ours(args, rank, world, dev):
         f1.record(stream)
         barrier()
         t64 = f0.elapsed_time(f1)
-        d = None
-        if r64["evals"].size == results[-1]["evals"].size:
-            d = float(np.max(np.abs(r64["evals"] - results[-1]["evals"])) / anorm)
+        d = rel = None
+        if r64["evals"].size == last["evals"].size:
+            dd = np.abs(r64["evals"] - last["evals"])
+            d = float(dd.max() / anorm)
+            rel = dd / np.maximum(np.abs(r64["evals"]), 1e-300)
         line["mixed_vs_fp64"] = {"fp64_ms": round(t64, 1), "mixed_ms": round(ms_step, 1),
                                  "speedup": round(t64 / ms_step, 3),
                                  "fp64_value": round(r64["evals"].size / (t64 / 1e3), 4),
-                                 "max_eig_diff_rel_anorm": d, "fp64_iterations": r64["iterations"]}
+                                 "max_eig_diff_rel_anorm": d, "fp64_iterations": r64["iterations"],
+                                 "fp64_pairs": int(r64["evals"].size),
+                                 "eig_rel_diff_max": float(rel.max()) if rel is not None and rel.size else None,
+                                 "eig_rel_diff": [float("%.3g" % v) for v in rel] if rel is not None else None}
 
-    # CPU oracle on a bounded sample (rank 0, N = 1 only)
+    # the n = 500 plain FP64 FEAST workload (and its oracle timed in full)
+    if args.config1:
+        line["config1"] = run_config1(fg, ctx, stream, dev, args.cpu and world == 1)
+
+    # CPU oracle (rank 0, N = 1 only): timed in full on the workload scaled to
+    # n = 2048, and extrapolated to this workload from a sample of its matrix
     if args.cpu and world == 1:
         A_host = Ah.numpy().T
         T, ns, ms_, samp = oracle_sample(A_host, w, st.filters, st.rr_k_sum, st.rr_k3_sum)
+        full = oracle_full_scaled(args.cpu_full_n) if args.cpu_full_n else None
         line["cpu_baseline"] = {"value": round(inside.size / T, 6), "unit": UNIT, "cores": os.cpu_count(),
-                                "kind": "oracle",
-                                "sample": (f"oracle LU of the leading {ns}x{ns} block of z_1 I - A, its solve of "
-                                           f"{ms_} right-hand sides and one {ns}x{ms_} Rayleigh-Ritz "
-                                           f"({samp:.1f} s of CPU work), scaled by operation counts to the full "
-                                           f"solve ({st.filters} filters, {st.rr_passes} Rayleigh-Ritz passes with the run's dimensions): "
-                                           f"{T:.0f} s extrapolated"),
-                                "extrapolated_s": round(T, 1)}
+                                "kind": "oracle", "extrapolated": True,
+                                "sample": (f"extrapolated: oracle LU of the leading {ns}x{ns} block of z_1 I - A "
+                                           f"(this matrix), its solve of {ms_} right-hand sides and one {ns}x{ms_} "
+                                           f"Rayleigh-Ritz ({samp:.1f} s of CPU work), scaled by operation counts "
+                                           f"to the full solve with this run's counts ({st.filters} filters, "
+                                           f"{st.rr_passes} Rayleigh-Ritz passes, their dimensions): {T:.0f} s"),
+                                "extrapolated_s": round(T, 1),
+                                "timed_in_full": [x for x in [full] if x is not None]}
+        if "config1" in line and "oracle" in line["config1"]:
+            c1 = line["config1"]
+            line["cpu_baseline"]["timed_in_full"].insert(0, {"n": 500, "seconds": c1["oracle"]["seconds"],
+                                                             "value": c1["oracle"]["value"], "unit": UNIT,
+                                                             "iterations": c1["oracle"]["iterations"],
+                                                             "workload": "n = 500 plain FP64 FEAST (config1)",
+                                                             "timed": "in full"})
     fg.feast_finalize(ctx)
     return line
 
 
 def run_reference(args, rank, world):
-    """The reference arm: the FP64 CPU oracle, timed on the host cores on
-    bounded samples of the same workload (each step one sample)."""
+    """The reference arm: the FP64 CPU oracle on the host cores, on this
+    workload's matrix (same spectrum and Gaussian seed; Q from the host's QR).
+    Each step is a bounded sample (the oracle's LU, solve and Rayleigh-Ritz on
+    a leading block), extrapolated by operation counts to the full solve with
+    the oracle's own counts from a solve it runs in full, once, on the
+    workload scaled to n = 1024 (its Rayleigh-Ritz dimensions scaled by n)."""
     if rank != 0:
         return None
     from workloads import spectrum_config2
-    from workloads import haar_unitary  # noqa: F401  (numpy generator for the host matrix)
-    w = dict(WORKLOAD)
-    if args.n:
-        scale = args.n / w["n"]
-        w.update(n=args.n, m0=max(8, int(w["m0"] * scale)))
-    lam, a, b = spectrum_config2(w["seed"])
-    # the sample needs only a leading block of A: build a planted matrix of the
-    # sample's largest block size with the same spectrum distribution
-    nb = min(2048, w["n"])
-    rng = np.random.default_rng(w["seed"])
-    G = rng.standard_normal((nb, nb)) + 1j * rng.standard_normal((nb, nb))
-    Qm, _ = np.linalg.qr(G)
-    lam_b = np.sort(rng.choice(lam, nb, replace=False))
-    A_host = (Qm * lam_b) @ Qm.conj().T
-    # the solve's own counts on this seeded workload: 2 rounds, 3 filter
-    # applications; Rayleigh-Ritz dimensions m0, 2 m0, 3 m0 in the first round,
-    # then m0 growing by the 17 of 300 residual columns that have not converged
-    filters, iters = 3, 2
-    m0, grow = w["m0"], max(1, round(17 * w["m0"] / 300))
-    rr_dims = [m0 * (j + 1) for j in range(w["s"])] + [m0 + grow * j for j in range(w["s"])]
+    from workloads.planted import planted_block_host
+    w = scaled_workload(args.n) if args.n else dict(WORKLOAD)
+    w["prec"], w["variant"] = args.prec, args.variant
+    lam, a, b = spectrum_config2(w["seed"], n=w["n"], m_in=w["m_in"], edge_in=w["edge_in"],
+                                 edge_out=w["edge_out"], width=w["width"], bulk=w["bulk"])
+    t_build = time.time()
+    A_host = planted_block_host(lam, w["seed"], min(1024, w["n"]), complex_=True)
+    t_build = time.time() - t_build
+    small = oracle_full_scaled(min(1024, w["n"]))
+    f = w["n"] / small["n"]
+    filters = small["filters"]
+    rr_dims = [d * f for d in small["rr_dims"]]
     k_sum, k3_sum = float(sum(rr_dims)), float(sum(k ** 3 for k in rr_dims))
     for _ in range(args.warmup):
-        oracle_sample(A_host, w, filters, k_sum, k3_sum, budget_s=10.0)
+        oracle_sample(A_host, w, filters, k_sum, k3_sum, budget_s=6.0, ns_max=1024)
     Ts, samples = [], []
     t0 = time.time()
     for _ in range(args.steps):
-        T, ns, ms_, samp = oracle_sample(A_host, w, filters, k_sum, k3_sum, budget_s=10.0)
+        T, ns, ms_, samp = oracle_sample(A_host, w, filters, k_sum, k3_sum, budget_s=6.0, ns_max=1024)
         Ts.append(T)
         samples.append(samp)
     wall = time.time() - t0
@@ -443,14 +604,22 @@ def run_reference(args, rank, world):
     return {"metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(1e3 * float(np.mean(Ts)), 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic planted spectrum (seeded)",
-            "impl": "reference",
+            "impl": "reference", "extrapolated": True,
+            "sample_ms_per_step": round(1e3 * float(np.mean(samples)), 1),
             "config": {"workload": workload_name(w), "n": w["n"], "m0": w["m0"], "n_c": w["n_c"],
-                       "variant": w["variant"], "s": w["s"], "prec": "f64 (CPU oracle)", "tol": w["tol"]},
+                       "variant": w["variant"], "s": w["s"], "prec": w["prec"], "tol": w["tol"],
+                       "rfeast_expand": w["rfeast_expand"], "response_stop": w["response_stop"],
+                       "l2": "inputs larger than L2 (A is %.2f GB, L2 129 MB)" % (16.0 * w["n"] ** 2 / 1e9),
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
             "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": (f"oracle LU/solve/Rayleigh-Ritz on a leading {ns}x{ns} block, "
-                                        f"{float(np.mean(samples)):.1f} s per step, extrapolated by operation "
-                                        f"counts to the full solve ({filters} filters, {iters} iterations, Rayleigh-Ritz "
-                                        f"dimensions {rr_dims})")},
+                             "sample": (f"extrapolated: the oracle's LU, solve and Rayleigh-Ritz on the leading "
+                                        f"{ns}x{ns} block of this workload's matrix (built on the host in "
+                                        f"{t_build:.0f} s), {float(np.mean(samples)):.1f} s per step, scaled by "
+                                        f"operation counts to the full solve with the oracle's own counts from its "
+                                        f"full solve of the workload scaled to n = {small['n']} ({small['seconds']} s: "
+                                        f"{filters} filters, {small['iterations']} iterations, Rayleigh-Ritz "
+                                        f"dimensions {small['rr_dims']} x {f:g})"),
+                             "timed_in_full": [small]},
             "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": round(wall, 1)}
 
@@ -468,6 +637,9 @@ def main():
     ap.add_argument("--variant", default="rfeast", choices=["feast", "xfeast", "rfeast"])
     ap.add_argument("--no-fp64", dest="fp64", action="store_false")
     ap.add_argument("--no-cpu", dest="cpu", action="store_false")
+    ap.add_argument("--no-config1", dest="config1", action="store_false")
+    ap.add_argument("--cpu-full-n", type=int, default=2048,
+                    help="n of the scaled workload the oracle solves in full (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -45,17 +45,14 @@ enum { FEAST_R64 = 0, /* real symmetric, double */
 /* iteration variant */
 enum { FEAST_PLAIN = 0,  /* FEAST Algorithm (Appendix) */
        FEAST_XFEAST = 1, /* expanding subspace from previous filtered blocks (Sect. II-A) */
-       FEAST_RFEAST = 2  /* expanding subspace with Ritz residuals (Sect. II-B); only the
-                            selected pairs whose relative residual is still above tol expand
-                            it (a converged pair's residual is rounding noise) */ };
+       FEAST_RFEAST = 2  /* expanding subspace with Ritz residuals (Sect. II-B) */ };
 
 /* arithmetic of the shifted factorisations and solves */
 enum { FEAST_PREC_F64 = 0,      /* complex FP64 LU and solves */
        FEAST_PREC_MIXED = 1,    /* complex FP32 LU and solves, FP64 iterative refinement */
        FEAST_PREC_MIXED_TC = 2  /* as FEAST_PREC_MIXED, the LU's trailing updates on the
-                                   tensor cores (4xTF32 split products, FP32 accumulate):
-                                   slightly less accurate factors, so refinement may take
-                                   one more step */ };
+                                   tensor cores (exact three-part TF32 split, six split
+                                   products, FP32 accumulate) */ };
 
 /* status codes */
 #define FEAST_OK 0
@@ -91,6 +88,18 @@ typedef struct {
                            on the FP32 SIMT pipes (0, default) or on the tensor cores (1: exact
                            three-part TF32 split, FP32 accumulate; bound by the operand planes'
                            L2 traffic, slower at m0 = 300) */
+  int rfeast_expand;    /* RFEAST step 2(iii) (Appendix, RFEAST Algorithm): 0 (default, the
+                           paper) appends the residual R = A X - X Lambda of every selected
+                           pair; 1 appends only those of selected pairs whose relative residual
+                           is still above tol and ends the passes once none is (a converged
+                           pair's residual is rounding noise whose direction adds spurious
+                           Ritz pairs, Sect. II-B) */
+  int response_stop;    /* XFEAST/RFEAST: 0 (default, the paper) stops on the step-3 check
+                           alone; 1 also stops when every selected pair inside I whose filter
+                           response Re(x^H rho(A) x) exceeds 1/2 has converged (rho > 1/2
+                           exactly inside I for the circle contour), returning those pairs:
+                           on spectra with eigenvalues on both sides of I, mixtures of outside
+                           eigenvectors give in-I Ritz values that never converge */
   int reserved;
 } feast_opts;
 
@@ -229,20 +238,24 @@ int feast_gemm_f64acc(feast_ctx* ctx, int method, int dtype, int transA, int tra
                       int64_t ldc);
 
 /* Allocation-free Jacobi eigensolver, for callers that cannot allocate device
- * memory at call time: code running while a CUDA stream is captured, services
- * that reserve their whole memory budget up front, frameworks whose caching
- * allocator holds the free memory.  (The paper has no counterpart; this is a
- * deployment variant of feast_jacobi_eigh.)  Same operation and outputs as
- * feast_jacobi_eigh, without a context: device is the CUDA device, stream a
- * cudaStream_t (NULL = legacy default stream), H device k x k (leading dim k,
- * not modified), evals host (k doubles, ascending), V device k x k.
+ * memory at call time: services that reserve their whole memory budget up
+ * front, frameworks whose caching allocator holds the free memory.  (The
+ * paper has no counterpart; this is a deployment variant of
+ * feast_jacobi_eigh.)  Same operation and outputs as feast_jacobi_eigh,
+ * without a context: device is the CUDA device, stream a cudaStream_t (NULL
+ * = legacy default stream), H device k x k (leading dim k, not modified),
+ * evals host (k doubles, ascending), V device k x k.
  * All scratch lives in one static device array of 2.25 MiB inside the library
  * (held by every GPU that loads the library until the process exits), so k is
  * limited to 1 <= k <= 256; larger k returns FEAST_ERR_ARG.  No cudaMalloc,
  * cudaFree or allocating library routine is called.  The first call on a
- * device looks up the array's device address (once per device); make that
- * first call before any stream capture.  Every call reuses the same array:
- * calls that overlap on the GPU (other streams or host threads) race. */
+ * device looks up the array's device address (once per device).  The call
+ * synchronises its stream and reads the eigenvalues back to the host to sort
+ * them, so a stream that is being captured into a CUDA graph is refused with
+ * FEAST_ERR_ARG before anything is enqueued on it (the capture stays valid).
+ * The caller's current device is restored on return.  Every call reuses the
+ * same array: calls that overlap on the GPU (other streams or host threads)
+ * race. */
 int feast_jacobi_eigh_noalloc(int device, void* stream, int dtype, int64_t k, const void* H,
                               double* evals, void* V, int* sweeps);
 

@@ -41,7 +41,8 @@ class FeastOpts(ctypes.Structure):
                 ("max_iter", ctypes.c_int), ("refine_max", ctypes.c_int), ("refine_gemm", ctypes.c_int),
                 ("aspect", ctypes.c_double), ("anorm", ctypes.c_double), ("refine_tol", ctypes.c_double),
                 ("seed", ctypes.c_ulonglong), ("x0", ctypes.c_void_p), ("refine_switch", ctypes.c_double),
-                ("tc_solve", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("tc_solve", ctypes.c_int), ("rfeast_expand", ctypes.c_int), ("response_stop", ctypes.c_int),
+                ("reserved", ctypes.c_int)]
 
 
 class FeastStats(ctypes.Structure):

@@ -1181,8 +1181,10 @@ struct Solver {
       S* oldest = ring[0];
       filter(Xsel, ms, oldest);                                   // step 4(i)
       ++out.filters;
-      Pending pd = make_pending(sel, tol);
-      if (pd.valid && response_test(pd, Xsel, oldest, ms, tol, out)) return out;
+      if (o.response_stop) {
+        Pending pd = make_pending(sel, tol);
+        if (pd.valid && response_test(pd, Xsel, oldest, ms, tol, out)) return out;
+      }
       std::rotate(ring.begin(), ring.begin() + 1, ring.end());    // step 4(ii)
     }
     finish(out, ins);
@@ -1233,17 +1235,18 @@ struct Solver {
           col_norms2<S>(R, n, ms, n, d_nrm, st);
           std::vector<double> nr2(ms), sc(ms);
           to_host(ctx, nr2.data(), d_nrm, ms);
-          // only the pairs that have not converged expand the subspace: a
+          // step 2(iii): the residual of every selected pair (the paper), or
+          // with rfeast_expand = 1 only of those that have not converged: a
           // converged pair's residual is at the rounding level of A X, and its
           // normalised direction would add spurious Ritz pairs, not information
           std::vector<int> act;
           for (int64_t i = 0; i < ms; ++i)
-            if (res[sel[i]] > tol && nr2[i] > 0) act.push_back((int)i);
+            if (nr2[i] > 0 && (o.rfeast_expand == 0 || res[sel[i]] > tol)) act.push_back((int)i);
           const int64_t ma = (int64_t)act.size();
           if (std::getenv("FEAST_LOG"))
             fprintf(stderr, "[feast] rfeast it %d j %d: %lld of %lld residuals appended\n", it, j, (long long)ma,
                     (long long)ms);
-          if (ma == 0) break;  // every selected pair has converged
+          if (ma == 0) break;  // nothing to append (every selected pair converged)
           for (int64_t c = 0; c < ma; ++c) sc[c] = 1.0 / std::sqrt(nr2[act[c]]);
           to_dev(ctx, d_scale, sc.data(), ma);
           to_dev(ctx, d_idx, act.data(), ma);
@@ -1299,7 +1302,7 @@ struct Solver {
         finish(out, ins);
         return out;
       }
-      pd = make_pending(sel, tol);
+      if (o.response_stop) pd = make_pending(sel, tol);
     }
     finish(out, ins);
     out.status = FEAST_WARN_MAXITER;
@@ -1515,6 +1518,7 @@ int feast_interval_solve(feast_ctx* ctx, const void* A, int dtype, int64_t n, in
   if (o.variant != FEAST_PLAIN && (o.s < 1 || (int64_t)o.s * m0 > 65536)) return FEAST_ERR_ARG;
   if (o.refine_max < 0 || !(o.refine_switch >= 0.0) || o.refine_gemm < 0 || o.refine_gemm > 1) return FEAST_ERR_ARG;
   if (o.tc_solve < 0 || o.tc_solve > 1) return FEAST_ERR_ARG;
+  if (o.rfeast_expand < 0 || o.rfeast_expand > 1 || o.response_stop < 0 || o.response_stop > 1) return FEAST_ERR_ARG;
   *m_found = 0;
   *iterations = 0;
   return guarded(ctx, [&]() {

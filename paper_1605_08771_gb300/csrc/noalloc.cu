@@ -1,10 +1,9 @@
 // Allocation-free variant of the Jacobi reduced eigensolver.
 //
-// Some callers cannot allocate device memory when they call in: code that
-// runs while a CUDA stream is being captured (cudaMalloc is not allowed
-// there), services that reserve their whole device memory budget up front,
-// or frameworks whose caching allocator already holds the free memory, so a
-// fresh cudaMalloc would fail.  feast_jacobi_eigh_noalloc serves them: it
+// Some callers cannot allocate device memory when they call in: services
+// that reserve their whole device memory budget up front, or frameworks whose
+// caching allocator already holds the free memory, so a fresh cudaMalloc
+// would fail or break the budget.  feast_jacobi_eigh_noalloc serves them: it
 // takes the caller's input and output buffers and keeps every piece of
 // scratch (the working copy of H, the unsorted eigenvectors, the barrier
 // counter, status words and rotation parameters of the cooperative kernel,
@@ -16,6 +15,12 @@
 // call's contents.  The parts that must start at zero (barrier counter,
 // status, sweep counters) are cleared by each call.  Calls that overlap on
 // the GPU (two streams, two host threads) race on the array.
+//
+// The call synchronises its stream and reads the eigenvalues back to the
+// host to sort them, so it cannot run on a stream that is being captured
+// into a CUDA graph: on a capturing stream it returns FEAST_ERR_ARG before
+// touching the stream, and the capture stays valid.  It restores the
+// caller's current device on every return.
 #include <algorithm>
 #include <mutex>
 
@@ -99,6 +104,20 @@ int run(void* scratch, int sms, int64_t k, const S* H, double* evals, S* V, int*
   }
 }
 
+// restores the calling thread's current device when it goes out of scope
+struct DeviceGuard {
+  int prev = -1;
+  DeviceGuard() {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      cudaGetLastError();
+      prev = -1;
+    }
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
 }  // namespace
 
 extern "C" int feast_jacobi_eigh_noalloc(int device, void* stream, int dtype, int64_t k, const void* H,
@@ -106,10 +125,19 @@ extern "C" int feast_jacobi_eigh_noalloc(int device, void* stream, int dtype, in
   if (!H || !evals || !V || k < 1 || k > kNoAllocMaxK || device < 0 || device >= kMaxDevices)
     return FEAST_ERR_ARG;
   if (dtype != FEAST_R64 && dtype != FEAST_C128) return FEAST_ERR_ARG;
+  DeviceGuard guard;
   if (cudaSetDevice(device) != cudaSuccess) {
     cudaGetLastError();
     return FEAST_ERR_CUDA;
   }
+  // the call synchronises and reads back: refuse a capturing stream without
+  // enqueuing anything on it
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing((cudaStream_t)stream, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return FEAST_ERR_ARG;
+  }
+  if (cap != cudaStreamCaptureStatusNone) return FEAST_ERR_ARG;
   void* scratch = nullptr;
   int sms = 0;
   if (int r = setup_device(device, &scratch, &sms)) return r;

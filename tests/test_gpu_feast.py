@@ -50,35 +50,51 @@ def test_small_planted_vs_oracle(ctx, vname, vor, cplx, prec):
     assert abs(out["iterations"] - ref.iterations) <= 1
 
 
+# readings of the expanded variants: the paper's text (every selected
+# residual appended, step-3 check alone) and the two named options
+READINGS = {"paper": ({}, {}),
+            "options": ({"rfeast_expand": 1, "response_stop": 1},
+                        {"expand": O.EXPAND_UNCONVERGED, "response_stop": True})}
+
+
 @pytest.mark.parametrize("vname,vor", VARIANTS)
-def test_n500_workload_vs_oracle(ctx, vname, vor):
+@pytest.mark.parametrize("reading", ["paper", "options"])
+def test_n500_workload_vs_oracle(ctx, vname, vor, reading):
     # n = 500 real symmetric, 40 eigenvalues in [-1, 1] (5 within 1e-3 of each
     # edge), n_c = 8, m0 = 60, tol 1e-10, FP64
+    if vor == O.PLAIN and reading == "options":
+        pytest.skip("plain FEAST has no options")
+    gk, ok = READINGS[reading]
+    if vor == O.XFEAST:
+        ok = {k: v for k, v in ok.items() if k != "expand"}
     lam, a, b = spectrum_config1(0)
     P = make_problem("c1", lam, a, b, 60, 8, seed=0)
     X0 = random_subspace(P.n, 60, seed=1)
     out = fg.feast_interval_solve(ctx, cuda(P.A), a, b, 60, 8, 1e-10,
-                                  fg.feast_opts_default(variant=vname, anorm=P.anorm), x0=cuda(X0))
+                                  fg.feast_opts_default(variant=vname, anorm=P.anorm, **gk), x0=cuda(X0))
     assert out["status"] == 0
     check_against_planted(out, P)
-    ref = O.feast_solve(P.A, a, b, 60, 8, 1e-10, X0, variant=vor, anorm=P.anorm)
+    ref = O.feast_solve(P.A, a, b, 60, 8, 1e-10, X0, variant=vor, anorm=P.anorm, **ok)
     np.testing.assert_allclose(out["evals"], ref.lam, atol=1e-12 * P.anorm)
-    if vor != O.XFEAST:
-        # XFEAST on a spectrum with eigenvalues on both sides of I stops when
-        # rounding-born spurious pairs leave its stopping set: its round count
-        # varies with rounding (x86 vs Arm oracle runs differ), so it is not pinned
+    if vor == O.PLAIN:
+        # the expanded variants on a spectrum with eigenvalues on both sides of
+        # I stop when rounding-born spurious pairs leave their stopping set:
+        # their round counts vary with rounding (x86 vs Arm oracle runs
+        # differ), so only plain FEAST's is pinned
         assert abs(out["iterations"] - ref.iterations) <= 1
 
 
 @pytest.mark.parametrize("prec", ["f64", "mixed"])
-def test_edge_clustered_complex_rfeast(ctx, prec):
+@pytest.mark.parametrize("reading", ["paper", "options"])
+def test_edge_clustered_complex_rfeast(ctx, prec, reading):
     # scaled-down edge-cluster workload: clusters within 1e-4 inside and
     # outside both edges, bulk in [-50, 50]; plain FEAST stalls here
     lam, a, b = spectrum_config2(0, n=640, m_in=16, edge_in=3, edge_out=5, width=1e-4, bulk=50.0)
     P = make_problem("c2s", lam, a, b, 24, 8, seed=0, complex_=True)
     X0 = random_subspace(P.n, 24, seed=1, complex_=True)
     out = fg.feast_interval_solve(ctx, cuda(P.A), a, b, 24, 8, 1e-10,
-                                  fg.feast_opts_default(variant="rfeast", prec=prec, anorm=P.anorm),
+                                  fg.feast_opts_default(variant="rfeast", prec=prec, anorm=P.anorm,
+                                                        **READINGS[reading][0]),
                                   x0=cuda(X0))
     assert out["status"] == 0
     check_against_planted(out, P)
@@ -153,3 +169,90 @@ def test_invariant_start_converges_in_one_round(ctx, vname, vor, prec):
     check_against_planted(out, P)
     if vname == "rfeast":
         assert out["stats"].m_expected == ins.size == ref.m_expected
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_rfeast_literal_expansion_matches_oracle(ctx, cplx):
+    # RFEAST step 2(iii) as the paper states it (every selected pair's
+    # residual appended): the Rayleigh-Ritz passes of each round have
+    # dimensions m0, 2 m0, 3 m0, like the oracle's, and the result matches it
+    lam, a, b = spectrum_uniform(150, 8, seed=3, bulk=10.0)
+    P = make_problem("lit", lam, a, b, 12, 8, seed=3, complex_=cplx)
+    X0 = random_subspace(P.n, P.m0, seed=5, complex_=cplx)
+    out = fg.feast_interval_solve(ctx, cuda(P.A), a, b, P.m0, 8, 1e-10,
+                                  fg.feast_opts_default(variant="rfeast", anorm=P.anorm), x0=cuda(X0))
+    ref = O.feast_solve(P.A, a, b, P.m0, 8, 1e-10, X0, variant=O.RFEAST, anorm=P.anorm)
+    assert out["status"] == 0 == ref.status
+    check_against_planted(out, P)
+    np.testing.assert_allclose(out["evals"], ref.lam, atol=1e-12 * P.anorm)
+    assert abs(out["iterations"] - ref.iterations) <= 1
+    st = out["stats"]
+    assert st.rr_passes == 3 * out["iterations"]
+    assert st.rr_k_sum == 6 * P.m0 * out["iterations"]
+    assert ref.rr_dims[:3] == [12, 24, 36]
+
+
+FULL_SPAN = [(v, s, r) for v in ("xfeast", "rfeast") for s in (2, 3) for r in ("paper", "options")]
+
+
+@pytest.mark.parametrize("vname,s,reading", FULL_SPAN)
+@pytest.mark.parametrize("prec", ["f64", "mixed"])
+@pytest.mark.parametrize("cplx", [False, True])
+def test_full_span_expansion_converges_in_one_round(ctx, vname, s, reading, prec, cplx):
+    # s m0 = n: the expanded subspace of round 1 spans the whole space
+    # (block Krylov of rho(A) for XFEAST, of A for RFEAST), so Rayleigh-Ritz
+    # is exact and round 1 returns exactly the planted pairs, as in the oracle
+    n = 60
+    lam, a, b = spectrum_uniform(n, n // 8, seed=1, bulk=2.0)
+    m0 = n // s
+    P = make_problem("full", lam, a, b, m0, 8, seed=1, complex_=cplx)
+    X0 = random_subspace(n, m0, seed=12, complex_=cplx)
+    gk = dict(READINGS[reading][0])
+    if vname == "xfeast":
+        gk.pop("rfeast_expand", None)
+    out = fg.feast_interval_solve(ctx, cuda(P.A), a, b, m0, 8, 1e-10,
+                                  fg.feast_opts_default(variant=vname, s=s, prec=prec, anorm=P.anorm, max_iter=3,
+                                                        **gk), x0=cuda(X0))
+    assert out["status"] == 0 and out["iterations"] == 1
+    assert out["evals"].size == P.inside.size
+    np.testing.assert_allclose(out["evals"], P.inside, atol=1e-12 * P.anorm)
+    check_against_planted(out, P)
+
+
+@pytest.mark.parametrize("n", [2048, 4096])
+def test_full_size_paths_mixed_rfeast_edge_clusters(ctx, n):
+    # the mixed path at sizes where the GEMM tile dispatch, the split-K
+    # Rayleigh-Ritz reductions, the two-phase eigensolver and the refinement
+    # stop all take their large-n branches: the edge-cluster workload scaled
+    # to n (clusters within 1e-4 inside and outside both edges, bulk in
+    # [-50, 50]), RFEAST s = 3 with the two named readings, as benchmarked
+    sc = n / 8192
+    m_in, e_in, e_out, m0 = int(200 * sc), int(30 * sc), int(60 * sc), int(300 * sc)
+    lam, a, b = spectrum_config2(0, n=n, m_in=m_in, edge_in=e_in, edge_out=e_out)
+    P = make_problem("c2n", lam, a, b, m0, 8, seed=0, complex_=True, keep_q=True)
+    out = fg.feast_interval_solve(ctx, cuda(P.A), a, b, m0, 8, 1e-10,
+                                  fg.feast_opts_default(variant="rfeast", prec="mixed", anorm=P.anorm,
+                                                        max_iter=20, rfeast_expand=1, response_stop=1))
+    assert out["status"] == 0
+    # count exact, |dl| <= 1e-10 |l| + 1e-12 ||A||, residuals (reported and
+    # recomputed on the host), span within the Davis-Kahan bound
+    check_against_planted(out, P)
+    assert out["stats"].refine_steps > 0
+
+
+@pytest.mark.parametrize("prec", ["f64", "mixed"])
+def test_filter_closed_form_n2048(ctx, prec):
+    # rho(A) X = Q diag(rho(lambda)) Q^H X on a planted n = 2048 complex
+    # Hermitian A (Eq. 3; rho from the oracle's scalar filter), a few columns
+    lam, a, b = spectrum_config2(0, n=2048, m_in=50, edge_in=8, edge_out=15)
+    P = make_problem("f2048", lam, a, b, 8, 8, seed=0, complex_=True)
+    X = random_subspace(P.n, 6, seed=3, complex_=True)
+    Y = host(fg.feast_filter_apply(ctx, cuda(P.A), a, b, 8, cuda(X),
+                                   fg.feast_opts_default(prec=prec, anorm=P.anorm)))
+    z, w = O.contour_nodes(a, b, 8)
+    rho = O.rational_filter(P.lam, z, w)
+    ref = P.Q @ (rho[:, None] * (P.Q.conj().T @ X))
+    # forward error of the shifted solves: kappa(z_j I - A) ~ 50 / 0.06 times
+    # their backward error (FP64 LU, or refinement to 16 eps sqrt(n))
+    err = np.abs(Y - ref).max() / np.abs(X).max()
+    assert err <= 2e-10, err

@@ -204,16 +204,20 @@ def make_problem(name, lam, lmin, lmax, m0, n_c, seed=0, complex_=False, keep_q=
 
 
 def planted_matrix_torch(lam, seed, complex_=False, device="cuda:0"):
-    """A = Q diag(lam) Q^H with Q from the QR factorisation of a seeded
-    Gaussian matrix, built with torch on the GPU (large n).  Returns the
-    column-major CUDA tensor A; Q is not kept."""
+    """A = Q diag(lam) Q^H with Q from the QR factorisation of the same seeded
+    Gaussian matrix haar_unitary(n, seed + 1000) draws (numpy generator, so the
+    host can rebuild the same matrix up to rounding), factored by torch on the
+    GPU (large n).  Returns the column-major CUDA tensor A; Q is not kept."""
     import torch
 
     n = int(lam.size)
-    g = torch.Generator(device=device)
-    g.manual_seed(int(seed) + 1000)
+    rng = np.random.default_rng(int(seed) + 1000)
+    Gh = rng.standard_normal((n, n))
+    if complex_:
+        Gh = (Gh + 1j * rng.standard_normal((n, n))) / np.sqrt(2.0)
     dt = torch.complex128 if complex_ else torch.float64
-    G = torch.randn((n, n), generator=g, dtype=dt, device=device)
+    G = torch.from_numpy(Gh).to(device=device, dtype=dt)
+    del Gh
     Q, R = torch.linalg.qr(G)
     d = torch.diagonal(R)
     Q = Q * (d / d.abs())[None, :]
@@ -223,3 +227,12 @@ def planted_matrix_torch(lam, seed, complex_=False, device="cuda:0"):
     del Q
     A = 0.5 * (A + A.conj().T)
     return A.transpose(0, 1).contiguous().transpose(0, 1)
+
+
+def planted_block_host(lam, seed, rows, complex_=False):
+    """The leading rows x rows block of the matrix planted_matrix_torch builds
+    (same spectrum and Gaussian seed; Q from the host's QR, equal up to
+    rounding): Q[:rows] diag(lam) Q[:rows]^H."""
+    Q = haar_unitary(lam.size, int(seed) + 1000, complex_)[:rows]
+    B = (Q * lam[None, :]) @ Q.conj().T
+    return np.asfortranarray(0.5 * (B + B.conj().T))
