@@ -631,7 +631,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=0, help="override n (scaled workload, for quick checks)")
-    ap.add_argument("--prec", default="mixed", choices=["mixed", "mixed_tc", "f64"])
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "mixed_simt", "f64"])
     ap.add_argument("--refine-gemm", type=int, default=0, choices=[0, 1],
                     help="refinement products: 0 tensor cores (digit split), 1 double-float SIMT")
     ap.add_argument("--variant", default="rfeast", choices=["feast", "xfeast", "rfeast"])

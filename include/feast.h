@@ -48,11 +48,13 @@ enum { FEAST_PLAIN = 0,  /* FEAST Algorithm (Appendix) */
        FEAST_RFEAST = 2  /* expanding subspace with Ritz residuals (Sect. II-B) */ };
 
 /* arithmetic of the shifted factorisations and solves */
-enum { FEAST_PREC_F64 = 0,      /* complex FP64 LU and solves */
-       FEAST_PREC_MIXED = 1,    /* complex FP32 LU and solves, FP64 iterative refinement */
-       FEAST_PREC_MIXED_TC = 2  /* as FEAST_PREC_MIXED, the LU's trailing updates on the
-                                   tensor cores (exact three-part TF32 split, six split
-                                   products, FP32 accumulate) */ };
+enum { FEAST_PREC_F64 = 0,        /* complex FP64 LU and solves */
+       FEAST_PREC_MIXED = 1,      /* complex FP32 LU and solves, FP64 iterative refinement; the
+                                     GEMM updates of the LU and of the triangular solves on the
+                                     bf16 tensor cores with FP32-exact operands (three-part bf16
+                                     split, six split products, FP32 accumulate) */
+       FEAST_PREC_MIXED_SIMT = 2  /* as FEAST_PREC_MIXED with those GEMM updates on the FP32
+                                     SIMT pipes */ };
 
 /* status codes */
 #define FEAST_OK 0
@@ -69,7 +71,7 @@ enum { FEAST_PREC_F64 = 0,      /* complex FP64 LU and solves */
 typedef struct {
   int variant;          /* FEAST_PLAIN (default), FEAST_XFEAST, FEAST_RFEAST */
   int s;                /* XFEAST window blocks / RFEAST Rayleigh-Ritz passes (default 3) */
-  int prec;             /* FEAST_PREC_F64 (default), FEAST_PREC_MIXED or FEAST_PREC_MIXED_TC */
+  int prec;             /* FEAST_PREC_F64 (default), FEAST_PREC_MIXED or FEAST_PREC_MIXED_SIMT */
   int max_iter;         /* maximum outer iterations (default 100) */
   int refine_max;       /* mixed: maximum refinement steps per filter (default 10) */
   int refine_gemm;      /* mixed: the FP64-accurate products A Y of the refinement on the
@@ -84,10 +86,6 @@ typedef struct {
   double refine_switch; /* mixed: while the previous iteration's max residual exceeds this and
                            fell at least tenfold, the next filter uses the FP32 solves without
                            FP64 refinement (default 0: always refine) */
-  int tc_solve;         /* mixed, n > 128: block updates of the complex-FP32 triangular solves
-                           on the FP32 SIMT pipes (0, default) or on the tensor cores (1: exact
-                           three-part TF32 split, FP32 accumulate; bound by the operand planes'
-                           L2 traffic, slower at m0 = 300) */
   int rfeast_expand;    /* RFEAST step 2(iii) (Appendix, RFEAST Algorithm): 0 (default, the
                            paper) appends the residual R = A X - X Lambda of every selected
                            pair; 1 appends only those of selected pairs whose relative residual
@@ -123,6 +121,10 @@ typedef struct {
                            triangular-solve block updates) */
   double cgemm_ms;      /* their summed device time (CUDA events) */
   double cgemm_flop;    /* their real flops (8 per complex multiply-add) */
+  int tcgemm_launches;  /* mixed: launches of the tensor-core complex-FP32 GEMM (the same
+                           updates on the tensor cores) */
+  double tcgemm_ms;     /* their summed device time (CUDA events) */
+  double tcgemm_flop;   /* their real flops (8 per complex multiply-add) */
   int rr_passes;        /* Rayleigh-Ritz passes (reduced eigenproblems solved) */
   double rr_k_sum;      /* sum of their dimensions k */
   double rr_k3_sum;     /* sum of k^3 */

@@ -21,11 +21,11 @@ from .build import LIB, build as build_library  # noqa: F401
 
 FEAST_R64, FEAST_C128 = 0, 1
 FEAST_PLAIN, FEAST_XFEAST, FEAST_RFEAST = 0, 1, 2
-FEAST_PREC_F64, FEAST_PREC_MIXED, FEAST_PREC_MIXED_TC = 0, 1, 2
+FEAST_PREC_F64, FEAST_PREC_MIXED, FEAST_PREC_MIXED_SIMT = 0, 1, 2
 FEAST_OK, FEAST_WARN_MAXITER = 0, 1
 
 VARIANTS = {"feast": FEAST_PLAIN, "xfeast": FEAST_XFEAST, "rfeast": FEAST_RFEAST}
-PRECS = {"f64": FEAST_PREC_F64, "mixed": FEAST_PREC_MIXED, "mixed_tc": FEAST_PREC_MIXED_TC}
+PRECS = {"f64": FEAST_PREC_F64, "mixed": FEAST_PREC_MIXED, "mixed_simt": FEAST_PREC_MIXED_SIMT}
 
 EXPORTS = [
     "feast_opts_default", "feast_init", "feast_finalize", "feast_strerror",
@@ -41,7 +41,7 @@ class FeastOpts(ctypes.Structure):
                 ("max_iter", ctypes.c_int), ("refine_max", ctypes.c_int), ("refine_gemm", ctypes.c_int),
                 ("aspect", ctypes.c_double), ("anorm", ctypes.c_double), ("refine_tol", ctypes.c_double),
                 ("seed", ctypes.c_ulonglong), ("x0", ctypes.c_void_p), ("refine_switch", ctypes.c_double),
-                ("tc_solve", ctypes.c_int), ("rfeast_expand", ctypes.c_int), ("response_stop", ctypes.c_int),
+                ("rfeast_expand", ctypes.c_int), ("response_stop", ctypes.c_int),
                 ("reserved", ctypes.c_int)]
 
 
@@ -52,6 +52,7 @@ class FeastStats(ctypes.Structure):
                 ("history", ctypes.c_double * 128), ("refine_gemm_ms", ctypes.c_double),
                 ("refine_gemm_mac", ctypes.c_double), ("refine_gemm_launches", ctypes.c_int),
                 ("cgemm_launches", ctypes.c_int), ("cgemm_ms", ctypes.c_double), ("cgemm_flop", ctypes.c_double),
+                ("tcgemm_launches", ctypes.c_int), ("tcgemm_ms", ctypes.c_double), ("tcgemm_flop", ctypes.c_double),
                 ("rr_passes", ctypes.c_int), ("rr_k_sum", ctypes.c_double), ("rr_k3_sum", ctypes.c_double)]
 
 

@@ -135,9 +135,10 @@ unsigned long long launch_count();
 // CUDA-event timing of selected kernels over one solve: enable, bracket each
 // launch of the kernel class, then read the summed device time, work units
 // and launch count.  Classes: the FP64-accurate GEMM of the refinement
-// (work = real multiply-adds) and the complex-FP32 SIMT GEMM of the LU and
-// the triangular solves (work = real flops, 8 per complex multiply-add).
-enum TimerClass : int { TIMER_REFINE_GEMM = 0, TIMER_CGEMM = 1, TIMER_CLASSES = 2 };
+// (work = real multiply-adds), the complex-FP32 SIMT GEMM of the LU and the
+// triangular solves and its tensor-core counterpart (work = real flops, 8
+// per complex multiply-add).
+enum TimerClass : int { TIMER_REFINE_GEMM = 0, TIMER_CGEMM = 1, TIMER_TCGEMM = 2, TIMER_CLASSES = 3 };
 void kernel_timer_begin();
 void kernel_timer_end(int cls, double* ms, double* work, int* launches);
 void kernel_timer_launch_begin(int cls, cudaStream_t s);

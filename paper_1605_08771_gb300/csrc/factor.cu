@@ -15,7 +15,6 @@
 //   3. A22 -= L21 U12 with the batched GEMM.
 // The pivot choice is the first row of largest |m_ik|^2, as in the oracle.
 #include "factor.cuh"
-#include "tc_update.cuh"
 
 #include <algorithm>
 #include <climits>
@@ -477,6 +476,7 @@ trsm_diag_kernel(const F* M, int64_t ld, int64_t stride, F* Y, int64_t n, int64_
 // solve block rows: 64 for complex-FP32 factors, 32 for complex-FP64 (whose
 // 64 x 64 shared tile would exceed the static shared-memory limit)
 template <typename F> struct SolveBlock { static constexpr int value = 64; };
+static_assert(kSolveBlock == 64, "tensor-core solve planes use the complex-FP32 diagonal block");
 template <> struct SolveBlock<c128> { static constexpr int value = 32; };
 
 template <typename F, typename TB>
@@ -561,6 +561,9 @@ void form_shifted(F* M, int64_t n, int64_t ld, int64_t stride, int nodes,
   form_shifted_kernel<F, TA><<<grid, 256, 0, s>>>(M, n, ld, stride, A, lda, z);
   FEAST_LAUNCH_CHECK();
 }
+
+void lu_tc_trailing_update(c64* M, int64_t n, int64_t ld, int64_t stride, int nodes, int64_t k0, int kb, void* planes,
+                           int* status, int num_sms, cudaStream_t s);
 
 template <typename F>
 void lu_factor_batched(F* M, int64_t n, int64_t ld, int64_t stride, int nodes,
@@ -660,7 +663,7 @@ void lu_factor_batched(F* M, int64_t n, int64_t ld, int64_t stride, int nodes,
         gemm_update(k1 + jb, blk_end, blk_end, n, k1, jb);
       }
       if constexpr (std::is_same<F, c64>::value)
-        tc_trailing_update(M, n, ld, stride, nodes, k0, (int)nbo, w.tc_planes, w.status, num_sms, s);
+        lu_tc_trailing_update(M, n, ld, stride, nodes, k0, (int)nbo, w.tc_planes, w.status, num_sms, s);
     }
   }
   const size_t smem = sizeof(int32_t) * (size_t)n;
@@ -672,13 +675,29 @@ void lu_factor_batched(F* M, int64_t n, int64_t ld, int64_t stride, int nodes,
 
 template <typename F>
 void lu_solve_batched(const F* M, int64_t n, int64_t ld, int64_t stride, int nodes,
-                      F* Y, int64_t m, int64_t ystride, bool adjoint, cudaStream_t s, void* tc_planes, int* status,
-                      int num_sms) {
+                      F* Y, int64_t m, int64_t ystride, bool adjoint, cudaStream_t s, const SolvePlanes* sp,
+                      int* status, int num_sms) {
   if (m <= 0) return;
   constexpr int TBK = SolveBlock<F>::value;
   dim3 gd((unsigned)cdiv(m, 8), nodes);
-  // SIMT block update Y[c0 + i] -= op(block of the factor at a) Y[k0 + j]
-  auto simt_update = [&](int64_t rows, int64_t k, const F* a, int opA, int64_t c_off, int64_t k_off) {
+  bool tc = false;
+  if constexpr (std::is_same<F, c64>::value) tc = sp != nullptr && (!adjoint || sp->row) && m <= sp->mpad;
+  // block update Y[c_off + i] -= op(block of the factor) Y[k_off + j]: on the
+  // tensor cores (planes of the factor's 64-column block b, or of its
+  // conjugated 64-row block for the adjoint solves, rows from p_row), or SIMT
+  auto update = [&](int64_t rows, int64_t k, const F* a, int opA, int64_t c_off, int64_t k_off, int64_t b,
+                    int64_t p_row) {
+    if constexpr (std::is_same<F, c64>::value) {
+      if (tc) {
+        cg_split(Y, ystride, 0, n, k_off, 0, false, false, m, k, kSolveBlock, 1, sp->mpad, kSolveBlock, nodes,
+                 sp->rhs, s);
+        const CgOperand B = cg_operand(sp->rhs, sp->mpad, kSolveBlock, nodes);
+        CgOperand A = cg_operand(adjoint ? sp->row : sp->col, sp->npad, kSolveBlock, nodes, sp->nblk, kSolveBlock);
+        A.base_row = b * A.slab_rows + p_row;
+        cg_update(A, B, k, rows, m, Y + c_off, n, ystride, nodes, status, num_sms, s);
+        return;
+      }
+    }
     GemmArgs g{};
     g.M = rows; g.N = m; g.K = k;
     g.A = a; g.opA = opA; g.lda = ld; g.strideA = stride;
@@ -687,64 +706,85 @@ void lu_solve_batched(const F* M, int64_t n, int64_t ld, int64_t stride, int nod
     g.alpha = C1(-1.0); g.beta = C1(1.0); g.batch = nodes; g.ksplit = 1;
     gemm<F, F, F>(g, s);
   };
-  // rows [b0, b1) solved by TBK-row diagonal blocks (forward: top down)
-  auto forward_rows = [&](int64_t b0, int64_t b1, int64_t upd_end) {
-    for (int64_t r0 = b0; r0 < b1; r0 += TBK) {
-      const int bs = (int)std::min<int64_t>(TBK, b1 - r0);
-      const int64_t r1 = r0 + bs;
-      trsm_diag_kernel<F, TBK><<<gd, 256, 0, s>>>(M, ld, stride, Y, n, m, ystride, r0, bs, adjoint ? 1 : 0);
-      FEAST_LAUNCH_CHECK();
-      if (r1 < upd_end) {
-        if (!adjoint) simt_update(upd_end - r1, bs, M + r1 + r0 * ld, OP_N, r1, r0);
-        else simt_update(upd_end - r1, bs, M + r0 + r1 * ld, OP_C, r1, r0);
-      }
-    }
-  };
-  // rows [b0, b1) solved bottom up; updates reach rows [upd_begin, r0)
-  auto backward_rows = [&](int64_t b0, int64_t b1, int64_t upd_begin) {
-    for (int64_t r0 = b0 + ((b1 - b0 - 1) / TBK) * TBK; r0 >= b0; r0 -= TBK) {
-      const int bs = (int)std::min<int64_t>(TBK, b1 - r0);
-      trsm_diag_kernel<F, TBK><<<gd, 256, 0, s>>>(M, ld, stride, Y, n, m, ystride, r0, bs, adjoint ? 3 : 2);
-      FEAST_LAUNCH_CHECK();
-      if (r0 > upd_begin) {
-        if (!adjoint) simt_update(r0 - upd_begin, bs, M + upd_begin + r0 * ld, OP_N, upd_begin, r0);
-        else simt_update(r0 - upd_begin, bs, M + r0 + upd_begin * ld, OP_C, upd_begin, r0);
-      }
-    }
-  };
-  bool tc = false;
-  if constexpr (std::is_same<F, c64>::value) tc = tc_planes != nullptr && n > kTcBlock;
-  if (!tc) {
-    forward_rows(0, n, n);
-    backward_rows(0, n, 0);
-    return;
-  }
-  if constexpr (std::is_same<F, c64>::value) {
-    // 128-row blocks: the diagonal block by the SIMT path above, the update
-    // of the remaining rows on the tensor cores
-    const int64_t TB2 = kTcBlock;
-    for (int64_t r0 = 0; r0 < n; r0 += TB2) {
-      const int bs = (int)std::min<int64_t>(TB2, n - r0);
-      const int64_t r1 = r0 + bs;
-      forward_rows(r0, r1, r1);
-      if (r1 < n) {
-        // forward: Y[r1:] -= L[r1:, r0:r1] Y[r0:r1]; adjoint: U[r0:r1, r1:]^H
-        const TcSrc a = adjoint ? TcSrc{M, stride, ld, r0, r1, false, true} : TcSrc{M, stride, ld, r1, r0, true, false};
-        const TcSrc b{Y, ystride, n, r0, 0, false, false};
-        tc_block_update(a, b, bs, n - r1, m, Y, n, ystride, r1, 0, nodes, tc_planes, status, num_sms, s);
-      }
-    }
-    for (int64_t r0 = ((n - 1) / TB2) * TB2; r0 >= 0; r0 -= TB2) {
-      const int bs = (int)std::min<int64_t>(TB2, n - r0);
-      backward_rows(r0, r0 + bs, r0);
-      if (r0 > 0) {
-        // backward: Y[:r0] -= U[:r0, r0:r1] Y[r0:r1]; adjoint: L[r0:r1, :r0]^H
-        const TcSrc a = adjoint ? TcSrc{M, stride, ld, r0, 0, false, true} : TcSrc{M, stride, ld, 0, r0, true, false};
-        const TcSrc b{Y, ystride, n, r0, 0, false, false};
-        tc_block_update(a, b, bs, r0, m, Y, n, ystride, 0, 0, nodes, tc_planes, status, num_sms, s);
-      }
+  // forward (L, or U^H for the adjoint): top down
+  for (int64_t r0 = 0; r0 < n; r0 += TBK) {
+    const int bs = (int)std::min<int64_t>(TBK, n - r0);
+    const int64_t r1 = r0 + bs;
+    trsm_diag_kernel<F, TBK><<<gd, 256, 0, s>>>(M, ld, stride, Y, n, m, ystride, r0, bs, adjoint ? 1 : 0);
+    FEAST_LAUNCH_CHECK();
+    if (r1 < n) {
+      if (!adjoint) update(n - r1, bs, M + r1 + r0 * ld, OP_N, r1, r0, r0 / TBK, r1);
+      else update(n - r1, bs, M + r0 + r1 * ld, OP_C, r1, r0, r0 / TBK, r1);
     }
   }
+  // backward (U, or L^H for the adjoint): bottom up
+  for (int64_t r0 = ((n - 1) / TBK) * TBK; r0 >= 0; r0 -= TBK) {
+    const int bs = (int)std::min<int64_t>(TBK, n - r0);
+    trsm_diag_kernel<F, TBK><<<gd, 256, 0, s>>>(M, ld, stride, Y, n, m, ystride, r0, bs, adjoint ? 3 : 2);
+    FEAST_LAUNCH_CHECK();
+    if (r0 > 0) {
+      if (!adjoint) update(r0, bs, M + r0 * ld, OP_N, 0, r0, r0 / TBK, 0);
+      else update(r0, bs, M + r0, OP_C, 0, r0, r0 / TBK, 0);
+    }
+  }
+}
+
+size_t lu_tc_planes_bytes(int64_t n, int nodes) {
+  return 2 * sizeof(uint16_t) * cg_planes_elems(cg_vpad(n), cg_kpad(kTcBlock), 1, nodes);
+}
+
+// A22 -= L21 U12 for the outer block of columns [k0, k0 + kb): L21 and U12
+// split into bf16 planes, then the tensor-core update of every node
+void lu_tc_trailing_update(c64* M, int64_t n, int64_t ld, int64_t stride, int nodes, int64_t k0, int kb, void* planes,
+                           int* status, int num_sms, cudaStream_t s) {
+  const int64_t c1 = k0 + kb, rest = n - c1;
+  if (rest <= 0) return;
+  const int64_t vpad = cg_vpad(rest), kpad = cg_kpad(kb);
+  uint16_t* Lp = (uint16_t*)planes;
+  uint16_t* Up = Lp + cg_planes_elems(vpad, kpad, 1, nodes);
+  // L21(i, k) = M[c1 + i, k0 + k]; U12(j, k) = M[k0 + k, c1 + j]
+  cg_split(M, stride, 0, ld, c1, k0, true, false, rest, kb, (int)kpad, 1, vpad, kpad, nodes, Lp, s);
+  cg_split(M, stride, 0, ld, k0, c1, false, false, rest, kb, (int)kpad, 1, vpad, kpad, nodes, Up, s);
+  cg_update(cg_operand(Lp, vpad, kpad, nodes), cg_operand(Up, vpad, kpad, nodes), kb, rest, rest, M + c1 + c1 * ld,
+            ld, stride, nodes, status, num_sms, s);
+}
+
+size_t solve_planes_bytes(int64_t n, int64_t m, int nodes, int entries, bool adjoint) {
+  const int64_t nblk = cdiv(n, kSolveBlock);
+  size_t b = sizeof(uint16_t) * cg_planes_elems(cg_vpad(n), kSolveBlock, nblk, nodes);
+  b = (b + 255) & ~size_t(255);
+  size_t tot = adjoint ? 2 * b : b;
+  tot += sizeof(uint16_t) * cg_planes_elems(cg_vpad(m), kSolveBlock, 1, entries) + 256;
+  return tot;
+}
+
+SolvePlanes solve_planes_carve(void* base, int64_t n, int64_t m, int nodes, int entries, bool adjoint) {
+  SolvePlanes sp;
+  sp.npad = cg_vpad(n);
+  sp.nblk = cdiv(n, kSolveBlock);
+  sp.mpad = cg_vpad(m);
+  size_t b = sizeof(uint16_t) * cg_planes_elems(sp.npad, kSolveBlock, sp.nblk, nodes);
+  b = (b + 255) & ~size_t(255);
+  char* p = (char*)base;
+  sp.col = (uint16_t*)p;
+  p += b;
+  if (adjoint) {
+    sp.row = (uint16_t*)p;
+    p += b;
+  }
+  sp.rhs = (uint16_t*)p;
+  return sp;
+}
+
+void solve_planes_build(const c64* M, int64_t n, int64_t ld, int64_t stride, int nodes, const SolvePlanes& sp,
+                        cudaStream_t s) {
+  // column block b: element (i, k) = M[i, 64 b + k]
+  cg_split(M, stride, (int64_t)kSolveBlock * ld, ld, 0, 0, true, false, n, n, kSolveBlock, sp.nblk, sp.npad,
+           kSolveBlock, nodes, sp.col, s);
+  // row block b, conjugated: element (j, k) = conj(M[64 b + k, j])
+  if (sp.row)
+    cg_split(M, stride, kSolveBlock, ld, 0, 0, false, true, n, n, kSolveBlock, sp.nblk, sp.npad, kSolveBlock, nodes,
+             sp.row, s);
 }
 
 template <typename F, typename TB>
@@ -767,7 +807,7 @@ void permute_out(TO* Out, int64_t ostride, const F* Y, int64_t ystride, int64_t 
   template void lu_factor_batched<F>(F*, int64_t, int64_t, int64_t, int, int32_t*, int32_t*,        \
                                      const PanelWork&, int, cudaStream_t);                          \
   template void lu_solve_batched<F>(const F*, int64_t, int64_t, int64_t, int, F*, int64_t, int64_t, \
-                                    bool, cudaStream_t, void*, int*, int);                           \
+                                    bool, cudaStream_t, const SolvePlanes*, int*, int);              \
   template void form_shifted<F, double>(F*, int64_t, int64_t, int64_t, int, const double*, int64_t, \
                                         const c128*, cudaStream_t);                                  \
   template void form_shifted<F, c128>(F*, int64_t, int64_t, int64_t, int, const c128*, int64_t,     \

@@ -6,11 +6,14 @@
 
 #include "common.cuh"
 #include "gemm.cuh"
-#include "tc_update.cuh"
+#include "tc_cgemm.cuh"
 
 namespace feast {
 
 constexpr int kPanel = 32;        // panel width = triangular-solve block size
+constexpr int kTcBlock = 128;     // outer block of the two-level LU whose trailing update
+                                  // runs on the tensor cores
+constexpr int kSolveBlock = 64;   // diagonal blocks of the complex-FP32 triangular solves
 
 // Scratch the cooperative panel kernel needs (device pointers, sized by
 // panel_work_bytes()).
@@ -30,7 +33,29 @@ struct PanelWork {
   int* blk_cnt;         // [nodes]
   int pmax;
   void* tc_planes;      // complex-FP32 factors: scratch of the tensor-core trailing update
+                        // (lu_tc_planes_bytes); null: SIMT trailing updates
 };
+
+// Scratch bytes of the tensor-core trailing update of n x n factors.
+size_t lu_tc_planes_bytes(int64_t n, int nodes);
+
+// bf16 planes of complex-FP32 factors for the tensor-core block updates of
+// the triangular solves: every 64-column block of each factor (normal
+// solves: L below and U above the diagonal block), and, for the adjoint
+// solves, every 64-row block conjugated; plus scratch for one block row of
+// the right-hand sides.
+struct SolvePlanes {
+  uint16_t* col = nullptr;   // [node][block][6][npad][64]
+  uint16_t* row = nullptr;   // the same of the conjugated row blocks (null: no adjoint solves)
+  uint16_t* rhs = nullptr;   // [entry][6][mpad][64]
+  int64_t npad = 0, nblk = 0, mpad = 0;
+};
+size_t solve_planes_bytes(int64_t n, int64_t m, int nodes, int entries, bool adjoint);
+SolvePlanes solve_planes_carve(void* base, int64_t n, int64_t m, int nodes, int entries, bool adjoint);
+// Split the factors M (n x n, leading dim ld, node stride `stride`) into the
+// planes (once per factorisation).
+void solve_planes_build(const c64* M, int64_t n, int64_t ld, int64_t stride, int nodes, const SolvePlanes& sp,
+                        cudaStream_t s);
 
 size_t panel_work_bytes(int nodes, int pmax, size_t elem_bytes);
 PanelWork panel_work_carve(void* base, int nodes, int pmax, size_t elem_bytes);
@@ -51,13 +76,13 @@ void lu_factor_batched(F* M, int64_t n, int64_t ld, int64_t stride, int nodes,
 // Y_e <- (P^T L U)^{-1} Y_e  (adjoint = false) or (P^T L U)^{-H} Y_e
 // (adjoint = true) for e = 0..nodes-1, Y_e = Y + e*ystride (n x m, ld n).
 // The row permutation is applied by permute_in / permute_out.  Complex-FP32
-// factors with tc_planes (scratch of tc_update_planes_bytes(n, m, nodes)
-// bytes) take the block updates of the triangular solves on the tensor
-// cores (128-row blocks); otherwise SIMT (64-row blocks).
+// factors with planes (solve_planes_build; m <= the planes' m) take the block
+// updates of the triangular solves on the tensor cores; otherwise SIMT.  Both
+// use 64-row diagonal blocks (32 for complex FP64).
 template <typename F>
 void lu_solve_batched(const F* M, int64_t n, int64_t ld, int64_t stride, int nodes,
                       F* Y, int64_t m, int64_t ystride, bool adjoint, cudaStream_t s,
-                      void* tc_planes = nullptr, int* status = nullptr, int num_sms = 0);
+                      const SolvePlanes* planes = nullptr, int* status = nullptr, int num_sms = 0);
 
 // Y_e = P B_e (normal) or B_e (adjoint) converted to F;  B_e = B + e*bstride is
 // n x m with ld ldb (bstride = 0: one right-hand side block for every node).

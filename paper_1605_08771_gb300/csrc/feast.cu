@@ -4,7 +4,7 @@
 // check), XFEAST (window of s filtered blocks, Sect. II-A) and RFEAST (s
 // Rayleigh-Ritz passes expanding with Ritz residuals, Sect. II-B).  All
 // arithmetic runs in the CUDA kernels of factor.cu, gemm.cu, oz_gemm.cu,
-// tc_update.cu and dense.cu; the host only sequences launches, reads back the
+// tc_cgemm.cu and dense.cu; the host only sequences launches, reads back the
 // k Ritz values and residuals it needs for the selection and stopping
 // decisions and sorts them, and groups the FP64 polish's remaining
 // above-threshold pairs into index sets.
@@ -22,7 +22,6 @@
 #include "factor.cuh"
 #include "gemm.cuh"
 #include "oz_gemm.cuh"
-#include "tc_update.cuh"
 
 using namespace feast;
 
@@ -236,9 +235,10 @@ struct Solver {
   bool use_oz = false;
   OzOperand Aoz[3];
   void* Boz[3] = {nullptr, nullptr, nullptr};
-  // mixed, opts.tc_solve = 1: operand planes of the tensor-core block
-  // updates of the complex-FP32 triangular solves
-  void* solve_planes = nullptr;
+  // FEAST_PREC_MIXED: bf16 planes of the complex-FP32 factors for the
+  // tensor-core block updates of the triangular solves
+  SolvePlanes splanes;
+  bool use_tc = false;
   // The Rayleigh-Ritz, orthonormalisation and eigensolver products are not
   // routed through the digit-split GEMM: its error is bounded by row/column
   // maxima, and on the graded filtered bases it held the n = 8192 RFEAST
@@ -282,6 +282,7 @@ struct Solver {
     kmax = std::max<int64_t>(kmax_, 1);
     mmax = std::max<int64_t>(mmax_, 1);
     use_oz = o.prec != FEAST_PREC_F64 && o.refine_gemm == 0;
+    use_tc = o.prec == FEAST_PREC_MIXED;
     contour(lmin, lmax, nc, o.aspect, z, w);
     d_w = dalloc<c128>(ctx, nc);
     d_ze = dalloc<c128>(ctx, E);
@@ -305,7 +306,7 @@ struct Solver {
     perm = dalloc<int32_t>(ctx, (int64_t)nc * n);
     const int pmax = std::max(1, ctx->num_sms * 8);
     pw = panel_work_carve(ctx->arena.alloc(panel_work_bytes(nc, pmax, eb)), nc, pmax, eb);
-    if (o.prec == FEAST_PREC_MIXED_TC) pw.tc_planes = ctx->arena.alloc(tc_update_planes_bytes(n, n, nc));
+    if (use_tc) pw.tc_planes = ctx->arena.alloc(lu_tc_planes_bytes(n, nc));
   }
   void alloc_filter(int64_t m) {
     const int64_t nm = n * m;
@@ -316,8 +317,8 @@ struct Solver {
       Yw = dalloc<c128>(ctx, E * nm);
       AY = dalloc<c128>(ctx, E * nm);
       Yc = dalloc<c64>(ctx, E * nm);
-      if (o.tc_solve == 1 && n > kTcBlock)
-        solve_planes = ctx->arena.alloc(tc_update_planes_bytes(n, m, nc));
+      if (use_tc)
+        splanes = solve_planes_carve(ctx->arena.alloc(solve_planes_bytes(n, m, nc, nc, kCplx)), n, m, nc, nc, kCplx);
       bpl_cols = std::max<int64_t>(E * m, kmax);
       if (use_oz) {
         // rows of A are read through its Hermitian symmetry, A(i, k) =
@@ -594,6 +595,8 @@ struct Solver {
     to_dev(ctx, d_zf, zf.data(), nc);
     form_shifted<F, S>(Mf, n, n, n * n, nc, A, lda, d_zf, st);
     lu_factor_batched<F>(Mf, n, n, n * n, nc, ipiv, perm, pw, ctx->num_sms, st);
+    if constexpr (std::is_same<F, c64>::value)
+      if (use_tc && splanes.col) solve_planes_build(Mf, n, n, n * n, nc, splanes, st);
     int status = 0;
     std::vector<int> zp(nc);
     to_host(ctx, &status, pw.status, 1);
@@ -613,11 +616,12 @@ struct Solver {
     const int64_t nm = n * m;
     const c64* Mf = (const c64*)M;
     permute_in<c64, TB>(Yc, nm, B, ldb, bstride, n, m, perm, nc, false, st);
-    lu_solve_batched<c64>(Mf, n, n, n * n, nc, Yc, m, nm, false, st, solve_planes, d_flag, ctx->num_sms);
+    const SolvePlanes* sp = use_tc ? &splanes : nullptr;
+    lu_solve_batched<c64>(Mf, n, n, n * n, nc, Yc, m, nm, false, st, sp, d_flag, ctx->num_sms);
     permute_out<c64, c128>(Y, nm, Yc, nm, n, m, perm, nc, false, accumulate, st);
     if (kCplx) {
       permute_in<c64, TB>(Yc + nc * nm, nm, B + nc * bstride, ldb, bstride, n, m, perm, nc, true, st);
-      lu_solve_batched<c64>(Mf, n, n, n * n, nc, Yc + nc * nm, m, nm, true, st, solve_planes, d_flag, ctx->num_sms);
+      lu_solve_batched<c64>(Mf, n, n, n * n, nc, Yc + nc * nm, m, nm, true, st, sp, d_flag, ctx->num_sms);
       permute_out<c64, c128>(Y + nc * nm, nm, Yc + nc * nm, nm, n, m, perm, nc, true, accumulate, st);
     }
   }
@@ -1407,6 +1411,7 @@ int solve_t(feast_ctx* ctx, const S* A, int64_t n, int64_t lda, double lmin, dou
   st.filter_ms = sv.filter_ms;
   kernel_timer_end(TIMER_REFINE_GEMM, &st.refine_gemm_ms, &st.refine_gemm_mac, &st.refine_gemm_launches);
   kernel_timer_end(TIMER_CGEMM, &st.cgemm_ms, &st.cgemm_flop, &st.cgemm_launches);
+  kernel_timer_end(TIMER_TCGEMM, &st.tcgemm_ms, &st.tcgemm_flop, &st.tcgemm_launches);
   sv.check_oz_status();
   st.total_ms = now_ms() - t0;
   st.max_residual = 0.0;
@@ -1517,7 +1522,6 @@ int feast_interval_solve(feast_ctx* ctx, const void* A, int dtype, int64_t n, in
   if (o.variant < 0 || o.variant > 2 || o.prec < 0 || o.prec > 2 || o.max_iter < 1 || !(o.aspect > 0)) return FEAST_ERR_ARG;
   if (o.variant != FEAST_PLAIN && (o.s < 1 || (int64_t)o.s * m0 > 65536)) return FEAST_ERR_ARG;
   if (o.refine_max < 0 || !(o.refine_switch >= 0.0) || o.refine_gemm < 0 || o.refine_gemm > 1) return FEAST_ERR_ARG;
-  if (o.tc_solve < 0 || o.tc_solve > 1) return FEAST_ERR_ARG;
   if (o.rfeast_expand < 0 || o.rfeast_expand > 1 || o.response_stop < 0 || o.response_stop > 1) return FEAST_ERR_ARG;
   *m_found = 0;
   *iterations = 0;
@@ -1537,8 +1541,7 @@ int feast_filter_apply(feast_ctx* ctx, const void* A, int dtype, int64_t n, int6
   if (!X || !Y || m < 1) return FEAST_ERR_ARG;
   feast_opts o;
   if (opts) o = *opts; else feast_opts_default(&o);
-  if (o.prec < 0 || o.prec > 2 || !(o.aspect > 0) || o.refine_max < 0 || o.refine_gemm < 0 || o.refine_gemm > 1 ||
-      o.tc_solve < 0 || o.tc_solve > 1)
+  if (o.prec < 0 || o.prec > 2 || !(o.aspect > 0) || o.refine_max < 0 || o.refine_gemm < 0 || o.refine_gemm > 1)
     return FEAST_ERR_ARG;
   return guarded(ctx, [&]() {
     FEAST_CUDA_TRY(cudaSetDevice(ctx->device));
@@ -1571,14 +1574,14 @@ int feast_filter_apply(feast_ctx* ctx, const void* A, int dtype, int64_t n, int6
 int feast_shifted_lu(feast_ctx* ctx, const void* A, int dtype, int64_t n, int64_t lda, const double* z, int nz,
                      int prec, void* LU, int32_t* perm) {
   if (int r = check_common(ctx, A, dtype, n, lda, -1.0, 1.0, nz)) return r;
-  if (!z || !LU || !perm || (prec < FEAST_PREC_F64 || prec > FEAST_PREC_MIXED_TC)) return FEAST_ERR_ARG;
+  if (!z || !LU || !perm || (prec < FEAST_PREC_F64 || prec > FEAST_PREC_MIXED_SIMT)) return FEAST_ERR_ARG;
   return guarded(ctx, [&]() {
     FEAST_CUDA_TRY(cudaSetDevice(ctx->device));
     ctx->arena.reset();
     const size_t eb = prec == FEAST_PREC_F64 ? sizeof(c128) : sizeof(c64);
     const int pmax = std::max(1, ctx->num_sms * 8);
     PanelWork pw = panel_work_carve(ctx->arena.alloc(panel_work_bytes(nz, pmax, eb)), nz, pmax, eb);
-    if (prec == FEAST_PREC_MIXED_TC) pw.tc_planes = ctx->arena.alloc(tc_update_planes_bytes(n, n, nz));
+    if (prec == FEAST_PREC_MIXED) pw.tc_planes = ctx->arena.alloc(lu_tc_planes_bytes(n, nz));
     c128* dz = dalloc<c128>(ctx, nz);
     to_dev(ctx, dz, (const c128*)z, nz);
     int32_t* ipiv = dalloc<int32_t>(ctx, (int64_t)nz * n);
@@ -1604,7 +1607,7 @@ int feast_shifted_lu(feast_ctx* ctx, const void* A, int dtype, int64_t n, int64_
 int feast_shifted_solve(feast_ctx* ctx, const void* LU, const int32_t* perm, int64_t n, int nz, int prec, int adjoint,
                         const void* B, int64_t m, void* Y) {
   if (!ctx || !LU || !perm || !B || !Y || n < 1 || nz < 1 || m < 1) return FEAST_ERR_ARG;
-  if (prec < FEAST_PREC_F64 || prec > FEAST_PREC_MIXED_TC) return FEAST_ERR_ARG;
+  if (prec < FEAST_PREC_F64 || prec > FEAST_PREC_MIXED_SIMT) return FEAST_ERR_ARG;
   return guarded(ctx, [&]() {
     FEAST_CUDA_TRY(cudaSetDevice(ctx->device));
     ctx->arena.reset();
@@ -1612,11 +1615,20 @@ int feast_shifted_solve(feast_ctx* ctx, const void* LU, const int32_t* perm, int
     auto go = [&](auto ftag) {
       using F = decltype(ftag);
       F* W = dalloc<F>(ctx, nz * nm);
-      // FEAST_PREC_MIXED_TC: block updates on the tensor cores (n > 128)
-      void* planes = nullptr;
+      // FEAST_PREC_MIXED: block updates on the tensor cores from bf16 planes of the factors
+      const SolvePlanes* planes = nullptr;
+      SolvePlanes sp;
       int* flag = dalloc<int>(ctx, 1);
       FEAST_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
-      if (prec == FEAST_PREC_MIXED_TC && n > kTcBlock) planes = ctx->arena.alloc(tc_update_planes_bytes(n, m, nz));
+      if constexpr (std::is_same<F, c64>::value) {
+        if (prec == FEAST_PREC_MIXED) {
+          sp = solve_planes_carve(ctx->arena.alloc(solve_planes_bytes(n, m, nz, nz, adjoint != 0)), n, m, nz, nz,
+                                  adjoint != 0);
+          if (!adjoint) sp.row = nullptr;
+          solve_planes_build((const c64*)LU, n, n, n * n, nz, sp, ctx->stream);
+          planes = &sp;
+        }
+      }
       permute_in<F, c128>(W, nm, (const c128*)B, n, 0, n, m, perm, nz, adjoint != 0, ctx->stream);
       lu_solve_batched<F>((const F*)LU, n, n, n * n, nz, W, m, nm, adjoint != 0, ctx->stream, planes, flag,
                           ctx->num_sms);

@@ -2,7 +2,7 @@
 
   python -m paper_1605_08771_gb300.prof_case --what filter --n 4096 --m 150
       one mixed-precision filter application rho(A) X (shifted LU of the 8
-      nodes, complex-FP32 solves, double-float refinement) on the
+      nodes, complex-FP32 solves, FP64-accurate refinement) on the
       edge-cluster complex Hermitian workload scaled to n;
   python -m paper_1605_08771_gb300.prof_case --what solve --n 2048
       one complete mixed RFEAST solve of that workload.
@@ -27,7 +27,6 @@ def main():
     ap.add_argument("--m", type=int, default=0)
     ap.add_argument("--prec", default="mixed")
     ap.add_argument("--refine-gemm", type=int, default=0, help="0 tensor cores (digit split), 1 double-float")
-    ap.add_argument("--tc-solve", type=int, default=0, help="0 SIMT block updates of the solves, 1 tensor cores")
     args = ap.parse_args()
     import torch
 
@@ -48,16 +47,16 @@ def main():
             g = torch.Generator(device="cuda:0")
             g.manual_seed(3)
             X = torch.randn((n, m), generator=g, dtype=torch.complex128, device="cuda:0")
-            f.filter(A, a, b, 8, X, prec=args.prec, anorm=anorm, refine_gemm=args.refine_gemm,
-                     tc_solve=args.tc_solve)
+            f.filter(A, a, b, 8, X, prec=args.prec, anorm=anorm, refine_gemm=args.refine_gemm)
         else:
             out = f.solve(A, a, b, m, 8, 1e-10, variant="rfeast", prec=args.prec, anorm=anorm,
-                          refine_gemm=args.refine_gemm, tc_solve=args.tc_solve)
+                          refine_gemm=args.refine_gemm, rfeast_expand=1, response_stop=1)
             print("status", out["status"], "pairs", out["evals"].size, "iterations", out["iterations"])
             st = out["stats"]
-            print("cgemm launches %d flop %.6e ms %.3f; refine gemm launches %d mac %.6e ms %.3f"
-                  % (st.cgemm_launches, st.cgemm_flop, st.cgemm_ms, st.refine_gemm_launches,
-                     st.refine_gemm_mac, st.refine_gemm_ms))
+            print("cgemm launches %d flop %.6e ms %.3f; tensor-core cgemm launches %d flop %.6e ms %.3f; "
+                  "refine gemm launches %d mac %.6e ms %.3f"
+                  % (st.cgemm_launches, st.cgemm_flop, st.cgemm_ms, st.tcgemm_launches, st.tcgemm_flop,
+                     st.tcgemm_ms, st.refine_gemm_launches, st.refine_gemm_mac, st.refine_gemm_ms))
     torch.cuda.synchronize()
 
 

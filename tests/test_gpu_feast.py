@@ -2,14 +2,19 @@
 oracle and with the planted spectra: eigenvalue count exact, eigenvalues to
 1e-10 relative, residuals <= 1e-10 relative to ||A||_2, eigenvector spans;
 all three variants, both precisions; edge cases."""
+import json
+import os
+
 import numpy as np
 import pytest
 
 import oracle as O
 import paper_1605_08771_gb300 as fg
 from gpu_common import cuda, ctx, host  # noqa: F401
-from workloads import (make_problem, random_subspace, spectrum_config1, spectrum_config2,
+from workloads import (make_problem, random_subspace, spectrum_config1, spectrum_config2, spectrum_paper,
                        spectrum_uniform)
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_setups.json")
 
 pytestmark = pytest.mark.gpu
 VARIANTS = [("feast", O.PLAIN), ("xfeast", O.XFEAST), ("rfeast", O.RFEAST)]
@@ -34,7 +39,7 @@ def check_against_planted(out, P, tol=1e-10):
 
 @pytest.mark.parametrize("vname,vor", VARIANTS)
 @pytest.mark.parametrize("cplx", [False, True])
-@pytest.mark.parametrize("prec", ["f64", "mixed", "mixed_tc"])
+@pytest.mark.parametrize("prec", ["f64", "mixed", "mixed_simt"])
 def test_small_planted_vs_oracle(ctx, vname, vor, cplx, prec):
     lam, a, b = spectrum_uniform(90, 8, seed=3, bulk=10.0)
     P = make_problem("s", lam, a, b, 12, 8, seed=3, complex_=cplx)
@@ -58,14 +63,17 @@ READINGS = {"paper": ({}, {}),
 
 
 @pytest.mark.parametrize("vname,vor", VARIANTS)
-@pytest.mark.parametrize("reading", ["paper", "options"])
-def test_n500_workload_vs_oracle(ctx, vname, vor, reading):
+def test_n500_workload_vs_oracle(ctx, vname, vor):
     # n = 500 real symmetric, 40 eigenvalues in [-1, 1] (5 within 1e-3 of each
-    # edge), n_c = 8, m0 = 60, tol 1e-10, FP64
-    if vor == O.PLAIN and reading == "options":
-        pytest.skip("plain FEAST has no options")
-    gk, ok = READINGS[reading]
+    # edge), 460 on both sides of I; n_c = 8, m0 = 60, tol 1e-10, FP64.  On a
+    # two-sided spectrum the expanded variants meet spurious in-I pairs
+    # (mixtures of eigenvectors from both sides) that the paper's step-3
+    # checks alone may never clear, so XFEAST and RFEAST run with the two
+    # named options here; the paper's text is checked on its own one-sided
+    # spectra below
+    gk, ok = READINGS["options"] if vor != O.PLAIN else ({}, {})
     if vor == O.XFEAST:
+        gk = {k: v for k, v in gk.items() if k != "rfeast_expand"}
         ok = {k: v for k, v in ok.items() if k != "expand"}
     lam, a, b = spectrum_config1(0)
     P = make_problem("c1", lam, a, b, 60, 8, seed=0)
@@ -77,11 +85,38 @@ def test_n500_workload_vs_oracle(ctx, vname, vor, reading):
     ref = O.feast_solve(P.A, a, b, 60, 8, 1e-10, X0, variant=vor, anorm=P.anorm, **ok)
     np.testing.assert_allclose(out["evals"], ref.lam, atol=1e-12 * P.anorm)
     if vor == O.PLAIN:
-        # the expanded variants on a spectrum with eigenvalues on both sides of
-        # I stop when rounding-born spurious pairs leave their stopping set:
-        # their round counts vary with rounding (x86 vs Arm oracle runs
-        # differ), so only plain FEAST's is pinned
+        # the expanded variants' round counts on a two-sided spectrum vary
+        # with rounding (x86 vs Arm oracle runs differ): only plain FEAST's
+        # is pinned
         assert abs(out["iterations"] - ref.iterations) <= 1
+
+
+@pytest.mark.parametrize("kind", ["sparse", "dense"])
+@pytest.mark.parametrize("vname,vor", VARIANTS[1:])
+def test_paper_spectra_literal_variants_vs_oracle(ctx, kind, vname, vor):
+    # the paper's n = 545 "Sparse" and "Dense" spectra (Sect. III; 50
+    # eigenvalues in [-1, 1], the other 495 above I), n_c = 8, m0 = 51, with
+    # XFEAST and RFEAST exactly as the Appendix states them (every selected
+    # residual appended, step-3 checks alone): GPU and oracle converge to the
+    # planted pairs in the same number of rounds (+-1; +-2 on Dense), and on
+    # Dense the expanded variant needs fewer right-hand sides than FEAST
+    g = json.load(open(GOLDEN))["fig1_fig2_matrices"]
+    lam, a, b = spectrum_paper(kind, seed=0, n=g["n"], m_in=g["inside"])
+    m0 = g["m0_expanded_variants"]
+    P = make_problem(kind, lam, a, b, m0, 8, seed=0)
+    X0 = random_subspace(P.n, m0, seed=1)
+    F = O.factor_shifts(P.A, a, b, 8)
+    out = fg.feast_interval_solve(ctx, cuda(P.A), a, b, m0, 8, 1e-10,
+                                  fg.feast_opts_default(variant=vname, anorm=P.anorm), x0=cuda(X0))
+    ref = O.feast_solve(P.A, a, b, m0, 8, 1e-10, X0, variant=vor, anorm=P.anorm, factors=F)
+    assert out["status"] == 0 == ref.status
+    check_against_planted(out, P)
+    np.testing.assert_allclose(out["evals"], ref.lam, atol=1e-12 * P.anorm)
+    assert abs(out["iterations"] - ref.iterations) <= (2 if kind == "dense" else 1)
+    if kind == "dense":
+        plain = fg.feast_interval_solve(ctx, cuda(P.A), a, b, m0, 8, 1e-10,
+                                        fg.feast_opts_default(anorm=P.anorm), x0=cuda(X0))
+        assert out["stats"].filters < plain["stats"].filters
 
 
 @pytest.mark.parametrize("prec", ["f64", "mixed"])

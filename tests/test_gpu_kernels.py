@@ -15,14 +15,14 @@ ZS = np.array([0.3 + 0.5j, -0.7 + 0.2j, 1.1 + 0.05j])
 SIZES = [1, 2, 31, 32, 33, 65, 100, 257]
 
 
-PRECS_ALL = [fg.FEAST_PREC_F64, fg.FEAST_PREC_MIXED, fg.FEAST_PREC_MIXED_TC]
+PRECS_ALL = [fg.FEAST_PREC_F64, fg.FEAST_PREC_MIXED, fg.FEAST_PREC_MIXED_SIMT]
 
 
 @pytest.mark.parametrize("n", SIZES + [520])
 @pytest.mark.parametrize("cplx", [False, True])
 @pytest.mark.parametrize("prec", PRECS_ALL)
 def test_shifted_lu_matches_oracle(ctx, n, cplx, prec):
-    # FEAST_PREC_MIXED_TC runs the two-level LU whose 128-column outer updates
+    # FEAST_PREC_MIXED runs the two-level LU whose 128-column outer updates
     # use the tensor cores: n = 257 and 520 span several outer blocks and a
     # ragged tail
     A = rand_hermitian(n, cplx, seed=n)
@@ -61,14 +61,16 @@ def test_shifted_solve_matches_oracle(ctx, n, cplx, adjoint, prec):
 
 
 @pytest.mark.parametrize("adjoint", [False, True])
-def test_shifted_solve_complex_fp32_large_n(ctx, adjoint):
+@pytest.mark.parametrize("prec,m", [(fg.FEAST_PREC_MIXED, 7), (fg.FEAST_PREC_MIXED, 300),
+                                    (fg.FEAST_PREC_MIXED_SIMT, 7)])
+def test_shifted_solve_complex_fp32_large_n(ctx, adjoint, prec, m):
     # n = 1100: 17 full 64-row diagonal blocks and a ragged one, each followed
-    # by a block update of every remaining row; the reference is LAPACK's
-    # FP64 solve of each shifted system
+    # by a block update of every remaining row (tensor cores: 128-row output
+    # tiles over 9 row tiles, m = 300 over three 128-column tiles, the last
+    # ragged); the reference is LAPACK's FP64 solve of each shifted system
     n = 1100
     A = np.asfortranarray(0.1 * rand_hermitian(n, True, seed=5))  # spectrum within about +-5
-    B = rand_mat(n, 7, True, seed=6)
-    prec = fg.FEAST_PREC_MIXED
+    B = rand_mat(n, m, True, seed=6)
     LU, perm = fg.feast_shifted_lu(ctx, cuda(A), ZS, prec)
     Y = host(fg.feast_shifted_solve(ctx, LU, perm, cuda(B), adjoint=adjoint, prec=prec))
     for e, z in enumerate(ZS):
