@@ -507,6 +507,34 @@ __global__ void permute_out_kernel(TO* Out, int64_t ostride, const F* Y, int64_t
   }
 }
 
+__global__ void invert_perm_kernel(const int32_t* perm, int32_t* pinv, int64_t n) {
+  const int64_t b = blockIdx.y;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    pinv[b * n + perm[b * n + i]] = (int32_t)i;
+}
+
+template <typename S, typename F>
+__global__ void solve_accumulate_kernel(S* Xf, int64_t ldx, const c128* base, const F* Yn, const F* Ya, int64_t n,
+                                        int64_t m, int nc, const int32_t* pinv, const c128* w) {
+  const int64_t nm = n * m;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nm; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t % n, c = t / n;
+    c128 acc{0.0, 0.0};
+    for (int e = 0; e < nc; ++e) {
+      c128 z = cvt<c128>(Yn[(int64_t)e * nm + t]);
+      if (base) z = z + base[(int64_t)e * nm + t];
+      acc = acc + w[e] * z;
+      if constexpr (is_cx<S>::value) {
+        c128 za = cvt<c128>(Ya[(int64_t)e * nm + pinv[(int64_t)e * n + i] + c * n]);
+        if (base) za = za + base[(int64_t)(nc + e) * nm + t];
+        acc = acc + conj(w[e]) * za;
+      }
+    }
+    if constexpr (is_cx<S>::value) Xf[i + c * ldx] = acc;
+    else Xf[i + c * ldx] = 2.0 * acc.re;
+  }
+}
+
 inline unsigned grid1d(int64_t total, int threads = 256) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(total, threads), 8192));
 }
@@ -802,6 +830,28 @@ void permute_out(TO* Out, int64_t ostride, const F* Y, int64_t ystride, int64_t 
   permute_out_kernel<F, TO><<<grid, 256, 0, s>>>(Out, ostride, Y, ystride, n, m, perm, adjoint, accumulate);
   FEAST_LAUNCH_CHECK();
 }
+
+void invert_perm(const int32_t* perm, int32_t* pinv, int64_t n, int nodes, cudaStream_t s) {
+  dim3 grid(grid1d(n), nodes);
+  invert_perm_kernel<<<grid, 256, 0, s>>>(perm, pinv, n);
+  FEAST_LAUNCH_CHECK();
+}
+
+template <typename S, typename F>
+void solve_accumulate(S* Xf, int64_t ldx, const c128* base, const F* Yn, const F* Ya, int64_t n, int64_t m, int nc,
+                      const int32_t* pinv, const c128* w, cudaStream_t s) {
+  solve_accumulate_kernel<S, F><<<grid1d(n * m), 256, 0, s>>>(Xf, ldx, base, Yn, Ya, n, m, nc, pinv, w);
+  FEAST_LAUNCH_CHECK();
+}
+
+template void solve_accumulate<double, c64>(double*, int64_t, const c128*, const c64*, const c64*, int64_t, int64_t,
+                                            int, const int32_t*, const c128*, cudaStream_t);
+template void solve_accumulate<c128, c64>(c128*, int64_t, const c128*, const c64*, const c64*, int64_t, int64_t, int,
+                                          const int32_t*, const c128*, cudaStream_t);
+template void solve_accumulate<double, c128>(double*, int64_t, const c128*, const c128*, const c128*, int64_t,
+                                             int64_t, int, const int32_t*, const c128*, cudaStream_t);
+template void solve_accumulate<c128, c128>(c128*, int64_t, const c128*, const c128*, const c128*, int64_t, int64_t,
+                                           int, const int32_t*, const c128*, cudaStream_t);
 
 #define INST_F(F)                                                                                    \
   template void lu_factor_batched<F>(F*, int64_t, int64_t, int64_t, int, int32_t*, int32_t*,        \

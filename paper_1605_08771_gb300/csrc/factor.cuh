@@ -96,4 +96,18 @@ template <typename F, typename TO>
 void permute_out(TO* Out, int64_t ostride, const F* Y, int64_t ystride, int64_t n, int64_t m,
                  const int32_t* perm, int nodes, bool adjoint, bool accumulate, cudaStream_t s);
 
+// pinv[e n + perm[e n + i]] = i for every node e.
+void invert_perm(const int32_t* perm, int32_t* pinv, int64_t n, int nodes, cudaStream_t s);
+
+// The weighted accumulation of Eq. 3 fused with the output step of the last
+// solves: with Z_e = base_e + Yn_e (normal solves, natural row order) and
+// Z'_e = base_{nc+e} + P_e^T Ya_e (adjoint solves; P_e^T applied through
+// pinv), Xf = sum_e 2 Re(w_e Z_e) for real S, or sum_e w_e Z_e + conj(w_e) Z'_e
+// for complex S.  base (complex FP64, E = nc or 2 nc entries of n x m, ld n)
+// may be null; Yn, Ya: nc entries of n x m (ld n) of the solve type F; Ya is
+// unused for real S.
+template <typename S, typename F>
+void solve_accumulate(S* Xf, int64_t ldx, const c128* base, const F* Yn, const F* Ya, int64_t n, int64_t m, int nc,
+                      const int32_t* pinv, const c128* w, cudaStream_t s);
+
 }  // namespace feast

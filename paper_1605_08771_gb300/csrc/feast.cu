@@ -188,6 +188,7 @@ struct Solver {
   void* M = nullptr;
   int32_t* ipiv = nullptr;
   int32_t* perm = nullptr;
+  int32_t* pinv = nullptr;   // inverse row permutations (adjoint solves' output step)
   PanelWork pw{};
   CoopWork cw{};
   int64_t kmax = 0, mmax = 0;
@@ -304,6 +305,7 @@ struct Solver {
     M = ctx->arena.alloc(eb * (size_t)nc * n * n);
     ipiv = dalloc<int32_t>(ctx, (int64_t)nc * n);
     perm = dalloc<int32_t>(ctx, (int64_t)nc * n);
+    pinv = dalloc<int32_t>(ctx, (int64_t)nc * n);
     const int pmax = std::max(1, ctx->num_sms * 8);
     pw = panel_work_carve(ctx->arena.alloc(panel_work_bytes(nc, pmax, eb)), nc, pmax, eb);
     if (use_tc) pw.tc_planes = ctx->arena.alloc(lu_tc_planes_bytes(n, nc));
@@ -595,6 +597,7 @@ struct Solver {
     to_dev(ctx, d_zf, zf.data(), nc);
     form_shifted<F, S>(Mf, n, n, n * n, nc, A, lda, d_zf, st);
     lu_factor_batched<F>(Mf, n, n, n * n, nc, ipiv, perm, pw, ctx->num_sms, st);
+    invert_perm(perm, pinv, n, nc, st);
     if constexpr (std::is_same<F, c64>::value)
       if (use_tc && splanes.col) solve_planes_build(Mf, n, n, n * n, nc, splanes, st);
     int status = 0;
@@ -611,19 +614,25 @@ struct Solver {
   }
 
   // ---- filter: Xf = rho(A) X (Eq. 3) ----
+  // the low-precision solves of both half-contours into Yc (before the
+  // adjoint solves' output permutation)
   template <typename TB>
-  void solve_lowp(const TB* B, int64_t ldb, int64_t bstride, int64_t m, bool accumulate) {
+  void solve_lowp_core(const TB* B, int64_t ldb, int64_t bstride, int64_t m) {
     const int64_t nm = n * m;
     const c64* Mf = (const c64*)M;
-    permute_in<c64, TB>(Yc, nm, B, ldb, bstride, n, m, perm, nc, false, st);
     const SolvePlanes* sp = use_tc ? &splanes : nullptr;
+    permute_in<c64, TB>(Yc, nm, B, ldb, bstride, n, m, perm, nc, false, st);
     lu_solve_batched<c64>(Mf, n, n, n * n, nc, Yc, m, nm, false, st, sp, d_flag, ctx->num_sms);
-    permute_out<c64, c128>(Y, nm, Yc, nm, n, m, perm, nc, false, accumulate, st);
     if (kCplx) {
       permute_in<c64, TB>(Yc + nc * nm, nm, B + nc * bstride, ldb, bstride, n, m, perm, nc, true, st);
       lu_solve_batched<c64>(Mf, n, n, n * n, nc, Yc + nc * nm, m, nm, true, st, sp, d_flag, ctx->num_sms);
-      permute_out<c64, c128>(Y + nc * nm, nm, Yc + nc * nm, nm, n, m, perm, nc, true, accumulate, st);
     }
+  }
+  // Y (+)= the solves' outputs in natural row order, in FP64
+  void lowp_out(int64_t m, bool accumulate) {
+    const int64_t nm = n * m;
+    permute_out<c64, c128>(Y, nm, Yc, nm, n, m, perm, nc, false, accumulate, st);
+    if (kCplx) permute_out<c64, c128>(Y + nc * nm, nm, Yc + nc * nm, nm, n, m, perm, nc, true, accumulate, st);
   }
 
   double filter_ms = 0.0;
@@ -634,6 +643,9 @@ struct Solver {
     check_oz_status();
     filter_ms += now_ms() - t0;
   }
+  // Xf = sum of the weighted solves (Eq. 3).  The weighted accumulation is
+  // fused with the output step of the last solves (solve_accumulate) except
+  // when the refinement ends on a residual check, whose Y is final already.
   void filter_body(const S* X, int64_t m, S* Xf) {
     const int64_t nm = n * m;
     if (o.prec == FEAST_PREC_F64) {
@@ -643,65 +655,72 @@ struct Solver {
       if (kCplx) {
         permute_in<c128, S>(Yw, nm, X, n, 0, n, m, perm, nc, true, st);
         lu_solve_batched<c128>(Mf, n, n, n * n, nc, Yw, m, nm, true, st);
-        permute_out<c128, c128>(Y + nc * nm, nm, Yw, nm, n, m, perm, nc, true, false, st);
       }
-    } else {
-      phase("c64 solves", [&] { solve_lowp<S>(X, n, 0, m, false); });
-      if (!refine_now) {
-        accumulate_filter<S>(Xf, n, Y, n, m, nc, d_w, st);
+      solve_accumulate<S, c128>(Xf, n, nullptr, Y, kCplx ? Yw : Y, n, m, nc, pinv, d_w, st);
+      return;
+    }
+    phase("c64 solves", [&] { solve_lowp_core<S>(X, n, 0, m); });
+    if (!refine_now) {
+      solve_accumulate<S, c64>(Xf, n, nullptr, Yc, Yc + (kCplx ? nc * nm : 0), n, m, nc, pinv, d_w, st);
+      return;
+    }
+    phase("c64 solves", [&] { lowp_out(m, false); });
+    // default target 16 eps sqrt(n): just above the accuracy floor of the
+    // double-float residual (about 2^-48 relative per product)
+    const double rtol = o.refine_tol > 0 ? o.refine_tol : 16.0 * 2.220446049250313e-16 * std::sqrt((double)n);
+    std::vector<double> en(2 * E), prev(E, -1.0);
+    double worst_prev = -1.0;
+    // entries whose residual met the target drop out of later steps: their
+    // A*Y product is skipped and their residual set to zero
+    std::vector<int> active(E, 1);
+    for (int step = 0; step < o.refine_max; ++step) {
+      // R_e = X - (z_e I - A) Y_e, FP64-accurate (double-float A Y)
+      for (int e0 = 0; e0 < E;) {
+        if (!active[e0]) { ++e0; continue; }
+        int e1 = e0;
+        while (e1 < E && active[e1]) ++e1;
+        phase("refine A*Y", [&] { apply_A_acc((const double*)(Y + e0 * nm), true, (e1 - e0) * m, (double*)(AY + e0 * nm)); });
+        e0 = e1;
+      }
+      to_dev(ctx, d_act, active.data(), E);
+      refine_residual<S>(Yw, X, n, Y, AY, n, m, E, d_ze, d_act, st);
+      entry_norms2(Yw, Y, n, m, E, d_en, st);
+      to_host(ctx, en.data(), d_en, 2 * E);
+      bool conv = true, stagnant = step > 0;
+      double worst = 0.0;
+      for (int e = 0; e < E; ++e) {
+        if (!active[e]) continue;
+        const c128 ze = e < nc ? z[e] : conj(z[e - nc]);
+        const double rn = std::sqrt(en[2 * e]), yn = std::sqrt(en[2 * e + 1]);
+        const double rel = rn / ((anorm + std::sqrt(abs2(ze))) * yn);
+        if (rel <= rtol) {
+          active[e] = 0;
+        } else {
+          conv = false;
+          worst = std::max(worst, rel);
+          if (prev[e] < 0 || rn < 0.5 * prev[e]) stagnant = false;
+        }
+        prev[e] = rn;
+      }
+      if (std::getenv("FEAST_LOG"))
+        fprintf(stderr, "[feast] refine step %d: worst active relative residual %.3e (target %.3e), active %d/%d\n",
+                step, worst, rtol, (int)std::count(active.begin(), active.end(), 1), E);
+      if (conv || stagnant) break;
+      // entries that met the target in this step still take this correction
+      // (their residual is fresh); earlier ones have R = 0
+      phase("c64 solves", [&] { solve_lowp_core<c128>(Yw, n, nm, m); });
+      ++refine_steps;
+      // when the observed contraction already puts the next residual below
+      // the target, the correction just applied finishes the refinement
+      // (saves one FP64-accurate A*Y product per filter); so does the last
+      // allowed step.  Then Y + correction goes straight into Xf.
+      const bool last = (worst_prev > 0.0 && worst * (worst / worst_prev) <= rtol) || step + 1 == o.refine_max;
+      if (last) {
+        solve_accumulate<S, c64>(Xf, n, Y, Yc, Yc + (kCplx ? nc * nm : 0), n, m, nc, pinv, d_w, st);
         return;
       }
-      // default target 16 eps sqrt(n): just above the accuracy floor of the
-      // double-float residual (about 2^-48 relative per product)
-      const double rtol = o.refine_tol > 0 ? o.refine_tol : 16.0 * 2.220446049250313e-16 * std::sqrt((double)n);
-      std::vector<double> en(2 * E), prev(E, -1.0);
-      double worst_prev = -1.0;
-      // entries whose residual met the target drop out of later steps: their
-      // A*Y product is skipped and their residual set to zero
-      std::vector<int> active(E, 1);
-      for (int step = 0; step < o.refine_max; ++step) {
-        // R_e = X - (z_e I - A) Y_e, FP64-accurate (double-float A Y)
-        for (int e0 = 0; e0 < E;) {
-          if (!active[e0]) { ++e0; continue; }
-          int e1 = e0;
-          while (e1 < E && active[e1]) ++e1;
-          phase("refine A*Y", [&] { apply_A_acc((const double*)(Y + e0 * nm), true, (e1 - e0) * m, (double*)(AY + e0 * nm)); });
-          e0 = e1;
-        }
-        to_dev(ctx, d_act, active.data(), E);
-        refine_residual<S>(Yw, X, n, Y, AY, n, m, E, d_ze, d_act, st);
-        entry_norms2(Yw, Y, n, m, E, d_en, st);
-        to_host(ctx, en.data(), d_en, 2 * E);
-        bool conv = true, stagnant = step > 0;
-        double worst = 0.0;
-        for (int e = 0; e < E; ++e) {
-          if (!active[e]) continue;
-          const c128 ze = e < nc ? z[e] : conj(z[e - nc]);
-          const double rn = std::sqrt(en[2 * e]), yn = std::sqrt(en[2 * e + 1]);
-          const double rel = rn / ((anorm + std::sqrt(abs2(ze))) * yn);
-          if (rel <= rtol) {
-            active[e] = 0;
-          } else {
-            conv = false;
-            worst = std::max(worst, rel);
-            if (prev[e] < 0 || rn < 0.5 * prev[e]) stagnant = false;
-          }
-          prev[e] = rn;
-        }
-        if (std::getenv("FEAST_LOG"))
-          fprintf(stderr, "[feast] refine step %d: worst active relative residual %.3e (target %.3e), active %d/%d\n",
-                  step, worst, rtol, (int)std::count(active.begin(), active.end(), 1), E);
-        if (conv || stagnant) break;
-        // entries that met the target in this step still take this correction
-        // (their residual is fresh); earlier ones have R = 0
-        phase("c64 solves", [&] { solve_lowp<c128>(Yw, n, nm, m, true); });
-        ++refine_steps;
-        // when the observed contraction already puts the next residual below
-        // the target, the correction just applied finishes the refinement
-        // (saves one FP64-accurate A*Y product per filter)
-        if (worst_prev > 0.0 && worst * (worst / worst_prev) <= rtol) break;
-        worst_prev = worst;
-      }
+      phase("c64 solves", [&] { lowp_out(m, true); });
+      worst_prev = worst;
     }
     accumulate_filter<S>(Xf, n, Y, n, m, nc, d_w, st);
   }
@@ -991,6 +1010,17 @@ struct Solver {
     std::vector<int> keep;
     for (int c : pd.in_cols)
       if (mu[c] > 0.5) keep.push_back(c);
+    if (std::getenv("FEAST_LOG")) {
+      int unconv = 0;
+      double worst = 0.0, mu_min = 1.0;
+      for (int c : keep) {
+        if (!(pd.rs[c] <= tol)) ++unconv;
+        worst = std::max(worst, pd.rs[c]);
+        mu_min = std::min(mu_min, mu[c]);
+      }
+      fprintf(stderr, "[feast] response test: %zu in-I pairs, %zu with mu > 1/2 (min mu %.6f), %d unconverged, "
+              "max residual %.2e\n", pd.in_cols.size(), keep.size(), mu_min, unconv, worst);
+    }
     if (keep.empty()) return false;
     for (int c : keep)
       if (!(pd.rs[c] <= tol)) return false;
