@@ -47,7 +47,7 @@ METRIC = "converged eigenpairs/sec at residual 1e-10; filter-apply TFLOP/s vs pe
 UNIT = "eigenpairs/s"
 WORKLOAD = dict(n=8192, m_in=200, edge_in=30, edge_out=60, width=1e-4, bulk=50.0,
                 lmin=-1.0, lmax=1.0, m0=300, n_c=8, tol=1e-10, variant="rfeast", s=3, seed=0,
-                rfeast_expand=1, response_stop=1)
+                rfeast_expand=1, response_stop=1, gen="torch_cpu")
 # the n = 500 plain FP64 FEAST workload (real symmetric, 40 of 500 eigenvalues in
 # [-1, 1], 5 within 1e-3 of each edge; n_c = 8, m0 = 60)
 CONFIG1 = dict(n=500, m0=60, n_c=8, tol=1e-10, lmin=-1.0, lmax=1.0, seed=0)
@@ -233,7 +233,7 @@ def build_problem(w, device):
     from workloads.planted import planted_matrix_torch
     lam, a, b = spectrum_config2(w["seed"], n=w["n"], m_in=w["m_in"], edge_in=w["edge_in"],
                                  edge_out=w["edge_out"], width=w["width"], bulk=w["bulk"])
-    A = planted_matrix_torch(lam, w["seed"], complex_=True, device=device)
+    A = planted_matrix_torch(lam, w["seed"], complex_=True, device=device, gen=w["gen"])
     # A_store: contiguous buffer holding A column-major; A is its transposed view
     A_store = A.transpose(0, 1)
     assert A_store.is_contiguous()
@@ -370,6 +370,7 @@ def run_ours(args, rank, world, dev):
     w = scaled_workload(args.n) if args.n else dict(WORKLOAD)
     w["prec"] = args.prec
     w["variant"] = args.variant
+    w["gen"] = args.gen
     fg.build_library()
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
@@ -494,6 +495,7 @@ def run_ours(args, rank, world, dev):
             "config": {"workload": workload_name(w), "n": n, "m0": m0, "n_c": nc, "variant": w["variant"],
                        "s": w["s"], "prec": w["prec"], "tol": w["tol"],
                        "rfeast_expand": w["rfeast_expand"], "response_stop": w["response_stop"],
+                       "q_gaussian": w["gen"],
                        "l2": "inputs larger than L2 (A is %.2f GB, L2 129 MB)" % (h2d / 1e9),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "correct": bool(ok),
@@ -580,11 +582,12 @@ def run_reference(args, rank, world):
     from workloads import spectrum_config2
     from workloads.planted import planted_block_host
     w = scaled_workload(args.n) if args.n else dict(WORKLOAD)
-    w["prec"], w["variant"] = args.prec, args.variant
+    w["prec"], w["variant"], w["gen"] = args.prec, args.variant, args.gen
     lam, a, b = spectrum_config2(w["seed"], n=w["n"], m_in=w["m_in"], edge_in=w["edge_in"],
                                  edge_out=w["edge_out"], width=w["width"], bulk=w["bulk"])
     t_build = time.time()
-    A_host = planted_block_host(lam, w["seed"], min(1024, w["n"]), complex_=True)
+    A_host = planted_block_host(lam, w["seed"], min(1024, w["n"]), complex_=True,
+                                gen=w["gen"] if w["gen"] != "torch_cuda" else "torch_cpu")
     t_build = time.time() - t_build
     small = oracle_full_scaled(min(1024, w["n"]))
     f = w["n"] / small["n"]
@@ -609,6 +612,7 @@ def run_reference(args, rank, world):
             "config": {"workload": workload_name(w), "n": w["n"], "m0": w["m0"], "n_c": w["n_c"],
                        "variant": w["variant"], "s": w["s"], "prec": w["prec"], "tol": w["tol"],
                        "rfeast_expand": w["rfeast_expand"], "response_stop": w["response_stop"],
+                       "q_gaussian": w["gen"],
                        "l2": "inputs larger than L2 (A is %.2f GB, L2 129 MB)" % (16.0 * w["n"] ** 2 / 1e9),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
@@ -638,6 +642,8 @@ def main():
     ap.add_argument("--no-fp64", dest="fp64", action="store_false")
     ap.add_argument("--no-cpu", dest="cpu", action="store_false")
     ap.add_argument("--no-config1", dest="config1", action="store_false")
+    ap.add_argument("--gen", default=WORKLOAD["gen"], choices=["torch_cpu", "torch_cuda", "numpy"],
+                    help="generator of the Gaussian whose QR gives Q")
     ap.add_argument("--cpu-full-n", type=int, default=2048,
                     help="n of the scaled workload the oracle solves in full (0: skip)")
     args = ap.parse_args()

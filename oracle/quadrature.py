@@ -87,3 +87,49 @@ def rational_filter(lam, z, w):
     for zj, wj in zip(z, w):
         out += 2.0 * np.real(wj / (zj - lam))
     return out
+
+
+def legendre_values(t, nmax):
+    """P_0..P_{nmax-1} at the points t (rows: degree), three-term recurrence."""
+    t = np.asarray(t, dtype=np.float64)
+    P = np.zeros((nmax, t.size))
+    P[0] = 1.0
+    if nmax > 1:
+        P[1] = t
+    for k in range(1, nmax - 1):
+        P[k + 1] = ((2 * k + 1) * t * P[k] - k * P[k - 1]) / (k + 1)
+    return P
+
+
+def offset_nodes(n_c: int, offsets):
+    """Abscissae and weights of the interpolatory rule on moved nodes (the
+    node placement a proposer may choose instead of Gauss-Legendre):
+    t_j' = tanh(atanh(t_j) + delta_j) for the Gauss-Legendre t_j, and weights
+    omega' solving sum_j omega'_j P_p(t_j') = integral of P_p over [-1, 1]
+    (= 2 for p = 0, else 0), p < n_c: exact for polynomials of degree
+    < n_c.  delta = 0 gives the Gauss rule back.  The moved nodes must stay
+    strictly increasing."""
+    t, om = gauss_legendre(n_c)
+    d = np.asarray(offsets, dtype=np.float64)
+    if d.size != n_c:
+        raise ValueError("one offset per node")
+    tp = np.tanh(np.arctanh(t) + d)
+    if np.any(np.diff(tp) <= 0) or np.any(np.abs(tp) >= 1):
+        raise ValueError("moved nodes must stay strictly increasing inside (-1, 1)")
+    rhs = np.zeros(n_c)
+    rhs[0] = 2.0
+    omp = np.linalg.solve(legendre_values(tp, n_c), rhs)
+    return tp, omp
+
+
+def contour_nodes_offset(lmin: float, lmax: float, n_c: int, offsets, aspect: float = 1.0):
+    """contour_nodes with the moved-node interpolatory rule of offset_nodes."""
+    if not lmin < lmax:
+        raise ValueError("lambda_min must be < lambda_max")
+    t, om = offset_nodes(n_c, offsets)
+    c = 0.5 * (lmin + lmax)
+    r = 0.5 * (lmax - lmin)
+    theta = 0.5 * np.pi * (1.0 - t)
+    z = c + r * np.cos(theta) + 1j * aspect * r * np.sin(theta)
+    w = 0.25 * om * (aspect * r * np.cos(theta) + 1j * r * np.sin(theta))
+    return z, w

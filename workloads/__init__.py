@@ -13,6 +13,7 @@ from .planted import (  # noqa: F401
     spectrum_config1,
     spectrum_config2,
     spectrum_config3,
+    spectrum_config4,
     spectrum_paper,
     spectrum_uniform,
     make_problem,

@@ -147,6 +147,24 @@ def spectrum_config3(seed):
     return lam, lmin, lmax, m0, n_c
 
 
+def spectrum_config4(seed, n=2048):
+    """One spectrum of the learned-proposer workload (2000 training and 500
+    held-out real symmetric problems, seeds 0..1999 and 10000..10499): n = 2048
+    eigenvalues, I = [-1, 1], m uniform in 10..170 eigenvalues inside, an edge
+    cluster at each edge of c eigenvalues (c uniform in 0..40; half inside and
+    half outside the edge, the reading of the unspecified side) within a
+    width w log-uniform in [1e-6, 1e-1], the rest uniform in [-10, 10] outside
+    I and outside the edge bands.  Returns (lam, lmin, lmax, meta)."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 4]))
+    m = int(rng.integers(10, 171))
+    c = int(rng.integers(0, 41))
+    w = float(10.0 ** rng.uniform(-6.0, -1.0))
+    c_in = min(c // 2, m // 2)
+    c_out = c - c // 2
+    lam = spectrum_edge_clusters(rng, n, m, -1.0, 1.0, -10.0, 10.0, n_edge_in=c_in, n_edge_out=c_out, width=w)
+    return lam, -1.0, 1.0, {"m": m, "cluster": c, "width": w, "edge_in": c_in, "edge_out": c_out}
+
+
 def spectrum_paper(kind, seed=0, n=545, m_in=50):
     """The two n = 545 spectra of the paper's Sect. III experiments: 50
     eigenvalues in I = [-1, 1]; the other 495 in [1.01, 20.81] ("Sparse") or
@@ -203,21 +221,35 @@ def make_problem(name, lam, lmin, lmax, m0, n_c, seed=0, complex_=False, keep_q=
                    meta={"seed": seed, "complex": complex_})
 
 
-def planted_matrix_torch(lam, seed, complex_=False, device="cuda:0"):
-    """A = Q diag(lam) Q^H with Q from the QR factorisation of the same seeded
-    Gaussian matrix haar_unitary(n, seed + 1000) draws (numpy generator, so the
-    host can rebuild the same matrix up to rounding), factored by torch on the
-    GPU (large n).  Returns the column-major CUDA tensor A; Q is not kept."""
+def gaussian_torch(n, seed, complex_=False, gen="torch_cpu"):
+    """The seeded Gaussian whose QR gives Q for the large planted matrices:
+    gen "torch_cpu" draws it with torch's CPU generator (reproducible on any
+    host), "numpy" with numpy's (the draw of haar_unitary), "torch_cuda" with
+    the CUDA generator on the current GPU (not reproducible on a host)."""
+    import torch
+
+    dt = torch.complex128 if complex_ else torch.float64
+    if gen == "numpy":
+        rng = np.random.default_rng(int(seed))
+        G = rng.standard_normal((n, n))
+        if complex_:
+            G = (G + 1j * rng.standard_normal((n, n))) / np.sqrt(2.0)
+        return torch.from_numpy(G)
+    dev = "cuda" if gen == "torch_cuda" else "cpu"
+    g = torch.Generator(device=dev)
+    g.manual_seed(int(seed))
+    return torch.randn((n, n), generator=g, dtype=dt, device=dev)
+
+
+def planted_matrix_torch(lam, seed, complex_=False, device="cuda:0", gen="torch_cpu"):
+    """A = Q diag(lam) Q^H with Q from the QR factorisation (on the GPU) of the
+    seeded Gaussian gaussian_torch(n, seed + 1000, gen).  Returns the
+    column-major CUDA tensor A; Q is not kept."""
     import torch
 
     n = int(lam.size)
-    rng = np.random.default_rng(int(seed) + 1000)
-    Gh = rng.standard_normal((n, n))
-    if complex_:
-        Gh = (Gh + 1j * rng.standard_normal((n, n))) / np.sqrt(2.0)
     dt = torch.complex128 if complex_ else torch.float64
-    G = torch.from_numpy(Gh).to(device=device, dtype=dt)
-    del Gh
+    G = gaussian_torch(n, int(seed) + 1000, complex_, gen).to(device=device, dtype=dt)
     Q, R = torch.linalg.qr(G)
     d = torch.diagonal(R)
     Q = Q * (d / d.abs())[None, :]
@@ -229,10 +261,15 @@ def planted_matrix_torch(lam, seed, complex_=False, device="cuda:0"):
     return A.transpose(0, 1).contiguous().transpose(0, 1)
 
 
-def planted_block_host(lam, seed, rows, complex_=False):
+def planted_block_host(lam, seed, rows, complex_=False, gen="torch_cpu"):
     """The leading rows x rows block of the matrix planted_matrix_torch builds
-    (same spectrum and Gaussian seed; Q from the host's QR, equal up to
-    rounding): Q[:rows] diag(lam) Q[:rows]^H."""
-    Q = haar_unitary(lam.size, int(seed) + 1000, complex_)[:rows]
+    with a host-reproducible generator (same spectrum and Gaussian; Q from the
+    host's QR, equal up to rounding): Q[:rows] diag(lam) Q[:rows]^H."""
+    import torch
+
+    G = gaussian_torch(lam.size, int(seed) + 1000, complex_, gen)
+    Q, R = torch.linalg.qr(G)
+    d = torch.diagonal(R)
+    Q = (Q * (d / d.abs())[None, :])[:rows].numpy()
     B = (Q * lam[None, :]) @ Q.conj().T
     return np.asfortranarray(0.5 * (B + B.conj().T))
