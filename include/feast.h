@@ -99,6 +99,12 @@ typedef struct {
                            on spectra with eigenvalues on both sides of I, mixtures of outside
                            eigenvectors give in-I Ritz values that never converge */
   int reserved;
+  const double* node_offsets; /* optional host array of n_c node offsets delta_j (NULL: the
+                           Gauss-Legendre rule): the abscissae become
+                           t_j' = tanh(atanh(t_j) + delta_j), which must stay strictly
+                           increasing, and the weights those of the interpolatory rule on
+                           them (exact for polynomials of degree < n_c); delta = 0 is the
+                           Gauss rule (a placement the learned proposer may choose) */
 } feast_opts;
 
 /* Per-call statistics of the last feast_interval_solve on a context. */
@@ -152,6 +158,12 @@ uint64_t feast_kernel_launches(void);
  * z_j = c + r cos(theta_j) + i aspect r sin(theta_j),
  * w_j = (omega_j/4)(aspect r cos(theta_j) + i r sin(theta_j)). */
 int feast_contour_nodes(double lmin, double lmax, int n_c, double aspect, double* z, double* w);
+
+/* feast_contour_nodes with moved nodes: offsets (host, n_c doubles) as
+ * feast_opts.node_offsets describes (NULL = Gauss).  Returns FEAST_ERR_ARG
+ * when the moved abscissae are not strictly increasing inside (-1, 1). */
+int feast_contour_nodes_offset(double lmin, double lmax, int n_c, double aspect, const double* offsets, double* z,
+                               double* w);
 
 /* Eigenpairs of the Hermitian n x n matrix A (device, leading dim lda >= n,
  * dtype FEAST_R64 or FEAST_C128, not modified) with eigenvalues in the open
@@ -238,6 +250,42 @@ int feast_rayleigh_ritz(feast_ctx* ctx, const void* A, int dtype, int64_t n, int
 int feast_gemm_f64acc(feast_ctx* ctx, int method, int dtype, int transA, int transB, int64_t M, int64_t N, int64_t K,
                       double alpha, const void* A, int64_t lda, const void* B, int64_t ldb, double beta, void* C,
                       int64_t ldc);
+
+/* ---- learned m0 / node proposer (spectrum estimation ahead of the solve,
+ * which the paper names as future work, Sect. IV) ---- */
+
+/* Stochastic-trace Chebyshev moments of the spectral density of the Hermitian
+ * A (device, dtype, leading dim lda): mu_k = (1/(n nv)) sum_v Re(v^H T_k(B) v)
+ * for k < M, B = (A - c I)/r, the T_k(B) v by the three-term recurrence
+ * t_{k+1} = 2 B t_k - t_{k-1}.  The spectrum of A must lie in [c - r, c + r].
+ * V: device n x nv probe vectors (leading dim n, dtype of A) with E[v v^H] = I
+ * (N(0,1) or random signs); mu: host, M doubles.  1 <= M <= 4096. */
+int feast_spectral_moments(feast_ctx* ctx, const void* A, int dtype, int64_t n, int64_t lda, double c, double r,
+                           const void* V, int64_t nv, int M, double* mu);
+
+/* Host: eigenvalue count estimate of (a, b) from the moments of
+ * feast_spectral_moments, n times the Jackson-damped kernel-polynomial
+ * density integrated over (a, b):  n [g_0 mu_0 (th_a - th_b)/pi +
+ * sum_{k>=1} g_k mu_k 2 (sin(k th_a) - sin(k th_b))/(k pi)], th = arccos((x - c)/r). */
+double feast_moments_count(const double* mu, int M, double c, double r, double a, double b, int64_t n);
+
+/* The proposer's multilayer perceptron, 64 -> 256 -> 256 -> 256 -> 9 with
+ * ReLU on the hidden layers, FP32.  params: one device array of
+ * feast_mlp_param_count() floats holding, layer by layer, W (d_out x d_in,
+ * row major) then b (d_out).  X: device B x 64, Y: device B x 9, T: device
+ * B x 9 targets, row major.  Scratch comes from the context. */
+int feast_mlp_param_count(void);
+int feast_mlp_forward(feast_ctx* ctx, const float* params, const float* X, int64_t B, float* Y);
+/* grad (device, feast_mlp_param_count floats) of the mean squared error
+ * (1/(9 B)) sum (Y - T)^2, whose value goes to *loss (host). */
+int feast_mlp_gradient(feast_ctx* ctx, const float* params, const float* X, const float* T, int64_t B, float* grad,
+                       double* loss);
+/* One Adam step (Kingma & Ba; b1 = 0.9, b2 = 0.999, eps = 1e-8) on the mean
+ * squared error of the batch: params, m, v (device, feast_mlp_param_count
+ * floats each) updated in place; step counts from 1; *loss (host, may be NULL)
+ * receives the loss before the step. */
+int feast_mlp_train_step(feast_ctx* ctx, float* params, float* m, float* v, const float* X, const float* T, int64_t B,
+                         int step, double lr, double* loss);
 
 /* Allocation-free Jacobi eigensolver, for callers that cannot allocate device
  * memory at call time: services that reserve their whole memory budget up

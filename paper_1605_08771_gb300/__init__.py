@@ -32,7 +32,8 @@ EXPORTS = [
     "feast_contour_nodes", "feast_interval_solve", "feast_filter_apply",
     "feast_shifted_lu", "feast_shifted_solve", "feast_orthonormalize",
     "feast_jacobi_eigh", "feast_rayleigh_ritz", "feast_kernel_launches", "feast_jacobi_eigh_noalloc",
-    "feast_gemm_f64acc",
+    "feast_gemm_f64acc", "feast_contour_nodes_offset", "feast_spectral_moments", "feast_moments_count",
+    "feast_mlp_param_count", "feast_mlp_forward", "feast_mlp_gradient", "feast_mlp_train_step",
 ]
 
 
@@ -42,7 +43,7 @@ class FeastOpts(ctypes.Structure):
                 ("aspect", ctypes.c_double), ("anorm", ctypes.c_double), ("refine_tol", ctypes.c_double),
                 ("seed", ctypes.c_ulonglong), ("x0", ctypes.c_void_p), ("refine_switch", ctypes.c_double),
                 ("rfeast_expand", ctypes.c_int), ("response_stop", ctypes.c_int),
-                ("reserved", ctypes.c_int)]
+                ("reserved", ctypes.c_int), ("node_offsets", ctypes.c_void_p)]
 
 
 class FeastStats(ctypes.Structure):
@@ -92,6 +93,13 @@ def lib():
         "feast_kernel_launches": (ctypes.c_uint64, []),
         "feast_jacobi_eigh_noalloc": (I, [I, P, I, I64, P, DP, P, IP]),
         "feast_gemm_f64acc": (I, [P, I, I, I, I, I64, I64, I64, D, P, I64, P, I64, D, P, I64]),
+        "feast_contour_nodes_offset": (I, [D, D, I, D, DP, DP, DP]),
+        "feast_spectral_moments": (I, [P, P, I, I64, I64, D, D, P, I64, I, DP]),
+        "feast_moments_count": (D, [DP, I, D, D, D, D, I64]),
+        "feast_mlp_param_count": (I, []),
+        "feast_mlp_forward": (I, [P, P, P, I64, P]),
+        "feast_mlp_gradient": (I, [P, P, P, P, I64, P, DP]),
+        "feast_mlp_train_step": (I, [P, P, P, P, P, P, I64, I, D, DP]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -157,6 +165,8 @@ def feast_kernel_launches() -> int:
 
 
 def feast_opts_default(**kw) -> FeastOpts:
+    """Default options with keyword overrides; node_offsets takes a sequence
+    of n_c floats (kept alive by the returned structure)."""
     o = FeastOpts()
     lib().feast_opts_default(ctypes.byref(o))
     for k, v in kw.items():
@@ -164,6 +174,13 @@ def feast_opts_default(**kw) -> FeastOpts:
             v = VARIANTS[v]
         if k == "prec" and isinstance(v, str):
             v = PRECS[v]
+        if k == "node_offsets":
+            if v is None:
+                o.node_offsets = None
+                continue
+            arr = np.ascontiguousarray(v, dtype=np.float64)
+            o._offsets_keep = arr
+            v = arr.ctypes.data
         setattr(o, k, v)
     return o
 
@@ -190,6 +207,73 @@ def feast_contour_nodes(lmin, lmax, n_c, aspect=1.0):
                                      z.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                      w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "feast_contour_nodes")
     return z[0::2] + 1j * z[1::2], w[0::2] + 1j * w[1::2]
+
+
+def feast_contour_nodes_offset(lmin, lmax, n_c, offsets, aspect=1.0):
+    """Contour nodes and weights of the moved-node interpolatory rule."""
+    z = np.zeros(2 * n_c)
+    w = np.zeros(2 * n_c)
+    d = np.ascontiguousarray(offsets, dtype=np.float64)
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(lib().feast_contour_nodes_offset(lmin, lmax, n_c, aspect, d.ctypes.data_as(dp), z.ctypes.data_as(dp),
+                                            w.ctypes.data_as(dp)), "feast_contour_nodes_offset")
+    return z[0::2] + 1j * z[1::2], w[0::2] + 1j * w[1::2]
+
+
+def feast_spectral_moments(ctx, A, V, c, r, M):
+    """Chebyshev moments mu_0..mu_{M-1} of the spectral density of the CUDA
+    matrix A scaled to (A - c I)/r, from the CUDA probe block V (n x nv)."""
+    A = colmajor(A)
+    V = colmajor(V.to(A.dtype))
+    n, nv = V.shape
+    mu = np.zeros(M)
+    _check(lib().feast_spectral_moments(ctx, _ptr(A), _dtype_code(A), n, n, float(c), float(r), _ptr(V), nv, int(M),
+                                        mu.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "feast_spectral_moments")
+    return mu
+
+
+def feast_moments_count(mu, c, r, a, b, n):
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    return float(lib().feast_moments_count(mu.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), mu.size, float(c),
+                                           float(r), float(a), float(b), int(n)))
+
+
+def feast_mlp_param_count() -> int:
+    return int(lib().feast_mlp_param_count())
+
+
+def _f32(t):
+    torch = _torch()
+    if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError("MLP arrays are contiguous float32 CUDA tensors")
+    return _ptr(t)
+
+
+def feast_mlp_forward(ctx, params, X):
+    """Outputs (B x 9) of the proposer MLP for the CUDA float32 batch X (B x 64)."""
+    torch = _torch()
+    B = X.shape[0]
+    Y = torch.empty((B, 9), dtype=torch.float32, device=X.device)
+    _check(lib().feast_mlp_forward(ctx, _f32(params), _f32(X), B, _ptr(Y)), "feast_mlp_forward")
+    return Y
+
+
+def feast_mlp_gradient(ctx, params, X, T):
+    """(gradient, loss) of the mean squared error of the batch."""
+    torch = _torch()
+    g = torch.empty_like(params)
+    loss = ctypes.c_double(0.0)
+    _check(lib().feast_mlp_gradient(ctx, _f32(params), _f32(X), _f32(T), X.shape[0], _ptr(g), ctypes.byref(loss)),
+           "feast_mlp_gradient")
+    return g, loss.value
+
+
+def feast_mlp_train_step(ctx, params, m, v, X, T, step, lr):
+    """One Adam step in place; returns the batch loss before the step."""
+    loss = ctypes.c_double(0.0)
+    _check(lib().feast_mlp_train_step(ctx, _f32(params), _f32(m), _f32(v), _f32(X), _f32(T), X.shape[0], int(step),
+                                      float(lr), ctypes.byref(loss)), "feast_mlp_train_step")
+    return loss.value
 
 
 def feast_interval_solve(ctx, A, lmin, lmax, m0, n_c, tol, opts: FeastOpts | None = None, x0=None):

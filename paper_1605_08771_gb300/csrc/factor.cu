@@ -734,25 +734,64 @@ void lu_solve_batched(const F* M, int64_t n, int64_t ld, int64_t stride, int nod
     g.alpha = C1(-1.0); g.beta = C1(1.0); g.batch = nodes; g.ksplit = 1;
     gemm<F, F, F>(g, s);
   };
-  // forward (L, or U^H for the adjoint): top down
-  for (int64_t r0 = 0; r0 < n; r0 += TBK) {
-    const int bs = (int)std::min<int64_t>(TBK, n - r0);
-    const int64_t r1 = r0 + bs;
-    trsm_diag_kernel<F, TBK><<<gd, 256, 0, s>>>(M, ld, stride, Y, n, m, ystride, r0, bs, adjoint ? 1 : 0);
+  auto diag = [&](int64_t r0, int bs, int mode) {
+    trsm_diag_kernel<F, TBK><<<gd, 256, 0, s>>>(M, ld, stride, Y, n, m, ystride, r0, bs, mode);
     FEAST_LAUNCH_CHECK();
-    if (r1 < n) {
-      if (!adjoint) update(n - r1, bs, M + r1 + r0 * ld, OP_N, r1, r0, r0 / TBK, r1);
-      else update(n - r1, bs, M + r0 + r1 * ld, OP_C, r1, r0, r0 / TBK, r1);
+  };
+  // forward (L, or U^H for the adjoint) over rows [b0, b1), top down; the
+  // updates reach rows [r1, upd_end)
+  auto forward_rows = [&](int64_t b0, int64_t b1, int64_t upd_end) {
+    for (int64_t r0 = b0; r0 < b1; r0 += TBK) {
+      const int bs = (int)std::min<int64_t>(TBK, b1 - r0);
+      const int64_t r1 = r0 + bs;
+      diag(r0, bs, adjoint ? 1 : 0);
+      if (r1 < upd_end) {
+        if (!adjoint) update(upd_end - r1, bs, M + r1 + r0 * ld, OP_N, r1, r0, r0 / TBK, r1);
+        else update(upd_end - r1, bs, M + r0 + r1 * ld, OP_C, r1, r0, r0 / TBK, r1);
+      }
     }
+  };
+  // backward (U, or L^H for the adjoint) over rows [b0, b1), bottom up; the
+  // updates reach rows [upd_begin, r0)
+  auto backward_rows = [&](int64_t b0, int64_t b1, int64_t upd_begin) {
+    for (int64_t r0 = b0 + ((b1 - b0 - 1) / TBK) * TBK; r0 >= b0; r0 -= TBK) {
+      const int bs = (int)std::min<int64_t>(TBK, b1 - r0);
+      diag(r0, bs, adjoint ? 3 : 2);
+      if (r0 > upd_begin) {
+        if (!adjoint) update(r0 - upd_begin, bs, M + upd_begin + r0 * ld, OP_N, upd_begin, r0, r0 / TBK, upd_begin);
+        else update(r0 - upd_begin, bs, M + r0 + upd_begin * ld, OP_C, upd_begin, r0, r0 / TBK, upd_begin);
+      }
+    }
+  };
+  if (!tc) {
+    forward_rows(0, n, n);
+    backward_rows(0, n, 0);
+    return;
   }
-  // backward (U, or L^H for the adjoint): bottom up
-  for (int64_t r0 = ((n - 1) / TBK) * TBK; r0 >= 0; r0 -= TBK) {
-    const int bs = (int)std::min<int64_t>(TBK, n - r0);
-    trsm_diag_kernel<F, TBK><<<gd, 256, 0, s>>>(M, ld, stride, Y, n, m, ystride, r0, bs, adjoint ? 3 : 2);
-    FEAST_LAUNCH_CHECK();
-    if (r0 > 0) {
-      if (!adjoint) update(r0, bs, M + r0 * ld, OP_N, 0, r0, r0 / TBK, 0);
-      else update(r0, bs, M + r0, OP_C, 0, r0, r0 / TBK, 0);
+  if constexpr (std::is_same<F, c64>::value) {
+    // two levels on the tensor cores: 256-row outer blocks solved by 64-row
+    // diagonal blocks with updates confined to the outer block, then one
+    // rank-256 update of every row past it (four times fewer passes over the
+    // right-hand sides than rank-64 updates)
+    const int64_t OB = kSolveOuter;
+    auto outer_update = [&](int64_t R0, int64_t R1, int64_t rows, int64_t c_off) {
+      const int64_t kb = R1 - R0;
+      cg_split(Y, ystride, 0, n, R0, 0, false, false, m, kb, kSolveOuter, 1, sp->mpad, kSolveOuter, nodes, sp->rhs,
+               s);
+      const CgOperand B = cg_operand(sp->rhs, sp->mpad, kSolveOuter, nodes);
+      CgOperand A = cg_operand(adjoint ? sp->row : sp->col, sp->npad, kSolveBlock, nodes, sp->nblk, kSolveBlock);
+      A.base_row = (R0 / kSolveBlock) * A.slab_rows + c_off;
+      cg_update(A, B, kb, rows, m, Y + c_off, n, ystride, nodes, status, num_sms, s);
+    };
+    for (int64_t R0 = 0; R0 < n; R0 += OB) {
+      const int64_t R1 = std::min(n, R0 + OB);
+      forward_rows(R0, R1, R1);
+      if (R1 < n) outer_update(R0, R1, n - R1, R1);
+    }
+    for (int64_t R0 = ((n - 1) / OB) * OB; R0 >= 0; R0 -= OB) {
+      const int64_t R1 = std::min(n, R0 + OB);
+      backward_rows(R0, R1, R0);
+      if (R0 > 0) outer_update(R0, R1, R0, 0);
     }
   }
 }
@@ -782,7 +821,7 @@ size_t solve_planes_bytes(int64_t n, int64_t m, int nodes, int entries, bool adj
   size_t b = sizeof(uint16_t) * cg_planes_elems(cg_vpad(n), kSolveBlock, nblk, nodes);
   b = (b + 255) & ~size_t(255);
   size_t tot = adjoint ? 2 * b : b;
-  tot += sizeof(uint16_t) * cg_planes_elems(cg_vpad(m), kSolveBlock, 1, entries) + 256;
+  tot += sizeof(uint16_t) * cg_planes_elems(cg_vpad(m), kSolveOuter, 1, entries) + 256;
   return tot;
 }
 

@@ -14,6 +14,7 @@ constexpr int kPanel = 32;        // panel width = triangular-solve block size
 constexpr int kTcBlock = 128;     // outer block of the two-level LU whose trailing update
                                   // runs on the tensor cores
 constexpr int kSolveBlock = 64;   // diagonal blocks of the complex-FP32 triangular solves
+constexpr int kSolveOuter = 256;  // outer blocks of the tensor-core triangular solves
 
 // Scratch the cooperative panel kernel needs (device pointers, sized by
 // panel_work_bytes()).
@@ -47,7 +48,7 @@ size_t lu_tc_planes_bytes(int64_t n, int nodes);
 struct SolvePlanes {
   uint16_t* col = nullptr;   // [node][block][6][npad][64]
   uint16_t* row = nullptr;   // the same of the conjugated row blocks (null: no adjoint solves)
-  uint16_t* rhs = nullptr;   // [entry][6][mpad][64]
+  uint16_t* rhs = nullptr;   // [entry][6][mpad][256]
   int64_t npad = 0, nblk = 0, mpad = 0;
 };
 size_t solve_planes_bytes(int64_t n, int64_t m, int nodes, int entries, bool adjoint);

@@ -22,6 +22,7 @@
 #include "factor.cuh"
 #include "gemm.cuh"
 #include "oz_gemm.cuh"
+#include "proposer.cuh"
 
 using namespace feast;
 
@@ -134,9 +135,63 @@ void gauss_legendre(int n, std::vector<double>& t, std::vector<double>& wt) {
   }
 }
 
-void contour(double lmin, double lmax, int nc, double aspect, std::vector<c128>& z, std::vector<c128>& w) {
+// Moved nodes t_j' = tanh(atanh(t_j) + delta_j) and the weights of the
+// interpolatory rule on them: sum_j om_j P_p(t_j') = 2 [p == 0] for the
+// Legendre polynomials P_p, p < n, by Gaussian elimination with partial
+// pivoting.  false when the moved nodes are not strictly increasing.
+bool offset_rule(int n, const double* delta, std::vector<double>& t, std::vector<double>& om) {
+  std::vector<double> t0, w0;
+  gauss_legendre(n, t0, w0);
+  t.resize(n);
+  for (int j = 0; j < n; ++j) {
+    if (!std::isfinite(delta[j])) return false;
+    t[j] = std::tanh(std::atanh(t0[j]) + delta[j]);
+    if (!(std::fabs(t[j]) < 1.0) || (j > 0 && !(t[j] > t[j - 1]))) return false;
+  }
+  // G[p][j] = P_p(t_j), augmented with the right-hand side
+  std::vector<double> G((size_t)n * (n + 1), 0.0);
+  auto at = [&](int p, int j) -> double& { return G[(size_t)p * (n + 1) + j]; };
+  for (int j = 0; j < n; ++j) {
+    double pm = 1.0, pc = t[j];
+    at(0, j) = 1.0;
+    if (n > 1) at(1, j) = pc;
+    for (int p = 1; p + 1 < n; ++p) {
+      const double pn = ((2.0 * p + 1.0) * t[j] * pc - p * pm) / (p + 1.0);
+      pm = pc;
+      pc = pn;
+      at(p + 1, j) = pn;
+    }
+  }
+  at(0, n) = 2.0;
+  for (int col = 0; col < n; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < n; ++r)
+      if (std::fabs(at(r, col)) > std::fabs(at(piv, col))) piv = r;
+    if (at(piv, col) == 0.0) return false;
+    if (piv != col)
+      for (int j = 0; j <= n; ++j) std::swap(at(piv, j), at(col, j));
+    for (int r = col + 1; r < n; ++r) {
+      const double f = at(r, col) / at(col, col);
+      for (int j = col; j <= n; ++j) at(r, j) -= f * at(col, j);
+    }
+  }
+  om.assign(n, 0.0);
+  for (int col = n - 1; col >= 0; --col) {
+    double v = at(col, n);
+    for (int j = col + 1; j < n; ++j) v -= at(col, j) * om[j];
+    om[col] = v / at(col, col);
+  }
+  return true;
+}
+
+void contour(double lmin, double lmax, int nc, double aspect, std::vector<c128>& z, std::vector<c128>& w,
+             const double* offsets = nullptr) {
   std::vector<double> t, om;
-  gauss_legendre(nc, t, om);
+  if (offsets) {
+    if (!offset_rule(nc, offsets, t, om)) throw FeastError{FEAST_ERR_ARG};
+  } else {
+    gauss_legendre(nc, t, om);
+  }
   const double c = 0.5 * (lmin + lmax), r = 0.5 * (lmax - lmin);
   z.resize(nc);
   w.resize(nc);
@@ -284,7 +339,7 @@ struct Solver {
     mmax = std::max<int64_t>(mmax_, 1);
     use_oz = o.prec != FEAST_PREC_F64 && o.refine_gemm == 0;
     use_tc = o.prec == FEAST_PREC_MIXED;
-    contour(lmin, lmax, nc, o.aspect, z, w);
+    contour(lmin, lmax, nc, o.aspect, z, w, o.node_offsets);
     d_w = dalloc<c128>(ctx, nc);
     d_ze = dalloc<c128>(ctx, E);
     std::vector<c128> ze(E);
@@ -1540,6 +1595,129 @@ int feast_contour_nodes(double lmin, double lmax, int n_c, double aspect, double
     w[2 * j + 1] = ww[j].im;
   }
   return FEAST_OK;
+}
+
+int feast_contour_nodes_offset(double lmin, double lmax, int n_c, double aspect, const double* offsets, double* z,
+                               double* w) {
+  if (!z || !w || n_c < 1 || n_c > 256 || !(lmin < lmax) || !(aspect > 0)) return FEAST_ERR_ARG;
+  std::vector<c128> zz, ww;
+  try {
+    contour(lmin, lmax, n_c, aspect, zz, ww, offsets);
+  } catch (const FeastError& e) {
+    return e.code;
+  }
+  for (int j = 0; j < n_c; ++j) {
+    z[2 * j] = zz[j].re;
+    z[2 * j + 1] = zz[j].im;
+    w[2 * j] = ww[j].re;
+    w[2 * j + 1] = ww[j].im;
+  }
+  return FEAST_OK;
+}
+
+int feast_spectral_moments(feast_ctx* ctx, const void* A, int dtype, int64_t n, int64_t lda, double c, double r,
+                           const void* V, int64_t nv, int M, double* mu) {
+  if (int e = check_common(ctx, A, dtype, n, lda, -1.0, 1.0, 1)) return e;
+  if (!V || !mu || nv < 1 || M < 1 || M > 4096 || !std::isfinite(c) || !(r > 0) || !std::isfinite(r))
+    return FEAST_ERR_ARG;
+  return guarded(ctx, [&]() {
+    FEAST_CUDA_TRY(cudaSetDevice(ctx->device));
+    ctx->arena.reset();
+    auto run = [&](auto tag) {
+      using S = decltype(tag);
+      S* T0 = dalloc<S>(ctx, n * nv);
+      S* T1 = dalloc<S>(ctx, n * nv);
+      S* AT = dalloc<S>(ctx, n * nv);
+      double* part = dalloc<double>(ctx, (int64_t)M * kMomentBlocks);
+      chebyshev_moments<S>((const S*)A, n, lda, c, r, (const S*)V, nv, M, T0, T1, AT, part, nullptr, ctx->stream);
+      std::vector<double> h((size_t)M * kMomentBlocks);
+      to_host(ctx, h.data(), part, (int64_t)M * kMomentBlocks);
+      for (int k = 0; k < M; ++k) {
+        double acc = 0.0;
+        for (int b = 0; b < kMomentBlocks; ++b) acc += h[(size_t)k * kMomentBlocks + b];
+        mu[k] = acc / ((double)n * (double)nv);
+      }
+      return FEAST_OK;
+    };
+    if (dtype == FEAST_R64) return run(double{});
+    return run(c128{});
+  });
+}
+
+double feast_moments_count(const double* mu, int M, double c, double r, double a, double b, int64_t n) {
+  if (!mu || M < 1 || !(r > 0)) return NAN;
+  auto theta = [&](double x) { return std::acos(std::min(1.0, std::max(-1.0, (x - c) / r))); };
+  const double ta = theta(a), tb = theta(b), q = M_PI / (M + 1);
+  double sum = 0.0;
+  for (int k = 0; k < M; ++k) {
+    // Jackson damping
+    const double g = ((M - k + 1) * std::cos(q * k) + std::sin(q * k) / std::tan(q)) / (M + 1);
+    const double ik = k == 0 ? (ta - tb) / M_PI : 2.0 * (std::sin(k * ta) - std::sin(k * tb)) / (k * M_PI);
+    sum += g * mu[k] * ik;
+  }
+  return (double)n * sum;
+}
+
+int feast_mlp_param_count(void) { return (int)mlp_param_count(); }
+
+int feast_mlp_forward(feast_ctx* ctx, const float* params, const float* X, int64_t B, float* Y) {
+  if (!ctx || !params || !X || !Y || B < 1 || B > (1 << 22)) return FEAST_ERR_ARG;
+  return guarded(ctx, [&]() {
+    FEAST_CUDA_TRY(cudaSetDevice(ctx->device));
+    ctx->arena.reset();
+    float* acts = dalloc<float>(ctx, (int64_t)mlp_act_floats(B));
+    mlp_forward(params, X, B, acts, ctx->stream);
+    const int64_t out = (int64_t)mlp_act_floats(B) - B * kMlpDims[kMlpLayers];
+    FEAST_CUDA_TRY(cudaMemcpyAsync(Y, acts + out, sizeof(float) * B * kMlpDims[kMlpLayers], cudaMemcpyDeviceToDevice,
+                                   ctx->stream));
+    sync(ctx);
+    return FEAST_OK;
+  });
+}
+
+namespace {
+// forward + backward into grad; the loss (mean squared error) to the host
+double mlp_grad_run(feast_ctx* ctx, const float* params, const float* X, const float* T, int64_t B, float* grad) {
+  float* acts = dalloc<float>(ctx, (int64_t)mlp_act_floats(B));
+  float* d0 = dalloc<float>(ctx, B * 256);
+  float* d1 = dalloc<float>(ctx, B * 256);
+  const int dlast = kMlpDims[kMlpLayers];
+  float* sq = dalloc<float>(ctx, B * dlast);
+  mlp_forward(params, X, B, acts, ctx->stream);
+  mlp_backward(params, acts, T, B, grad, d0, d1, sq, ctx->stream);
+  std::vector<float> h((size_t)B * dlast);
+  to_host(ctx, h.data(), sq, B * dlast);
+  double acc = 0.0;
+  for (float v : h) acc += v;
+  return acc / ((double)B * dlast);
+}
+}  // namespace
+
+int feast_mlp_gradient(feast_ctx* ctx, const float* params, const float* X, const float* T, int64_t B, float* grad,
+                       double* loss) {
+  if (!ctx || !params || !X || !T || !grad || B < 1 || B > (1 << 22)) return FEAST_ERR_ARG;
+  return guarded(ctx, [&]() {
+    FEAST_CUDA_TRY(cudaSetDevice(ctx->device));
+    ctx->arena.reset();
+    const double l = mlp_grad_run(ctx, params, X, T, B, grad);
+    if (loss) *loss = l;
+    return FEAST_OK;
+  });
+}
+
+int feast_mlp_train_step(feast_ctx* ctx, float* params, float* m, float* v, const float* X, const float* T, int64_t B,
+                         int step, double lr, double* loss) {
+  if (!ctx || !params || !m || !v || !X || !T || B < 1 || B > (1 << 22) || step < 1 || !(lr > 0)) return FEAST_ERR_ARG;
+  return guarded(ctx, [&]() {
+    FEAST_CUDA_TRY(cudaSetDevice(ctx->device));
+    ctx->arena.reset();
+    float* grad = dalloc<float>(ctx, (int64_t)mlp_param_count());
+    const double l = mlp_grad_run(ctx, params, X, T, B, grad);
+    adam_update(params, grad, m, v, (int64_t)mlp_param_count(), step, (float)lr, ctx->stream);
+    sync(ctx);
+    if (loss) *loss = l;
+    return FEAST_OK;
+  });
 }
 
 int feast_interval_solve(feast_ctx* ctx, const void* A, int dtype, int64_t n, int64_t lda, double lmin, double lmax,

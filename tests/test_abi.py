@@ -66,3 +66,28 @@ def test_argument_errors_without_device(L):
     assert L.feast_contour_nodes(-1.0, 1.0, 0, 1.0, z.ctypes.data_as(dp), z.ctypes.data_as(dp)) == -1
     assert fg.feast_strerror(-5).startswith("subspace size")
     assert fg.feast_strerror(0) == "success"
+
+
+def test_offset_contour_nodes_match_oracle(L):
+    # the moved-node interpolatory rule: library (host code) against the oracle
+    for (a, b, nc) in [(-1.0, 1.0, 8), (0.5, 3.0, 3), (-7.0, 2.0, 16)]:
+        d = 0.2 * np.sin(np.arange(nc) + 1.0)
+        z, w = fg.feast_contour_nodes_offset(a, b, nc, d)
+        zo, wo = oracle.quadrature.contour_nodes_offset(a, b, nc, d)
+        np.testing.assert_allclose(z, zo, rtol=0, atol=1e-13 * max(1, abs(a), abs(b)))
+        np.testing.assert_allclose(w, wo, rtol=0, atol=1e-13 * max(1, abs(a), abs(b)))
+        z0, w0 = fg.feast_contour_nodes_offset(a, b, nc, np.zeros(nc))
+        zg, wg = fg.feast_contour_nodes(a, b, nc, 1.0)
+        np.testing.assert_allclose(z0, zg, atol=1e-14 * max(1, abs(a), abs(b)))
+    with pytest.raises(fg.FeastError):
+        fg.feast_contour_nodes_offset(-1.0, 1.0, 8, np.array([0, 0, 0, 3.0, -3.0, 0, 0, 0]))
+
+
+def test_moments_count_matches_oracle(L):
+    from oracle.density import count_estimate, exact_moments
+    lam = np.concatenate([np.linspace(-9, -2, 70), np.linspace(-0.6, 0.6, 25), np.linspace(2, 9, 70)])
+    mu = exact_moments(lam, 0.0, 10.0, 64)
+    for (a, b) in [(-1.3, 1.3), (-10.0, 10.0), (0.1, 5.0)]:
+        assert abs(fg.feast_moments_count(mu, 0.0, 10.0, a, b, lam.size)
+                   - count_estimate(mu, 0.0, 10.0, a, b, lam.size)) < 1e-9
+    assert fg.feast_mlp_param_count() == 64 * 256 + 256 + 2 * (256 * 256 + 256) + 256 * 9 + 9
