@@ -65,6 +65,9 @@ CGEMM_DRAM_BYTES_PER_FLOP = 171.81e9 / 5.2540e12
 CGEMM_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum over the 3151 cgemm_prefetch_kernel "
                         "launches of the n = 4096 solve (171.81 GB, cold-cache replay) / their 5.254e12 flops, "
                         "x flops per launch")
+# the same for the tensor-core cg_update_kernel (profiles/); None until captured
+TCG_DRAM_BYTES_PER_FLOP = None
+TCG_TRAFFIC_SOURCE = "not captured yet"
 
 
 
@@ -256,32 +259,56 @@ def aggregate_ranks(ms_total, pairs, world, device="cpu"):
 
 
 def tc_peak(peaks):
-    """Tensor-core roof of the complex-FP32 factorisation and solve GEMMs:
-    TF32 dense = the measured sustained bf16 rate x the nominal TF32:bf16
-    ratio 1:2 (the kernels run inside a seconds-long step)."""
+    """The measured sustained bf16 rate (the kernels run inside a seconds-long
+    step) and the dense TF32 roof derived from it (nominal TF32:bf16 1:2)."""
     bf16 = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0))
     return bf16 / 2.0, bf16
 
 
+# bf16 multiply-adds per complex multiply-add of the tensor-core complex-FP32
+# GEMM: 4 real products x 6 split products of three-part bf16 operands
+CG_BF16_PER_CMAC = 24
+
+
 def factor_solve_roofline(st, ms_step, peaks, peak_kind, sm_max):
-    """Roofline of the dominant kernel of the shifted factorisations and
-    solves (the complex-FP32 GEMM updates): achieved = its algorithmic flops
-    (8 per complex multiply-add, M N K per launch) / its CUDA-event time per
-    launch, against the tensor-core roof of the step's factorisation GEMMs."""
+    """Roofline of the GEMM updates of the shifted factorisations and solves:
+    on the tensor cores (cg_update_kernel) by default, on the FP32 SIMT pipes
+    (cgemm_prefetch_kernel) with --prec mixed_simt.  achieved = algorithmic
+    flops (8 per complex multiply-add, M N K per launch) / CUDA-event time per
+    launch.  Tensor cores: the FP32-exact products cost 24 bf16 multiply-adds
+    per complex multiply-add, so the roof of this arithmetic is the measured
+    sustained bf16 rate x 8/48; the fraction equals executed bf16 flops over
+    the bf16 rate."""
     tf32, bf16 = tc_peak(peaks)
+    fp32_simt = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    if st.tcgemm_launches > 0:
+        launches, ms, flop = st.tcgemm_launches, st.tcgemm_ms, st.tcgemm_flop
+        avg_ms = ms / launches
+        achieved = flop / launches / (avg_ms / 1e3) / 1e12
+        peak = bf16 * 8.0 / (2.0 * CG_BF16_PER_CMAC)
+        traffic = int(TCG_DRAM_BYTES_PER_FLOP * flop / launches) if TCG_DRAM_BYTES_PER_FLOP else None
+        return {"kernel": "cg_update_kernel (tcgen05 complex-FP32 GEMM updates of the LU and solves)",
+                "bound": "tensor", "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "peak_source": ("MEASURED_PEAKS.json bf16_tflops_sustained (%s, %.1f) x 8/48: 24 bf16 "
+                                "multiply-adds per complex-FP32 multiply-add" % (peak_kind, bf16)),
+                "flop_def": "8 real flops per complex multiply-add, M N K per launch",
+                "executed_bf16_tflops": round(achieved * 2 * CG_BF16_PER_CMAC / 8, 1),
+                "frac_of_tf32_roof": round(achieved / tf32, 4),
+                "traffic_source": TCG_TRAFFIC_SOURCE,
+                "launches_per_step": launches, "avg_launch_ms": round(avg_ms, 4),
+                "share_of_step": round(ms / ms_step, 3)}
     cg_launches = max(1, st.cgemm_launches)
     cg_avg_ms = st.cgemm_ms / cg_launches
     cg_flop_per_launch = st.cgemm_flop / cg_launches
     achieved = cg_flop_per_launch / (cg_avg_ms / 1e3) / 1e12 if st.cgemm_ms > 0 else 0.0
-    fp32_simt = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     traffic = int(CGEMM_DRAM_BYTES_PER_FLOP * cg_flop_per_launch) if CGEMM_DRAM_BYTES_PER_FLOP else None
     return {"kernel": "cgemm_prefetch_kernel (complex-FP32 GEMM updates of the LU and solves, SIMT)",
-            "bound": "tensor", "achieved": round(achieved, 3), "peak": round(tf32, 1), "unit": "TFLOP/s",
-            "frac": round(achieved / tf32, 4), "traffic": traffic,
-            "peak_source": ("dense TF32 tensor roof = MEASURED_PEAKS.json bf16_tflops_sustained (%s, %.1f) x "
-                            "nominal TF32:bf16 ratio 1/2" % (peak_kind, bf16)),
+            "bound": "alu", "achieved": round(achieved, 3), "peak": round(fp32_simt, 2), "unit": "TFLOP/s",
+            "frac": round(achieved / fp32_simt, 4), "traffic": traffic,
+            "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x max SM clock (unit counts)",
             "flop_def": "8 real flops per complex multiply-add, M N K per launch",
-            "frac_of_fp32_simt_lanes": round(achieved / fp32_simt, 4),
+            "frac_of_tf32_roof": round(achieved / tf32, 4),
             "traffic_source": CGEMM_TRAFFIC_SOURCE,
             "launches_per_step": st.cgemm_launches, "avg_launch_ms": round(cg_avg_ms, 4),
             "share_of_step": round(st.cgemm_ms / ms_step, 3)}
@@ -449,7 +476,7 @@ def run_ours(args, rank, world, dev):
     peaks, peak_kind = measured_peaks()
     clocks = clk.summary()
     sm_max = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    roofline = factor_solve_roofline(st, ms_step, peaks, peak_kind, sm_max)
+    roofline_fs = factor_solve_roofline(st, ms_step, peaks, peak_kind, sm_max)
     tf32_peak, _ = tc_peak(peaks)
 
     # the refinement GEMM: tensor-core digit-split GEMM by default,
@@ -480,12 +507,19 @@ def run_ours(args, rank, world, dev):
                                            "(152 SMs x 128 lanes x max SM clock)")}
     roofline_refine.update({"launches_per_step": st.refine_gemm_launches, "avg_launch_ms": round(rg_avg_ms, 3),
                             "share_of_step": round(st.refine_gemm_ms / ms_step, 3)})
+    # `roofline` is the kernel with the larger share of the step; the other
+    # tensor-core contraction is reported beside it
+    if roofline_refine["share_of_step"] > roofline_fs["share_of_step"]:
+        roofline, roofline_other, other_key = roofline_refine, roofline_fs, "roofline_factor_solve_gemm"
+    else:
+        roofline, roofline_other, other_key = roofline_fs, roofline_refine, "roofline_refine_gemm"
 
     # filter-apply rate: algorithmic flops of the solves (8 n^2 m per entry,
     # complex MAC = 8 real flops) per filter application, refinement excluded
     n, m0, nc = w["n"], w["m0"], w["n_c"]
     filt_flop = 2 * nc * 8.0 * n * n * m0
     filter_tflops = filt_flop * st.filters / (st.filter_ms / 1e3) / 1e12 if st.filter_ms > 0 else None
+    emu_peak = roofline_fs["peak"] if roofline_fs["bound"] == "tensor" else tf32_peak
 
     pe = errs[-1] or {}
     line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -506,13 +540,15 @@ def run_ours(args, rank, world, dev):
             "factor_ms": round(st.factor_ms, 1), "filter_ms": round(st.filter_ms, 1),
             "pairs_vs_planted": pe,
             "host_residual_max": float(hres.max()) if hres.size else None,
-            "roofline": roofline, "roofline_refine_gemm": roofline_refine,
+            "roofline": roofline, other_key: roofline_other,
             "filter_apply": {"tflops": round(filter_tflops, 3) if filter_tflops else None,
-                             "peak": round(tf32_peak, 1),
-                             "frac": round(filter_tflops / tf32_peak, 4) if filter_tflops else None,
+                             "peak": round(emu_peak, 1),
+                             "frac": round(filter_tflops / emu_peak, 4) if filter_tflops else None,
+                             "frac_of_tf32_roof": round(filter_tflops / tf32_peak, 4) if filter_tflops else None,
                              "flop_per_filter": filt_flop,
                              "note": ("solve flops 8 n^2 m0 per entry, 2 n_c entries, refinement excluded, over "
-                                      "the whole filter time (solves, refinement, accumulation); peak as roofline")},
+                                      "the whole filter time (solves, refinement, accumulation); peak: the "
+                                      "tensor-core roof of the complex-FP32 solve arithmetic (roofline_factor_solve)")},
             "e2e": {"value": round(e2e_found / e2e_steps / (e2e_ms / 1e3), 4), "unit": UNIT,
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_ms, 1)},
             "gpu_launches": int(launches), "clocks": clocks, "peak_source": peak_kind}
