@@ -368,6 +368,54 @@ def run_config1(fg, ctx, stream, dev, cpu):
     return line
 
 
+def run_config5(fg, ctx, stream, dev, n=32768):
+    """The largest single problem (real symmetric n = 32768, m0 = 1000, 700
+    eigenvalues in I, 80 within 1e-5 outside each edge; plain FEAST, mixed
+    precision): one timed solve after the matrix is built on the GPU."""
+    import torch
+    from workloads import spectrum_config5
+    from workloads.planted import planted_matrix_torch
+    lam, a, b = spectrum_config5(0, n=n, m_in=int(700 * n / 32768), edge_out=int(80 * n / 32768))
+    m0 = int(1000 * n / 32768)
+    t0 = time.time()
+    A = planted_matrix_torch(lam, 0, complex_=False, device=f"cuda:{dev}")
+    torch.cuda.synchronize()
+    build_s = time.time() - t0
+    torch.cuda.empty_cache()
+    inside = lam[(lam > a) & (lam < b)]
+    anorm = float(np.max(np.abs(lam)))
+    opts = fg.feast_opts_default(variant="feast", prec="mixed", anorm=anorm, max_iter=20)
+    # a context of its own: its workspace (about 200 GB at n = 32768) is freed after
+    ctx5 = fg.feast_init(dev, stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = fg.feast_interval_solve(ctx5, A, a, b, m0, 8, 1e-10, opts)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    pe = pair_errors(out["evals"], out["res"], inside, anorm)
+    hres = host_residuals(A, out["evecs"], out["evals"], anorm)
+    st = out["stats"]
+    free, total = torch.cuda.mem_get_info()
+    res = {"workload": f"real symmetric planted n={n}, {inside.size} eigenvalues in [-1,1], "
+                       f"{int(80 * n / 32768)}+{int(80 * n / 32768)} within 1e-5 outside the edges, bulk in [-50,50]; "
+                       f"n_c=8, m0={m0}, plain FEAST, mixed precision",
+           "ms_per_solve": round(ms, 1), "value": round(out["evals"].size / (ms / 1e3), 3), "unit": UNIT,
+           "iterations": out["iterations"], "filters": st.filters, "refine_steps": st.refine_steps,
+           "factor_ms": round(st.factor_ms, 1), "filter_ms": round(st.filter_ms, 1),
+           "tcgemm_tflops": round(st.tcgemm_flop / max(st.tcgemm_ms, 1e-9) / 1e9, 1),
+           "correct": bool(out["status"] == 0 and pe is not None and pe["gate"] and pe["residual_max"] <= 1e-10
+                           and hres.max() <= 2e-10),
+           "eig_rel_err_max": pe["eig_rel_err_max"] if pe else None,
+           "residual_max": pe["residual_max"] if pe else None,
+           "host_residual_max": float(hres.max()) if hres.size else None,
+           "matrix_build_s": round(build_s, 1), "device_free_gb_during": round(free / 1e9, 1)}
+    fg.feast_finalize(ctx5)
+    del A
+    torch.cuda.empty_cache()
+    return res
+
+
 def oracle_full_scaled(n):
     """The oracle timed in full on the benchmark workload scaled to n (same
     generator and readings), with its own iteration and filter counts."""
@@ -576,6 +624,10 @@ def run_ours(args, rank, world, dev):
                                  "eig_rel_diff_max": float(rel.max()) if rel is not None and rel.size else None,
                                  "eig_rel_diff": [float("%.3g" % v) for v in rel] if rel is not None else None}
 
+    # the largest single problem (opt-in: the matrix takes minutes to build)
+    if args.config5:
+        line["config5"] = run_config5(fg, ctx, stream, dev, n=args.config5)
+
     # the n = 500 plain FP64 FEAST workload (and its oracle timed in full)
     if args.config1:
         line["config1"] = run_config1(fg, ctx, stream, dev, args.cpu and world == 1)
@@ -678,6 +730,8 @@ def main():
     ap.add_argument("--no-fp64", dest="fp64", action="store_false")
     ap.add_argument("--no-cpu", dest="cpu", action="store_false")
     ap.add_argument("--no-config1", dest="config1", action="store_false")
+    ap.add_argument("--config5", type=int, default=0,
+                    help="also run the largest single problem at this n (32768 = full size; 0: skip)")
     ap.add_argument("--gen", default=WORKLOAD["gen"], choices=["torch_cpu", "torch_cuda", "numpy"],
                     help="generator of the Gaussian whose QR gives Q")
     ap.add_argument("--cpu-full-n", type=int, default=2048,

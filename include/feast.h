@@ -181,6 +181,36 @@ int feast_interval_solve(feast_ctx* ctx, const void* A, int dtype, int64_t n, in
                          const feast_opts* opts, double* evals, void* evecs, double* res,
                          int* m_found, int* iterations, feast_stats* stats);
 
+/* One problem of a batch (feast_interval_solve_batch): inputs and outputs as
+ * feast_interval_solve's, with its own device matrix, interval, m0 and n_c. */
+typedef struct {
+  const void* A;        /* device n x n, leading dim lda, dtype; not modified */
+  int dtype;
+  int64_t n, lda;
+  double lmin, lmax, tol;
+  int m0, n_c;
+  double* evals;        /* host, >= m0 doubles */
+  void* evecs;          /* device n x m0, leading dim n */
+  double* res;          /* host, >= m0 doubles */
+  int m_found, iterations, status;  /* outputs: pairs, outer iterations, return code */
+  int route;            /* output: FEAST_PREC_* the autotuner chose (mixed requests) */
+  double ms;            /* output: wall time of this problem's solve */
+} feast_problem;
+
+/* Many independent interval problems of uneven n and m0 (the intervals are
+ * independent, Sect. I): `workers` host threads, each with its own CUDA
+ * stream and context on `device`, take the problems largest first from a
+ * shared queue, so small problems run concurrently and fill the GPU.  With
+ * autotune != 0 and a mixed precision requested, the route of the complex-FP32
+ * GEMM updates (tensor cores, FEAST_PREC_MIXED, or SIMT, FEAST_PREC_MIXED_SIMT)
+ * is chosen per size bucket (n rounded up to 256) by timing both on a probe
+ * factorisation the first time the bucket is met (cached for the process).
+ * opts: shared by every problem (NULL = defaults; x0 must be NULL).  Returns
+ * FEAST_OK when every problem returned >= 0, else the first negative status;
+ * each problem's own status is in its `status`. */
+int feast_interval_solve_batch(int device, int nproblems, feast_problem* problems, const feast_opts* opts,
+                               int workers, int autotune);
+
 /* Y = rho(A) X by the quadrature of Eq. 3 over both half-contours: real A:
  * sum_j 2 Re(w_j (z_j I - A)^{-1} X); complex Hermitian A:
  * sum_j [w_j (z_j I - A)^{-1} + conj(w_j) (conj(z_j) I - A)^{-1}] X.

@@ -516,8 +516,10 @@ struct KernelTimer {
   double work[TIMER_CLASSES] = {};
   int launches[TIMER_CLASSES] = {};
 };
+// one timer per host thread: the batched solver runs problems on several
+// threads, each timing its own launches
 KernelTimer& kernel_timer() {
-  static KernelTimer t;
+  static thread_local KernelTimer t;
   return t;
 }
 std::atomic<unsigned long long> g_launches{0};

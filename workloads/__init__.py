@@ -14,6 +14,7 @@ from .planted import (  # noqa: F401
     spectrum_config2,
     spectrum_config3,
     spectrum_config4,
+    spectrum_config5,
     spectrum_paper,
     spectrum_uniform,
     make_problem,

@@ -165,6 +165,18 @@ def spectrum_config4(seed, n=2048):
     return lam, -1.0, 1.0, {"m": m, "cluster": c, "width": w, "edge_in": c_in, "edge_out": c_out}
 
 
+def spectrum_config5(seed=0, n=32768, m_in=700, edge_out=80, width=1e-5, bulk=50.0):
+    """The largest single problem: real symmetric n = 32768, 700 eigenvalues
+    uniform in I = [-1, 1], 80 packed within 1e-5 outside each edge (the
+    hard case of Sect. I: eigenvalues just outside the interval), the rest
+    uniform in [-50, 50] outside I and the edge bands (m0 = 1000, n_c = 8
+    upper-half nodes)."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 5]))
+    lam = spectrum_edge_clusters(rng, n, m_in, -1.0, 1.0, -bulk, bulk, n_edge_in=0, n_edge_out=edge_out,
+                                 width=width)
+    return lam, -1.0, 1.0
+
+
 def spectrum_paper(kind, seed=0, n=545, m_in=50):
     """The two n = 545 spectra of the paper's Sect. III experiments: 50
     eigenvalues in I = [-1, 1]; the other 495 in [1.01, 20.81] ("Sparse") or
