@@ -416,6 +416,45 @@ def run_config5(fg, ctx, stream, dev, n=32768):
     return res
 
 
+def run_config3(fg, dev, count=64, workers=8):
+    """The batched workload: `count` independent real symmetric problems of
+    uneven n (512..4096) and m0, mixed precision, plain FEAST: one batch on a
+    pool of streams (autotuned route) against the same problems one after
+    another on one stream; both timed on the host clock around the call."""
+    import torch
+    from workloads.planted import planted_matrix_torch, spectrum_config3
+    probs, inside = [], []
+    for seed in range(count):
+        lam, a, b, m0, n_c = spectrum_config3(seed)
+        A = planted_matrix_torch(lam, seed, complex_=False, device=f"cuda:{dev}")
+        probs.append({"A": A, "lmin": a, "lmax": b, "m0": m0, "n_c": n_c, "tol": 1e-10})
+        inside.append(lam[(lam > a) & (lam < b)])
+    torch.cuda.synchronize()
+    opts = fg.feast_opts_default(prec="mixed", max_iter=40)
+    fg.feast_interval_solve_batch(probs[:2], opts, workers=2, autotune=True)   # warm-up, fills the tuner
+    res = {}
+    for label, w in (("batched", workers), ("sequential", 1)):
+        torch.cuda.synchronize()
+        t0 = time.time()
+        out = fg.feast_interval_solve_batch(probs, opts, workers=w, autotune=True)
+        torch.cuda.synchronize()
+        t = time.time() - t0
+        ok = sum(int(r["status"] == 0 and r["evals"].size == ins.size and
+                     np.all(np.abs(r["evals"] - ins) <= 1e-10 * np.abs(ins) + 1e-12 * np.max(np.abs(ins))))
+                 for r, ins in zip(out, inside))
+        pairs = sum(r["evals"].size for r in out)
+        res[label] = {"workers": w, "seconds": round(t, 3), "value": round(pairs / t, 2), "unit": UNIT,
+                      "pairs": pairs, "problems_correct": ok,
+                      "routes": {"tensor": sum(r["route"] == fg.FEAST_PREC_MIXED for r in out),
+                                 "simt": sum(r["route"] == fg.FEAST_PREC_MIXED_SIMT for r in out)}}
+    res["workload"] = (f"{count} real symmetric planted problems, n in 512..4096, 10..170 eigenvalues in each own "
+                       "interval with edge clusters, m0 = ceil(1.5 m), n_c in {8, 16}; plain FEAST, mixed")
+    res["speedup"] = round(res["sequential"]["seconds"] / res["batched"]["seconds"], 3)
+    del probs
+    torch.cuda.empty_cache()
+    return res
+
+
 def oracle_full_scaled(n):
     """The oracle timed in full on the benchmark workload scaled to n (same
     generator and readings), with its own iteration and filter counts."""
@@ -624,6 +663,10 @@ def run_ours(args, rank, world, dev):
                                  "eig_rel_diff_max": float(rel.max()) if rel is not None and rel.size else None,
                                  "eig_rel_diff": [float("%.3g" % v) for v in rel] if rel is not None else None}
 
+    # the batched uneven workload (opt-in)
+    if args.config3:
+        line["config3"] = run_config3(fg, dev, count=args.config3)
+
     # the largest single problem (opt-in: the matrix takes minutes to build)
     if args.config5:
         line["config5"] = run_config5(fg, ctx, stream, dev, n=args.config5)
@@ -730,6 +773,8 @@ def main():
     ap.add_argument("--no-fp64", dest="fp64", action="store_false")
     ap.add_argument("--no-cpu", dest="cpu", action="store_false")
     ap.add_argument("--no-config1", dest="config1", action="store_false")
+    ap.add_argument("--config3", type=int, default=0,
+                    help="also run the batched workload with this many problems (64 = full; 0: skip)")
     ap.add_argument("--config5", type=int, default=0,
                     help="also run the largest single problem at this n (32768 = full size; 0: skip)")
     ap.add_argument("--gen", default=WORKLOAD["gen"], choices=["torch_cpu", "torch_cuda", "numpy"],

@@ -34,6 +34,7 @@ EXPORTS = [
     "feast_jacobi_eigh", "feast_rayleigh_ritz", "feast_kernel_launches", "feast_jacobi_eigh_noalloc",
     "feast_gemm_f64acc", "feast_contour_nodes_offset", "feast_spectral_moments", "feast_moments_count",
     "feast_mlp_param_count", "feast_mlp_forward", "feast_mlp_gradient", "feast_mlp_train_step",
+    "feast_interval_solve_batch",
 ]
 
 
@@ -55,6 +56,14 @@ class FeastStats(ctypes.Structure):
                 ("cgemm_launches", ctypes.c_int), ("cgemm_ms", ctypes.c_double), ("cgemm_flop", ctypes.c_double),
                 ("tcgemm_launches", ctypes.c_int), ("tcgemm_ms", ctypes.c_double), ("tcgemm_flop", ctypes.c_double),
                 ("rr_passes", ctypes.c_int), ("rr_k_sum", ctypes.c_double), ("rr_k3_sum", ctypes.c_double)]
+
+
+class FeastProblem(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("dtype", ctypes.c_int), ("n", ctypes.c_int64), ("lda", ctypes.c_int64),
+                ("lmin", ctypes.c_double), ("lmax", ctypes.c_double), ("tol", ctypes.c_double),
+                ("m0", ctypes.c_int), ("n_c", ctypes.c_int), ("evals", ctypes.c_void_p), ("evecs", ctypes.c_void_p),
+                ("res", ctypes.c_void_p), ("m_found", ctypes.c_int), ("iterations", ctypes.c_int),
+                ("status", ctypes.c_int), ("route", ctypes.c_int), ("ms", ctypes.c_double)]
 
 
 class FeastError(RuntimeError):
@@ -100,6 +109,7 @@ def lib():
         "feast_mlp_forward": (I, [P, P, P, I64, P]),
         "feast_mlp_gradient": (I, [P, P, P, P, I64, P, DP]),
         "feast_mlp_train_step": (I, [P, P, P, P, P, P, I64, I, D, DP]),
+        "feast_interval_solve_batch": (I, [I, I, ctypes.POINTER(FeastProblem), ctypes.POINTER(FeastOpts), I, I]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -412,6 +422,34 @@ def feast_gemm_f64acc(ctx, A, B, method=0, transA=False, transB=False, alpha=1.0
                                    float(alpha), _ptr(A), A.shape[0], _ptr(B), B.shape[0], float(beta), _ptr(C), M),
            "feast_gemm_f64acc")
     return C
+
+
+def feast_interval_solve_batch(problems, opts: FeastOpts | None = None, workers=4, autotune=True, device=0):
+    """Solve many independent problems concurrently.  problems: list of dicts
+    with A (CUDA, Hermitian), lmin, lmax, m0, n_c, tol.  Returns a list of
+    dicts (status, evals, evecs, res, iterations, route, ms) in input order."""
+    keep = []
+    arr = (FeastProblem * len(problems))()
+    for i, p in enumerate(problems):
+        A = colmajor(p["A"])
+        n = A.shape[0]
+        ev = np.zeros(p["m0"])
+        rs = np.zeros(p["m0"])
+        V = empty_colmajor(n, p["m0"], A.dtype, A.device)
+        keep.append((A, ev, rs, V))
+        arr[i] = FeastProblem(A.data_ptr(), _dtype_code(A), n, n, float(p["lmin"]), float(p["lmax"]),
+                              float(p.get("tol", 1e-10)), int(p["m0"]), int(p.get("n_c", 8)), ev.ctypes.data,
+                              V.data_ptr(), rs.ctypes.data, 0, 0, 0, 0, 0.0)
+    opts = opts or feast_opts_default()
+    _check(lib().feast_interval_solve_batch(int(device), len(problems), arr, ctypes.byref(opts), int(workers),
+                                            int(bool(autotune))), "feast_interval_solve_batch")
+    out = []
+    for i in range(len(problems)):
+        A, ev, rs, V = keep[i]
+        m = arr[i].m_found
+        out.append({"status": arr[i].status, "evals": ev[:m].copy(), "evecs": V[:, :m], "res": rs[:m].copy(),
+                    "iterations": arr[i].iterations, "route": arr[i].route, "ms": arr[i].ms})
+    return out
 
 
 class Feast:

@@ -123,7 +123,7 @@ def spectrum_config2(seed=0, n=8192, m_in=200, edge_in=30, edge_out=60,
     return lam, -1.0, 1.0
 
 
-def spectrum_config3(seed):
+def spectrum_config3(seed, scale=1.0):
     """One problem of the batched workload (64 independent real symmetric
     problems, seeds 0..63): n uniform in 512..4096, m uniform in 10..170
     eigenvalues inside the problem's own interval, an edge cluster of 2..20
@@ -134,9 +134,16 @@ def spectrum_config3(seed):
     rng = np.random.default_rng(np.random.SeedSequence([seed, 3]))
     n = int(rng.integers(512, 4097))
     m = int(rng.integers(10, 171))
+    if scale != 1.0:    # the same draw scaled down (small parity cases)
+        n = max(64, int(n * scale))
+        m = max(4, int(m * scale))
     cl = int(rng.integers(2, 21))
     c_in = min(cl // 2, m // 2)
     c_out = cl - cl // 2
+    if scale != 1.0:
+        cl = max(2, int(cl * scale))
+        c_in = min(cl // 2, m // 2)
+        c_out = cl - cl // 2
     c = float(rng.uniform(-5.0, 5.0))
     r = float(rng.uniform(0.5, 2.0))
     lmin, lmax = c - r, c + r
