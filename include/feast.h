@@ -181,6 +181,23 @@ int feast_interval_solve(feast_ctx* ctx, const void* A, int dtype, int64_t n, in
                          const feast_opts* opts, double* evals, void* evecs, double* res,
                          int* m_found, int* iterations, feast_stats* stats);
 
+/* The generalized problem A x = lambda B x with A Hermitian and B Hermitian
+ * positive definite (the extension of FEAST to A x = lambda B x, Sect. I):
+ * eigenpairs with lambda in (lmin, lmax).  B = R^H R (Cholesky) reduces it
+ * to the standard problem C y = lambda y with C = R^{-H} A R^{-1}, which
+ * feast_interval_solve solves (same options; opts.anorm is ignored, ||C|| is
+ * estimated; opts.x0 must be NULL); the eigenvectors x = R^{-1} y are
+ * returned B-orthonormal (x^H B x = 1).  B: device n x n, leading dim ldb,
+ * dtype of A, not modified.  res: relative residuals of the reduced
+ * problem, ||C y - lambda y|| / ||C||_2 = ||R^{-H}(A x - lambda B x)|| /
+ * ||C||_2.  n * element size <= 200 KB (the Cholesky kernel keeps a column in
+ * shared memory).  Returns FEAST_ERR_ARG when B is not numerically positive
+ * definite; otherwise as feast_interval_solve. */
+int feast_interval_solve_gen(feast_ctx* ctx, const void* A, const void* B, int dtype, int64_t n, int64_t lda,
+                             int64_t ldb, double lmin, double lmax, int m0, int n_c, double tol,
+                             const feast_opts* opts, double* evals, void* evecs, double* res, int* m_found,
+                             int* iterations, feast_stats* stats);
+
 /* One problem of a batch (feast_interval_solve_batch): inputs and outputs as
  * feast_interval_solve's, with its own device matrix, interval, m0 and n_c. */
 typedef struct {

@@ -362,3 +362,63 @@ def _rfeast(A, F, lmin, lmax, m0, tol, X0, s, max_iter, anorm, expand, response_
         if response_stop and any(rp.res[sel[c]] <= tol for c in in_cols):
             pend = {"in_cols": in_cols, "res": rp.res[sel], "sel": sel, "rp": rp, "m": m_expected}
     return _result(1, rp, ins, max_iter, filters, hist, m_expected, dims=dims)
+
+
+# --------------------------------------------------------------------------
+# the generalized problem A x = lambda B x (B Hermitian positive definite)
+# --------------------------------------------------------------------------
+def feast_solve_generalized(A, B, lmin, lmax, m0, n_c, tol, X0, max_iter=100, aspect=1.0):
+    """Plain FEAST for A x = lambda B x as the FEAST Algorithm states it with
+    B (Appendix: A' = X'^H A X', B' = X'^H B X'): the filter
+    sum_j w_j (z_j B - A)^{-1} B X (both half-contours), the subspace
+    B-orthonormalised (Cholesky of X'^H B X', twice) so that B' = I, then the
+    standard reduced problem.  Residual: ||A x - lambda B x|| / ((||A|| +
+    |lambda| ||B||) ||x||), the backward error of the pencil, with the
+    2-norms of A and B from eigvalsh (test infrastructure)."""
+    from .dense import cholesky_upper, solve_right_upper
+    A = np.asarray(A)
+    B = np.asarray(B)
+    n = A.shape[0]
+    cplx = np.iscomplexobj(A) or np.iscomplexobj(B)
+    an = float(np.max(np.abs(np.linalg.eigvalsh(A))))
+    bn = float(np.max(np.abs(np.linalg.eigvalsh(B))))
+    z, w = contour_nodes(lmin, lmax, n_c, aspect)
+    lus = [lu_factor(zj * B - A) for zj in z]
+
+    def filt(X):
+        BX = B @ X
+        if cplx:
+            out = np.zeros(X.shape, dtype=np.complex128)
+            for wj, (LU, piv) in zip(w, lus):
+                out += wj * lu_solve(LU, piv, BX) + np.conj(wj) * lu_solve_adjoint(LU, piv, BX)
+            return out
+        out = np.zeros(X.shape)
+        for wj, (LU, piv) in zip(w, lus):
+            out += 2.0 * np.real(wj * lu_solve(LU, piv, BX))
+        return out
+
+    def b_orth(X):
+        for _ in range(2):
+            G = X.conj().T @ (B @ X)
+            R = cholesky_upper(0.5 * (G + G.conj().T))
+            X = solve_right_upper(X, R)
+        return X
+
+    X = np.array(X0, copy=True)
+    hist = []
+    for it in range(1, max_iter + 1):
+        Q = b_orth(filt(X))
+        Ar = Q.conj().T @ (A @ Q)
+        lam, V, _ = jacobi_eigh(0.5 * (Ar + Ar.conj().T))
+        X = Q @ V
+        R = A @ X - (B @ X) * lam[None, :]
+        res = np.linalg.norm(R, axis=0) / ((an + np.abs(lam) * bn) * np.linalg.norm(X, axis=0))
+        ins = np.where(inside(lam, lmin, lmax))[0]
+        r = float(np.max(res[ins])) if ins.size else np.inf
+        hist.append(r)
+        if (ins.size and r <= tol) or (ins.size == 0 and it >= 2):
+            return FeastResult(status=0, lam=lam[ins], X=X[:, ins], res=res[ins], iterations=it, filters=it,
+                               history=hist)
+    ins = np.where(inside(lam, lmin, lmax))[0]
+    return FeastResult(status=1, lam=lam[ins], X=X[:, ins], res=res[ins], iterations=max_iter, filters=max_iter,
+                       history=hist)

@@ -34,7 +34,7 @@ EXPORTS = [
     "feast_jacobi_eigh", "feast_rayleigh_ritz", "feast_kernel_launches", "feast_jacobi_eigh_noalloc",
     "feast_gemm_f64acc", "feast_contour_nodes_offset", "feast_spectral_moments", "feast_moments_count",
     "feast_mlp_param_count", "feast_mlp_forward", "feast_mlp_gradient", "feast_mlp_train_step",
-    "feast_interval_solve_batch",
+    "feast_interval_solve_batch", "feast_interval_solve_gen",
 ]
 
 
@@ -110,6 +110,8 @@ def lib():
         "feast_mlp_gradient": (I, [P, P, P, P, I64, P, DP]),
         "feast_mlp_train_step": (I, [P, P, P, P, P, P, I64, I, D, DP]),
         "feast_interval_solve_batch": (I, [I, I, ctypes.POINTER(FeastProblem), ctypes.POINTER(FeastOpts), I, I]),
+        "feast_interval_solve_gen": (I, [P, P, P, I, I64, I64, I64, D, D, I, I, D, ctypes.POINTER(FeastOpts),
+                                         DP, P, DP, IP, IP, ctypes.POINTER(FeastStats)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -309,6 +311,30 @@ def feast_interval_solve(ctx, A, lmin, lmax, m0, n_c, tol, opts: FeastOpts | Non
                                       res.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                       ctypes.byref(mf), ctypes.byref(it), ctypes.byref(st))
     _check(code, "feast_interval_solve")
+    m = mf.value
+    return {"status": code, "evals": evals[:m].copy(), "evecs": V[:, :m], "res": res[:m].copy(),
+            "iterations": it.value, "stats": st}
+
+
+def feast_interval_solve_gen(ctx, A, B, lmin, lmax, m0, n_c, tol, opts: FeastOpts | None = None):
+    """Eigenpairs of A x = lambda B x (A Hermitian, B Hermitian positive
+    definite, CUDA tensors) with lambda in (lmin, lmax); eigenvectors
+    B-orthonormal."""
+    A = colmajor(A)
+    B = colmajor(B.to(A.dtype))
+    n = A.shape[0]
+    opts = opts or feast_opts_default()
+    evals = np.zeros(m0)
+    res = np.zeros(m0)
+    V = empty_colmajor(n, m0, A.dtype, A.device)
+    mf, it = ctypes.c_int(0), ctypes.c_int(0)
+    st = FeastStats()
+    code = lib().feast_interval_solve_gen(ctx, _ptr(A), _ptr(B), _dtype_code(A), n, n, n, float(lmin), float(lmax),
+                                          int(m0), int(n_c), float(tol), ctypes.byref(opts),
+                                          evals.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(V),
+                                          res.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(mf),
+                                          ctypes.byref(it), ctypes.byref(st))
+    _check(code, "feast_interval_solve_gen")
     m = mf.value
     return {"status": code, "evals": evals[:m].copy(), "evecs": V[:, :m], "res": res[:m].copy(),
             "iterations": it.value, "stats": st}

@@ -69,6 +69,7 @@ struct feast_ctx {
   cudaStream_t stream = nullptr;
   int num_sms = 0;
   Arena arena;
+  Arena aux;   // the generalized solve's reduction (kept across the inner solve's arena resets)
   feast_stats last{};
 };
 
@@ -1562,6 +1563,7 @@ int feast_finalize(feast_ctx* ctx) {
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   ctx->arena.release();
+  ctx->aux.release();
   delete ctx;
   return FEAST_OK;
 }
@@ -1741,6 +1743,62 @@ int feast_interval_solve(feast_ctx* ctx, const void* A, int dtype, int64_t n, in
     return solve_t<c128>(ctx, (const c128*)A, n, lda, lmin, lmax, m0, n_c, tol, o, evals, (c128*)evecs, res, m_found,
                          iterations, stats);
   });
+}
+
+int feast_interval_solve_gen(feast_ctx* ctx, const void* A, const void* B, int dtype, int64_t n, int64_t lda,
+                             int64_t ldb, double lmin, double lmax, int m0, int n_c, double tol, const feast_opts* opts,
+                             double* evals, void* evecs, double* res, int* m_found, int* iterations,
+                             feast_stats* stats) {
+  if (int r = check_common(ctx, A, dtype, n, lda, lmin, lmax, n_c)) return r;
+  if (!B || ldb < n || m0 < 1 || m0 > n || !(tol > 0) || !evals || !evecs || !res || !m_found || !iterations)
+    return FEAST_ERR_ARG;
+  const size_t es = dtype == FEAST_R64 ? sizeof(double) : sizeof(c128);
+  if (es * (size_t)n > 200 * 1024) return FEAST_ERR_ARG;  // the Cholesky kernel keeps a column in shared memory
+  feast_opts o;
+  if (opts) o = *opts; else feast_opts_default(&o);
+  o.anorm = 0.0;   // ||C|| is estimated for the reduced matrix
+  if (o.x0) return FEAST_ERR_ARG;
+  *m_found = 0;
+  *iterations = 0;
+  int status = guarded(ctx, [&]() {
+    FEAST_CUDA_TRY(cudaSetDevice(ctx->device));
+    ctx->aux.reset();
+    auto run = [&](auto tag) -> int {
+      using S = decltype(tag);
+      auto aux = [&](int64_t count) { return (S*)ctx->aux.alloc(sizeof(S) * (size_t)std::max<int64_t>(count, 1)); };
+      const cudaStream_t st = ctx->stream;
+      if (int r = check_finite_dev<S>(ctx, (const S*)B, n, n, ldb)) return r;
+      // B = R^H R (Cholesky, upper), Ri = R^{-1}, C = Ri^H A Ri
+      S* Rb = aux(n * n);
+      S* Ri = aux(n * n);
+      S* T = aux(n * n);
+      S* C = aux(n * n);
+      CoopWork cw = coop_work_carve(ctx->aux.alloc(coop_work_bytes(n, ctx->num_sms)), n, ctx->num_sms);
+      copy_matrix<S>(Rb, n, (const S*)B, ldb, n, n, st);
+      cholesky_upper<S>(Rb, n, n, cw, ctx->num_sms, st);
+      int info = 0, cst = 0;
+      to_host(ctx, &info, cw.info, 1);
+      to_host(ctx, &cst, cw.status, 1);
+      if (cst == DEV_BARRIER_TIMEOUT) return FEAST_ERR_TIMEOUT;
+      if (info != 0) return FEAST_ERR_ARG;   // B not numerically positive definite
+      tri_inverse_upper<S>(Rb, n, n, Ri, n, st);
+      gemm_simple<S, S, S>(n, n, n, C1(1.0), (const S*)A, lda, OP_N, Ri, n, OP_N, C1(0.0), T, n, st);
+      gemm_simple<S, S, S>(n, n, n, C1(1.0), Ri, n, OP_C, T, n, OP_N, C1(0.0), C, n, st);
+      hermitize<S>(C, n, n, st);
+      sync(ctx);
+      // the standard problem C y = lambda y, then x = Ri y (B-orthonormal)
+      S* Y = aux(n * m0);
+      const int r = solve_t<S>(ctx, C, n, n, lmin, lmax, m0, n_c, tol, o, evals, Y, res, m_found, iterations, stats);
+      if (r < 0) return r;
+      if (*m_found > 0)
+        gemm_simple<S, S, S>(n, *m_found, n, C1(1.0), Ri, n, OP_N, Y, n, OP_N, C1(0.0), (S*)evecs, n, st);
+      sync(ctx);
+      return r;
+    };
+    if (dtype == FEAST_R64) return run(double{});
+    return run(c128{});
+  });
+  return status;
 }
 
 int feast_filter_apply(feast_ctx* ctx, const void* A, int dtype, int64_t n, int64_t lda, double lmin, double lmax,

@@ -291,3 +291,29 @@ def test_filter_closed_form_n2048(ctx, prec):
     # their backward error (FP64 LU, or refinement to 16 eps sqrt(n))
     err = np.abs(Y - ref).max() / np.abs(X).max()
     assert err <= 2e-10, err
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+@pytest.mark.parametrize("prec", ["f64", "mixed"])
+def test_generalized_problem_vs_oracle(ctx, cplx, prec):
+    # A x = lambda B x (planted pencil): the library's Cholesky-reduced solve
+    # against the oracle's generalized FEAST with B-inner products (a
+    # different algorithm for the same eigenpairs) and the planted values
+    from workloads.planted import planted_pencil
+    lam, a, b = spectrum_uniform(300, 14, seed=9, bulk=8.0)
+    A, B, X = planted_pencil(lam, 9, complex_=cplx)
+    out = fg.feast_interval_solve_gen(ctx, cuda(A), cuda(B), a, b, 21, 8, 1e-10,
+                                      fg.feast_opts_default(prec=prec))
+    assert out["status"] == 0
+    ins = (lam > a) & (lam < b)
+    assert out["evals"].size == ins.sum()
+    np.testing.assert_allclose(out["evals"], lam[ins], rtol=1e-10, atol=1e-12 * np.abs(lam).max())
+    V = host(out["evecs"])
+    assert np.abs(V.conj().T @ B @ V - np.eye(V.shape[1])).max() < 1e-9
+    an = np.abs(lam).max()
+    bn = np.abs(np.linalg.eigvalsh(B)).max()
+    R = A @ V - (B @ V) * out["evals"][None, :]
+    assert np.max(np.linalg.norm(R, axis=0) / ((an + np.abs(out["evals"]) * bn) * np.linalg.norm(V, axis=0))) < 1e-10
+    ref = O.feast.feast_solve_generalized(A, B, a, b, 21, 8, 1e-10, random_subspace(300, 21, seed=2, complex_=cplx))
+    assert ref.status == 0
+    np.testing.assert_allclose(out["evals"], ref.lam, rtol=1e-10, atol=1e-12 * an)

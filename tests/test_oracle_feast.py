@@ -269,3 +269,28 @@ def test_invariant_start_converges_in_one_round(variant):
     assert r.res.max() < 1e-13
     if variant == O.RFEAST:
         assert r.m_expected == ins.size
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_generalized_feast_on_planted_pencil(cplx):
+    # A x = lambda B x with B = L L^H, A = L Q diag(lam) Q^H L^H: the oracle's
+    # generalized FEAST (filter (z B - A)^{-1} B X, B-orthonormal subspace)
+    # returns the planted eigenvalues, B-orthonormal vectors spanning the
+    # planted ones, and agrees with LAPACK's generalized eigvalsh
+    from scipy.linalg import eigh
+    from workloads.planted import planted_pencil
+    lam, a, b = spectrum_uniform(70, 7, seed=6, bulk=8.0)
+    A, B, X = planted_pencil(lam, 6, complex_=cplx)
+    X0 = random_subspace(70, 11, seed=2, complex_=cplx)
+    r = O.feast.feast_solve_generalized(A, B, a, b, 11, 8, 1e-10, X0)
+    assert r.status == 0
+    ins = (lam > a) & (lam < b)
+    np.testing.assert_allclose(r.lam, lam[ins], atol=1e-11 * np.abs(lam).max())
+    ev = eigh(A, B, eigvals_only=True)
+    np.testing.assert_allclose(r.lam, ev[(ev > a) & (ev < b)], atol=1e-11 * np.abs(lam).max())
+    G = r.X.conj().T @ B @ r.X
+    assert np.abs(G - np.eye(G.shape[0])).max() < 1e-10
+    Xi = X[:, ins]
+    # span: the planted B-orthonormal vectors are combinations of the returned ones
+    C = r.X.conj().T @ B @ Xi
+    assert np.linalg.norm(Xi - r.X @ C) < 1e-8

@@ -222,6 +222,26 @@ def planted_matrix(Q, lam):
     return np.asfortranarray(A)
 
 
+def planted_pencil(lam, seed, complex_=False, cond=10.0):
+    """A planted generalized problem A x = lambda B x: B = L L^H with L lower
+    triangular (seeded, diagonal in [1, cond]), Q Haar, A = L Q diag(lam) Q^H
+    L^H, so the eigenvalues are lam and the B-orthonormal eigenvectors are
+    X = L^{-H} Q.  Returns (A, B, X), Fortran order."""
+    n = lam.size
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0xB]))
+    Lm = np.tril(rng.standard_normal((n, n)), -1) / np.sqrt(n)
+    if complex_:
+        Lm = Lm + 1j * np.tril(rng.standard_normal((n, n)), -1) / np.sqrt(n)
+    Lm = Lm + np.diag(rng.uniform(1.0, cond, n))
+    Q = haar_unitary(n, seed + 2000, complex_)
+    LQ = Lm @ Q
+    A = (LQ * lam[None, :]) @ LQ.conj().T
+    B = Lm @ Lm.conj().T
+    X = np.linalg.solve(Lm.conj().T, Q)
+    return (np.asfortranarray(0.5 * (A + A.conj().T)), np.asfortranarray(0.5 * (B + B.conj().T)),
+            np.asfortranarray(X))
+
+
 def random_subspace(n, m, seed, complex_=False):
     """Seeded N(0,1) starting subspace X0 (n x m), Fortran order.  Complex
     entries have independent N(0, 1/2) real and imaginary parts."""
