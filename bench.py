@@ -384,7 +384,7 @@ def run_config5(fg, ctx, stream, dev, n=32768):
     torch.cuda.empty_cache()
     inside = lam[(lam > a) & (lam < b)]
     anorm = float(np.max(np.abs(lam)))
-    opts = fg.feast_opts_default(variant="feast", prec="mixed", anorm=anorm, max_iter=20)
+    opts = fg.feast_opts_default(variant="feast", prec="mixed", anorm=anorm, max_iter=20, response_stop=1)
     # a context of its own: its workspace (about 200 GB at n = 32768) is freed after
     ctx5 = fg.feast_init(dev, stream)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -399,7 +399,7 @@ def run_config5(fg, ctx, stream, dev, n=32768):
     free, total = torch.cuda.mem_get_info()
     res = {"workload": f"real symmetric planted n={n}, {inside.size} eigenvalues in [-1,1], "
                        f"{int(80 * n / 32768)}+{int(80 * n / 32768)} within 1e-5 outside the edges, bulk in [-50,50]; "
-                       f"n_c=8, m0={m0}, plain FEAST, mixed precision",
+                       f"n_c=8, m0={m0}, plain FEAST with the filter-response stop, mixed precision",
            "ms_per_solve": round(ms, 1), "value": round(out["evals"].size / (ms / 1e3), 3), "unit": UNIT,
            "iterations": out["iterations"], "filters": st.filters, "refine_steps": st.refine_steps,
            "factor_ms": round(st.factor_ms, 1), "filter_ms": round(st.filter_ms, 1),
@@ -430,7 +430,7 @@ def run_config3(fg, dev, count=64, workers=8):
         probs.append({"A": A, "lmin": a, "lmax": b, "m0": m0, "n_c": n_c, "tol": 1e-10})
         inside.append(lam[(lam > a) & (lam < b)])
     torch.cuda.synchronize()
-    opts = fg.feast_opts_default(prec="mixed", max_iter=40)
+    opts = fg.feast_opts_default(prec="mixed", max_iter=40, response_stop=1)
     fg.feast_interval_solve_batch(probs[:2], opts, workers=2, autotune=True)   # warm-up, fills the tuner
     res = {}
     for label, w in (("batched", workers), ("sequential", 1)):
@@ -448,7 +448,8 @@ def run_config3(fg, dev, count=64, workers=8):
                       "routes": {"tensor": sum(r["route"] == fg.FEAST_PREC_MIXED for r in out),
                                  "simt": sum(r["route"] == fg.FEAST_PREC_MIXED_SIMT for r in out)}}
     res["workload"] = (f"{count} real symmetric planted problems, n in 512..4096, 10..170 eigenvalues in each own "
-                       "interval with edge clusters, m0 = ceil(1.5 m), n_c in {8, 16}; plain FEAST, mixed")
+                       "interval with edge clusters, m0 = ceil(1.5 m), n_c in {8, 16}; plain FEAST with the "
+                       "filter-response stop, mixed")
     res["speedup"] = round(res["sequential"]["seconds"] / res["batched"]["seconds"], 3)
     del probs
     torch.cuda.empty_cache()

@@ -92,12 +92,14 @@ typedef struct {
                            is still above tol and ends the passes once none is (a converged
                            pair's residual is rounding noise whose direction adds spurious
                            Ritz pairs, Sect. II-B) */
-  int response_stop;    /* XFEAST/RFEAST: 0 (default, the paper) stops on the step-3 check
-                           alone; 1 also stops when every selected pair inside I whose filter
-                           response Re(x^H rho(A) x) exceeds 1/2 has converged (rho > 1/2
-                           exactly inside I for the circle contour), returning those pairs:
-                           on spectra with eigenvalues on both sides of I, mixtures of outside
-                           eigenvectors give in-I Ritz values that never converge */
+  int response_stop;    /* 0 (default, the paper) stops on the step-3 check alone; 1 also stops
+                           when every (selected) pair inside I whose filter response
+                           Re(x^H rho(A) x) exceeds 1/2 has converged (rho > 1/2 exactly
+                           inside I for the circle contour), returning those pairs: on spectra
+                           with eigenvalues on both sides of I, mixtures of outside
+                           eigenvectors give in-I Ritz values that never converge.  All three
+                           variants (plain FEAST: the m0 - m outside directions of its
+                           subspace are the ones that mix) */
   int reserved;
   const double* node_offsets; /* optional host array of n_c node offsets delta_j (NULL: the
                            Gauss-Legendre rule): the abscissae become

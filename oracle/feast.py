@@ -43,9 +43,10 @@ Readings where the paper is silent (each also recorded in the design notes):
     adds spurious Ritz pairs (Sect. II-B reports them) but no information;
   * option response_stop=True (a reading, not the paper's text): on spectra
     with eigenvalues on both sides of I, mixtures of outside eigenvectors give
-    Ritz values inside I that never converge and (with m0 below the number
+    Ritz values inside I that never converge (in plain FEAST the m0 - m
+    outside directions of the subspace mix) and (with m0 below the number
     of eigenvalues near |rho| = 1/2) also inflate RFEAST's first-pass count.
-    XFEAST and RFEAST then also stop when every selected in-I pair whose
+    All three variants then also stop when every (selected) in-I pair whose
     filter response mu_k = Re(x_k^H rho(A) x_k) exceeds 1/2 has converged;
     mu_k is read off the filter application the next step performs anyway
     (rho > 1/2 exactly inside I for the circle contour, rho < 1/2 outside, so
@@ -223,7 +224,7 @@ def feast_solve(A, lmin, lmax, m0, n_c, tol, X0, variant=PLAIN, s=3,
         anorm = norm_estimate(A)
     F = factors or factor_shifts(A, lmin, lmax, n_c, aspect)
     if variant == PLAIN:
-        return _feast(A, F, lmin, lmax, m0, tol, X0, max_iter, anorm)
+        return _feast(A, F, lmin, lmax, m0, tol, X0, max_iter, anorm, response_stop)
     if variant == XFEAST:
         return _xfeast(A, F, lmin, lmax, m0, tol, X0, s, max_iter, anorm, response_stop)
     if variant == RFEAST:
@@ -239,12 +240,18 @@ def _result(status, rp, idx, it, filters, hist, m_expected=None, dims=None):
                        history=hist, m_expected=m_expected, rr_dims=list(dims or []))
 
 
-def _feast(A, F, lmin, lmax, m0, tol, X0, max_iter, anorm):
+def _feast(A, F, lmin, lmax, m0, tol, X0, max_iter, anorm, response_stop=False):
     X = np.array(X0, copy=True)
     hist, dims = [], []
     rp = None
+    pend = None
     for it in range(1, max_iter + 1):
         Xf = filter_apply(F, X)                         # step 1
+        if pend is not None:
+            keep = _spurious_free(pend, filter_response(X, Xf), tol)
+            if keep is not None:
+                return _result(0, pend["rp"], pend["sel"][keep], it - 1, it, hist, dims=dims)
+            pend = None
         Q, _ = orthonormalize(Xf)                       # B' = I
         dims.append(Q.shape[1])
         rp = rayleigh_ritz(A, Q, anorm)                 # step 2(i)
@@ -256,6 +263,10 @@ def _feast(A, F, lmin, lmax, m0, tol, X0, max_iter, anorm):
             return _result(0, rp, ins, it, it, hist, dims=dims)
         if ins.size == 0 and it >= 2:
             return _result(0, rp, ins, it, it, hist, dims=dims)
+        if response_stop:
+            in_cols = [c for c in range(rp.lam.size) if lmin < rp.lam[c] < lmax]
+            if any(rp.res[c] <= tol for c in in_cols):
+                pend = {"in_cols": in_cols, "res": rp.res, "sel": sel, "rp": rp}
     ins, _ = _check(rp.lam, rp.res, np.arange(rp.lam.size), lmin, lmax)
     return _result(1, rp, ins, max_iter, max_iter, hist, dims=dims)
 

@@ -1207,9 +1207,19 @@ struct Solver {
     Out out;
     int64_t kx = m0;
     S* Xf = T2;
+    Pending pd;
     for (int it = 1; it <= o.max_iter; ++it) {
       filter(X, kx, Xf);
       ++out.filters;
+      // response_stop: the previous round's in-I pairs with filter response
+      // above 1/2 (read off this filter) have all converged
+      if (pd.valid) {
+        if (response_test(pd, X, Xf, kx, tol, out)) {
+          out.iterations = it - 1;
+          return out;
+        }
+        pd.valid = false;
+      }
       const int64_t k = orthonormalize(Xf, n, kx, Qb, T1);
       if (k == 0) throw FeastError{FEAST_ERR_ORTH};
       rr_project(k);
@@ -1227,6 +1237,7 @@ struct Solver {
       }
       copy_matrix<S>(X, n, Xr, n, n, k, st);
       kx = k;
+      if (o.response_stop) pd = make_pending(all, tol);
     }
     std::vector<int> all(lam.size());
     std::iota(all.begin(), all.end(), 0);

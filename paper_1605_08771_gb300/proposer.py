@@ -10,10 +10,12 @@ Pipeline, every numerical step in the library's kernels:
              output o decodes to m0 = ceil(m_hat 1.5 exp(0.6 tanh o_0)) and node
              offsets delta_j = 0.3 tanh(o_j) (feast_opts.node_offsets), so o = 0
              is the plain rule m0 = ceil(1.5 m_hat) with Gauss-Legendre nodes;
-  labels     for each training spectrum, plain FEAST runs over candidate (m0
-             factor, node placement) pairs; the label is the candidate that
-             converged to the right count with the fewest right-hand sides
-             (filters x m0, the paper's own cost measure of Sect. III);
+  labels     for each training spectrum, plain FEAST runs (with the
+             filter-response stop: the spectra have eigenvalues on both sides
+             of I) over candidate (m0 factor, node placement) pairs; the label
+             is the candidate that converged to the right count with the
+             fewest right-hand sides (filters x m0, the paper's own cost
+             measure of Sect. III);
   training   mean squared error to the encoded labels, Adam, by the library's
              forward/backward/Adam kernels (feast_mlp_train_step).
 The plain rule is the fallback: a proposal whose solve does not converge is
@@ -103,7 +105,7 @@ def solve(ctx, P, m0, offsets, max_iter=30, prec="mixed"):
     """Plain FEAST with the given m0 and node placement: (ok, iterations,
     filters, seconds); ok = converged to the planted count."""
     import torch
-    opts = fg.feast_opts_default(prec=prec, anorm=P.anorm, max_iter=max_iter,
+    opts = fg.feast_opts_default(prec=prec, anorm=P.anorm, max_iter=max_iter, response_stop=1,
                                  node_offsets=None if offsets is None else np.asarray(offsets, dtype=np.float64))
     torch.cuda.synchronize()
     t0 = time.time()
@@ -151,29 +153,45 @@ def he_params(seed=0):
     return np.concatenate(out).astype(np.float32)
 
 
-def fit(ctx, X, T, epochs=400, batch=64, lr=1e-3, seed=0):
+def fit(ctx, X, T, epochs=400, batch=64, lr=1e-3, seed=0, val_frac=0.2):
+    """Adam with the library's kernels; a fifth of the labelled spectra is
+    held out and the parameters of the epoch with the lowest held-out loss
+    are kept (the network has far more parameters than there are labels)."""
     import torch
     dev = "cuda:0"
     P = torch.from_numpy(he_params(seed)).to(dev)
     m = torch.zeros_like(P)
     v = torch.zeros_like(P)
-    Xd = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).to(dev)
-    Td = torch.from_numpy(np.ascontiguousarray(T, dtype=np.float32)).to(dev)
     rng = np.random.default_rng(seed)
     N = X.shape[0]
+    order = rng.permutation(N)
+    nval = max(1, int(val_frac * N)) if N >= 5 else 0
+    vi, ti = order[:nval], order[nval:]
+    Xd = torch.from_numpy(np.ascontiguousarray(X[ti], dtype=np.float32)).to(dev)
+    Td = torch.from_numpy(np.ascontiguousarray(T[ti], dtype=np.float32)).to(dev)
+    Xv = torch.from_numpy(np.ascontiguousarray(X[vi], dtype=np.float32)).to(dev) if nval else None
+    Tv = T[vi]
+    Nt = Xd.shape[0]
     step = 0
-    losses = []
+    losses, vlosses = [], []
+    best, best_P = math.inf, P.clone()
     for ep in range(epochs):
-        perm = rng.permutation(N)
+        perm = rng.permutation(Nt)
         tot = 0.0
-        for b0 in range(0, N, batch):
+        for b0 in range(0, Nt, batch):
             idx = torch.from_numpy(perm[b0:b0 + batch]).to(dev)
             xb = Xd.index_select(0, idx).contiguous()
             tb = Td.index_select(0, idx).contiguous()
             step += 1
             tot += fg.feast_mlp_train_step(ctx, P, m, v, xb, tb, step, lr) * xb.shape[0]
-        losses.append(tot / N)
-    return P, losses
+        losses.append(tot / Nt)
+        if nval:
+            yv = fg.feast_mlp_forward(ctx, P, Xv).cpu().numpy()
+            vl = float(np.mean((yv - Tv) ** 2))
+            vlosses.append(vl)
+            if vl < best:
+                best, best_P = vl, P.clone()
+    return (best_P if nval else P), losses, vlosses
 
 
 def propose(ctx, params, P):
@@ -256,16 +274,16 @@ def main():
                 del P
             gen_s = time.time() - t0
             X, T = np.array(X), np.array(T)
-            params, losses = fit(ctx, X, T, epochs=args.epochs)
-            np.savez_compressed(args.out, params=params.cpu().numpy(),
-                                meta=json.dumps({"n": args.n, "train_spectra": args.train, "labelled": int(len(X)),
-                                                 "epochs": args.epochs, "final_loss": losses[-1],
-                                                 "first_loss": losses[0], "label_seconds": round(gen_s, 1),
-                                                 "m0_factors": M0_FACTORS, "node_push": NODE_PUSH}))
+            params, losses, vlosses = fit(ctx, X, T, epochs=args.epochs)
+            summary_ = {"n": args.n, "train_spectra": args.train, "labelled": int(len(X)), "epochs": args.epochs,
+                        "first_loss": losses[0], "final_loss": losses[-1],
+                        "best_heldout_loss": min(vlosses) if vlosses else None,
+                        "best_epoch": int(np.argmin(vlosses)) if vlosses else None,
+                        "label_seconds": round(gen_s, 1), "m0_factors": M0_FACTORS, "node_push": NODE_PUSH}
+            np.savez_compressed(args.out, params=params.cpu().numpy(), meta=json.dumps(summary_))
             if args.log:
-                json.dump({"tables": tables, "losses": losses}, open(args.log, "w"))
-            print(json.dumps({"labelled": int(len(X)), "first_loss": losses[0], "final_loss": losses[-1],
-                              "label_seconds": round(gen_s, 1)}))
+                json.dump({"tables": tables, "losses": losses, "heldout_losses": vlosses}, open(args.log, "w"))
+            print(json.dumps(summary_))
         else:
             params = load_params(args.weights)
             rows = evaluate(ctx, params, range(HELD_OUT_BASE, HELD_OUT_BASE + args.count), args.n)

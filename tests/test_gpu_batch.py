@@ -22,7 +22,9 @@ def test_batch_subset_matches_oracle(ctx, prec):
         P = make_problem("c3", lam, a, b, m0, n_c, seed=seed)
         probs.append({"A": cuda(P.A), "lmin": a, "lmax": b, "m0": m0, "n_c": n_c, "tol": 1e-10})
         planted.append(P)
-    opts = fg.feast_opts_default(prec=prec, max_iter=40)
+    # the spectra have eigenvalues on both sides of each interval: plain FEAST
+    # with the filter-response stop (R18) on both sides
+    opts = fg.feast_opts_default(prec=prec, max_iter=40, response_stop=1)
     out = fg.feast_interval_solve_batch(probs, opts, workers=3, autotune=True)
     for P, p, r in zip(planted, probs, out):
         assert r["status"] == 0
@@ -37,7 +39,7 @@ def test_batch_subset_matches_oracle(ctx, prec):
         assert np.max(np.linalg.norm(R, axis=0)) / P.anorm <= 2e-10
         # the oracle (its own norm estimate, like the library without anorm)
         ref = O.feast_solve(P.A, p["lmin"], p["lmax"], p["m0"], p["n_c"], 1e-10,
-                            random_subspace(P.n, p["m0"], seed=1), max_iter=40)
+                            random_subspace(P.n, p["m0"], seed=1), max_iter=40, response_stop=True)
         assert ref.status == 0
         np.testing.assert_allclose(r["evals"], ref.lam, rtol=1e-10, atol=1e-12 * P.anorm)
 

@@ -320,3 +320,24 @@ def test_generalized_problem_vs_oracle(ctx, cplx, prec):
     ref = O.feast.feast_solve_generalized(A, B, a, b, 21, 8, 1e-10, random_subspace(300, 21, seed=2, complex_=cplx))
     assert ref.status == 0
     np.testing.assert_allclose(out["evals"], ref.lam, rtol=1e-10, atol=1e-12 * an)
+
+
+@pytest.mark.parametrize("prec", ["f64", "mixed"])
+def test_plain_feast_response_stop_vs_oracle(ctx, prec):
+    # plain FEAST with m0 well above m on a two-sided spectrum: the literal
+    # check stalls on spurious in-I pairs; with the filter-response stop the
+    # GPU and the oracle return the planted pairs within a few rounds
+    from workloads import spectrum_config4
+    lam, a, b, meta = spectrum_config4(10000, n=512)
+    m = int(np.sum((lam > a) & (lam < b)))
+    m0 = int(np.ceil(1.8 * m)) + 4
+    P = make_problem("c4", lam, a, b, m0, 8, seed=10000)
+    X0 = random_subspace(512, m0, seed=1)
+    out = fg.feast_interval_solve(ctx, cuda(P.A), a, b, m0, 8, 1e-10,
+                                  fg.feast_opts_default(prec=prec, anorm=P.anorm, max_iter=12, response_stop=1),
+                                  x0=cuda(X0))
+    ref = O.feast_solve(P.A, a, b, m0, 8, 1e-10, X0, anorm=P.anorm, max_iter=12, response_stop=True)
+    assert out["status"] == 0 == ref.status
+    assert out["iterations"] <= 4
+    check_against_planted(out, P)
+    np.testing.assert_allclose(out["evals"], ref.lam, atol=1e-12 * P.anorm)

@@ -71,35 +71,27 @@ def test_mlp_forward_and_gradient_match_oracle(ctx):
 
 
 def test_adam_step_matches_oracle(ctx):
+    # three Adam steps of the kernel against the oracle's update applied to
+    # the kernel's own gradient and parameters (the gradients themselves are
+    # compared above; here only the update arithmetic is)
     import torch
     rng = np.random.default_rng(2)
     ps = init_params(seed=8)
     B = 16
-    X = rng.standard_normal((B, 64))
-    T = rng.standard_normal((B, 9))
-    flat = pack(ps)
+    X = rng.standard_normal((B, 64)).astype(np.float32)
+    T = rng.standard_normal((B, 9)).astype(np.float32)
     dev = "cuda:0"
-    P = torch.from_numpy(flat.copy()).to(dev)
+    P = torch.from_numpy(pack(ps)).to(dev)
     m = torch.zeros_like(P)
     v = torch.zeros_like(P)
-    Xd = torch.from_numpy(X.astype(np.float32)).to(dev)
-    Td = torch.from_numpy(T.astype(np.float32)).to(dev)
-    p64 = [x.astype(np.float64) for x in unpack(flat)]
-    mo = [np.zeros_like(x) for x in p64]
-    vo = [np.zeros_like(x) for x in p64]
-    X64, T64 = X.astype(np.float32).astype(np.float64), T.astype(np.float32).astype(np.float64)
-    g1 = backward(p64, X64, T64)
+    Xd = torch.from_numpy(X).to(dev)
+    Td = torch.from_numpy(T).to(dev)
+    mo = [np.zeros(P.numel())]
+    vo = [np.zeros(P.numel())]
     lr = 1e-3
     for step in (1, 2, 3):
+        g, _ = fg.feast_mlp_gradient(ctx, P, Xd, Td)
+        ref = [host(P).astype(np.float64)]
+        adam_step(ref, [host(g).astype(np.float64)], mo, vo, step, lr=lr)
         fg.feast_mlp_train_step(ctx, P, m, v, Xd, Td, step, lr)
-        adam_step(p64, backward(p64, X64, T64), mo, vo, step, lr=lr)
-    got = unpack(host(P).astype(np.float64))
-    for a_, b_, g in zip(got, p64, g1):
-        # Adam moves every coordinate by about lr per step whatever the size
-        # of its gradient, so where the gradient is at the FP32 rounding level
-        # of the kernels the two sides may step differently (at most 2 lr per
-        # step); elsewhere they must agree closely
-        d = np.abs(a_ - b_)
-        big = np.abs(g) > 1e-3 * np.abs(g).max()
-        assert d[big].max() <= 2e-5
-        assert d.max() <= 6 * lr
+        assert np.abs(host(P) - ref[0]).max() <= 1e-3 * lr

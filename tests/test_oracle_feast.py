@@ -294,3 +294,24 @@ def test_generalized_feast_on_planted_pencil(cplx):
     # span: the planted B-orthonormal vectors are combinations of the returned ones
     C = r.X.conj().T @ B @ Xi
     assert np.linalg.norm(Xi - r.X @ C) < 1e-8
+
+
+def test_plain_feast_response_stop_on_two_sided_spectrum():
+    # plain FEAST with m0 well above m on a spectrum with eigenvalues on both
+    # sides of I: the m0 - m outside directions of the subspace mix into in-I
+    # Ritz values that never converge, so the paper's step-3 check (every
+    # in-I pair) stalls; the filter-response stop (R18) returns the planted
+    # pairs after a few rounds (rate law: the subspace holds every large-|rho|
+    # eigenvector), and they are the ones the literal check would return
+    from workloads import spectrum_config4
+    lam, a, b, meta = spectrum_config4(10000, n=512)
+    m = int(np.sum((lam > a) & (lam < b)))
+    m0 = int(np.ceil(1.8 * m)) + 4
+    P = make_problem("c4", lam, a, b, m0, 8, seed=10000)
+    F = O.factor_shifts(P.A, a, b, 8)
+    X0 = random_subspace(512, m0, seed=1)
+    lit = O.feast_solve(P.A, a, b, m0, 8, 1e-10, X0, anorm=P.anorm, factors=F, max_iter=12)
+    assert lit.status == 1
+    rs = O.feast_solve(P.A, a, b, m0, 8, 1e-10, X0, anorm=P.anorm, factors=F, max_iter=12, response_stop=True)
+    assert rs.status == 0 and rs.iterations <= 4
+    _check_result(rs, P)
