@@ -19,11 +19,11 @@
 // Operands are split once into K-major bf16 planes (cg_split; the factor
 // panels of the solves once per factorisation) and loaded by TMA.
 //
-// Kernel: persistent, one 128 x 128 complex output tile at a time per CTA,
-// six warps.  Warp 0 issues the TMA loads (64B swizzle, 32 k of all twelve
+// Kernel: persistent, one 128 x BN complex output tile at a time per CTA
+// (BN = 128, or 112 when that pads fewer columns), six warps.  Warp 0 issues the TMA loads (64B swizzle, 32 k of all twelve
 // planes per stage, two stages); one thread of warp 1 issues tcgen05.mma
-// kind::f16 (M = 128, N = 128, K = 16) into a Re and an Im accumulator of
-// 128 TMEM columns each, double-buffered across tiles so the next tile's
+// kind::f16 (M = 128, N = BN, K = 16) into a Re and an Im accumulator of
+// BN TMEM columns each, double-buffered across tiles so the next tile's
 // products overlap this tile's epilogue; warps 2-5 read the accumulators
 // back (lane = output row) and apply C -= D to the complex-FP32 C in place.
 // Every mbarrier wait is bounded; on expiry the kernel records the failure,
@@ -39,25 +39,29 @@ namespace feast {
 
 namespace {
 
-constexpr int CG_BM = kCgTileM, CG_BN = kCgTileN, CG_BK = kCgChunk;
+constexpr int CG_BM = kCgTileM, CG_BK = kCgChunk;
 constexpr int CG_P = kCgPlanes;
 constexpr int CG_STAGES = 2;
 constexpr int CG_A_TILE = CG_BM * CG_BK * 2;                     // 8 KB
-constexpr int CG_B_TILE = CG_BN * CG_BK * 2;                     // 8 KB
-constexpr int CG_STAGE_BYTES = CG_P * (CG_A_TILE + CG_B_TILE);   // 96 KB
-constexpr int CG_SMEM = CG_STAGES * CG_STAGE_BYTES + 1024 + 256;
-constexpr int CG_TMEM_COLS = 512;                                // 2 buffers x (Re, Im) x 128
+constexpr int CG_TMEM_COLS = 512;                                // 2 buffers x (Re, Im) x BN
 constexpr int CG_EPI_WARPS = 4;
 constexpr int CG_THREADS = 32 * (2 + CG_EPI_WARPS);
 
-static_assert(4 * CG_BN <= CG_TMEM_COLS, "TMEM columns");
-static_assert(CG_SMEM <= 227 * 1024, "shared memory");
-
-// kind::f16 instruction descriptor: D = F32 (bits 4-5 = 1), A = B = BF16
-// (bits 7-9, 10-12 = 1), both K-major, N >> 3 in 17-22, M >> 4 in 24-28;
-// bit 13 negates A.
-constexpr uint32_t kIdesc =
-    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(CG_BN >> 3) << 17) | ((uint32_t)(CG_BM >> 4) << 24);
+// Tile width BN (128, or 112 for the solves' 300 right-hand sides: 3 tiles
+// of 112 compute 336 columns, 3 of 128 compute 384)
+template <int BN> struct CgTile {
+  static constexpr int B_TILE = BN * CG_BK * 2;                  // 8 KB or 7 KB
+  static constexpr int STAGE_BYTES = CG_P * (CG_A_TILE + B_TILE);
+  static constexpr int SMEM = CG_STAGES * STAGE_BYTES + 1024 + 256;
+  // kind::f16 instruction descriptor: D = F32 (bits 4-5 = 1), A = B = BF16
+  // (bits 7-9, 10-12 = 1), both K-major, N >> 3 in 17-22, M >> 4 in 24-28;
+  // bit 13 negates A.
+  static constexpr uint32_t IDESC =
+      (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(CG_BM >> 4) << 24);
+  static_assert(4 * BN <= CG_TMEM_COLS, "TMEM columns");
+  static_assert(SMEM <= 227 * 1024, "shared memory");
+  static_assert(BN % 16 == 0 && B_TILE % 512 == 0, "MMA N and 64B-swizzle alignment");
+};
 constexpr uint32_t kNegA = 1u << 13;
 
 __device__ __forceinline__ void mma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t accum) {
@@ -75,10 +79,14 @@ struct OpCoords {
   int base_row, node_rows, slab_rows, plane_rows, cps;  // cps: 32-wide k chunks per slab
 };
 
+template <int CG_BN>
 __global__ void __launch_bounds__(CG_THREADS, 1)
 cg_update_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, OpCoords ca,
                  OpCoords cb, int kchunks, int R, int N, int mtiles, int ntiles, int nodes, c64* C, int64_t ldc,
                  int64_t cstride, int* status) {
+  constexpr int CG_B_TILE = CgTile<CG_BN>::B_TILE;
+  constexpr int CG_STAGE_BYTES = CgTile<CG_BN>::STAGE_BYTES;
+  constexpr uint32_t kIdesc = CgTile<CG_BN>::IDESC;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = (uint64_t*)(smem + CG_STAGES * CG_STAGE_BYTES);  // full[2] empty[2] tfull[2] tempty[2] final
@@ -359,24 +367,35 @@ void cg_update(const CgOperand& A, const CgOperand& B, int64_t K, int64_t R, int
   if (R <= 0 || N <= 0 || K <= 0 || nodes <= 0) return;
   const int kchunks = (int)cdiv(K, CG_BK);
   const int64_t lim = (int64_t)1 << 31;
-  if (A.total_rows + CG_BM >= lim || B.total_rows + CG_BN >= lim || A.kdim % CG_BK || B.kdim % CG_BK ||
+  if (A.total_rows + CG_BM >= lim || B.total_rows + 128 >= lim || A.kdim % CG_BK || B.kdim % CG_BK ||
       A.kslab % CG_BK || B.kslab % CG_BK || A.kslab <= 0 || B.kslab <= 0 || R >= lim || N >= lim)
     throw CudaFailure(cudaErrorInvalidValue);
+  // the tile width that computes the fewest padded columns (ties: 128)
+  const int bn = (cdiv(N, 112) * 112 < cdiv(N, 128) * 128) ? 112 : 128;
   CUtensorMap mA, mB;
   make_map(&mA, A.planes, A.total_rows, A.kdim, CG_BM);
-  make_map(&mB, B.planes, B.total_rows, B.kdim, CG_BN);
+  make_map(&mB, B.planes, B.total_rows, B.kdim, bn);
   static std::once_flag attr;
   cudaError_t aerr = cudaSuccess;
   std::call_once(attr, [&] {
-    aerr = cudaFuncSetAttribute(cg_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, CG_SMEM);
+    aerr = cudaFuncSetAttribute(cg_update_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, CgTile<128>::SMEM);
+    if (aerr == cudaSuccess)
+      aerr = cudaFuncSetAttribute(cg_update_kernel<112>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  CgTile<112>::SMEM);
   });
   FEAST_CUDA_TRY(aerr);
-  const int mtiles = (int)cdiv(R, CG_BM), ntiles = (int)cdiv(N, CG_BN);
+  const int mtiles = (int)cdiv(R, CG_BM), ntiles = (int)cdiv(N, bn);
   const int64_t tiles = (int64_t)mtiles * ntiles * nodes;
   const unsigned grid = (unsigned)std::min<int64_t>(tiles, num_sms);
   kernel_timer_launch_begin(TIMER_TCGEMM, s);
-  cg_update_kernel<<<grid, CG_THREADS, CG_SMEM, s>>>(mA, mB, coords(A), coords(B), kchunks, (int)R, (int)N, mtiles,
-                                                     ntiles, nodes, C, ldc, cstride, status);
+  if (bn == 112)
+    cg_update_kernel<112><<<grid, CG_THREADS, CgTile<112>::SMEM, s>>>(mA, mB, coords(A), coords(B), kchunks, (int)R,
+                                                                      (int)N, mtiles, ntiles, nodes, C, ldc, cstride,
+                                                                      status);
+  else
+    cg_update_kernel<128><<<grid, CG_THREADS, CgTile<128>::SMEM, s>>>(mA, mB, coords(A), coords(B), kchunks, (int)R,
+                                                                      (int)N, mtiles, ntiles, nodes, C, ldc, cstride,
+                                                                      status);
   FEAST_LAUNCH_CHECK();
   kernel_timer_launch_end(TIMER_TCGEMM, s, 8.0 * (double)R * (double)N * (double)K * nodes);
 }

@@ -95,3 +95,4 @@ def test_adam_step_matches_oracle(ctx):
         adam_step(ref, [host(g).astype(np.float64)], mo, vo, step, lr=lr)
         fg.feast_mlp_train_step(ctx, P, m, v, Xd, Td, step, lr)
         assert np.abs(host(P) - ref[0]).max() <= 1e-3 * lr
+
