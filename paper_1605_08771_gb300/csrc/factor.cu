@@ -407,7 +407,8 @@ __global__ void form_shifted_kernel(F* M, int64_t n, int64_t ld, int64_t stride,
 template <typename F, int TB>
 __global__ void __launch_bounds__(256)
 trsm_diag_kernel(const F* M, int64_t ld, int64_t stride, F* Y, int64_t n, int64_t m,
-                 int64_t ystride, int64_t r0, int bs, int mode) {
+                 int64_t ystride, int64_t r0, int bs, int mode, uint16_t* planes = nullptr, int64_t mpad = 0,
+                 int kdim = 0, int koff = 0) {
   constexpr int R = TB / 32;
   const int b = blockIdx.y;
   const F* Mb = M + (int64_t)b * stride;
@@ -471,6 +472,29 @@ trsm_diag_kernel(const F* M, int64_t ld, int64_t stride, F* Y, int64_t n, int64_
 #pragma unroll
   for (int r = 0; r < R; ++r)
     if (lane + 32 * r < bs) y[lane + 32 * r] = x[r];
+  // complex-FP32 solves on the tensor cores: the solved block also goes out
+  // as the six bf16 planes of the right operand of the block updates
+  // (K-major, K offset koff; zero past bs)
+  if constexpr (std::is_same<F, c64>::value) {
+    if (planes) {
+      const int64_t plane = mpad * kdim;
+      uint16_t* o = planes + (int64_t)b * 6 * plane + cidx * kdim + koff;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int t = lane + 32 * r;
+        const F v = t < bs ? x[r] : num<F>::zero();
+        uint16_t a0, a1, a2, b0, b1, b2;
+        cg_split3(v.re, a0, a1, a2);
+        cg_split3(v.im, b0, b1, b2);
+        o[t] = a0;
+        o[plane + t] = a1;
+        o[2 * plane + t] = a2;
+        o[3 * plane + t] = b0;
+        o[4 * plane + t] = b1;
+        o[5 * plane + t] = b2;
+      }
+    }
+  }
 }
 
 // solve block rows: 64 for complex-FP32 factors, 32 for complex-FP64 (whose
@@ -710,22 +734,8 @@ void lu_solve_batched(const F* M, int64_t n, int64_t ld, int64_t stride, int nod
   dim3 gd((unsigned)cdiv(m, 8), nodes);
   bool tc = false;
   if constexpr (std::is_same<F, c64>::value) tc = sp != nullptr && (!adjoint || sp->row) && m <= sp->mpad;
-  // block update Y[c_off + i] -= op(block of the factor) Y[k_off + j]: on the
-  // tensor cores (planes of the factor's 64-column block b, or of its
-  // conjugated 64-row block for the adjoint solves, rows from p_row), or SIMT
-  auto update = [&](int64_t rows, int64_t k, const F* a, int opA, int64_t c_off, int64_t k_off, int64_t b,
-                    int64_t p_row) {
-    if constexpr (std::is_same<F, c64>::value) {
-      if (tc) {
-        cg_split(Y, ystride, 0, n, k_off, 0, false, false, m, k, kSolveBlock, 1, sp->mpad, kSolveBlock, nodes,
-                 sp->rhs, s);
-        const CgOperand B = cg_operand(sp->rhs, sp->mpad, kSolveBlock, nodes);
-        CgOperand A = cg_operand(adjoint ? sp->row : sp->col, sp->npad, kSolveBlock, nodes, sp->nblk, kSolveBlock);
-        A.base_row = b * A.slab_rows + p_row;
-        cg_update(A, B, k, rows, m, Y + c_off, n, ystride, nodes, status, num_sms, s);
-        return;
-      }
-    }
+  // SIMT block update Y[c_off + i] -= op(block of the factor at a) Y[k_off + j]
+  auto update = [&](int64_t rows, int64_t k, const F* a, int opA, int64_t c_off, int64_t k_off) {
     GemmArgs g{};
     g.M = rows; g.N = m; g.K = k;
     g.A = a; g.opA = opA; g.lda = ld; g.strideA = stride;
@@ -746,8 +756,8 @@ void lu_solve_batched(const F* M, int64_t n, int64_t ld, int64_t stride, int nod
       const int64_t r1 = r0 + bs;
       diag(r0, bs, adjoint ? 1 : 0);
       if (r1 < upd_end) {
-        if (!adjoint) update(upd_end - r1, bs, M + r1 + r0 * ld, OP_N, r1, r0, r0 / TBK, r1);
-        else update(upd_end - r1, bs, M + r0 + r1 * ld, OP_C, r1, r0, r0 / TBK, r1);
+        if (!adjoint) update(upd_end - r1, bs, M + r1 + r0 * ld, OP_N, r1, r0);
+        else update(upd_end - r1, bs, M + r0 + r1 * ld, OP_C, r1, r0);
       }
     }
   };
@@ -758,8 +768,8 @@ void lu_solve_batched(const F* M, int64_t n, int64_t ld, int64_t stride, int nod
       const int bs = (int)std::min<int64_t>(TBK, b1 - r0);
       diag(r0, bs, adjoint ? 3 : 2);
       if (r0 > upd_begin) {
-        if (!adjoint) update(r0 - upd_begin, bs, M + upd_begin + r0 * ld, OP_N, upd_begin, r0, r0 / TBK, upd_begin);
-        else update(r0 - upd_begin, bs, M + r0 + upd_begin * ld, OP_C, upd_begin, r0, r0 / TBK, upd_begin);
+        if (!adjoint) update(r0 - upd_begin, bs, M + upd_begin + r0 * ld, OP_N, upd_begin, r0);
+        else update(r0 - upd_begin, bs, M + r0 + upd_begin * ld, OP_C, upd_begin, r0);
       }
     }
   };
@@ -772,26 +782,44 @@ void lu_solve_batched(const F* M, int64_t n, int64_t ld, int64_t stride, int nod
     // two levels on the tensor cores: 256-row outer blocks solved by 64-row
     // diagonal blocks with updates confined to the outer block, then one
     // rank-256 update of every row past it (four times fewer passes over the
-    // right-hand sides than rank-64 updates)
+    // right-hand sides than rank-64 updates).  Each diagonal-block solve also
+    // writes its block as bf16 planes into the outer block's right-operand
+    // buffer (K offset = its row offset in the outer block), which both the
+    // inner and the outer updates read: no separate split launches.
     const int64_t OB = kSolveOuter;
-    auto outer_update = [&](int64_t R0, int64_t R1, int64_t rows, int64_t c_off) {
-      const int64_t kb = R1 - R0;
-      cg_split(Y, ystride, 0, n, R0, 0, false, false, m, kb, kSolveOuter, 1, sp->mpad, kSolveOuter, nodes, sp->rhs,
-               s);
-      const CgOperand B = cg_operand(sp->rhs, sp->mpad, kSolveOuter, nodes);
-      CgOperand A = cg_operand(adjoint ? sp->row : sp->col, sp->npad, kSolveBlock, nodes, sp->nblk, kSolveBlock);
-      A.base_row = (R0 / kSolveBlock) * A.slab_rows + c_off;
-      cg_update(A, B, kb, rows, m, Y + c_off, n, ystride, nodes, status, num_sms, s);
+    const CgOperand Abase = cg_operand(adjoint ? sp->row : sp->col, sp->npad, kSolveBlock, nodes, sp->nblk,
+                                       kSolveBlock);
+    auto diag_tc = [&](int64_t r0, int bs, int mode, int64_t R0) {
+      trsm_diag_kernel<F, TBK><<<gd, 256, 0, s>>>(M, ld, stride, Y, n, m, ystride, r0, bs, mode, sp->rhs, sp->mpad,
+                                                  kSolveOuter, (int)(r0 - R0));
+      FEAST_LAUNCH_CHECK();
+    };
+    // Y[c_off .. c_off + rows) -= A_rows(blocks from R0 / 64, K = k) B(K offset kx)
+    auto tc_update = [&](int64_t R0, int64_t kx, int64_t k, int64_t rows, int64_t c_off) {
+      CgOperand B = cg_operand(sp->rhs, sp->mpad, kSolveOuter, nodes);
+      B.base_x = (int)kx;
+      CgOperand A = Abase;
+      A.base_row = ((R0 + kx) / kSolveBlock) * A.slab_rows + c_off;
+      cg_update(A, B, k, rows, m, Y + c_off, n, ystride, nodes, status, num_sms, s);
     };
     for (int64_t R0 = 0; R0 < n; R0 += OB) {
       const int64_t R1 = std::min(n, R0 + OB);
-      forward_rows(R0, R1, R1);
-      if (R1 < n) outer_update(R0, R1, n - R1, R1);
+      for (int64_t r0 = R0; r0 < R1; r0 += TBK) {
+        const int bs = (int)std::min<int64_t>(TBK, R1 - r0);
+        const int64_t r1 = r0 + bs;
+        diag_tc(r0, bs, adjoint ? 1 : 0, R0);
+        if (r1 < R1) tc_update(R0, r0 - R0, bs, R1 - r1, r1);
+      }
+      if (R1 < n) tc_update(R0, 0, R1 - R0, n - R1, R1);
     }
     for (int64_t R0 = ((n - 1) / OB) * OB; R0 >= 0; R0 -= OB) {
       const int64_t R1 = std::min(n, R0 + OB);
-      backward_rows(R0, R1, R0);
-      if (R0 > 0) outer_update(R0, R1, R0, 0);
+      for (int64_t r0 = R0 + ((R1 - R0 - 1) / TBK) * TBK; r0 >= R0; r0 -= TBK) {
+        const int bs = (int)std::min<int64_t>(TBK, R1 - r0);
+        diag_tc(r0, bs, adjoint ? 3 : 2, R0);
+        if (r0 > R0) tc_update(R0, r0 - R0, bs, r0 - R0, R0);
+      }
+      if (R0 > 0) tc_update(R0, 0, R1 - R0, R0, 0);
     }
   }
 }

@@ -76,7 +76,7 @@ __device__ __forceinline__ void mma(uint32_t tmem, uint64_t da, uint64_t db, uin
 
 // TMA row of an operand tile: base + node + slab of chunk c + plane
 struct OpCoords {
-  int base_row, node_rows, slab_rows, plane_rows, cps;  // cps: 32-wide k chunks per slab
+  int base_row, node_rows, slab_rows, plane_rows, cps, base_x;  // cps: 32-wide k chunks per slab
 };
 
 template <int CG_BN>
@@ -139,7 +139,7 @@ cg_update_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
           if (*fail) break;
           const uint32_t base = smem_u32(smem + st * CG_STAGE_BYTES);
           mbar_expect_tx(bar_full + 8 * st, CG_STAGE_BYTES);
-          const int xa = (c % ca.cps) * CG_BK, xb = (c % cb.cps) * CG_BK;
+          const int xa = ca.base_x + (c % ca.cps) * CG_BK, xb = cb.base_x + (c % cb.cps) * CG_BK;
           const int ya = ca.base_row + e * ca.node_rows + (c / ca.cps) * ca.slab_rows + mt * CG_BM;
           const int yb = cb.base_row + e * cb.node_rows + (c / cb.cps) * cb.slab_rows + nt * CG_BN;
 #pragma unroll
@@ -256,17 +256,6 @@ cg_update_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
   if (threadIdx.x == 0 && s_fail) atomicExch(status, DEV_BARRIER_TIMEOUT);
 }
 
-__device__ __forceinline__ void split3(float x, uint16_t& p0, uint16_t& p1, uint16_t& p2) {
-  const __nv_bfloat16 h = __float2bfloat16_rn(x);
-  const float r1 = __fsub_rn(x, __bfloat162float(h));   // exact
-  const __nv_bfloat16 m = __float2bfloat16_rn(r1);
-  const float r2 = __fsub_rn(r1, __bfloat162float(m));  // exact, at most 8 significant bits
-  const __nv_bfloat16 l = __float2bfloat16_rn(r2);
-  p0 = __bfloat16_as_ushort(h);
-  p1 = __bfloat16_as_ushort(m);
-  p2 = __bfloat16_as_ushort(l);
-}
-
 // 32 x 32 (v, k) tile per CTA of 32 x 8 threads: read coalesced along the
 // source's contiguous dimension, transpose in shared memory, write the six
 // planes coalesced along k.
@@ -304,8 +293,8 @@ cg_split_kernel(const c64* __restrict__ src, int64_t node_stride, int64_t slab_s
     c64 x = tile[tx][r];
     if (conj_src) x.im = -x.im;
     uint16_t a0, a1, a2, b0, b1, b2;
-    split3(x.re, a0, a1, a2);
-    split3(x.im, b0, b1, b2);
+    cg_split3(x.re, a0, a1, a2);
+    cg_split3(x.im, b0, b1, b2);
     const int64_t at = v * kdim + k;
     o[at] = a0;
     o[plane + at] = a1;
@@ -330,7 +319,7 @@ void make_map(CUtensorMap* map, const uint16_t* base, int64_t rows, int64_t kdim
 }
 
 OpCoords coords(const CgOperand& o) {
-  return OpCoords{(int)o.base_row, (int)o.node_rows, (int)o.slab_rows, (int)o.plane_rows, o.kslab / CG_BK};
+  return OpCoords{(int)o.base_row, (int)o.node_rows, (int)o.slab_rows, (int)o.plane_rows, o.kslab / CG_BK, o.base_x};
 }
 
 }  // namespace
@@ -368,7 +357,10 @@ void cg_update(const CgOperand& A, const CgOperand& B, int64_t K, int64_t R, int
   const int kchunks = (int)cdiv(K, CG_BK);
   const int64_t lim = (int64_t)1 << 31;
   if (A.total_rows + CG_BM >= lim || B.total_rows + 128 >= lim || A.kdim % CG_BK || B.kdim % CG_BK ||
-      A.kslab % CG_BK || B.kslab % CG_BK || A.kslab <= 0 || B.kslab <= 0 || R >= lim || N >= lim)
+      A.kslab % CG_BK || B.kslab % CG_BK || A.kslab <= 0 || B.kslab <= 0 || R >= lim || N >= lim ||
+      A.base_x % CG_BK || B.base_x % CG_BK ||
+      A.base_x + std::min<int64_t>(A.kslab, cdiv(K, CG_BK) * CG_BK) > A.kdim ||
+      B.base_x + std::min<int64_t>(B.kslab, cdiv(K, CG_BK) * CG_BK) > B.kdim)
     throw CudaFailure(cudaErrorInvalidValue);
   // the tile width that computes the fewest padded columns (ties: 128)
   const int bn = (cdiv(N, 112) * 112 < cdiv(N, 128) * 128) ? 112 : 128;

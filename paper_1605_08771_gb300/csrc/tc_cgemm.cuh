@@ -3,6 +3,8 @@
 // operands: every FP32 value is split into three bf16 parts.
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace feast {
@@ -22,7 +24,21 @@ struct CgOperand {
   int64_t total_rows, kdim;
   int64_t node_rows, slab_rows, plane_rows, base_row;
   int kslab;
+  int base_x = 0;   // first k column of the operand inside a slab (a multiple of 32)
 };
+
+// x = p0 + p1 + p2 exactly: p0 = bf16(x), p1 = bf16(x - p0), p2 = x - p0 - p1
+// (both subtractions exact in FP32; 3 x 8 significant bits cover FP32's 24)
+__device__ __forceinline__ void cg_split3(float x, uint16_t& p0, uint16_t& p1, uint16_t& p2) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(x);
+  const float r1 = __fsub_rn(x, __bfloat162float(h));
+  const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+  const float r2 = __fsub_rn(r1, __bfloat162float(m));
+  const __nv_bfloat16 l = __float2bfloat16_rn(r2);
+  p0 = __bfloat16_as_ushort(h);
+  p1 = __bfloat16_as_ushort(m);
+  p2 = __bfloat16_as_ushort(l);
+}
 
 // bf16 elements of the planes of `slabs` slabs of vpad x kdim for `nodes`
 // nodes.
