@@ -439,26 +439,6 @@ __global__ void set_identity_kernel(S* X, int64_t k, int64_t ld) {
   }
 }
 
-// U = I + E, E_ij = h_ij / (d_j - d_i) for the pairs with |h_ij| <= sep |d_j - d_i|
-// (d = diag H), else 0: the first-order unitary that diagonalises the nearly
-// diagonal Hermitian H (E is anti-Hermitian, so U^H H U has off-diagonal
-// entries of second order)
-template <typename S>
-__global__ void newton_e_kernel(S* U, const S* H, int64_t k, int64_t ld, double sep) {
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < k * k; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = t % k, j = t / k;
-    if (i == j) {
-      U[i + j * k] = one<S>();
-      continue;
-    }
-    const double di = real_part(H[i + i * ld]), dj = real_part(H[j + j * ld]);
-    const double gap = dj - di;
-    const S h = H[i + j * ld];
-    const double ah = sqrt(abs2(h));
-    U[i + j * k] = (gap != 0.0 && ah <= sep * fabs(gap)) ? h * (1.0 / gap) : num<S>::zero();
-  }
-}
-
 template <typename S>
 __global__ void check_finite_kernel(const S* X, int64_t n, int64_t m, int64_t ld, int* flag) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * m; t += (int64_t)gridDim.x * blockDim.x) {
@@ -621,11 +601,6 @@ template <typename S> void copy_matrix(S* dst, int64_t ldd, const S* src, int64_
 
 template <typename S> void set_diag(S* X, int64_t k, int64_t ld, const double* d, cudaStream_t s) {
   set_diag_kernel<S><<<grid1d(k * k), 256, 0, s>>>(X, k, ld, d);
-  FEAST_LAUNCH_CHECK();
-}
-
-template <typename S> void newton_unitary(S* U, const S* H, int64_t k, int64_t ld, double sep, cudaStream_t s) {
-  newton_e_kernel<S><<<grid1d(k * k), 256, 0, s>>>(U, H, k, ld, sep);
   FEAST_LAUNCH_CHECK();
 }
 
@@ -1131,7 +1106,6 @@ void cluster_jacobi(S* H, int64_t k, int64_t ld, S* V, int64_t ldv, const int* i
   template void random_normal<S>(S*, int64_t, int64_t, int64_t, unsigned long long, cudaStream_t);         \
   template void copy_matrix<S>(S*, int64_t, const S*, int64_t, int64_t, int64_t, cudaStream_t);            \
   template void set_identity<S>(S*, int64_t, int64_t, cudaStream_t);                                       \
-  template void newton_unitary<S>(S*, const S*, int64_t, int64_t, double, cudaStream_t);                   \
   template void set_diag<S>(S*, int64_t, int64_t, const double*, cudaStream_t);                            \
   template void check_finite<S>(const S*, int64_t, int64_t, int64_t, int*, cudaStream_t);                  \
   template void offdiag_scan<S>(const S*, int64_t, int64_t, double, int*, int*, int, cudaStream_t);        \

@@ -132,10 +132,6 @@ template <typename S> void random_normal(S* X, int64_t n, int64_t m, int64_t ld,
 template <typename S> void copy_matrix(S* dst, int64_t ldd, const S* src, int64_t lds, int64_t n, int64_t m,
                                        cudaStream_t s);
 template <typename S> void set_identity(S* X, int64_t k, int64_t ld, cudaStream_t s);
-// U (k x k, ld k) = I + E with E_ij = h_ij / (d_j - d_i) where |h_ij| <= sep |d_j - d_i|
-// (d = diag H, ld ld), else 0: the first-order diagonalising unitary of a
-// nearly diagonal Hermitian H (Newton step of the reduced eigensolver)
-template <typename S> void newton_unitary(S* U, const S* H, int64_t k, int64_t ld, double sep, cudaStream_t s);
 // X = diag(d) (k x k)
 template <typename S> void set_diag(S* X, int64_t k, int64_t ld, const double* d, cudaStream_t s);
 

@@ -280,8 +280,6 @@ struct Solver {
   int* d_csw = nullptr;
   S* Ucl = nullptr;
   int64_t ccap = 0;
-  S *Nw1 = nullptr, *Nw2 = nullptr, *Nw3 = nullptr;   // Newton steps of the FP64 polish
-  static constexpr int kNewtonSteps = 3;
   static constexpr int kPolishSweeps = 2;  // full FP64 sweeps before the cluster finish
   // mixed, opts.refine_gemm = 1: double-float planes of A (hi/lo of Re, Im,
   // Re + Im) and of the right-hand block of an A product
@@ -437,7 +435,6 @@ struct Solver {
       d_coff = dalloc<int>(ctx, kmax / 2 + 2);
       d_csw = dalloc<int>(ctx, kmax / 2 + 1);
       Ucl = dalloc<S>(ctx, (kmax / 2 + 1) * kClusterMax * kClusterMax);
-      Nw1 = dalloc<S>(ctx, kk); Nw2 = dalloc<S>(ctx, kk); Nw3 = dalloc<S>(ctx, kk);
     }
     part_elems = 32 * kk;
     part = dalloc<S>(ctx, part_elems);
@@ -883,48 +880,12 @@ struct Solver {
   // entries), each set is finished in shared memory (cluster_jacobi) instead
   // of by further sweeps, which would walk all k - 1 rounds to rotate a few
   // pairs.  Otherwise one more full sweep.  Returns the full sweeps taken.
-  // One Newton step on the nearly diagonal H (ld k): U = I + E with
-  // E_ij = h_ij / (d_j - d_i) for the pairs coupled at most 1e-2 of their gap
-  // (first order, E anti-Hermitian), made exactly orthonormal by one FP64
-  // Cholesky-QR pass; H <- U^H H U (off-diagonal entries of second order),
-  // T2e <- T2e U.  The pairs left out (near-degenerate relative to their
-  // coupling) keep their size and go to the cluster finish.  false when the
-  // Cholesky factorisation breaks down (nothing changed).
-  bool newton_step(S* H, int64_t k) {
-    newton_unitary<S>(Nw1, H, k, k, 1e-2, st);
-    mm_square(k, Nw1, OP_C, Nw1, Nw2);
-    hermitize<S>(Nw2, k, k, st);
-    cholesky_upper<S>(Nw2, k, k, cw, ctx->num_sms, st);
-    int info = 0;
-    to_host(ctx, &info, cw.info, 1);
-    jacobi_status(nullptr);
-    if (info != 0) return false;
-    tri_inverse_upper<S>(Nw2, k, k, Nw3, k, st);
-    mm_square(k, Nw1, OP_N, Nw3, Nw2);   // orthonormal U
-    mm_square(k, H, OP_N, Nw2, Nw1);     // H U
-    mm_square(k, Nw2, OP_C, Nw1, H);     // U^H H U
-    hermitize<S>(H, k, k, st);
-    mm_square(k, T2e, OP_N, Nw2, Nw1);
-    copy_matrix<S>(T2e, k, Nw1, k, k, k, st);
-    return true;
-  }
   int polish(S* H, int64_t k) {
     const bool log = std::getenv("FEAST_LOG") != nullptr;
     int sweeps = 0, s1 = 0;
-    bool newton = Nw1 != nullptr && d_ccnt != nullptr;
-    if (newton) {
-      // Newton steps instead of the first full sweeps (quadratic convergence
-      // of every well-separated pair; FP64 products)
-      set_identity<S>(T2e, k, k, st);
-      for (int it = 0; it < kNewtonSteps && newton; ++it) newton = newton_step(H, k);
-      if (log) fprintf(stderr, "[feast] FP64 polish k=%lld: %d Newton steps%s\n", (long long)k, kNewtonSteps,
-                       newton ? "" : " (stopped: Cholesky breakdown)");
-    }
-    if (!newton) {
-      jacobi_eigh<S>(H, k, k, T2e, k, 1e-15, cw, ctx->num_sms, st, kPolishSweeps, Nw1 == nullptr || d_ccnt == nullptr);
-      jacobi_status(&s1);
-      sweeps += s1;
-    }
+    jacobi_eigh<S>(H, k, k, T2e, k, 1e-15, cw, ctx->num_sms, st, kPolishSweeps, true);
+    jacobi_status(&s1);
+    sweeps += s1;
     if (!d_ccnt) {
       if (s1 >= kPolishSweeps) {
         jacobi_eigh<S>(H, k, k, T2e, k, 1e-15, cw, ctx->num_sms, st, kMaxSweeps, false);
