@@ -123,9 +123,7 @@ typedef struct {
   double history[128];  /* max residual per iteration (first 128) */
   double refine_gemm_ms;    /* mixed: summed device time (CUDA events) of the FP64-accurate
                                refinement GEMM launches */
-  double refine_gemm_mac;   /* their real multiply-adds (M*N*K summed over launches; a digit-split
-                               launch with d < 6 digits counts d (d + 1) / 42 of its M*N*K, its
-                               share of the 21 digit products of six digits) */
+  double refine_gemm_mac;   /* their real multiply-adds (M*N*K summed over launches) */
   int refine_gemm_launches; /* their number */
   int cgemm_launches;   /* mixed: launches of the complex-FP32 SIMT GEMM (LU trailing and
                            triangular-solve block updates) */
@@ -293,9 +291,6 @@ int feast_rayleigh_ritz(feast_ctx* ctx, const void* A, int dtype, int64_t n, int
  * digit products accumulated exactly in 128-long K chunks; complex by three
  * real products), error about 2^-47 sum_k 2^(e_i + f_j) per real product
  * where 2^e_i > max_k |op(A)_ik| and 2^f_j > max_k |op(B)_kj|.
- * method 12 + (d - 2), d = 2..5 (i.e. 12..15): the same with d digits, error
- * about 2^-(8d - 1) sum_k 2^(e_i + f_j) (the refinement's early steps use 4
- * and 5 digits).
  * method 1: double-float arithmetic on the FP32 pipes, error about
  * 2^-44 sum_k |A_ik| |B_kj|; real, transA = transB = 0 and beta = 0 only.
  * Scratch comes from the context.  Returns FEAST_ERR_ARG for bad sizes,

@@ -427,8 +427,8 @@ def feast_rayleigh_ritz(ctx, A, Q, anorm):
 def feast_gemm_f64acc(ctx, A, B, method=0, transA=False, transB=False, alpha=1.0, beta=0.0, C=None):
     """C = alpha op(A) op(B) + beta C, FP64-accurate, for float64 or complex128
     CUDA matrices; op = conjugate transpose when trans*.  method 0 on the bf16
-    tensor cores (digit splitting, six digits), 12..15 the same with 2..5
-    digits, 1 in double-float arithmetic (real, no transposes, beta = 0)."""
+    tensor cores (digit splitting), 1 in double-float arithmetic (real,
+    no transposes, beta = 0)."""
     torch = _torch()
     cplx = A.is_complex() or B.is_complex()
     dt = torch.complex128 if cplx else torch.float64

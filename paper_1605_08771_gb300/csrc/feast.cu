@@ -582,7 +582,7 @@ struct Solver {
   }
   // Out = A * B on the tensor cores: each real product from digit planes
   // (oz_gemm), complex A by the same three products (3M) as apply_A_df
-  void apply_A_oz(const double* B, bool bcplx, int64_t k, double* Out, int ndig = kOzDigits) {
+  void apply_A_oz(const double* B, bool bcplx, int64_t k, double* Out) {
     OzOperand Bo[3];
     const int nb = kCplx ? 3 : (bcplx ? 2 : 1);
     for (int t = 0; t < nb; ++t) Bo[t] = oz_operand(Boz[t], k, n, false);
@@ -591,21 +591,20 @@ struct Solver {
     if (bcplx) oz_split(B, 2, 1, n, 1, n, Bo[1], st);
     if (kCplx) {
       oz_split(B, 2, 2, n, 1, n, Bo[2], st);
-      oz_gemm(n, k, Aoz[0], Bo[0], Out, n, 2, 0, d_flag, sms, st, ndig);
-      oz_gemm(n, k, Aoz[1], Bo[1], Tdf, n, 1, 0, d_flag, sms, st, ndig);
-      oz_gemm(n, k, Aoz[2], Bo[2], Out, n, 2, 1, d_flag, sms, st, ndig);
+      oz_gemm(n, k, Aoz[0], Bo[0], Out, n, 2, 0, d_flag, sms, st);
+      oz_gemm(n, k, Aoz[1], Bo[1], Tdf, n, 1, 0, d_flag, sms, st);
+      oz_gemm(n, k, Aoz[2], Bo[2], Out, n, 2, 1, d_flag, sms, st);
       combine_3m(Out, Tdf, n, k, st);
     } else if (bcplx) {
-      oz_gemm(n, k, Aoz[0], Bo[0], Out, n, 2, 0, d_flag, sms, st, ndig);
-      oz_gemm(n, k, Aoz[0], Bo[1], Out, n, 2, 1, d_flag, sms, st, ndig);
+      oz_gemm(n, k, Aoz[0], Bo[0], Out, n, 2, 0, d_flag, sms, st);
+      oz_gemm(n, k, Aoz[0], Bo[1], Out, n, 2, 1, d_flag, sms, st);
     } else {
-      oz_gemm(n, k, Aoz[0], Bo[0], Out, n, 1, 0, d_flag, sms, st, ndig);
+      oz_gemm(n, k, Aoz[0], Bo[0], Out, n, 1, 0, d_flag, sms, st);
     }
   }
-  // FP64-accurate A times an n x k block on the mixed path (ndig < 6: the
-  // digit-split route with fewer digits, for residuals that need less)
-  void apply_A_acc(const double* B, bool bcplx, int64_t k, double* Out, int ndig = kOzDigits) {
-    if (use_oz) apply_A_oz(B, bcplx, k, Out, ndig);
+  // FP64-accurate A times an n x k block on the mixed path
+  void apply_A_acc(const double* B, bool bcplx, int64_t k, double* Out) {
+    if (use_oz) apply_A_oz(B, bcplx, k, Out);
     else apply_A_df(B, bcplx, k, Out);
   }
   // a timed-out wait inside the tensor-core GEMM
@@ -730,29 +729,13 @@ struct Solver {
     // entries whose residual met the target drop out of later steps: their
     // A*Y product is skipped and their residual set to zero
     std::vector<int> active(E, 1);
-    double worst_prev2 = -1.0;
     for (int step = 0; step < o.refine_max; ++step) {
-      // R_e = X - (z_e I - A) Y_e, FP64-accurate.  The digits of the split
-      // products follow the residual this step is expected to see: its
-      // computed value must be accurate to well below (expected residual) x
-      // (contraction) / 10, which the first steps reach with 4 or 5 of the 6
-      // digits (error about 2^-(8d - 1)); the later steps take all 6
-      int ndig = kOzDigits;
-      if (step == 0) {
-        ndig = 4;
-      } else if (worst_prev > 0.0) {
-        const double c = worst_prev2 > 0.0 ? std::min(0.1, worst_prev / worst_prev2) : 3e-3;
-        const double need = worst_prev * c * c / 10.0;
-        ndig = 4;
-        while (ndig < kOzDigits && std::ldexp(1.0, -(8 * ndig - 1)) > need) ++ndig;
-      }
+      // R_e = X - (z_e I - A) Y_e, FP64-accurate (double-float A Y)
       for (int e0 = 0; e0 < E;) {
         if (!active[e0]) { ++e0; continue; }
         int e1 = e0;
         while (e1 < E && active[e1]) ++e1;
-        phase("refine A*Y", [&] {
-          apply_A_acc((const double*)(Y + e0 * nm), true, (e1 - e0) * m, (double*)(AY + e0 * nm), ndig);
-        });
+        phase("refine A*Y", [&] { apply_A_acc((const double*)(Y + e0 * nm), true, (e1 - e0) * m, (double*)(AY + e0 * nm)); });
         e0 = e1;
       }
       to_dev(ctx, d_act, active.data(), E);
@@ -776,8 +759,8 @@ struct Solver {
         prev[e] = rn;
       }
       if (std::getenv("FEAST_LOG"))
-        fprintf(stderr, "[feast] refine step %d (%d digits): worst active relative residual %.3e (target %.3e), "
-                "active %d/%d\n", step, ndig, worst, rtol, (int)std::count(active.begin(), active.end(), 1), E);
+        fprintf(stderr, "[feast] refine step %d: worst active relative residual %.3e (target %.3e), active %d/%d\n",
+                step, worst, rtol, (int)std::count(active.begin(), active.end(), 1), E);
       if (conv || stagnant) break;
       // entries that met the target in this step still take this correction
       // (their residual is fresh); earlier ones have R = 0
@@ -793,7 +776,6 @@ struct Solver {
         return;
       }
       phase("c64 solves", [&] { lowp_out(m, true); });
-      worst_prev2 = worst_prev;
       worst_prev = worst;
     }
     accumulate_filter<S>(Xf, n, Y, n, m, nc, d_w, st);
@@ -2045,9 +2027,7 @@ int feast_gemm_f64acc(feast_ctx* ctx, int method, int dtype, int transA, int tra
   if ((transA != 0 && transA != 1) || (transB != 0 && transB != 1)) return FEAST_ERR_ARG;
   if (lda < (transA ? K : M) || ldb < (transB ? N : K)) return FEAST_ERR_ARG;
   if (!std::isfinite(alpha) || !std::isfinite(beta)) return FEAST_ERR_ARG;
-  if (method != 0 && method != 1 && !(method >= 12 && method <= 15)) return FEAST_ERR_ARG;
-  const int ndig = method >= 12 ? method - 10 : kOzDigits;
-  if (method >= 12) method = 0;
+  if (method != 0 && method != 1) return FEAST_ERR_ARG;
   // the double-float route: real, no transposes, C = alpha A B
   if (method == 1 && (dtype != FEAST_R64 || transA || transB || beta != 0.0)) return FEAST_ERR_ARG;
   if (M > INT32_MAX / kOzDigits || N > INT32_MAX / kOzDigits) return FEAST_ERR_ARG;
@@ -2067,7 +2047,7 @@ int feast_gemm_f64acc(feast_ctx* ctx, int method, int dtype, int transA, int tra
       w.T = dalloc<double>(ctx, (cplx ? 2 : 1) * M * N);
       w.T2 = cplx ? dalloc<double>(ctx, M * N) : nullptr;
       oz_gemm_op(cplx, M, N, K, alpha, (const double*)A, lda, transA != 0, (const double*)B, ldb, transB != 0, beta,
-                 (double*)C, ldc, w, flag, ctx->num_sms, st, ndig);
+                 (double*)C, ldc, w, flag, ctx->num_sms, st);
       int f = 0;
       to_host(ctx, &f, flag, 1);
       if (f == DEV_BARRIER_TIMEOUT) return FEAST_ERR_TIMEOUT;

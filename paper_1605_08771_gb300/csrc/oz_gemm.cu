@@ -103,7 +103,7 @@ __device__ __forceinline__ void tile_coords(int t, int mtiles, int ntiles, int& 
 __global__ void __launch_bounds__(OZ_THREADS, 1)
 oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
                int Mpad, int Npad, int kstages, const int* __restrict__ eA, const int* __restrict__ eB, double* C,
-               int64_t ldc, int cs, int co, int ndig, int* status) {
+               int64_t ldc, int cs, int co, int* status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   float* lo_sm = (float*)(smem + OZ_STAGES * OZ_STAGE_BYTES);        // [column][row]
@@ -155,11 +155,13 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           }
           if (*fail) break;
           const uint32_t base = smem_u32(smem + st * OZ_STAGE_BYTES);
-          mbar_expect_tx(bar_full + 8 * st, ndig * (OZ_A_TILE + OZ_B_TILE));
+          mbar_expect_tx(bar_full + 8 * st, OZ_STAGE_BYTES);
           const int x = ks * OZ_BK;
-          for (int p = 0; p < ndig; ++p)
+#pragma unroll
+          for (int p = 0; p < OZ_D; ++p)
             tma_load_2d(base + p * OZ_A_TILE, &tmA, x, p * Mpad + mt * OZ_BM, bar_full + 8 * st);
-          for (int q = 0; q < ndig; ++q)
+#pragma unroll
+          for (int q = 0; q < OZ_D; ++q)
             tma_load_2d(base + OZ_D * OZ_A_TILE + q * OZ_B_TILE, &tmB, x, q * Npad + nt * OZ_BN, bar_full + 8 * st);
         }
       }
@@ -195,7 +197,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
               for (int p = 0; p < OZ_D; ++p) {
 #pragma unroll
                 for (int qq = 0; qq < OZ_D; ++qq) {
-                  if (p + qq < OZ_EXACT || p + qq > ndig - 1) continue;
+                  if (p + qq < OZ_EXACT || p + qq > OZ_D - 1) continue;
                   mma_bf16(tmem + OZ_MERGED_COL, sw64_desc(abase + p * OZ_A_TILE + kk * 32),
                            sw64_desc(bbase + qq * OZ_B_TILE + kk * 32), first ? 0u : 1u);
                   first = false;
@@ -211,7 +213,6 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             for (int kk = 0; kk < OZ_BK / 16; ++kk) {
 #pragma unroll
               for (int l = 0; l < OZ_EXACT; ++l) {
-                if (l >= ndig) continue;
 #pragma unroll
                 for (int p = 0; p <= l; ++p) {
                   const bool restart = chunk_first && kk == 0 && p == 0;
@@ -267,23 +268,19 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             float& lo = Lo[(gcol * 16 + j) * OZ_BM];
             lo = __fadd_rn(lo, __fadd_rn(e0, e1));
           }
-          // levels 2 and 3 exist only with at least that many digits (a level
-          // that no product wrote holds a previous tile's values)
           tmem_ld16(ta + 2 * OZ_BN, va);
           tmem_ld16(ta + 3 * OZ_BN, vb);
           tmem_wait_ld();
-          if (ndig > 2) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              float& h = H[gcol * 16 + j];
-              float e2;
-              two_sum(h, __uint_as_float(va[j]), h, e2);
-              float& lo = Lo[(gcol * 16 + j) * OZ_BM];
-              lo = __fadd_rn(lo, __fadd_rn(e2, ndig > 3 ? __uint_as_float(vb[j]) : 0.f));
-            }
+          for (int j = 0; j < 16; ++j) {
+            float& h = H[gcol * 16 + j];
+            float e2;
+            two_sum(h, __uint_as_float(va[j]), h, e2);
+            float& lo = Lo[(gcol * 16 + j) * OZ_BM];
+            lo = __fadd_rn(lo, __fadd_rn(e2, __uint_as_float(vb[j])));
           }
         }
-        if (c == nchunks - 1 && ndig > OZ_EXACT) {
+        if (c == nchunks - 1) {
 #pragma unroll
           for (int gcol = 0; gcol < OZ_COLS_PER_WARP / 16; ++gcol) {
             uint32_t v[16];
@@ -410,9 +407,8 @@ void oz_split(const double* src, int ss, int mode, int64_t K, int64_t se, int64_
 }
 
 void oz_gemm(int64_t M, int64_t N, const OzOperand& A, const OzOperand& B, double* C, int64_t ldc, int cs, int co,
-             int* status, int num_sms, cudaStream_t s, int ndig) {
+             int* status, int num_sms, cudaStream_t s) {
   if (M <= 0 || N <= 0) return;
-  if (ndig < 2 || ndig > OZ_D) throw CudaFailure(cudaErrorInvalidValue);
   if (A.K != B.K || A.kpad != B.kpad || A.vpad % OZ_BM || B.vpad % OZ_BN || A.kpad % OZ_BK || M > A.nvec || N > B.nvec)
     throw CudaFailure(cudaErrorInvalidValue);
   CUtensorMap mA, mB;
@@ -428,14 +424,14 @@ void oz_gemm(int64_t M, int64_t N, const OzOperand& A, const OzOperand& B, doubl
   const unsigned grid = (unsigned)std::min<int64_t>(tiles, num_sms);
   kernel_timer_launch_begin(TIMER_REFINE_GEMM, s);
   oz_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM, s>>>(mA, mB, (int)M, (int)N, (int)A.vpad, (int)B.vpad,
-                                                   (int)(A.kpad / OZ_BK), A.exps, B.exps, C, ldc, cs, co, ndig, status);
+                                                   (int)(A.kpad / OZ_BK), A.exps, B.exps, C, ldc, cs, co, status);
   FEAST_LAUNCH_CHECK();
-  kernel_timer_launch_end(TIMER_REFINE_GEMM, s, (double)M * (double)N * (double)A.K * ndig * (ndig + 1) / 42.0);
+  kernel_timer_launch_end(TIMER_REFINE_GEMM, s, (double)M * (double)N * (double)A.K);
 }
 
 void oz_gemm_op(bool cplx, int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda, bool transA,
                 const double* B, int64_t ldb, bool transB, double beta, double* C, int64_t ldc, const OzScratch& w,
-                int* status, int num_sms, cudaStream_t s, int ndig) {
+                int* status, int num_sms, cudaStream_t s) {
   if (M <= 0 || N <= 0) return;
   OzOperand L[3], R[3];
   const int parts = cplx ? 3 : 1;
@@ -455,13 +451,13 @@ void oz_gemm_op(bool cplx, int64_t M, int64_t N, int64_t K, double alpha, const 
       oz_split(A, 2, lm[t], K, lse, lsv, L[t], s);
       oz_split(B, 2, rm[t], K, rse, rsv, R[t], s);
     }
-    oz_gemm(M, N, L[0], R[0], w.T, M, 2, 0, status, num_sms, s, ndig);   // T1 in the real slots
-    oz_gemm(M, N, L[1], R[1], w.T2, M, 1, 0, status, num_sms, s, ndig);  // T2
-    oz_gemm(M, N, L[2], R[2], w.T, M, 2, 1, status, num_sms, s, ndig);   // T3 in the imaginary slots
+    oz_gemm(M, N, L[0], R[0], w.T, M, 2, 0, status, num_sms, s);   // T1 in the real slots
+    oz_gemm(M, N, L[1], R[1], w.T2, M, 1, 0, status, num_sms, s);  // T2
+    oz_gemm(M, N, L[2], R[2], w.T, M, 2, 1, status, num_sms, s);   // T3 in the imaginary slots
   } else {
     oz_split(A, 1, 0, K, lse, lsv, L[0], s);
     oz_split(B, 1, 0, K, rse, rsv, R[0], s);
-    oz_gemm(M, N, L[0], R[0], w.T, M, 1, 0, status, num_sms, s, ndig);
+    oz_gemm(M, N, L[0], R[0], w.T, M, 1, 0, status, num_sms, s);
   }
   combine_axpby(C, ldc, cplx, w.T, w.T2, M, N, alpha, beta, s);
 }

@@ -47,10 +47,8 @@ void oz_split(const double* src, int ss, int mode, int64_t K, int64_t se, int64_
 // operands (A: M vectors = rows, B: N vectors = columns, same K).  Error about
 // 2^-47 sum_k 2^(eA_i + eB_j) per element.  A timed-out device wait sets
 // *status to DEV_BARRIER_TIMEOUT (the output is then undefined).
-// ndig (2..6): the digits of each operand used, i.e. the products p + q <
-// ndig; error about 2^-(8 ndig - 1) K 2^(e_i + f_j) (six digits: 2^-47).
 void oz_gemm(int64_t M, int64_t N, const OzOperand& A, const OzOperand& B, double* C, int64_t ldc, int cs, int co,
-             int* status, int num_sms, cudaStream_t s, int ndig = kOzDigits);
+             int* status, int num_sms, cudaStream_t s);
 
 // General FP64-accurate product C = alpha op(A) op(B) + beta C (alpha, beta
 // real) from column-major A, B, C: real (cplx = false) or interleaved complex
@@ -69,6 +67,6 @@ struct OzScratch {
 };
 void oz_gemm_op(bool cplx, int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda, bool transA,
                 const double* B, int64_t ldb, bool transB, double beta, double* C, int64_t ldc, const OzScratch& w,
-                int* status, int num_sms, cudaStream_t s, int ndig = kOzDigits);
+                int* status, int num_sms, cudaStream_t s);
 
 }  // namespace feast

@@ -164,35 +164,3 @@ def test_gemm_f64acc_rejects_bad_arguments(ctx):
         fg.feast_gemm_f64acc(ctx, A, A.T.contiguous(), 2)
     with pytest.raises(RuntimeError):   # the double-float route has no transposes
         fg.feast_gemm_f64acc(ctx, A, B, 1, transA=True)
-
-
-@pytest.mark.parametrize("digits", [2, 3, 4, 5])
-@pytest.mark.parametrize("cplx", [False, True])
-def test_gemm_f64acc_fewer_digits(ctx, digits, cplx):
-    # the digit split with d < 6 digits (the refinement's early steps): error
-    # within 2^-(8d - 3) K 2^(e_i + f_j) (the six-digit bound scaled by the
-    # dropped levels), and clearly above the six-digit error, so the digits
-    # that were asked for are the ones used
-    M, N, K = 193, 131, 700
-    rng = np.random.default_rng(digits * 10 + int(cplx))
-    A = rng.standard_normal((M, K))
-    B = rng.standard_normal((K, N))
-    if cplx:
-        A = A + 1j * rng.standard_normal((M, K))
-        B = B + 1j * rng.standard_normal((K, N))
-    C = host(fg.feast_gemm_f64acc(ctx, cuda(A), cuda(B), method=10 + digits))
-    C6 = host(fg.feast_gemm_f64acc(ctx, cuda(A), cuda(B), method=0))
-    rows, cols = _sample(M, N, 200, digits)
-    parts = [(A.real, B.real), (A.imag, B.imag), (A.real + A.imag, B.real + B.imag)] if cplx else [(A, B)]
-    bound = 0.0
-    for Ap, Bp in parts:
-        sa = _pow2_above(np.abs(Ap).max(axis=1))[rows]
-        sb = _pow2_above(np.abs(Bp).max(axis=0))[cols]
-        bound = bound + 2.0 ** -(8 * digits - 3) * K * sa * sb
-    ref = (O.matmul_entries(A.real, B.real, rows, cols) - O.matmul_entries(A.imag, B.imag, rows, cols)
-           + 1j * (O.matmul_entries(A.real, B.imag, rows, cols) + O.matmul_entries(A.imag, B.real, rows, cols))
-           if cplx else O.matmul_entries(A, B, rows, cols))
-    err = np.abs(C[rows, cols] - ref)
-    assert np.all(err <= bound), (err / bound).max()
-    err6 = np.abs(C6[rows, cols] - ref)
-    assert err.max() > 16 * err6.max()
