@@ -65,9 +65,14 @@ CGEMM_DRAM_BYTES_PER_FLOP = 171.81e9 / 5.2540e12
 CGEMM_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum over the 3151 cgemm_prefetch_kernel "
                         "launches of the n = 4096 solve (171.81 GB, cold-cache replay) / their 5.254e12 flops, "
                         "x flops per launch")
-# the same for the tensor-core cg_update_kernel (profiles/); None until captured
-TCG_DRAM_BYTES_PER_FLOP = None
-TCG_TRAFFIC_SOURCE = "not captured yet"
+# the same for the tensor-core cg_update_kernel: two single-launch ncu captures of the n = 4096
+# filter (profiles/cg_update_kernel_lu_solve_n4096.md), an LU trailing update (M = N = 2688,
+# K = 128, 8 nodes: 931.6 MB for 5.92e10 flops) and a rank-256 solve update (M = 3840, N = 150,
+# K = 256, 8 nodes: 150.4 MB for 9.44e9 flops); both near 0.0157 B/flop, the C read-modify-write
+# plus the operand planes, so traffic is taken in proportion to a launch's flops
+TCG_DRAM_BYTES_PER_FLOP = (931.6e6 + 150.4e6) / (5.92e10 + 9.44e9)
+TCG_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one LU and one solve cg_update_kernel "
+                      "launch (n = 4096 filter, 1082 MB for 6.86e10 flops) x flops per launch")
 
 
 
