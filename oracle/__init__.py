@@ -13,6 +13,9 @@ Modules:
               RFEAST drivers (Appendix algorithms)
   exact       correctly rounded FP64 dot products (TwoProduct + exact
               summation): reference of the FP64-accurate refinement products
+  general     FEAST for a general (non-Hermitian) matrix on a circle contour
+  density     stochastic-trace Chebyshev moments and the count they estimate
+  mlp         the proposer's MLP (forward, backward, Adam)
 
 Parity pins: every function is checked in tests/test_oracle_*.py against
 closed forms, brute force or independent library routines.  The XFEAST and
@@ -23,7 +26,7 @@ dimensions the literal RFEAST expansion must produce.  Their iterates beyond
 that (which pairs are selected at each round of a multi-round solve, the
 residual histories) have no independent pin: "parity unpinned" there.
 """
-from .quadrature import gauss_legendre, contour_nodes, rational_filter  # noqa: F401
+from .quadrature import gauss_legendre, contour_nodes, rational_filter, circle_nodes, circle_filter  # noqa: F401
 from .dense import (lu_factor, lu_solve, lu_solve_adjoint, lu_unpack,  # noqa: F401
                     cholesky_upper, cholqr, cholqr2, jacobi_eigh, gram_eig_orth,
                     round_robin_pairs, solve_right_upper, CholeskyBreakdown)
@@ -31,3 +34,4 @@ from .feast import (factor_shifts, filter_apply, rayleigh_ritz, select_pairs,  #
                     feast_solve, norm_estimate, orthonormalize, FeastResult,
                     PLAIN, XFEAST, RFEAST, EXPAND_ALL, EXPAND_UNCONVERGED)
 from .exact import two_prod, dot_exact, matmul_entries  # noqa: F401
+from .general import feast_solve_general, filter_apply_general, factor_circle  # noqa: F401

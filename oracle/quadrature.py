@@ -133,3 +133,34 @@ def contour_nodes_offset(lmin: float, lmax: float, n_c: int, offsets, aspect: fl
     z = c + r * np.cos(theta) + 1j * aspect * r * np.sin(theta)
     w = 0.25 * om * (aspect * r * np.cos(theta) + 1j * r * np.sin(theta))
     return z, w
+
+
+def circle_nodes(center: complex, radius: float, n_c: int):
+    """Nodes and weights of the whole circle |z - center| = radius for a
+    general (non-Hermitian) matrix, whose filter takes both half-circles:
+    2 n_c nodes.  The first n_c are the upper half-circle nodes of the
+    Hermitian rule (theta_j = (pi/2)(1 - t_j), z_j = center + r e^{i theta_j},
+    w_j = (omega_j / 4) r e^{i theta_j}); the last n_c their mirror images
+    z = center + r e^{-i theta_j}, w = (omega_j / 4) r e^{-i theta_j} (the
+    Gauss-Legendre rule on the lower half, theta in (pi, 2 pi), has these
+    nodes because the abscissae are symmetric).  With a real center the
+    mirror is the complex conjugate."""
+    if not radius > 0.0:
+        raise ValueError("radius must be positive")
+    t, om = gauss_legendre(n_c)
+    theta = 0.5 * np.pi * (1.0 - t)
+    e_up = np.exp(1j * theta)
+    e_lo = np.exp(-1j * theta)
+    z = np.concatenate([center + radius * e_up, center + radius * e_lo])
+    w = np.concatenate([0.25 * om * radius * e_up, 0.25 * om * radius * e_lo])
+    return z, w
+
+
+def circle_filter(lam, z, w):
+    """Scalar filter rho(lambda) = sum_k w_k / (z_k - lambda) of the whole
+    circle at complex lambda (Eq. 3 applied to a 1 x 1 matrix)."""
+    lam = np.asarray(lam, dtype=np.complex128)
+    out = np.zeros(lam.shape, dtype=np.complex128)
+    for zk, wk in zip(z, w):
+        out += wk / (zk - lam)
+    return out

@@ -8,6 +8,7 @@ their inputs from it without sharing any method code.
 from .planted import (  # noqa: F401
     Problem,
     planted_matrix,
+    planted_general,
     haar_unitary,
     random_subspace,
     spectrum_config1,
@@ -15,6 +16,7 @@ from .planted import (  # noqa: F401
     spectrum_config3,
     spectrum_config4,
     spectrum_config5,
+    spectrum_disk,
     spectrum_paper,
     spectrum_uniform,
     make_problem,

@@ -242,6 +242,57 @@ def planted_pencil(lam, seed, complex_=False, cond=10.0):
             np.asfortranarray(X))
 
 
+def spectrum_disk(seed, n, m_in, center=0.0 + 0.0j, radius=1.0, gap=0.1, outer=10.0, real_pairs=False):
+    """Complex eigenvalues for the general (non-Hermitian) problem: m_in
+    uniform in the disk |z - center| < radius (1 - gap), the other n - m_in
+    uniform in the annulus radius (1 + gap) < |z - center| < outer radius.
+    real_pairs: the spectrum of a real matrix (closed under conjugation,
+    center real, n and m_in even)."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0xD15C]))
+
+    def disk(count, r0, r1):
+        rho = np.sqrt(rng.uniform(r0 * r0, r1 * r1, count))
+        return rho * np.exp(2j * np.pi * rng.uniform(0.0, 1.0, count))
+
+    if real_pairs:
+        if n % 2 or m_in % 2 or complex(center).imag != 0.0:
+            raise ValueError("real_pairs needs even n, m_in and a real center")
+        a = disk(m_in // 2, 0.0, radius * (1.0 - gap))
+        b = disk((n - m_in) // 2, radius * (1.0 + gap), outer * radius)
+        half = np.concatenate([a, b])
+        lam = np.concatenate([half, np.conj(half)])
+    else:
+        lam = np.concatenate([disk(m_in, 0.0, radius * (1.0 - gap)), disk(n - m_in, radius * (1.0 + gap),
+                                                                          outer * radius)])
+    return center + lam
+
+
+def planted_general(lam, seed, cond=10.0, real=False):
+    """A general (non-normal) matrix with eigenvalues lam: A = V diag(lam)
+    V^{-1} with V = Q1 diag(s) Q2, Q1 and Q2 Haar unitary and singular values
+    s log-uniform in [1, cond] (eigenvector condition number <= cond).  real:
+    lam closed under conjugation and listed as (half, conj(half)); then V's
+    columns come in conjugate pairs and A is real.  Returns (A, V), Fortran
+    order."""
+    lam = np.asarray(lam, dtype=np.complex128)
+    n = lam.size
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0x6E4]))
+    s = np.exp(rng.uniform(0.0, np.log(cond), n))
+    Q1 = haar_unitary(n, seed + 3000, True)
+    Q2 = haar_unitary(n, seed + 4000, True)
+    V = (Q1 * s[None, :]) @ Q2
+    if real:
+        h = n // 2
+        if not np.allclose(lam[h:], np.conj(lam[:h])):
+            raise ValueError("real: lam must be (half, conj(half))")
+        V = np.concatenate([V[:, :h], np.conj(V[:, :h])], axis=1)
+    Vinv = np.linalg.inv(V)
+    A = (V * lam[None, :]) @ Vinv
+    if real:
+        A = A.real
+    return np.asfortranarray(A), np.asfortranarray(V)
+
+
 def random_subspace(n, m, seed, complex_=False):
     """Seeded N(0,1) starting subspace X0 (n x m), Fortran order.  Complex
     entries have independent N(0, 1/2) real and imaginary parts."""
