@@ -358,6 +358,69 @@ int feast_mlp_train_step(feast_ctx* ctx, float* params, float* m, float* v, cons
 int feast_jacobi_eigh_noalloc(int device, void* stream, int dtype, int64_t k, const void* H,
                               double* evals, void* V, int* sweeps);
 
+/* ------------------------------------------------------------------------
+ * General (non-Hermitian) matrices.  Sect. I names the non-Hermitian problem
+ * among the extensions FEAST takes directly; the paper gives no algorithm.
+ * Reading: the contour is the whole circle |z - c| = r and the filter
+ * sum_k w_k (z_k I - A)^{-1} X (Eq. 3) takes both half-circles (2 n_c
+ * shifted factorisations, no Hermitian mirror); Rayleigh-Ritz uses an
+ * orthonormal basis Q of the filtered block, A' = Q^H A Q is diagonalised
+ * by Hessenberg reduction and shifted QR to Schur form, Ritz vectors
+ * x = Q v have unit 2-norm; the check is max ||A x - lambda x|| / ||A||_2
+ * over the Ritz values inside the disk (FEAST Algorithm step 3).  FP64
+ * complex arithmetic throughout.  Complex numbers on the host are
+ * interleaved (re, im) doubles.
+ * ------------------------------------------------------------------------ */
+
+/* The 2 n_c nodes and weights of the whole circle (host arrays of 2 n_c
+ * complex numbers each): first the upper half-circle nodes of the Hermitian
+ * rule, c + r e^{i theta_j}, theta_j = (pi/2)(1 - t_j) for the ascending
+ * Gauss-Legendre abscissae t_j, with weights (omega_j / 4) r e^{i theta_j};
+ * then their mirror images c + r e^{-i theta_j} with weights
+ * (omega_j / 4) r e^{-i theta_j}.  1 <= n_c <= 64, r > 0.  Returns FEAST_OK
+ * or FEAST_ERR_ARG. */
+int feast_circle_nodes(double c_re, double c_im, double radius, int n_c, double* z, double* w);
+
+/* Eigenpairs of the general complex k x k matrix H (device, column-major,
+ * leading dim k, not modified), the reduced problem of the general
+ * Rayleigh-Ritz step: Hessenberg reduction, implicit single-shift QR with
+ * Wilkinson shifts to the Schur form H = Z T Z^H (one CTA), eigenvectors of
+ * T by back substitution, V = Z Y with unit 2-norm columns.  evals: host,
+ * k complex numbers in the order of T's diagonal; V: device k x k.
+ * *sweeps (may be NULL): QR sweeps taken.  1 <= k <= 2048.  Returns
+ * FEAST_ERR_NONFINITE for NaN/Inf in H, FEAST_ERR_ORTH when QR does not
+ * converge within 30 k sweeps, FEAST_ERR_TIMEOUT when the kernel's 20 s
+ * limit expires. */
+int feast_eig_general(feast_ctx* ctx, int64_t k, const void* H, double* evals, void* V, int* sweeps);
+
+/* Y = sum_k w_k (z_k I - A)^{-1} X over the 2 n_c nodes of feast_circle_nodes:
+ * the filter of a general n x n matrix A (device, dtype FEAST_R64 or
+ * FEAST_C128, leading dim lda) on the complex n x m block X (device, leading
+ * dim n); Y: device complex n x m (leading dim n).  Scratch: 2 n_c complex
+ * FP64 factors of n x n.  Returns FEAST_ERR_SINGULAR when a shifted matrix is
+ * exactly singular (a node on an eigenvalue). */
+int feast_filter_apply_general(feast_ctx* ctx, const void* A, int dtype, int64_t n, int64_t lda, double c_re,
+                               double c_im, double radius, int n_c, const void* X, int64_t m, void* Y);
+
+/* Eigenpairs of the general n x n matrix A (device, dtype FEAST_R64 or
+ * FEAST_C128, leading dim lda, not modified) with eigenvalues inside the open
+ * disk |lambda - c| < r.  m0: subspace size (more than the expected count,
+ * 1 <= m0 <= min(n, 2048)); n_c: nodes per half-circle; tol: stopping
+ * tolerance on the relative residuals of the Ritz pairs inside the disk
+ * (||A||_2 by 40 power iterations of A^H A).  x0: optional device complex
+ * n x m0 starting block (NULL: seeded N(0, 1/2) + i N(0, 1/2)).  The next
+ * iteration filters all m0 Ritz vectors.  Outputs: evals (host, >= 2 m0
+ * doubles: complex eigenvalues ordered by real then imaginary part), X
+ * (device complex n x m0, leading dim n; unit 2-norm eigenvectors), res
+ * (host, >= m0 doubles), *m_found pairs, *iterations.  Stops with no pairs
+ * when no Ritz value lies inside after two iterations.  When the filtered
+ * block is numerically rank deficient the basis keeps the directions with
+ * sigma^2 >= 1e-12 sigma_1^2 and the subspace shrinks to that rank.
+ * Returns FEAST_OK, FEAST_WARN_MAXITER or an error. */
+int feast_disk_solve(feast_ctx* ctx, const void* A, int dtype, int64_t n, int64_t lda, double c_re, double c_im,
+                     double radius, int m0, int n_c, double tol, int max_iter, const void* x0, double* evals,
+                     void* X, double* res, int* m_found, int* iterations);
+
 #ifdef __cplusplus
 }
 #endif

@@ -35,6 +35,7 @@ EXPORTS = [
     "feast_gemm_f64acc", "feast_contour_nodes_offset", "feast_spectral_moments", "feast_moments_count",
     "feast_mlp_param_count", "feast_mlp_forward", "feast_mlp_gradient", "feast_mlp_train_step",
     "feast_interval_solve_batch", "feast_interval_solve_gen",
+    "feast_circle_nodes", "feast_eig_general", "feast_filter_apply_general", "feast_disk_solve",
 ]
 
 
@@ -112,6 +113,10 @@ def lib():
         "feast_interval_solve_batch": (I, [I, I, ctypes.POINTER(FeastProblem), ctypes.POINTER(FeastOpts), I, I]),
         "feast_interval_solve_gen": (I, [P, P, P, I, I64, I64, I64, D, D, I, I, D, ctypes.POINTER(FeastOpts),
                                          DP, P, DP, IP, IP, ctypes.POINTER(FeastStats)]),
+        "feast_circle_nodes": (I, [D, D, D, I, DP, DP]),
+        "feast_eig_general": (I, [P, I64, P, DP, P, IP]),
+        "feast_filter_apply_general": (I, [P, P, I, I64, I64, D, D, D, I, P, I64, P]),
+        "feast_disk_solve": (I, [P, P, I, I64, I64, D, D, D, I, I, D, I, P, DP, P, DP, IP, IP]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -338,6 +343,72 @@ def feast_interval_solve_gen(ctx, A, B, lmin, lmax, m0, n_c, tol, opts: FeastOpt
     m = mf.value
     return {"status": code, "evals": evals[:m].copy(), "evecs": V[:, :m], "res": res[:m].copy(),
             "iterations": it.value, "stats": st}
+
+
+def feast_circle_nodes(center, radius, n_c):
+    """The 2 n_c nodes and weights of the whole circle |z - center| = radius
+    (general matrices): upper half-circle nodes, then their mirror images."""
+    z = np.zeros(4 * n_c)
+    w = np.zeros(4 * n_c)
+    c = complex(center)
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(lib().feast_circle_nodes(c.real, c.imag, float(radius), int(n_c), z.ctypes.data_as(dp),
+                                    w.ctypes.data_as(dp)), "feast_circle_nodes")
+    return z[0::2] + 1j * z[1::2], w[0::2] + 1j * w[1::2]
+
+
+def feast_eig_general(ctx, H):
+    """Eigenvalues (numpy complex, order of the Schur diagonal), unit-norm
+    eigenvectors (CUDA complex128 k x k) and QR sweeps of the general k x k
+    CUDA matrix H."""
+    torch = _torch()
+    H = colmajor(H.to(torch.complex128))
+    k = H.shape[0]
+    ev = np.zeros(2 * k)
+    V = empty_colmajor(k, k, torch.complex128, H.device)
+    sw = ctypes.c_int(0)
+    _check(lib().feast_eig_general(ctx, k, _ptr(H), ev.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(V),
+                                   ctypes.byref(sw)), "feast_eig_general")
+    return ev[0::2] + 1j * ev[1::2], V, sw.value
+
+
+def feast_filter_apply_general(ctx, A, center, radius, n_c, X):
+    """sum_k w_k (z_k I - A)^{-1} X over the whole circle for a general CUDA
+    matrix A (float64 or complex128) and a CUDA block X (n x m); complex128."""
+    torch = _torch()
+    A = colmajor(A)
+    X = colmajor(X.to(torch.complex128))
+    n, m = X.shape
+    Y = empty_colmajor(n, m, torch.complex128, A.device)
+    c = complex(center)
+    _check(lib().feast_filter_apply_general(ctx, _ptr(A), _dtype_code(A), n, n, c.real, c.imag, float(radius),
+                                            int(n_c), _ptr(X), m, _ptr(Y)), "feast_filter_apply_general")
+    return Y
+
+
+def feast_disk_solve(ctx, A, center, radius, m0, n_c, tol, max_iter=100, x0=None):
+    """Eigenpairs of the general CUDA matrix A (float64 or complex128) with
+    eigenvalues inside the disk |lambda - center| < radius."""
+    torch = _torch()
+    A = colmajor(A)
+    n = A.shape[0]
+    x0p = None
+    if x0 is not None:
+        x0 = colmajor(x0.to(torch.complex128))
+        x0p = _ptr(x0)
+    ev = np.zeros(2 * m0)
+    res = np.zeros(m0)
+    V = empty_colmajor(n, m0, torch.complex128, A.device)
+    mf, it = ctypes.c_int(0), ctypes.c_int(0)
+    c = complex(center)
+    dp = ctypes.POINTER(ctypes.c_double)
+    code = lib().feast_disk_solve(ctx, _ptr(A), _dtype_code(A), n, n, c.real, c.imag, float(radius), int(m0),
+                                  int(n_c), float(tol), int(max_iter), x0p, ev.ctypes.data_as(dp), _ptr(V),
+                                  res.ctypes.data_as(dp), ctypes.byref(mf), ctypes.byref(it))
+    _check(code, "feast_disk_solve")
+    m = mf.value
+    return {"status": code, "evals": ev[0:2 * m:2] + 1j * ev[1:2 * m:2], "evecs": V[:, :m], "res": res[:m].copy(),
+            "iterations": it.value}
 
 
 def feast_filter_apply(ctx, A, lmin, lmax, n_c, X, opts: FeastOpts | None = None):

@@ -841,6 +841,7 @@ template void convert_matrix<float, double>(float*, int64_t, const double*, int6
 template void convert_matrix<double, float>(double*, int64_t, const float*, int64_t, int64_t, int64_t, cudaStream_t);
 template void convert_matrix<c64, c128>(c64*, int64_t, const c128*, int64_t, int64_t, int64_t, cudaStream_t);
 template void convert_matrix<c128, c64>(c128*, int64_t, const c64*, int64_t, int64_t, int64_t, cudaStream_t);
+template void convert_matrix<c128, double>(c128*, int64_t, const double*, int64_t, int64_t, int64_t, cudaStream_t);
 template void jacobi_eigh<float>(float*, int64_t, int64_t, float*, int64_t, double, const CoopWork&, int, cudaStream_t,
                                  int, bool);
 template void jacobi_eigh<c64>(c64*, int64_t, int64_t, c64*, int64_t, double, const CoopWork&, int, cudaStream_t, int,

@@ -21,6 +21,7 @@
 #include "dense.cuh"
 #include "factor.cuh"
 #include "gemm.cuh"
+#include "general.cuh"
 #include "oz_gemm.cuh"
 #include "proposer.cuh"
 
@@ -383,9 +384,8 @@ struct Solver {
         // conj(A[k + i lda]), so every split reads contiguous columns
         if (kCplx) {
           for (int t = 0; t < 3; ++t) Aoz[t] = oz_operand(ctx->arena.alloc(oz_operand_bytes(n, n, true)), n, n, true);
-          oz_split((const double*)A, 2, 0, n, 1, lda, Aoz[0], st);  // Re A(i, k)
-          oz_split((const double*)A, 2, 3, n, 1, lda, Aoz[1], st);  // Im A(i, k)
-          oz_split((const double*)A, 2, 4, n, 1, lda, Aoz[2], st);  // Re + Im
+          static const int modes[3] = {0, 3, 4};  // Re A(i, k), Im A(i, k), Re + Im
+          oz_split_modes((const double*)A, 2, modes, 3, n, 1, lda, Aoz, st);
         } else {
           Aoz[0] = oz_operand(ctx->arena.alloc(oz_operand_bytes(n, n, true)), n, n, true);
           oz_split((const double*)A, 1, 0, n, 1, lda, Aoz[0], st);
@@ -587,10 +587,10 @@ struct Solver {
     const int nb = kCplx ? 3 : (bcplx ? 2 : 1);
     for (int t = 0; t < nb; ++t) Bo[t] = oz_operand(Boz[t], k, n, false);
     const int sms = ctx->num_sms;
-    oz_split(B, bcplx ? 2 : 1, 0, n, 1, n, Bo[0], st);
-    if (bcplx) oz_split(B, 2, 1, n, 1, n, Bo[1], st);
+    static const int modes[3] = {0, 1, 2};  // Re, Im, Re + Im
+    if (kCplx) oz_split_modes(B, 2, modes, 3, n, 1, n, Bo, st);
+    else oz_split_modes(B, bcplx ? 2 : 1, modes, bcplx ? 2 : 1, n, 1, n, Bo, st);
     if (kCplx) {
-      oz_split(B, 2, 2, n, 1, n, Bo[2], st);
       oz_gemm(n, k, Aoz[0], Bo[0], Out, n, 2, 0, d_flag, sms, st);
       oz_gemm(n, k, Aoz[1], Bo[1], Tdf, n, 1, 0, d_flag, sms, st);
       oz_gemm(n, k, Aoz[2], Bo[2], Out, n, 2, 1, d_flag, sms, st);
@@ -1524,6 +1524,249 @@ int solve_t(feast_ctx* ctx, const S* A, int64_t n, int64_t lda, double lmin, dou
   return out.status;
 }
 
+// ---------------------------------------------------------------------------
+// general (non-Hermitian) matrices: FEAST on the whole circle |z - c| = r
+// (Sect. I names the extension; the reading: 2 n_c Gauss nodes, the filter
+// without the Hermitian mirror, Rayleigh-Ritz on an orthonormal basis with
+// the reduced general eigenproblem by Schur form)
+// ---------------------------------------------------------------------------
+// Upper half-circle nodes of the Hermitian rule, then their mirror images
+// c + r e^{-i theta_j} with weights (omega_j / 4) r e^{-i theta_j}.
+void circle(c128 center, double r, int nc, std::vector<c128>& z, std::vector<c128>& w) {
+  std::vector<double> t, om;
+  gauss_legendre(nc, t, om);
+  z.resize(2 * nc);
+  w.resize(2 * nc);
+  for (int j = 0; j < nc; ++j) {
+    const double th = 0.5 * M_PI * (1.0 - t[j]), cs = std::cos(th), sn = std::sin(th);
+    z[j] = c128{center.re + r * cs, center.im + r * sn};
+    w[j] = c128{0.25 * om[j] * r * cs, 0.25 * om[j] * r * sn};
+    z[nc + j] = c128{center.re + r * cs, center.im - r * sn};
+    w[nc + j] = c128{0.25 * om[j] * r * cs, -0.25 * om[j] * r * sn};
+  }
+}
+
+struct General {
+  feast_ctx* ctx;
+  cudaStream_t st;
+  int64_t n = 0, mmax = 0;
+  int nc = 0, E = 0;
+  c128* A = nullptr;  // complex copy of the input, ld n
+  c128* M = nullptr;  // E shifted factors
+  int32_t *ipiv = nullptr, *perm = nullptr;
+  PanelWork pw{};
+  CoopWork cw{};
+  c128* d_w = nullptr;
+  c128* Wsol = nullptr;  // E n x mmax solutions
+  c128 *G = nullptr, *Ri = nullptr, *Vg = nullptr, *Cg = nullptr, *part = nullptr, *tmp = nullptr;
+  c128 *Q = nullptr, *Wq = nullptr, *Hr = nullptr, *Zs = nullptr, *Ys = nullptr, *Vr = nullptr;
+  c128 *X = nullptr, *AX = nullptr, *d_lam = nullptr;
+  double *d_nrm = nullptr, *d_scale = nullptr;
+  int* d_idx = nullptr;
+  int* d_info = nullptr;
+  int64_t part_elems = 0;
+  double anorm = 1.0;
+  int last_sweeps = 0;
+
+  General(feast_ctx* c) : ctx(c), st(c->stream) {}
+
+  // scratch of the k x k steps, k <= kmax
+  void setup_small(int64_t kmax) {
+    mmax = kmax;
+    cw = coop_work_carve(ctx->arena.alloc(coop_work_bytes(kmax, ctx->num_sms)), kmax, ctx->num_sms);
+    const int64_t kk = kmax * kmax;
+    G = dalloc<c128>(ctx, kk);
+    Ri = dalloc<c128>(ctx, kk);
+    Vg = dalloc<c128>(ctx, kk);
+    Cg = dalloc<c128>(ctx, kk);
+    Hr = dalloc<c128>(ctx, kk);
+    Zs = dalloc<c128>(ctx, kk);
+    Ys = dalloc<c128>(ctx, kk);
+    Vr = dalloc<c128>(ctx, kk);
+    part_elems = 32 * kk;
+    part = dalloc<c128>(ctx, part_elems);
+    d_lam = dalloc<c128>(ctx, kmax);
+    d_nrm = dalloc<double>(ctx, kmax);
+    d_scale = dalloc<double>(ctx, kmax);
+    d_idx = dalloc<int>(ctx, kmax);
+    d_info = dalloc<int>(ctx, 2);
+  }
+  // A (dtype R64 or C128, ld lda) -> complex copy (ld n)
+  void setup_matrix(const void* Ain, int dtype, int64_t n_, int64_t lda) {
+    n = n_;
+    A = dalloc<c128>(ctx, n * n);
+    if (dtype == FEAST_R64) convert_matrix<c128, double>(A, n, (const double*)Ain, lda, n, n, st);
+    else copy_matrix<c128>(A, n, (const c128*)Ain, lda, n, n, st);
+  }
+  // n x mmax blocks of the Rayleigh-Ritz step
+  void setup_blocks() {
+    tmp = dalloc<c128>(ctx, n * mmax);
+    Q = dalloc<c128>(ctx, n * mmax);
+    Wq = dalloc<c128>(ctx, n * mmax);
+    X = dalloc<c128>(ctx, n * mmax);
+    AX = dalloc<c128>(ctx, n * mmax);
+  }
+  // ||A||_2 by 40 power iterations of A^H A from ones / sqrt(n)
+  double norm_estimate() {
+    c128* v = dalloc<c128>(ctx, n);
+    c128* u = dalloc<c128>(ctx, n);
+    c128* wv = dalloc<c128>(ctx, n);
+    double* nr = dalloc<double>(ctx, 1);
+    std::vector<c128> h(n, c128{1.0 / std::sqrt((double)n), 0.0});
+    to_dev(ctx, v, h.data(), n);
+    double est = 0.0;
+    for (int it = 0; it < 40; ++it) {
+      gemm_simple<c128, c128, c128>(n, 1, n, C1(1.0), A, n, OP_N, v, n, OP_N, C1(0.0), u, n, st);
+      gemm_simple<c128, c128, c128>(n, 1, n, C1(1.0), A, n, OP_C, u, n, OP_N, C1(0.0), wv, n, st);
+      col_norms2<c128>(wv, n, 1, n, nr, st);
+      double nw2 = 0.0;
+      to_host(ctx, &nw2, nr, 1);
+      const double nw = std::sqrt(nw2);
+      if (!(nw > 0.0)) return 0.0;
+      est = std::sqrt(nw);
+      const double inv = 1.0 / nw;
+      to_dev(ctx, d_scale, &inv, 1);
+      copy_matrix<c128>(v, n, wv, n, n, 1, st);
+      scale_cols<c128>(v, n, 1, n, d_scale, st);
+    }
+    return est;
+  }
+  void factor(c128 center, double r, int nc_) {
+    nc = nc_;
+    E = 2 * nc;
+    std::vector<c128> z, w;
+    circle(center, r, nc, z, w);
+    d_w = dalloc<c128>(ctx, E);
+    c128* dz = dalloc<c128>(ctx, E);
+    to_dev(ctx, d_w, w.data(), E);
+    to_dev(ctx, dz, z.data(), E);
+    M = dalloc<c128>(ctx, (int64_t)E * n * n);
+    ipiv = dalloc<int32_t>(ctx, (int64_t)E * n);
+    perm = dalloc<int32_t>(ctx, (int64_t)E * n);
+    const int pmax = std::max(1, ctx->num_sms * 8);
+    pw = panel_work_carve(ctx->arena.alloc(panel_work_bytes(E, pmax, sizeof(c128))), E, pmax, sizeof(c128));
+    Wsol = dalloc<c128>(ctx, (int64_t)E * n * mmax);
+    form_shifted<c128, c128>(M, n, n, n * n, E, A, n, dz, st);
+    lu_factor_batched<c128>(M, n, n, n * n, E, ipiv, perm, pw, ctx->num_sms, st);
+    int status = 0;
+    std::vector<int> zp(E);
+    to_host(ctx, &status, pw.status, 1);
+    to_host(ctx, zp.data(), pw.zero_pivot, E);
+    if (status == DEV_BARRIER_TIMEOUT) throw FeastError{FEAST_ERR_TIMEOUT};
+    for (int v : zp)
+      if (v) throw FeastError{FEAST_ERR_SINGULAR};
+  }
+  // Y = sum_k w_k (z_k I - A)^{-1} Xin (n x m)
+  void filter(const c128* Xin, int64_t m, c128* Y) {
+    const int64_t nm = n * m;
+    permute_in<c128, c128>(Wsol, nm, Xin, n, 0, n, m, perm, E, false, st);
+    lu_solve_batched<c128>(M, n, n, n * n, E, Wsol, m, nm, false, st, nullptr, nullptr, ctx->num_sms);
+    weighted_sum(Y, Wsol, nm, E, d_w, st);
+  }
+  // C (r x c) = X^H Y with the long reduction over n split
+  void reduce(int64_t r, int64_t c, const c128* Xm, const c128* Ym, c128* C) {
+    int ks = (int)std::max<int64_t>(1, std::min<int64_t>(32, n / 256));
+    while (ks > 1 && (int64_t)ks * r * c > part_elems) --ks;
+    gemm_simple<c128, c128, c128>(r, c, n, C1(1.0), Xm, n, OP_C, Ym, n, OP_N, C1(0.0), C, r, st, ks,
+                                  ks > 1 ? (void*)part : nullptr);
+  }
+  bool cholqr_once(const c128* Xm, int64_t k, c128* Qout) {
+    reduce(k, k, Xm, Xm, G);
+    hermitize<c128>(G, k, k, st);
+    cholesky_upper<c128>(G, k, k, cw, ctx->num_sms, st);
+    int info = 0, status = 0;
+    to_host(ctx, &info, cw.info, 1);
+    to_host(ctx, &status, cw.status, 1);
+    if (status == DEV_BARRIER_TIMEOUT) throw FeastError{FEAST_ERR_TIMEOUT};
+    if (info != 0) return false;
+    tri_inverse_upper<c128>(G, k, k, Ri, k, st);
+    gemm_simple<c128, c128, c128>(n, k, k, C1(1.0), Xm, n, OP_N, Ri, k, OP_N, C1(0.0), Qout, n, st);
+    return true;
+  }
+  // orthonormal basis of span(Y) (n x k): Cholesky-QR twice, else the Gram
+  // eigendecomposition route (keep sigma^2 >= 1e-12 sigma_1^2, then one
+  // Cholesky-QR pass); returns the rank
+  int64_t orth(const c128* Y, int64_t k, c128* Qout) {
+    if (cholqr_once(Y, k, tmp) && cholqr_once(tmp, k, Qout)) return k;
+    reduce(k, k, Y, Y, G);
+    hermitize<c128>(G, k, k, st);
+    jacobi_eigh<c128>(G, k, k, Vg, k, 1e-15, cw, ctx->num_sms, st);
+    int status = 0;
+    to_host(ctx, &status, cw.status, 1);
+    if (status == DEV_BARRIER_TIMEOUT) throw FeastError{FEAST_ERR_TIMEOUT};
+    get_diag<c128>(G, k, k, d_nrm, st);
+    std::vector<double> s2(k);
+    to_host(ctx, s2.data(), d_nrm, k);
+    std::vector<int> ord(k);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return s2[a] > s2[b]; });
+    if (!(s2[ord[0]] > 0.0)) throw FeastError{FEAST_ERR_ORTH};
+    std::vector<int> keep;
+    std::vector<double> sc;
+    for (int i : ord)
+      if (s2[i] >= 1e-12 * s2[ord[0]]) {
+        keep.push_back(i);
+        sc.push_back(1.0 / std::sqrt(s2[i]));
+      }
+    const int64_t r = (int64_t)keep.size();
+    to_dev(ctx, d_idx, keep.data(), r);
+    to_dev(ctx, d_scale, sc.data(), r);
+    gather_cols<c128>(Cg, k, Vg, k, k, d_idx, r, d_scale, st);
+    gemm_simple<c128, c128, c128>(n, r, k, C1(1.0), Y, n, OP_N, Cg, k, OP_N, C1(0.0), tmp, n, st);
+    if (!cholqr_once(tmp, r, Qout)) throw FeastError{FEAST_ERR_ORTH};
+    return r;
+  }
+  // eigenpairs of the general k x k matrix H (ld k, overwritten): values in
+  // ev, unit-norm vectors in Vr (ld k)
+  void eig(c128* H, int64_t k, std::vector<c128>& ev) {
+    frobenius_norm(H, k, d_nrm, st);
+    double hn = 0.0;
+    to_host(ctx, &hn, d_nrm, 1);
+    FEAST_CUDA_TRY(cudaMemsetAsync(d_info, 0, 2 * sizeof(int), st));
+    schur_complex(H, Zs, (int)k, d_info, st);
+    int info[2] = {0, 0};
+    to_host(ctx, info, d_info, 2);
+    if (info[0] == 2) throw FeastError{FEAST_ERR_TIMEOUT};
+    if (info[0] != 0) throw FeastError{FEAST_ERR_ORTH};
+    last_sweeps = info[1];
+    triangular_eigvecs(H, Ys, (int)k, std::max(2.220446049250313e-16 * hn, 1e-300), st);
+    gemm_simple<c128, c128, c128>(k, k, k, C1(1.0), Zs, k, OP_N, Ys, k, OP_N, C1(0.0), Vr, k, st);
+    col_norms2<c128>(Vr, k, k, k, d_nrm, st);
+    std::vector<double> nr(k);
+    to_host(ctx, nr.data(), d_nrm, k);
+    for (auto& x : nr) x = x > 0.0 ? 1.0 / std::sqrt(x) : 1.0;
+    to_dev(ctx, d_scale, nr.data(), k);
+    scale_cols<c128>(Vr, k, k, k, d_scale, st);
+    ev.resize(k);  // the diagonal of T, stride k + 1
+    FEAST_CUDA_TRY(cudaMemcpy2DAsync(ev.data(), sizeof(c128), H, (k + 1) * sizeof(c128), sizeof(c128), k,
+                                     cudaMemcpyDeviceToHost, st));
+    sync(ctx);
+  }
+  // Rayleigh-Ritz on the orthonormal Q (n x k): ev, X = Q V (unit columns),
+  // AX, relative residuals
+  void rayleigh_ritz(int64_t k, std::vector<c128>& ev, std::vector<double>& res) {
+    gemm_simple<c128, c128, c128>(n, k, n, C1(1.0), A, n, OP_N, Q, n, OP_N, C1(0.0), Wq, n, st);
+    reduce(k, k, Q, Wq, Hr);
+    eig(Hr, k, ev);
+    gemm_simple<c128, c128, c128>(n, k, k, C1(1.0), Q, n, OP_N, Vr, k, OP_N, C1(0.0), X, n, st);
+    gemm_simple<c128, c128, c128>(n, k, k, C1(1.0), Wq, n, OP_N, Vr, k, OP_N, C1(0.0), AX, n, st);
+    col_norms2<c128>(X, n, k, n, d_nrm, st);
+    std::vector<double> nr(k);
+    to_host(ctx, nr.data(), d_nrm, k);
+    for (auto& x : nr) x = x > 0.0 ? 1.0 / std::sqrt(x) : 1.0;
+    to_dev(ctx, d_scale, nr.data(), k);
+    scale_cols<c128>(X, n, k, n, d_scale, st);
+    scale_cols<c128>(AX, n, k, n, d_scale, st);
+    to_dev(ctx, d_lam, ev.data(), k);
+    resid_norms2_complex(AX, X, n, k, d_lam, d_nrm, st);
+    res.resize(k);
+    to_host(ctx, res.data(), d_nrm, k);
+    for (auto& r : res) r = std::sqrt(r) / anorm;
+  }
+};
+
+bool in_disk(c128 l, c128 c, double r) { return std::hypot(l.re - c.re, l.im - c.im) < r; }
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -2060,6 +2303,149 @@ int feast_gemm_f64acc(feast_ctx* ctx, int method, int dtype, int transA, int tra
       sync(ctx);
     }
     return FEAST_OK;
+  });
+}
+
+// ---------------------------------------------------------------------------
+// general (non-Hermitian) matrices
+// ---------------------------------------------------------------------------
+int feast_circle_nodes(double c_re, double c_im, double radius, int n_c, double* z, double* w) {
+  if (!z || !w || n_c < 1 || n_c > 64 || !std::isfinite(c_re) || !std::isfinite(c_im) || !(radius > 0.0) ||
+      !std::isfinite(radius))
+    return FEAST_ERR_ARG;
+  std::vector<c128> zz, ww;
+  circle(c128{c_re, c_im}, radius, n_c, zz, ww);
+  for (int j = 0; j < 2 * n_c; ++j) {
+    z[2 * j] = zz[j].re;
+    z[2 * j + 1] = zz[j].im;
+    w[2 * j] = ww[j].re;
+    w[2 * j + 1] = ww[j].im;
+  }
+  return FEAST_OK;
+}
+
+int feast_eig_general(feast_ctx* ctx, int64_t k, const void* H, double* evals, void* V, int* sweeps) {
+  if (!ctx || !H || !evals || !V || k < 1 || k > kSchurMaxK) return FEAST_ERR_ARG;
+  return guarded(ctx, [&]() {
+    FEAST_CUDA_TRY(cudaSetDevice(ctx->device));
+    ctx->arena.reset();
+    General g(ctx);
+    g.setup_small(k);
+    c128* Hw = dalloc<c128>(ctx, k * k);
+    copy_matrix<c128>(Hw, k, (const c128*)H, k, k, k, ctx->stream);
+    if (int r = check_finite_dev<c128>(ctx, Hw, k, k, k)) return r;
+    std::vector<c128> ev;
+    g.eig(Hw, k, ev);
+    copy_matrix<c128>((c128*)V, k, g.Vr, k, k, k, ctx->stream);
+    sync(ctx);
+    for (int64_t i = 0; i < k; ++i) {
+      evals[2 * i] = ev[i].re;
+      evals[2 * i + 1] = ev[i].im;
+    }
+    if (sweeps) *sweeps = g.last_sweeps;
+    return FEAST_OK;
+  });
+}
+
+int feast_filter_apply_general(feast_ctx* ctx, const void* A, int dtype, int64_t n, int64_t lda, double c_re,
+                               double c_im, double radius, int n_c, const void* X, int64_t m, void* Y) {
+  if (!ctx || !A || !X || !Y || n < 1 || lda < n || m < 1 || n_c < 1 || n_c > 64) return FEAST_ERR_ARG;
+  if ((dtype != FEAST_R64 && dtype != FEAST_C128) || !(radius > 0.0) || !std::isfinite(radius) ||
+      !std::isfinite(c_re) || !std::isfinite(c_im))
+    return FEAST_ERR_ARG;
+  return guarded(ctx, [&]() {
+    FEAST_CUDA_TRY(cudaSetDevice(ctx->device));
+    ctx->arena.reset();
+    if (dtype == FEAST_R64) {
+      if (int r = check_finite_dev<double>(ctx, (const double*)A, n, n, lda)) return r;
+    } else if (int r = check_finite_dev<c128>(ctx, (const c128*)A, n, n, lda)) {
+      return r;
+    }
+    if (int r = check_finite_dev<c128>(ctx, (const c128*)X, n, m, n)) return r;
+    General g(ctx);
+    g.mmax = m;
+    g.setup_matrix(A, dtype, n, lda);
+    g.factor(c128{c_re, c_im}, radius, n_c);
+    g.filter((const c128*)X, m, (c128*)Y);
+    sync(ctx);
+    return FEAST_OK;
+  });
+}
+
+int feast_disk_solve(feast_ctx* ctx, const void* A, int dtype, int64_t n, int64_t lda, double c_re, double c_im,
+                     double radius, int m0, int n_c, double tol, int max_iter, const void* x0, double* evals,
+                     void* X, double* res, int* m_found, int* iterations) {
+  if (!ctx || !A || !evals || !X || !res || !m_found || !iterations) return FEAST_ERR_ARG;
+  if ((dtype != FEAST_R64 && dtype != FEAST_C128) || n < 1 || lda < n || m0 < 1 || m0 > n || m0 > kSchurMaxK ||
+      n_c < 1 || n_c > 64 || max_iter < 1 || !(tol > 0.0) || !(radius > 0.0) || !std::isfinite(radius) ||
+      !std::isfinite(c_re) || !std::isfinite(c_im))
+    return FEAST_ERR_ARG;
+  return guarded(ctx, [&]() {
+    FEAST_CUDA_TRY(cudaSetDevice(ctx->device));
+    ctx->arena.reset();
+    cudaStream_t st = ctx->stream;
+    if (dtype == FEAST_R64) {
+      if (int r = check_finite_dev<double>(ctx, (const double*)A, n, n, lda)) return r;
+    } else if (int r = check_finite_dev<c128>(ctx, (const c128*)A, n, n, lda)) {
+      return r;
+    }
+    const c128 center{c_re, c_im};
+    General g(ctx);
+    g.setup_small(m0);
+    g.setup_matrix(A, dtype, n, lda);
+    g.setup_blocks();
+    g.anorm = g.norm_estimate();
+    if (!(g.anorm > 0.0)) g.anorm = 1.0;
+    g.factor(center, radius, n_c);
+    c128* X0 = dalloc<c128>(ctx, n * m0);
+    c128* Yf = dalloc<c128>(ctx, n * m0);
+    if (x0) {
+      copy_matrix<c128>(X0, n, (const c128*)x0, n, n, m0, st);
+      if (int r = check_finite_dev<c128>(ctx, X0, n, m0, n)) return r;
+    } else {
+      random_normal<c128>(X0, n, m0, n, 0x5eedull, st);
+    }
+    const c128* Xcur = X0;
+    int64_t k = m0;
+    std::vector<c128> ev;
+    std::vector<double> rs;
+    std::vector<int> ins;
+    int status = FEAST_WARN_MAXITER, it = 0;
+    for (it = 1; it <= max_iter; ++it) {
+      g.filter(Xcur, k, Yf);
+      k = g.orth(Yf, k, g.Q);
+      g.rayleigh_ritz(k, ev, rs);
+      ins.clear();
+      double r = 0.0;
+      for (int64_t i = 0; i < k; ++i)
+        if (in_disk(ev[i], center, radius)) {
+          ins.push_back((int)i);
+          r = std::max(r, rs[i]);
+        }
+      if ((!ins.empty() && r <= tol) || (ins.empty() && it >= 2)) {
+        status = FEAST_OK;
+        break;
+      }
+      Xcur = g.X;
+    }
+    if (it > max_iter) it = max_iter;
+    std::stable_sort(ins.begin(), ins.end(), [&](int a, int b) {
+      return ev[a].re < ev[b].re || (ev[a].re == ev[b].re && ev[a].im < ev[b].im);
+    });
+    const int mf = (int)ins.size();
+    if (mf > 0) {
+      to_dev(ctx, g.d_idx, ins.data(), mf);
+      gather_cols<c128>((c128*)X, n, g.X, n, n, g.d_idx, mf, nullptr, st);
+    }
+    sync(ctx);
+    for (int i = 0; i < mf; ++i) {
+      evals[2 * i] = ev[ins[i]].re;
+      evals[2 * i + 1] = ev[ins[i]].im;
+      res[i] = rs[ins[i]];
+    }
+    *m_found = mf;
+    *iterations = it;
+    return status;
   });
 }
 }  // extern "C"

@@ -4,10 +4,11 @@
 // low-precision tensor-core variants.
 //
 // Splitting.  Each row i of A (and each column j of B) gets an exponent e with
-// max |x| < 2^e and is written as x = 2^(e-8) sum_{p<6} d_p 2^(-8p), where the
-// integer digits come from r <- 256 r, d = rint(r), r <- r - d starting at
-// r = x 2^-e (all exact in FP64): |d_0| <= 256, |d_p| <= 128.  Plane p stores
-// d_p 2^(-8p), exact in bf16 (at most 8 significant bits).  Then
+// max |x| < 2^e and is written as x = 2^(e-8) sum_{p<6} d_p 2^(-8p) + r with
+// |r| <= 2^(e-49): X = x 2^(48-e) rounded to the nearest integer, then its
+// balanced base-256 digits from the top (each rounded to nearest, so
+// |d_0| <= 256, |d_p| <= 128).  Plane p stores d_p 2^(-8p), exact in bf16 (at
+// most 8 significant bits).  Then
 //     (A B)_ij = 2^(eA_i + eB_j - 16) sum_{p,q} sum_k a_p(i,k) b_q(k,j),
 // and the 21 plane products with p + q <= 5 keep about 47 bits; the rest are
 // below 2^-48 relative to sum_k 2^(eA_i + eB_j).
@@ -319,55 +320,168 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   if (threadIdx.x == 0 && s_fail) atomicExch(status, DEV_BARRIER_TIMEOUT);
 }
 
-// One CTA per vector: exponent from the vector's max |x|, then the six digits
-// of every element.  Padded vectors and the K padding are zero.
-__global__ void oz_split_kernel(const double* __restrict__ src, int ss, int mode, int64_t K, int64_t se, int64_t sv,
-                                int64_t nvec, int64_t vpad, int64_t kpad, uint16_t* __restrict__ planes,
-                                int* __restrict__ exps) {
+// Split kernel.  One CTA per vector, up to three combinations (modes) of the
+// same source elements per launch, so a complex operand is read once for its
+// Re, Im and Re +- Im planes.  The exponent comes from the vector's max |x|
+// (an integer max over the FP64 bit patterns); the digits of x are taken with
+// integer arithmetic from its bit pattern: X = x 2^(48-e) rounded to the
+// nearest integer (ties to even), |X| <= 2^48, then balanced base-256 digits
+// from the top.  The only FP64 instruction is the add of the Re +- Im modes:
+// FP64 arithmetic is slow on this part, and an FP64 digit loop made the split
+// compute-bound.  Padded vectors and the K padding are zero.
+constexpr int OZ_SPLIT_THREADS = 256;
+constexpr int OZ_SPLIT_VEC = 4;  // consecutive k per thread (one 8-byte store per plane)
+
+struct OzSplitOut {
+  uint16_t* planes[3];
+  int* exps[3];
+  int mode[3];
+};
+
+__device__ __forceinline__ double oz_mode_value(int mode, double re, double im) {
+  switch (mode) {
+    case 1: return im;
+    case 2: return re + im;
+    case 3: return -im;
+    case 4: return re - im;
+    default: return re;
+  }
+}
+
+// round(|x| 2^(48-e)) with ties to even, signed; requires |x| < 2^e
+__device__ __forceinline__ long long oz_fixed48(double x, int e) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7ff);
+  unsigned long long mant = b & 0x000fffffffffffffull;
+  if (E != 0) mant |= 0x0010000000000000ull;
+  if (mant == 0) return 0;
+  // |x| = mant 2^(max(E, 1) - 1075); |x| 2^(48 - e) = mant 2^(-s)
+  const int s = 1027 + e - (E != 0 ? E : 1);
+  unsigned long long q;
+  if (s <= 0) {
+    q = mant << (-s);  // subnormal vectors only; q < 2^48 since |x| < 2^e
+  } else if (s >= 55) {
+    q = 0;             // mant < 2^53 <= 2^(s-2): below half a unit
+  } else {
+    q = mant >> s;
+    const unsigned long long r = mant & ((1ull << s) - 1), half = 1ull << (s - 1);
+    q += (r > half || (r == half && (q & 1ull))) ? 1ull : 0ull;
+  }
+  return (b >> 63) ? -(long long)q : (long long)q;
+}
+
+// bf16 pattern of the integer digit d (|d| <= 256) times 2^(-8p): exact, the
+// upper half of the FP32 pattern
+__device__ __forceinline__ uint16_t oz_digit_bf16(long long d, float scale) {
+  return (uint16_t)(__float_as_uint((float)d * scale) >> 16);
+}
+
+template <int NM>
+__global__ void __launch_bounds__(OZ_SPLIT_THREADS, 3)
+oz_split_kernel(const double* __restrict__ src, int ss, int64_t K, int64_t se, int64_t sv, int64_t nvec,
+                int64_t vpad, int64_t kpad, OzSplitOut out) {
   const int64_t v = blockIdx.x;
   const int64_t plane = vpad * kpad;
-  uint16_t* out = planes + v * kpad;
+  const int64_t step = (int64_t)OZ_SPLIT_VEC * blockDim.x;
   if (v >= nvec) {
-    for (int64_t k = threadIdx.x; k < kpad; k += blockDim.x)
-      for (int p = 0; p < OZ_D; ++p) out[p * plane + k] = 0;
-    if (threadIdx.x == 0) exps[v] = 0;
+    for (int t = 0; t < NM; ++t) {
+      uint16_t* o = out.planes[t] + v * kpad;
+      for (int64_t k = (int64_t)OZ_SPLIT_VEC * threadIdx.x; k < kpad; k += step)
+        for (int p = 0; p < OZ_D; ++p) *reinterpret_cast<uint2*>(o + p * plane + k) = make_uint2(0u, 0u);
+      if (threadIdx.x == 0) out.exps[t][v] = 0;
+    }
     return;
   }
-  auto value = [&](int64_t k) -> double {
-    const double* e = src + (k * se + v * sv) * ss;
-    switch (mode) {
-      case 1: return e[1];
-      case 2: return e[0] + e[1];
-      case 3: return -e[1];
-      case 4: return e[0] - e[1];
-      default: return e[0];
+  auto load = [&](int64_t k, double& re, double& im) {
+    re = 0.0;
+    im = 0.0;
+    if (k < K) {
+      const double* e = src + (k * se + v * sv) * ss;
+      if (ss == 2) {
+        const double2 z = *reinterpret_cast<const double2*>(e);
+        re = z.x;
+        im = z.y;
+      } else {
+        re = e[0];
+      }
     }
   };
-  double amax = 0.0;
-  for (int64_t k = threadIdx.x; k < K; k += blockDim.x) amax = fmax(amax, fabs(value(k)));
-  __shared__ double red[32];
-  for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = amax;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (threadIdx.x == 0) red[0] = m;
+  // pass 1: max |x| per mode over the bit patterns (finite doubles order as
+  // their magnitudes' patterns)
+  unsigned long long amax[NM];
+#pragma unroll
+  for (int t = 0; t < NM; ++t) amax[t] = 0;
+  for (int64_t k0 = (int64_t)OZ_SPLIT_VEC * threadIdx.x; k0 < K; k0 += step) {
+#pragma unroll
+    for (int j = 0; j < OZ_SPLIT_VEC; ++j) {
+      double re, im;
+      load(k0 + j, re, im);
+#pragma unroll
+      for (int t = 0; t < NM; ++t) {
+        const unsigned long long m =
+            (unsigned long long)__double_as_longlong(oz_mode_value(out.mode[t], re, im)) & 0x7fffffffffffffffull;
+        amax[t] = m > amax[t] ? m : amax[t];
+      }
+    }
+  }
+  __shared__ unsigned long long red[NM][OZ_SPLIT_THREADS / 32];
+  __shared__ int s_e[NM];
+#pragma unroll
+  for (int t = 0; t < NM; ++t) {
+    unsigned long long m = amax[t];
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long x = __shfl_xor_sync(0xffffffffu, m, o);
+      m = x > m ? x : m;
+    }
+    if ((threadIdx.x & 31) == 0) red[t][threadIdx.x >> 5] = m;
   }
   __syncthreads();
-  int e = 0;
-  if (red[0] > 0.0) frexp(red[0], &e);  // max |x| < 2^e
-  if (threadIdx.x == 0) exps[v] = e;
-  for (int64_t k = threadIdx.x; k < kpad; k += blockDim.x) {
-    double r = k < K ? ldexp(value(k), -e) : 0.0;
 #pragma unroll
-    for (int p = 0; p < OZ_D; ++p) {
-      r *= 256.0;
-      const double d = rint(r);
-      r -= d;
-      // d 2^(-8p) has at most 8 significant bits: its bf16 pattern is the
-      // upper half of the FP32 pattern
-      out[p * plane + k] = (uint16_t)(__float_as_uint((float)ldexp(d, -8 * p)) >> 16);
+  for (int t = 0; t < NM; ++t) {
+    if (threadIdx.x == t) {
+      unsigned long long m = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = red[t][w] > m ? red[t][w] : m;
+      int e = 0;
+      if (m != 0) frexp(__longlong_as_double((long long)m), &e);  // max |x| < 2^e
+      s_e[t] = e;
+      out.exps[t][v] = e;
+    }
+  }
+  __syncthreads();
+  int ev[NM];
+#pragma unroll
+  for (int t = 0; t < NM; ++t) ev[t] = s_e[t];
+  // pass 2: digits (the vector is re-read, mostly from L2)
+  for (int64_t k0 = (int64_t)OZ_SPLIT_VEC * threadIdx.x; k0 < kpad; k0 += step) {
+    double re[OZ_SPLIT_VEC], im[OZ_SPLIT_VEC];
+#pragma unroll
+    for (int j = 0; j < OZ_SPLIT_VEC; ++j) load(k0 + j, re[j], im[j]);
+#pragma unroll
+    for (int t = 0; t < NM; ++t) {
+      long long X[OZ_SPLIT_VEC];
+#pragma unroll
+      for (int j = 0; j < OZ_SPLIT_VEC; ++j) X[j] = oz_fixed48(oz_mode_value(out.mode[t], re[j], im[j]), ev[t]);
+      uint16_t* o = out.planes[t] + v * kpad + k0;
+      float scale = 1.0f;
+#pragma unroll
+      for (int p = 0; p < OZ_D; ++p) {
+        uint16_t d16[OZ_SPLIT_VEC];
+#pragma unroll
+        for (int j = 0; j < OZ_SPLIT_VEC; ++j) {
+          long long d;
+          if (p < OZ_D - 1) {
+            const int sh = 8 * (OZ_D - 1 - p);  // 40, 32, ..., 8
+            d = (X[j] + (1ll << (sh - 1))) >> sh;
+            X[j] -= d << sh;
+          } else {
+            d = X[j];
+          }
+          d16[j] = oz_digit_bf16(d, scale);
+        }
+        *reinterpret_cast<uint2*>(o + p * plane) =
+            make_uint2((uint32_t)d16[0] | ((uint32_t)d16[1] << 16), (uint32_t)d16[2] | ((uint32_t)d16[3] << 16));
+        scale *= 0.00390625f;  // 2^-8
+      }
     }
   }
 }
@@ -398,12 +512,32 @@ OzOperand oz_operand(void* buf, int64_t nvec, int64_t K, bool left) {
   return op;
 }
 
+void oz_split_modes(const double* src, int ss, const int* modes, int nm, int64_t K, int64_t se, int64_t sv,
+                    const OzOperand* ops, cudaStream_t s) {
+  if (nm < 1 || nm > 3) throw CudaFailure(cudaErrorInvalidValue);
+  const OzOperand& op = ops[0];
+  if (op.vpad <= 0) return;
+  OzSplitOut out{};
+  for (int t = 0; t < nm; ++t) {
+    if (ops[t].vpad != op.vpad || ops[t].kpad != op.kpad || ops[t].nvec != op.nvec || ops[t].K != op.K ||
+        op.kpad % OZ_SPLIT_VEC)
+      throw CudaFailure(cudaErrorInvalidValue);
+    out.planes[t] = ops[t].planes;
+    out.exps[t] = ops[t].exps;
+    out.mode[t] = modes[t];
+  }
+  const dim3 grid((unsigned)op.vpad);
+  switch (nm) {
+    case 1: oz_split_kernel<1><<<grid, OZ_SPLIT_THREADS, 0, s>>>(src, ss, K, se, sv, op.nvec, op.vpad, op.kpad, out); break;
+    case 2: oz_split_kernel<2><<<grid, OZ_SPLIT_THREADS, 0, s>>>(src, ss, K, se, sv, op.nvec, op.vpad, op.kpad, out); break;
+    default: oz_split_kernel<3><<<grid, OZ_SPLIT_THREADS, 0, s>>>(src, ss, K, se, sv, op.nvec, op.vpad, op.kpad, out); break;
+  }
+  FEAST_LAUNCH_CHECK();
+}
+
 void oz_split(const double* src, int ss, int mode, int64_t K, int64_t se, int64_t sv, const OzOperand& op,
               cudaStream_t s) {
-  if (op.vpad <= 0) return;
-  oz_split_kernel<<<(unsigned)op.vpad, 256, 0, s>>>(src, ss, mode, K, se, sv, op.nvec, op.vpad, op.kpad, op.planes,
-                                                     op.exps);
-  FEAST_LAUNCH_CHECK();
+  oz_split_modes(src, ss, &mode, 1, K, se, sv, &op, s);
 }
 
 void oz_gemm(int64_t M, int64_t N, const OzOperand& A, const OzOperand& B, double* C, int64_t ldc, int cs, int co,
@@ -447,10 +581,8 @@ void oz_gemm_op(bool cplx, int64_t M, int64_t N, int64_t K, double alpha, const 
     static const int plain[3] = {0, 1, 2}, conjugated[3] = {0, 3, 4};  // Re, Im, Re + Im
     const int* lm = transA ? conjugated : plain;
     const int* rm = transB ? conjugated : plain;
-    for (int t = 0; t < 3; ++t) {
-      oz_split(A, 2, lm[t], K, lse, lsv, L[t], s);
-      oz_split(B, 2, rm[t], K, rse, rsv, R[t], s);
-    }
+    oz_split_modes(A, 2, lm, 3, K, lse, lsv, L, s);
+    oz_split_modes(B, 2, rm, 3, K, rse, rsv, R, s);
     oz_gemm(M, N, L[0], R[0], w.T, M, 2, 0, status, num_sms, s);   // T1 in the real slots
     oz_gemm(M, N, L[1], R[1], w.T2, M, 1, 0, status, num_sms, s);  // T2
     oz_gemm(M, N, L[2], R[2], w.T, M, 2, 1, status, num_sms, s);   // T3 in the imaginary slots

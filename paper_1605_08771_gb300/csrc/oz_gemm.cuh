@@ -42,6 +42,10 @@ OzOperand oz_operand(void* buf, int64_t nvec, int64_t K, bool left);
 // 3 -im, 4 re - im (modes 1-4 need ss = 2).
 void oz_split(const double* src, int ss, int mode, int64_t K, int64_t se, int64_t sv, const OzOperand& op,
               cudaStream_t s);
+// The same for nm <= 3 modes of the same elements in one pass (modes[t] into
+// ops[t]; the operands must have the same shape).
+void oz_split_modes(const double* src, int ss, const int* modes, int nm, int64_t K, int64_t se, int64_t sv,
+                    const OzOperand* ops, cudaStream_t s);
 
 // C[(i + j ldc) cs + co] = sum_k A(i,k) B(k,j) for i < M, j < N from split
 // operands (A: M vectors = rows, B: N vectors = columns, same K).  Error about

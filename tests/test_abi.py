@@ -91,3 +91,19 @@ def test_moments_count_matches_oracle(L):
         assert abs(fg.feast_moments_count(mu, 0.0, 10.0, a, b, lam.size)
                    - count_estimate(mu, 0.0, 10.0, a, b, lam.size)) < 1e-9
     assert fg.feast_mlp_param_count() == 64 * 256 + 256 + 2 * (256 * 256 + 256) + 256 * 9 + 9
+
+
+def test_circle_nodes_match_oracle(L):
+    # the whole-circle rule of general matrices: library (host code) against
+    # the oracle
+    for (c, r, nc) in [(0.0, 1.0, 8), (0.3 - 0.7j, 2.5, 5), (-4.0 + 1.0j, 0.01, 16), (1.0j, 3.0, 1)]:
+        z, w = fg.feast_circle_nodes(c, r, nc)
+        zo, wo = oracle.quadrature.circle_nodes(c, r, nc)
+        scale = max(1.0, abs(c), r)
+        np.testing.assert_allclose(z, zo, rtol=0, atol=1e-14 * scale)
+        np.testing.assert_allclose(w, wo, rtol=0, atol=1e-14 * scale)
+    dp = ctypes.POINTER(ctypes.c_double)
+    z = np.zeros(8)
+    assert L.feast_circle_nodes(0.0, 0.0, -1.0, 2, z.ctypes.data_as(dp), z.ctypes.data_as(dp)) == -1
+    assert L.feast_circle_nodes(0.0, 0.0, 1.0, 0, z.ctypes.data_as(dp), z.ctypes.data_as(dp)) == -1
+    assert L.feast_circle_nodes(float("nan"), 0.0, 1.0, 2, z.ctypes.data_as(dp), z.ctypes.data_as(dp)) == -1
