@@ -722,7 +722,7 @@ struct Solver {
     }
     phase("c64 solves", [&] { lowp_out(m, false); });
     // default target 16 eps sqrt(n): just above the accuracy floor of the
-    // double-float residual (about 2^-48 relative per product)
+    // FP64-accurate residual
     const double rtol = o.refine_tol > 0 ? o.refine_tol : 16.0 * 2.220446049250313e-16 * std::sqrt((double)n);
     std::vector<double> en(2 * E), prev(E, -1.0);
     double worst_prev = -1.0;
