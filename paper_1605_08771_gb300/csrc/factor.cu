@@ -497,6 +497,124 @@ trsm_diag_kernel(const F* M, int64_t ld, int64_t stride, F* Y, int64_t n, int64_
   }
 }
 
+// Triangular solve on a whole outer block (bs <= 256 rows) for the
+// tensor-core route: one launch replaces the four 64-row diagonal solves and
+// the three inner block updates of the outer block.  Warp per right-hand-side
+// column with the column's 256 entries in registers (8 per lane, register r
+// holding rows 32 r + lane); the block's triangle goes through shared memory
+// in 32-column panels (column-major, zero outside the triangle and past bs),
+// the next panel loaded into registers while the current one is used.  Panel
+// p holds the columns of register p, so every register index is a
+// compile-time constant and the rows a step cannot touch are skipped whole.
+// Modes as trsm_diag_kernel.  The solved block also goes out as the six bf16
+// planes of the outer update's right operand (K index = row within the outer
+// block, zero past bs).
+constexpr int kTrsmOuterWarps = 16;
+constexpr int kTrsmOuterThreads = kTrsmOuterWarps * 32;
+constexpr int kTrsmOuterLd = kSolveOuter + 1;  // padded panel column
+constexpr size_t kTrsmOuterSmem = sizeof(c64) * 32 * kTrsmOuterLd;
+
+template <int MODE>
+__global__ void __launch_bounds__(kTrsmOuterThreads, 1)
+trsm_outer_kernel(const c64* __restrict__ M, int64_t ld, int64_t stride, c64* __restrict__ Y, int64_t n, int64_t m,
+                  int64_t ystride, int64_t R0, int bs, uint16_t* __restrict__ planes, int64_t mpad) {
+  constexpr int OB = kSolveOuter, LDP = kTrsmOuterLd, R = OB / 32;
+  constexpr int PER = 32 * OB / kTrsmOuterThreads;  // panel elements per thread
+  constexpr bool kFwd = MODE <= 1, kStored = MODE == 0 || MODE == 2, kUnit = MODE == 0 || MODE == 3;
+  extern __shared__ __align__(16) unsigned char trsm_smem[];
+  c64* P = reinterpret_cast<c64*>(trsm_smem);
+  const int b = blockIdx.y;
+  const c64* Mb = M + (int64_t)b * stride;
+  const int tid = threadIdx.x, wp = tid >> 5, lane = tid & 31;
+  const int64_t cidx = (int64_t)blockIdx.x * kTrsmOuterWarps + wp;
+  const bool active = cidx < m;
+  c64* y = Y + (int64_t)b * ystride + cidx * n + R0;
+  c64 x[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) x[r] = (active && lane + 32 * r < bs) ? y[lane + 32 * r] : num<c64>::zero();
+  // T[rr][cc] of panel p (columns 32 p .. 32 p + 31) into registers: the rows a
+  // forward step reaches are [32 p, bs), a backward one [0, 32 p + 32)
+  c64 pre[PER];
+  auto fetch = [&](int p) {
+    const int c0 = 32 * p;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int l = tid + kTrsmOuterThreads * i;
+      int rr, cc;
+      if (kStored) {  // rows fastest: contiguous in the stored factor
+        rr = l & (OB - 1);
+        cc = c0 + (l >> 8);
+      } else {        // columns fastest: contiguous in the stored row of the transpose
+        cc = c0 + (l & 31);
+        rr = l >> 5;
+      }
+      const bool in = rr < bs && cc < bs && (kFwd ? rr >= c0 : rr < c0 + 32);
+      c64 v = num<c64>::zero();
+      if (in) v = kStored ? Mb[(R0 + rr) + (R0 + cc) * ld] : conj(Mb[(R0 + cc) + (R0 + rr) * ld]);
+      pre[i] = v;
+    }
+  };
+  auto stash = [&](int p) {
+    const int c0 = 32 * p;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int l = tid + kTrsmOuterThreads * i;
+      const int rr = kStored ? (l & (OB - 1)) : (l >> 5);
+      const int cc = kStored ? (c0 + (l >> 8)) : (c0 + (l & 31));
+      P[(cc - c0) * LDP + rr] = pre[i];
+    }
+  };
+  const int np = (bs + 31) / 32;
+  fetch(kFwd ? 0 : np - 1);
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    const int p = kFwd ? q : R - 1 - q;  // panel = register index (compile-time)
+    if (p >= np) continue;              // panels past bs (uniform)
+    __syncthreads();                    // the previous panel has been used
+    stash(p);
+    __syncthreads();
+    const int pn = kFwd ? p + 1 : p - 1;
+    if (kFwd ? pn < np : pn >= 0) fetch(pn);  // in flight during this panel
+    if (!active) continue;
+    const int jend = min(32, bs - 32 * p);
+    for (int t = 0; t < jend; ++t) {
+      const int jl = kFwd ? t : jend - 1 - t;
+      const c64* Tj = P + jl * LDP;
+      if (!kUnit && lane == jl) x[p] = x[p] * recip(Tj[32 * p + jl]);
+      const c64 xj = shfl(x[p], jl);
+      if (kFwd) {
+        if (lane > jl) x[p] = x[p] - Tj[32 * p + lane] * xj;
+#pragma unroll
+        for (int r = p + 1; r < R; ++r) x[r] = x[r] - Tj[32 * r + lane] * xj;
+      } else {
+        if (lane < jl) x[p] = x[p] - Tj[32 * p + lane] * xj;
+#pragma unroll
+        for (int r = 0; r < p; ++r) x[r] = x[r] - Tj[32 * r + lane] * xj;
+      }
+    }
+  }
+  if (!active) return;
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    if (lane + 32 * r < bs) y[lane + 32 * r] = x[r];
+  const int64_t plane = mpad * OB;
+  uint16_t* o = planes + (int64_t)b * 6 * plane + cidx * OB;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int t = lane + 32 * r;
+    const c64 v = t < bs ? x[r] : num<c64>::zero();
+    uint16_t a0, a1, a2, b0, b1, b2;
+    cg_split3(v.re, a0, a1, a2);
+    cg_split3(v.im, b0, b1, b2);
+    o[t] = a0;
+    o[plane + t] = a1;
+    o[2 * plane + t] = a2;
+    o[3 * plane + t] = b0;
+    o[4 * plane + t] = b1;
+    o[5 * plane + t] = b2;
+  }
+}
+
 // solve block rows: 64 for complex-FP32 factors, 32 for complex-FP64 (whose
 // 64 x 64 shared tile would exceed the static shared-memory limit)
 template <typename F> struct SolveBlock { static constexpr int value = 64; };
@@ -779,21 +897,14 @@ void lu_solve_batched(const F* M, int64_t n, int64_t ld, int64_t stride, int nod
     return;
   }
   if constexpr (std::is_same<F, c64>::value) {
-    // two levels on the tensor cores: 256-row outer blocks solved by 64-row
-    // diagonal blocks with updates confined to the outer block, then one
-    // rank-256 update of every row past it (four times fewer passes over the
-    // right-hand sides than rank-64 updates).  Each diagonal-block solve also
-    // writes its block as bf16 planes into the outer block's right-operand
-    // buffer (K offset = its row offset in the outer block), which both the
-    // inner and the outer updates read: no separate split launches.
+    // two levels on the tensor cores: each 256-row outer block solved in one
+    // launch (trsm_outer_kernel: its diagonal blocks and the updates inside
+    // it), then one rank-256 update of every row past it on the tensor cores.
+    // The outer-block solve writes its block as bf16 planes into the outer
+    // update's right-operand buffer: no separate split launches.
     const int64_t OB = kSolveOuter;
     const CgOperand Abase = cg_operand(adjoint ? sp->row : sp->col, sp->npad, kSolveBlock, nodes, sp->nblk,
                                        kSolveBlock);
-    auto diag_tc = [&](int64_t r0, int bs, int mode, int64_t R0) {
-      trsm_diag_kernel<F, TBK><<<gd, 256, 0, s>>>(M, ld, stride, Y, n, m, ystride, r0, bs, mode, sp->rhs, sp->mpad,
-                                                  kSolveOuter, (int)(r0 - R0));
-      FEAST_LAUNCH_CHECK();
-    };
     // Y[c_off .. c_off + rows) -= A_rows(blocks from R0 / 64, K = k) B(K offset kx)
     auto tc_update = [&](int64_t R0, int64_t kx, int64_t k, int64_t rows, int64_t c_off) {
       CgOperand B = cg_operand(sp->rhs, sp->mpad, kSolveOuter, nodes);
@@ -802,23 +913,29 @@ void lu_solve_batched(const F* M, int64_t n, int64_t ld, int64_t stride, int nod
       A.base_row = ((R0 + kx) / kSolveBlock) * A.slab_rows + c_off;
       cg_update(A, B, k, rows, m, Y + c_off, n, ystride, nodes, status, num_sms, s);
     };
+    const dim3 go((unsigned)cdiv(m, kTrsmOuterWarps), nodes);
+    auto solve_outer = [&](int64_t R0, int bs, int mode) {
+      auto launch = [&](auto kernel) {
+        FEAST_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrsmOuterSmem));
+        kernel<<<go, kTrsmOuterThreads, kTrsmOuterSmem, s>>>(M, ld, stride, Y, n, m, ystride, R0, bs, sp->rhs,
+                                                             sp->mpad);
+      };
+      switch (mode) {
+        case 0: launch(trsm_outer_kernel<0>); break;
+        case 1: launch(trsm_outer_kernel<1>); break;
+        case 2: launch(trsm_outer_kernel<2>); break;
+        default: launch(trsm_outer_kernel<3>); break;
+      }
+      FEAST_LAUNCH_CHECK();
+    };
     for (int64_t R0 = 0; R0 < n; R0 += OB) {
       const int64_t R1 = std::min(n, R0 + OB);
-      for (int64_t r0 = R0; r0 < R1; r0 += TBK) {
-        const int bs = (int)std::min<int64_t>(TBK, R1 - r0);
-        const int64_t r1 = r0 + bs;
-        diag_tc(r0, bs, adjoint ? 1 : 0, R0);
-        if (r1 < R1) tc_update(R0, r0 - R0, bs, R1 - r1, r1);
-      }
+      solve_outer(R0, (int)(R1 - R0), adjoint ? 1 : 0);
       if (R1 < n) tc_update(R0, 0, R1 - R0, n - R1, R1);
     }
     for (int64_t R0 = ((n - 1) / OB) * OB; R0 >= 0; R0 -= OB) {
       const int64_t R1 = std::min(n, R0 + OB);
-      for (int64_t r0 = R0 + ((R1 - R0 - 1) / TBK) * TBK; r0 >= R0; r0 -= TBK) {
-        const int bs = (int)std::min<int64_t>(TBK, R1 - r0);
-        diag_tc(r0, bs, adjoint ? 3 : 2, R0);
-        if (r0 > R0) tc_update(R0, r0 - R0, bs, r0 - R0, R0);
-      }
+      solve_outer(R0, (int)(R1 - R0), adjoint ? 3 : 2);
       if (R0 > 0) tc_update(R0, 0, R1 - R0, R0, 0);
     }
   }
