@@ -7,6 +7,8 @@
 
 #include <algorithm>
 
+#include "dfloat.cuh"
+
 namespace feast {
 
 namespace {
@@ -329,6 +331,34 @@ __global__ void gather_cols_kernel(S* dst, int64_t lddst, const S* src, int64_t 
   }
 }
 
+// dst (ks x ks, ld ks) = src[idx, idx] (src ld lds)
+template <typename S>
+__global__ void gather_sub_kernel(S* dst, const S* src, int64_t lds, const int* idx, int64_t ks) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ks * ks; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = t % ks, b = t / ks;
+    dst[t] = src[idx[a] + (int64_t)idx[b] * lds];
+  }
+}
+
+// dst[idx, idx] (ld ldd) = src (ks x ks, ld ks)
+template <typename S>
+__global__ void scatter_sub_kernel(S* dst, int64_t ldd, const S* src, const int* idx, int64_t ks) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ks * ks; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = t % ks, b = t / ks;
+    dst[idx[a] + (int64_t)idx[b] * ldd] = src[t];
+  }
+}
+
+// dst[:, idx[j]] = src[:, j]
+template <typename S>
+__global__ void scatter_cols_kernel(S* dst, int64_t lddst, const S* src, int64_t ldsrc, int64_t n, const int* idx,
+                                    int64_t k) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * k; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t % n, j = t / n;
+    dst[i + (int64_t)idx[j] * lddst] = src[i + j * ldsrc];
+  }
+}
+
 template <typename S>
 __global__ void scale_cols_kernel(S* X, int64_t n, int64_t k, int64_t ld, const double* scale) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * k; t += (int64_t)gridDim.x * blockDim.x) {
@@ -498,6 +528,208 @@ void tri_inverse_upper(const S* R, int64_t k, int64_t ld, S* Rinv, int64_t ldi, 
   FEAST_LAUNCH_CHECK();
 }
 
+// ---------------------------------------------------------------------------
+// Jacobi in double-float arithmetic (FP64-accurate polish on the FP32 pipes).
+// The same round-robin sweeps as jacobi_kernel, with H and V stored as
+// double-float values (T = dfr for real symmetric, dfc for complex Hermitian
+// matrices; 8 or 16 bytes, like double and c128) and every rotation applied
+// in double-float.  The rotation parameters are computed in FP64 from the
+// pair's entry and the diagonal, which lives in FP64 (dg) and is updated
+// there by the closed form d_p - t |h_pq|, d_q + t |h_pq|, so the
+// eigenvalues keep FP64 accuracy; the stored diagonal entries are not used.
+// ---------------------------------------------------------------------------
+template <typename T> struct df_of;
+template <> struct df_of<dfr> { using D = double; };
+template <> struct df_of<dfc> { using D = c128; };
+__device__ __forceinline__ double df_to_d(dfr a) { return a.to_double(); }
+__device__ __forceinline__ c128 df_to_d(dfc a) { return c128{a.re.to_double(), a.im.to_double()}; }
+__device__ __forceinline__ dfr df_from_d(double x) { return dfr(x); }
+__device__ __forceinline__ dfc df_from_d(c128 x) { return dfc{dfr(x.re), dfr(x.im)}; }
+__device__ __forceinline__ dfr df_ldcg(const dfr* p) {
+  const float2 v = __ldcg((const float2*)p);
+  return dfr(v.x, v.y);
+}
+__device__ __forceinline__ dfc df_ldcg(const dfc* p) {
+  const float4 v = __ldcg((const float4*)p);
+  return dfc{dfr(v.x, v.y), dfr(v.z, v.w)};
+}
+__device__ __forceinline__ dfr df_zero(dfr) { return dfr(0.0f, 0.0f); }
+__device__ __forceinline__ dfc df_zero(dfc) { return dfc{dfr(0.0f, 0.0f), dfr(0.0f, 0.0f)}; }
+__device__ __forceinline__ dfr df_one(dfr) { return dfr(1.0f, 0.0f); }
+__device__ __forceinline__ dfc df_one(dfc) { return dfc{dfr(1.0f, 0.0f), dfr(0.0f, 0.0f)}; }
+__device__ __forceinline__ dfr df_conj(dfr a) { return a; }
+__device__ __forceinline__ dfc df_conj(dfc a) { return dfc{a.re, -a.im}; }
+// x c - y u and x s + y v (c, s real; u, v of the storage type)
+__device__ __forceinline__ dfr df_mulr(dfr x, dfr c) { return x * c; }
+__device__ __forceinline__ dfc df_mulr(dfc x, dfr c) { return dfc{x.re * c, x.im * c}; }
+__device__ __forceinline__ dfr df_mul(dfr x, dfr u) { return x * u; }
+__device__ __forceinline__ dfc df_mul(dfc x, dfc u) {
+  return dfc{x.re * u.re - x.im * u.im, x.re * u.im + x.im * u.re};
+}
+__device__ __forceinline__ dfr df_sub(dfr a, dfr b) { return a - b; }
+__device__ __forceinline__ dfc df_sub(dfc a, dfc b) { return dfc{a.re - b.re, a.im - b.im}; }
+__device__ __forceinline__ dfr df_add(dfr a, dfr b) { return a + b; }
+__device__ __forceinline__ dfc df_add(dfc a, dfc b) { return dfc{a.re + b.re, a.im + b.im}; }
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+jacobi_df_kernel(T* H, int64_t k, int64_t ld, T* V, int64_t ldv, double* dg, double tol, CoopWork w, int P,
+                 int max_sweeps, int init_v) {
+  using D = typename df_of<T>::D;
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t NT = (int64_t)P * blockDim.x;
+  unsigned nb = 0;
+  const int64_t kk = k + (k & 1), np = kk / 2, m1 = kk - 1;
+  dfr* rc = (dfr*)w.rot;
+  dfr* rs = rc + np;
+  T* rse = (T*)(rs + np);
+  T* rce = rse + np;
+  int* ron = (int*)(rce + np);
+  int* rpp = ron + np;
+  int* rqq = rpp + np;
+
+  double part = 0.0;
+  for (int64_t idx = gt; idx < k * k; idx += NT) {
+    const int64_t i = idx % k, j = idx / k;
+    if (init_v) V[i + j * ldv] = (i == j) ? df_one(T{}) : df_zero(T{});
+    const D h = df_to_d(H[i + j * ld]);
+    part += abs2(h);
+    if (i == j) dg[i] = real_part(h);
+  }
+  part = block_sum(part);
+  if (threadIdx.x == 0) w.partial[blockIdx.x] = part;
+  if (!group_barrier(w.counter, (++nb) * (unsigned)P, w.status)) return;
+  double fro2 = 0.0;
+  for (int q = 0; q < P; ++q) fro2 += __ldcg(&w.partial[q]);
+  const double thr = tol * sqrt(fro2);
+
+  int sweeps = 0;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    for (int64_t r = 0; r < m1; ++r) {
+      int any_on = 0;
+      for (int64_t i = gt; i < np; i += NT) {
+        int64_t a, b;
+        if (i == 0) { a = r % m1; b = m1; }
+        else { a = (r + i) % m1; b = ((r - i) % m1 + m1) % m1; }
+        const int64_t p = a < b ? a : b, q = a < b ? b : a;
+        double c = 1.0, sn = 0.0;
+        D se = cvt<D>(0.0), ce = cvt<D>(1.0);
+        int on = 0;
+        if (q < k) {
+          const D apq = df_to_d(df_ldcg(&H[p + q * ld]));
+          const double g = sqrt(abs2(apq));
+          if (g > thr) {
+            const double app = __ldcg(&dg[p]), aqq = __ldcg(&dg[q]);
+            const D e = conj(apq) * (1.0 / g);
+            const double tau = (aqq - app) / (2.0 * g);
+            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + hypot(1.0, tau));
+            c = 1.0 / hypot(1.0, t);
+            sn = t * c;
+            se = e * sn;
+            ce = e * c;
+            dg[p] = app - t * g;
+            dg[q] = aqq + t * g;
+            on = 1;
+          }
+        }
+        any_on |= on;
+        rc[i] = dfr(c); rs[i] = dfr(sn); rse[i] = df_from_d(se); rce[i] = df_from_d(ce);
+        ron[i] = on; rpp[i] = (int)p; rqq[i] = (int)q;
+      }
+      const int64_t gr = (int64_t)sweep * m1 + r;
+      if (__syncthreads_or(any_on) && threadIdx.x == 0) {
+        atomicAdd(&w.roundcount[gr], 1u);
+        atomicAdd(&w.rotcount[sweep], 1u);
+      }
+      if (!group_barrier(w.counter, (++nb) * (unsigned)P, w.status)) return;
+      if (__ldcg(&w.roundcount[gr]) == 0u) continue;
+      const int64_t nblk = np * np;
+      for (int64_t task = gt; task < nblk + k * np; task += NT) {
+        if (task < nblk) {
+          const int64_t I = task % np, J = task / np;
+          if (I > J) continue;
+          const int onI = __ldcg(&ron[I]), onJ = __ldcg(&ron[J]);
+          if (!onI && !onJ) continue;
+          const int pI = __ldcg(&rpp[I]), qI = __ldcg(&rqq[I]);
+          const int pJ = __ldcg(&rpp[J]), qJ = __ldcg(&rqq[J]);
+          const bool vqI = qI < k, vqJ = qJ < k;
+          if (I == J) {  // the pair's own 2 x 2 block: diagonal from dg, the pair annihilated
+            H[pI + (int64_t)pI * ld] = df_from_d(cvt<D>(__ldcg(&dg[pI])));
+            if (vqI) {
+              H[qI + (int64_t)qI * ld] = df_from_d(cvt<D>(__ldcg(&dg[qI])));
+              H[pI + (int64_t)qI * ld] = df_zero(T{});
+              H[qI + (int64_t)pI * ld] = df_zero(T{});
+            }
+            continue;
+          }
+          T b00 = df_ldcg(&H[pI + (int64_t)pJ * ld]);
+          T b01 = vqJ ? df_ldcg(&H[pI + (int64_t)qJ * ld]) : df_zero(T{});
+          T b10 = vqI ? df_ldcg(&H[qI + (int64_t)pJ * ld]) : df_zero(T{});
+          T b11 = (vqI && vqJ) ? df_ldcg(&H[qI + (int64_t)qJ * ld]) : df_zero(T{});
+          if (onJ) {
+            const dfr c = df_ldcg(&rc[J]), sn = df_ldcg(&rs[J]);
+            const T se = df_ldcg(&rse[J]), ce = df_ldcg(&rce[J]);
+            const T n00 = df_sub(df_mulr(b00, c), df_mul(b01, se)), n01 = df_add(df_mulr(b00, sn), df_mul(b01, ce));
+            const T n10 = df_sub(df_mulr(b10, c), df_mul(b11, se)), n11 = df_add(df_mulr(b10, sn), df_mul(b11, ce));
+            b00 = n00; b01 = n01; b10 = n10; b11 = n11;
+          }
+          if (onI) {
+            const dfr c = df_ldcg(&rc[I]), sn = df_ldcg(&rs[I]);
+            const T sec = df_conj(df_ldcg(&rse[I])), cec = df_conj(df_ldcg(&rce[I]));
+            const T n00 = df_sub(df_mulr(b00, c), df_mul(b10, sec)), n10 = df_add(df_mulr(b00, sn), df_mul(b10, cec));
+            const T n01 = df_sub(df_mulr(b01, c), df_mul(b11, sec)), n11 = df_add(df_mulr(b01, sn), df_mul(b11, cec));
+            b00 = n00; b01 = n01; b10 = n10; b11 = n11;
+          }
+          H[pI + (int64_t)pJ * ld] = b00;
+          if (vqJ) H[pI + (int64_t)qJ * ld] = b01;
+          if (vqI) H[qI + (int64_t)pJ * ld] = b10;
+          if (vqI && vqJ) H[qI + (int64_t)qJ * ld] = b11;
+          H[pJ + (int64_t)pI * ld] = df_conj(b00);
+          if (vqJ) H[qJ + (int64_t)pI * ld] = df_conj(b01);
+          if (vqI) H[pJ + (int64_t)qI * ld] = df_conj(b10);
+          if (vqI && vqJ) H[qJ + (int64_t)qI * ld] = df_conj(b11);
+        } else {
+          const int64_t tv = task - nblk;
+          const int64_t row = tv % k, J = tv / k;
+          if (!__ldcg(&ron[J])) continue;
+          const int pJ = __ldcg(&rpp[J]), qJ = __ldcg(&rqq[J]);
+          const dfr c = df_ldcg(&rc[J]), sn = df_ldcg(&rs[J]);
+          const T se = df_ldcg(&rse[J]), ce = df_ldcg(&rce[J]);
+          T* vp = &V[row + (int64_t)pJ * ldv];
+          T* vq = &V[row + (int64_t)qJ * ldv];
+          const T a = df_ldcg(vp), b = df_ldcg(vq);
+          *vp = df_sub(df_mulr(a, c), df_mul(b, se));
+          *vq = df_add(df_mulr(a, sn), df_mul(b, ce));
+        }
+      }
+      if (!group_barrier(w.counter, (++nb) * (unsigned)P, w.status)) return;
+    }
+    sweeps = sweep + 1;
+    if (__ldcg(&w.rotcount[sweep]) == 0u) break;
+  }
+  if (gt == 0) w.info[1] = sweeps;
+}
+
+// in place: FP64 storage <-> double-float storage (same bytes per element)
+template <typename S, typename T>
+__global__ void to_df_kernel(S* X, int64_t k, int64_t ld) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < k * k; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t % k, j = t / k;
+    S* e = &X[i + j * ld];
+    const T v = df_from_d(*e);
+    *reinterpret_cast<T*>(e) = v;
+  }
+}
+template <typename S, typename T>
+__global__ void from_df_kernel(S* X, int64_t k, int64_t ld, const double* dg) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < k * k; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t % k, j = t / k;
+    S* e = &X[i + j * ld];
+    const T v = *reinterpret_cast<const T*>(e);
+    *e = (dg && i == j) ? cvt<S>(dg[i]) : df_to_d(v);
+  }
+}
+
 template <typename S>
 void jacobi_eigh(S* H, int64_t k, int64_t ld, S* V, int64_t ldv, double tol, const CoopWork& w, int num_sms,
                  cudaStream_t s, int max_sweeps, bool init_v) {
@@ -515,6 +747,39 @@ void jacobi_eigh(S* H, int64_t k, int64_t ld, S* V, int64_t ldv, double tol, con
   void* args[] = {&H, &k, &ld, &V, &ldv, &tol, &wl, &P, &maxs, &iv};
   FEAST_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)jacobi_kernel<S>, dim3(P), dim3(256), args, 0, s));
   note_launch();
+}
+
+template <typename S>
+void jacobi_eigh_df(S* H, int64_t k, int64_t ld, S* V, int64_t ldv, double* dg, double tol, const CoopWork& w,
+                    int num_sms, cudaStream_t s, int max_sweeps, bool init_v) {
+  using T = typename std::conditional<is_cx<S>::value, dfc, dfr>::type;
+  static_assert(sizeof(T) == sizeof(S), "double-float storage takes the FP64 element's bytes");
+  FEAST_CUDA_TRY(cudaMemsetAsync(w.counter, 0, 256 * 3, s));
+  FEAST_CUDA_TRY(cudaMemsetAsync(w.rotcount, 0, sizeof(unsigned) * kMaxSweeps, s));
+  FEAST_CUDA_TRY(cudaMemsetAsync(w.roundcount, 0, sizeof(unsigned) * kMaxSweeps * (size_t)(k + 2), s));
+  to_df_kernel<S, T><<<grid1d(k * k), 256, 0, s>>>(H, k, ld);
+  FEAST_LAUNCH_CHECK();
+  if (!init_v) {
+    to_df_kernel<S, T><<<grid1d(k * k), 256, 0, s>>>(V, k, ldv);
+    FEAST_LAUNCH_CHECK();
+  }
+  int occ = 0;
+  FEAST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, jacobi_df_kernel<T>, 256, 0));
+  const int64_t tasks = (k / 2 + 1) * (k / 2 + 1) + k * (k / 2 + 1);
+  int P = (int)std::min<int64_t>((int64_t)std::max(1, occ) * num_sms, cdiv(tasks, 256 * 8));
+  P = std::max(1, std::min(P, num_sms));
+  int maxs = std::max(1, std::min(max_sweeps, kMaxSweeps));
+  int iv = init_v ? 1 : 0;
+  CoopWork wl = w;
+  T* Ht = reinterpret_cast<T*>(H);
+  T* Vt = reinterpret_cast<T*>(V);
+  void* args[] = {&Ht, &k, &ld, &Vt, &ldv, &dg, &tol, &wl, &P, &maxs, &iv};
+  FEAST_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)jacobi_df_kernel<T>, dim3(P), dim3(256), args, 0, s));
+  note_launch();
+  from_df_kernel<S, T><<<grid1d(k * k), 256, 0, s>>>(H, k, ld, dg);
+  FEAST_LAUNCH_CHECK();
+  from_df_kernel<S, T><<<grid1d(k * k), 256, 0, s>>>(V, k, ldv, nullptr);
+  FEAST_LAUNCH_CHECK();
 }
 
 template <typename S> void get_diag(const S* H, int64_t k, int64_t ld, double* d, cudaStream_t s) {
@@ -554,6 +819,26 @@ void gather_cols(S* dst, int64_t lddst, const S* src, int64_t ldsrc, int64_t n, 
                  const double* scale, cudaStream_t s) {
   if (k <= 0) return;
   gather_cols_kernel<S><<<grid1d(n * k), 256, 0, s>>>(dst, lddst, src, ldsrc, n, idx, k, scale);
+  FEAST_LAUNCH_CHECK();
+}
+
+template <typename S> void gather_sub(S* dst, const S* src, int64_t lds, const int* idx, int64_t ks, cudaStream_t s) {
+  if (ks <= 0) return;
+  gather_sub_kernel<S><<<grid1d(ks * ks), 256, 0, s>>>(dst, src, lds, idx, ks);
+  FEAST_LAUNCH_CHECK();
+}
+
+template <typename S> void scatter_sub(S* dst, int64_t ldd, const S* src, const int* idx, int64_t ks, cudaStream_t s) {
+  if (ks <= 0) return;
+  scatter_sub_kernel<S><<<grid1d(ks * ks), 256, 0, s>>>(dst, ldd, src, idx, ks);
+  FEAST_LAUNCH_CHECK();
+}
+
+template <typename S>
+void scatter_cols(S* dst, int64_t lddst, const S* src, int64_t ldsrc, int64_t n, const int* idx, int64_t k,
+                  cudaStream_t s) {
+  if (k <= 0) return;
+  scatter_cols_kernel<S><<<grid1d(n * k), 256, 0, s>>>(dst, lddst, src, ldsrc, n, idx, k);
   FEAST_LAUNCH_CHECK();
 }
 
@@ -1100,6 +1385,11 @@ void cluster_jacobi(S* H, int64_t k, int64_t ld, S* V, int64_t ldv, const int* i
   template void gather_cols<S>(S*, int64_t, const S*, int64_t, int64_t, const int*, int64_t, const double*, \
                                cudaStream_t);                                                             \
   template void scale_cols<S>(S*, int64_t, int64_t, int64_t, const double*, cudaStream_t);                 \
+  template void jacobi_eigh_df<S>(S*, int64_t, int64_t, S*, int64_t, double*, double, const CoopWork&, int,  \
+                                  cudaStream_t, int, bool);                                                \
+  template void gather_sub<S>(S*, const S*, int64_t, const int*, int64_t, cudaStream_t);                   \
+  template void scatter_sub<S>(S*, int64_t, const S*, const int*, int64_t, cudaStream_t);                  \
+  template void scatter_cols<S>(S*, int64_t, const S*, int64_t, int64_t, const int*, int64_t, cudaStream_t); \
   template void accumulate_filter<S>(S*, int64_t, const c128*, int64_t, int64_t, int, const c128*,         \
                                      cudaStream_t);                                                       \
   template void refine_residual<S>(c128*, const S*, int64_t, const c128*, const c128*, int64_t, int64_t,   \

@@ -44,6 +44,14 @@ template <typename S>
 void jacobi_eigh(S* H, int64_t k, int64_t ld, S* V, int64_t ldv, double tol, const CoopWork& w,
                  int num_sms, cudaStream_t s, int max_sweeps = kMaxSweeps, bool init_v = true);
 
+// The same sweeps with H and V held as double-float values and every
+// rotation applied on the FP32 pipes (converted in place from and back to
+// FP64; S = double or c128); the diagonal is kept and updated in FP64 in dg
+// (k doubles of scratch), so the eigenvalues keep FP64 accuracy while the
+// off-diagonal entries and the vectors carry about 48 bits.
+template <typename S>
+void jacobi_eigh_df(S* H, int64_t k, int64_t ld, S* V, int64_t ldv, double* dg, double tol, const CoopWork& w,
+                    int num_sms, cudaStream_t s, int max_sweeps = kMaxSweeps, bool init_v = true);
 // Cluster finish of the FP64 Jacobi.  offdiag_scan lists the pairs i < j with
 // |h_ij| > thr (absolute): *cnt (device) receives their number, list the
 // first cap of them as (i, j).  cluster_jacobi diagonalises, for each of the
@@ -104,6 +112,13 @@ template <typename S>
 void gather_cols(S* dst, int64_t lddst, const S* src, int64_t ldsrc, int64_t n, const int* idx, int64_t k,
                  const double* scale, cudaStream_t s);
 
+// dst (ks x ks, ld ks) = src[idx, idx] (ld lds); scatter_sub the reverse
+template <typename S> void gather_sub(S* dst, const S* src, int64_t lds, const int* idx, int64_t ks, cudaStream_t s);
+template <typename S> void scatter_sub(S* dst, int64_t ldd, const S* src, const int* idx, int64_t ks, cudaStream_t s);
+// dst[:, idx[j]] = src[:, j] (n rows, k columns)
+template <typename S>
+void scatter_cols(S* dst, int64_t lddst, const S* src, int64_t ldsrc, int64_t n, const int* idx, int64_t k,
+                  cudaStream_t s);
 // X[:, j] *= scale[j]
 template <typename S> void scale_cols(S* X, int64_t n, int64_t k, int64_t ld, const double* scale, cudaStream_t s);
 

@@ -17,6 +17,7 @@
 #include "factor.cuh"
 
 #include <algorithm>
+#include <cstdlib>
 #include <climits>
 
 namespace feast {
@@ -506,9 +507,9 @@ trsm_diag_kernel(const F* M, int64_t ld, int64_t stride, F* Y, int64_t n, int64_
 // the next panel loaded into registers while the current one is used.  Panel
 // p holds the columns of register p, so every register index is a
 // compile-time constant and the rows a step cannot touch are skipped whole.
-// Modes as trsm_diag_kernel.  The solved block also goes out as the six bf16
-// planes of the outer update's right operand (K index = row within the outer
-// block, zero past bs).
+// Modes as trsm_diag_kernel; a non-unit diagonal is stored as its reciprocal.
+// The solved block also goes out as the six bf16 planes of the outer update's
+// right operand (K index = row within the outer block, zero past bs).
 constexpr int kTrsmOuterWarps = 16;
 constexpr int kTrsmOuterThreads = kTrsmOuterWarps * 32;
 constexpr int kTrsmOuterLd = kSolveOuter + 1;  // padded panel column
@@ -561,7 +562,8 @@ trsm_outer_kernel(const c64* __restrict__ M, int64_t ld, int64_t stride, c64* __
       const int l = tid + kTrsmOuterThreads * i;
       const int rr = kStored ? (l & (OB - 1)) : (l >> 5);
       const int cc = kStored ? (c0 + (l >> 8)) : (c0 + (l & 31));
-      P[(cc - c0) * LDP + rr] = pre[i];
+      // non-unit diagonal: its reciprocal, the only use of the entry
+      P[(cc - c0) * LDP + rr] = (!kUnit && rr == cc) ? recip(pre[i]) : pre[i];
     }
   };
   const int np = (bs + 31) / 32;
@@ -580,8 +582,11 @@ trsm_outer_kernel(const c64* __restrict__ M, int64_t ld, int64_t stride, c64* __
     for (int t = 0; t < jend; ++t) {
       const int jl = kFwd ? t : jend - 1 - t;
       const c64* Tj = P + jl * LDP;
-      if (!kUnit && lane == jl) x[p] = x[p] * recip(Tj[32 * p + jl]);
-      const c64 xj = shfl(x[p], jl);
+      c64 xj = shfl(x[p], jl);
+      if (!kUnit) {  // every lane scales the broadcast value; lane jl keeps it
+        xj = xj * Tj[32 * p + jl];
+        if (lane == jl) x[p] = xj;
+      }
       if (kFwd) {
         if (lane > jl) x[p] = x[p] - Tj[32 * p + lane] * xj;
 #pragma unroll

@@ -281,6 +281,9 @@ struct Solver {
   int* d_csw = nullptr;
   S* Ucl = nullptr;
   int64_t ccap = 0;
+  // sweeps restricted to the indices of the above-threshold pairs
+  S *Hsub = nullptr, *Vsub = nullptr, *Tsub = nullptr, *Tsub2 = nullptr;
+  double* d_dg = nullptr;  // FP64 diagonal of the double-float sweeps
   static constexpr int kPolishSweeps = 2;  // full FP64 sweeps before the cluster finish
   // mixed, opts.refine_gemm = 1: double-float planes of A (hi/lo of Re, Im,
   // Re + Im) and of the right-hand block of an A product
@@ -301,8 +304,7 @@ struct Solver {
   // routed through the digit-split GEMM: its error is bounded by row/column
   // maxima, and on the graded filtered bases it held the n = 8192 RFEAST
   // residuals above 1e-10 ||A||.  Their op-N products take the double-float
-  // GEMM (mm_df below); the Hermitian reductions over n (Gram matrices,
-  // Q^H W) stay FP64.
+  // GEMM (mm_df below); the Gram matrices of the filtered bases stay FP64.
   // Rayleigh-Ritz scratch
   S *Qb = nullptr, *Wb = nullptr, *Xr = nullptr, *AXr = nullptr, *T1 = nullptr, *T2 = nullptr;
   S *Ar0 = nullptr, *Ar = nullptr, *Vk = nullptr, *Gs = nullptr, *Ri = nullptr, *Cs = nullptr, *Cs2 = nullptr;
@@ -435,6 +437,8 @@ struct Solver {
       d_coff = dalloc<int>(ctx, kmax / 2 + 2);
       d_csw = dalloc<int>(ctx, kmax / 2 + 1);
       Ucl = dalloc<S>(ctx, (kmax / 2 + 1) * kClusterMax * kClusterMax);
+      Hsub = dalloc<S>(ctx, kk); Vsub = dalloc<S>(ctx, kk); Tsub = dalloc<S>(ctx, kk); Tsub2 = dalloc<S>(ctx, kk);
+      d_dg = dalloc<double>(ctx, kmax);
     }
     part_elems = 32 * kk;
     part = dalloc<S>(ctx, part_elems);
@@ -451,7 +455,8 @@ struct Solver {
   // FP64 rate of this GPU.  The low word of each product sum is accumulated in
   // FP32 and flushed to FP64 every 32 terms; the error stays within 2^-44 of
   // sum |a||b| (the parity tests' bound), against ~1e-16 sqrt(K) in FP64.  The
-  // eigensolver's k x k products and the Gram matrices stay FP64.  Complex
+  // Gram matrices of the filtered bases stay FP64 (Cholesky-QR squares their
+  // condition number); the eigensolver's k x k products use mm_eig.  Complex
   // products take the four real products (4M): the three-product form (3M)
   // forms Im as T3 - T1 - T2, whose cancellation made the n = 8192 RFEAST solve
   // take 4 iterations instead of 2; 4M keeps 2.
@@ -541,6 +546,23 @@ struct Solver {
     while (ks > 1 && (int64_t)ks * k * k > part_elems) --ks;
     gemm_simple<S, S, S>(k, k, k, C1(1.0), Am, k, opA, Bm, k, OP_N, C1(0.0), Cm, k, st, ks,
                          ks > 1 ? (void*)part : nullptr);
+  }
+  // k x k products of the two-phase eigensolver on the mixed path in
+  // double-float: their operands are unitary, nearly unitary or the reduced
+  // matrix itself, so the error (2^-44 of sum |a||b|) stays near 1e-13 ||A||,
+  // far below what the Ritz pairs need; FP64 otherwise
+  void mm_eig(int64_t k, const S* Am, int opA, const S* Bm, S* Cm) {
+    if (Ldf && Pdf && o.prec != FEAST_PREC_F64 && (double)k * k * k >= kDfMinWork && Cm != Am && Cm != Bm) {
+      if (opA == OP_N) {
+        mm_df(k, k, k, 1.0, Am, k, Bm, k, 0.0, Cm, k);
+        return;
+      }
+      if (opA == OP_C) {
+        mm_df_reduce(k, k, k, Am, k, Bm, k, Cm, k);
+        return;
+      }
+    }
+    mm_square(k, Am, opA, Bm, Cm);
   }
   // C (Mr x Nc) = op(A) op(B) with a long reduction K: split-K
   void mm_reduce(int64_t Mr, int64_t Nc, int64_t K, const S* Am, int64_t la, int opA, const S* Bm, int64_t lb,
@@ -833,7 +855,7 @@ struct Solver {
     int info = 0;
     phase("eig: Cholesky-QR of V", [&] {
       convert_matrix<S, F32>(Ve, k, V32, k, k, k, st);
-      mm_square(k, Ve, OP_C, Ve, Te);
+      mm_eig(k, Ve, OP_C, Ve, Te);
       hermitize<S>(Te, k, k, st);
       cholesky_upper<S>(Te, k, k, cw, ctx->num_sms, st);
       to_host(ctx, &info, cw.info, 1);
@@ -842,14 +864,14 @@ struct Solver {
     if (info != 0) return false;
     phase("eig: V^H H V", [&] {
       tri_inverse_upper<S>(Te, k, k, T2e, k, st);
-      mm_square(k, Ve, OP_N, T2e, Te);   // Te: orthonormal V
-      mm_square(k, H, OP_N, Te, T2e);    // H V
-      mm_square(k, Te, OP_C, T2e, H);    // V^H H V
+      mm_eig(k, Ve, OP_N, T2e, Te);   // Te: orthonormal V
+      mm_eig(k, H, OP_N, Te, T2e);    // H V
+      mm_eig(k, Te, OP_C, T2e, H);    // V^H H V
       hermitize<S>(H, k, k, st);
     });
     int sw64 = 0;
     phase("eig: FP64 Jacobi", [&] { sw64 = polish(H, k); });
-    phase("eig: V V'", [&] { mm_square(k, Te, OP_N, T2e, Vk); });
+    phase("eig: V V'", [&] { mm_eig(k, Te, OP_N, T2e, Vk); });
     *sweeps = sw32 + sw64;
     if (std::getenv("FEAST_LOG"))
       fprintf(stderr, "[feast] two-phase eig k=%lld: %d FP32 + %d FP64 sweeps\n", (long long)k, sw32, sw64);
@@ -865,12 +887,20 @@ struct Solver {
   int polish(S* H, int64_t k) {
     const bool log = std::getenv("FEAST_LOG") != nullptr;
     int sweeps = 0, s1 = 0;
-    jacobi_eigh<S>(H, k, k, T2e, k, 1e-15, cw, ctx->num_sms, st, kPolishSweeps, true);
+    // mixed path: the sweeps in double-float on the FP32 pipes (the diagonal
+    // in FP64); the FP64 path keeps FP64 sweeps
+    auto sweep = [&](S* Hm, int64_t km, S* Vm, double tol, int maxs, bool init) {
+      if (o.prec != FEAST_PREC_F64 && d_dg)
+        jacobi_eigh_df<S>(Hm, km, km, Vm, km, d_dg, tol, cw, ctx->num_sms, st, maxs, init);
+      else
+        jacobi_eigh<S>(Hm, km, km, Vm, km, tol, cw, ctx->num_sms, st, maxs, init);
+    };
+    sweep(H, k, T2e, 1e-15, kPolishSweeps, true);
     jacobi_status(&s1);
     sweeps += s1;
     if (!d_ccnt) {
       if (s1 >= kPolishSweeps) {
-        jacobi_eigh<S>(H, k, k, T2e, k, 1e-15, cw, ctx->num_sms, st, kMaxSweeps, false);
+        sweep(H, k, T2e, 1e-15, kMaxSweeps, false);
         jacobi_status(&s1);
         sweeps += s1;
       }
@@ -892,6 +922,7 @@ struct Solver {
       if (cnt == 0) return sweeps;
       bool sets_ok = cnt <= ccap;
       int nsets = 0, maxset = 0;
+      std::vector<int> act;  // indices of the above-threshold pairs
       if (sets_ok) {
         list.resize(2 * (size_t)cnt);
         to_host(ctx, list.data(), d_clist, 2 * (int64_t)cnt);
@@ -908,6 +939,8 @@ struct Solver {
         std::vector<int> root_of(k, -1), count;
         std::vector<char> used(k, 0);
         for (int e = 0; e < 2 * cnt; ++e) used[list[e]] = 1;
+        for (int64_t i = 0; i < k; ++i)
+          if (used[i]) act.push_back((int)i);
         std::vector<int> setid(k, -1);
         for (int64_t i = 0; i < k; ++i)
           if (used[i]) {
@@ -932,9 +965,16 @@ struct Solver {
             if (setid[i] >= 0) setidx[fill[setid[i]]++] = (int)i;
         }
       }
+      // a set too large for the shared-memory finish: one sweep restricted to
+      // the indices of the above-threshold pairs (a sweep's cost is its
+      // rounds, one per index); the entries between them and the other
+      // indices are at most thr and stay as they are
+      const int64_t ks = (int64_t)act.size();
+      const bool restricted = !sets_ok && ks >= 2 && ks < k && Hsub != nullptr;
       if (log)
         fprintf(stderr, "[feast] FP64 polish k=%lld pass %d: %d pairs above threshold, %d sets, largest %d%s\n",
-                (long long)k, pass, cnt, nsets, maxset, sets_ok ? "" : " -> full sweep");
+                (long long)k, pass, cnt, nsets, maxset,
+                sets_ok ? "" : (restricted ? " -> sweep over the linked indices" : " -> full sweep"));
       if (sets_ok) {
         to_dev(ctx, d_cidx, setidx.data(), (int64_t)setidx.size());
         to_dev(ctx, d_coff, setoff.data(), (int64_t)nsets + 1);
@@ -945,14 +985,31 @@ struct Solver {
           fprintf(stderr, "[feast] FP64 polish k=%lld: set sweeps max %d\n", (long long)k,
                   *std::max_element(swc.begin(), swc.end()));
         }
+      } else if (restricted) {
+        to_dev(ctx, d_cidx, act.data(), ks);
+        gather_sub<S>(Hsub, H, k, d_cidx, ks, st);
+        col_norms2<S>(Hsub, ks, ks, ks, d_nrm, st);
+        std::vector<double> sn(ks);
+        to_host(ctx, sn.data(), d_nrm, ks);
+        double sub2 = 0.0;
+        for (double v : sn) sub2 += v;
+        // the same absolute threshold as the whole matrix's
+        const double tol_sub = sub2 > 0.0 ? thr / std::sqrt(sub2) : 1e-15;
+        sweep(Hsub, ks, Vsub, tol_sub, 1, true);
+        jacobi_status(&s1);
+        sweeps += s1;
+        scatter_sub<S>(H, k, Hsub, d_cidx, ks, st);
+        gather_cols<S>(Tsub, k, T2e, k, k, d_cidx, ks, nullptr, st);
+        gemm_simple<S, S, S>(k, ks, ks, C1(1.0), Tsub, k, OP_N, Vsub, ks, OP_N, C1(0.0), Tsub2, k, st);
+        scatter_cols<S>(T2e, k, Tsub2, k, k, d_cidx, ks, st);
       } else {
-        jacobi_eigh<S>(H, k, k, T2e, k, 1e-15, cw, ctx->num_sms, st, 1, false);
+        sweep(H, k, T2e, 1e-15, 1, false);
         jacobi_status(&s1);
         sweeps += s1;
       }
     }
     // still not below the threshold: finish with full sweeps
-    jacobi_eigh<S>(H, k, k, T2e, k, 1e-15, cw, ctx->num_sms, st, kMaxSweeps, false);
+    sweep(H, k, T2e, 1e-15, kMaxSweeps, false);
     jacobi_status(&s1);
     return sweeps + s1;
   }
