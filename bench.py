@@ -73,6 +73,13 @@ CGEMM_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum over t
 TCG_DRAM_BYTES_PER_FLOP = (931.6e6 + 150.4e6) / (5.92e10 + 9.44e9)
 TCG_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one LU and one solve cg_update_kernel "
                       "launch (n = 4096 filter, 1082 MB for 6.86e10 flops) x flops per launch")
+# the same for the digit-split GEMM: one full-size launch of the n = 8192 solve (the second oz_gemm_kernel
+# launch, M = K = 8192, N = 16 x 300: 6.90 GB read + 0.31 GB written for 3.22e11 multiply-adds; one pass,
+# profiles/oz_gemm_kernel_filter_n4096.md); a launch's waves of 152 tiles each stream their row and column
+# panels, so traffic grows with the launch's multiply-adds
+OZ_DRAM_BYTES_PER_MAC = (6.90e9 + 0.31387e9) / (8192.0 * 8192.0 * 4800.0)
+OZ_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one full-size oz_gemm_kernel launch "
+                     "(M = K = 8192, N = 4800: 7.21 GB for 3.22e11 multiply-adds) x multiply-adds per launch")
 
 
 
@@ -586,7 +593,8 @@ def run_ours(args, rank, world, dev):
         achieved = OZ_PAIRS * 2.0 * rg_mac_per_launch / rg_secs / 1e12 if rg_secs > 0 else 0.0
         roofline_refine = {"kernel": "oz_gemm_kernel", "bound": "tensor", "achieved": round(achieved, 2),
                            "peak": round(peak, 1), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                           "traffic": None,
+                           "traffic": int(OZ_DRAM_BYTES_PER_MAC * rg_mac_per_launch),
+                           "traffic_source": OZ_TRAFFIC_SOURCE,
                            "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (%s)" % peak_kind,
                            "flop_def": "21 bf16 digit products x 2 x M N K per launch",
                            "fp64_equiv_tflops": round(achieved / OZ_PAIRS, 3)}
