@@ -8,7 +8,10 @@
 //      bounded group barrier, then every CTA picks the same winner, swaps the
 //      pivot row with the diagonal row where it owns them, scales its part of
 //      the column and applies the rank-1 update to the rest of the panel,
-//      tracking the next column's local maximum on the way.
+//      tracking the next column's local maximum on the way.  When every
+//      node's rows fit in co-resident CTAs of at most kPanelCacheRows rows,
+//      each CTA keeps its rows of the panel in shared memory for the whole
+//      panel (loaded once, written back once).
 //   2. laswp_trsm_kernel: the panel's row interchanges applied to every column
 //      outside the panel (as a gather of at most 2*kPanel touched rows), and
 //      U12 = L11^{-1} A12 by a warp-per-column forward substitution.
@@ -25,6 +28,7 @@ namespace feast {
 namespace {
 
 constexpr int kPanelThreads = 256;
+constexpr int kPanelCacheRows = 128;  // rows per CTA of the shared-memory panel
 
 template <typename F>
 __device__ __forceinline__ void argmax_merge(double& v, int& i, double v2, int i2) {
@@ -52,7 +56,9 @@ __device__ void block_argmax(double& v, int& i) {
   i = si[0];
 }
 
-template <typename F>
+// CACHE: the CTA's rows of the panel stay in shared memory (R x jb, dynamic)
+// for the whole panel instead of being re-read from L2 every column.
+template <typename F, bool CACHE>
 __global__ void __launch_bounds__(kPanelThreads)
 panel_lu_kernel(F* M, int64_t n, int64_t ld, int64_t stride, int k0, int jb, int P, int64_t R,
                 int32_t* ipiv, PanelWork w, unsigned base) {
@@ -69,12 +75,27 @@ panel_lu_kernel(F* M, int64_t n, int64_t ld, int64_t stride, int k0, int jb, int
   __shared__ F s_d[kPanel];
   __shared__ int s_p;
   __shared__ int s_win;
+  extern __shared__ __align__(16) unsigned char panel_smem[];
+  F* T = reinterpret_cast<F*>(panel_smem);
+  // element (row i, panel column cc) of a row this CTA owns
+  auto at = [&](int64_t i, int cc) -> F& {
+    if constexpr (CACHE) return T[(i - row_lo) + (int64_t)cc * R];
+    else return Mb[i + (int64_t)(k0 + cc) * ld];
+  };
+  if constexpr (CACHE) {
+    const int64_t nr = row_hi - row_lo;
+    for (int64_t l = t; l < nr * jb; l += kPanelThreads) {
+      const int64_t i = l % nr, cc = l / nr;
+      T[i + cc * R] = Mb[(row_lo + i) + (k0 + cc) * ld];
+    }
+    __syncthreads();
+  }
 
   // local maximum of column k0
   double v = -1.0;
   int vi = -1;
   for (int64_t i = row_lo + t; i < row_hi; i += kPanelThreads) {
-    double a = (double)abs2(Mb[i + (int64_t)k0 * ld]);
+    double a = (double)abs2(at(i, 0));
     argmax_merge<F>(v, vi, a, (int)i);
   }
   block_argmax<F>(v, vi);
@@ -90,10 +111,10 @@ panel_lu_kernel(F* M, int64_t n, int64_t ld, int64_t stride, int k0, int jb, int
     }
     if (vi >= 0)
       for (int cc = t; cc < jb; cc += kPanelThreads)
-        cand_row[slot * kPanel + cc] = Mb[vi + (int64_t)(k0 + cc) * ld];
+        cand_row[slot * kPanel + cc] = at(vi, cc);
     if (d >= row_lo && d < row_hi)
       for (int cc = t; cc < jb; cc += kPanelThreads)
-        diag_row[((int64_t)b * 2 + par) * kPanel + cc] = Mb[d + (int64_t)(k0 + cc) * ld];
+        diag_row[((int64_t)b * 2 + par) * kPanel + cc] = at(d, cc);
     if (!group_barrier(ctr, base + (unsigned)(j + 1) * (unsigned)P, w.status)) return;
 
     if (t < 32) {
@@ -158,9 +179,9 @@ panel_lu_kernel(F* M, int64_t n, int64_t ld, int64_t stride, int k0, int jb, int
       inv = recip(piv);
     }
     if (d >= row_lo && d < row_hi)
-      for (int cc = t; cc < jb; cc += kPanelThreads) Mb[d + (int64_t)(k0 + cc) * ld] = s_u[cc];
+      for (int cc = t; cc < jb; cc += kPanelThreads) at(d, cc) = s_u[cc];
     if (p != d && p >= row_lo && p < row_hi)
-      for (int cc = t; cc < jb; cc += kPanelThreads) Mb[p + (int64_t)(k0 + cc) * ld] = s_d[cc];
+      for (int cc = t; cc < jb; cc += kPanelThreads) at(p, cc) = s_d[cc];
     if (c == 0 && t == 0) ipiv[(int64_t)b * n + d] = p;
     __syncthreads();
 
@@ -168,17 +189,23 @@ panel_lu_kernel(F* M, int64_t n, int64_t ld, int64_t stride, int k0, int jb, int
     vi = -1;
     const int64_t lo = max(row_lo, d + 1);
     for (int64_t i = lo + t; i < row_hi; i += kPanelThreads) {
-      F* ri = Mb + i;
-      F l = ri[col * ld] * inv;
-      ri[col * ld] = l;
+      F l = at(i, j) * inv;
+      at(i, j) = l;
       for (int cc = j + 1; cc < jb; ++cc) {
-        F x = ri[(int64_t)(k0 + cc) * ld] - l * s_u[cc];
-        ri[(int64_t)(k0 + cc) * ld] = x;
+        F x = at(i, cc) - l * s_u[cc];
+        at(i, cc) = x;
         if (cc == j + 1) argmax_merge<F>(v, vi, (double)abs2(x), (int)i);
       }
     }
     if (j + 1 < jb) block_argmax<F>(v, vi);
     else __syncthreads();
+  }
+  if constexpr (CACHE) {
+    const int64_t nr = row_hi - row_lo;
+    for (int64_t l = t; l < nr * jb; l += kPanelThreads) {
+      const int64_t i = l % nr, cc = l / nr;
+      Mb[(row_lo + i) + (k0 + cc) * ld] = T[i + cc * R];
+    }
   }
 
   // net effect of the panel's interchanges on the rows it touched:
@@ -748,8 +775,16 @@ void lu_factor_batched(F* M, int64_t n, int64_t ld, int64_t stride, int nodes,
   FEAST_CUDA_TRY(cudaMemsetAsync(w.status, 0, sizeof(int), s));
   FEAST_CUDA_TRY(cudaMemsetAsync(w.zero_pivot, 0, sizeof(int) * nodes, s));
   int occ = 0;
-  FEAST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, panel_lu_kernel<F>, kPanelThreads, 0));
+  FEAST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, panel_lu_kernel<F, false>, kPanelThreads, 0));
   const int max_coop = std::max(1, occ) * num_sms;
+  // the shared-memory variant: at most kPanelCacheRows rows per CTA
+  const size_t cache_max = sizeof(F) * (size_t)kPanelCacheRows * kPanel;
+  FEAST_CUDA_TRY(cudaFuncSetAttribute(panel_lu_kernel<F, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)cache_max));
+  int occ_c = 0;
+  FEAST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_c, panel_lu_kernel<F, true>, kPanelThreads,
+                                                               cache_max));
+  const int max_coop_c = occ_c * num_sms;
   unsigned base = 0;
   // complex-FP32 factors with tensor-core scratch: two-level blocking, outer
   // blocks of kTcBlock columns whose trailing update runs on the tensor cores,
@@ -770,14 +805,27 @@ void lu_factor_batched(F* M, int64_t n, int64_t ld, int64_t stride, int nodes,
   };
   auto panel = [&](int64_t k1, int jb) {
     const int64_t H = n - k1;
+    int k1i = (int)k1;
+    PanelWork wl = w;
+    // rows of the panel in shared memory when every node's rows fit in
+    // co-resident CTAs of at most kPanelCacheRows rows each
+    int Pc = (int)std::min<int64_t>({cdiv(H, 64), (int64_t)(max_coop_c / nodes), (int64_t)w.pmax});
+    if (Pc >= 1 && cdiv(H, Pc) <= kPanelCacheRows) {
+      const int64_t Rc = cdiv(H, Pc);
+      int P = (int)cdiv(H, Rc);
+      void* args[] = {&M, &n, &ld, &stride, &k1i, (void*)&jb, &P, (void*)&Rc, &ipiv, &wl, &base};
+      FEAST_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)panel_lu_kernel<F, true>, dim3(nodes * P),
+                                                 dim3(kPanelThreads), args, sizeof(F) * (size_t)Rc * kPanel, s));
+      note_launch();
+      base += (unsigned)jb * (unsigned)P;
+      return;
+    }
     int P = (int)std::min<int64_t>(cdiv(H, 64), std::max(1, max_coop / nodes));
     P = std::max(1, std::min(P, w.pmax));
     const int64_t R = cdiv(H, P);
     P = (int)cdiv(H, R);  // no empty CTAs
-    int k1i = (int)k1;
-    PanelWork wl = w;
     void* args[] = {&M, &n, &ld, &stride, &k1i, (void*)&jb, &P, (void*)&R, &ipiv, &wl, &base};
-    FEAST_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)panel_lu_kernel<F>, dim3(nodes * P),
+    FEAST_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)panel_lu_kernel<F, false>, dim3(nodes * P),
                                                dim3(kPanelThreads), args, 0, s));
     note_launch();
     base += (unsigned)jb * (unsigned)P;
