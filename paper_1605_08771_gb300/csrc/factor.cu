@@ -11,13 +11,19 @@
 //      tracking the next column's local maximum on the way.  When every
 //      node's rows fit in co-resident CTAs of at most kPanelCacheRows rows,
 //      each CTA keeps its rows of the panel in shared memory for the whole
-//      panel (loaded once, written back once).
+//      panel (loaded once, written back once).  When a node's panel fits in
+//      the shared memory of one 16-CTA thread-block cluster (complex FP32 up to
+//      8192 rows), panel_lu_cluster_kernel takes it instead: candidates and
+//      rows go through distributed shared memory and hardware cluster
+//      barriers.
 //   2. laswp_trsm_kernel: the panel's row interchanges applied to every column
 //      outside the panel (as a gather of at most 2*kPanel touched rows), and
 //      U12 = L11^{-1} A12 by a warp-per-column forward substitution.
 //   3. A22 -= L21 U12 with the batched GEMM.
 // The pivot choice is the first row of largest |m_ik|^2, as in the oracle.
 #include "factor.cuh"
+
+#include <cooperative_groups.h>
 
 #include <algorithm>
 #include <cstdlib>
@@ -54,6 +60,35 @@ __device__ void block_argmax(double& v, int& i) {
   __syncthreads();
   v = sv[0];
   i = si[0];
+}
+
+// net effect of a panel's interchanges on the rows it touched: after the
+// swaps, row dst holds the former row src (one thread)
+__device__ void panel_swap_summary(int b, int64_t n, int k0, int jb, const int32_t* ipiv, const PanelWork& w) {
+  int rows[2 * kPanel], content[2 * kPanel];
+  int cnt = 0;
+  auto slot_of = [&](int r) {
+    for (int q = 0; q < cnt; ++q)
+      if (rows[q] == r) return q;
+    rows[cnt] = r;
+    content[cnt] = r;
+    return cnt++;
+  };
+  for (int j = 0; j < jb; ++j) {
+    int a = slot_of(k0 + j);
+    int bb = slot_of(ipiv[(int64_t)b * n + k0 + j]);
+    int tmp = content[a];
+    content[a] = content[bb];
+    content[bb] = tmp;
+  }
+  int out = 0;
+  for (int q = 0; q < cnt; ++q)
+    if (content[q] != rows[q]) {
+      w.swap_dst[b * 2 * kPanel + out] = rows[q];
+      w.swap_src[b * 2 * kPanel + out] = content[q];
+      ++out;
+    }
+  w.swap_cnt[b] = out;
 }
 
 // CACHE: the CTA's rows of the panel stay in shared memory (R x jb, dynamic)
@@ -208,34 +243,122 @@ panel_lu_kernel(F* M, int64_t n, int64_t ld, int64_t stride, int k0, int jb, int
     }
   }
 
-  // net effect of the panel's interchanges on the rows it touched:
-  // after the swaps, row dst holds the former row src
-  if (c == 0 && t == 0) {
-    int rows[2 * kPanel], content[2 * kPanel];
-    int cnt = 0;
-    auto slot_of = [&](int r) {
-      for (int q = 0; q < cnt; ++q)
-        if (rows[q] == r) return q;
-      rows[cnt] = r;
-      content[cnt] = r;
-      return cnt++;
-    };
-    for (int j = 0; j < jb; ++j) {
-      int a = slot_of(k0 + j);
-      int bb = slot_of(ipiv[(int64_t)b * n + k0 + j]);
-      int tmp = content[a];
-      content[a] = content[bb];
-      content[bb] = tmp;
-    }
-    int out = 0;
-    for (int q = 0; q < cnt; ++q)
-      if (content[q] != rows[q]) {
-        w.swap_dst[b * 2 * kPanel + out] = rows[q];
-        w.swap_src[b * 2 * kPanel + out] = content[q];
-        ++out;
-      }
-    w.swap_cnt[b] = out;
+  if (c == 0 && t == 0) panel_swap_summary(b, n, k0, jb, ipiv, w);
+}
+
+// The panel factored by one thread-block cluster per node: the cluster's
+// kPanelCluster CTAs hold all of the panel's rows in their shared memory
+// (distributed shared memory, R <= kPanelClusterRows rows each), so a column
+// step exchanges its pivot candidates and the pivot and diagonal rows through
+// the cluster's shared memory with two hardware cluster barriers, instead of
+// global memory and a software barrier.  Same arithmetic and pivot choice as
+// panel_lu_kernel.  Clusters (nodes) are independent of one another.
+constexpr int kPanelCluster = 16;
+constexpr int kPanelClusterRows = 512;
+
+template <typename F>
+__global__ void __launch_bounds__(kPanelThreads, 1)
+panel_lu_cluster_kernel(F* M, int64_t n, int64_t ld, int64_t stride, int k0, int jb, int64_t R, int32_t* ipiv,
+                        PanelWork w) {
+  namespace cgx = cooperative_groups;
+  cgx::cluster_group cluster = cgx::this_cluster();
+  const int b = blockIdx.x / kPanelCluster;
+  const int c = (int)cluster.block_rank();
+  const int t = threadIdx.x;
+  F* Mb = M + (int64_t)b * stride;
+  const int64_t row_lo = k0 + (int64_t)c * R;
+  const int64_t row_hi = min(n, row_lo + R);
+  const int64_t nr = row_hi > row_lo ? row_hi - row_lo : 0;
+  extern __shared__ __align__(16) unsigned char cpanel_smem[];
+  F* T = reinterpret_cast<F*>(cpanel_smem);
+  __shared__ double s_cv;   // this CTA's pivot candidate (read by the cluster)
+  __shared__ int s_ci;
+  __shared__ F s_u[kPanel];
+  __shared__ F s_d[kPanel];
+  __shared__ int s_p;
+  auto at = [&](int64_t i, int cc) -> F& { return T[(i - row_lo) + (int64_t)cc * R]; };
+  for (int64_t l = t; l < nr * jb; l += kPanelThreads) {
+    const int64_t i = l % nr, cc = l / nr;
+    T[i + cc * R] = Mb[(row_lo + i) + (k0 + cc) * ld];
   }
+  __syncthreads();
+  double v = -1.0;
+  int vi = -1;
+  for (int64_t i = row_lo + t; i < row_hi; i += kPanelThreads) argmax_merge<F>(v, vi, (double)abs2(at(i, 0)), (int)i);
+  block_argmax<F>(v, vi);
+
+  for (int j = 0; j < jb; ++j) {
+    const int64_t d = k0 + j;
+    if (t == 0) {
+      s_cv = v;
+      s_ci = vi;
+    }
+    cluster.sync();  // every CTA's candidate is in place
+    if (t < 32) {
+      double bv = -1.0;
+      int bi = -1;
+      if (t < kPanelCluster) {
+        bv = *cluster.map_shared_rank(&s_cv, t);
+        bi = *cluster.map_shared_rank(&s_ci, t);
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        const double v2 = __shfl_down_sync(0xffffffffu, bv, off);
+        const int i2 = __shfl_down_sync(0xffffffffu, bi, off);
+        if (i2 >= 0 && (v2 > bv || (v2 == bv && (bi < 0 || i2 < bi)))) {
+          bv = v2;
+          bi = i2;
+        }
+      }
+      if (t == 0) s_p = bi;
+    }
+    __syncthreads();
+    const int p = s_p;
+    // the pivot row and the diagonal row from the CTAs that hold them
+    if (p >= 0 && t < jb) {
+      const int op = (int)((p - k0) / R), od = (int)((d - k0) / R);
+      F* Tp = cluster.map_shared_rank(T, op);
+      F* Td = cluster.map_shared_rank(T, od);
+      const int64_t lp = p - (k0 + (int64_t)op * R), ldd = d - (k0 + (int64_t)od * R);
+      s_u[t] = Tp[lp + (int64_t)t * R];
+      s_d[t] = Td[ldd + (int64_t)t * R];
+    }
+    cluster.sync();  // every CTA has read both rows before their owners overwrite them
+    if (p < 0) continue;  // cannot happen for jb <= rows (uniform across the cluster)
+    const F piv = s_u[j];
+    F inv;
+    if (abs2(piv) == 0) {
+      inv = num<F>::zero();
+      if (c == 0 && t == 0) atomicCAS(&w.zero_pivot[b], 0, (int)d + 1);
+    } else {
+      inv = recip(piv);
+    }
+    if (d >= row_lo && d < row_hi)
+      for (int cc = t; cc < jb; cc += kPanelThreads) at(d, cc) = s_u[cc];
+    if (p != d && p >= row_lo && p < row_hi)
+      for (int cc = t; cc < jb; cc += kPanelThreads) at(p, cc) = s_d[cc];
+    if (c == 0 && t == 0) ipiv[(int64_t)b * n + d] = p;
+    __syncthreads();
+    v = -1.0;
+    vi = -1;
+    const int64_t lo = max(row_lo, d + 1);
+    for (int64_t i = lo + t; i < row_hi; i += kPanelThreads) {
+      F l = at(i, j) * inv;
+      at(i, j) = l;
+      for (int cc = j + 1; cc < jb; ++cc) {
+        F x = at(i, cc) - l * s_u[cc];
+        at(i, cc) = x;
+        if (cc == j + 1) argmax_merge<F>(v, vi, (double)abs2(x), (int)i);
+      }
+    }
+    if (j + 1 < jb) block_argmax<F>(v, vi);
+    else __syncthreads();
+  }
+  for (int64_t l = t; l < nr * jb; l += kPanelThreads) {
+    const int64_t i = l % nr, cc = l / nr;
+    Mb[(row_lo + i) + (k0 + cc) * ld] = T[i + cc * R];
+  }
+  if (c == 0 && t == 0) panel_swap_summary(b, n, k0, jb, ipiv, w);
+  cluster.sync();  // no CTA leaves while another may still read its shared memory
 }
 
 constexpr int kSwapWarps = 8;
@@ -785,6 +908,32 @@ void lu_factor_batched(F* M, int64_t n, int64_t ld, int64_t stride, int nodes,
   FEAST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_c, panel_lu_kernel<F, true>, kPanelThreads,
                                                                cache_max));
   const int max_coop_c = occ_c * num_sms;
+  // the cluster variant: can a cluster of kPanelCluster CTAs with the largest
+  // panel slice be resident at all?
+  const size_t cl_max = sizeof(F) * (size_t)kPanelClusterRows * kPanel;
+  bool cluster_ok = cl_max <= 200 * 1024;
+  if (cluster_ok) {
+    FEAST_CUDA_TRY(cudaFuncSetAttribute(panel_lu_cluster_kernel<F>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    FEAST_CUDA_TRY(cudaFuncSetAttribute(panel_lu_cluster_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)cl_max));
+    cudaLaunchConfig_t q{};
+    cudaLaunchAttribute qa[1];
+    qa[0].id = cudaLaunchAttributeClusterDimension;
+    qa[0].val.clusterDim.x = kPanelCluster;
+    qa[0].val.clusterDim.y = 1;
+    qa[0].val.clusterDim.z = 1;
+    q.gridDim = dim3(kPanelCluster);
+    q.blockDim = dim3(kPanelThreads);
+    q.dynamicSmemBytes = cl_max;
+    q.attrs = qa;
+    q.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, panel_lu_cluster_kernel<F>, &q) != cudaSuccess) {
+      cudaGetLastError();
+      nclusters = 0;
+    }
+    cluster_ok = nclusters > 0;
+  }
   unsigned base = 0;
   // complex-FP32 factors with tensor-core scratch: two-level blocking, outer
   // blocks of kTcBlock columns whose trailing update runs on the tensor cores,
@@ -807,6 +956,25 @@ void lu_factor_batched(F* M, int64_t n, int64_t ld, int64_t stride, int nodes,
     const int64_t H = n - k1;
     int k1i = (int)k1;
     PanelWork wl = w;
+    // one cluster per node holding the whole panel in its shared memory
+    if (cluster_ok && cdiv(H, kPanelCluster) <= kPanelClusterRows) {
+      int64_t Rc = cdiv(H, kPanelCluster);
+      cudaLaunchConfig_t q{};
+      cudaLaunchAttribute qa[1];
+      qa[0].id = cudaLaunchAttributeClusterDimension;
+      qa[0].val.clusterDim.x = kPanelCluster;
+      qa[0].val.clusterDim.y = 1;
+      qa[0].val.clusterDim.z = 1;
+      q.gridDim = dim3((unsigned)(nodes * kPanelCluster));
+      q.blockDim = dim3(kPanelThreads);
+      q.dynamicSmemBytes = sizeof(F) * (size_t)Rc * kPanel;
+      q.stream = s;
+      q.attrs = qa;
+      q.numAttrs = 1;
+      FEAST_CUDA_TRY(cudaLaunchKernelEx(&q, panel_lu_cluster_kernel<F>, M, n, ld, stride, k1i, jb, Rc, ipiv, wl));
+      note_launch();
+      return;
+    }
     // rows of the panel in shared memory when every node's rows fit in
     // co-resident CTAs of at most kPanelCacheRows rows each
     int Pc = (int)std::min<int64_t>({cdiv(H, 64), (int64_t)(max_coop_c / nodes), (int64_t)w.pmax});
