@@ -52,7 +52,10 @@ enum { FEAST_PREC_F64 = 0,        /* complex FP64 LU and solves */
        FEAST_PREC_MIXED = 1,      /* complex FP32 LU and solves, FP64 iterative refinement; the
                                      GEMM updates of the LU and of the triangular solves on the
                                      bf16 tensor cores with FP32-exact operands (three-part bf16
-                                     split, six split products, FP32 accumulate) */
+                                     split, six split products, FP32 accumulate); the
+                                     Rayleigh-Ritz products and the reduced eigensolver's polish
+                                     in double-float arithmetic on the FP32 pipes (the polish's
+                                     diagonal in FP64) */
        FEAST_PREC_MIXED_SIMT = 2  /* as FEAST_PREC_MIXED with those GEMM updates on the FP32
                                      SIMT pipes */ };
 
