@@ -47,7 +47,7 @@ METRIC = "converged eigenpairs/sec at residual 1e-10; filter-apply TFLOP/s vs pe
 UNIT = "eigenpairs/s"
 WORKLOAD = dict(n=8192, m_in=200, edge_in=30, edge_out=60, width=1e-4, bulk=50.0,
                 lmin=-1.0, lmax=1.0, m0=300, n_c=8, tol=1e-10, variant="rfeast", s=3, seed=0,
-                rfeast_expand=1, response_stop=1, gen="torch_cpu")
+                rfeast_expand=1, response_stop=1, gen="torch_cpu", refine_switch=0.0)
 # the n = 500 plain FP64 FEAST workload (real symmetric, 40 of 500 eigenvalues in
 # [-1, 1], 5 within 1e-3 of each edge; n_c = 8, m0 = 60)
 CONFIG1 = dict(n=500, m0=60, n_c=8, tol=1e-10, lmin=-1.0, lmax=1.0, seed=0)
@@ -498,6 +498,7 @@ def run_ours(args, rank, world, dev):
     w["prec"] = args.prec
     w["variant"] = args.variant
     w["gen"] = args.gen
+    w["refine_switch"] = args.refine_switch
     fg.build_library()
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
@@ -510,7 +511,7 @@ def run_ours(args, rank, world, dev):
     if w["variant"] == "xfeast":
         rd.pop("rfeast_expand")
     opts = fg.feast_opts_default(variant=w["variant"], s=w["s"], prec=w["prec"], anorm=anorm, max_iter=30,
-                                 refine_gemm=args.refine_gemm, **rd)
+                                 refine_gemm=args.refine_gemm, refine_switch=w["refine_switch"], **rd)
 
     def solve(Adev):
         return fg.feast_interval_solve(ctx, Adev, w["lmin"], w["lmax"], w["m0"], w["n_c"], w["tol"], opts)
@@ -630,7 +631,7 @@ def run_ours(args, rank, world, dev):
             "config": {"workload": workload_name(w), "n": n, "m0": m0, "n_c": nc, "variant": w["variant"],
                        "s": w["s"], "prec": w["prec"], "tol": w["tol"],
                        "rfeast_expand": w["rfeast_expand"], "response_stop": w["response_stop"],
-                       "q_gaussian": w["gen"],
+                       "refine_switch": w["refine_switch"], "q_gaussian": w["gen"],
                        "l2": "inputs larger than L2 (A is %.2f GB, L2 129 MB)" % (h2d / 1e9),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "correct": bool(ok),
@@ -793,6 +794,9 @@ def main():
                     help="also run the largest single problem at this n (32768 = full size; 0: skip)")
     ap.add_argument("--gen", default=WORKLOAD["gen"], choices=["torch_cpu", "torch_cuda", "numpy"],
                     help="generator of the Gaussian whose QR gives Q")
+    ap.add_argument("--refine-switch", type=float, default=WORKLOAD["refine_switch"],
+                    help="mixed: skip the FP64 refinement of a filter while the previous residual is above this "
+                         "and still falling tenfold (0: always refine)")
     ap.add_argument("--cpu-full-n", type=int, default=2048,
                     help="n of the scaled workload the oracle solves in full (0: skip)")
     args = ap.parse_args()
