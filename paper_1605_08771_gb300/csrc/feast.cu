@@ -550,9 +550,11 @@ struct Solver {
   // k x k products of the two-phase eigensolver on the mixed path in
   // double-float: their operands are unitary, nearly unitary or the reduced
   // matrix itself, so the error (2^-44 of sum |a||b|) stays near 1e-13 ||A||,
-  // far below what the Ritz pairs need; FP64 otherwise
+  // far below what the Ritz pairs need.  FP64 otherwise, and for k below 512,
+  // where the double-float kernel's few output tiles leave most SMs idle and
+  // the split-K FP64 product is faster
   void mm_eig(int64_t k, const S* Am, int opA, const S* Bm, S* Cm) {
-    if (Ldf && Pdf && o.prec != FEAST_PREC_F64 && (double)k * k * k >= kDfMinWork && Cm != Am && Cm != Bm) {
+    if (Ldf && Pdf && o.prec != FEAST_PREC_F64 && k >= 512 && Cm != Am && Cm != Bm) {
       if (opA == OP_N) {
         mm_df(k, k, k, 1.0, Am, k, Bm, k, 0.0, Cm, k);
         return;
