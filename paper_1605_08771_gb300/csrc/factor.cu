@@ -558,8 +558,7 @@ __global__ void form_shifted_kernel(F* M, int64_t n, int64_t ld, int64_t stride,
 template <typename F, int TB>
 __global__ void __launch_bounds__(256)
 trsm_diag_kernel(const F* M, int64_t ld, int64_t stride, F* Y, int64_t n, int64_t m,
-                 int64_t ystride, int64_t r0, int bs, int mode, uint16_t* planes = nullptr, int64_t mpad = 0,
-                 int kdim = 0, int koff = 0) {
+                 int64_t ystride, int64_t r0, int bs, int mode) {
   constexpr int R = TB / 32;
   const int b = blockIdx.y;
   const F* Mb = M + (int64_t)b * stride;
@@ -623,29 +622,6 @@ trsm_diag_kernel(const F* M, int64_t ld, int64_t stride, F* Y, int64_t n, int64_
 #pragma unroll
   for (int r = 0; r < R; ++r)
     if (lane + 32 * r < bs) y[lane + 32 * r] = x[r];
-  // complex-FP32 solves on the tensor cores: the solved block also goes out
-  // as the six bf16 planes of the right operand of the block updates
-  // (K-major, K offset koff; zero past bs)
-  if constexpr (std::is_same<F, c64>::value) {
-    if (planes) {
-      const int64_t plane = mpad * kdim;
-      uint16_t* o = planes + (int64_t)b * 6 * plane + cidx * kdim + koff;
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int t = lane + 32 * r;
-        const F v = t < bs ? x[r] : num<F>::zero();
-        uint16_t a0, a1, a2, b0, b1, b2;
-        cg_split3(v.re, a0, a1, a2);
-        cg_split3(v.im, b0, b1, b2);
-        o[t] = a0;
-        o[plane + t] = a1;
-        o[2 * plane + t] = a2;
-        o[3 * plane + t] = b0;
-        o[4 * plane + t] = b1;
-        o[5 * plane + t] = b2;
-      }
-    }
-  }
 }
 
 // Triangular solve on a whole outer block (bs <= 256 rows) for the
