@@ -27,3 +27,23 @@ def test_config3_batch_ranges_and_determinism():
     assert ncs == {8, 16}
     assert min(ns) < 1500 and max(ns) > 3000   # the size range is exercised
     assert min(ms) < 50 and max(ms) > 120
+
+
+def test_disk_spectra_and_general_planted_matrices():
+    from workloads import planted_general, spectrum_disk
+    for real in (False, True):
+        c = 0.4 if real else 0.4 - 0.2j
+        lam = spectrum_disk(3, 60, 12, center=c, radius=2.0, gap=0.1, outer=5.0, real_pairs=real)
+        d = np.abs(lam - c)
+        assert lam.size == 60 and np.sum(d < 2.0) == 12
+        assert np.all((d < 2.0 * 0.9) | ((d > 2.0 * 1.1) & (d < 10.0)))
+        if real:
+            np.testing.assert_allclose(lam[30:], np.conj(lam[:30]), rtol=0, atol=0)
+        A, V = planted_general(lam, 5, cond=6.0, real=real)
+        assert A.dtype == (np.float64 if real else np.complex128)
+        # the planted pairs are eigenpairs and the eigenvector basis is as conditioned as stated
+        assert np.max(np.abs(A @ V - V * lam[None, :])) < 1e-11 * np.linalg.norm(A, 2)
+        if not real:
+            assert np.linalg.cond(V) <= 6.0 * (1 + 1e-9)
+        np.testing.assert_array_equal(spectrum_disk(3, 60, 12, center=c, radius=2.0, gap=0.1, outer=5.0,
+                                                    real_pairs=real), lam)

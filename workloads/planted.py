@@ -271,9 +271,10 @@ def planted_general(lam, seed, cond=10.0, real=False):
     """A general (non-normal) matrix with eigenvalues lam: A = V diag(lam)
     V^{-1} with V = Q1 diag(s) Q2, Q1 and Q2 Haar unitary and singular values
     s log-uniform in [1, cond] (eigenvector condition number <= cond).  real:
-    lam closed under conjugation and listed as (half, conj(half)); then V's
-    columns come in conjugate pairs and A is real.  Returns (A, V), Fortran
-    order."""
+    lam closed under conjugation and listed as (half, conj(half)); then V keeps
+    the first half of those columns and appends their conjugates, so A is real
+    (that V's conditioning is no longer bounded by cond).  Returns (A, V),
+    Fortran order."""
     lam = np.asarray(lam, dtype=np.complex128)
     n = lam.size
     rng = np.random.default_rng(np.random.SeedSequence([seed, 0x6E4]))
