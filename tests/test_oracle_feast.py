@@ -7,6 +7,7 @@ import os
 import numpy as np
 import pytest
 
+import closed_forms as CF
 import oracle as O
 from oracle.feast import inside, select_pairs
 from workloads import (make_problem, random_subspace, spectrum_config1, spectrum_config2, spectrum_paper,
@@ -315,3 +316,83 @@ def test_plain_feast_response_stop_on_two_sided_spectrum():
     rs = O.feast_solve(P.A, a, b, m0, 8, 1e-10, X0, anorm=P.anorm, factors=F, max_iter=12, response_stop=True)
     assert rs.status == 0 and rs.iterations <= 4
     _check_result(rs, P)
+
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_plain_feast_iterates_are_subspace_iteration_on_rho(cplx):
+    # Sect. I: FEAST is subspace iteration on rho(A); keeping every Ritz
+    # vector, round k works on span(rho(A)^k X0).  In the planted eigenbasis
+    # (closed_forms.plain_feast_rounds) every round's in-I Ritz values and
+    # maximum residual (the history) follow without the oracle's LU solves,
+    # orthonormalisation or Jacobi; the round count is the first round whose
+    # closed-form residual reaches tol.  The complex draw takes 14 rounds with
+    # one spurious in-I pair along the way, so the pin covers a long sequence.
+    lam, a, b = spectrum_config1(0)
+    m0, tol = 60, 1e-10
+    P = make_problem("c1", lam, a, b, m0, 8, seed=0, complex_=cplx)
+    X0 = random_subspace(P.n, m0, seed=1, complex_=cplx)
+    F = O.factor_shifts(P.A, a, b, 8)
+    rho = O.rational_filter(P.lam, F.z, F.w)
+    full = O.feast_solve(P.A, a, b, m0, 8, tol, X0, anorm=P.anorm, factors=F)
+    _check_result(full, P)
+    closed = CF.plain_feast_rounds(P.lam, P.Q.conj().T @ X0, rho, P.anorm, a, b, full.iterations)
+    # the round count and the residual history above tol
+    assert [k for k, (_, r) in enumerate(closed, 1) if r <= tol][:1] == [full.iterations]
+    for h, (_, r) in zip(full.history[:-1], closed[:-1]):
+        assert abs(h - r) <= 1e-6 * r
+    # the Ritz values inside I of the first rounds (they move by ~1e-3 ||A||
+    # from round to round)
+    for k in (1, 2, 3):
+        r = O.feast_solve(P.A, a, b, m0, 8, tol, X0, anorm=P.anorm, factors=F, max_iter=k)
+        assert r.lam.size == closed[k - 1][0].size
+        np.testing.assert_allclose(r.lam, closed[k - 1][0], rtol=0, atol=1e-10 * P.anorm)
+
+
+ROUND1_CASES = [(120, 10, 3.0, 14, 2, 1), (120, 10, 3.0, 14, 3, 1), (200, 12, 5.0, 18, 3, 2)]
+
+
+@pytest.mark.parametrize("n,m_in,bulk,m0,s,seed", ROUND1_CASES)
+@pytest.mark.parametrize("cplx", [False, True])
+def test_xfeast_first_round_is_rayleigh_ritz_on_the_krylov_window(n, m_in, bulk, m0, s, seed, cplx):
+    # Sect. II-A: the first XFEAST round applies Rayleigh-Ritz to the window
+    # [X0, rho(A) X0, ..., rho(A)^{s-1} X0] (s m0 < n here) and selects m0
+    # pairs; the selected in-I Ritz values follow in closed form
+    # (closed_forms.xfeast_first_round).  The window's smallest singular
+    # value is ~1e-7 of its largest for s = 3, hence the 1e-8 ||A|| bound.
+    lam, a, b = spectrum_uniform(n, m_in, seed=seed, bulk=bulk)
+    P = make_problem("x1", lam, a, b, m0, 8, seed=seed, complex_=cplx)
+    X0 = random_subspace(n, m0, seed=seed + 5, complex_=cplx)
+    F = O.factor_shifts(P.A, a, b, 8)
+    rho = O.rational_filter(P.lam, F.z, F.w)
+    mu, rmax = CF.xfeast_first_round(P.lam, P.Q.conj().T @ X0, rho, P.anorm, a, b, m0, s)
+    r = O.feast_solve(P.A, a, b, m0, 8, 1e-10, X0, variant=O.XFEAST, s=s, anorm=P.anorm, factors=F, max_iter=1)
+    assert r.rr_dims == [s * m0]
+    assert r.lam.size == mu.size
+    np.testing.assert_allclose(r.lam, mu, rtol=0, atol=1e-8 * P.anorm)
+    assert abs(r.history[0] - rmax) <= 1e-6 * rmax
+
+
+@pytest.mark.parametrize("n,m_in,bulk,m0,seed", [(120, 10, 3.0, 14, 1), (200, 12, 5.0, 18, 2)])
+@pytest.mark.parametrize("kw", [{}, {"expand": O.EXPAND_UNCONVERGED}])
+@pytest.mark.parametrize("cplx", [False, True])
+def test_rfeast_first_round_is_rayleigh_ritz_on_y_and_ay(n, m_in, bulk, m0, seed, kw, cplx):
+    # Sect. II-B with s = 2: the first pass works on Y = rho(A) X0 and fixes
+    # the expected count m; every pair is selected, so R = A X - X Lambda
+    # adds A Y and the second pass works on span([Y, A Y]).  No pair has
+    # converged after the first pass, so the "unconverged" reading appends
+    # the same R (closed_forms.rfeast_first_round_s2).
+    lam, a, b = spectrum_uniform(n, m_in, seed=seed, bulk=bulk)
+    P = make_problem("r1", lam, a, b, m0, 8, seed=seed, complex_=cplx)
+    X0 = random_subspace(n, m0, seed=seed + 5, complex_=cplx)
+    F = O.factor_shifts(P.A, a, b, 8)
+    rho = O.rational_filter(P.lam, F.z, F.w)
+    m_exp, mu, rmax, r1min = CF.rfeast_first_round_s2(P.lam, P.Q.conj().T @ X0, rho, P.anorm, a, b, m0)
+    assert r1min > 1e-10
+    r = O.feast_solve(P.A, a, b, m0, 8, 1e-10, X0, variant=O.RFEAST, s=2, anorm=P.anorm, factors=F, max_iter=1,
+                      **kw)
+    assert r.rr_dims == [m0, 2 * m0]
+    assert r.m_expected == m_exp
+    assert r.lam.size == mu.size
+    np.testing.assert_allclose(r.lam, mu, rtol=0, atol=1e-10 * P.anorm)
+    assert abs(r.history[0] - rmax) <= 1e-6 * rmax
