@@ -8,6 +8,7 @@ import os
 import numpy as np
 import pytest
 
+import closed_forms as CF
 import oracle as O
 import paper_1605_08771_gb300 as fg
 from gpu_common import cuda, ctx, host  # noqa: F401
@@ -252,6 +253,65 @@ def test_full_span_expansion_converges_in_one_round(ctx, vname, s, reading, prec
     assert out["evals"].size == P.inside.size
     np.testing.assert_allclose(out["evals"], P.inside, atol=1e-12 * P.anorm)
     check_against_planted(out, P)
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_plain_feast_rounds_follow_subspace_iteration(ctx, cplx):
+    # plain FEAST on the n = 500 workload (FP64), round by round against
+    # subspace iteration on rho(A) in the planted eigenbasis (Sect. I): the
+    # round count, the residual history (stats) and, stopped after k rounds
+    # (max_iter = k), that round's in-I Ritz values
+    lam, a, b = spectrum_config1(0)
+    m0, tol = 60, 1e-10
+    P = make_problem("c1", lam, a, b, m0, 8, seed=0, complex_=cplx)
+    X0 = random_subspace(P.n, m0, seed=1, complex_=cplx)
+    z, w = O.contour_nodes(a, b, 8)
+    rho = O.rational_filter(P.lam, z, w)
+    full = fg.feast_interval_solve(ctx, cuda(P.A), a, b, m0, 8, tol, fg.feast_opts_default(prec="f64", anorm=P.anorm),
+                                   x0=cuda(X0))
+    assert full["status"] == 0
+    K = full["iterations"]
+    closed = CF.plain_feast_rounds(P.lam, P.Q.conj().T @ X0, rho, P.anorm, a, b, K)
+    assert [k for k, (_, r) in enumerate(closed, 1) if r <= tol][:1] == [K]
+    hist = list(full["stats"].history)[:K]
+    for h, (_, r) in zip(hist[:-1], closed[:-1]):
+        assert abs(h - r) <= 1e-5 * r
+    for k in (1, 2, 3):
+        out = fg.feast_interval_solve(ctx, cuda(P.A), a, b, m0, 8, tol,
+                                      fg.feast_opts_default(prec="f64", anorm=P.anorm, max_iter=k), x0=cuda(X0))
+        assert out["status"] == fg.FEAST_WARN_MAXITER and out["iterations"] == k
+        assert out["evals"].size == closed[k - 1][0].size
+        np.testing.assert_allclose(out["evals"], closed[k - 1][0], rtol=0, atol=1e-10 * P.anorm)
+
+
+@pytest.mark.parametrize("vname,s", [("xfeast", 2), ("xfeast", 3), ("rfeast", 2)])
+@pytest.mark.parametrize("cplx", [False, True])
+def test_first_expanded_round_closed_form(ctx, vname, s, cplx):
+    # the first XFEAST round (Rayleigh-Ritz on [X0, rho X0, ..., rho^{s-1}
+    # X0], then the m0-pair selection) and the first RFEAST round with s = 2
+    # (span[Y, A Y], Y = rho(A) X0, the paper's expansion), s m0 < n, FP64,
+    # against their closed forms in the planted eigenbasis
+    n, m0 = 120, 14
+    lam, a, b = spectrum_uniform(n, 10, seed=1, bulk=3.0)
+    P = make_problem("x1", lam, a, b, m0, 8, seed=1, complex_=cplx)
+    X0 = random_subspace(n, m0, seed=6, complex_=cplx)
+    z, w = O.contour_nodes(a, b, 8)
+    rho = O.rational_filter(P.lam, z, w)
+    C0 = P.Q.conj().T @ X0
+    out = fg.feast_interval_solve(ctx, cuda(P.A), a, b, m0, 8, 1e-10,
+                                  fg.feast_opts_default(variant=vname, s=s, prec="f64", anorm=P.anorm, max_iter=1),
+                                  x0=cuda(X0))
+    assert out["status"] == fg.FEAST_WARN_MAXITER
+    if vname == "xfeast":
+        mu, rmax = CF.xfeast_first_round(P.lam, C0, rho, P.anorm, a, b, m0, s)
+        atol = 1e-8 * P.anorm       # the s = 3 window's condition number is ~1e7
+    else:
+        m_exp, mu, rmax, _ = CF.rfeast_first_round_s2(P.lam, C0, rho, P.anorm, a, b, m0)
+        assert out["stats"].m_expected == m_exp
+        atol = 1e-10 * P.anorm
+    assert out["evals"].size == mu.size
+    np.testing.assert_allclose(out["evals"], mu, rtol=0, atol=atol)
+    assert abs(out["stats"].history[0] - rmax) <= 1e-5 * rmax
 
 
 @pytest.mark.parametrize("n", [2048, 4096])
