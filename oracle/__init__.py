@@ -22,14 +22,14 @@ closed forms, brute force or independent library routines.  Plain FEAST's
 iterates are pinned round by round: every round's in-I Ritz values, its
 residual history and its round count follow from subspace iteration on
 rho(A) computed in the planted eigenbasis.  The XFEAST and RFEAST drivers are
-pinned by the end result on planted spectra, by their first round in closed
-form (Rayleigh-Ritz on the Krylov window of rho(A), and on [Y, A Y] for
-RFEAST with s = 2), by one-round convergence where the mathematics fixes it
-(an invariant start; an expanded subspace that spans the whole space,
-s m0 = n), and by the Rayleigh-Ritz dimensions the literal RFEAST expansion
-must produce.  Their later rounds (which pairs are selected at each round of
-a multi-round solve, the residual histories after round 1) have no
-independent pin: "parity unpinned" there.
+pinned by the end result on planted spectra, by their first rounds in closed
+form (Rayleigh-Ritz on the Krylov windows of rho(A) of XFEAST's rounds 1 and
+2, and on [Y, A Y] for RFEAST's round 1 with s = 2), by one-round
+convergence where the mathematics fixes it (an invariant start; an expanded
+subspace that spans the whole space, s m0 = n), and by the Rayleigh-Ritz
+dimensions the literal RFEAST expansion must produce.  Their later rounds
+(XFEAST from round 3, RFEAST from round 2: which pairs are selected, the
+residual histories) have no independent pin: "parity unpinned" there.
 """
 from .quadrature import gauss_legendre, contour_nodes, rational_filter, circle_nodes, circle_filter  # noqa: F401
 from .dense import (lu_factor, lu_solve, lu_solve_adjoint, lu_unpack,  # noqa: F401

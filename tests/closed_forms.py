@@ -31,18 +31,30 @@ def plain_feast_rounds(lam, C0, rho, anorm, a, b, rounds):
     return out
 
 
-def xfeast_first_round(lam, C0, rho, anorm, a, b, m0, s):
-    """First XFEAST round (Sect. II-A): Rayleigh-Ritz on the window
-    [C0, D C0, ..., D^{s-1} C0], D = diag(rho), then the m0-pair selection.
-    Returns the selected Ritz values in (a, b) (ascending) and their maximum
-    residual."""
-    blocks = [C0]
+def xfeast_round(lam, C0, rho, anorm, a, b, m0, s, k=1):
+    """Round k = 1 or 2 of XFEAST (Sect. II-A): Rayleigh-Ritz on the Krylov
+    window span[D^{k-1} C0, ..., D^{k+s-2} C0], D = diag(rho), then the
+    m0-pair selection.  Round 1's window is [X0, rho X0, ..., rho^{s-1} X0]
+    itself.  Round 2's is [rho X0, ..., rho^{s-1} X0, rho X_sel] with X_sel
+    in round 1's window W, so it lies in rho(A) W, and equals it when it has
+    full dimension s m0 (X_sel has components along rho^{s-1} X0 for a
+    generic X0).  From round 3 on the window holds selections of two
+    different rounds and no such closed form exists.  Returns the selected
+    Ritz values in (a, b) (ascending) and their maximum residual."""
+    if k not in (1, 2):
+        raise ValueError(k)
+    blocks = [C0 if k == 1 else rho[:, None] * C0]
     for _ in range(1, s):
         blocks.append(rho[:, None] * blocks[-1])
     mu, res = ritz_in_eigencoordinates(lam, np.hstack(blocks), anorm)
     sel = select_pairs(mu, res, a, b, m0)
     ins = sel[inside(mu[sel], a, b)]
     return np.sort(mu[ins]), float(res[ins].max())
+
+
+def xfeast_first_round(lam, C0, rho, anorm, a, b, m0, s):
+    """The first XFEAST round: xfeast_round with k = 1."""
+    return xfeast_round(lam, C0, rho, anorm, a, b, m0, s, 1)
 
 
 def rfeast_first_round_s2(lam, C0, rho, anorm, a, b, m0):

@@ -373,6 +373,35 @@ def test_xfeast_first_round_is_rayleigh_ritz_on_the_krylov_window(n, m_in, bulk,
     assert abs(r.history[0] - rmax) <= 1e-6 * rmax
 
 
+@pytest.mark.parametrize("n,m_in,bulk,m0,s,seed", ROUND1_CASES + [(200, 12, 5.0, 18, 2, 2)])
+@pytest.mark.parametrize("cplx", [False, True])
+def test_xfeast_second_round_is_rayleigh_ritz_on_rho_times_the_first_window(n, m_in, bulk, m0, s, seed, cplx):
+    # Sect. II-A: round 2 filters round 1's selected Ritz vectors X_sel and
+    # drops X0 from the window, [rho X0, ..., rho^{s-1} X0, rho X_sel]; X_sel
+    # lies in the first window W, so the second window is rho(A) W =
+    # span[rho X0, ..., rho^s X0] (full dimension for a generic X0).  Both
+    # sides build that space from a Krylov power basis whose smallest
+    # singular value is ~1e-7 (s = 2) or ~1e-12 (s = 3) of its largest, so
+    # the bounds are 1e-9 and 1e-5 ||A||; the in-I Ritz values move by more
+    # than 1e-2 ||A|| from round 1 to round 2.
+    lam, a, b = spectrum_uniform(n, m_in, seed=seed, bulk=bulk)
+    P = make_problem("x2", lam, a, b, m0, 8, seed=seed, complex_=cplx)
+    X0 = random_subspace(n, m0, seed=seed + 5, complex_=cplx)
+    F = O.factor_shifts(P.A, a, b, 8)
+    rho = O.rational_filter(P.lam, F.z, F.w)
+    C0 = P.Q.conj().T @ X0
+    mu1, _ = CF.xfeast_round(P.lam, C0, rho, P.anorm, a, b, m0, s, 1)
+    mu, rmax = CF.xfeast_round(P.lam, C0, rho, P.anorm, a, b, m0, s, 2)
+    r = O.feast_solve(P.A, a, b, m0, 8, 1e-10, X0, variant=O.XFEAST, s=s, anorm=P.anorm, factors=F, max_iter=2)
+    assert r.status == 1 and r.iterations == 2 and r.rr_dims == [s * m0, s * m0]
+    assert r.lam.size == mu.size
+    atol = (1e-9 if s == 2 else 1e-5) * P.anorm
+    np.testing.assert_allclose(r.lam, mu, rtol=0, atol=atol)
+    assert abs(r.history[1] - rmax) <= 1e-4 * rmax
+    if mu1.size == mu.size:
+        assert np.abs(mu1 - mu).max() > 1e3 * atol
+
+
 @pytest.mark.parametrize("n,m_in,bulk,m0,seed", [(120, 10, 3.0, 14, 1), (200, 12, 5.0, 18, 2)])
 @pytest.mark.parametrize("kw", [{}, {"expand": O.EXPAND_UNCONVERGED}])
 @pytest.mark.parametrize("cplx", [False, True])
