@@ -314,6 +314,30 @@ def test_first_expanded_round_closed_form(ctx, vname, s, cplx):
     assert abs(out["stats"].history[0] - rmax) <= 1e-5 * rmax
 
 
+@pytest.mark.parametrize("s", [2, 3])
+@pytest.mark.parametrize("cplx", [False, True])
+def test_second_xfeast_round_closed_form(ctx, s, cplx):
+    # round 2 of XFEAST works on rho(A) times the first window,
+    # span[rho X0, ..., rho^s X0] (the selected vectors it filters lie in
+    # the first window), FP64, against the closed form in the planted
+    # eigenbasis; the power basis's condition (~1e7 for s = 2, ~1e12 for
+    # s = 3) sets the bounds
+    n, m0 = 120, 14
+    lam, a, b = spectrum_uniform(n, 10, seed=1, bulk=3.0)
+    P = make_problem("x2", lam, a, b, m0, 8, seed=1, complex_=cplx)
+    X0 = random_subspace(n, m0, seed=6, complex_=cplx)
+    z, w = O.contour_nodes(a, b, 8)
+    rho = O.rational_filter(P.lam, z, w)
+    mu, rmax = CF.xfeast_round(P.lam, P.Q.conj().T @ X0, rho, P.anorm, a, b, m0, s, 2)
+    out = fg.feast_interval_solve(ctx, cuda(P.A), a, b, m0, 8, 1e-10,
+                                  fg.feast_opts_default(variant="xfeast", s=s, prec="f64", anorm=P.anorm, max_iter=2),
+                                  x0=cuda(X0))
+    assert out["status"] == fg.FEAST_WARN_MAXITER and out["iterations"] == 2
+    assert out["evals"].size == mu.size
+    np.testing.assert_allclose(out["evals"], mu, rtol=0, atol=(1e-9 if s == 2 else 1e-5) * P.anorm)
+    assert abs(out["stats"].history[1] - rmax) <= 1e-4 * rmax
+
+
 @pytest.mark.parametrize("n", [2048, 4096])
 def test_full_size_paths_mixed_rfeast_edge_clusters(ctx, n):
     # the mixed path at sizes where the GEMM tile dispatch, the split-K
