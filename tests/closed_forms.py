@@ -1,8 +1,10 @@
 """Closed forms of FEAST iterates on planted spectra A = Q diag(lam) Q^H,
 computed in the planted eigenbasis with LAPACK (SVD, eigh) and the rational
 filter's values rho(lam): no linear solve, orthonormalisation or Jacobi of
-the oracle or of the CUDA path is involved.  Shared by the oracle pins and
-the CUDA parity tests."""
+the oracle or of the CUDA path is involved.  The pair selection (Sect.
+II-A) is the oracle's select_pairs, itself pinned by hand-worked cases in
+test_oracle_feast.py.  Shared by the oracle pins and the CUDA parity
+tests."""
 import numpy as np
 
 from oracle.feast import inside, select_pairs
