@@ -108,3 +108,22 @@ def test_filter_above_half_exactly_inside_the_circle(n_c):
     c /= np.linalg.norm(c)
     lam_out = rng.choice(outside, 40)
     assert np.sum(np.abs(c) ** 2 * rational_filter(lam_out, z, w)) < 0.5
+
+
+@pytest.mark.parametrize("m", [50, 100, 200])
+def test_rate_of_order_ten_thousand_at_n_c_8_and_m0_one_and_a_half_m(m):
+    # Sect. I: FEAST's rate is rho(lambda_i) / rho(lambda_{m0+1}) (the
+    # (m0+1)-th largest filter value), and with n_c = 8 and m0 ~ 1.5 m a rate
+    # of 10^4 is common.  For a spectrum of uniform density across I and far
+    # beyond, the worst in-I eigenvalue (half a spacing from an edge, rho ~
+    # 1/2) gets 3-4e3 and the median one ~5e3: order 10^4, and far from what
+    # another rule gives (n_c = 2: 6-11; n_c = 16: ~3e7)
+    z, w = contour_nodes(-1.0, 1.0, 8)
+    h = 2.0 / m
+    lam = np.arange(-50.0 + h / 2, 50.0, h)
+    rho = np.abs(rational_filter(lam, z, w))
+    ins = (lam > -1.0) & (lam < 1.0)
+    assert ins.sum() == m
+    nxt = np.sort(rho)[::-1][int(1.5 * m)]
+    assert 1e3 <= rho[ins].min() / nxt <= 1e5
+    assert 1e3 <= np.median(rho[ins]) / nxt <= 1e5
