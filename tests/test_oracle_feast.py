@@ -119,6 +119,41 @@ def test_feast_rate_law_config1():
 
 
 @pytest.mark.slow
+@pytest.mark.parametrize("s", [2, 3])
+def test_per_iteration_comparison_dense_and_sparse_spectra(s):
+    # Sect. III, at equal subspace size k = s * 51 (FEAST with m0 = k;
+    # XFEAST and RFEAST with m0 = 51 expanded s times): on the "Dense"
+    # spectrum (n_c = 8) XFEAST and RFEAST outperform FEAST per subspace
+    # iteration; on the "Sparse" one (n_c = 3) they do not, but their total
+    # work (right-hand sides solved, n_c * m0 per filter) stays comparable
+    # (here within a factor of 2)
+    g = json.load(open(GOLDEN))["fig1_fig2_matrices"]
+    m0 = g["m0_expanded_variants"]
+    k = s * m0
+    its, rhs = {}, {}
+    for kind, n_c in (("dense", g["n_c_dense"]), ("sparse", g["n_c_sparse"])):
+        lam, a, b = spectrum_paper(kind, seed=0, n=g["n"], m_in=g["inside"])
+        P = make_problem(kind, lam, a, b, k, n_c, seed=0)
+        F = O.factor_shifts(P.A, a, b, n_c)
+        X0 = random_subspace(P.n, k, seed=1)
+        for v, mm in ((O.PLAIN, k), (O.XFEAST, m0), (O.RFEAST, m0)):
+            r = O.feast_solve(P.A, a, b, mm, n_c, 1e-10, X0[:, :mm], variant=v, s=s, anorm=P.anorm, factors=F,
+                              max_iter=100)
+            # (the span is not checked here: the 0.01 gap to the outside
+            # eigenvalues lets a 1e-10 residual leave angles near 1e-8)
+            assert r.status == 0 and r.lam.size == P.inside.size and r.res.max() <= 1e-10
+            np.testing.assert_allclose(r.lam, P.inside, rtol=1e-10, atol=1e-12 * P.anorm)
+            its[kind, v] = r.iterations
+            rhs[kind, v] = r.filters * n_c * mm
+    assert its["dense", O.XFEAST] < its["dense", O.PLAIN]
+    assert its["dense", O.RFEAST] < its["dense", O.PLAIN]
+    assert its["sparse", O.XFEAST] >= its["sparse", O.PLAIN]
+    assert its["sparse", O.RFEAST] >= its["sparse", O.PLAIN]
+    for v in (O.XFEAST, O.RFEAST):
+        assert 0.5 <= rhs["sparse", v] / rhs["sparse", O.PLAIN] <= 2.0
+
+
+@pytest.mark.slow
 def test_expanded_variants_beat_feast_on_dense_spectrum():
     # Sect. III: on the "Dense" n = 545 matrix XFEAST and RFEAST (m0 = 51) need
     # fewer linear right-hand sides than FEAST to reach the same residual.

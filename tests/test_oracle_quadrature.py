@@ -1,10 +1,15 @@
 """Pins of the oracle's quadrature (Eqs. 2-3) against closed forms and an
 independent Gauss-Legendre implementation."""
+import json
+import os
+
 import numpy as np
 import pytest
 
 from oracle import contour_nodes, gauss_legendre, rational_filter
 import oracle.quadrature as quad
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_setups.json")
 
 
 @pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 13, 16, 24, 32])
@@ -118,12 +123,14 @@ def test_rate_of_order_ten_thousand_at_n_c_8_and_m0_one_and_a_half_m(m):
     # beyond, the worst in-I eigenvalue (half a spacing from an edge, rho ~
     # 1/2) gets 3-4e3 and the median one ~5e3: order 10^4, and far from what
     # another rule gives (n_c = 2: 6-11; n_c = 16: ~3e7)
-    z, w = contour_nodes(-1.0, 1.0, 8)
+    g = json.load(open(GOLDEN))["typical_rate"]
+    z, w = contour_nodes(-1.0, 1.0, g["n_c"])
     h = 2.0 / m
     lam = np.arange(-50.0 + h / 2, 50.0, h)
     rho = np.abs(rational_filter(lam, z, w))
     ins = (lam > -1.0) & (lam < 1.0)
     assert ins.sum() == m
-    nxt = np.sort(rho)[::-1][int(1.5 * m)]
-    assert 1e3 <= rho[ins].min() / nxt <= 1e5
-    assert 1e3 <= np.median(rho[ins]) / nxt <= 1e5
+    nxt = np.sort(rho)[::-1][int(g["m0_over_m"] * m)]
+    lo, hi = g["rate_order"] / 10, g["rate_order"] * 10
+    assert lo <= rho[ins].min() / nxt <= hi
+    assert lo <= np.median(rho[ins]) / nxt <= hi
