@@ -1,5 +1,6 @@
-"""The batched workload's generator: 64 seeded problems within the stated
-ranges (n, in-interval count, edge clusters, m0, n_c)."""
+"""The input generators: the batched workload's 64 seeded problems within the
+stated ranges (n, in-interval count, edge clusters, m0, n_c), the disk
+spectra and planted general matrices, the dense-edge stand-in spectrum."""
 import numpy as np
 
 from workloads import spectrum_config3
@@ -47,3 +48,15 @@ def test_disk_spectra_and_general_planted_matrices():
             assert np.linalg.cond(V) <= 6.0 * (1 + 1e-9)
         np.testing.assert_array_equal(spectrum_disk(3, 60, 12, center=c, radius=2.0, gap=0.1, outer=5.0,
                                                     real_pairs=real), lam)
+
+
+def test_dense_edge_spectrum():
+    from workloads import spectrum_dense_edge
+    lam, a, b = spectrum_dense_edge(0)
+    assert lam.size == 600 and np.all(np.diff(lam) > 0)
+    assert np.sum((lam > a) & (lam < b)) == 43
+    # the group straddles the upper edge: 15 inside and 15 outside within 0.05
+    near = lam[np.abs(lam - b) < 0.05]
+    assert np.sum(near < b) == 15 and np.sum(near > b) == 15
+    assert np.min(np.abs(lam - b)) > 1e-4
+    np.testing.assert_array_equal(lam, spectrum_dense_edge(0)[0])

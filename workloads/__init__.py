@@ -18,6 +18,7 @@ from .planted import (  # noqa: F401
     spectrum_config5,
     spectrum_disk,
     spectrum_paper,
+    spectrum_dense_edge,
     spectrum_uniform,
     make_problem,
 )

@@ -195,6 +195,25 @@ def spectrum_paper(kind, seed=0, n=545, m_in=50):
     return np.sort(np.concatenate([inside, outside])), -1.0, 1.0
 
 
+def spectrum_dense_edge(seed=0, n=600, m_in=43, group=30, width=0.1, bulk=20.0):
+    """A stand-in for the second interval of the paper's Fig. 4 (43 pairs,
+    its upper edge through the middle of a dense group of eigenvalues; the
+    Hamiltonian itself is not available): I = [-1, 1] holds m_in eigenvalues,
+    group of them equally spaced across (1 - width/2, 1 + width/2), half
+    inside and half outside, the other inside ones uniform in
+    (-0.95, 1 - width/2), the rest uniform in [-bulk, -1.1] and [1.2, bulk]."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 7]))
+    g_in, g_out = group // 2, group - group // 2
+    half = width / 2
+    grp_in = 1.0 - half + (np.arange(g_in) + 0.5) * half / g_in
+    grp_out = 1.0 + (np.arange(g_out) + 0.5) * half / g_out
+    rest_in = rng.uniform(-0.95, 1.0 - half, m_in - g_in)
+    n_out = n - m_in - g_out
+    lo = rng.uniform(-bulk, -1.1, n_out // 2)
+    hi = rng.uniform(1.2, bulk, n_out - n_out // 2)
+    return np.sort(np.concatenate([rest_in, grp_in, grp_out, lo, hi])), -1.0, 1.0
+
+
 def spectrum_uniform(n, m_in, seed=0, lmin=-1.0, lmax=1.0, bulk=10.0):
     """Uniform spectrum with exactly m_in eigenvalues in (lmin, lmax)."""
     rng = np.random.default_rng(seed)
