@@ -27,9 +27,11 @@ form (Rayleigh-Ritz on the Krylov windows of rho(A) of XFEAST's rounds 1 and
 2, and on [Y, A Y] for RFEAST's round 1 with s = 2), by one-round
 convergence where the mathematics fixes it (an invariant start; an expanded
 subspace that spans the whole space, s m0 = n), and by the Rayleigh-Ritz
-dimensions the literal RFEAST expansion must produce.  Their later rounds
-(XFEAST from round 3, RFEAST from round 2: which pairs are selected, the
-residual histories) have no independent pin: "parity unpinned" there.
+dimensions the literal RFEAST expansion must produce; with s = 1 both reduce
+to subspace iteration on rho(A) and are pinned at every round.  Their later
+rounds with s >= 2 (XFEAST from round 3, RFEAST from round 2: which pairs
+are selected, the residual histories) have no independent pin: "parity
+unpinned" there.
 """
 from .quadrature import gauss_legendre, contour_nodes, rational_filter, circle_nodes, circle_filter  # noqa: F401
 from .dense import (lu_factor, lu_solve, lu_solve_adjoint, lu_unpack,  # noqa: F401

@@ -410,6 +410,37 @@ def test_plain_feast_iterates_are_subspace_iteration_on_rho(cplx):
         np.testing.assert_allclose(r.lam, closed[k - 1][0], rtol=0, atol=1e-10 * P.anorm)
 
 
+@pytest.mark.parametrize("cplx", [False, True])
+def test_expanded_drivers_with_one_block_are_subspace_iteration(cplx):
+    # special cases that reduce to plain subspace iteration on rho(A), at
+    # every round: RFEAST with s = 1 appends nothing, so each round filters
+    # the m0 selected (all) Ritz vectors, exactly FEAST's rounds; XFEAST with
+    # s = 1 starts from the unfiltered window [X0] (Rayleigh-Ritz on span X0)
+    # and then filters its selected block each round, so its round k + 1 is
+    # FEAST's round k.  Both multi-round drivers are thereby pinned round by
+    # round against closed_forms.plain_feast_rounds.
+    lam, a, b = spectrum_config1(0)
+    m0, tol = 60, 1e-10
+    P = make_problem("c1", lam, a, b, m0, 8, seed=0, complex_=cplx)
+    X0 = random_subspace(P.n, m0, seed=1, complex_=cplx)
+    F = O.factor_shifts(P.A, a, b, 8)
+    rho = O.rational_filter(P.lam, F.z, F.w)
+    C0 = P.Q.conj().T @ X0
+    closed = CF.plain_feast_rounds(P.lam, C0, rho, P.anorm, a, b, 30)
+    K = [k for k, (_, r) in enumerate(closed, 1) if r <= tol][0]
+    hist = [r for _, r in closed[:K - 1]]
+    rr = O.feast_solve(P.A, a, b, m0, 8, tol, X0, variant=O.RFEAST, s=1, anorm=P.anorm, factors=F)
+    _check_result(rr, P)
+    assert rr.iterations == K and rr.filters == K and rr.rr_dims == [m0] * K
+    np.testing.assert_allclose(rr.history[:K - 1], hist, rtol=1e-6)
+    rx = O.feast_solve(P.A, a, b, m0, 8, tol, X0, variant=O.XFEAST, s=1, anorm=P.anorm, factors=F)
+    _check_result(rx, P)
+    assert rx.iterations == K + 1 and rx.filters == K
+    mu0, res0 = CF.ritz_in_eigencoordinates(P.lam, C0, P.anorm)
+    assert abs(rx.history[0] - res0[inside(mu0, a, b)].max()) <= 1e-6 * rx.history[0]
+    np.testing.assert_allclose(rx.history[1:K], hist, rtol=1e-6)
+
+
 ROUND1_CASES = [(120, 10, 3.0, 14, 2, 1), (120, 10, 3.0, 14, 3, 1), (200, 12, 5.0, 18, 3, 2)]
 
 
