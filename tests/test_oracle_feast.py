@@ -358,6 +358,33 @@ def test_generalized_feast_on_planted_pencil(cplx):
     assert np.linalg.norm(Xi - r.X @ C) < 1e-8
 
 
+@pytest.mark.parametrize("cplx", [False, True])
+def test_generalized_feast_iterates_are_subspace_iteration_on_rho(cplx):
+    # for A x = lambda B x with B-orthonormal eigenvectors V (planted), the
+    # filter sum_j w_j (z_j B - A)^{-1} B X is V diag(rho(lam)) V^{-1} X and
+    # V^{-1} = V^H B, so in the coordinates C = V^H B X the generalised FEAST
+    # is the same subspace iteration as the standard one (B-orthonormal bases
+    # are orthonormal coordinates; Rayleigh-Ritz of (A, B) on span(V C) is
+    # that of diag(lam) on span C): every round's in-I Ritz values follow
+    # from closed_forms.plain_feast_rounds with C0 = V^H B X0
+    from workloads.planted import planted_pencil
+    lam, a, b = spectrum_uniform(120, 10, seed=6, bulk=3.0)
+    A, B, V = planted_pencil(lam, 6, complex_=cplx)
+    m0 = 14
+    X0 = random_subspace(120, m0, seed=2, complex_=cplx)
+    z, w = O.contour_nodes(a, b, 8)
+    rho = O.rational_filter(lam, z, w)
+    scale = np.abs(lam).max()
+    full = O.feast.feast_solve_generalized(A, B, a, b, m0, 8, 1e-10, X0)
+    assert full.status == 0 and full.iterations >= 4
+    closed = CF.plain_feast_rounds(lam, V.conj().T @ (B @ X0), rho, scale, a, b, 4)
+    for k in range(1, 5):
+        r = O.feast.feast_solve_generalized(A, B, a, b, m0, 8, 1e-10, X0, max_iter=k)
+        assert r.lam.size == closed[k - 1][0].size
+        np.testing.assert_allclose(np.sort(r.lam), closed[k - 1][0], rtol=0, atol=1e-11 * scale)
+    assert closed[0][0].size != closed[-1][0].size   # the iterates do move
+
+
 def test_plain_feast_response_stop_on_two_sided_spectrum():
     # plain FEAST with m0 well above m on a spectrum with eigenvalues on both
     # sides of I: the m0 - m outside directions of the subspace mix into in-I
