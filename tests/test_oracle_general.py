@@ -1,8 +1,9 @@
 """Pins of the general (non-Hermitian) FEAST oracle against what the
 mathematics fixes: the whole-circle quadrature at the center and against the
 Hermitian half-circle rule, the filter against the eigendecomposition of a
-planted matrix, the end result against planted spectra, one-round exactness
-on the full space, and the Hermitian special case."""
+planted matrix, the end result against planted spectra, the iterates round
+by round against subspace iteration on rho(A), one-round exactness on the
+full space, and the Hermitian special case."""
 import numpy as np
 import pytest
 
@@ -120,3 +121,43 @@ def test_hermitian_matrix_gives_the_hermitian_solvers_eigenvalues():
     assert g.status == 0 and h.status == 0 and g.lam.size == h.lam.size == 7
     assert np.max(np.abs(g.lam.imag)) < 1e-12
     assert np.max(np.abs(g.lam.real - h.lam)) < 1e-12 * 6.0
+
+
+@pytest.mark.parametrize("real", [False, True])
+def test_iterates_are_subspace_iteration_on_rho(real):
+    # FEAST for a general A = V diag(lam) V^{-1} is subspace iteration on
+    # rho(A) = V diag(rho(lam)) V^{-1} (Sect. I, the whole circle): round k
+    # works on span W_k, W_k = orth(rho(A) W_{k-1}), W_0 = X0, here from the
+    # planted eigendecomposition (LAPACK SVD and eig, no LU solve).  Every
+    # round's Ritz values in the disk (eigenvalues of W_k^H A W_k) and its
+    # maximum residual follow.
+    n, m_in, m0, n_c = 120, 10, 14, 8
+    c, r = (0.3 if real else 0.3 + 0.4j), 1.0
+    lam = spectrum_disk(7, n, m_in, center=c, radius=r, gap=0.15, outer=8.0, real_pairs=real)
+    A, V = planted_general(lam, 7, cond=8.0, real=real)
+    X0 = random_subspace(n, m0, 11, complex_=True)
+    z, w = circle_nodes(c, r, n_c)
+    rho = circle_filter(lam, z, w)
+    an = np.linalg.norm(A, 2)
+    full = feast_solve_general(A, c, r, m0, n_c, 1e-11, X0, max_iter=30, anorm=an)
+    assert full.status == 0 and full.iterations >= 3
+    Vi = np.linalg.inv(V)
+    W = X0.astype(np.complex128)
+    prev = None
+    for k in range(1, full.iterations + 1):
+        W = np.linalg.svd(V @ (rho[:, None] * (Vi @ W)), full_matrices=False)[0]
+        mu, Y = np.linalg.eig(W.conj().T @ A @ W)
+        X = W @ Y
+        X /= np.linalg.norm(X, axis=0)[None, :]
+        res = np.linalg.norm(A @ X - X * mu[None, :], axis=0) / an
+        ins = np.abs(mu - c) < r
+        want = np.array(sorted(mu[ins], key=lambda x: (x.real, x.imag)))
+        if k < full.iterations:
+            assert abs(full.history[k - 1] - res[ins].max()) <= 1e-6 * res[ins].max() + 1e-15
+        if k <= 2:
+            out = feast_solve_general(A, c, r, m0, n_c, 1e-11, X0, max_iter=k, anorm=an)
+            assert out.lam.size == want.size
+            assert np.abs(out.lam - want).max() <= 1e-12 * an
+            if prev is not None:
+                assert np.abs(prev - want).max() > 1e3 * 1e-12 * an   # the iterates move
+            prev = want
